@@ -1,0 +1,135 @@
+"""Pins for the oracle's grounded-slab Green's function.
+
+The paper does not print G~ (it cites it); these tests tie the oracle's formula
+to physics that is fixed independently of it: the textbook surface-wave
+dispersion relations of a grounded slab, the thin-slab static limit,
+rotational covariance of a dyadic in a horizontally isotropic medium, the
+radiation condition on the free-space branch, and the side of the real axis
+on which lossy-substrate poles lie (which decides the side of the contour of
+Eq. 8).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from oracle import green
+
+K0 = 2 * math.pi
+
+
+def tm_textbook(beta, eps_r, h, k0=K0):
+    """TM surface waves of a grounded slab: eps_r * a = k1 tan(k1 h), a = sqrt(beta^2 - k0^2)."""
+    a = math.sqrt(beta ** 2 - k0 ** 2)
+    k1 = math.sqrt(eps_r * k0 ** 2 - beta ** 2)
+    return eps_r * a * math.cos(k1 * h) - k1 * math.sin(k1 * h)
+
+
+def te_textbook(beta, eps_r, h, k0=K0):
+    """TE surface waves of a grounded slab: -k1 cot(k1 h) = a."""
+    a = math.sqrt(beta ** 2 - k0 ** 2)
+    k1 = math.sqrt(eps_r * k0 ** 2 - beta ** 2)
+    return k1 * math.cos(k1 * h) + a * math.sin(k1 * h)
+
+
+def _scale(beta, eps_r, h):
+    te, tm = green.te_tm(beta ** 2, eps_r, h, K0)
+    return abs(tm), abs(te)
+
+
+@pytest.mark.parametrize("eps_r,h,expect", [(2.2, 0.05, 1.0150), (4.4, 0.03, 1.0113)])
+def test_tm0_pole_is_zero_of_tm(eps_r, h, expect):
+    kd = K0 * math.sqrt(eps_r)
+    root = brentq(lambda b: tm_textbook(b, eps_r, h), K0 * (1 + 1e-12), kd * (1 - 1e-12),
+                  xtol=1e-15)
+    assert abs(root / K0 - expect) < 5e-4
+    te, tm = green.te_tm(np.array(root ** 2), eps_r, h, K0)
+    # Tm vanishes at the textbook root (relative to its size nearby), Te does not.
+    te_n, tm_n = green.te_tm(np.array((root * 1.01) ** 2), eps_r, h, K0)
+    assert abs(tm) < 1e-10 * abs(tm_n)
+    assert abs(te) > 1e-3 * abs(te_n)
+
+
+def test_te1_pole_thick_high_permittivity_slab():
+    eps_r, h = 10.0, 0.1
+    kd = K0 * math.sqrt(eps_r)
+    grid = np.linspace(K0 * (1 + 1e-9), kd * (1 - 1e-9), 20001)
+    vals = np.array([te_textbook(b, eps_r, h) for b in grid])
+    idx = np.nonzero(np.sign(vals[:-1]) != np.sign(vals[1:]))[0]
+    assert idx.size >= 1
+    root = brentq(lambda b: te_textbook(b, eps_r, h), grid[idx[0]], grid[idx[0] + 1], xtol=1e-15)
+    te, _ = green.te_tm(np.array(root ** 2), eps_r, h, K0)
+    te_n, _ = green.te_tm(np.array((root * 1.01) ** 2), eps_r, h, K0)
+    assert abs(te) < 1e-9 * abs(te_n)
+
+
+def test_free_space_branch_radiation_condition():
+    # propagating: k2 real positive; evanescent: k2 = -j sqrt(beta^2 - k0^2)
+    b = np.array([0.3, 0.9]) * K0
+    k2 = green.kz_free(b ** 2, K0)
+    assert np.allclose(k2, np.sqrt(K0 ** 2 - b ** 2), rtol=1e-14)
+    b = np.array([1.1, 3.0]) * K0
+    k2 = green.kz_free(b ** 2, K0)
+    assert np.allclose(k2, -1j * np.sqrt(b ** 2 - K0 ** 2), rtol=1e-14)
+    # upper half of the beta plane (the contour side): Im k2 < 0
+    bc = np.array([0.5, 1.0, 1.5]) * K0 + 0.05j
+    assert np.all(green.kz_free(bc ** 2, K0).imag < 0)
+
+
+def test_thin_slab_static_limit():
+    # h -> 0: G ~ -j Z0 k0 h I + j Z0 h k k^T / (eps_r k0)   (current sheet over ground)
+    eps_r = 3.0
+    kx = np.array([0.3, 1.7, 4.0]) * K0
+    ky = np.array([0.8, -0.4, 2.5]) * K0
+    errs = []
+    for h in (1e-4, 1e-5, 1e-6):
+        gxx, gxy, gyy = green.dyadic_green(kx, ky, eps_r, h, K0)
+        exx = -1j * green.Z0 * K0 * h + 1j * green.Z0 * h * kx * kx / (eps_r * K0)
+        eyy = -1j * green.Z0 * K0 * h + 1j * green.Z0 * h * ky * ky / (eps_r * K0)
+        exy = 1j * green.Z0 * h * kx * ky / (eps_r * K0)
+        scale = np.abs(exx) + np.abs(eyy)
+        errs.append(max(np.max(np.abs(gxx - exx) / scale), np.max(np.abs(gyy - eyy) / scale),
+                        np.max(np.abs(gxy - exy) / scale)))
+    # the relative deviation is first order in k0 h: it shrinks tenfold per decade of h
+    assert errs[-1] < 1e-5
+    assert 9.0 < errs[0] / errs[1] < 11.0 and 9.0 < errs[1] / errs[2] < 11.0
+
+
+def test_rotational_covariance():
+    # G(R k) = R G(k) R^T for any rotation (isotropic in the transverse plane); pins the
+    # sign and size of the off-diagonal term relative to the diagonal ones.
+    eps_r, h = 4.4, 0.03
+    k = np.array([1.3 * K0 + 0.02j, 0.7 * K0 + 0.01j])
+    for th in (0.3, 1.1, 2.5):
+        r = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        rk = r @ k
+        gxx, gxy, gyy = green.dyadic_green(k[0], k[1], eps_r, h, K0)
+        g = np.array([[gxx, gxy], [gxy, gyy]])
+        gxx2, gxy2, gyy2 = green.dyadic_green(rk[0], rk[1], eps_r, h, K0)
+        g2 = np.array([[gxx2, gxy2], [gxy2, gyy2]])
+        assert np.allclose(g2, r @ g @ r.T, rtol=1e-12, atol=1e-12 * np.abs(g).max())
+
+
+def test_lossy_pole_below_real_axis():
+    # With exp(+j w t) a lossy slab, eps_r (1 - j tan d), moves the TM0 pole below the real
+    # axis; the lossless limit of the real-axis integral therefore passes ABOVE the pole,
+    # which is the side the contour of Eq. 8 takes (beta_I >= 0).
+    eps_r, h = 2.2, 0.05
+    b = brentq(lambda x: tm_textbook(x, eps_r, h), K0 * (1 + 1e-12), K0 * math.sqrt(eps_r) * (1 - 1e-12))
+    eps_l = eps_r * (1 - 0.01j)
+    z = complex(b)
+    for _ in range(60):  # Newton on Tm(beta) with a complex-step-free finite difference
+        f = green.te_tm(np.array(z * z), eps_l, h, K0)[1]
+        d = 1e-7
+        fp = (green.te_tm(np.array((z + d) ** 2), eps_l, h, K0)[1] - f) / d
+        z = z - complex(f / fp)
+    assert abs(complex(green.te_tm(np.array(z * z), eps_l, h, K0)[1])) < 1e-9
+    assert z.imag < 0
+
+
+def test_vanishing_slab_gives_zero():
+    kx = np.array([0.5, 2.0]) * K0
+    ky = np.array([0.1, 1.0]) * K0
+    g = green.dyadic_green(kx, ky, 2.2, 0.0, K0)
+    assert all(np.all(np.abs(c) == 0) for c in g)
