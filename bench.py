@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the C-FFT hot path on GB300.
+
+Headline: C-FFT table samples/s on the rooftop-patch workload (200 rooftops,
+M = 4 MBFs, all 16 MBF pairs, eps_r 4.4, h 0.03 lambda0, contour N = 16384,
+|q| <= 16, 8192 rho points to 50 lambda0, FP32-mixed).  One step is one
+cfft_tabulate_reactions call (contour + Green's function, MBF spectra and
+harmonics, Taylor x pruned FFTs, back-projection) on inputs resident in HBM;
+the L2 cache is flushed between timed steps.  Beside it, the same metric end
+to end through the host-buffer C-ABI path, the reduced-matrix fill of the
+10,000-element irregular array (entries/s), the roofline of the dominant
+kernel, and the FP64 oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cfft|reference]
+Under torchrun every rank runs its own replica of the workload (the path
+shards into independent problems; no collective on the data path) and the
+slowest rank's time sets the whole-job throughput.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA pipe peak: 152 SMs x 128 lanes x 2 flops x clock."""
+    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def table_workload():
+    return workloads.patch_m4(precision="fp32")
+
+
+def fill_workload():
+    """Irregular array: 10,000 Poisson-disc elements (min spacing 0.5) in a disc of
+    radius 60 lambda0, rotations in {0, 90}; table of the patch element to
+    rho_max = 121 lambda0 with four rotation classes."""
+    wl = workloads.patch_m4(n=16384, n_rho=16384, rho_max=121.0, q_max=16, precision="fp32",
+                            rotation_classes=4)
+    pos, rot = workloads.irregular_array()
+    return wl, pos, rot
+
+
+def set_problem(ctx, wl):
+    s = wl.substrate
+    ctx.set_substrate(s.eps_r, s.h, s.k0)
+    el = wl.element
+    ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+    c = wl.contour
+    ctx.build_contour(c.n, c.beta_max, c.beta_p, c.height, -1)
+
+
+def table_samples(wl):
+    m = wl.element.n_mbf
+    classes = 3 if wl.rotation_classes == 4 else 1   # tabulated classes ((90,90) is derived)
+    return classes * m * m * (2 * wl.q_max + 1) * wl.n_rho
+
+
+def oracle_sample(wl, rows, workers):
+    """FP64 oracle on a bounded sample: harmonics at every contour node (needed by any
+    rho), Bessel sums for the given rows, all pairs and harmonics."""
+    from oracle import contour as oc, reaction as orx, spectra as osp
+    el = wl.element
+    bs = osp.BasisSet("rooftop", el.q, cx=el.cx, cy=el.cy, direction=el.direction,
+                      half_len=el.half_len, width=el.width)
+    c = wl.contour
+    nodes = oc.contour_nodes(c.n, c.beta_max, c.beta_p, c.height)
+    s = wl.substrate
+    hq = orx.harmonics(bs, nodes["beta_c"], wl.qs, 128, s.eps_r, s.h, s.k0, workers=workers)
+    z = orx.table_bessel(hq, wl.qs, nodes["beta_c"], nodes["weight"], wl.rho[rows])
+    m = el.n_mbf
+    return z.reshape(m * m, len(wl.qs), len(rows))
+
+
+def run_reference(args):
+    """The oracle timed on the host cores (rank 0 only)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = table_workload()
+    workers = max(1, min(32, os.cpu_count() or 1))
+    rows = np.linspace(0, wl.n_rho - 1, 8).astype(int)
+    # warm-up: imports and the worker pool start (a small call)
+    small = workloads.patch_m4(n=256, n_rho=16, rho_max=2.0, q_max=wl.q_max)
+    for _ in range(args.warmup):
+        oracle_sample(small, np.array([0, 5]), workers)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_sample(wl, rows, workers)
+        times.append(time.perf_counter() - t0)
+    samples = wl.element.n_mbf ** 2 * len(wl.qs) * len(rows)
+    total = sum(times)
+    value = samples * args.steps / total
+    sample_desc = ("all %d contour nodes x 128 angles of harmonics, Bessel sums for %d of %d rho rows, "
+                   "16 pairs x 33 harmonics" % (wl.contour.n, len(rows), wl.n_rho))
+    line = {"impl": "reference", "metric": "C-FFT table samples/s", "value": value,
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_desc(wl),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_desc(wl):
+    return {"workload": "patch-m4: 200 rooftops, M=4 (16 pairs), eps_r=4.4, h=0.03 lambda0, "
+                        "contour N=%d, |q|<=%d, %d rho points to %g lambda0, FP32-mixed"
+                        % (wl.contour.n, wl.q_max, wl.n_rho, wl.rho_max),
+            "table_samples_per_step": table_samples(wl), "l2": "flushed between timed steps",
+            "parallelism": "replicas"}
+
+
+def flush_l2(torch, buf):
+    buf.zero_()
+
+
+def bench_tabulation(torch, cfft, args, dev):
+    wl = table_workload()
+    ctx = cfft.Context(dev)
+    set_problem(ctx, wl)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    infos = []
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush_l2(torch, flush)
+        evs[k][0].record(stream)
+        ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 1)
+        evs[k][1].record(stream)
+        infos.append(ctx.info())
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    return wl, ctx, step_ms, infos, clk
+
+
+def bench_e2e(torch, cfft, args, dev, wl):
+    """Same metric through the host-buffer C-ABI path: element arrays from host memory,
+    table copied back to pinned host memory, inside the timed region."""
+    ctx = cfft.Context(dev)
+    el = wl.element
+    centers = np.ascontiguousarray(np.stack([el.cx, el.cy], 1))
+    h2d = centers.nbytes + el.direction.astype(np.int32).nbytes + el.half_len.nbytes + \
+        el.width.nbytes + el.q.astype(np.complex128).nbytes
+    out = None
+    times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = wl.substrate
+        ctx.set_substrate(s.eps_r, s.h, s.k0)
+        ctx.set_mbf_spectra(centers, el.direction, el.half_len, el.width, el.q)
+        c = wl.contour
+        ctx.build_contour(c.n, c.beta_max, c.beta_p, c.height, -1)
+        ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 1)
+        out = ctx.copy_table(out=out, host=True)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            times.append(t1 - t0)
+    d2h = out.numel() * out.element_size()
+    return {"value": table_samples(wl) * len(times) / sum(times), "unit": "samples/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}, out
+
+
+def bench_fill(torch, cfft, args, dev):
+    wl, pos, rot = fill_workload()
+    ctx = cfft.Context(dev)
+    set_problem(ctx, wl)
+    t0 = time.perf_counter()
+    ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 4)
+    tab_s = time.perf_counter() - t0
+    info = ctx.info()
+    a, m = len(pos), wl.element.n_mbf
+    z = torch.empty((a * m, a * m), dtype=torch.complex64, device=dev)
+    dpos = torch.tensor(pos, dtype=torch.float64, device=dev)
+    drot = torch.tensor(rot, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(1, min(args.warmup, 2))):
+        ctx.fill_reduced_matrix(dpos, drot, z)
+    steps = max(1, min(args.steps, 3))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        evs[k][0].record(stream)
+        ctx.fill_reduced_matrix(dpos, drot, z)   # 12.8 GB output: far larger than L2
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [x.elapsed_time(y) for x, y in evs]
+    entries = float(a * m) ** 2
+    res = {"metric": "Z-fill entries/s", "value": entries * steps / (sum(ms) / 1e3),
+           "unit": "entries/s", "ms_per_step": sum(ms) / steps,
+           "workload": "irregular array: A=%d Poisson-disc elements (min spacing 0.5) in a disc of "
+                       "radius 60 lambda0, rotations {0,90}, M=4, complex64 %dx%d, table to rho %g "
+                       "lambda0 (%d points, 4 rotation classes)" % (a, a * m, a * m, wl.rho_max, wl.n_rho),
+           "table_ms": 1e3 * tab_s, "table_info": {k: info[k] for k in
+                                                   ("taylor_order", "grid_half", "sigma", "fill_taps")}}
+    # fill roofline: FP32 pipe (interpolation + harmonic sum) vs HBM write of the matrix
+    taps = info["fill_taps"]
+    nh = 2 * wl.q_max + 1
+    flops_per_pair = m * m * nh * (4 * taps + 8)
+    sec = sum(ms) / steps / 1e3
+    res["alu_tflops"] = flops_per_pair * float(a) ** 2 / sec / 1e12
+    res["hbm_gbs_write"] = entries * 8 / sec / 1e9
+    del z
+    torch.cuda.empty_cache()
+    return res
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(torch, value):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([value], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return value
+
+
+def roofline(infos, wl, peaks, clk):
+    """Dominant kernel of the tabulation step and its fraction of the bounding pipe."""
+    inf = infos[-1]
+    ms = {k: float(np.mean([i["ms_" + k] for i in infos])) for k in
+          ("contour", "integrand", "fft", "backproject")}
+    dominant = max(ms, key=ms.get)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    m = wl.element.n_mbf
+    if dominant == "backproject":
+        flops = inf["work_bp_nodes"] * (4 * inf["bp_taps"] + 8)
+    elif dominant == "fft":
+        L = inf["sub_len"]
+        flops = inf["work_subffts"] * 5.0 * L * math.log2(L)
+    elif dominant == "integrand":
+        # complex GEMM of the MBF spectra (both sides) + kernel + harmonic DFT per point
+        flops = inf["work_points"] * (2 * 8.0 * inf["n_basis"] * m + m * m * (8.0 * inf["n_harm"] + 30.0))
+    else:
+        flops = wl.contour.n * 200.0
+    achieved = flops / (ms[dominant] / 1e3) / 1e12
+    return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_alu,
+            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
+            "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)"
+                         % peaks.get("sm_max_mhz", 2070.0),
+            "stage_ms": ms, "algorithmic_flops_per_launch": flops}
+
+
+def run_cfft(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    from paper_1404_7357_gb300 import cfft
+    peaks = load_peaks()
+
+    wl, ctx, step_ms, infos, clk = bench_tabulation(torch, cfft, args, dev)
+    total_s = max_over_ranks(torch, sum(step_ms) / 1e3)
+    samples = table_samples(wl)
+    value = samples * args.steps * world / total_s
+    e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
+    fill = None if args.skip_fill else bench_fill(torch, cfft, args, dev)
+    launches = int(sum(i["launches"] for i in infos))
+    line = {"metric": "C-FFT table samples/s", "value": value, "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_desc(wl),
+            "roofline": roofline(infos, wl, peaks, clk), "clocks": clk,
+            "gpu_launches": launches, "e2e": e2e, "info": infos[-1]}
+    if fill is not None:
+        fill["alu_frac"] = fill["alu_tflops"] / fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        line["fill"] = fill
+    line["peaks_source"] = peaks["_source"]
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        workers = max(1, min(32, os.cpu_count() or 1))
+        rows = np.linspace(0, wl.n_rho - 1, 8).astype(int)
+        t0 = time.perf_counter()
+        ref = oracle_sample(wl, rows, workers)
+        dt = time.perf_counter() - t0
+        ns = ref.size
+        line["cpu_baseline"] = {"value": ns / dt, "unit": "samples/s", "cores": workers,
+                                "kind": "oracle",
+                                "sample": "all %d contour nodes (harmonics), %d of %d rho rows, all "
+                                          "16 pairs x 33 harmonics; %.1f s" % (wl.contour.n, len(rows),
+                                                                               wl.n_rho, dt)}
+        got = host_table.numpy()[0][..., rows].astype(np.complex128)
+        err = np.abs(got - ref).reshape(ref.shape[0], -1).max(-1) / \
+            np.abs(ref).reshape(ref.shape[0], -1).max(-1)
+        line["parity"] = {"max_rel_err_vs_oracle": float(err.max()), "rows": rows.tolist(),
+                          "tolerance": 1e-5}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cfft", choices=["cfft", "reference"])
+    ap.add_argument("--skip-fill", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "cfft":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cfft(args)
+
+
+if __name__ == "__main__":
+    main()

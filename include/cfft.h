@@ -1,0 +1,232 @@
+/*
+ * cfft.h -- C ABI of the GB300 Contour-FFT (C-FFT) MBF reaction library.
+ *
+ * The library tabulates the substrate-related reaction terms between the
+ * Macro Basis Functions (MBFs) of one printed element on a grounded slab for
+ * all relative positions (Jha & Craeye, "Contour-FFT based spectral domain MBF
+ * analysis of large printed antenna arrays", Section III), and fills the
+ * reduced MoM matrix of an array of identical elements by interpolating that
+ * table (Section III-B-1 and III-B-3).
+ *
+ * The problem statement it follows (Section III-B-1): once the table exists
+ * for a given substrate and element, the reduced matrix of any array layout
+ * follows by low-order interpolation at every element pair's relative
+ * position (rho, phi).  Calls therefore follow the order
+ *     set_substrate -> set_mbf_spectra* -> build_contour -> tabulate_reactions
+ *     -> fill_reduced_matrix (any number of times, any layout)
+ * and a call out of this order returns CFFT_ERR_STATE.
+ *
+ * Conventions for every entry point:
+ *   - Lengths in any unit consistent with k0 (the tests use free-space
+ *     wavelengths, k0 = 2 pi).  Spectral variables are in 1/length.
+ *   - Time convention exp(+j omega t); the spectral kernel of Eq. 5 carries
+ *     exp(-i k . Delta) with Delta = r_test - r_basis = rho (cos phi, sin phi).
+ *   - Complex arrays are interleaved (re, im) pairs of the stated real type.
+ *   - "host" pointers are read during the call only and never retained.
+ *     "device" pointers must be CUDA device memory of the context's device;
+ *     the library reads/writes them in stream order on the context stream and
+ *     never frees them.  Buffers the library allocates itself (contour,
+ *     spectra, scratch, table) are owned by the context and released by
+ *     cfft_destroy.
+ *   - Every call is stream-ordered on the context's stream; the calls that
+ *     return results to the host (cfft_copy_table to host memory,
+ *     cfft_synchronize, the NaN/Inf check in cfft_tabulate_reactions)
+ *     synchronize that stream.
+ *   - No C++ exception crosses this boundary.  On failure a call returns a
+ *     non-zero cfft_status and cfft_last_error() describes it; the context
+ *     stays usable unless the status is CFFT_ERR_CUDA from a sticky device
+ *     error.
+ */
+#ifndef CFFT_H
+#define CFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cfft_ctx cfft_ctx; /* opaque, library-owned */
+
+typedef enum {
+  CFFT_OK = 0,
+  CFFT_ERR_ARG = 1,      /* invalid argument (null pointer, size, range) */
+  CFFT_ERR_STATE = 2,    /* call out of order (e.g. tabulate before contour) */
+  CFFT_ERR_OOM = 3,      /* device allocation failed */
+  CFFT_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+  CFFT_ERR_NUMERIC = 5,  /* NaN or Inf in a produced table */
+  CFFT_ERR_TIMEOUT = 6   /* a bounded device-side wait gave up */
+} cfft_status;
+
+typedef enum {
+  CFFT_FP64 = 0,        /* all arithmetic in float64, table complex128 */
+  CFFT_FP32_MIXED = 1   /* float32 spectra/FFT/back-projection, float64 contour,
+                           Green's function denominators and branch-point
+                           square roots; table complex64 */
+} cfft_precision;
+
+/* Tunables of the tabulation (cfft_set_option).  A value <= 0 restores the
+ * automatic choice, which depends on precision and element size:
+ *   N_ALPHA     angular samples for the azimuthal harmonics (multiple of 4)
+ *   SIGMA       zero-padding factor of the beta FFT (power of two >= 2)
+ *   BP_TAPS     Lagrange taps of the back-projection interpolation
+ *               (one of 4, 6, 8, 10, 12, 16, 20, 24)
+ *   FILL_TAPS   Lagrange taps of the fill interpolation in rho (even)
+ *   ALPHA_MARGIN extra angular nodes of the back-projection quadrature
+ *   CHECK_FINITE a value < 0 skips the NaN/Inf scan (and its stream sync)
+ *                at the end of cfft_tabulate_reactions                     */
+typedef enum {
+  CFFT_OPT_N_ALPHA = 0,
+  CFFT_OPT_SIGMA = 1,
+  CFFT_OPT_BP_TAPS = 2,
+  CFFT_OPT_FILL_TAPS = 3,
+  CFFT_OPT_ALPHA_MARGIN = 4,
+  CFFT_OPT_CHECK_FINITE = 5
+} cfft_option;
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Errors: CFFT_ERR_ARG (out == NULL), CFFT_ERR_CUDA (bad device). */
+cfft_status cfft_create(cfft_ctx** out, int device, void* cuda_stream);
+
+/* Release every buffer the context owns.  NULL is ignored. */
+void cfft_destroy(cfft_ctx* ctx);
+
+/* Message of the last failing call on this context (never NULL). */
+const char* cfft_last_error(const cfft_ctx* ctx);
+
+/* Grounded dielectric slab (Section II, Eq. 2: the layered medium of Z^l):
+ * relative permittivity eps_r > 0, thickness h >= 0, free-space wavenumber
+ * k0 > 0.  Invalidates any contour and table. */
+cfft_status cfft_set_substrate(cfft_ctx* ctx, double eps_r, double h, double k0);
+
+/* Element made of one x-directed cosine strip dipole of length `length` and
+ * width `width` centred at the origin (one MBF, M = 1).  Its spectrum is
+ * analytic (Section III-A).  Invalidates contour-independent caches. */
+cfft_status cfft_set_mbf_spectra_strip(cfft_ctx* ctx, double length, double width);
+
+/* Element made of n_basis rooftop basis functions combined into n_mbf MBFs
+ * by the coefficient matrix Q (Eq. 3 and Eq. 11, M~ = sum_j q_j^* F~_j):
+ *   centers  host, float64[2 * n_basis]: (x, y) of each rooftop centre,
+ *            relative to the element centre
+ *   dir      host, int32[n_basis]: 0 = x-directed, 1 = y-directed
+ *   half_len host, float64[n_basis]: half-length a of the triangle
+ *   width    host, float64[n_basis]: width w across the current
+ *   q        host, float64[2 * n_basis * n_mbf]: complex Q, row-major
+ *            [basis i][mbf a], interleaved (re, im)
+ * Limits: 1 <= n_basis <= 4096, 1 <= n_mbf <= 8.
+ * Errors: CFFT_ERR_ARG on null pointers or sizes out of range. */
+cfft_status cfft_set_mbf_spectra(cfft_ctx* ctx, int n_basis, const double* centers,
+                                 const int* dir, const double* half_len,
+                                 const double* width, int n_mbf, const double* q);
+
+/* Deformed contour of Eq. 8 (Fig. 1): n rectangle-rule samples (Eq. 23) at
+ * beta_R = (j + 1/2) beta_max / n, j = 0..n-1, with the parabola
+ * beta_I = 4 height beta_R (beta_p - beta_R) / beta_p^2 on [0, beta_p] and
+ * the real axis beyond; weight (1 + i d beta_I / d beta_R) beta_max / n.
+ * beta_max bounds the spectral integration (5 k_d in Section III-A);
+ * beta_p must exceed every surface-wave pole (> k0 sqrt(eps_r)).
+ * taylor_order is the highest power N_t kept in the Taylor expansion of the
+ * contour factor (Eq. 22); -1 chooses it from the precision's tolerance and
+ * the largest rho of the table at tabulation time.
+ * Limits: 16 <= n <= 1048576; 0 < beta_p < beta_max; height >= 0;
+ * -1 <= taylor_order <= 64.  Requires a substrate (else CFFT_ERR_STATE). */
+cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double beta_p,
+                               double height, int taylor_order);
+
+/* Override a tunable (see cfft_option); value <= 0 restores automatic. */
+cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value);
+
+/* Tabulate Z_ab,q(rho_r) for all MBF pairs (a, b), harmonics q = -q_max..q_max
+ * and rho_r = r * rho_max / (n_rho - 1), r = 0..n_rho-1:
+ *   Z'_ab(rho, phi) = sum_q Z_ab,q(rho) exp(i q phi)               (Eq. 9)
+ * computed by the C-FFT: MBF spectra along the contour (Eq. 11), the kernel
+ * H = M_t . G . M_b^* (Eq. 10), azimuthal harmonics, the Taylor expansion of
+ * the contour factor (Eq. 22), one zero-padded FFT per (pair, harmonic,
+ * Taylor term) (Eq. 23-24) and a back-projection over the angle to the
+ * uniform rho grid.
+ * rotation_classes = 1: elements unrotated (one class);
+ * rotation_classes = 4: element rotations in {0, 90 deg}; the table holds the
+ * classes (test, basis) = (0,0), (0,90), (90,0), (90,90) in that order.
+ * Limits: 0 <= q_max <= 64; 2 <= n_rho <= 1048576; rho_max > 0.
+ * Errors: CFFT_ERR_STATE (no substrate/element/contour), CFFT_ERR_ARG,
+ * CFFT_ERR_OOM, CFFT_ERR_NUMERIC (NaN/Inf produced). */
+cfft_status cfft_tabulate_reactions(cfft_ctx* ctx, int q_max, double rho_max, int n_rho,
+                                    cfft_precision precision, int rotation_classes);
+
+/* Borrow the table: *dev_ptr = device address (owned by ctx, valid until the
+ * next tabulate or destroy), shape = {classes, M*M, 2*q_max+1, n_rho}, row-
+ * major with pair index a*M + b, element type complex128 (precision FP64) or
+ * complex64 (FP32_MIXED) as *is_complex128 says.  CFFT_ERR_STATE if no table. */
+cfft_status cfft_get_table(const cfft_ctx* ctx, const void** dev_ptr, int64_t shape[4],
+                           int* is_complex128);
+
+/* Copy the table into caller memory `dst` (bytes must equal the table size);
+ * dst_is_host != 0: dst is host memory and the call synchronizes the stream;
+ * dst_is_host == 0: dst is device memory (stream-ordered copy). */
+cfft_status cfft_copy_table(const cfft_ctx* ctx, void* dst, int64_t bytes, int dst_is_host);
+
+/* Fill the dense reduced matrix of n_elements identical elements (Eq. 3 per
+ * block, Eq. 9 per entry, interpolated in the table; Section III-B-3):
+ *   Z_out[(m*M + a) * ld + n*M + b] = sum_q exp(i q phi_mn) Z^{cls}_ab,q(rho_mn)
+ * with (rho_mn, phi_mn) the polar form of r_m - r_n (m = test element,
+ * n = basis element) and cls the rotation class of (rot[m], rot[n]).  The
+ * diagonal blocks (m = n) take the table at rho = 0.
+ *   pos_xy  device, float64[2 * n_elements]: element centres (x, y)
+ *   rot     device, int32[n_elements]: 0 or 1 (0 or 90 deg); may be NULL when
+ *           the table has one class (all elements unrotated)
+ *   z_out   device, caller-owned: complex128 (out_complex128 != 0) or
+ *           complex64, at least n_elements*M rows of ld entries
+ *   ld      row stride in complex entries, >= n_elements * M
+ * Requires a table (CFFT_ERR_STATE).  A pair farther apart than the table's
+ * rho_max makes the call return CFFT_ERR_ARG (after the kernel ran; the
+ * affected entries are zero).  Stream-ordered; synchronizes for that check. */
+cfft_status cfft_fill_reduced_matrix(cfft_ctx* ctx, int n_elements, const double* pos_xy,
+                                     const int* rot, void* z_out, int64_t ld,
+                                     int out_complex128);
+
+/* Same as cfft_fill_reduced_matrix with HOST arrays: pos_xy, rot and z_out
+ * are host memory; the call copies them to and from the device through
+ * context-owned buffers and synchronizes. */
+cfft_status cfft_fill_reduced_matrix_host(cfft_ctx* ctx, int n_elements, const double* pos_xy,
+                                          const int* rot, void* z_out, int64_t ld,
+                                          int out_complex128);
+
+/* Diagnostics of the last tabulation (host values): taylor order used,
+ * n_alpha, sigma, FFT length, sub-FFT length, grid half-width K, back-
+ * projection taps, fill taps, series count, the device time of each stage in
+ * milliseconds (contour, integrand, fft, backproject; CUDA events on the
+ * context stream), the number of kernels launched, and the work of each
+ * stage: integrand points (nodes x angles), sub-FFTs run (each of length
+ * sub_len), and back-projection node evaluations (series x rows x angles). */
+typedef struct {
+  int taylor_order, n_alpha, sigma, fft_len, sub_len, grid_half, bp_taps, fill_taps;
+  int series, classes, n_pairs, n_harm;
+  double delta_s, ms_contour, ms_integrand, ms_fft, ms_backproject;
+  int launches, n_basis;
+  double work_points, work_subffts, work_bp_nodes;
+} cfft_info;
+cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
+
+/* Device address of an intermediate buffer of the last tabulation, for
+ * stage-by-stage verification:
+ *   "harmonics": the contour integrand H_ab,q(beta_j) beta_c,j w_j,
+ *                shape {computed classes, M*M, 2*q_max+1, n}
+ *   "grid":      the Taylor-summed transform on s_k = k delta_s, k = -K..K,
+ *                demodulated: g_ab,q(s_k) exp(i beta_max s_k / 2),
+ *                shape {computed classes, M*M, 2*q_max+1, 2K+1}
+ *   "contour":   the nodes beta_c,j (complex128), shape {1, n, 1, 1}
+ * "computed classes" is 1, or 3 with four rotation classes (the (90, 90)
+ * class is derived from (0, 0)).  Element type as the table's except
+ * "contour".  Borrowed; valid until the next tabulate. */
+cfft_status cfft_debug_buffer(const cfft_ctx* ctx, const char* name, const void** dev_ptr,
+                              int64_t shape[4]);
+
+/* Wait for all work issued on the context stream. */
+cfft_status cfft_synchronize(cfft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFFT_H */

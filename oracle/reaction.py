@@ -58,14 +58,39 @@ def kernel(basis, kx, ky, eps_r, h, k0, theta_t=0.0, theta_b=0.0, green_fn=None)
     return tx[:, None] * gx[None, :] + ty[:, None] * gy[None, :]
 
 
+def _harmonics_slice(args):
+    return harmonics(*args)
+
+
 def harmonics(basis, beta, qs, n_alpha, eps_r, h, k0, theta_t=0.0, theta_b=0.0,
-              green_fn=None, chunk=2048):
+              green_fn=None, chunk=256, workers=None):
     """H_ab,q(beta_j) by the n_alpha-point trapezoid rule in alpha.
 
     beta: complex array (n,).  Returns (M, M, len(qs), n) complex128.
+    workers > 1 splits the nodes over that many spawned processes (each node is
+    independent; the arithmetic per node is unchanged).
     """
     beta = np.asarray(beta, dtype=np.complex128)
     qs = np.asarray(qs)
+    if workers and workers > 1 and beta.size > 4 * chunk:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import os
+        parts = np.array_split(beta, workers * 4)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+        try:
+            with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+                res = list(ex.map(_harmonics_slice,
+                                  [(basis, p, qs, n_alpha, eps_r, h, k0, theta_t, theta_b,
+                                    green_fn, chunk, None) for p in parts]))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        return np.concatenate(res, axis=-1)
     alpha = 2.0 * np.pi * np.arange(n_alpha) / n_alpha
     ca, sa = np.cos(alpha), np.sin(alpha)
     dft = np.exp(-1j * np.outer(alpha, qs)) / n_alpha          # (n_alpha, nq)

@@ -1,0 +1,227 @@
+"""ctypes binding of libcfft.so (include/cfft.h), argument marshalling only.
+
+Every method maps to one C entry point of the same name.  Device buffers are
+torch CUDA tensors (PyTorch supplies device memory and streams); host buffers
+are numpy arrays.  No part of the method runs here: a missing or unloadable
+library raises ``CfftLibraryError`` at import time.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcfft.so")
+
+CFFT_FP64 = 0
+CFFT_FP32_MIXED = 1
+OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE = range(6)
+STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
+          4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
+
+# every symbol include/cfft.h declares
+EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate",
+           "cfft_set_mbf_spectra_strip", "cfft_set_mbf_spectra", "cfft_build_contour",
+           "cfft_set_option", "cfft_tabulate_reactions", "cfft_get_table", "cfft_copy_table",
+           "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
+           "cfft_debug_buffer", "cfft_synchronize"]
+
+
+class CfftLibraryError(ImportError):
+    pass
+
+
+class CfftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("taylor_order", "n_alpha", "sigma", "fft_len", "sub_len", "grid_half", "bp_taps",
+                 "fill_taps", "series", "classes", "n_pairs", "n_harm")] + \
+               [(n, ctypes.c_double) for n in
+                ("delta_s", "ms_contour", "ms_integrand", "ms_fft", "ms_backproject")] + \
+               [(n, ctypes.c_int) for n in ("launches", "n_basis")] + \
+               [(n, ctypes.c_double) for n in ("work_points", "work_subffts", "work_bp_nodes")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise CfftLibraryError("libcfft.so not built (run __graft_entry__.build()): %s" % LIB_PATH)
+    try:
+        lib = ctypes.CDLL(LIB_PATH)
+    except OSError as e:
+        raise CfftLibraryError("cannot load %s: %s" % (LIB_PATH, e))
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "cfft_create": ([ctypes.POINTER(P), I, P], I),
+        "cfft_destroy": ([P], None),
+        "cfft_last_error": ([P], ctypes.c_char_p),
+        "cfft_set_substrate": ([P, D, D, D], I),
+        "cfft_set_mbf_spectra_strip": ([P, D, D], I),
+        "cfft_set_mbf_spectra": ([P, I, P, P, P, P, I, P], I),
+        "cfft_build_contour": ([P, I, D, D, D, I], I),
+        "cfft_set_option": ([P, I, D], I),
+        "cfft_tabulate_reactions": ([P, I, D, I, I, I], I),
+        "cfft_get_table": ([P, ctypes.POINTER(P), ctypes.POINTER(L), ctypes.POINTER(I)], I),
+        "cfft_copy_table": ([P, P, L, I], I),
+        "cfft_fill_reduced_matrix": ([P, I, P, P, P, L, I], I),
+        "cfft_fill_reduced_matrix_host": ([P, I, P, P, P, L, I], I),
+        "cfft_get_info": ([P, ctypes.POINTER(Info)], I),
+        "cfft_debug_buffer": ([P, ctypes.c_char_p, ctypes.POINTER(P), ctypes.POINTER(L)], I),
+        "cfft_synchronize": ([P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class _DeviceArray:
+    """Zero-copy view of a borrowed device buffer for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+class Context:
+    """One cfft_ctx on a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.device = device
+        self._h = ctypes.c_void_p()
+        st = _lib.cfft_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(handle))
+        if st != 0:
+            raise CfftError(st, "cfft_create failed")
+
+    def close(self):
+        if self._h:
+            _lib.cfft_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise CfftError(st, _lib.cfft_last_error(self._h).decode())
+
+    # ---- problem description
+    def set_substrate(self, eps_r, h, k0):
+        self._check(_lib.cfft_set_substrate(self._h, eps_r, h, k0))
+
+    def set_mbf_spectra_strip(self, length, width):
+        self._check(_lib.cfft_set_mbf_spectra_strip(self._h, length, width))
+
+    def set_mbf_spectra(self, centers, direction, half_len, width, q):
+        centers = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 2)
+        direction = np.ascontiguousarray(direction, dtype=np.int32)
+        half_len = np.ascontiguousarray(half_len, dtype=np.float64)
+        width = np.ascontiguousarray(width, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=np.complex128)
+        b, m = q.shape
+        self._check(_lib.cfft_set_mbf_spectra(self._h, b, _ptr(centers), _ptr(direction),
+                                              _ptr(half_len), _ptr(width), m, _ptr(q)))
+
+    def build_contour(self, n, beta_max, beta_p, height, taylor_order=-1):
+        self._check(_lib.cfft_build_contour(self._h, n, beta_max, beta_p, height, taylor_order))
+
+    def set_option(self, key, value):
+        self._check(_lib.cfft_set_option(self._h, key, float(value)))
+
+    def tabulate_reactions(self, q_max, rho_max, n_rho, precision, rotation_classes=1):
+        self._check(_lib.cfft_tabulate_reactions(self._h, q_max, rho_max, n_rho, precision,
+                                                 rotation_classes))
+
+    # ---- results
+    def table_shape(self):
+        ptr = ctypes.c_void_p()
+        shape = (ctypes.c_int64 * 4)()
+        is128 = ctypes.c_int()
+        self._check(_lib.cfft_get_table(self._h, ctypes.byref(ptr), shape, ctypes.byref(is128)))
+        return tuple(shape), bool(is128.value), ptr.value
+
+    def get_table(self):
+        """Borrowed zero-copy torch view of the context-owned table."""
+        shape, is128, ptr = self.table_shape()
+        return self._torch.as_tensor(_DeviceArray(ptr, shape, "<c16" if is128 else "<c8"),
+                                     device="cuda:%d" % self.device)
+
+    def copy_table(self, out=None, host=False):
+        shape, is128, _ = self.table_shape()
+        torch = self._torch
+        dt = torch.complex128 if is128 else torch.complex64
+        if out is None:
+            out = (torch.empty(shape, dtype=dt, pin_memory=True) if host
+                   else torch.empty(shape, dtype=dt, device="cuda:%d" % self.device))
+        self._check(_lib.cfft_copy_table(self._h, ctypes.c_void_p(out.data_ptr()),
+                                         out.numel() * out.element_size(), int(not out.is_cuda)))
+        return out
+
+    def fill_reduced_matrix(self, pos, rot, out, out_complex128=None):
+        """pos: cuda float64 (A, 2); rot: cuda int32 (A,) or None; out: cuda complex (A*M, ld)."""
+        torch = self._torch
+        assert pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()
+        if rot is not None:
+            assert rot.is_cuda and rot.dtype == torch.int32 and rot.is_contiguous()
+        assert out.is_cuda and out.stride(-1) == 1
+        is128 = out.dtype == torch.complex128 if out_complex128 is None else out_complex128
+        self._check(_lib.cfft_fill_reduced_matrix(
+            self._h, pos.shape[0], ctypes.c_void_p(pos.data_ptr()),
+            ctypes.c_void_p(rot.data_ptr() if rot is not None else 0),
+            ctypes.c_void_p(out.data_ptr()), out.stride(0), int(is128)))
+        return out
+
+    def fill_reduced_matrix_host(self, pos, rot, out):
+        """Host variant: numpy (or pinned torch CPU) arrays in and out."""
+        def addr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        is128 = str(out.dtype).endswith("complex128")
+        ld = out.stride(0) if hasattr(out, "data_ptr") else out.strides[0] // out.itemsize
+        self._check(_lib.cfft_fill_reduced_matrix_host(
+            self._h, len(pos), ctypes.c_void_p(addr(pos)),
+            ctypes.c_void_p(addr(rot) if rot is not None else 0), ctypes.c_void_p(addr(out)),
+            ld, int(is128)))
+        return out
+
+    def info(self):
+        inf = Info()
+        self._check(_lib.cfft_get_info(self._h, ctypes.byref(inf)))
+        return {n: getattr(inf, n) for n, _ in Info._fields_}
+
+    def debug_buffer(self, name):
+        """Copy of an intermediate device buffer ("harmonics", "grid", "contour")."""
+        ptr = ctypes.c_void_p()
+        shape = (ctypes.c_int64 * 4)()
+        self._check(_lib.cfft_debug_buffer(self._h, name.encode(), ctypes.byref(ptr), shape))
+        _, is128, _ = self.table_shape()
+        ts = "<c16" if (is128 or name == "contour") else "<c8"
+        view = self._torch.as_tensor(_DeviceArray(ptr.value, tuple(shape), ts),
+                                     device="cuda:%d" % self.device)
+        return view.clone()
+
+    def synchronize(self):
+        self._check(_lib.cfft_synchronize(self._h))

@@ -1,0 +1,235 @@
+// Shared device/host helpers of the GB300 C-FFT kernels: a small complex type,
+// precision-overloaded math, and the kernel argument structs.  Nothing here
+// is specific to one stage; every formula lives in the kernel that uses it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cfft {
+
+template <class T>
+struct alignas(2 * sizeof(T)) cpx {
+  T re, im;
+};
+
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> mk(T r, T i) {
+  cpx<T> z;
+  z.re = r;
+  z.im = i;
+  return z;
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) {
+  return mk(a.re + b.re, a.im + b.im);
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) {
+  return mk(a.re - b.re, a.im - b.im);
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) {
+  return mk(s * a.re, s * a.im);
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> conj(cpx<T> a) {
+  return mk(a.re, -a.im);
+}
+// a += b * c
+template <class T>
+__host__ __device__ __forceinline__ void cmac(cpx<T>& a, cpx<T> b, cpx<T> c) {
+  a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+  a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+// a += conj(b) * c
+template <class T>
+__host__ __device__ __forceinline__ void cmac_conj(cpx<T>& a, cpx<T> b, cpx<T> c) {
+  a.re = fma(b.re, c.re, fma(b.im, c.im, a.re));
+  a.im = fma(b.re, c.im, fma(-b.im, c.re, a.im));
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> cdiv(cpx<T> a, cpx<T> b) {
+  // Smith's algorithm
+  if (fabs(b.re) >= fabs(b.im)) {
+    T r = b.im / b.re, d = b.re + b.im * r;
+    return mk((a.re + a.im * r) / d, (a.im - a.re * r) / d);
+  }
+  T r = b.re / b.im, d = b.im + b.re * r;
+  return mk((a.re * r + a.im) / d, (a.im * r - a.re) / d);
+}
+template <class TO, class TI>
+__host__ __device__ __forceinline__ cpx<TO> ccast(cpx<TI> a) {
+  return mk<TO>((TO)a.re, (TO)a.im);
+}
+
+// precision-overloaded accurate math (never the fast-math intrinsics)
+__device__ __forceinline__ void sincospi_(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float cospi_(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_(double x) { return cospi(x); }
+
+// e^{i pi x} with x reduced exactly modulo 2 in float64 first
+template <class T>
+__device__ __forceinline__ cpx<T> expipi(double x) {
+  double r = x - 2.0 * floor(0.5 * x);  // [0, 2)
+  T s, c;
+  sincospi_((T)r, &s, &c);
+  return mk(c, s);
+}
+
+// sin(z), cos(z) for complex z
+template <class T>
+__device__ __forceinline__ void csincos(cpx<T> z, cpx<T>* sz, cpx<T>* cz) {
+  T s, c;
+  sincos_(z.re, &s, &c);
+  T ep = exp_(z.im), em = exp_(-z.im);
+  T ch = (T)0.5 * (ep + em);
+  T sh = (T)0.5 * (ep - em);
+  *sz = mk(s * ch, c * sh);
+  *cz = mk(c * ch, -s * sh);
+}
+
+// sin(z)/z for complex z (series near zero)
+template <class T>
+__device__ __forceinline__ cpx<T> csinc(cpx<T> z) {
+  T a2 = z.re * z.re + z.im * z.im;
+  if (a2 < (T)1e-4) {
+    cpx<T> z2 = z * z;
+    // 1 - z^2/6 + z^4/120 - z^6/5040
+    cpx<T> t = mk((T)(-1.0 / 5040.0) * z2.re, (T)(-1.0 / 5040.0) * z2.im);
+    t = mk(t.re + (T)(1.0 / 120.0), t.im);
+    t = t * z2;
+    t = mk(t.re - (T)(1.0 / 6.0), t.im);
+    t = t * z2;
+    return mk(t.re + (T)1, t.im);
+  }
+  cpx<T> s, c;
+  csincos(z, &s, &c);
+  return cdiv(s, z);
+}
+
+// principal complex square root
+template <class T>
+__device__ __forceinline__ cpx<T> csqrt_(cpx<T> z) {
+  T r = hypot(z.re, z.im);
+  if (r == (T)0) return mk((T)0, (T)0);
+  if (z.re >= (T)0) {
+    T t = sqrt((T)0.5 * (r + z.re));
+    return mk(t, z.im / ((T)2 * t));
+  }
+  T t = sqrt((T)0.5 * (r - z.re));
+  return mk(fabs(z.im) / ((T)2 * t), copysign(t, z.im));
+}
+
+// ---------------------------------------------------------------------------
+// kernel arguments
+
+struct ContourArgs {
+  int n;
+  double beta_max, beta_p, height, step;  // step = beta_max / n
+  double eps_r, hs, k0;
+};
+
+// per-node contour data written by the contour kernel (float64 throughout)
+struct ContourData {
+  double2* beta_c;  // beta_R + i beta_I
+  double2* weight;  // step * (1 + i dbeta_I/dbeta_R)
+  double2* bw;      // beta_c * weight  (the factor of Eq. 9's beta d beta)
+  double* bi_rel;   // beta_I / height  (0 beyond beta_p); in [0, 1]
+  double2* green_p; // G = P I - R k k^T  (P, R: functions of beta only)
+  double2* green_r; // R * beta_c^2
+};
+
+struct ShapeClass {
+  int kind;      // 0 = rooftop, 1 = cosine strip
+  int dir;       // 0 = x, 1 = y
+  int begin;     // basis range [begin, end) of this class (bases sorted by class)
+  int end;
+  double p1, p2; // rooftop: half-length, width; strip: length, width
+};
+
+constexpr int kMaxShapeClasses = 32;
+constexpr int kMaxBasis = 4096;
+
+template <class T>
+struct IntegrandArgs {
+  int n, n_alpha, q_max, n_cls;  // n_cls computed classes (1 or 3)
+  int n_mbf;                      // real MBF count (q holds a padded column count)
+  int n_shape, n_basis;
+  const ShapeClass* shapes;       // device, n_shape
+  const T* bx;                    // device, basis centres x (sorted by class)
+  const T* by;
+  const cpx<T>* q;                // device, [n_basis][M padded]
+  const double2* beta_c;
+  const double2* bw;
+  const double2* green_p;
+  const double2* green_r;
+  cpx<T>* y;                      // out [cls][pair][qi][n]
+};
+
+template <class T>
+struct FftArgs {
+  int series, n, sub_len, log2_sub, n_sub;   // n_sub = D = P / sub_len
+  int64_t fft_len;                            // P = sigma * n
+  int grid_half;                              // K
+  int taylor;                                 // N_t
+  int n_active;                               // nodes with beta_I > 0 (prefix)
+  int sigma;
+  double ds_height;                           // delta_s * height  (Taylor variable scale)
+  const cpx<T>* y;                            // [series][n]
+  const double* bi_rel;                       // [n]
+  const cpx<T>* twiddle;                      // [sub_len] e^{-2 pi i t / sub_len}
+  cpx<T>* grid;                               // [series][2K+1]
+};
+
+template <class T>
+struct BackprojArgs {
+  int series_per_q;        // classes * pairs
+  int n_harm, q_max, n_rho, grid_half, sigma, taps, group, rchunk;
+  double d_rho, d_s;       // rho step, s step
+  double beta_abs_max;     // max |beta_c| (angular content of the integrand)
+  double alpha_margin;
+  const cpx<T>* grid;      // [series][2K+1]   series = (cls*pairs + pair) * n_harm + qi
+  cpx<T>* table;           // [series][n_rho]
+};
+
+template <class T, class TO>
+struct FillArgs {
+  int n_el, n_mbf, q_max, n_harm, n_rho, taps, n_cls;
+  double inv_d_rho, rho_max;
+  int64_t ld;
+  const cpx<T>* table;     // [cls][pair][qi][r]
+  const double* pos;       // [2 * n_el]
+  const int* rot;          // [n_el] or null
+  cpx<TO>* z;              // [(m*M + a) * ld + n*M + b]
+  int* err;                // set when a pair lies beyond rho_max
+};
+
+// host launchers (one translation unit per stage)
+void launch_contour(const ContourArgs& a, const ContourData& d, cudaStream_t s);
+template <class T>
+void launch_twiddle(cpx<T>* tw, int len, cudaStream_t s);
+template <class T>
+cudaError_t launch_integrand(const IntegrandArgs<T>& a, int n_mbf_padded, cudaStream_t s);
+template <class T>
+cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s);
+template <class T>
+cudaError_t launch_backproject(const BackprojArgs<T>& a, cudaStream_t s);
+template <class T>
+void launch_class_phase(cpx<T>* table, int pairs, int n_harm, int q_max, int n_rho,
+                        cudaStream_t s);
+template <class T>
+void launch_nonfinite(const cpx<T>* buf, int64_t count, int* flag, cudaStream_t s);
+template <class T, class TO>
+cudaError_t launch_fill(const FillArgs<T, TO>& a, cudaStream_t s);
+
+}  // namespace cfft

@@ -1,0 +1,137 @@
+// Contour nodes (Eq. 8) and the grounded-slab Green's function along them.
+//
+// One thread per rectangle-rule node j (Eq. 23): beta_R = (j + 1/2) step,
+// beta_I the parabola of peak `height` on [0, beta_p] (Fig. 1), and the
+// Jacobian weight step * (1 + i dbeta_I/dbeta_R).  The grounded-slab dyadic
+// of Eq. 6/10 is written as G = P(beta) I - R(beta) k k^T: for a horizontally
+// isotropic slab every tangential dyadic has this form, so only two scalars
+// per node are needed and the angular dependence enters through k alone.
+// With exp(+j w t), k1 = sqrt(eps_r k0^2 - beta^2) (any branch: G is even in
+// k1), k2 = -j sqrt(beta^2 - k0^2) (Im k2 <= 0), c = cos k1 h, s = sin k1 h:
+//   Te = k1 c + j k2 s,  Tm = eps_r k2 c + j k1 s   (TE / TM denominators)
+//   P = -j Z0/k0 s (eps_r k0^2 k2 c + j k0^2 k1 s) / (Te Tm)
+//   R = -j Z0/k0 s (k2 c + j k1 s) / (Te Tm)
+// Everything here is float64: the denominators near the surface-wave poles and
+// the branch-point square roots are where float32 loses the most digits.
+#include "cfft_common.cuh"
+
+namespace cfft {
+
+namespace {
+
+constexpr double kEta0 = 376.730313668;  // free-space wave impedance, ohm
+
+__global__ void contour_kernel(ContourArgs a, ContourData d) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n) return;
+  double br = (j + 0.5) * a.step;
+  double bi = 0.0, slope = 0.0;
+  if (br < a.beta_p) {
+    double ip2 = 1.0 / (a.beta_p * a.beta_p);
+    bi = 4.0 * a.height * br * (a.beta_p - br) * ip2;
+    slope = 4.0 * a.height * (a.beta_p - 2.0 * br) * ip2;
+  }
+  cpx<double> bc = mk(br, bi);
+  cpx<double> w = mk(a.step, a.step * slope);
+  cpx<double> b2 = bc * bc;
+  double k02 = a.k0 * a.k0;
+  cpx<double> k1 = csqrt_(mk(a.eps_r * k02 - b2.re, -b2.im));
+  cpx<double> arg2 = mk(b2.re - k02, b2.im);
+  if (arg2.im == 0.0) arg2.im = 0.0;  // +0: real beta < k0 gives k2 > 0 (outgoing)
+  cpx<double> r2 = csqrt_(arg2);
+  cpx<double> k2 = mk(r2.im, -r2.re);  // -j * sqrt(.)
+  cpx<double> sn, cs;
+  csincos(mk(k1.re * a.hs, k1.im * a.hs), &sn, &cs);
+  cpx<double> j1 = mk(0.0, 1.0);
+  cpx<double> te = k1 * cs + j1 * (k2 * sn);
+  cpx<double> tm = a.eps_r * (k2 * cs) + j1 * (k1 * sn);
+  // C = -j eta0/k0 * s / (Te Tm)
+  cpx<double> cfac = cdiv(mk(0.0, -kEta0 / a.k0) * sn, te * tm);
+  cpx<double> p = cfac * ((a.eps_r * k02) * (k2 * cs) + j1 * (k02 * (k1 * sn)));
+  cpx<double> r = cfac * (k2 * cs + j1 * (k1 * sn));
+  d.beta_c[j] = make_double2(bc.re, bc.im);
+  d.weight[j] = make_double2(w.re, w.im);
+  cpx<double> bw = bc * w;
+  d.bw[j] = make_double2(bw.re, bw.im);
+  d.bi_rel[j] = a.height > 0.0 ? bi / a.height : 0.0;
+  d.green_p[j] = make_double2(p.re, p.im);
+  cpx<double> rb2 = r * b2;  // R beta_c^2: the k k^T term is R beta_c^2 u u^T
+  d.green_r[j] = make_double2(rb2.re, rb2.im);
+}
+
+template <class T>
+__global__ void twiddle_kernel(cpx<T>* tw, int len) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  double s, c;
+  sincospi(-2.0 * (double)t / (double)len, &s, &c);
+  tw[t] = mk((T)c, (T)s);
+}
+
+// table of class (90, 90) = class (0, 0) times (-i)^q: both elements rotated by
+// the same angle theta multiply harmonic q by exp(-i q theta)
+template <class T>
+__global__ void class_phase_kernel(cpx<T>* table, int pairs, int n_harm, int q_max,
+                                   int n_rho) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t per_class = (int64_t)pairs * n_harm * n_rho;
+  if (idx >= per_class) return;
+  int qi = (int)((idx / n_rho) % n_harm);
+  int q = qi - q_max;
+  int m = ((q % 4) + 4) % 4;  // (-i)^q = (-i)^(q mod 4)
+  cpx<T> v = table[idx];
+  cpx<T> o;
+  if (m == 0) o = v;
+  else if (m == 1) o = mk(v.im, -v.re);     // -i v
+  else if (m == 2) o = mk(-v.re, -v.im);    // -v
+  else o = mk(-v.im, v.re);                 // +i v
+  table[3 * per_class + idx] = o;
+}
+
+template <class T>
+__global__ void nonfinite_kernel(const cpx<T>* buf, int64_t count, int* flag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (; i < count; i += stride) {
+    cpx<T> v = buf[i];
+    bad |= !isfinite(v.re) || !isfinite(v.im);
+  }
+  if (bad) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+void launch_contour(const ContourArgs& a, const ContourData& d, cudaStream_t s) {
+  contour_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a, d);
+}
+
+template <class T>
+void launch_twiddle(cpx<T>* tw, int len, cudaStream_t s) {
+  twiddle_kernel<T><<<(len + 255) / 256, 256, 0, s>>>(tw, len);
+}
+
+template <class T>
+void launch_class_phase(cpx<T>* table, int pairs, int n_harm, int q_max, int n_rho,
+                        cudaStream_t s) {
+  int64_t n = (int64_t)pairs * n_harm * n_rho;
+  class_phase_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(table, pairs, n_harm,
+                                                                     q_max, n_rho);
+}
+
+template <class T>
+void launch_nonfinite(const cpx<T>* buf, int64_t count, int* flag, cudaStream_t s) {
+  int blocks = (int)((count + 255) / 256);
+  if (blocks > 4 * 152) blocks = 4 * 152;
+  if (blocks < 1) blocks = 1;
+  nonfinite_kernel<T><<<blocks, 256, 0, s>>>(buf, count, flag);
+}
+
+template void launch_twiddle<float>(cpx<float>*, int, cudaStream_t);
+template void launch_twiddle<double>(cpx<double>*, int, cudaStream_t);
+template void launch_class_phase<float>(cpx<float>*, int, int, int, int, cudaStream_t);
+template void launch_class_phase<double>(cpx<double>*, int, int, int, int, cudaStream_t);
+template void launch_nonfinite<float>(const cpx<float>*, int64_t, int*, cudaStream_t);
+template void launch_nonfinite<double>(const cpx<double>*, int64_t, int*, cudaStream_t);
+
+}  // namespace cfft
