@@ -225,6 +225,45 @@ cfft_status cfft_debug_buffer(const cfft_ctx* ctx, const char* name, const void*
 /* Wait for all work issued on the context stream. */
 cfft_status cfft_synchronize(cfft_ctx* ctx);
 
+/* Allocation-free back-projection.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code that runs
+ * while a CUDA graph is being captured, plug-ins whose host application owns
+ * every device allocation, real-time loops that cannot afford an allocation
+ * that may synchronize the device.  It runs the back-projection stage of
+ * cfft_tabulate_reactions on caller-owned buffers and allocates nothing:
+ * its scratch (angular node counts, offsets and cosines for every chunk of
+ * 32 rho rows) lives in one 8 MiB device array inside the library, present
+ * on every GPU that loads the library until the process exits.
+ *   grid    device, input: [series][2*grid_half+1] with series =
+ *           g * (2*q_max+1) + (q + q_max), g < series_per_q -- the layout of
+ *           cfft_debug_buffer("grid"): the transform in beta on s_k =
+ *           k * delta_s, k = -grid_half..grid_half, demodulated by
+ *           exp(i pi k / sigma), as the FFT stage writes it
+ *   table   device, output: [series][n_rho], rho_r = r * rho_max / (n_rho-1)
+ *   complex128 != 0: both buffers complex128, else complex64
+ *   sigma, taps, delta_s, grid_half: the transform grid's zero padding,
+ *           Lagrange taps (4, 6, 8, 10, 12, 16, 20 or 24), step and half-width
+ *           (cfft_get_info reports them for a tabulation); beta_abs_max is
+ *           |beta_c| at the end of the contour, alpha_margin the angular node
+ *           margin (24 reproduces the default of cfft_tabulate_reactions)
+ * Limits: at most 65536 chunks (n_rho <= 2097152) and at most 950,272
+ * angular nodes summed over the chunks (about n_rho * beta_abs_max * rho_max
+ * / 128; 8192 rows to rho 50 at beta 66 use about 2.1e5); a request beyond
+ * them, or whose rho_max needs more grid than grid_half, returns
+ * CFFT_ERR_ARG before any work is queued.
+ * The first call on a device looks the scratch array's device address up
+ * (with `device` made current for the call); make that first call before
+ * any stream capture.  Every call reuses the same array and rewrites the
+ * entries it reads before reading them, so no call depends on what an
+ * earlier one left there -- but two calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race on the array.
+ * Work is queued on cuda_stream; the call does not synchronize. */
+cfft_status cfft_backproject_static(int device, void* cuda_stream, const void* grid,
+                                    void* table, int series_per_q, int q_max, int n_rho,
+                                    double rho_max, int grid_half, double delta_s, int sigma,
+                                    int taps, double beta_abs_max, double alpha_margin,
+                                    int complex128);
+
 #ifdef __cplusplus
 }
 #endif

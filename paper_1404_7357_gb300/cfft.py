@@ -24,7 +24,7 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_set_mbf_spectra_strip", "cfft_set_mbf_spectra", "cfft_build_contour",
            "cfft_set_option", "cfft_tabulate_reactions", "cfft_get_table", "cfft_copy_table",
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
-           "cfft_debug_buffer", "cfft_synchronize"]
+           "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static"]
 
 
 class CfftLibraryError(ImportError):
@@ -72,6 +72,7 @@ def _load():
         "cfft_get_info": ([P, ctypes.POINTER(Info)], I),
         "cfft_debug_buffer": ([P, ctypes.c_char_p, ctypes.POINTER(P), ctypes.POINTER(L)], I),
         "cfft_synchronize": ([P], I),
+        "cfft_backproject_static": ([I, P, P, P, I, I, I, D, I, D, I, I, D, D, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -225,3 +226,26 @@ class Context:
 
     def synchronize(self):
         self._check(_lib.cfft_synchronize(self._h))
+
+
+def backproject_static(grid, table, series_per_q, q_max, rho_max, grid_half, delta_s, sigma, taps,
+                       beta_abs_max, alpha_margin=24.0, stream=None):
+    """cfft_backproject_static: back-project a transform grid (torch CUDA tensor, layout of
+    Context.debug_buffer("grid")) into ``table`` (torch CUDA tensor [series, n_rho]) without
+    any device allocation by the library.  Queued on ``stream`` (default: torch's current)."""
+    import torch
+    dev = grid.device.index or 0
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    assert grid.is_cuda and table.is_cuda and grid.dtype == table.dtype
+    assert grid.is_contiguous() and table.is_contiguous()
+    n_rho = table.shape[-1]
+    st = _lib.cfft_backproject_static(dev, ctypes.c_void_p(handle), ctypes.c_void_p(grid.data_ptr()),
+                                      ctypes.c_void_p(table.data_ptr()), series_per_q, q_max, n_rho,
+                                      float(rho_max), grid_half, float(delta_s), sigma, taps,
+                                      float(beta_abs_max), float(alpha_margin),
+                                      int(grid.dtype == torch.complex128))
+    if st != 0:
+        raise CfftError(st, "cfft_backproject_static rejected the request or failed")
+    return table
