@@ -1,0 +1,166 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each test plants one mistake in the oracle (on the CPU, through monkeypatch)
+-- a dropped contour Jacobian, a flipped off-diagonal Green's term, a
+conjugate on the wrong side, a (+i)^q instead of (-i)^q, a transposed
+rotation, a wrong free-space branch -- and checks that the quantity the
+corresponding pin asserts moves far outside that pin's tolerance.
+"""
+import math
+
+import numpy as np
+
+from oracle import contour, green, reaction, spectra
+
+K0 = 2 * math.pi
+
+
+def gaussian_hankel_error():
+    """Richardson-extrapolated error of the Gaussian Hankel pair (pin: < 1e-9)."""
+    q, s = 1, 0.35
+    rho = np.array([0.4, 1.3])
+    exact = ((-1j) ** q / (2 * np.pi)) * rho ** q / (2 * s * s) ** (q + 1) * np.exp(-rho ** 2 / (4 * s * s))
+    zs = []
+    for n in (1000, 2000):
+        c = contour.contour_nodes(n, 30.0, 8.1, 0.6)
+        hq = (c["beta_c"] * np.exp(-s * s * c["beta_c"] ** 2))[None, :]
+        zs.append(reaction.table_bessel(hq, [q], c["beta_c"], c["weight"], rho)[0])
+    rich = (4 * zs[1] - zs[0]) / 3
+    return np.abs(rich - exact).max() / np.abs(exact).max()
+
+
+def rotational_covariance_error():
+    """max |G(Rk) - R G(k) R^T| / |G| (pin: < 1e-12)."""
+    k = np.array([1.3 * K0 + 0.02j, 0.7 * K0 + 0.01j])
+    th = 0.7
+    r = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    g = np.array(green.dyadic_green(k[0], k[1], 4.4, 0.03, K0))
+    g = np.array([[g[0], g[1]], [g[1], g[2]]])
+    rk = r @ k
+    g2 = np.array(green.dyadic_green(rk[0], rk[1], 4.4, 0.03, K0))
+    g2 = np.array([[g2[0], g2[1]], [g2[1], g2[2]]])
+    return np.abs(g2 - r @ g @ r.T).max() / np.abs(g).max()
+
+
+def _patch(seed=11):
+    rng = np.random.default_rng(seed)
+    ax = np.array([-0.1, 0.0, 0.1])
+    gx, gy = np.meshgrid(ax, ax)
+    cx = np.concatenate([gx.ravel(), gx.ravel()])
+    cy = np.concatenate([gy.ravel(), gy.ravel()])
+    d = np.concatenate([np.zeros(9, int), np.ones(9, int)])
+    q = rng.standard_normal((18, 2)) + 1j * rng.standard_normal((18, 2))
+    return spectra.BasisSet("rooftop", q, cx=cx, cy=cy, direction=d, half_len=np.full(18, 0.1),
+                            width=np.full(18, 0.1))
+
+
+def reciprocity_error():
+    """|Z_ab,q[Q] - (-1)^q Z_ba,q[conj Q]| / max|Z| (pin: < 1e-11)."""
+    kd = K0 * math.sqrt(4.4)
+    c = contour.contour_nodes(300, 5 * kd, 1.3 * kd, 6 * 5 * kd / 300)
+    bs = _patch()
+    bsc = spectra.BasisSet("rooftop", np.conj(bs.q), **bs.geom)
+    qs = np.arange(-3, 4)
+    rho = np.array([0.3, 1.2])
+    z = reaction.table_bessel(reaction.harmonics(bs, c["beta_c"], qs, 64, 4.4, 0.03, K0), qs,
+                              c["beta_c"], c["weight"], rho)
+    zc = reaction.table_bessel(reaction.harmonics(bsc, c["beta_c"], qs, 64, 4.4, 0.03, K0), qs,
+                               c["beta_c"], c["weight"], rho)
+    sign = ((-1.0) ** np.abs(qs))[:, None]
+    return np.abs(z - np.swapaxes(zc, 0, 1) * sign).max() / np.abs(z).max()
+
+
+def gaussian_2d_error():
+    """Z'(rho, phi) of two Gaussian currents vs the 2-D Fourier pair (pin: < 1e-10)."""
+    s = 0.12
+    c0, c1 = np.array([0.05, -0.03]), np.array([-0.04, 0.02])
+    bs = spectra.BasisSet("gaussian", np.eye(2), cx=np.array([c0[0], c1[0]]),
+                          cy=np.array([c0[1], c1[1]]), direction=np.array([0, 0]), s=s)
+    qs = np.arange(-14, 15)
+    c = contour.contour_nodes(3000, 45.0, 9.9, 0.5)
+    hq = reaction.harmonics(bs, c["beta_c"], qs, 64, 0, 0, K0, green_fn=green.identity_green)
+    zq = reaction.table_bessel(hq, qs, c["beta_c"], c["weight"], np.array([0.3]))[..., 0]
+    phi = 1.0
+    z = reaction.reaction_from_table(zq, qs, phi)
+    d = 0.3 * np.array([math.cos(phi), math.sin(phi)]) + c0 - c1
+    exact = np.exp(-d @ d / (8 * s * s)) / (8 * np.pi * s * s)
+    return abs(z[0, 1] - exact) / exact
+
+
+def rotation_error():
+    """spectra at theta = 90 deg vs an explicitly rotated mesh (pin: < 1e-12)."""
+    bs = _patch()
+    g = bs.geom
+    d = g["direction"]
+    sign = np.where(d == 1, -1.0, 1.0)
+    rot = spectra.BasisSet("rooftop", bs.q * sign[:, None], cx=-g["cy"], cy=g["cx"], direction=1 - d,
+                           half_len=g["half_len"], width=g["width"])
+    kx, ky = np.array([2.0, 11.0 + 0.1j]), np.array([5.0, -3.0 + 0.05j])
+    a = spectra.mbf_spectra(bs, kx, ky, theta=math.pi / 2)
+    b = spectra.mbf_spectra(rot, kx, ky)
+    return max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()) / np.abs(b[0]).max()
+
+
+def test_unmutated_oracle_meets_every_pin():
+    assert gaussian_hankel_error() < 1e-9
+    assert rotational_covariance_error() < 1e-12
+    assert reciprocity_error() < 1e-11
+    assert gaussian_2d_error() < 1e-5   # single resolution here (no Richardson): O(h^2)
+    assert rotation_error() < 1e-12
+
+
+def test_dropped_contour_jacobian_is_caught(monkeypatch):
+    orig = contour.contour_nodes
+
+    def no_jacobian(n, beta_max, beta_p, height):
+        d = orig(n, beta_max, beta_p, height)
+        d["weight"] = np.full(n, d["h"], dtype=np.complex128)
+        return d
+
+    monkeypatch.setattr(contour, "contour_nodes", no_jacobian)
+    assert gaussian_hankel_error() > 1e-3
+
+
+def test_flipped_off_diagonal_green_is_caught(monkeypatch):
+    orig = green.dyadic_green
+    monkeypatch.setattr(green, "dyadic_green",
+                        lambda kx, ky, e, h, k0: (lambda g: (g[0], -g[1], g[2]))(orig(kx, ky, e, h, k0)))
+    assert rotational_covariance_error() > 1e-3
+
+
+def test_conjugate_on_both_sides_is_caught(monkeypatch):
+    orig = spectra.mbf_spectra
+
+    def both_conj(basis, kx, ky, theta=0.0, conjugate_side=False):
+        if conjugate_side:
+            b2 = spectra.BasisSet(basis.kind, np.conj(basis.q), **basis.geom)
+            return orig(b2, kx, ky, theta=theta, conjugate_side=True)
+        return orig(basis, kx, ky, theta=theta, conjugate_side=False)
+
+    monkeypatch.setattr(spectra, "mbf_spectra", both_conj)
+    assert reciprocity_error() > 1e-3
+
+
+def test_wrong_harmonic_phase_is_caught(monkeypatch):
+    orig = reaction.table_bessel
+
+    def plus_i(hq, qs, beta_c, weight, rho):
+        z = orig(hq, qs, beta_c, weight, rho)
+        fix = np.array([(1j) ** int(q) / (-1j) ** int(q) for q in qs])
+        return z * fix.reshape((1,) * (z.ndim - 2) + (-1, 1))
+
+    monkeypatch.setattr(reaction, "table_bessel", plus_i)
+    assert gaussian_2d_error() > 1e-2
+
+
+def test_transposed_rotation_is_caught(monkeypatch):
+    orig = spectra._rotate_k
+    monkeypatch.setattr(spectra, "_rotate_k", lambda kx, ky, th: orig(kx, ky, -th))
+    assert rotation_error() > 1e-3
+
+
+def test_wrong_free_space_branch_is_caught(monkeypatch):
+    # k2 with Im k2 >= 0 (growing field) instead of the radiation condition
+    monkeypatch.setattr(green, "_branch_sqrt_free", lambda w: 1j * np.sqrt(np.asarray(w, dtype=np.complex128)))
+    bc = np.array([0.5, 1.5]) * K0 + 0.05j
+    assert np.any(green.kz_free(bc ** 2, K0).imag > 0)   # the radiation-condition pin fails
