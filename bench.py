@@ -116,8 +116,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+TABLE_SIZE = {}
+
+
 def table_workload():
-    return workloads.patch_m4(precision="fp32")
+    """The patch-m4 workload (sizes overridable for small profiling cases)."""
+    return workloads.patch_m4(precision="fp32", **TABLE_SIZE)
 
 
 def fill_workload():
@@ -309,6 +313,75 @@ def bench_fill(torch, cfft, args, dev):
     return res
 
 
+def bench_batch(torch, cfft, args, dev):
+    """Batched sweep: 64 frequencies x 8 substrates, contours of 4k..64k samples, patch
+    element (M = 4), |q| <= 16, 2048 rho points to 50 lambda0, FP32-mixed, one CUDA graph."""
+    items = workloads.sweep_items()
+    q_max, rho_max, n_rho = 16, 50.0, 2048
+    el = table_workload().element
+    ctx = cfft.Context(dev)
+    ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+    out = torch.empty((len(items), 16, 2 * q_max + 1, n_rho), dtype=torch.complex64, device=dev)
+    t0 = time.perf_counter()
+    ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True,
+                       autotune=True)      # tunes, captures and runs the graph once
+    first_s = time.perf_counter() - t0
+    steps = max(1, min(args.steps, 2))
+    times = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True)
+        times.append(time.perf_counter() - t0)
+    info = ctx.batch_info()
+    samples = len(items) * 16 * (2 * q_max + 1) * n_rho
+    ns = [it["n"] for it in items]
+    return {"metric": "C-FFT table samples/s (batched sweep)", "value": samples * steps / sum(times),
+            "unit": "samples/s", "ms_per_sweep": 1e3 * sum(times) / steps,
+            "ms_graph_replay": info["ms_graph"], "first_call_s": first_s,
+            "workload": "64 frequencies (0.8..1.2) x 8 substrates (eps_r U[2,10], h U[0.02,0.1]); "
+                        "contours n in [%d, %d] (mean %.0f); M=4; |q|<=16; %d rho points to %g lambda0; "
+                        "FP32-mixed; one CUDA graph" % (min(ns), max(ns), np.mean(ns), n_rho, rho_max),
+            "info": info}
+
+
+def bench_grad(torch, cfft, args, dev):
+    """Differentiable fill: 2000 Poisson-disc elements in a disc of radius 25 lambda0, M = 4,
+    L = sum |Z v - t|^2; forward (table + fill) and backward (table with substrate
+    derivatives recomputed + adjoint fill), FP32-mixed."""
+    from paper_1404_7357_gb300.autograd import FillProblem, ReducedMatrix
+    wl = workloads.patch_m4(precision="fp32", rotation_classes=4)
+    pos, rot = workloads.poisson_disc(2000, 25.0, 0.5, seed=5), workloads.rotations(2000, seed=5)
+    prob = FillProblem(wl.element, wl.substrate.k0, wl.contour, wl.q_max, wl.rho_max, wl.n_rho,
+                       "fp32", rot=torch.tensor(rot, device=dev), device=dev)
+    m = wl.element.n_mbf
+    v = torch.tensor(workloads.complex_normal(2000 * m, 5), device=dev).to(torch.complex64)
+    t = torch.tensor(workloads.complex_normal(2000 * m, 6), device=dev).to(torch.complex64)
+    pos_t = torch.tensor(pos, device=dev, requires_grad=True)
+    eh = torch.tensor([wl.substrate.eps_r, wl.substrate.h], dtype=torch.float64, device=dev,
+                      requires_grad=True)
+    res = []
+    for k in range(2):
+        pos_t.grad = None
+        eh.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        z = ReducedMatrix.apply(pos_t, eh, prob)
+        loss = ((z @ v - t).abs() ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res.append((t1 - t0, t2 - t1))
+    fw, bw = res[-1]
+    return {"metric": "objective + gradient (2A + 2 parameters) per second", "value": 1.0 / (fw + bw),
+            "unit": "gradients/s", "forward_ms": 1e3 * fw, "backward_ms": 1e3 * bw,
+            "workload": "A=2000 Poisson-disc elements in a disc of radius 25 lambda0, rotations "
+                        "{0,90}, M=4, table of patch-m4 (4 classes), FP32-mixed; L=sum|Zv-t|^2",
+            "grad_norm_pos": float(pos_t.grad.norm()), "grad_eps_h": eh.grad.tolist()}
+
+
 def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -363,12 +436,19 @@ def run_cfft(args):
     from paper_1404_7357_gb300 import cfft
     peaks = load_peaks()
 
+    if args.only_fill:
+        fill = bench_fill(torch, cfft, args, dev)
+        if rank == 0:
+            print(json.dumps({"fill": fill}), flush=True)
+        return
     wl, ctx, step_ms, infos, clk = bench_tabulation(torch, cfft, args, dev)
     total_s = max_over_ranks(torch, sum(step_ms) / 1e3)
     samples = table_samples(wl)
     value = samples * args.steps * world / total_s
     e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
     fill = None if args.skip_fill else bench_fill(torch, cfft, args, dev)
+    batch = None if args.skip_batch else bench_batch(torch, cfft, args, dev)
+    grad = None if args.skip_grad else bench_grad(torch, cfft, args, dev)
     launches = int(sum(i["launches"] for i in infos))
     line = {"metric": "C-FFT table samples/s", "value": value, "unit": "samples/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -379,6 +459,10 @@ def run_cfft(args):
     if fill is not None:
         fill["alu_frac"] = fill["alu_tflops"] / fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         line["fill"] = fill
+    if batch is not None:
+        line["batch"] = batch
+    if grad is not None:
+        line["grad"] = grad
     line["peaks_source"] = peaks["_source"]
     if rank == 0 and world == 1 and not args.skip_cpu:
         workers = max(1, min(32, os.cpu_count() or 1))
@@ -412,7 +496,16 @@ def main():
     ap.add_argument("--impl", default="cfft", choices=["cfft", "reference"])
     ap.add_argument("--skip-fill", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--only-fill", action="store_true", help="time the fill alone")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-grad", action="store_true")
+    ap.add_argument("--table-n", type=int, help="contour samples (small profiling case)")
+    ap.add_argument("--table-nrho", type=int, help="rho points (small profiling case)")
+    ap.add_argument("--table-rho", type=float, help="rho_max (small profiling case)")
     args = ap.parse_args()
+    for k, v in (("n", args.table_n), ("n_rho", args.table_nrho), ("rho_max", args.table_rho)):
+        if v is not None:
+            TABLE_SIZE[k] = v
     if args.warmup < 3 and args.impl == "cfft":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

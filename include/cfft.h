@@ -74,14 +74,23 @@ typedef enum {
  *   FILL_TAPS   Lagrange taps of the fill interpolation in rho (even)
  *   ALPHA_MARGIN extra angular nodes of the back-projection quadrature
  *   CHECK_FINITE a value < 0 skips the NaN/Inf scan (and its stream sync)
- *                at the end of cfft_tabulate_reactions                     */
+ *                at the end of cfft_tabulate_reactions
+ *   DERIVATIVES  a value > 0 makes cfft_tabulate_reactions also tabulate
+ *                d Z_ab,q / d eps_r and d Z_ab,q / d h with the contour held
+ *                fixed (three times the work; see cfft_get_derivative_table)
+ *   BP_GATHER    a value > 0 selects the direct gather form of the
+ *                back-projection instead of its matrix form (both evaluate
+ *                the same quadrature; the matrix form needs at most 64 series
+ *                per harmonic and 8, 12 or 16 taps)                        */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
   CFFT_OPT_BP_TAPS = 2,
   CFFT_OPT_FILL_TAPS = 3,
   CFFT_OPT_ALPHA_MARGIN = 4,
-  CFFT_OPT_CHECK_FINITE = 5
+  CFFT_OPT_CHECK_FINITE = 5,
+  CFFT_OPT_DERIVATIVES = 6,
+  CFFT_OPT_BP_GATHER = 7
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -180,7 +189,11 @@ cfft_status cfft_copy_table(const cfft_ctx* ctx, void* dst, int64_t bytes, int d
  *   ld      row stride in complex entries, >= n_elements * M
  * Requires a table (CFFT_ERR_STATE).  A pair farther apart than the table's
  * rho_max makes the call return CFFT_ERR_ARG (after the kernel ran; the
- * affected entries are zero).  Stream-ordered; synchronizes for that check. */
+ * affected entries are zero).  Stream-ordered; synchronizes for that check.
+ * The element pairs are counting-sorted by (rotation class, stencil row)
+ * before the interpolation so that pairs sharing table rows run together;
+ * the context owns that scratch (4 bytes per element pair plus 12 bytes per
+ * table row and class) and keeps it for the next fill. */
 cfft_status cfft_fill_reduced_matrix(cfft_ctx* ctx, int n_elements, const double* pos_xy,
                                      const int* rot, void* z_out, int64_t ld,
                                      int out_complex128);
@@ -191,6 +204,82 @@ cfft_status cfft_fill_reduced_matrix(cfft_ctx* ctx, int n_elements, const double
 cfft_status cfft_fill_reduced_matrix_host(cfft_ctx* ctx, int n_elements, const double* pos_xy,
                                           const int* rot, void* z_out, int64_t ld,
                                           int out_complex128);
+
+/* One item of a batched sweep: substrate (eps_r, h), free-space wavenumber k0
+ * (the frequency, with lengths in fixed units) and its own contour (n samples,
+ * beta_max, beta_p, height as in cfft_build_contour; taylor_order -1 = auto). */
+typedef struct {
+  double eps_r, h, k0;
+  int n;
+  double beta_max, beta_p, height;
+  int taylor_order;
+} cfft_batch_item;
+
+/* Batched sweep (the paper fixes one substrate and frequency; sweeping many is
+ * the same Section III-B tabulation repeated): tabulate the element set by
+ * cfft_set_mbf_spectra for n_items (substrate, frequency, contour) items with
+ * uneven contour lengths, one rotation class, harmonics -q_max..q_max and
+ * n_rho points to rho_max, into
+ *   tables  device, caller-owned: n_items consecutive tables of
+ *           M*M * (2*q_max+1) * n_rho entries (layout of cfft_get_table),
+ *           complex128 (precision FP64) or complex64.
+ * Every stage runs as one launch over all items of a wave (items are split
+ * into waves only when their scratch would exceed 24 GiB): contour and
+ * integrand as multi-item grids, the FFTs and the back-projection as
+ * persistent kernels that pull (item, series, residue) and (item, group,
+ * harmonic, row chunk) tasks from a counter, largest first.
+ * flags bit 0: capture the launch sequence into a CUDA graph on the first
+ *              call with a given structure (items' n and Taylor orders,
+ *              sizes, output buffer) and replay it on later calls, which only
+ *              refresh the per-item parameters.  The batch runs on a
+ *              library-owned stream ordered after the context's stream, so
+ *              any context stream (also the legacy default one) works.
+ * flags bit 1: autotune the sub-FFT length and the back-projection row chunk
+ *              by timing the candidates on this batch (cached per structure).
+ * Each n must be a multiple of 256 (sigma * n divisible by 1024).  Requires
+ * cfft_set_mbf_spectra* (CFFT_ERR_STATE).  Synchronizes. */
+cfft_status cfft_tabulate_batch(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
+                                int q_max, double rho_max, int n_rho, cfft_precision precision,
+                                void* tables, int flags);
+
+/* Diagnostics of the last batch: stage times of the first wave (contour +
+ * integrand, FFT, back-projection), the whole graph replay, work counts,
+ * chosen sub-FFT length and row chunk, waves and kernel launches. */
+typedef struct {
+  double ms_integrand, ms_fft, ms_backproject, ms_graph;
+  double work_subffts, work_bp_nodes;
+  int sub_len, rchunk, waves, launches;
+} cfft_batch_info;
+cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info);
+
+/* Substrate derivatives of the table (forward mode; no counterpart in the
+ * paper, which fixes the substrate).  The table is linear in the Green's
+ * function, G = P(beta) I - R(beta) k k^T, so d Z / d theta is the same C-FFT
+ * applied to dP/dtheta and dR/dtheta (analytic derivatives of the TE/TM
+ * expressions, float64) with the contour, Taylor order and grids unchanged.
+ * which = 0: the table itself; 1: d/d eps_r; 2: d/d h.  Same layout and
+ * element type as cfft_get_table; borrowed.  CFFT_ERR_STATE unless the last
+ * tabulation ran with CFFT_OPT_DERIVATIVES > 0 (which > 0). */
+cfft_status cfft_get_derivative_table(const cfft_ctx* ctx, int which, const void** dev_ptr,
+                                      int64_t shape[4]);
+
+/* Adjoint of cfft_fill_reduced_matrix (no counterpart in the paper): given
+ * grad_z = dL/dZ' of a real objective L in the convention
+ * dL = Re sum_ij conj(grad_z_ij) dZ'_ij (the one PyTorch uses for complex
+ * tensors), write
+ *   grad_pos[2m + {0,1}] = dL / d(x_m, y_m)      (device float64[2 * n_elements])
+ *   grad_eps_h[{0,1}]    = dL / d(eps_r, h)      (device float64[2], optional)
+ * through the interpolated table: d rho and d phi of every element pair
+ * (the Lagrange stencil's slope and i q exp(i q phi)), and the derivative
+ * tables for the substrate (requires CFFT_OPT_DERIVATIVES at tabulation,
+ * else CFFT_ERR_STATE when grad_eps_h is not NULL).  grad_z: device,
+ * complex128 (grad_complex128 != 0) or complex64, rows of ld entries, layout
+ * of Z_out.  Outputs are overwritten.  Pairs are sorted as in the fill;
+ * accumulation uses float64 atomics (results can differ in the last bits
+ * from run to run).  Synchronizes the stream. */
+cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_xy,
+                               const int* rot, const void* grad_z, int64_t ld,
+                               int grad_complex128, double* grad_pos, double* grad_eps_h);
 
 /* Diagnostics of the last tabulation (host values): taylor order used,
  * n_alpha, sigma, FFT length, sub-FFT length, grid half-width K, back-

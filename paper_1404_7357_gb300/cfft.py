@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_PKG, "libcfft.so")
 
 CFFT_FP64 = 0
 CFFT_FP32_MIXED = 1
-OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE = range(6)
+(OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
+ OPT_DERIVATIVES, OPT_BP_GATHER) = range(8)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 
@@ -24,7 +25,9 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_set_mbf_spectra_strip", "cfft_set_mbf_spectra", "cfft_build_contour",
            "cfft_set_option", "cfft_tabulate_reactions", "cfft_get_table", "cfft_copy_table",
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
-           "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static"]
+           "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
+           "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
+           "cfft_get_batch_info"]
 
 
 class CfftLibraryError(ImportError):
@@ -35,6 +38,18 @@ class CfftError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
         self.status = status
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("eps_r", ctypes.c_double), ("h", ctypes.c_double), ("k0", ctypes.c_double),
+                ("n", ctypes.c_int), ("beta_max", ctypes.c_double), ("beta_p", ctypes.c_double),
+                ("height", ctypes.c_double), ("taylor_order", ctypes.c_int)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("ms_integrand", "ms_fft", "ms_backproject", "ms_graph",
+                                                "work_subffts", "work_bp_nodes")] + \
+               [(n, ctypes.c_int) for n in ("sub_len", "rchunk", "waves", "launches")]
 
 
 class Info(ctypes.Structure):
@@ -73,6 +88,10 @@ def _load():
         "cfft_debug_buffer": ([P, ctypes.c_char_p, ctypes.POINTER(P), ctypes.POINTER(L)], I),
         "cfft_synchronize": ([P], I),
         "cfft_backproject_static": ([I, P, P, P, I, I, I, D, I, D, I, I, D, D, I], I),
+        "cfft_get_derivative_table": ([P, I, ctypes.POINTER(P), ctypes.POINTER(L)], I),
+        "cfft_fill_backward": ([P, I, P, P, P, L, I, P, P], I),
+        "cfft_tabulate_batch": ([P, I, ctypes.POINTER(BatchItem), I, D, I, I, P, I], I),
+        "cfft_get_batch_info": ([P, ctypes.POINTER(BatchInfo)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -136,6 +155,7 @@ class Context:
 
     def set_mbf_spectra_strip(self, length, width):
         self._check(_lib.cfft_set_mbf_spectra_strip(self._h, length, width))
+        self.n_mbf = 1
 
     def set_mbf_spectra(self, centers, direction, half_len, width, q):
         centers = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 2)
@@ -146,6 +166,7 @@ class Context:
         b, m = q.shape
         self._check(_lib.cfft_set_mbf_spectra(self._h, b, _ptr(centers), _ptr(direction),
                                               _ptr(half_len), _ptr(width), m, _ptr(q)))
+        self.n_mbf = m
 
     def build_contour(self, n, beta_max, beta_p, height, taylor_order=-1):
         self._check(_lib.cfft_build_contour(self._h, n, beta_max, beta_p, height, taylor_order))
@@ -207,6 +228,54 @@ class Context:
             ctypes.c_void_p(addr(rot) if rot is not None else 0), ctypes.c_void_p(addr(out)),
             ld, int(is128)))
         return out
+
+    def derivative_table(self, which):
+        """Borrowed device view of the table (0) or its d/d eps_r (1), d/d h (2) companion."""
+        ptr = ctypes.c_void_p()
+        shape = (ctypes.c_int64 * 4)()
+        self._check(_lib.cfft_get_derivative_table(self._h, which, ctypes.byref(ptr), shape))
+        _, is128, _ = self.table_shape()
+        return self._torch.as_tensor(_DeviceArray(ptr.value, tuple(shape), "<c16" if is128 else "<c8"),
+                                     device="cuda:%d" % self.device)
+
+    def fill_backward(self, pos, rot, grad_z, substrate=True):
+        """Adjoint of the fill: (grad_pos (A, 2) float64, grad_eps_h (2,) float64 or None)."""
+        torch = self._torch
+        assert grad_z.is_cuda and grad_z.stride(-1) == 1
+        grad_pos = torch.empty_like(pos)
+        g_th = torch.empty(2, dtype=torch.float64, device=pos.device) if substrate else None
+        self._check(_lib.cfft_fill_backward(
+            self._h, pos.shape[0], ctypes.c_void_p(pos.data_ptr()),
+            ctypes.c_void_p(rot.data_ptr() if rot is not None else 0),
+            ctypes.c_void_p(grad_z.data_ptr()), grad_z.stride(0),
+            int(grad_z.dtype == torch.complex128), ctypes.c_void_p(grad_pos.data_ptr()),
+            ctypes.c_void_p(g_th.data_ptr() if g_th is not None else 0)))
+        return grad_pos, g_th
+
+    def tabulate_batch(self, items, q_max, rho_max, n_rho, precision, out=None, graph=True,
+                       autotune=False):
+        """cfft_tabulate_batch over dict-like items (eps_r, h, k0, n, beta_max, beta_p, height,
+        taylor_order); returns the (n_items, M*M, 2*q_max+1, n_rho) device tensor."""
+        torch = self._torch
+        arr = (BatchItem * len(items))()
+        for i, it in enumerate(items):
+            arr[i] = BatchItem(it["eps_r"], it["h"], it["k0"], int(it["n"]), it["beta_max"],
+                               it["beta_p"], it["height"], int(it.get("taylor_order", -1)))
+        m2 = self.n_mbf ** 2
+        dt = torch.complex128 if precision == CFFT_FP64 else torch.complex64
+        shape = (len(items), m2, 2 * q_max + 1, n_rho)
+        if out is None:
+            out = torch.empty(shape, dtype=dt, device="cuda:%d" % self.device)
+        assert tuple(out.shape) == shape and out.dtype == dt and out.is_contiguous()
+        self._check(_lib.cfft_tabulate_batch(self._h, len(items), arr, q_max, float(rho_max), n_rho,
+                                             precision, ctypes.c_void_p(out.data_ptr()),
+                                             int(graph) | (2 if autotune else 0)))
+        return out
+
+    def batch_info(self):
+        inf = BatchInfo()
+        self._check(_lib.cfft_get_batch_info(self._h, ctypes.byref(inf)))
+        return {n: getattr(inf, n) for n, _ in BatchInfo._fields_}
 
     def info(self):
         inf = Info()

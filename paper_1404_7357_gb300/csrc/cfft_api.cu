@@ -84,11 +84,23 @@ struct cfft_ctx {
   cfft_precision prec = CFFT_FP64;
   cfft_info info{};
   // device buffers
-  DevBuf beta_c, weight, bw, bi_rel, green_p, green_r;
+  DevBuf beta_c, weight, bw, bi_rel, green_p, green_r, dp_eps, dr_eps, dp_h, dr_h;
+  int channels = 1;  // 1: table; 3: table, d/d eps_r, d/d h
   DevBuf d_shapes, d_bx, d_by, d_q, d_y, d_grid, d_table, d_tw, d_cnodes, d_coff, d_cos, d_lag,
-      d_flag, d_pos, d_rot, d_zbuf;
+      d_flag, d_pos, d_rot, d_zbuf, d_fill;
   int tw_len = 0, tw_prec = -1;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // batched sweep: plan arrays, scratch, stream, captured graph, tuned shape
+  DevBuf b_cargs, b_cdata, b_iargs, b_fargs, b_bargs, b_cmap, b_imap, b_ftask, b_btask, b_count,
+      b_cnodes, b_coff, b_cos, b_contour, b_y, b_grid, b_flag;
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t bev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t bgraph = nullptr;
+  std::string bsig;           // signature of the captured graph
+  std::map<std::string, std::pair<int, int>> tuned;  // signature -> (sub_len, rchunk)
+  double b_ms[4] = {0, 0, 0, 0};
+  double b_work_bp = 0, b_work_fft = 0;
+  int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0;
 };
 
 namespace {
@@ -206,14 +218,21 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(ctx->beta_c.ensure(n * sizeof(double2)), "alloc contour");
   CFFT_CUDA(ctx->weight.ensure(n * sizeof(double2)), "alloc contour");
   CFFT_CUDA(ctx->bw.ensure(n * sizeof(double2)), "alloc contour");
-  CFFT_CUDA(ctx->bi_rel.ensure(n * sizeof(double)), "alloc contour");
+  CFFT_CUDA(ctx->bi_rel.ensure(n * (sizeof(double) + sizeof(float)) + 16), "alloc contour");
   CFFT_CUDA(ctx->green_p.ensure(n * sizeof(double2)), "alloc contour");
   CFFT_CUDA(ctx->green_r.ensure(n * sizeof(double2)), "alloc contour");
   CFFT_CUDA(ctx->d_y.ensure((size_t)series * n * sizeof(cpx<T>)), "alloc harmonics");
   CFFT_CUDA(ctx->d_grid.ensure((size_t)series * (2 * K + 1) * sizeof(cpx<T>)), "alloc grid");
   const int cls_s = ctx->cls_stored;
+  const int channels = ctx->opt[6] > 0 ? 3 : 1;
   const size_t table_elems = (size_t)cls_s * pairs * nh * ctx->n_rho;
-  CFFT_CUDA(ctx->d_table.ensure(table_elems * sizeof(cpx<T>)), "alloc table");
+  CFFT_CUDA(ctx->d_table.ensure(channels * table_elems * sizeof(cpx<T>)), "alloc table");
+  if (channels == 3) {
+    CFFT_CUDA(ctx->dp_eps.ensure(n * sizeof(double2)), "alloc contour");
+    CFFT_CUDA(ctx->dr_eps.ensure(n * sizeof(double2)), "alloc contour");
+    CFFT_CUDA(ctx->dp_h.ensure(n * sizeof(double2)), "alloc contour");
+    CFFT_CUDA(ctx->dr_h.ensure(n * sizeof(double2)), "alloc contour");
+  }
   CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");
 
   // element data in T
@@ -245,13 +264,23 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   // ---- a1: contour + Green's function (float64)
   ContourArgs ca{n, ctx->beta_max, ctx->beta_p, ctx->height, step, ctx->eps_r, ctx->hs, ctx->k0};
   ContourData cd{ctx->beta_c.as<double2>(), ctx->weight.as<double2>(), ctx->bw.as<double2>(),
-                 ctx->bi_rel.as<double>(), ctx->green_p.as<double2>(), ctx->green_r.as<double2>()};
+                 ctx->bi_rel.as<double>(), reinterpret_cast<float*>(ctx->bi_rel.as<double>() + n),
+                 ctx->green_p.as<double2>(), ctx->green_r.as<double2>(),
+                 nullptr, nullptr, nullptr, nullptr};
+  if (channels == 3) {
+    cd.dp_eps = ctx->dp_eps.as<double2>();
+    cd.dr_eps = ctx->dr_eps.as<double2>();
+    cd.dp_h = ctx->dp_h.as<double2>();
+    cd.dr_h = ctx->dr_h.as<double2>();
+  }
   int launches = 0;
   launch_contour(ca, cd, st);
   ++launches;
   CFFT_CUDA(cudaGetLastError(), "contour kernel");
   CFFT_CUDA(cudaEventRecord(ctx->ev[1], st), "event");
 
+  double bp_nodes = 0;
+  for (int ch = 0; ch < channels; ++ch) {
   // ---- a2/a3: spectra, kernel, harmonics
   IntegrandArgs<T> ia{};
   ia.n = n;
@@ -267,12 +296,14 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ia.q = ctx->d_q.as<cpx<T>>();
   ia.beta_c = ctx->beta_c.as<double2>();
   ia.bw = ctx->bw.as<double2>();
-  ia.green_p = ctx->green_p.as<double2>();
-  ia.green_r = ctx->green_r.as<double2>();
+  const double2* gp_ch[3] = {ctx->green_p.as<double2>(), ctx->dp_eps.as<double2>(), ctx->dp_h.as<double2>()};
+  const double2* gr_ch[3] = {ctx->green_r.as<double2>(), ctx->dr_eps.as<double2>(), ctx->dr_h.as<double2>()};
+  ia.green_p = gp_ch[ch];
+  ia.green_r = gr_ch[ch];
   ia.y = ctx->d_y.as<cpx<T>>();
   CFFT_CUDA(launch_integrand<T>(ia, ctx->n_mbf_pad, st), "integrand kernel");
   ++launches;
-  CFFT_CUDA(cudaEventRecord(ctx->ev[2], st), "event");
+  if (ch == 0) CFFT_CUDA(cudaEventRecord(ctx->ev[2], st), "event");
 
   // ---- a4: Taylor terms x pruned zero-padded FFTs
   const int prec_id = fp64 ? 1 : 0;
@@ -298,21 +329,26 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   fa.ds_height = ds * ctx->height;
   fa.y = ctx->d_y.as<cpx<T>>();
   fa.bi_rel = ctx->bi_rel.as<double>();
+  fa.bi_rel_f = reinterpret_cast<const float*>(ctx->bi_rel.as<double>() + n);
   fa.twiddle = ctx->d_tw.as<cpx<T>>();
   fa.grid = ctx->d_grid.as<cpx<T>>();
   CFFT_CUDA(launch_fft<T>(fa, st), "fft kernel");
   ++launches;
-  CFFT_CUDA(cudaEventRecord(ctx->ev[3], st), "event");
+  if (ch == 0) CFFT_CUDA(cudaEventRecord(ctx->ev[3], st), "event");
 
   // ---- a5: back-projection to the rho grid
-  const int rchunk = 32;
+  // the matrix-form back-projection handles up to 64 series per harmonic with 8/12/16 taps;
+  // otherwise the direct gather form runs
+  const bool wform = series_per_q <= 64 && (bp_taps == 8 || bp_taps == 12 || bp_taps == 16) &&
+                     !(ctx->opt[CFFT_OPT_BP_GATHER] > 0);
+  const int rchunk = wform ? backproject_w_rows() : 32;
   const int n_chunks = (ctx->n_rho + rchunk - 1) / rchunk;
   const double d_rho = ctx->rho_max / (ctx->n_rho - 1);
   std::vector<int> cn(n_chunks);
   std::vector<int64_t> coff(n_chunks);
   int64_t tot = 0;
   int max_nodes = 0, max_seg = 0;
-  double bp_nodes = 0;
+  bp_nodes = 0;
   for (int c = 0; c < n_chunks; ++c) {
     int r_top = std::min((c + 1) * rchunk, ctx->n_rho) - 1;
     double rho_top = r_top * d_rho;
@@ -336,14 +372,18 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(cudaMemcpyAsync(ctx->d_cnodes.p, cn.data(), n_chunks * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
   CFFT_CUDA(cudaMemcpyAsync(ctx->d_coff.p, coff.data(), n_chunks * sizeof(int64_t), cudaMemcpyHostToDevice, st), "upload");
   CFFT_CUDA(cudaMemcpyAsync(ctx->d_lag.p, lag.data(), bp_taps * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
-  CFFT_CUDA(launch_chunk_cosines(ctx->d_cnodes.as<int>(), ctx->d_coff.as<int64_t>(), n_chunks,
-                                 max_nodes, ctx->d_cos.as<double>(), st), "cosine kernel");
-  ++launches;
+  if (ch == 0) {
+    CFFT_CUDA(launch_chunk_cosines(ctx->d_cnodes.as<int>(), ctx->d_coff.as<int64_t>(), n_chunks,
+                                   max_nodes, ctx->d_cos.as<double>(), st), "cosine kernel");
+    ++launches;
+  }
   int group = 8;
   const size_t smem_cap = 225 * 1024;
   while (group > 1 && backproject_smem<T>(group, max_seg, max_nodes) > smem_cap) --group;
-  if (backproject_smem<T>(group, max_seg, max_nodes) > smem_cap)
+  if (!wform && backproject_smem<T>(group, max_seg, max_nodes) > smem_cap)
     return fail(ctx, CFFT_ERR_ARG, "rho_max too large for one shared-memory segment");
+  if (wform && backproject_w_smem<T>(max_nodes, series_per_q) > smem_cap)
+    return fail(ctx, CFFT_ERR_ARG, "rho_max too large for the angular node table");
   group = std::min(group, series_per_q);
   BackprojArgs<T> ba{};
   ba.series_per_q = series_per_q;
@@ -360,15 +400,23 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ba.beta_abs_max = beta_abs_max;
   ba.alpha_margin = margin;
   ba.grid = ctx->d_grid.as<cpx<T>>();
-  ba.table = ctx->d_table.as<cpx<T>>();
-  CFFT_CUDA(launch_backproject_impl<T>(ba, ctx->d_cnodes.as<int>(), ctx->d_coff.as<int64_t>(),
-                                       ctx->d_cos.as<double>(), ctx->d_lag.as<double>(), n_chunks,
-                                       max_nodes, max_seg, st), "backprojection kernel");
+  ba.table = ctx->d_table.as<cpx<T>>() + ch * table_elems;
+  if (wform) {
+    ba.chunk_nodes = ctx->d_cnodes.as<int>();
+    ba.chunk_off = ctx->d_coff.as<int64_t>();
+    ba.cosv = ctx->d_cos.as<double>();
+    CFFT_CUDA(launch_backproject_w<T>(ba, n_chunks, max_nodes, st), "backprojection kernel");
+  } else {
+    CFFT_CUDA(launch_backproject_impl<T>(ba, ctx->d_cnodes.as<int>(), ctx->d_coff.as<int64_t>(),
+                                         ctx->d_cos.as<double>(), ctx->d_lag.as<double>(), n_chunks,
+                                         max_nodes, max_seg, st), "backprojection kernel");
+  }
   ++launches;
   if (cls_s == 4) {
-    launch_class_phase<T>(ctx->d_table.as<cpx<T>>(), pairs, nh, ctx->q_max, ctx->n_rho, st);
+    launch_class_phase<T>(ctx->d_table.as<cpx<T>>() + ch * table_elems, pairs, nh, ctx->q_max, ctx->n_rho, st);
     ++launches;
     CFFT_CUDA(cudaGetLastError(), "class phase kernel");
+  }
   }
   CFFT_CUDA(cudaEventRecord(ctx->ev[4], st), "event");
 
@@ -376,7 +424,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   bool check = !(ctx->opt[5] < 0);
   if (check) {
     CFFT_CUDA(cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), st), "flag");
-    launch_nonfinite<T>(ctx->d_table.as<cpx<T>>(), (int64_t)table_elems, ctx->d_flag.as<int>(), st);
+    launch_nonfinite<T>(ctx->d_table.as<cpx<T>>(), (int64_t)(channels * table_elems), ctx->d_flag.as<int>(), st);
     ++launches;
     CFFT_CUDA(cudaGetLastError(), "nonfinite kernel");
   }
@@ -413,6 +461,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   in.work_subffts = (double)series * D * (taylor + 1);
   in.work_bp_nodes = bp_nodes;
   ctx->fill_taps = fill_taps;
+  ctx->channels = channels;
   ctx->has_table = true;
   if (flag) return fail(ctx, CFFT_ERR_NUMERIC, "non-finite value in the reaction table");
   return CFFT_OK;
@@ -437,12 +486,56 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
   fa.rot = rot;
   fa.z = reinterpret_cast<cpx<TO>*>(z);
   fa.err = ctx->d_flag.as<int>() + 1;
+  CFFT_CUDA(ctx->d_fill.ensure(fill_scratch_bytes(n_el, ctx->cls_stored * ctx->n_rho)), "alloc fill scratch");
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
-  cudaError_t le = launch_fill<T, TO>(fa, ctx->stream);
+  cudaError_t le = launch_fill<T, TO>(fa, ctx->d_fill.p, ctx->stream);
   if (le != cudaSuccess) return cuda_fail(ctx, le, "fill kernel");
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "fill");
+  if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the table's rho_max");
+  return CFFT_OK;
+}
+
+template <class T, class TG>
+cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot,
+                               const void* grad, int64_t ld_g, double* grad_pos, double* grad_theta) {
+  FillBackArgs<T, TG> b{};
+  FillArgs<T, float>& fa = b.f;
+  fa.n_el = n_el;
+  fa.n_mbf = ctx->n_mbf;
+  fa.q_max = ctx->q_max;
+  fa.n_harm = 2 * ctx->q_max + 1;
+  fa.n_rho = ctx->n_rho;
+  fa.taps = ctx->fill_taps;
+  fa.n_cls = ctx->cls_stored;
+  fa.inv_d_rho = (ctx->n_rho - 1) / ctx->rho_max;
+  fa.rho_max = ctx->rho_max;
+  fa.ld = 0;
+  fa.table = ctx->d_table.as<cpx<T>>();
+  fa.pos = pos;
+  fa.rot = rot;
+  fa.z = nullptr;
+  fa.err = ctx->d_flag.as<int>() + 1;
+  const size_t table_elems = (size_t)ctx->cls_stored * ctx->n_mbf * ctx->n_mbf * fa.n_harm * ctx->n_rho;
+  if (ctx->channels == 3) {
+    b.dtab_eps = fa.table + table_elems;
+    b.dtab_h = fa.table + 2 * table_elems;
+  }
+  b.grad = reinterpret_cast<const cpx<TG>*>(grad);
+  b.ld_g = ld_g;
+  b.d_rho = ctx->rho_max / (ctx->n_rho - 1);
+  b.grad_pos = grad_pos;
+  b.grad_theta = grad_theta;
+  CFFT_CUDA(ctx->d_fill.ensure(fill_scratch_bytes(n_el, ctx->cls_stored * ctx->n_rho)), "alloc fill scratch");
+  CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
+  if (grad_pos) CFFT_CUDA(cudaMemsetAsync(grad_pos, 0, (size_t)2 * n_el * sizeof(double), ctx->stream), "zero");
+  if (grad_theta) CFFT_CUDA(cudaMemsetAsync(grad_theta, 0, 2 * sizeof(double), ctx->stream), "zero");
+  cudaError_t le = launch_fill_backward<T, TG>(b, ctx->d_fill.p, ctx->stream);
+  if (le != cudaSuccess) return cuda_fail(ctx, le, "fill backward kernel");
+  int flag = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "fill backward");
   if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the table's rho_max");
   return CFFT_OK;
 }
@@ -464,6 +557,476 @@ cfft_status check_fill_args(cfft_ctx* ctx, int n_el, const double* pos, const in
   if (!pos || !z) return fail(ctx, CFFT_ERR_ARG, "null pointer");
   if (ld < (int64_t)n_el * ctx->n_mbf) return fail(ctx, CFFT_ERR_ARG, "ld < n_elements * M");
   if (ctx->cls_stored == 4 && !rot) return fail(ctx, CFFT_ERR_ARG, "rot is required with 4 rotation classes");
+  return CFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched sweep: many (substrate, frequency) items of one element, every stage
+// one persistent or multi-item launch over all items of a wave, the whole
+// sequence captured once into a CUDA graph and replayed.
+
+struct BatchItemPlan {
+  int n, taylor, n_active, K, D;
+  int64_t P;
+  double step, ds, beta_abs;
+};
+
+constexpr size_t kWaveScratch = size_t(24) << 30;  // Y + grid bytes per wave
+
+template <class T>
+cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items, int q_max,
+                       double rho_max, int n_rho, void* tables, int flags) {
+  const bool fp64 = sizeof(T) == 8;
+  const int M = ctx->n_mbf;
+  const int pairs = M * M;
+  const int nh = 2 * q_max + 1;
+  const int series = pairs * nh;
+  const int sigma = ctx->opt[CFFT_OPT_SIGMA] > 0 ? (int)ctx->opt[CFFT_OPT_SIGMA] : (fp64 ? 8 : 4);
+  const int bp_taps = ctx->opt[CFFT_OPT_BP_TAPS] > 0 ? (int)ctx->opt[CFFT_OPT_BP_TAPS] : (fp64 ? 16 : 12);
+  if (bp_taps != 8 && bp_taps != 12 && bp_taps != 16)
+    return fail(ctx, CFFT_ERR_ARG, "batched back-projection taps must be 8, 12 or 16");
+  const double margin = ctx->opt[CFFT_OPT_ALPHA_MARGIN] > 0 ? ctx->opt[CFFT_OPT_ALPHA_MARGIN] : 24.0;
+  const double d_rho = rho_max / (n_rho - 1);
+  const size_t table_elems = (size_t)pairs * nh * n_rho;
+  cudaStream_t st = ctx->bstream;
+
+  // ---- per-item parameters (same rules as the single tabulation)
+  std::vector<BatchItemPlan> ip(n_items);
+  int n_alpha = (int)ctx->opt[CFFT_OPT_N_ALPHA];
+  int l_common = fp64 ? 8192 : 16384;
+  for (int i = 0; i < n_items; ++i) {
+    const cfft_batch_item& it = items[i];
+    BatchItemPlan& p = ip[i];
+    p.n = it.n;
+    p.step = it.beta_max / it.n;
+    p.beta_abs = std::hypot(it.beta_max, it.height);
+    p.taylor = it.taylor_order >= 0 ? it.taylor_order
+                                    : auto_taylor(it.height * rho_max, fp64 ? 1e-13 : 1e-7);
+    p.P = (int64_t)sigma * it.n;
+    p.ds = 2.0 * kPi / ((double)p.P * p.step);
+    p.K = (int)std::ceil(rho_max / p.ds) + bp_taps / 2 + 2;
+    if (2 * (int64_t)p.K + 1 > p.P)
+      return fail(ctx, CFFT_ERR_ARG, "batch item: rho_max exceeds the unaliased range of its contour");
+    p.n_active = it.height > 0 ? (int)std::min<double>(it.n, std::ceil(it.beta_p / p.step - 0.5)) : 0;
+    int lp = 1;
+    while ((p.P % (2 * (int64_t)lp)) == 0 && 2 * lp <= l_common) lp *= 2;
+    l_common = std::min(l_common, lp);
+    if (ctx->opt[CFFT_OPT_N_ALPHA] <= 0) {
+      double need = 2.0 * p.beta_abs * ctx->elem_radius + 2.0 * q_max + 32.0;
+      n_alpha = std::max(n_alpha, std::max(8, next_pow2((int)std::ceil(need))));
+    }
+  }
+  if (l_common < 1024) return fail(ctx, CFFT_ERR_ARG, "batch: sigma * n must be divisible by 1024");
+  if (n_alpha % 4 != 0) return fail(ctx, CFFT_ERR_ARG, "n_alpha must be a multiple of 4");
+
+  // ---- signature (graph and tuning cache key)
+  std::string sig = std::to_string(n_items) + ":" + std::to_string(q_max) + ":" + std::to_string(n_rho) +
+                    ":" + std::to_string(rho_max) + ":" + std::to_string(sizeof(T)) + ":" +
+                    std::to_string(n_alpha) + ":" + std::to_string((size_t)tables) + ":" +
+                    std::to_string(ctx->n_basis) + ":" + std::to_string(M);
+  for (int i = 0; i < n_items; ++i) sig += ":" + std::to_string(ip[i].n) + "/" + std::to_string(ip[i].taylor);
+
+  // ---- element data in T (shared by all items)
+  {
+    std::vector<T> hx(ctx->n_basis), hy(ctx->n_basis);
+    std::vector<cpx<T>> hq((size_t)ctx->n_basis * ctx->n_mbf_pad);
+    for (int i = 0; i < ctx->n_basis; ++i) {
+      hx[i] = (T)ctx->bx[i];
+      hy[i] = (T)ctx->by[i];
+    }
+    for (size_t i = 0; i < hq.size(); ++i) hq[i] = mk((T)ctx->q[i].real(), (T)ctx->q[i].imag());
+    CFFT_CUDA(ctx->d_bx.ensure(hx.size() * sizeof(T)), "alloc element");
+    CFFT_CUDA(ctx->d_by.ensure(hy.size() * sizeof(T)), "alloc element");
+    CFFT_CUDA(ctx->d_q.ensure(hq.size() * sizeof(cpx<T>)), "alloc element");
+    CFFT_CUDA(ctx->d_shapes.ensure(ctx->shapes.size() * sizeof(ShapeClass)), "alloc element");
+    CFFT_CUDA(cudaMemcpy(ctx->d_bx.p, hx.data(), hx.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+    CFFT_CUDA(cudaMemcpy(ctx->d_by.p, hy.data(), hy.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+    CFFT_CUDA(cudaMemcpy(ctx->d_q.p, hq.data(), hq.size() * sizeof(cpx<T>), cudaMemcpyHostToDevice), "upload");
+    CFFT_CUDA(cudaMemcpy(ctx->d_shapes.p, ctx->shapes.data(), ctx->shapes.size() * sizeof(ShapeClass),
+                         cudaMemcpyHostToDevice), "upload");
+  }
+
+  // ---- waves: consecutive items whose harmonics + transform grids fit the wave scratch
+  struct Wave { int i0, i1; };
+  std::vector<Wave> waves;
+  size_t max_nodes_wave = 0, max_y = 0, max_grid = 0;
+  {
+    int i0 = 0;
+    size_t nodes = 0, yb = 0, gb = 0;
+    for (int i = 0; i < n_items; ++i) {
+      size_t yi = (size_t)series * ip[i].n * sizeof(cpx<T>);
+      size_t gi = (size_t)series * (2 * ip[i].K + 1) * sizeof(cpx<T>);
+      if (i > i0 && yb + gb + yi + gi > kWaveScratch) {
+        waves.push_back({i0, i});
+        i0 = i;
+        nodes = yb = gb = 0;
+      }
+      nodes += ip[i].n;
+      yb += yi;
+      gb += gi;
+      max_nodes_wave = std::max(max_nodes_wave, nodes);
+      max_y = std::max(max_y, yb);
+      max_grid = std::max(max_grid, gb);
+    }
+    waves.push_back({i0, n_items});
+  }
+  CFFT_CUDA(ctx->b_contour.ensure(max_nodes_wave * (4 * sizeof(double2) + sizeof(double) + sizeof(double2) + 64)), "alloc batch contour");
+  CFFT_CUDA(ctx->b_y.ensure(max_y), "alloc batch harmonics");
+  CFFT_CUDA(ctx->b_grid.ensure(max_grid), "alloc batch grid");
+
+  // contour buffers carved from b_contour: beta_c, weight, bw, green_p, green_r (double2), bi_rel (double)
+  double2* c_beta = ctx->b_contour.as<double2>();
+  double2* c_w = c_beta + max_nodes_wave;
+  double2* c_bw = c_w + max_nodes_wave;
+  double2* c_gp = c_bw + max_nodes_wave;
+  double2* c_gr = c_gp + max_nodes_wave;
+  double* c_bi = reinterpret_cast<double*>(c_gr + max_nodes_wave);
+  float* c_bif = reinterpret_cast<float*>(c_bi + max_nodes_wave);
+
+  // integrand tile height (the same element and n_alpha for every item)
+  IntegrandArgs<T> shape_args{};
+  shape_args.n_alpha = n_alpha;
+  shape_args.n_mbf = M;
+  shape_args.n_basis = ctx->n_basis;
+  const int jt = integrand_tile_nodes<T>(shape_args, ctx->n_mbf_pad);
+  if (jt < 1) return fail(ctx, CFFT_ERR_ARG, "element too large for the integrand tile");
+
+  // back-projection chunk shapes depend on rchunk; FFT tasks on the sub-FFT length
+  // mode 0: plan + plain launches; 1: plan + capture into a new graph; 2: plan only
+  // (the captured graph reads the refreshed plan); 3: plan + launches, time one stage
+  auto build_and_run = [&](int L, int rchunk, int mode, int stage_to_time,
+                           float* stage_ms) -> cfft_status {
+    int log2L = 0;
+    while ((1 << log2L) < L) ++log2L;
+    const int n_chunks = (n_rho + rchunk - 1) / rchunk;
+    std::vector<ContourArgs> hca(n_items);
+    std::vector<ContourData> hcd(n_items);
+    std::vector<IntegrandArgs<T>> hia(n_items);
+    std::vector<FftArgs<T>> hfa(n_items);
+    std::vector<BackprojArgs<T>> hba(n_items);
+    std::vector<int2> cmap, imap;
+    std::vector<int4> ftask, btask;
+    std::vector<int> cnodes((size_t)n_items * n_chunks);
+    std::vector<int64_t> coff((size_t)n_items * n_chunks);
+    struct FftBucket { int log2L; size_t f0, f1; int max_nout; };
+    struct WaveRanges { size_t c0, c1, i0, i1, f0, f1, b0, b1; std::vector<FftBucket> fb; };
+    std::vector<WaveRanges> wr;
+    int64_t cos_total = 0;
+    int max_nodes = 0, max_seg = 0, max_nout = 0, max_active = 0, max_n_item = 0;
+    for (int i = 0; i < n_items; ++i) {
+      max_active = std::max(max_active, ip[i].n_active);
+      max_n_item = std::max(max_n_item, ip[i].n);
+    }
+    for (int i = 0; i < n_items; ++i) {
+      for (int c = 0; c < n_chunks; ++c) {
+        int r_top = std::min((c + 1) * rchunk, n_rho) - 1;
+        double rho_top = r_top * d_rho;
+        int np = alpha_nodes(ip[i].beta_abs, rho_top, q_max, margin);
+        cnodes[(size_t)i * n_chunks + c] = np;
+        coff[(size_t)i * n_chunks + c] = cos_total;
+        cos_total += np;
+        max_nodes = std::max(max_nodes, np);
+        int kseg = std::min(ip[i].K, (int)std::ceil(rho_top / ip[i].ds) + bp_taps / 2 + 2);
+        max_seg = std::max(max_seg, 2 * kseg + 1);
+      }
+    }
+    // every buffer the per-item arguments point into is sized here, before those
+    // pointers are taken (a later reallocation would leave them dangling)
+    CFFT_CUDA(ctx->b_cnodes.ensure(cnodes.size() * sizeof(int)), "alloc plan");
+    CFFT_CUDA(ctx->b_coff.ensure(coff.size() * sizeof(int64_t)), "alloc plan");
+    CFFT_CUDA(ctx->b_cos.ensure(cos_total * sizeof(double)), "alloc plan");
+    CFFT_CUDA(ctx->d_tw.ensure((size_t)L * sizeof(cpx<T>)), "alloc twiddles");
+    if (backproject_w_smem<T>(max_nodes, pairs) > 225 * 1024 || pairs > 64)
+      return fail(ctx, CFFT_ERR_ARG, "batch: rho_max too large for the angular node table");
+    const int group = std::min(8, pairs);
+    double work_bp = 0, work_fft = 0;
+    // sub-FFT length of each item: at most L, a divisor of its P, at least 4 residues
+    // when the item allows, and a shared-memory footprint that fits
+    std::vector<int> li(n_items);
+    for (int i = 0; i < n_items; ++i) {
+      const BatchItemPlan& p = ip[i];
+      int l = 1;
+      while ((p.P % (2 * (int64_t)l)) == 0 && 2 * l <= L) l *= 2;
+      while (l > 1024 && p.P / l < 4) l /= 2;
+      auto smem_of = [&](int ll) {
+        int d = (int)(p.P / ll);
+        return (size_t)ll * sizeof(cpx<T>) +
+               fft_task_extra<T>(0, (2 * p.K + 1) / d + 4, (p.n + 127) / 128);
+      };
+      while (l > 1024 && smem_of(l) > 220 * 1024) l /= 2;
+      if (smem_of(l) > 220 * 1024)
+        return fail(ctx, CFFT_ERR_ARG, "batch item too large for a shared-memory transform");
+      li[i] = l;
+    }
+    for (const Wave& w : waves) {
+      WaveRanges r{cmap.size(), 0, imap.size(), 0, ftask.size(), 0, btask.size(), 0, {}};
+      int64_t node_off = 0, grid_off = 0;
+      for (int i = w.i0; i < w.i1; ++i) {
+        const cfft_batch_item& it = items[i];
+        const BatchItemPlan& p = ip[i];
+        hca[i] = ContourArgs{it.n, it.beta_max, it.beta_p, it.height, p.step, it.eps_r, it.h, it.k0};
+        hcd[i] = ContourData{c_beta + node_off, c_w + node_off, c_bw + node_off, c_bi + node_off,
+                             c_bif + node_off, c_gp + node_off, c_gr + node_off,
+                             nullptr, nullptr, nullptr, nullptr};
+        for (int j0 = 0; j0 < it.n; j0 += 256) cmap.push_back(make_int2(i, j0));
+        for (int j0 = 0; j0 < it.n; j0 += jt) imap.push_back(make_int2(i, j0));
+        IntegrandArgs<T>& ia = hia[i];
+        ia = IntegrandArgs<T>{};
+        ia.n = it.n;
+        ia.n_alpha = n_alpha;
+        ia.q_max = q_max;
+        ia.n_cls = 1;
+        ia.n_mbf = M;
+        ia.n_shape = (int)ctx->shapes.size();
+        ia.n_basis = ctx->n_basis;
+        ia.shapes = ctx->d_shapes.as<ShapeClass>();
+        ia.bx = ctx->d_bx.as<T>();
+        ia.by = ctx->d_by.as<T>();
+        ia.q = ctx->d_q.as<cpx<T>>();
+        ia.beta_c = c_beta + node_off;
+        ia.bw = c_bw + node_off;
+        ia.green_p = c_gp + node_off;
+        ia.green_r = c_gr + node_off;
+        ia.y = ctx->b_y.as<cpx<T>>() + (size_t)series * node_off;
+        const int Li = li[i];
+        int log2Li = 0;
+        while ((1 << log2Li) < Li) ++log2Li;
+        const int D = (int)(p.P / Li);
+        FftArgs<T>& fa = hfa[i];
+        fa = FftArgs<T>{};
+        fa.series = series;
+        fa.n = it.n;
+        fa.sub_len = Li;
+        fa.log2_sub = log2Li;
+        fa.n_sub = D;
+        fa.fft_len = p.P;
+        fa.grid_half = p.K;
+        fa.taylor = p.taylor;
+        fa.n_active = p.n_active;
+        fa.sigma = sigma;
+        fa.ds_height = p.ds * it.height;
+        fa.y = ia.y;
+        fa.bi_rel = c_bi + node_off;
+        fa.bi_rel_f = c_bif + node_off;
+        fa.twiddle = ctx->d_tw.as<cpx<T>>();
+        fa.grid = ctx->b_grid.as<cpx<T>>() + grid_off;
+        max_nout = std::max(max_nout, (2 * p.K + 1) / D + 2);
+        for (int sr = 0; sr < series; ++sr)
+          for (int k2 = 0; k2 < D; ++k2) ftask.push_back(make_int4(i, sr, k2, log2Li));
+        work_fft += (double)series * D * (p.taylor + 1);
+        BackprojArgs<T>& ba = hba[i];
+        ba = BackprojArgs<T>{};
+        ba.series_per_q = pairs;
+        ba.n_harm = nh;
+        ba.q_max = q_max;
+        ba.n_rho = n_rho;
+        ba.grid_half = p.K;
+        ba.sigma = sigma;
+        ba.taps = bp_taps;
+        ba.group = group;
+        ba.rchunk = rchunk;
+        ba.d_rho = d_rho;
+        ba.d_s = p.ds;
+        ba.beta_abs_max = p.beta_abs;
+        ba.alpha_margin = margin;
+        ba.grid = fa.grid;
+        ba.table = reinterpret_cast<cpx<T>*>(tables) + (size_t)i * table_elems;
+        ba.chunk_nodes = ctx->b_cnodes.as<int>() + (size_t)i * n_chunks;
+        ba.chunk_off = ctx->b_coff.as<int64_t>() + (size_t)i * n_chunks;
+        ba.cosv = ctx->b_cos.as<double>();
+        for (int c = n_chunks - 1; c >= 0; --c) {  // larger rho (more nodes) first
+          int rows = std::min((c + 1) * rchunk, n_rho) - c * rchunk;
+          for (int q = 0; q < nh; ++q) btask.push_back(make_int4(i, q, c, 0));
+          work_bp += (double)cnodes[(size_t)i * n_chunks + c] * rows * series;
+        }
+        node_off += it.n;
+        grid_off += (int64_t)series * (2 * p.K + 1);
+      }
+      r.c1 = cmap.size();
+      r.i1 = imap.size();
+      r.f1 = ftask.size();
+      r.b1 = btask.size();
+      // FFT tasks of the wave grouped by sub-FFT length (one persistent launch per length),
+      // the larger transforms first inside each group
+      std::stable_sort(ftask.begin() + r.f0, ftask.end(),
+                       [](const int4& a, const int4& b) { return a.w > b.w; });
+      for (size_t t = r.f0; t < r.f1;) {
+        size_t u = t;
+        int mo = 0;
+        while (u < r.f1 && ftask[u].w == ftask[t].w) {
+          const int i = ftask[u].x;
+          mo = std::max(mo, (2 * ip[i].K + 1) / (int)(ip[i].P / li[i]) + 2);
+          ++u;
+        }
+        r.fb.push_back(FftBucket{ftask[t].w, t, u, mo});
+        t = u;
+      }
+      // within a wave, the costliest back-projection tasks (largest rho) first
+      std::stable_sort(btask.begin() + r.b0, btask.end(),
+                       [](const int4& a, const int4& b) { return a.z > b.z; });
+      wr.push_back(r);
+    }
+    // upload the plan
+    auto up = [&](DevBuf& b, const void* src, size_t bytes) -> cudaError_t {
+      cudaError_t e = b.ensure(bytes);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
+    };
+    CFFT_CUDA(up(ctx->b_cargs, hca.data(), hca.size() * sizeof(ContourArgs)), "upload plan");
+    CFFT_CUDA(up(ctx->b_cdata, hcd.data(), hcd.size() * sizeof(ContourData)), "upload plan");
+    CFFT_CUDA(up(ctx->b_iargs, hia.data(), hia.size() * sizeof(IntegrandArgs<T>)), "upload plan");
+    CFFT_CUDA(up(ctx->b_fargs, hfa.data(), hfa.size() * sizeof(FftArgs<T>)), "upload plan");
+    CFFT_CUDA(up(ctx->b_bargs, hba.data(), hba.size() * sizeof(BackprojArgs<T>)), "upload plan");
+    CFFT_CUDA(up(ctx->b_cmap, cmap.data(), cmap.size() * sizeof(int2)), "upload plan");
+    CFFT_CUDA(up(ctx->b_imap, imap.data(), imap.size() * sizeof(int2)), "upload plan");
+    CFFT_CUDA(up(ctx->b_ftask, ftask.data(), ftask.size() * sizeof(int4)), "upload plan");
+    CFFT_CUDA(up(ctx->b_btask, btask.data(), btask.size() * sizeof(int4)), "upload plan");
+    CFFT_CUDA(up(ctx->b_cnodes, cnodes.data(), cnodes.size() * sizeof(int)), "upload plan");
+    CFFT_CUDA(up(ctx->b_coff, coff.data(), coff.size() * sizeof(int64_t)), "upload plan");
+    CFFT_CUDA(ctx->b_count.ensure(8 * wr.size() * sizeof(int)), "alloc plan");
+    ctx->tw_len = -1;  // the single-table cache no longer holds these twiddles
+    ctx->b_work_bp = work_bp;
+    ctx->b_work_fft = work_fft;
+    ctx->b_sub_len = L;
+    ctx->b_rchunk = rchunk;
+    ctx->b_waves = (int)waves.size();
+
+    // the launch sequence (stream-ordered on the batch stream)
+    int launches = 0;
+    // stage events: inside a capture they become event-record nodes of the graph
+    auto rec = [&](cudaEvent_t ev) {
+      if (mode == 1) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+      else cudaEventRecord(ev, st);
+    };
+    auto issue = [&]() -> cudaError_t {
+      launch_twiddle<T>(ctx->d_tw.as<cpx<T>>(), L, st);
+      ++launches;
+      cudaError_t e = launch_chunk_cosines(ctx->b_cnodes.as<int>(), ctx->b_coff.as<int64_t>(),
+                                           n_items * n_chunks, max_nodes, ctx->b_cos.as<double>(), st);
+      if (e != cudaSuccess) return e;
+      ++launches;
+      e = cudaMemsetAsync(ctx->b_count.p, 0, 8 * wr.size() * sizeof(int), st);
+      if (e != cudaSuccess) return e;
+      const size_t n_waves = mode == 3 ? 1 : wr.size();  // tuning times the first wave only
+      for (size_t w = 0; w < n_waves; ++w) {
+        const WaveRanges& r = wr[w];
+        int* counters = ctx->b_count.as<int>() + 8 * w;  // [0]: back-projection, [1..]: FFT buckets
+        if (w == 0) rec(ctx->bev[0]);
+        launch_contour_batch(ctx->b_cargs.as<ContourArgs>(), ctx->b_cdata.as<ContourData>(),
+                             ctx->b_cmap.as<int2>() + r.c0, (int)(r.c1 - r.c0), st);
+        ++launches;
+        e = launch_integrand_batch<T>(shape_args, ctx->b_iargs.as<IntegrandArgs<T>>(),
+                                      ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), jt,
+                                      ctx->n_mbf_pad, st);
+        if (e != cudaSuccess) return e;
+        ++launches;
+        if (w == 0) rec(ctx->bev[1]);
+        for (size_t bkt = 0; bkt < r.fb.size() && bkt < 7; ++bkt) {
+          const FftBucket& fb = r.fb[bkt];
+          e = launch_fft_batch<T>(ctx->b_fargs.as<FftArgs<T>>(), ctx->b_ftask.as<int4>() + fb.f0,
+                                  (int)(fb.f1 - fb.f0), counters + 1 + bkt, fb.log2L, fb.max_nout,
+                                  max_active, (max_n_item + 127) / 128, 152, st);
+          if (e != cudaSuccess) return e;
+          ++launches;
+        }
+        if (w == 0) rec(ctx->bev[2]);
+        e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
+                                          ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
+                                          counters, bp_taps, max_nodes, pairs, 152, st);
+        if (e != cudaSuccess) return e;
+        ++launches;
+        if (w == 0) rec(ctx->bev[3]);
+      }
+      return cudaGetLastError();
+    };
+    if (mode == 2) return CFFT_OK;
+    if (mode == 3) {
+      // tuning run: plain launches, time the requested stage of the first wave
+      CFFT_CUDA(issue(), "batch launch");
+      CFFT_CUDA(cudaStreamSynchronize(st), "batch tuning");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ctx->bev[stage_to_time], ctx->bev[stage_to_time + 1]);
+      *stage_ms = ms;
+      return CFFT_OK;
+    }
+    if (mode == 1) {
+      if (ctx->bgraph) {
+        cudaGraphExecDestroy(ctx->bgraph);
+        ctx->bgraph = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      CFFT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "graph capture");
+      cudaError_t e = issue();
+      cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+      if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "batch capture");
+      }
+      CFFT_CUDA(e2, "graph capture");
+      e = cudaGraphInstantiate(&ctx->bgraph, graph, 0);
+      cudaGraphDestroy(graph);
+      CFFT_CUDA(e, "graph instantiate");
+      ctx->bsig = sig;
+    } else {
+      CFFT_CUDA(issue(), "batch launch");
+    }
+    ctx->b_launches = launches;
+    return CFFT_OK;
+  };
+
+  for (auto& e : ctx->bev)
+    if (!e) CFFT_CUDA(cudaEventCreate(&e), "event");
+
+  // ---- autotune the sub-FFT length and the back-projection row chunk (cached per signature)
+  int L = std::min(l_common, fp64 ? 8192 : 16384);
+  int rchunk = backproject_w_rows();  // row tile of the matrix-form back-projection
+  auto tc = ctx->tuned.find(sig);
+  if (tc != ctx->tuned.end()) {
+    L = tc->second.first;
+    rchunk = tc->second.second;
+  } else if (flags & 2) {
+    float best = 1e30f;
+    for (int cand = 2048; cand <= l_common; cand *= 2) {
+      float ms = 0;
+      cfft_status s = build_and_run(cand, rchunk, 3, 1, &ms);
+      if (s != CFFT_OK) return s;
+      if (ms < best) {
+        best = ms;
+        L = cand;
+      }
+    }
+    ctx->tuned[sig] = {L, rchunk};
+  }
+
+  const bool use_graph = (flags & 1) != 0;
+  const bool reuse = use_graph && ctx->bgraph && ctx->bsig == sig && ctx->b_sub_len == L &&
+                     ctx->b_rchunk == rchunk;
+  {
+    // same structure: refresh the per-item parameters (substrate, contour) that the
+    // captured graph reads; otherwise plan again and launch or capture
+    cfft_status s = build_and_run(L, rchunk, reuse ? 2 : (use_graph ? 1 : 0), -1, nullptr);
+    if (s != CFFT_OK) return s;
+  }
+  if (use_graph) {
+    CFFT_CUDA(cudaEventRecord(ctx->bev[4], st), "event");
+    CFFT_CUDA(cudaGraphLaunch(ctx->bgraph, st), "graph launch");
+    CFFT_CUDA(cudaEventRecord(ctx->bev[5], st), "event");
+  }
+  // NaN / Inf scan of all tables
+  CFFT_CUDA(ctx->b_flag.ensure(sizeof(int)), "alloc flag");
+  CFFT_CUDA(cudaMemsetAsync(ctx->b_flag.p, 0, sizeof(int), st), "flag");
+  launch_nonfinite<T>(reinterpret_cast<const cpx<T>*>(tables), (int64_t)(n_items * table_elems),
+                      ctx->b_flag.as<int>(), st);
+  int flag = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&flag, ctx->b_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+  CFFT_CUDA(cudaStreamSynchronize(st), "batch");
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, ctx->bev[0], ctx->bev[1]) == cudaSuccess) ctx->b_ms[0] = ms;
+  if (cudaEventElapsedTime(&ms, ctx->bev[1], ctx->bev[2]) == cudaSuccess) ctx->b_ms[1] = ms;
+  if (cudaEventElapsedTime(&ms, ctx->bev[2], ctx->bev[3]) == cudaSuccess) ctx->b_ms[2] = ms;
+  if (use_graph && cudaEventElapsedTime(&ms, ctx->bev[4], ctx->bev[5]) == cudaSuccess) ctx->b_ms[3] = ms;
+  cudaGetLastError();  // an unrecorded timing event is not an error of the batch
+  if (flag) return fail(ctx, CFFT_ERR_NUMERIC, "non-finite value in a batch table");
   return CFFT_OK;
 }
 
@@ -493,13 +1056,22 @@ void cfft_destroy(cfft_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->beta_c, &ctx->weight, &ctx->bw, &ctx->bi_rel, &ctx->green_p,
-                      &ctx->green_r, &ctx->d_shapes, &ctx->d_bx, &ctx->d_by, &ctx->d_q,
+                      &ctx->green_r, &ctx->dp_eps, &ctx->dr_eps, &ctx->dp_h, &ctx->dr_h, &ctx->d_shapes, &ctx->d_bx, &ctx->d_by, &ctx->d_q,
                       &ctx->d_y, &ctx->d_grid, &ctx->d_table, &ctx->d_tw, &ctx->d_cnodes,
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
-                      &ctx->d_rot, &ctx->d_zbuf};
+                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill};
     for (DevBuf* b : bufs) b->release();
     for (auto& e : ctx->ev)
       if (e) cudaEventDestroy(e);
+    DevBuf* bb[] = {&ctx->b_cargs, &ctx->b_cdata, &ctx->b_iargs, &ctx->b_fargs, &ctx->b_bargs,
+                    &ctx->b_cmap, &ctx->b_imap, &ctx->b_ftask, &ctx->b_btask, &ctx->b_count,
+                    &ctx->b_cnodes, &ctx->b_coff, &ctx->b_cos, &ctx->b_contour, &ctx->b_y,
+                    &ctx->b_grid, &ctx->b_flag};
+    for (DevBuf* b : bb) b->release();
+    for (auto& e : ctx->bev)
+      if (e) cudaEventDestroy(e);
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
   }
   delete ctx;
 }
@@ -605,7 +1177,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 5) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 7) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   return CFFT_OK;
 }
@@ -695,6 +1267,84 @@ cfft_status cfft_fill_reduced_matrix_host(cfft_ctx* ctx, int n_elements, const d
   CFFT_CUDA(cudaMemcpyAsync(z_out, ctx->d_zbuf.p, zbytes, cudaMemcpyDeviceToHost, ctx->stream), "download");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "download");
   return CFFT_OK;
+}
+
+cfft_status cfft_tabulate_batch(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
+                                int q_max, double rho_max, int n_rho, cfft_precision precision,
+                                void* tables, int flags) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (!ctx->has_el) return fail(ctx, CFFT_ERR_STATE, "batch needs the element (set_mbf_spectra)");
+  if (n_items < 1 || n_items > (1 << 19) || !items || !tables)
+    return fail(ctx, CFFT_ERR_ARG, "batch: need 1..524288 items and a table buffer");
+  if (q_max < 0 || q_max > 64 || n_rho < 16 || n_rho > (1 << 20) || !(rho_max > 0))
+    return fail(ctx, CFFT_ERR_ARG, "batch: bad q_max, n_rho or rho_max");
+  if (precision != CFFT_FP64 && precision != CFFT_FP32_MIXED) return fail(ctx, CFFT_ERR_ARG, "bad precision");
+  for (int i = 0; i < n_items; ++i) {
+    const cfft_batch_item& it = items[i];
+    if (!(it.eps_r > 0) || !(it.h >= 0) || !(it.k0 > 0) || it.n < 256 || it.n > (1 << 20) ||
+        it.n % 256 != 0 || !(it.beta_p > 0) || !(it.beta_p < it.beta_max) || !(it.height >= 0) ||
+        it.taylor_order < -1 || it.taylor_order > 64 ||
+        (it.height > 0 && !(it.beta_p > it.k0 * std::sqrt(it.eps_r))))
+      return fail(ctx, CFFT_ERR_ARG, "batch item " + std::to_string(i) + " is invalid");
+  }
+  DeviceGuard g(ctx->device);
+  if (!ctx->bstream) CFFT_CUDA(cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking), "stream");
+  // order the batch after the work already issued on the context stream
+  if (!ctx->ev[0]) CFFT_CUDA(cudaEventCreate(&ctx->ev[0]), "event");
+  CFFT_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
+  CFFT_CUDA(cudaStreamWaitEvent(ctx->bstream, ctx->ev[0], 0), "event");
+  cfft_status s = precision == CFFT_FP64
+                      ? batch_impl<double>(ctx, n_items, items, q_max, rho_max, n_rho, tables, flags)
+                      : batch_impl<float>(ctx, n_items, items, q_max, rho_max, n_rho, tables, flags);
+  return s;
+}
+
+cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info) {
+  if (!ctx || !info) return CFFT_ERR_ARG;
+  info->ms_integrand = ctx->b_ms[0];
+  info->ms_fft = ctx->b_ms[1];
+  info->ms_backproject = ctx->b_ms[2];
+  info->ms_graph = ctx->b_ms[3];
+  info->work_subffts = ctx->b_work_fft;
+  info->work_bp_nodes = ctx->b_work_bp;
+  info->sub_len = ctx->b_sub_len;
+  info->rchunk = ctx->b_rchunk;
+  info->waves = ctx->b_waves;
+  info->launches = ctx->b_launches;
+  return CFFT_OK;
+}
+
+cfft_status cfft_get_derivative_table(const cfft_ctx* ctx, int which, const void** dev_ptr,
+                                      int64_t shape[4]) {
+  if (!ctx || !dev_ptr || !shape || which < 0 || which > 2) return CFFT_ERR_ARG;
+  if (!ctx->has_table || (which > 0 && ctx->channels != 3)) return CFFT_ERR_STATE;
+  const size_t es = ctx->prec == CFFT_FP64 ? 16 : 8;
+  const size_t elems = (size_t)ctx->cls_stored * ctx->n_mbf * ctx->n_mbf * (2 * ctx->q_max + 1) * ctx->n_rho;
+  *dev_ptr = reinterpret_cast<const unsigned char*>(ctx->d_table.p) + which * elems * es;
+  shape[0] = ctx->cls_stored;
+  shape[1] = (int64_t)ctx->n_mbf * ctx->n_mbf;
+  shape[2] = 2 * ctx->q_max + 1;
+  shape[3] = ctx->n_rho;
+  return CFFT_OK;
+}
+
+cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_xy, const int* rot,
+                               const void* grad_z, int64_t ld, int grad_complex128,
+                               double* grad_pos, double* grad_eps_h) {
+  cfft_status s = check_fill_args(ctx, n_elements, pos_xy, rot, const_cast<void*>(grad_z), ld);
+  if (s != CFFT_OK) return s;
+  if (!grad_pos && !grad_eps_h) return fail(ctx, CFFT_ERR_ARG, "nothing to compute");
+  if (grad_eps_h && ctx->channels != 3)
+    return fail(ctx, CFFT_ERR_STATE, "substrate gradient needs a tabulation with CFFT_OPT_DERIVATIVES");
+  DeviceGuard g(ctx->device);
+  const int* r = ctx->cls_stored == 4 ? rot : nullptr;
+  const bool t64 = ctx->prec == CFFT_FP64;
+  if (t64 && grad_complex128)
+    return fill_backward_impl<double, double>(ctx, n_elements, pos_xy, r, grad_z, ld, grad_pos, grad_eps_h);
+  if (t64) return fill_backward_impl<double, float>(ctx, n_elements, pos_xy, r, grad_z, ld, grad_pos, grad_eps_h);
+  if (grad_complex128)
+    return fill_backward_impl<float, double>(ctx, n_elements, pos_xy, r, grad_z, ld, grad_pos, grad_eps_h);
+  return fill_backward_impl<float, float>(ctx, n_elements, pos_xy, r, grad_z, ld, grad_pos, grad_eps_h);
 }
 
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info) {

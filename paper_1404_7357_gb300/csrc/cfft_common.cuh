@@ -145,8 +145,15 @@ struct ContourData {
   double2* weight;  // step * (1 + i dbeta_I/dbeta_R)
   double2* bw;      // beta_c * weight  (the factor of Eq. 9's beta d beta)
   double* bi_rel;   // beta_I / height  (0 beyond beta_p); in [0, 1]
+  float* bi_rel_f;  // the same in float32 (read by the float32 transform)
   double2* green_p; // G = P I - R k k^T  (P, R: functions of beta only)
   double2* green_r; // R * beta_c^2
+  // optional (null to skip): derivatives of P and R beta_c^2 with respect to
+  // eps_r and to the slab thickness h, contour held fixed
+  double2* dp_eps;
+  double2* dr_eps;
+  double2* dp_h;
+  double2* dr_h;
 };
 
 struct ShapeClass {
@@ -187,6 +194,7 @@ struct FftArgs {
   double ds_height;                           // delta_s * height  (Taylor variable scale)
   const cpx<T>* y;                            // [series][n]
   const double* bi_rel;                       // [n]
+  const float* bi_rel_f;                      // [n] float32 copy
   const cpx<T>* twiddle;                      // [sub_len] e^{-2 pi i t / sub_len}
   cpx<T>* grid;                               // [series][2K+1]
 };
@@ -200,6 +208,9 @@ struct BackprojArgs {
   double alpha_margin;
   const cpx<T>* grid;      // [series][2K+1]   series = (cls*pairs + pair) * n_harm + qi
   cpx<T>* table;           // [series][n_rho]
+  const int* chunk_nodes;  // [chunks] angular nodes of each chunk of rows
+  const int64_t* chunk_off;// [chunks] offset of its cosines in cosv
+  const double* cosv;      // node cosines
 };
 
 template <class T, class TO>
@@ -223,13 +234,67 @@ cudaError_t launch_integrand(const IntegrandArgs<T>& a, int n_mbf_padded, cudaSt
 template <class T>
 cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s);
 template <class T>
-cudaError_t launch_backproject(const BackprojArgs<T>& a, cudaStream_t s);
+int integrand_tile_nodes(const IntegrandArgs<T>& a, int n_mbf_padded);
+template <class T>
+cudaError_t launch_integrand_batch(const IntegrandArgs<T>& shape_args, const IntegrandArgs<T>* items,
+                                   const int2* map, int n_blocks, int jt, int n_mbf_padded,
+                                   cudaStream_t s);
+void launch_contour_batch(const ContourArgs* items, const ContourData* data, const int2* map,
+                          int n_blocks, cudaStream_t s);
+// shared-memory bytes of one transform task beyond its FFT buffer
+template <class T>
+__host__ __device__ constexpr size_t fft_task_extra(int /*n_active_max*/, int n_out_max, int hi_max) {
+  return (size_t)(256 + hi_max + 128 + 128) * sizeof(cpx<T>) +
+         (size_t)n_out_max * (sizeof(cpx<T>) + 2 * sizeof(T)) + 64;
+}
+
+template <class T>
+cudaError_t launch_fft_batch(const FftArgs<T>* items, const int4* tasks, int n_tasks, int* counter,
+                             int log2_sub, int max_n_out, int max_active, int max_hi, int n_ctas,
+                             cudaStream_t s);
+template <class T>
+size_t backproject_smem(int group, int max_seg, int max_nodes);
+template <class T>
+cudaError_t launch_backproject_impl(const BackprojArgs<T>& a, const int* chunk_nodes,
+                                    const int64_t* chunk_off, const double* cosv,
+                                    const double* lag_den, int n_chunks, int max_nodes,
+                                    int max_seg, cudaStream_t s);
+template <class T>
+cudaError_t launch_backproject_batch(const BackprojArgs<T>* items, const int4* tasks, int n_tasks,
+                                     int* counter, int taps, int group, int max_nodes, int max_seg,
+                                     int n_ctas, cudaStream_t s);
+cudaError_t launch_chunk_cosines(const int* n_nodes, const int64_t* offset, int n_chunks,
+                                 int max_nodes, double* cosv, cudaStream_t s);
+template <class T>
+size_t backproject_w_smem(int max_nodes, int series);
+int backproject_w_rows();
+template <class T>
+cudaError_t launch_backproject_w(const BackprojArgs<T>& a, int n_tiles, int max_nodes, cudaStream_t s);
+template <class T>
+cudaError_t launch_backproject_w_batch(const BackprojArgs<T>* items, const int4* tasks, int n_tasks,
+                                       int* counter, int taps, int max_nodes, int series, int n_ctas,
+                                       cudaStream_t s);
 template <class T>
 void launch_class_phase(cpx<T>* table, int pairs, int n_harm, int q_max, int n_rho,
                         cudaStream_t s);
 template <class T>
 void launch_nonfinite(const cpx<T>* buf, int64_t count, int* flag, cudaStream_t s);
+template <class T, class TG>
+struct FillBackArgs {
+  FillArgs<T, float> f;      // geometry and table (f.z unused)
+  const cpx<T>* dtab_eps;    // d table / d eps_r  (null: no substrate gradient)
+  const cpx<T>* dtab_h;      // d table / d h
+  const cpx<TG>* grad;       // dL/dZ (torch convention: dL = Re sum conj(G) dZ)
+  int64_t ld_g;
+  double d_rho;
+  double* grad_pos;          // [2 * n_el], accumulated
+  double* grad_theta;        // [2], accumulated (eps_r, h)
+};
+
+size_t fill_scratch_bytes(int n_el, int n_keys);
+template <class T, class TG>
+cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& a, void* scratch, cudaStream_t s);
 template <class T, class TO>
-cudaError_t launch_fill(const FillArgs<T, TO>& a, cudaStream_t s);
+cudaError_t launch_fill(const FillArgs<T, TO>& a, void* scratch, cudaStream_t s);
 
 }  // namespace cfft

@@ -32,17 +32,19 @@ namespace cfft {
 
 namespace {
 
-constexpr int kWarps = 8;
+constexpr int kWarps = 16;
 constexpr int kGroupMax = 8;
 
 __global__ void chunk_cosine_kernel(const int* n_nodes, const int64_t* offset, int n_chunks,
                                     double* cosv) {
-  int c = blockIdx.y;
-  if (c >= n_chunks) return;
-  int np = n_nodes[c];
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < np; l += gridDim.x * blockDim.x)
-    cosv[offset[c] + l] = cospi(((double)l + 0.5) / (double)np);
+  for (int c = blockIdx.y; c < n_chunks; c += gridDim.y) {
+    int np = n_nodes[c];
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < np; l += gridDim.x * blockDim.x)
+      cosv[offset[c] + l] = cospi(((double)l + 0.5) / (double)np);
+  }
 }
+
+__host__ __device__ __forceinline__ int padded(int i) { return i + (i >> 4); }
 
 template <class T>
 struct NodeCos;
@@ -55,16 +57,16 @@ struct NodeCos<double> {
   double v, pad;
 };
 
+// one task: (group of series g0.., harmonic qi, chunk of rows)
 template <class T, int TAPS>
-__global__ void __launch_bounds__(kWarps * 32)
-backproject_kernel(BackprojArgs<T> a, const int* chunk_nodes, const int64_t* chunk_off,
-                   const double* cosv) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void backproject_task(const BackprojArgs<T>& a, int gidx, int qi,
+                                                 int chunk, unsigned char* smem_raw) {
   constexpr int HALF = TAPS / 2 - 1;  // stencil nodes at base - HALF .. base - HALF + TAPS - 1
-  const int g0 = blockIdx.x * a.group;
+  const int* chunk_nodes = a.chunk_nodes;
+  const int64_t* chunk_off = a.chunk_off;
+  const double* cosv = a.cosv;
+  const int g0 = gidx * a.group;
   const int ng = min(a.group, a.series_per_q - g0);
-  const int qi = blockIdx.y;
-  const int chunk = blockIdx.z;
   const int r0 = chunk * a.rchunk;
   const int r1 = min(r0 + a.rchunk, a.n_rho);
   const int q = qi - a.q_max;
@@ -75,14 +77,17 @@ backproject_kernel(BackprojArgs<T> a, const int* chunk_nodes, const int64_t* chu
   const int seg = 2 * kseg + 1;
 
   cpx<T>* sg = reinterpret_cast<cpx<T>*>(smem_raw);                     // [ng][seg]
-  NodeCos<T>* scos = reinterpret_cast<NodeCos<T>*>(sg + (size_t)a.group * seg);  // [np]
+  NodeCos<T>* scos = reinterpret_cast<NodeCos<T>*>(sg + (size_t)a.group * padded(seg));  // [np]
   T* scq = reinterpret_cast<T*>(scos + np);                             // [np] cos(q alpha)
 
   const int tid = threadIdx.x;
+  // staged with one padding slot every 16 entries: lanes whose nodes sit a few grid
+  // steps apart then fall into different shared-memory banks
+  const int seg_p = padded(seg);
   for (int g = 0; g < ng; ++g) {
     const cpx<T>* src = a.grid + ((size_t)(g0 + g) * a.n_harm + qi) * (2 * a.grid_half + 1) +
                         (a.grid_half - kseg);
-    for (int t = tid; t < seg; t += blockDim.x) sg[(size_t)g * seg + t] = src[t];
+    for (int t = tid; t < seg; t += blockDim.x) sg[(size_t)g * seg_p + padded(t)] = src[t];
   }
   const int four_np = 4 * np;
   for (int t = tid; t < np; t += blockDim.x) {
@@ -181,12 +186,12 @@ backproject_kernel(BackprojArgs<T> a, const int* chunk_nodes, const int64_t* chu
 #pragma unroll
       for (int g = 0; g < kGroupMax; ++g) {
         if (g < ng) {
-          const cpx<T>* sgp = sg + (size_t)g * seg;
+          const cpx<T>* sgp = sg + (size_t)g * seg_p;
           cpx<T> va = mk((T)0, (T)0), vb = mk((T)0, (T)0);
 #pragma unroll
           for (int m = 0; m < TAPS; ++m) {
-            const cpx<T> xa = sgp[ia + m];
-            const cpx<T> xb = sgp[ib - m];
+            const cpx<T> xa = sgp[padded(ia + m)];
+            const cpx<T> xb = sgp[padded(ib - m)];
             va.re = fma(w[m], xa.re, va.re);
             va.im = fma(w[m], xa.im, va.im);
             vb.re = fma(w[m], xb.re, vb.re);
@@ -213,14 +218,294 @@ backproject_kernel(BackprojArgs<T> a, const int* chunk_nodes, const int64_t* chu
   }
 }
 
+// ---------------------------------------------------------------------------
+// Matrix form of the back-projection.  For harmonic q the table rows are a
+// linear map of the transform grid that is the same for every MBF pair:
+//   Z_q,g(rho_r) = sum_k W_q(r, k) g_q,g(s_k),
+//   W_q(r, k) = 1/(2 pi N') sum_l cos(q alpha_l) exp(-i pi u_rl / sigma) L_m(u_rl),
+// with u_rl = rho_r cos(alpha_l) / ds and L_m the Lagrange weight of grid
+// point k = floor(u_rl) - HALF + m.  One CTA owns a tile of WR rows and one q:
+// for each tile of WK grid points it scatters the stencils of the nodes that
+// reach the tile into W (shared memory), then multiplies W by the grid tile of
+// all MBF pairs of that q (a register-tiled complex product; 2 rows x up to
+// 8 series per thread).  The weights of a node are computed once per q instead
+// of once per series, and the grid values are read once per tile.
+constexpr int kWR = 64;       // rows per tile
+constexpr int kWK = 64;       // grid points per tile
+constexpr int kWThreads = 256;
+constexpr int kWSeriesMax = 64;
+
+template <class T>
+__host__ __device__ constexpr size_t wbp_smem_bytes(int n_nodes_max, int series) {
+  return (size_t)kWK * (kWR + 2) * sizeof(cpx<T>) + (size_t)kWK * series * sizeof(cpx<T>) +
+         (size_t)n_nodes_max * (sizeof(NodeCos<T>) + sizeof(T)) + (size_t)(3 * kWR + 2) * sizeof(int) + 64;
+}
+
 template <class T, int TAPS>
-cudaError_t launch_taps(const BackprojArgs<T>& a, const int* chunk_nodes, const int64_t* chunk_off,
-                        const double* cosv, int n_chunks, size_t smem, cudaStream_t s) {
+__device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int tile, int qi,
+                                                   unsigned char* smem_raw) {
+  constexpr int HALF = TAPS / 2 - 1;
+  const int S = a.series_per_q;
+  const int r0 = tile * a.rchunk;                 // a.rchunk == kWR
+  const int r1 = min(r0 + a.rchunk, a.n_rho);
+  const int q = qi - a.q_max;
+  const int np = a.chunk_nodes[tile];
+  const int tid = threadIdx.x;
+  // shared layout: W [WK][WR + 2] | G [WK][S] | node cos | cos(q alpha) | row ranges
+  cpx<T>* W = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* G = W + kWK * (kWR + 2);
+  NodeCos<T>* scos = reinterpret_cast<NodeCos<T>*>(G + kWK * S);
+  T* scq = reinterpret_cast<T*>(scos + np);
+  int* l_lo = reinterpret_cast<int*>(scq + np);
+  int* off = l_lo + kWR;                           // [WR + 1]
+  const int four_np = 4 * np;
+  for (int t = tid; t < np; t += blockDim.x) {
+    const double c = a.cosv[a.chunk_off[tile] + t];
+    NodeCos<T> nc;
+    if constexpr (sizeof(T) == 4) {
+      nc.hi = (float)c;
+      nc.lo = (float)(c - (double)nc.hi);
+    } else {
+      nc.v = c;
+      nc.pad = 0.0;
+    }
+    scos[t] = nc;
+    int e = (int)(((int64_t)q * (2 * t + 1)) % four_np);
+    if (e < 0) e += four_np;
+    scq[t] = cospi_((T)e / (T)(2 * np));
+  }
+  T den[TAPS];
+#pragma unroll
+  for (int m = 0; m < TAPS; ++m) {
+    long long d = 1;
+#pragma unroll
+    for (int j = 0; j < TAPS; ++j)
+      if (j != m) d *= (long long)(m - j);
+    den[m] = (T)1 / (T)d;
+  }
+  // GEMM thread layout: rows 2 rp, 2 rp + 1; series sg, sg + 8, ...
+  const int rp = tid & 31, sg = tid >> 5;
+  constexpr int SPT = kWSeriesMax / 8;
+  cpx<T> acc0[SPT], acc1[SPT];
+#pragma unroll
+  for (int j = 0; j < SPT; ++j) {
+    acc0[j] = mk((T)0, (T)0);
+    acc1[j] = mk((T)0, (T)0);
+  }
+  const double rho_top = (r1 - 1) * a.d_rho;
+  const int kmax = min(a.grid_half - 1, (int)ceil(rho_top / a.d_s) + TAPS);
+  const int k_first = -kmax, n_tiles = (2 * kmax + kWK) / kWK;
+  __syncthreads();
+  for (int kt = 0; kt < n_tiles; ++kt) {
+    const int k0 = k_first + kt * kWK;
+    // ---- zero W, load the grid tile of every series of this q, find node ranges
+    for (int t = tid; t < kWK * (kWR + 2); t += blockDim.x) W[t] = mk((T)0, (T)0);
+    for (int t = tid; t < kWK * S; t += blockDim.x) {
+      const int g = t / kWK, kk = t - g * kWK;
+      const int k = k0 + kk;
+      G[kk * S + g] = (k >= -a.grid_half && k <= a.grid_half)
+                          ? a.grid[((size_t)g * a.n_harm + qi) * (2 * a.grid_half + 1) + k + a.grid_half]
+                          : mk((T)0, (T)0);
+    }
+    if (tid < kWR) {
+      const int r = r0 + tid;
+      int lo = 0, hi = -1;
+      if (r < r1) {
+        const double arow = (double)r * a.d_rho / a.d_s;
+        if (arow <= 0.0) {
+          if (k0 <= TAPS - 1 - HALF && k0 + kWK - 1 >= -HALF) { lo = 0; hi = np - 1; }
+        } else {
+          // stencil bases b with [b - HALF, b - HALF + TAPS - 1] meeting [k0, k0 + WK)
+          const double ulo = (double)(k0 + HALF - TAPS + 1), uhi = (double)(k0 + kWK + HALF);
+          const double chi = fmin(1.0, uhi / arow), clo = fmax(-1.0, ulo / arow);
+          if (chi >= clo) {
+            const float scale = (float)np / 3.14159265f;
+            lo = (int)floorf(acosf((float)chi) * scale - 0.5f) - 1;
+            hi = (int)ceilf(acosf((float)clo) * scale - 0.5f) + 1;
+            lo = max(lo, 0);
+            hi = min(hi, np - 1);
+          }
+        }
+      }
+      l_lo[tid] = lo;
+      off[tid + 1] = max(hi - lo + 1, 0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      off[0] = 0;
+      for (int t = 0; t < kWR; ++t) off[t + 1] += off[t];
+    }
+    __syncthreads();
+    // ---- scatter the node stencils that reach this tile into W
+    const int total = off[kWR];
+    for (int it = tid; it < total; it += blockDim.x) {
+      int row = 0;
+      for (int step = kWR / 2; step > 0; step >>= 1)
+        if (off[row + step] <= it) row += step;
+      const int l = l_lo[row] + (it - off[row]);
+      const int r = r0 + row;
+      const double arow = (double)r * a.d_rho / a.d_s;
+      const NodeCos<T> nc = scos[l];
+      int base;
+      T fr;
+      cpx<T> ph;
+      if constexpr (sizeof(T) == 4) {
+        const float ahi = (float)arow, alo = (float)(arow - (double)ahi);
+        float p = ahi * nc.hi;
+        float e = fmaf(ahi, nc.hi, -p);
+        e = fmaf(ahi, nc.lo, e);
+        e = fmaf(alo, nc.hi, e);
+        float fl = floorf(p);
+        float f = (p - fl) + e;
+        if (f < 0.f) { f += 1.f; fl -= 1.f; }
+        if (f >= 1.f) { f -= 1.f; fl += 1.f; }
+        base = (int)fl;
+        fr = f;
+        const float inv_sigma = 1.0f / (float)a.sigma;
+        float ps = p * inv_sigma;
+        float red = ps - 2.f * floorf(0.5f * ps);
+        float sv, cv;
+        sincospif(-(red + e * inv_sigma), &sv, &cv);
+        ph = mk(cv, sv);
+      } else {
+        const double u = arow * nc.v;
+        const double fl = floor(u);
+        base = (int)fl;
+        fr = (T)(u - fl);
+        ph = expipi<T>(-u / (double)a.sigma);
+      }
+      const int kb = base - HALF - k0;   // tile column of tap 0
+      if (kb + TAPS - 1 < 0 || kb >= kWK) continue;
+      T w[TAPS];
+      {
+        T pre = (T)1;
+#pragma unroll
+        for (int m = 0; m < TAPS; ++m) {
+          w[m] = pre;
+          pre *= (fr - (T)(m - HALF));
+        }
+        T suf = (T)1;
+#pragma unroll
+        for (int m = TAPS - 1; m >= 0; --m) {
+          w[m] *= suf * den[m];
+          suf *= (fr - (T)(m - HALF));
+        }
+      }
+      const cpx<T> wc = scq[l] * ph;
+#pragma unroll
+      for (int m = 0; m < TAPS; ++m) {
+        const int kk = kb + m;
+        if (kk >= 0 && kk < kWK) {
+          T* dst = reinterpret_cast<T*>(&W[kk * (kWR + 2) + row]);
+          atomicAdd(dst, wc.re * w[m]);
+          atomicAdd(dst + 1, wc.im * w[m]);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- acc[rows 2rp, 2rp+1][series] += W[:, rows] x G[:, series]
+    for (int kk = 0; kk < kWK; ++kk) {
+      const cpx<T> w0 = W[kk * (kWR + 2) + 2 * rp];
+      const cpx<T> w1 = W[kk * (kWR + 2) + 2 * rp + 1];
+      const cpx<T>* gk = G + kk * S;
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        const int g = sg + 8 * j;
+        if (g < S) {
+          const cpx<T> gv = gk[g];
+          cmac(acc0[j], w0, gv);
+          cmac(acc1[j], w1, gv);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const T norm = (T)(1.0 / (2.0 * 3.14159265358979323846 * (double)np));
+#pragma unroll
+  for (int j = 0; j < SPT; ++j) {
+    const int g = sg + 8 * j;
+    if (g < S) {
+      cpx<T>* dst = a.table + ((size_t)g * a.n_harm + qi) * a.n_rho;
+      const int ra = r0 + 2 * rp, rb = ra + 1;
+      if (ra < r1) dst[ra] = mk(acc0[j].re * norm, acc0[j].im * norm);
+      if (rb < r1) dst[rb] = mk(acc1[j].re * norm, acc1[j].im * norm);
+    }
+  }
+}
+
+template <class T, int TAPS>
+__global__ void __launch_bounds__(kWThreads) backproject_w_kernel(BackprojArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  backproject_w_task<T, TAPS>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// persistent form over (item, row tile, harmonic) tasks
+template <class T, int TAPS>
+__global__ void __launch_bounds__(kWThreads)
+backproject_w_batch_kernel(const BackprojArgs<T>* items, const int4* tasks, int n_tasks, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    const int4 tk = tasks[t];
+    const BackprojArgs<T> a = items[tk.x];
+    backproject_w_task<T, TAPS>(a, tk.z, tk.y, smem_raw);
+    __syncthreads();
+  }
+}
+
+template <class T, int TAPS>
+__global__ void __launch_bounds__(kWarps * 32) backproject_kernel(BackprojArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  backproject_task<T, TAPS>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// persistent form over (item, group, harmonic, chunk) tasks
+template <class T, int TAPS>
+__global__ void __launch_bounds__(kWarps * 32)
+backproject_batch_kernel(const BackprojArgs<T>* items, const int4* tasks, int n_tasks, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    const int4 tk = tasks[t];
+    const int item = tk.x >> 12, gidx = tk.x & 4095;
+    const BackprojArgs<T> a = items[item];
+    backproject_task<T, TAPS>(a, gidx, tk.y, tk.z, smem_raw);
+    __syncthreads();
+  }
+}
+
+template <class T, int TAPS>
+cudaError_t launch_taps(const BackprojArgs<T>& a, int n_chunks, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(backproject_kernel<T, TAPS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.series_per_q + a.group - 1) / a.group, a.n_harm, n_chunks);
-  backproject_kernel<T, TAPS><<<grid, kWarps * 32, smem, s>>>(a, chunk_nodes, chunk_off, cosv);
+  backproject_kernel<T, TAPS><<<grid, kWarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T, int TAPS>
+cudaError_t launch_taps_batch(const BackprojArgs<T>* items, const int4* tasks, int n_tasks,
+                              int* counter, size_t smem, int n_ctas, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(backproject_batch_kernel<T, TAPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_batch_kernel<T, TAPS>,
+                                                    kWarps * 32, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  backproject_batch_kernel<T, TAPS><<<n_ctas * per_sm, kWarps * 32, smem, s>>>(items, tasks, n_tasks,
+                                                                             counter);
   return cudaGetLastError();
 }
 
@@ -229,32 +514,120 @@ cudaError_t launch_taps(const BackprojArgs<T>& a, const int* chunk_nodes, const 
 // shared memory bytes of one CTA for a group size, segment length and node count
 template <class T>
 size_t backproject_smem(int group, int max_seg, int max_nodes) {
-  return (size_t)group * max_seg * sizeof(cpx<T>) + (size_t)max_nodes * (sizeof(NodeCos<T>) + sizeof(T)) + 64;
+  return (size_t)group * padded(max_seg) * sizeof(cpx<T>) +
+         (size_t)max_nodes * (sizeof(NodeCos<T>) + sizeof(T)) + 64;
 }
 
 template <class T>
-cudaError_t launch_backproject_impl(const BackprojArgs<T>& a, const int* chunk_nodes,
+cudaError_t launch_backproject_impl(const BackprojArgs<T>& a0, const int* chunk_nodes,
                                     const int64_t* chunk_off, const double* cosv,
                                     const double* /*unused*/, int n_chunks, int max_nodes,
                                     int max_seg, cudaStream_t s) {
-  if (a.group > kGroupMax || a.group < 1) return cudaErrorInvalidValue;
+  if (a0.group > kGroupMax || a0.group < 1) return cudaErrorInvalidValue;
+  BackprojArgs<T> a = a0;
+  a.chunk_nodes = chunk_nodes;
+  a.chunk_off = chunk_off;
+  a.cosv = cosv;
   const size_t smem = backproject_smem<T>(a.group, max_seg, max_nodes);
   switch (a.taps) {
-    case 4: return launch_taps<T, 4>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 6: return launch_taps<T, 6>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 8: return launch_taps<T, 8>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 10: return launch_taps<T, 10>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 12: return launch_taps<T, 12>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 16: return launch_taps<T, 16>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 20: return launch_taps<T, 20>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
-    case 24: return launch_taps<T, 24>(a, chunk_nodes, chunk_off, cosv, n_chunks, smem, s);
+    case 4: return launch_taps<T, 4>(a, n_chunks, smem, s);
+    case 6: return launch_taps<T, 6>(a, n_chunks, smem, s);
+    case 8: return launch_taps<T, 8>(a, n_chunks, smem, s);
+    case 10: return launch_taps<T, 10>(a, n_chunks, smem, s);
+    case 12: return launch_taps<T, 12>(a, n_chunks, smem, s);
+    case 16: return launch_taps<T, 16>(a, n_chunks, smem, s);
+    case 20: return launch_taps<T, 20>(a, n_chunks, smem, s);
+    case 24: return launch_taps<T, 24>(a, n_chunks, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
+template <class T>
+cudaError_t launch_backproject_batch(const BackprojArgs<T>* items, const int4* tasks, int n_tasks,
+                                     int* counter, int taps, int group, int max_nodes, int max_seg,
+                                     int n_ctas, cudaStream_t s) {
+  if (group > kGroupMax || group < 1) return cudaErrorInvalidValue;
+  const size_t smem = backproject_smem<T>(group, max_seg, max_nodes);
+  switch (taps) {
+    case 8: return launch_taps_batch<T, 8>(items, tasks, n_tasks, counter, smem, n_ctas, s);
+    case 12: return launch_taps_batch<T, 12>(items, tasks, n_tasks, counter, smem, n_ctas, s);
+    case 16: return launch_taps_batch<T, 16>(items, tasks, n_tasks, counter, smem, n_ctas, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_backproject_batch<float>(const BackprojArgs<float>*, const int4*, int,
+                                                     int*, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_backproject_batch<double>(const BackprojArgs<double>*, const int4*, int,
+                                                      int*, int, int, int, int, int, cudaStream_t);
+
+template <class T>
+size_t backproject_w_smem(int max_nodes, int series) { return wbp_smem_bytes<T>(max_nodes, series); }
+int backproject_w_rows() { return kWR; }
+
+template <class T, int TAPS>
+cudaError_t launch_w_taps(const BackprojArgs<T>& a, int n_tiles, int max_nodes, cudaStream_t s) {
+  const size_t smem = wbp_smem_bytes<T>(max_nodes, a.series_per_q);
+  cudaError_t e = cudaFuncSetAttribute(backproject_w_kernel<T, TAPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(n_tiles, a.n_harm);
+  backproject_w_kernel<T, TAPS><<<grid, kWThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_backproject_w(const BackprojArgs<T>& a, int n_tiles, int max_nodes, cudaStream_t s) {
+  if (a.series_per_q > kWSeriesMax || a.rchunk != kWR) return cudaErrorInvalidValue;
+  switch (a.taps) {
+    case 8: return launch_w_taps<T, 8>(a, n_tiles, max_nodes, s);
+    case 12: return launch_w_taps<T, 12>(a, n_tiles, max_nodes, s);
+    case 16: return launch_w_taps<T, 16>(a, n_tiles, max_nodes, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T, int TAPS>
+cudaError_t launch_w_batch_taps(const BackprojArgs<T>* items, const int4* tasks, int n_tasks,
+                                int* counter, int max_nodes, int series, int n_ctas, cudaStream_t s) {
+  const size_t smem = wbp_smem_bytes<T>(max_nodes, series);
+  cudaError_t e = cudaFuncSetAttribute(backproject_w_batch_kernel<T, TAPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_w_batch_kernel<T, TAPS>,
+                                                    kWThreads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  backproject_w_batch_kernel<T, TAPS><<<n_ctas * per_sm, kWThreads, smem, s>>>(items, tasks, n_tasks,
+                                                                              counter);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_backproject_w_batch(const BackprojArgs<T>* items, const int4* tasks, int n_tasks,
+                                       int* counter, int taps, int max_nodes, int series, int n_ctas,
+                                       cudaStream_t s) {
+  if (series > kWSeriesMax) return cudaErrorInvalidValue;
+  switch (taps) {
+    case 8: return launch_w_batch_taps<T, 8>(items, tasks, n_tasks, counter, max_nodes, series, n_ctas, s);
+    case 12: return launch_w_batch_taps<T, 12>(items, tasks, n_tasks, counter, max_nodes, series, n_ctas, s);
+    case 16: return launch_w_batch_taps<T, 16>(items, tasks, n_tasks, counter, max_nodes, series, n_ctas, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template size_t backproject_w_smem<float>(int, int);
+template size_t backproject_w_smem<double>(int, int);
+template cudaError_t launch_backproject_w<float>(const BackprojArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_backproject_w<double>(const BackprojArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_backproject_w_batch<float>(const BackprojArgs<float>*, const int4*, int, int*,
+                                                       int, int, int, int, cudaStream_t);
+template cudaError_t launch_backproject_w_batch<double>(const BackprojArgs<double>*, const int4*, int,
+                                                        int*, int, int, int, int, cudaStream_t);
+
 cudaError_t launch_chunk_cosines(const int* n_nodes, const int64_t* offset, int n_chunks,
                                  int max_nodes, double* cosv, cudaStream_t s) {
-  dim3 grid((max_nodes + 255) / 256, n_chunks);
+  dim3 grid((max_nodes + 255) / 256, n_chunks < 65535 ? n_chunks : 65535);
   chunk_cosine_kernel<<<grid, 256, 0, s>>>(n_nodes, offset, n_chunks, cosv);
   return cudaGetLastError();
 }

@@ -21,9 +21,7 @@ namespace {
 
 constexpr double kEta0 = 376.730313668;  // free-space wave impedance, ohm
 
-__global__ void contour_kernel(ContourArgs a, ContourData d) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n) return;
+__device__ __forceinline__ void contour_node(const ContourArgs& a, const ContourData& d, int j) {
   double br = (j + 0.5) * a.step;
   double bi = 0.0, slope = 0.0;
   if (br < a.beta_p) {
@@ -54,9 +52,53 @@ __global__ void contour_kernel(ContourArgs a, ContourData d) {
   cpx<double> bw = bc * w;
   d.bw[j] = make_double2(bw.re, bw.im);
   d.bi_rel[j] = a.height > 0.0 ? bi / a.height : 0.0;
+  if (d.bi_rel_f) d.bi_rel_f[j] = (float)d.bi_rel[j];
   d.green_p[j] = make_double2(p.re, p.im);
   cpx<double> rb2 = r * b2;  // R beta_c^2: the k k^T term is R beta_c^2 u u^T
   d.green_r[j] = make_double2(rb2.re, rb2.im);
+  if (d.dp_eps) {
+    // derivatives with respect to eps_r (dk1 = k0^2 / (2 k1)) and h (k2 does not
+    // depend on either): c' = -s (k1 h)', s' = c (k1 h)', then the quotient rule
+    // on C = -j eta0/k0 s / (Te Tm) and the products P = C N_P, R = C N_R
+    for (int which = 0; which < 2; ++which) {
+      const bool eps = which == 0;
+      cpx<double> dk1 = eps ? cdiv(mk(0.5 * k02, 0.0), k1) : mk(0.0, 0.0);
+      cpx<double> darg = eps ? mk(dk1.re * a.hs, dk1.im * a.hs) : k1;  // d(k1 h)
+      cpx<double> dc = mk(0.0, 0.0) - sn * darg;
+      cpx<double> ds = cs * darg;
+      double de = eps ? 1.0 : 0.0;
+      cpx<double> dte = dk1 * cs + k1 * dc + j1 * (k2 * ds);
+      cpx<double> dtm = de * (k2 * cs) + a.eps_r * (k2 * dc) + j1 * (dk1 * sn + k1 * ds);
+      cpx<double> tt = te * tm;
+      cpx<double> dtt = dte * tm + te * dtm;
+      // dC = -j eta0/k0 (ds Te Tm - s d(Te Tm)) / (Te Tm)^2
+      cpx<double> dcf = cdiv(mk(0.0, -kEta0 / a.k0) * (ds * tt - sn * dtt), tt * tt);
+      cpx<double> np = (a.eps_r * k02) * (k2 * cs) + j1 * (k02 * (k1 * sn));
+      cpx<double> dnp = (de * k02) * (k2 * cs) + (a.eps_r * k02) * (k2 * dc) +
+                        j1 * (k02 * (dk1 * sn + k1 * ds));
+      cpx<double> nr = k2 * cs + j1 * (k1 * sn);
+      cpx<double> dnr = k2 * dc + j1 * (dk1 * sn + k1 * ds);
+      cpx<double> dp = dcf * np + cfac * dnp;
+      cpx<double> dr = (dcf * nr + cfac * dnr) * b2;
+      (eps ? d.dp_eps : d.dp_h)[j] = make_double2(dp.re, dp.im);
+      (eps ? d.dr_eps : d.dr_h)[j] = make_double2(dr.re, dr.im);
+    }
+  }
+}
+
+__global__ void contour_kernel(ContourArgs a, ContourData d) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.n) contour_node(a, d, j);
+}
+
+// batched form: block b covers nodes map[b].y .. + 255 of item map[b].x
+__global__ void contour_batch_kernel(const ContourArgs* items, const ContourData* data,
+                                     const int2* map) {
+  const int2 bm = map[blockIdx.x];
+  const ContourArgs a = items[bm.x];
+  const ContourData d = data[bm.x];
+  int j = bm.y + threadIdx.x;
+  if (j < a.n) contour_node(a, d, j);
 }
 
 template <class T>
@@ -104,6 +146,11 @@ __global__ void nonfinite_kernel(const cpx<T>* buf, int64_t count, int* flag) {
 
 void launch_contour(const ContourArgs& a, const ContourData& d, cudaStream_t s) {
   contour_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a, d);
+}
+
+void launch_contour_batch(const ContourArgs* items, const ContourData* data, const int2* map,
+                          int n_blocks, cudaStream_t s) {
+  contour_batch_kernel<<<n_blocks, 256, 0, s>>>(items, data, map);
 }
 
 template <class T>

@@ -54,8 +54,8 @@ __device__ __forceinline__ cpx<T> shape_factor(const ShapeClass& c, cpx<T> kx, c
 // M is the MBF count padded to a compiled size (padding columns of Q are zero);
 // a.n_mbf is the real count.  Pairs are processed pc at a time through hbuf.
 template <class T, int M>
-__global__ void __launch_bounds__(kThreads) integrand_kernel(IntegrandArgs<T> a, int jt, int pc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void integrand_tile(const IntegrandArgs<T>& a, const int j0, int jt,
+                                               int pc, unsigned char* smem_raw) {
   const int na = a.n_alpha;
   const int pts = jt * na;
   const int nh = 2 * a.q_max + 1;
@@ -70,7 +70,6 @@ __global__ void __launch_bounds__(kThreads) integrand_kernel(IntegrandArgs<T> a,
   T* sy = sx + a.n_basis;
 
   const int tid = threadIdx.x;
-  const int j0 = blockIdx.x * jt;
   for (int t = tid; t < na; t += kThreads) {
     T s, c;
     sincospi_((T)(-2.0 * (double)t / (double)na), &s, &c);
@@ -215,6 +214,60 @@ __global__ void __launch_bounds__(kThreads) integrand_kernel(IntegrandArgs<T> a,
 }
 
 template <class T, int M>
+__global__ void __launch_bounds__(kThreads) integrand_kernel(IntegrandArgs<T> a, int jt, int pc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  integrand_tile<T, M>(a, blockIdx.x * jt, jt, pc, smem_raw);
+}
+
+// batched form: block b processes node tile map[b].y of item map[b].x
+template <class T, int M>
+__global__ void __launch_bounds__(kThreads) integrand_batch_kernel(const IntegrandArgs<T>* items,
+                                                                   const int2* map, int jt, int pc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 bm = map[blockIdx.x];
+  const IntegrandArgs<T> a = items[bm.x];
+  integrand_tile<T, M>(a, bm.y, jt, pc, smem_raw);
+}
+
+// points per block: all n_alpha angles of jt contour nodes; pairs through hbuf in chunks
+template <class T, int M>
+bool integrand_shape(const IntegrandArgs<T>& a, int* jt_out, int* pc_out, size_t* smem_out) {
+  const int n_pairs = a.n_mbf * a.n_mbf;
+  const int fixed = a.n_alpha * (int)sizeof(cpx<T>) +
+                    a.n_basis * (M * (int)sizeof(cpx<T>) + 2 * (int)sizeof(T)) + 64;
+  const int budget = 200 * 1024;
+  int pc = n_pairs < 16 ? n_pairs : 16;
+  int jt = 0;
+  for (;;) {
+    int per_point = (4 * M + pc) * (int)sizeof(cpx<T>);
+    jt = (budget - fixed) / (per_point * a.n_alpha);
+    if (jt >= 1 || pc == 1) break;
+    pc = (pc + 1) / 2;
+  }
+  if (jt < 1) return false;
+  if (jt > 8) jt = 8;
+  while (jt > 1 && jt * a.n_alpha > 4 * kThreads) --jt;
+  *jt_out = jt;
+  *pc_out = pc;
+  *smem_out = (size_t)fixed + (size_t)(4 * M + pc) * sizeof(cpx<T>) * jt * a.n_alpha;
+  return true;
+}
+
+template <class T, int M>
+cudaError_t launch_m_batch(const IntegrandArgs<T>& shape_args, const IntegrandArgs<T>* items,
+                           const int2* map, int n_blocks, int jt, cudaStream_t s) {
+  int jt0, pc;
+  size_t smem;
+  if (!integrand_shape<T, M>(shape_args, &jt0, &pc, &smem)) return cudaErrorInvalidConfiguration;
+  if (jt != jt0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(integrand_batch_kernel<T, M>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  integrand_batch_kernel<T, M><<<n_blocks, kThreads, smem, s>>>(items, map, jt, pc);
+  return cudaGetLastError();
+}
+
+template <class T, int M>
 cudaError_t launch_m(const IntegrandArgs<T>& a, cudaStream_t s) {
   const int n_pairs = a.n_mbf * a.n_mbf;
   const int fixed = a.n_alpha * (int)sizeof(cpx<T>) +
@@ -242,6 +295,43 @@ cudaError_t launch_m(const IntegrandArgs<T>& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// node-tile height used by the batched launch for this element and angle count
+template <class T>
+int integrand_tile_nodes(const IntegrandArgs<T>& a, int n_mbf_padded) {
+  int jt = 0, pc = 0;
+  size_t smem = 0;
+  bool ok = false;
+  switch (n_mbf_padded) {
+    case 1: ok = integrand_shape<T, 1>(a, &jt, &pc, &smem); break;
+    case 2: ok = integrand_shape<T, 2>(a, &jt, &pc, &smem); break;
+    case 4: ok = integrand_shape<T, 4>(a, &jt, &pc, &smem); break;
+    case 8: ok = integrand_shape<T, 8>(a, &jt, &pc, &smem); break;
+    default: ok = false;
+  }
+  return ok ? jt : 0;
+}
+
+template <class T>
+cudaError_t launch_integrand_batch(const IntegrandArgs<T>& shape_args, const IntegrandArgs<T>* items,
+                                   const int2* map, int n_blocks, int jt, int n_mbf_padded,
+                                   cudaStream_t s) {
+  switch (n_mbf_padded) {
+    case 1: return launch_m_batch<T, 1>(shape_args, items, map, n_blocks, jt, s);
+    case 2: return launch_m_batch<T, 2>(shape_args, items, map, n_blocks, jt, s);
+    case 4: return launch_m_batch<T, 4>(shape_args, items, map, n_blocks, jt, s);
+    case 8: return launch_m_batch<T, 8>(shape_args, items, map, n_blocks, jt, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template int integrand_tile_nodes<float>(const IntegrandArgs<float>&, int);
+template int integrand_tile_nodes<double>(const IntegrandArgs<double>&, int);
+template cudaError_t launch_integrand_batch<float>(const IntegrandArgs<float>&, const IntegrandArgs<float>*,
+                                                   const int2*, int, int, int, cudaStream_t);
+template cudaError_t launch_integrand_batch<double>(const IntegrandArgs<double>&,
+                                                    const IntegrandArgs<double>*, const int2*, int,
+                                                    int, int, cudaStream_t);
 
 template <class T>
 cudaError_t launch_integrand(const IntegrandArgs<T>& a, int n_mbf_padded, cudaStream_t s) {

@@ -182,3 +182,18 @@ def test_patch_full_size_sampled(torch_cuda):
     err = cc.rel_err_per_pair(got[..., rows], ref)
     print("full-size sampled rel err", err.max(), ctx.info())
     assert err.max() < TOL["fp32"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_backprojection_forms_agree(torch_cuda, precision):
+    """The matrix form and the direct gather form of the back-projection evaluate the
+    same quadrature; both against the oracle (3 rotation classes: 48 series per q)."""
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch(precision, n=1024, n_rho=200, rho_max=4.0, q_max=2, rotation_classes=4)
+    _, w_form = cc.gpu_table(wl)
+    _, g_form = cc.gpu_table(wl, options={cfft.OPT_BP_GATHER: 1})
+    ref, _, _ = cc.oracle_table(wl, classes=(0, 1, 2, 3))
+    ew = cc.rel_err_per_pair(w_form, ref).max()
+    eg = cc.rel_err_per_pair(g_form, ref).max()
+    print(precision, "matrix form", ew, "gather form", eg)
+    assert ew < TOL[precision] and eg < TOL[precision]

@@ -202,3 +202,31 @@ def patch_m4(n=16384, n_rho=8192, rho_max=50.0, q_max=16, precision="fp32",
 def irregular_array(n_elements=10000, radius=60.0, r_min=0.5, seed=3):
     """Poisson-disc positions (radius read as the disc radius) and rotations."""
     return poisson_disc(n_elements, radius, r_min, seed), rotations(n_elements, seed)
+
+
+def sweep_items(n_freq=64, n_sub=8, seed=4, rho_max=50.0, oversample=3.0, f_lo=0.8, f_hi=1.2,
+                n_base=4096, n_levels=5, height_in_steps=6.0):
+    """Batched sweep: n_freq frequencies (k0 = 2 pi f, lengths in wavelengths at the band
+    centre) x n_sub substrates with eps_r ~ U[2, 10], h ~ U[0.02, 0.1] (seeded).  Each item
+    gets its own contour: beta_max = 5 k_d, beta_p ~ 1.3 k_d on a cell boundary, height a
+    few node spacings, and n = n_base * 2^u with u uniform in {0 .. n_levels-1}, raised
+    until the s-period 2 pi / step covers 2 rho_max `oversample` times (the 1-D form of
+    the paper's sampling rule, Eq. 26)."""
+    rng = np.random.default_rng(seed)
+    eps = rng.uniform(2.0, 10.0, n_sub)
+    hs = rng.uniform(0.02, 0.1, n_sub)
+    freqs = np.linspace(f_lo, f_hi, n_freq)
+    items = []
+    for fi, f in enumerate(freqs):
+        for si in range(n_sub):
+            k0 = TWO_PI * f
+            kd = k0 * math.sqrt(eps[si])
+            beta_max = 5.0 * kd
+            n = n_base * 2 ** int(rng.integers(0, n_levels))
+            while TWO_PI / (beta_max / n) < 2.0 * rho_max * oversample:
+                n *= 2
+            step = beta_max / n
+            items.append({"eps_r": float(eps[si]), "h": float(hs[si]), "k0": k0, "n": int(n),
+                          "beta_max": beta_max, "beta_p": round(1.3 * kd / step) * step,
+                          "height": height_in_steps * step, "taylor_order": -1})
+    return items
