@@ -124,13 +124,18 @@ def table_workload():
     return workloads.patch_m4(precision="fp32", **TABLE_SIZE)
 
 
+FILL_SIZE = {}
+
+
 def fill_workload():
     """Irregular array: 10,000 Poisson-disc elements (min spacing 0.5) in a disc of
     radius 60 lambda0, rotations in {0, 90}; table of the patch element to
-    rho_max = 121 lambda0 with four rotation classes."""
+    rho_max = 121 lambda0 with four rotation classes.  A smaller element count (for
+    profiling) keeps the areal density: the disc radius scales with sqrt(A)."""
     wl = workloads.patch_m4(n=16384, n_rho=16384, rho_max=121.0, q_max=16, precision="fp32",
                             rotation_classes=4)
-    pos, rot = workloads.irregular_array()
+    a = FILL_SIZE.get("n_elements", 10000)
+    pos, rot = workloads.irregular_array(n_elements=a, radius=60.0 * math.sqrt(a / 10000.0))
     return wl, pos, rot
 
 
@@ -272,6 +277,8 @@ def bench_fill(torch, cfft, args, dev):
     wl, pos, rot = fill_workload()
     ctx = cfft.Context(dev)
     set_problem(ctx, wl)
+    if "block" in FILL_SIZE:
+        ctx.set_option(cfft.OPT_FILL_BLOCK, FILL_SIZE["block"])
     t0 = time.perf_counter()
     ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 4)
     tab_s = time.perf_counter() - t0
@@ -502,7 +509,13 @@ def main():
     ap.add_argument("--table-n", type=int, help="contour samples (small profiling case)")
     ap.add_argument("--table-nrho", type=int, help="rho points (small profiling case)")
     ap.add_argument("--table-rho", type=float, help="rho_max (small profiling case)")
+    ap.add_argument("--fill-elements", type=int, help="array size of the fill (small profiling case)")
+    ap.add_argument("--fill-block", type=int, help="test elements per row block of the fill")
     args = ap.parse_args()
+    if args.fill_elements is not None:
+        FILL_SIZE["n_elements"] = args.fill_elements
+    if args.fill_block is not None:
+        FILL_SIZE["block"] = args.fill_block
     for k, v in (("n", args.table_n), ("n_rho", args.table_nrho), ("rho_max", args.table_rho)):
         if v is not None:
             TABLE_SIZE[k] = v

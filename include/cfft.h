@@ -81,7 +81,12 @@ typedef enum {
  *   BP_GATHER    a value > 0 selects the direct gather form of the
  *                back-projection instead of its matrix form (both evaluate
  *                the same quadrature; the matrix form needs at most 64 series
- *                per harmonic and 8, 12 or 16 taps)                        */
+ *                per harmonic and 8, 12 or 16 taps)
+ *   FILL_BLOCK   test elements per row block of the bucketed fill (default
+ *                1024); a value < 0 selects the per-row fill, which also
+ *                serves the cases the bucketed fill does not cover (M other
+ *                than 1, 2, 4; fill taps other than 8, 12, 16; an output
+ *                precision different from the table's)                    */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -90,7 +95,8 @@ typedef enum {
   CFFT_OPT_ALPHA_MARGIN = 4,
   CFFT_OPT_CHECK_FINITE = 5,
   CFFT_OPT_DERIVATIVES = 6,
-  CFFT_OPT_BP_GATHER = 7
+  CFFT_OPT_BP_GATHER = 7,
+  CFFT_OPT_FILL_BLOCK = 8
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -190,10 +196,12 @@ cfft_status cfft_copy_table(const cfft_ctx* ctx, void* dst, int64_t bytes, int d
  * Requires a table (CFFT_ERR_STATE).  A pair farther apart than the table's
  * rho_max makes the call return CFFT_ERR_ARG (after the kernel ran; the
  * affected entries are zero).  Stream-ordered; synchronizes for that check.
- * The element pairs are counting-sorted by (rotation class, stencil row)
- * before the interpolation so that pairs sharing table rows run together;
- * the context owns that scratch (4 bytes per element pair plus 12 bytes per
- * table row and class) and keeps it for the next fill. */
+ * The element pairs of each block of test elements are counting-sorted by
+ * (rotation class, stencil row) before the interpolation, so that pairs that
+ * share table rows run together on one copy of those rows in shared memory;
+ * the context owns that scratch (4 bytes per element pair of up to 2^27 pairs
+ * at a time, 8 bytes per (row block, class, table row), 16 bytes per element)
+ * and keeps it for the next fill. */
 cfft_status cfft_fill_reduced_matrix(cfft_ctx* ctx, int n_elements, const double* pos_xy,
                                      const int* rot, void* z_out, int64_t ld,
                                      int out_complex128);

@@ -11,6 +11,8 @@
 #include <vector>
 
 #include "../../include/cfft.h"
+#include <type_traits>
+
 #include "cfft_common.cuh"
 
 namespace cfft {
@@ -76,7 +78,7 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic)
-  double opt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -339,9 +341,12 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   // ---- a5: back-projection to the rho grid
   // the matrix-form back-projection handles up to 64 series per harmonic with 8/12/16 taps;
   // otherwise the direct gather form runs
-  const bool wform = series_per_q <= 64 && (bp_taps == 8 || bp_taps == 12 || bp_taps == 16) &&
-                     !(ctx->opt[CFFT_OPT_BP_GATHER] > 0);
-  const int rchunk = wform ? backproject_w_rows() : 32;
+  // FP32-mixed: the paired-harmonic matrix form (one interpolation matrix per |q|)
+  const bool taps_ok = bp_taps == 8 || bp_taps == 12 || bp_taps == 16;
+  const bool gather = ctx->opt[CFFT_OPT_BP_GATHER] > 0;
+  const bool pform = !fp64 && taps_ok && !gather;
+  const bool wform = !pform && series_per_q <= 64 && taps_ok && !gather;
+  const int rchunk = pform ? backproject_pm_rows() : (wform ? backproject_w_rows() : 32);
   const int n_chunks = (ctx->n_rho + rchunk - 1) / rchunk;
   const double d_rho = ctx->rho_max / (ctx->n_rho - 1);
   std::vector<int> cn(n_chunks);
@@ -384,6 +389,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
     return fail(ctx, CFFT_ERR_ARG, "rho_max too large for one shared-memory segment");
   if (wform && backproject_w_smem<T>(max_nodes, series_per_q) > smem_cap)
     return fail(ctx, CFFT_ERR_ARG, "rho_max too large for the angular node table");
+  if (pform && backproject_pm_smem(max_nodes) > smem_cap)
+    return fail(ctx, CFFT_ERR_ARG, "rho_max too large for the angular node table");
   group = std::min(group, series_per_q);
   BackprojArgs<T> ba{};
   ba.series_per_q = series_per_q;
@@ -401,11 +408,19 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ba.alpha_margin = margin;
   ba.grid = ctx->d_grid.as<cpx<T>>();
   ba.table = ctx->d_table.as<cpx<T>>() + ch * table_elems;
-  if (wform) {
+  if (pform || wform) {
     ba.chunk_nodes = ctx->d_cnodes.as<int>();
     ba.chunk_off = ctx->d_coff.as<int64_t>();
     ba.cosv = ctx->d_cos.as<double>();
-    CFFT_CUDA(launch_backproject_w<T>(ba, n_chunks, max_nodes, st), "backprojection kernel");
+    if constexpr (sizeof(T) == 4) {
+      if (pform) {
+        CFFT_CUDA(launch_backproject_pm(ba, n_chunks, max_nodes, st), "backprojection kernel");
+      } else {
+        CFFT_CUDA(launch_backproject_w<T>(ba, n_chunks, max_nodes, st), "backprojection kernel");
+      }
+    } else {
+      CFFT_CUDA(launch_backproject_w<T>(ba, n_chunks, max_nodes, st), "backprojection kernel");
+    }
   } else {
     CFFT_CUDA(launch_backproject_impl<T>(ba, ctx->d_cnodes.as<int>(), ctx->d_coff.as<int64_t>(),
                                          ctx->d_cos.as<double>(), ctx->d_lag.as<double>(), n_chunks,
@@ -486,13 +501,19 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
   fa.rot = rot;
   fa.z = reinterpret_cast<cpx<TO>*>(z);
   fa.err = ctx->d_flag.as<int>() + 1;
-  CFFT_CUDA(ctx->d_fill.ensure(fill_scratch_bytes(n_el, ctx->cls_stored * ctx->n_rho)), "alloc fill scratch");
+  FillBucketPlan plan{};
+  plan.ok = false;
+  if (std::is_same<T, TO>::value && ctx->opt[CFFT_OPT_FILL_BLOCK] >= 0)
+    plan = plan_fill_bucketed<T>(n_el, fa.n_mbf, fa.n_harm, fa.n_rho, fa.taps, fa.n_cls,
+                                 (int)ctx->opt[CFFT_OPT_FILL_BLOCK]);
+  if (plan.ok) CFFT_CUDA(ctx->d_fill.ensure(plan.scratch), "alloc fill scratch");
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
-  cudaError_t le = launch_fill<T, TO>(fa, ctx->d_fill.p, ctx->stream);
+  cudaError_t le = launch_fill<T, TO>(fa, plan, ctx->d_fill.p, ctx->stream);
   if (le != cudaSuccess) return cuda_fail(ctx, le, "fill kernel");
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "fill");
+  if (flag & 2) return fail(ctx, CFFT_ERR_NUMERIC, "fill: a stencil left its bucket (internal error)");
   if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the table's rho_max");
   return CFFT_OK;
 }
@@ -527,11 +548,10 @@ cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const
   b.d_rho = ctx->rho_max / (ctx->n_rho - 1);
   b.grad_pos = grad_pos;
   b.grad_theta = grad_theta;
-  CFFT_CUDA(ctx->d_fill.ensure(fill_scratch_bytes(n_el, ctx->cls_stored * ctx->n_rho)), "alloc fill scratch");
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
   if (grad_pos) CFFT_CUDA(cudaMemsetAsync(grad_pos, 0, (size_t)2 * n_el * sizeof(double), ctx->stream), "zero");
   if (grad_theta) CFFT_CUDA(cudaMemsetAsync(grad_theta, 0, 2 * sizeof(double), ctx->stream), "zero");
-  cudaError_t le = launch_fill_backward<T, TG>(b, ctx->d_fill.p, ctx->stream);
+  cudaError_t le = launch_fill_backward<T, TG>(b, ctx->stream);
   if (le != cudaSuccess) return cuda_fail(ctx, le, "fill backward kernel");
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
@@ -585,6 +605,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   const int bp_taps = ctx->opt[CFFT_OPT_BP_TAPS] > 0 ? (int)ctx->opt[CFFT_OPT_BP_TAPS] : (fp64 ? 16 : 12);
   if (bp_taps != 8 && bp_taps != 12 && bp_taps != 16)
     return fail(ctx, CFFT_ERR_ARG, "batched back-projection taps must be 8, 12 or 16");
+  const bool pform_b = !fp64;  // paired-harmonic matrix form in FP32-mixed
   const double margin = ctx->opt[CFFT_OPT_ALPHA_MARGIN] > 0 ? ctx->opt[CFFT_OPT_ALPHA_MARGIN] : 24.0;
   const double d_rho = rho_max / (n_rho - 1);
   const size_t table_elems = (size_t)pairs * nh * n_rho;
@@ -736,7 +757,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     CFFT_CUDA(ctx->b_coff.ensure(coff.size() * sizeof(int64_t)), "alloc plan");
     CFFT_CUDA(ctx->b_cos.ensure(cos_total * sizeof(double)), "alloc plan");
     CFFT_CUDA(ctx->d_tw.ensure((size_t)L * sizeof(cpx<T>)), "alloc twiddles");
-    if (backproject_w_smem<T>(max_nodes, pairs) > 225 * 1024 || pairs > 64)
+    if (pform_b ? backproject_pm_smem(max_nodes) > 225 * 1024
+                : (backproject_w_smem<T>(max_nodes, pairs) > 225 * 1024 || pairs > 64))
       return fail(ctx, CFFT_ERR_ARG, "batch: rho_max too large for the angular node table");
     const int group = std::min(8, pairs);
     double work_bp = 0, work_fft = 0;
@@ -836,7 +858,13 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         ba.cosv = ctx->b_cos.as<double>();
         for (int c = n_chunks - 1; c >= 0; --c) {  // larger rho (more nodes) first
           int rows = std::min((c + 1) * rchunk, n_rho) - c * rchunk;
-          for (int q = 0; q < nh; ++q) btask.push_back(make_int4(i, q, c, 0));
+          if (pform_b) {
+            const int n_sc = (pairs + backproject_pm_series_chunk() - 1) / backproject_pm_series_chunk();
+            for (int pq = 0; pq <= q_max; ++pq)
+              for (int sc = 0; sc < n_sc; ++sc) btask.push_back(make_int4(i, pq, c, sc));
+          } else {
+            for (int q = 0; q < nh; ++q) btask.push_back(make_int4(i, q, c, 0));
+          }
           work_bp += (double)cnodes[(size_t)i * n_chunks + c] * rows * series;
         }
         node_off += it.n;
@@ -930,9 +958,20 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
           ++launches;
         }
         if (w == 0) rec(ctx->bev[2]);
-        e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
-                                          ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
-                                          counters, bp_taps, max_nodes, pairs, 152, st);
+        if constexpr (sizeof(T) == 4) {
+          if (pform_b)
+            e = launch_backproject_pm_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
+                                            ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
+                                            bp_taps, max_nodes, 152, st);
+          else
+            e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
+                                              ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
+                                              counters, bp_taps, max_nodes, pairs, 152, st);
+        } else {
+          e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
+                                            ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
+                                            counters, bp_taps, max_nodes, pairs, 152, st);
+        }
         if (e != cudaSuccess) return e;
         ++launches;
         if (w == 0) rec(ctx->bev[3]);
@@ -979,7 +1018,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
 
   // ---- autotune the sub-FFT length and the back-projection row chunk (cached per signature)
   int L = std::min(l_common, fp64 ? 8192 : 16384);
-  int rchunk = backproject_w_rows();  // row tile of the matrix-form back-projection
+  // row tile of the matrix-form back-projection (paired-harmonic form in FP32-mixed)
+  int rchunk = pform_b ? backproject_pm_rows() : backproject_w_rows();
   auto tc = ctx->tuned.find(sig);
   if (tc != ctx->tuned.end()) {
     L = tc->second.first;
@@ -1177,7 +1217,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 7) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 8) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   return CFFT_OK;
 }

@@ -267,6 +267,14 @@ cudaError_t launch_chunk_cosines(const int* n_nodes, const int64_t* offset, int 
                                  int max_nodes, double* cosv, cudaStream_t s);
 template <class T>
 size_t backproject_w_smem(int max_nodes, int series);
+// paired-harmonic matrix form (FP32-mixed, taps 8/12/16): tiles of backproject_pm_rows()
+// rows, tasks (tile, |q|, chunk of backproject_pm_series_chunk() series per sign)
+size_t backproject_pm_smem(int max_nodes);
+int backproject_pm_rows();
+int backproject_pm_series_chunk();
+cudaError_t launch_backproject_pm(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s);
+cudaError_t launch_backproject_pm_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
+                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s);
 int backproject_w_rows();
 template <class T>
 cudaError_t launch_backproject_w(const BackprojArgs<T>& a, int n_tiles, int max_nodes, cudaStream_t s);
@@ -291,10 +299,24 @@ struct FillBackArgs {
   double* grad_theta;        // [2], accumulated (eps_r, h)
 };
 
-size_t fill_scratch_bytes(int n_el, int n_keys);
+// plan of the bucketed fill (pairs counting-sorted by rotation class and
+// stencil row, table windows staged in shared memory); ok = false: per-row fill
+struct FillBucketPlan {
+  bool ok;
+  int win, n_cells, nb_bits, block_rows, rows_per_wave;
+  size_t n_keys_max, smem, scratch;
+};
+template <class T>
+FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, int taps, int n_cls,
+                                  int block_rows);
+template <class T>
+cudaError_t launch_fill_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& plan, void* scratch,
+                                 cudaStream_t s);
+
 template <class T, class TG>
-cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& a, void* scratch, cudaStream_t s);
+cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& a, cudaStream_t s);
+// plan.ok: bucketed fill with `scratch` of plan.scratch bytes; else the per-row fill
 template <class T, class TO>
-cudaError_t launch_fill(const FillArgs<T, TO>& a, void* scratch, cudaStream_t s);
+cudaError_t launch_fill(const FillArgs<T, TO>& a, const FillBucketPlan& plan, void* scratch, cudaStream_t s);
 
 }  // namespace cfft

@@ -236,28 +236,46 @@ constexpr int kWThreads = 256;
 constexpr int kWSeriesMax = 64;
 
 template <class T>
+__host__ __device__ constexpr int wbp_series_pad(int series) { return (series + 1) & ~1; }
+
+template <class T>
 __host__ __device__ constexpr size_t wbp_smem_bytes(int n_nodes_max, int series) {
-  return (size_t)kWK * (kWR + 2) * sizeof(cpx<T>) + (size_t)kWK * series * sizeof(cpx<T>) +
-         (size_t)n_nodes_max * (sizeof(NodeCos<T>) + sizeof(T)) + (size_t)(3 * kWR + 2) * sizeof(int) + 64;
+  return (size_t)kWK * (kWR + 2) * sizeof(cpx<T>) + (size_t)kWK * wbp_series_pad<T>(series) * sizeof(cpx<T>) +
+         (size_t)n_nodes_max * (sizeof(NodeCos<T>) + sizeof(T)) + (size_t)(2 * kWR) * sizeof(int) + 64;
+}
+
+// two adjacent complex values from shared memory (16-byte aligned)
+template <class T>
+__device__ __forceinline__ void ld_pair(const cpx<T>* p, cpx<T>& x0, cpx<T>& x1) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    x0 = mk(f.x, f.y);
+    x1 = mk(f.z, f.w);
+  } else {
+    x0 = p[0];
+    x1 = p[1];
+  }
 }
 
 template <class T, int TAPS>
 __device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int tile, int qi,
                                                    unsigned char* smem_raw) {
   constexpr int HALF = TAPS / 2 - 1;
+  constexpr int kSub = kWThreads / kWR;            // threads per row in the scatter
   const int S = a.series_per_q;
+  const int S2 = wbp_series_pad<T>(S);
   const int r0 = tile * a.rchunk;                 // a.rchunk == kWR
   const int r1 = min(r0 + a.rchunk, a.n_rho);
   const int q = qi - a.q_max;
   const int np = a.chunk_nodes[tile];
   const int tid = threadIdx.x;
-  // shared layout: W [WK][WR + 2] | G [WK][S] | node cos | cos(q alpha) | row ranges
+  // shared layout: W [WK][WR + 2] | G [WK][S2] | node cos | cos(q alpha) | row node ranges
   cpx<T>* W = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* G = W + kWK * (kWR + 2);
-  NodeCos<T>* scos = reinterpret_cast<NodeCos<T>*>(G + kWK * S);
+  NodeCos<T>* scos = reinterpret_cast<NodeCos<T>*>(G + kWK * S2);
   T* scq = reinterpret_cast<T*>(scos + np);
   int* l_lo = reinterpret_cast<int*>(scq + np);
-  int* off = l_lo + kWR;                           // [WR + 1]
+  int* l_hi = l_lo + kWR;
   const int four_np = 4 * np;
   for (int t = tid; t < np; t += blockDim.x) {
     const double c = a.cosv[a.chunk_off[tile] + t];
@@ -283,15 +301,21 @@ __device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int
       if (j != m) d *= (long long)(m - j);
     den[m] = (T)1 / (T)d;
   }
-  // GEMM thread layout: rows 2 rp, 2 rp + 1; series sg, sg + 8, ...
-  const int rp = tid & 31, sg = tid >> 5;
-  constexpr int SPT = kWSeriesMax / 8;
-  cpx<T> acc0[SPT], acc1[SPT];
+  // GEMM thread layout: a warp holds 8 row pairs x 4 series pairs, so each of its
+  // shared-memory loads covers one 128-byte line (W) or a broadcast (G)
+  const int lane = tid & 31, warp = tid >> 5;
+  const int rp = (warp & 3) * 8 + (lane & 7);     // rows 2 rp, 2 rp + 1
+  const int sp = (warp >> 2) * 4 + (lane >> 3);   // series 2 sp, 2 sp + 1 (+ 16 per pass)
+  constexpr int NPASS = kWSeriesMax / 16;
+  cpx<T> acc[NPASS][4];                           // [pass][row0 s0, row0 s1, row1 s0, row1 s1]
 #pragma unroll
-  for (int j = 0; j < SPT; ++j) {
-    acc0[j] = mk((T)0, (T)0);
-    acc1[j] = mk((T)0, (T)0);
-  }
+  for (int j = 0; j < NPASS; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[j][k] = mk((T)0, (T)0);
+  const int npass = (S2 + 15) / 16;
+  // scatter layout: kSub threads per row, nodes interleaved among them
+  const int srow = tid % kWR, ssub = tid / kWR;
+  const double arow = (double)(r0 + srow) * a.d_rho / a.d_s;
   const double rho_top = (r1 - 1) * a.d_rho;
   const int kmax = min(a.grid_half - 1, (int)ceil(rho_top / a.d_s) + TAPS);
   const int k_first = -kmax, n_tiles = (2 * kmax + kWK) / kWK;
@@ -300,18 +324,17 @@ __device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int
     const int k0 = k_first + kt * kWK;
     // ---- zero W, load the grid tile of every series of this q, find node ranges
     for (int t = tid; t < kWK * (kWR + 2); t += blockDim.x) W[t] = mk((T)0, (T)0);
-    for (int t = tid; t < kWK * S; t += blockDim.x) {
+    for (int t = tid; t < kWK * S2; t += blockDim.x) {
       const int g = t / kWK, kk = t - g * kWK;
       const int k = k0 + kk;
-      G[kk * S + g] = (k >= -a.grid_half && k <= a.grid_half)
-                          ? a.grid[((size_t)g * a.n_harm + qi) * (2 * a.grid_half + 1) + k + a.grid_half]
-                          : mk((T)0, (T)0);
+      G[kk * S2 + g] = (g < S && k >= -a.grid_half && k <= a.grid_half)
+                           ? a.grid[((size_t)g * a.n_harm + qi) * (2 * a.grid_half + 1) + k + a.grid_half]
+                           : mk((T)0, (T)0);
     }
     if (tid < kWR) {
       const int r = r0 + tid;
       int lo = 0, hi = -1;
       if (r < r1) {
-        const double arow = (double)r * a.d_rho / a.d_s;
         if (arow <= 0.0) {
           if (k0 <= TAPS - 1 - HALF && k0 + kWK - 1 >= -HALF) { lo = 0; hi = np - 1; }
         } else {
@@ -328,108 +351,335 @@ __device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int
         }
       }
       l_lo[tid] = lo;
-      off[tid + 1] = max(hi - lo + 1, 0);
+      l_hi[tid] = hi;
     }
     __syncthreads();
-    if (tid == 0) {
-      off[0] = 0;
-      for (int t = 0; t < kWR; ++t) off[t + 1] += off[t];
-    }
-    __syncthreads();
-    // ---- scatter the node stencils that reach this tile into W
-    const int total = off[kWR];
-    for (int it = tid; it < total; it += blockDim.x) {
-      int row = 0;
-      for (int step = kWR / 2; step > 0; step >>= 1)
-        if (off[row + step] <= it) row += step;
-      const int l = l_lo[row] + (it - off[row]);
-      const int r = r0 + row;
-      const double arow = (double)r * a.d_rho / a.d_s;
-      const NodeCos<T> nc = scos[l];
-      int base;
-      T fr;
-      cpx<T> ph;
+    // ---- scatter the node stencils that reach this tile into W (each thread one row:
+    // the lanes of a warp add into 32 different rows)
+    {
+      const int lo = l_lo[srow], hi = l_hi[srow];
+      float ahi = 0.f, alo = 0.f;
       if constexpr (sizeof(T) == 4) {
-        const float ahi = (float)arow, alo = (float)(arow - (double)ahi);
-        float p = ahi * nc.hi;
-        float e = fmaf(ahi, nc.hi, -p);
-        e = fmaf(ahi, nc.lo, e);
-        e = fmaf(alo, nc.hi, e);
-        float fl = floorf(p);
-        float f = (p - fl) + e;
-        if (f < 0.f) { f += 1.f; fl -= 1.f; }
-        if (f >= 1.f) { f -= 1.f; fl += 1.f; }
-        base = (int)fl;
-        fr = f;
-        const float inv_sigma = 1.0f / (float)a.sigma;
-        float ps = p * inv_sigma;
-        float red = ps - 2.f * floorf(0.5f * ps);
-        float sv, cv;
-        sincospif(-(red + e * inv_sigma), &sv, &cv);
-        ph = mk(cv, sv);
-      } else {
-        const double u = arow * nc.v;
-        const double fl = floor(u);
-        base = (int)fl;
-        fr = (T)(u - fl);
-        ph = expipi<T>(-u / (double)a.sigma);
+        ahi = (float)arow;
+        alo = (float)(arow - (double)ahi);
       }
-      const int kb = base - HALF - k0;   // tile column of tap 0
-      if (kb + TAPS - 1 < 0 || kb >= kWK) continue;
-      T w[TAPS];
-      {
-        T pre = (T)1;
+      for (int l = lo + ssub; l <= hi; l += kSub) {
+        const NodeCos<T> nc = scos[l];
+        int base;
+        T fr;
+        cpx<T> ph;
+        if constexpr (sizeof(T) == 4) {
+          float p = ahi * nc.hi;
+          float e = fmaf(ahi, nc.hi, -p);
+          e = fmaf(ahi, nc.lo, e);
+          e = fmaf(alo, nc.hi, e);
+          float fl = floorf(p);
+          float f = (p - fl) + e;
+          if (f < 0.f) { f += 1.f; fl -= 1.f; }
+          if (f >= 1.f) { f -= 1.f; fl += 1.f; }
+          base = (int)fl;
+          fr = f;
+          const float inv_sigma = 1.0f / (float)a.sigma;
+          float ps = p * inv_sigma;
+          float red = ps - 2.f * floorf(0.5f * ps);
+          float sv, cv;
+          sincospif(-(red + e * inv_sigma), &sv, &cv);
+          ph = mk(cv, sv);
+        } else {
+          const double u = arow * nc.v;
+          const double fl = floor(u);
+          base = (int)fl;
+          fr = (T)(u - fl);
+          ph = expipi<T>(-u / (double)a.sigma);
+        }
+        const int kb = base - HALF - k0;   // tile column of tap 0
+        if (kb + TAPS - 1 < 0 || kb >= kWK) continue;
+        T w[TAPS];
+        {
+          T pre = (T)1;
+#pragma unroll
+          for (int m = 0; m < TAPS; ++m) {
+            w[m] = pre;
+            pre *= (fr - (T)(m - HALF));
+          }
+          T suf = (T)1;
+#pragma unroll
+          for (int m = TAPS - 1; m >= 0; --m) {
+            w[m] *= suf * den[m];
+            suf *= (fr - (T)(m - HALF));
+          }
+        }
+        const cpx<T> wc = scq[l] * ph;
 #pragma unroll
         for (int m = 0; m < TAPS; ++m) {
-          w[m] = pre;
-          pre *= (fr - (T)(m - HALF));
-        }
-        T suf = (T)1;
-#pragma unroll
-        for (int m = TAPS - 1; m >= 0; --m) {
-          w[m] *= suf * den[m];
-          suf *= (fr - (T)(m - HALF));
-        }
-      }
-      const cpx<T> wc = scq[l] * ph;
-#pragma unroll
-      for (int m = 0; m < TAPS; ++m) {
-        const int kk = kb + m;
-        if (kk >= 0 && kk < kWK) {
-          T* dst = reinterpret_cast<T*>(&W[kk * (kWR + 2) + row]);
-          atomicAdd(dst, wc.re * w[m]);
-          atomicAdd(dst + 1, wc.im * w[m]);
+          const int kk = kb + m;
+          if (kk >= 0 && kk < kWK) {
+            T* dst = reinterpret_cast<T*>(&W[kk * (kWR + 2) + srow]);
+            atomicAdd(dst, wc.re * w[m]);
+            atomicAdd(dst + 1, wc.im * w[m]);
+          }
         }
       }
     }
     __syncthreads();
-    // ---- acc[rows 2rp, 2rp+1][series] += W[:, rows] x G[:, series]
+    // ---- acc[rows 2rp, 2rp+1][series 2sp, 2sp+1 (+16 j)] += W[:, rows] x G[:, series]
+#pragma unroll 4
     for (int kk = 0; kk < kWK; ++kk) {
-      const cpx<T> w0 = W[kk * (kWR + 2) + 2 * rp];
-      const cpx<T> w1 = W[kk * (kWR + 2) + 2 * rp + 1];
-      const cpx<T>* gk = G + kk * S;
+      cpx<T> w0, w1;
+      ld_pair(W + kk * (kWR + 2) + 2 * rp, w0, w1);
+      const cpx<T>* gk = G + kk * S2 + 2 * sp;
 #pragma unroll
-      for (int j = 0; j < SPT; ++j) {
-        const int g = sg + 8 * j;
-        if (g < S) {
-          const cpx<T> gv = gk[g];
-          cmac(acc0[j], w0, gv);
-          cmac(acc1[j], w1, gv);
+      for (int j = 0; j < NPASS; ++j) {
+        if (j < npass && 2 * sp + 16 * j < S2) {
+          cpx<T> g0, g1;
+          ld_pair(gk + 16 * j, g0, g1);
+          cmac(acc[j][0], w0, g0);
+          cmac(acc[j][1], w0, g1);
+          cmac(acc[j][2], w1, g0);
+          cmac(acc[j][3], w1, g1);
         }
       }
     }
     __syncthreads();
   }
   const T norm = (T)(1.0 / (2.0 * 3.14159265358979323846 * (double)np));
+  const int ra = r0 + 2 * rp, rb = ra + 1;
 #pragma unroll
-  for (int j = 0; j < SPT; ++j) {
-    const int g = sg + 8 * j;
-    if (g < S) {
-      cpx<T>* dst = a.table + ((size_t)g * a.n_harm + qi) * a.n_rho;
-      const int ra = r0 + 2 * rp, rb = ra + 1;
-      if (ra < r1) dst[ra] = mk(acc0[j].re * norm, acc0[j].im * norm);
-      if (rb < r1) dst[rb] = mk(acc1[j].re * norm, acc1[j].im * norm);
+  for (int j = 0; j < NPASS; ++j) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int g = 2 * sp + 16 * j + (k & 1);
+      const int r = (k < 2) ? ra : rb;
+      if (j < npass && g < S && r < r1)
+        a.table[((size_t)g * a.n_harm + qi) * a.n_rho + r] = mk(acc[j][k].re * norm, acc[j][k].im * norm);
     }
+  }
+}
+
+// ---- paired-harmonic matrix form (FP32-mixed)
+//
+// cos(q alpha) is even in q, so the interpolation matrix W_q of the matrix form
+// is the same for q and -q: one W per |q| serves the grids of both harmonics
+// (32 series: 16 of q = +|q| and 16 of q = -|q|), halving the scatter.  A CTA
+// owns 256 rows (one thread per row), so every thread adds the stencils of its
+// row's nodes into its own column of W with plain read-modify-write (no
+// atomics, no search for the row of a work item).  The product
+// W [256 rows x 32 grid points] x G [32 points x 32 series] is register-tiled
+// 4 rows x 8 series per thread; the lanes of a warp cover 8 row quads x 4
+// series octets, so each 16-byte shared-memory load is one wavefront.
+constexpr int kPR = 256;           // rows per tile = threads
+constexpr int kPK = 32;            // grid points per K-tile
+constexpr int kPStride = kPR + 8;  // W row stride (complex entries)
+constexpr int kPSeries = 16;       // series per sign per task
+
+size_t pm_smem_bytes(int n_nodes_max) {
+  return (size_t)kPK * kPStride * sizeof(cpx<float>) + (size_t)kPK * 2 * kPSeries * sizeof(cpx<float>) +
+         (size_t)n_nodes_max * (sizeof(NodeCos<float>) + sizeof(float)) + 64;
+}
+
+template <int TAPS>
+__device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a, int tile, int p, int chunk,
+                                                    unsigned char* smem_raw) {
+  constexpr int HALF = TAPS / 2 - 1;
+  const int S = a.series_per_q;
+  const int r0 = tile * kPR;
+  const int r1 = min(r0 + kPR, a.n_rho);
+  const int np = a.chunk_nodes[tile];
+  const int tid = threadIdx.x;
+  cpx<float>* W = reinterpret_cast<cpx<float>*>(smem_raw);
+  cpx<float>* G = W + kPK * kPStride;
+  NodeCos<float>* scos = reinterpret_cast<NodeCos<float>*>(G + kPK * 2 * kPSeries);
+  float* scq = reinterpret_cast<float*>(scos + np);
+  const int four_np = 4 * np;
+  for (int t = tid; t < np; t += blockDim.x) {
+    const double c = a.cosv[a.chunk_off[tile] + t];
+    NodeCos<float> nc;
+    nc.hi = (float)c;
+    nc.lo = (float)(c - (double)nc.hi);
+    scos[t] = nc;
+    int e = (int)(((int64_t)p * (2 * t + 1)) % four_np);
+    scq[t] = cospif((float)e / (float)(2 * np));
+  }
+  float den[TAPS];
+#pragma unroll
+  for (int m = 0; m < TAPS; ++m) {
+    long long d = 1;
+#pragma unroll
+    for (int j = 0; j < TAPS; ++j)
+      if (j != m) d *= (long long)(m - j);
+    den[m] = 1.0f / (float)d;
+  }
+  // GEMM layout
+  const int lane = tid & 31, warp = tid >> 5;
+  const int rq = warp * 8 + (lane & 7);     // rows 4 rq .. 4 rq + 3
+  const int so = lane >> 3;                 // series 8 so .. 8 so + 7
+  cpx<float> acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = mk(0.f, 0.f);
+  // scatter: this thread's row
+  const int r = r0 + tid;
+  const bool row_ok = r < r1;
+  const double arow = (double)r * a.d_rho / a.d_s;
+  const double inv_arow = arow > 0.0 ? 1.0 / arow : 0.0;
+  const float ahi = (float)arow, alo = (float)(arow - (double)ahi);
+  const float inv_sigma = 1.0f / (float)a.sigma;
+  const float scale = (float)np / 3.14159265f;
+  const double rho_top = (r1 - 1) * a.d_rho;
+  const int kmax = min(a.grid_half - 1, (int)ceil(rho_top / a.d_s) + TAPS);
+  const int k_first = -kmax, n_ktiles = (2 * kmax + kPK) / kPK;
+  const int qi_pos = a.q_max + p, qi_neg = a.q_max - p;
+  __syncthreads();
+  for (int kt = 0; kt < n_ktiles; ++kt) {
+    const int k0 = k_first + kt * kPK;
+    // ---- own column of W to zero, then the row's node stencils that reach this tile
+#pragma unroll
+    for (int kk = 0; kk < kPK; ++kk) W[kk * kPStride + tid] = mk(0.f, 0.f);
+    if (row_ok) {
+      int lo = 0, hi = -1;
+      if (arow <= 0.0) {
+        if (k0 <= TAPS - 1 - HALF && k0 + kPK - 1 >= -HALF) { lo = 0; hi = np - 1; }
+      } else {
+        // stencil bases b with [b - HALF, b - HALF + TAPS - 1] meeting [k0, k0 + PK)
+        const double chi = fmin(1.0, (double)(k0 + kPK + HALF) * inv_arow);
+        const double clo = fmax(-1.0, (double)(k0 + HALF - TAPS + 1) * inv_arow);
+        if (chi >= clo) {
+          lo = max((int)floorf(acosf((float)chi) * scale - 0.5f) - 1, 0);
+          hi = min((int)ceilf(acosf((float)clo) * scale - 0.5f) + 1, np - 1);
+        }
+      }
+      cpx<float>* wcol = W + tid;
+      for (int l = lo; l <= hi; ++l) {
+        const NodeCos<float> nc = scos[l];
+        float pr = ahi * nc.hi;
+        float e = fmaf(ahi, nc.hi, -pr);
+        e = fmaf(ahi, nc.lo, e);
+        e = fmaf(alo, nc.hi, e);
+        float fl = floorf(pr);
+        float f = (pr - fl) + e;
+        if (f < 0.f) { f += 1.f; fl -= 1.f; }
+        if (f >= 1.f) { f -= 1.f; fl += 1.f; }
+        const int kb = (int)fl - HALF - k0;   // tile column of tap 0
+        if (kb + TAPS - 1 < 0 || kb >= kPK) continue;
+        const float ps = pr * inv_sigma;
+        const float red = ps - 2.f * floorf(0.5f * ps);
+        float sv, cv;
+        sincospif(-(red + e * inv_sigma), &sv, &cv);
+        float w[TAPS];
+        {
+          float pre = 1.f;
+#pragma unroll
+          for (int m = 0; m < TAPS; ++m) {
+            w[m] = pre;
+            pre *= (f - (float)(m - HALF));
+          }
+          float suf = 1.f;
+#pragma unroll
+          for (int m = TAPS - 1; m >= 0; --m) {
+            w[m] *= suf * den[m];
+            suf *= (f - (float)(m - HALF));
+          }
+        }
+        const float cq = scq[l];
+        const float wr = cq * cv, wi = cq * sv;
+        if (kb >= 0 && kb + TAPS <= kPK) {
+#pragma unroll
+          for (int m = 0; m < TAPS; ++m) {
+            cpx<float> v = wcol[(kb + m) * kPStride];
+            v.re = fmaf(wr, w[m], v.re);
+            v.im = fmaf(wi, w[m], v.im);
+            wcol[(kb + m) * kPStride] = v;
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < TAPS; ++m) {
+            const int kk = kb + m;
+            if (kk >= 0 && kk < kPK) {
+              cpx<float> v = wcol[kk * kPStride];
+              v.re = fmaf(wr, w[m], v.re);
+              v.im = fmaf(wi, w[m], v.im);
+              wcol[kk * kPStride] = v;
+            }
+          }
+        }
+      }
+    }
+    // ---- grid tile: columns 0..15 the series of q = +p, 16..31 those of q = -p
+    for (int t = tid; t < kPK * 2 * kPSeries; t += blockDim.x) {
+      const int c = t / kPK, kk = t - c * kPK;
+      const int k = k0 + kk;
+      const int g = chunk * kPSeries + (c & (kPSeries - 1));
+      const int qi = c < kPSeries ? qi_pos : qi_neg;
+      const bool ok = g < S && (c < kPSeries || p > 0) && k >= -a.grid_half && k <= a.grid_half;
+      G[kk * 2 * kPSeries + c] =
+          ok ? a.grid[((size_t)g * a.n_harm + qi) * (2 * a.grid_half + 1) + k + a.grid_half] : mk(0.f, 0.f);
+    }
+    __syncthreads();
+    // ---- acc[4 rows][8 series] += W[:, rows] x G[:, series]
+#pragma unroll 2
+    for (int kk = 0; kk < kPK; ++kk) {
+      const float4* wp = reinterpret_cast<const float4*>(W + kk * kPStride + 4 * rq);
+      const float4 wa = wp[0], wb = wp[1];
+      const cpx<float> wv[4] = {mk(wa.x, wa.y), mk(wa.z, wa.w), mk(wb.x, wb.y), mk(wb.z, wb.w)};
+      const float4* gp = reinterpret_cast<const float4*>(G + kk * 2 * kPSeries + 8 * so);
+#pragma unroll
+      for (int j2 = 0; j2 < 4; ++j2) {
+        const float4 gv = gp[j2];
+        const cpx<float> g0 = mk(gv.x, gv.y), g1 = mk(gv.z, gv.w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          cmac(acc[i][2 * j2], wv[i], g0);
+          cmac(acc[i][2 * j2 + 1], wv[i], g1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const float norm = (float)(1.0 / (2.0 * 3.14159265358979323846 * (double)np));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = 8 * so + j;
+    const int g = chunk * kPSeries + (c & (kPSeries - 1));
+    if (g >= S || (c >= kPSeries && p == 0)) continue;
+    const int qi = c < kPSeries ? qi_pos : qi_neg;
+    cpx<float>* dst = a.table + ((size_t)g * a.n_harm + qi) * a.n_rho;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rr = r0 + 4 * rq + i;
+      if (rr < r1) dst[rr] = mk(acc[i][j].re * norm, acc[i][j].im * norm);
+    }
+  }
+}
+
+// tasks in a 1-D grid, larger rho tiles (more work) first
+template <int TAPS>
+__global__ void __launch_bounds__(kPR, 2) backproject_pm_kernel(BackprojArgs<float> a, int n_tiles, int n_p,
+                                                                int n_chunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int per_tile = n_p * n_chunk;
+  const int t = blockIdx.x;
+  const int tile = n_tiles - 1 - t / per_tile;
+  const int rem = t - (t / per_tile) * per_tile;
+  backproject_pm_task<TAPS>(a, tile, rem / n_chunk, rem - (rem / n_chunk) * n_chunk, smem_raw);
+}
+
+// persistent form over (item, |q|, tile, series chunk) tasks
+template <int TAPS>
+__global__ void __launch_bounds__(kPR, 2)
+backproject_pm_batch_kernel(const BackprojArgs<float>* items, const int4* tasks, int n_tasks, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    const int4 tk = tasks[t];
+    const BackprojArgs<float> a = items[tk.x];
+    backproject_pm_task<TAPS>(a, tk.z, tk.y, tk.w, smem_raw);
+    __syncthreads();
   }
 }
 
@@ -624,6 +874,57 @@ template cudaError_t launch_backproject_w_batch<float>(const BackprojArgs<float>
                                                        int, int, int, int, cudaStream_t);
 template cudaError_t launch_backproject_w_batch<double>(const BackprojArgs<double>*, const int4*, int,
                                                         int*, int, int, int, int, cudaStream_t);
+
+size_t backproject_pm_smem(int max_nodes) { return pm_smem_bytes(max_nodes); }
+int backproject_pm_rows() { return kPR; }
+int backproject_pm_series_chunk() { return kPSeries; }
+
+template <int TAPS>
+cudaError_t launch_pm_taps(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s) {
+  const size_t smem = pm_smem_bytes(max_nodes);
+  cudaError_t e = cudaFuncSetAttribute(backproject_pm_kernel<TAPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int n_p = a.q_max + 1;
+  const int n_chunk = (a.series_per_q + kPSeries - 1) / kPSeries;
+  backproject_pm_kernel<TAPS><<<n_tiles * n_p * n_chunk, kPR, smem, s>>>(a, n_tiles, n_p, n_chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_pm(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s) {
+  if (a.rchunk != kPR) return cudaErrorInvalidValue;
+  switch (a.taps) {
+    case 8: return launch_pm_taps<8>(a, n_tiles, max_nodes, s);
+    case 12: return launch_pm_taps<12>(a, n_tiles, max_nodes, s);
+    case 16: return launch_pm_taps<16>(a, n_tiles, max_nodes, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int TAPS>
+cudaError_t launch_pm_batch_taps(const BackprojArgs<float>* items, const int4* tasks, int n_tasks, int* counter,
+                                 int max_nodes, int n_ctas, cudaStream_t s) {
+  const size_t smem = pm_smem_bytes(max_nodes);
+  cudaError_t e = cudaFuncSetAttribute(backproject_pm_batch_kernel<TAPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_pm_batch_kernel<TAPS>, kPR, smem) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  backproject_pm_batch_kernel<TAPS><<<n_ctas * per_sm, kPR, smem, s>>>(items, tasks, n_tasks, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_pm_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
+                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s) {
+  switch (taps) {
+    case 8: return launch_pm_batch_taps<8>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 12: return launch_pm_batch_taps<12>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 16: return launch_pm_batch_taps<16>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_chunk_cosines(const int* n_nodes, const int64_t* offset, int n_chunks,
                                  int max_nodes, double* cosv, cudaStream_t s) {

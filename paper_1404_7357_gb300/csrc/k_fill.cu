@@ -19,6 +19,8 @@
 // warp touches one or two cache lines instead of 32, while every store stays
 // inside the CTA's 4 rows of the matrix (one page range, not the whole
 // matrix).  Each thread writes its M x M block as M runs of M entries.
+#include <type_traits>
+
 #include "cfft_common.cuh"
 
 namespace cfft {
@@ -343,10 +345,11 @@ void row_bins(int n_rho, double inv_d_rho, float* inv_bin, int* bins_per_class) 
 
 }  // namespace
 
-size_t fill_scratch_bytes(int, int) { return 16; }
-
 template <class T, class TO>
-cudaError_t launch_fill(const FillArgs<T, TO>& a, void* /*scratch*/, cudaStream_t s) {
+cudaError_t launch_fill(const FillArgs<T, TO>& a, const FillBucketPlan& plan, void* scratch, cudaStream_t s) {
+  if constexpr (std::is_same<T, TO>::value) {
+    if (plan.ok) return launch_fill_bucketed<T>(a, plan, scratch, s);
+  }
   if (a.n_mbf > kMaxM || a.taps > kMaxTaps || a.taps < 2) return cudaErrorInvalidValue;
   float inv_bin;
   int bpc;
@@ -361,7 +364,7 @@ cudaError_t launch_fill(const FillArgs<T, TO>& a, void* /*scratch*/, cudaStream_
 }
 
 template <class T, class TG>
-cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& b, void* /*scratch*/, cudaStream_t s) {
+cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& b, cudaStream_t s) {
   const FillArgs<T, float>& a = b.f;
   if (a.n_mbf > kMaxM || a.taps > kMaxTaps || a.taps < 2) return cudaErrorInvalidValue;
   float inv_bin;
@@ -376,13 +379,13 @@ cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& b, void* /*scratch*/
   return cudaGetLastError();
 }
 
-template cudaError_t launch_fill<float, float>(const FillArgs<float, float>&, void*, cudaStream_t);
-template cudaError_t launch_fill<float, double>(const FillArgs<float, double>&, void*, cudaStream_t);
-template cudaError_t launch_fill<double, double>(const FillArgs<double, double>&, void*, cudaStream_t);
-template cudaError_t launch_fill<double, float>(const FillArgs<double, float>&, void*, cudaStream_t);
-template cudaError_t launch_fill_backward<float, float>(const FillBackArgs<float, float>&, void*, cudaStream_t);
-template cudaError_t launch_fill_backward<float, double>(const FillBackArgs<float, double>&, void*, cudaStream_t);
-template cudaError_t launch_fill_backward<double, double>(const FillBackArgs<double, double>&, void*, cudaStream_t);
-template cudaError_t launch_fill_backward<double, float>(const FillBackArgs<double, float>&, void*, cudaStream_t);
+template cudaError_t launch_fill<float, float>(const FillArgs<float, float>&, const FillBucketPlan&, void*, cudaStream_t);
+template cudaError_t launch_fill<float, double>(const FillArgs<float, double>&, const FillBucketPlan&, void*, cudaStream_t);
+template cudaError_t launch_fill<double, double>(const FillArgs<double, double>&, const FillBucketPlan&, void*, cudaStream_t);
+template cudaError_t launch_fill<double, float>(const FillArgs<double, float>&, const FillBucketPlan&, void*, cudaStream_t);
+template cudaError_t launch_fill_backward<float, float>(const FillBackArgs<float, float>&, cudaStream_t);
+template cudaError_t launch_fill_backward<float, double>(const FillBackArgs<float, double>&, cudaStream_t);
+template cudaError_t launch_fill_backward<double, double>(const FillBackArgs<double, double>&, cudaStream_t);
+template cudaError_t launch_fill_backward<double, float>(const FillBackArgs<double, float>&, cudaStream_t);
 
 }  // namespace cfft

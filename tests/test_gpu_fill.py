@@ -1,0 +1,102 @@
+"""The bucketed fill (pairs counting-sorted by class and stencil row, table windows in
+shared memory) against the per-row fill and the oracle, over the cases it covers:
+M in {1, 2, 4}, 8/12/16 taps, several row-block sizes (blocks that split the element
+set raggedly), padded and odd leading dimensions, and pairs on the parity rows."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads
+from tests import cfft_cases as cc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _fill(torch, ctx, pos, rot, m, dt, ld=None, block=None):
+    from paper_1404_7357_gb300 import cfft
+    a = len(pos)
+    ld = ld or a * m
+    if block is not None:
+        ctx.set_option(cfft.OPT_FILL_BLOCK, block)
+    z = torch.full((a * m, ld), 7.0, dtype=dt, device="cuda:0")
+    rt = None if rot is None else torch.tensor(rot, device="cuda:0")
+    ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), rt, z)
+    out = z.cpu().numpy()
+    assert np.all(out[:, a * m:] == 7.0)   # padding untouched
+    return out[:, :a * m]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_bucketed_matches_per_row(torch_cuda, precision):
+    torch = torch_cuda
+    wl = cc.small_patch(precision, n=1024, n_rho=1024, rho_max=9.0, q_max=4, rotation_classes=4)
+    ctx, _ = cc.gpu_table(wl)
+    pos = workloads.poisson_disc(300, 4.4, 0.3, seed=31)
+    rot = workloads.rotations(len(pos), seed=31)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    ref = _fill(torch, ctx, pos, rot, 4, dt, block=-1)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    scale = np.abs(ref).max()
+    for block in (0, 5, 37, 1000):
+        got = _fill(torch, ctx, pos, rot, 4, dt, block=block)
+        err = np.abs(got - ref).max() / scale
+        print(precision, "block", block, "bucketed vs per-row", err)
+        assert err < tol
+
+
+@pytest.mark.parametrize("ld_pad", [0, 1, 2])
+def test_bucketed_leading_dimensions(torch_cuda, ld_pad):
+    torch = torch_cuda
+    wl = cc.small_patch("fp32", n=1024, n_rho=512, rho_max=5.0, q_max=3)
+    ctx, _ = cc.gpu_table(wl)
+    pos = workloads.poisson_disc(40, 2.4, 0.5, seed=7)
+    a = len(pos)
+    ref = _fill(torch, ctx, pos, None, 4, torch.complex64, block=-1)
+    got = _fill(torch, ctx, pos, None, 4, torch.complex64, ld=a * 4 + ld_pad, block=0)
+    assert np.abs(got - ref).max() < 2e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("taps", [8, 12, 16])
+def test_bucketed_taps_and_m2(torch_cuda, taps):
+    """M = 2 (two MBFs from the rooftop set) and each templated stencil width."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp32", n=1024, n_rho=512, rho_max=5.0, q_max=2, rotation_classes=4)
+    el = wl.element
+    wl = dataclasses.replace(wl, element=dataclasses.replace(el, q=np.ascontiguousarray(el.q[:, :2])))
+    ctx = cc.gpu_context(wl, options={cfft.OPT_FILL_TAPS: taps})
+    ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 4)
+    pos = workloads.poisson_disc(40, 2.4, 0.5, seed=8)
+    rot = workloads.rotations(len(pos), seed=8)
+    ref = _fill(torch, ctx, pos, rot, 2, torch.complex64, block=-1)
+    got = _fill(torch, ctx, pos, rot, 2, torch.complex64, block=0)
+    assert np.abs(got - ref).max() < 2e-6 * np.abs(ref).max()
+
+
+def test_bucketed_strip_m1_against_oracle(torch_cuda):
+    """M = 1 (strip dipole, FP64) against the oracle, including pairs closer than one
+    stencil half-width to rho = 0 (parity rows) and the diagonal."""
+    torch = torch_cuda
+    wl = workloads.strip_fp64(n=1024, n_rho=512, rho_max=4.0, q_max=4)
+    ctx, _ = cc.gpu_table(wl)
+    rng = np.random.default_rng(3)
+    pos = np.concatenate([rng.uniform(-1.3, 1.3, (18, 2)),
+                          np.array([[0.0, 0.0], [0.004, 0.003], [-0.002, 0.01]])])
+    got = _fill(torch, ctx, pos, None, 1, torch.complex128, block=0)
+    nodes, hq = cc.oracle_harmonics(wl)
+    a = len(pos)
+    pairs = [(i, j) for i in range(a) for j in range(a)]
+    rot0 = np.zeros(a, dtype=np.int32)
+    ref = np.array([blk[0, 0] for blk in cc.oracle_fill_entries(wl, hq, nodes, pos, rot0, pairs)])
+    err = np.abs(got.reshape(-1) - ref).max() / np.abs(ref).max()
+    print("strip M=1 bucketed vs oracle", err)
+    assert err < 1e-10

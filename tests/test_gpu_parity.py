@@ -197,3 +197,14 @@ def test_backprojection_forms_agree(torch_cuda, precision):
     eg = cc.rel_err_per_pair(g_form, ref).max()
     print(precision, "matrix form", ew, "gather form", eg)
     assert ew < TOL[precision] and eg < TOL[precision]
+
+
+def test_fp32_single_harmonic_and_ragged_tiles(torch_cuda):
+    """FP32-mixed with q_max = 0 (the paired-harmonic back-projection with |q| = 0 only)
+    and a rho grid that ends inside a row tile."""
+    wl = cc.small_patch("fp32", n=1024, n_rho=300, rho_max=4.0, q_max=0)
+    ctx, got = cc.gpu_table(wl)
+    ref, _, _ = cc.oracle_table(wl)
+    err = cc.rel_err_per_pair(got, ref).max()
+    print("fp32 q_max=0 rel err", err)
+    assert err < TOL["fp32"]
