@@ -304,8 +304,9 @@ def bench_fill(torch, cfft, args, dev):
     res = {"metric": "Z-fill entries/s", "value": entries * steps / (sum(ms) / 1e3),
            "unit": "entries/s", "ms_per_step": sum(ms) / steps,
            "workload": "irregular array: A=%d Poisson-disc elements (min spacing 0.5) in a disc of "
-                       "radius 60 lambda0, rotations {0,90}, M=4, complex64 %dx%d, table to rho %g "
-                       "lambda0 (%d points, 4 rotation classes)" % (a, a * m, a * m, wl.rho_max, wl.n_rho),
+                       "radius %.3g lambda0, rotations {0,90}, M=4, complex64 %dx%d, table to rho %g "
+                       "lambda0 (%d points, 4 rotation classes)" % (a, 60.0 * math.sqrt(a / 10000.0), a * m,
+                                                                   a * m, wl.rho_max, wl.n_rho),
            "table_ms": 1e3 * tab_s, "table_info": {k: info[k] for k in
                                                    ("taylor_order", "grid_half", "sigma", "fill_taps")}}
     # fill roofline: FP32 pipe (interpolation + harmonic sum) vs HBM write of the matrix
