@@ -361,6 +361,23 @@ cfft_status cfft_backproject_static(int device, void* cuda_stream, const void* g
                                     int taps, double beta_abs_max, double alpha_margin,
                                     int complex128);
 
+/* MBF spectra (Eq. 11) of the element set by cfft_set_mbf_spectra at n_points
+ * complex wavevectors, as a complex GEMM on the tensor cores:
+ *   out[p][0][a][d] = M_a,d(k_p)    = sum_i conj(Q_ia) F_i(k_p) d_i
+ *   out[p][1][a][d] = Mbar_a,d(k_p) = sum_i Q_ia F_i(-k_p) d_i
+ * (d = x, y: the basis directions; the second side is the analytic
+ * continuation of the conjugated basis spectrum of Eq. 10).
+ *   k    device, complex64 [n_points][2]: (kx, ky), any complex values
+ *   out  device, complex64 [n_points][2][M][2], caller-owned
+ * Arithmetic: FP32 operands split into TF32 head + tail, three tensor-core
+ * products per term, FP32 accumulation (float32 accuracy).  Applies to
+ * rooftop elements with 2 * classes * max(2 M, 8) <= 64, where classes counts
+ * the distinct (direction, half-length, width) rooftop shapes: CFFT_ERR_ARG
+ * otherwise, CFFT_ERR_STATE without an element.  A tensor-core wait that
+ * runs past its bound returns CFFT_ERR_TIMEOUT.  Stream-ordered on the
+ * context stream; synchronizes to read the error flag. */
+cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void* k, void* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
-           "cfft_get_batch_info"]
+           "cfft_get_batch_info", "cfft_mbf_spectra"]
 
 
 class CfftLibraryError(ImportError):
@@ -92,6 +92,7 @@ def _load():
         "cfft_fill_backward": ([P, I, P, P, P, L, I, P, P], I),
         "cfft_tabulate_batch": ([P, I, ctypes.POINTER(BatchItem), I, D, I, I, P, I], I),
         "cfft_get_batch_info": ([P, ctypes.POINTER(BatchInfo)], I),
+        "cfft_mbf_spectra": ([P, I, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -270,6 +271,20 @@ class Context:
         self._check(_lib.cfft_tabulate_batch(self._h, len(items), arr, q_max, float(rho_max), n_rho,
                                              precision, ctypes.c_void_p(out.data_ptr()),
                                              int(graph) | (2 if autotune else 0)))
+        return out
+
+    def mbf_spectra(self, k, out=None):
+        """cfft_mbf_spectra: k cuda complex64 (n, 2) wavevectors -> (n, 2 sides, M, 2 comps)
+        complex64 MBF spectra (side 0: Eq. 11; side 1: the conjugated continuation)."""
+        torch = self._torch
+        assert k.is_cuda and k.dtype == torch.complex64 and k.is_contiguous() and k.shape[-1] == 2
+        n = k.shape[0]
+        shape = (n, 2, self.n_mbf, 2)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device=k.device)
+        assert tuple(out.shape) == shape and out.dtype == torch.complex64 and out.is_contiguous()
+        self._check(_lib.cfft_mbf_spectra(self._h, n, ctypes.c_void_p(k.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr())))
         return out
 
     def batch_info(self):

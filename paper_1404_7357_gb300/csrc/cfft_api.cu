@@ -103,6 +103,9 @@ struct cfft_ctx {
   double b_ms[4] = {0, 0, 0, 0};
   double b_work_bp = 0, b_work_fft = 0;
   int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0;
+  // tensor-core spectra: float copies of the element and its GEMM B operand
+  DevBuf tc_bx, tc_by, tc_bmat, tc_shapes;
+  bool tc_ready = false;
 };
 
 namespace {
@@ -1147,6 +1150,7 @@ cfft_status cfft_set_mbf_spectra_strip(cfft_ctx* ctx, double length, double widt
   ctx->elem_radius = 0.5 * std::hypot(length, width);
   ctx->has_el = true;
   ctx->has_table = false;
+  ctx->tc_ready = false;
   return CFFT_OK;
 }
 
@@ -1192,6 +1196,7 @@ cfft_status cfft_set_mbf_spectra(cfft_ctx* ctx, int n_basis, const double* cente
   ctx->elem_radius = radius;
   ctx->has_el = true;
   ctx->has_table = false;
+  ctx->tc_ready = false;
   return CFFT_OK;
 }
 
@@ -1434,3 +1439,57 @@ cfft_status cfft_synchronize(cfft_ctx* ctx) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// device copies of the element for the tensor-core spectra (built once per element)
+cfft_status ensure_tc_element(cfft_ctx* ctx) {
+  if (ctx->tc_ready) return CFFT_OK;
+  for (const ShapeClass& c : ctx->shapes)
+    if (c.kind != 0) return fail(ctx, CFFT_ERR_ARG, "tensor-core spectra: rooftop elements only");
+  const int n_shape = (int)ctx->shapes.size();
+  if (spectra_tc_columns(n_shape, ctx->n_mbf) == 0)
+    return fail(ctx, CFFT_ERR_ARG, "tensor-core spectra: too many rooftop shapes x MBFs for one GEMM tile");
+  std::vector<int> cls(ctx->n_basis);
+  for (int s = 0; s < n_shape; ++s)
+    for (int i = ctx->shapes[s].begin; i < ctx->shapes[s].end; ++i) cls[i] = s;
+  std::vector<float> bm;
+  spectra_tc_bmatrix(ctx->n_basis, n_shape, cls.data(), ctx->n_mbf,
+                     reinterpret_cast<const double*>(ctx->q.data()), ctx->n_mbf_pad, &bm);
+  std::vector<float> fx(ctx->bx.begin(), ctx->bx.end()), fy(ctx->by.begin(), ctx->by.end());
+  CFFT_CUDA(ctx->tc_bmat.ensure(bm.size() * sizeof(float)), "alloc tensor-core operand");
+  CFFT_CUDA(ctx->tc_bx.ensure(fx.size() * sizeof(float)), "alloc element");
+  CFFT_CUDA(ctx->tc_by.ensure(fy.size() * sizeof(float)), "alloc element");
+  CFFT_CUDA(ctx->tc_shapes.ensure(ctx->shapes.size() * sizeof(ShapeClass)), "alloc element");
+  CFFT_CUDA(cudaMemcpy(ctx->tc_bmat.p, bm.data(), bm.size() * sizeof(float), cudaMemcpyHostToDevice), "upload");
+  CFFT_CUDA(cudaMemcpy(ctx->tc_bx.p, fx.data(), fx.size() * sizeof(float), cudaMemcpyHostToDevice), "upload");
+  CFFT_CUDA(cudaMemcpy(ctx->tc_by.p, fy.data(), fy.size() * sizeof(float), cudaMemcpyHostToDevice), "upload");
+  CFFT_CUDA(cudaMemcpy(ctx->tc_shapes.p, ctx->shapes.data(), ctx->shapes.size() * sizeof(ShapeClass),
+                       cudaMemcpyHostToDevice), "upload");
+  ctx->tc_ready = true;
+  return CFFT_OK;
+}
+
+}  // namespace
+
+extern "C" cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void* k, void* out) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (n_points < 0 || (n_points > 0 && (!k || !out))) return fail(ctx, CFFT_ERR_ARG, "bad spectra arguments");
+  if (!ctx->has_el) return fail(ctx, CFFT_ERR_STATE, "spectra need an element (cfft_set_mbf_spectra)");
+  if (n_points == 0) return CFFT_OK;
+  DeviceGuard g(ctx->device);
+  cfft_status st = ensure_tc_element(ctx);
+  if (st != CFFT_OK) return st;
+  CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");
+  int* flag = ctx->d_flag.as<int>() + 2;
+  CFFT_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream), "flag");
+  cudaError_t e = launch_spectra_tc(n_points, ctx->n_basis, (int)ctx->shapes.size(), ctx->n_mbf,
+                                    ctx->tc_shapes.as<ShapeClass>(), ctx->tc_bx.as<float>(),
+                                    ctx->tc_by.as<float>(), ctx->tc_bmat.as<float>(), k, out, flag, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core spectra kernel");
+  int h = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "spectra");
+  if (h & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "tensor-core spectra: an mbarrier wait ran past its bound");
+  return CFFT_OK;
+}

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace cfft {
 
 template <class T>
@@ -312,6 +314,14 @@ FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, in
 template <class T>
 cudaError_t launch_fill_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& plan, void* scratch,
                                  cudaStream_t s);
+
+// MBF spectra on the tensor cores (FP32 with TF32 head/tail splitting)
+int spectra_tc_columns(int n_shape, int n_mbf);
+void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_mbf,
+                        const double* q_re_im, int q_stride, std::vector<float>* out);
+cudaError_t launch_spectra_tc(int n_points, int n_basis, int n_shape, int n_mbf, const ShapeClass* shapes,
+                              const float* bx, const float* by, const float* bmat, const void* k, void* out,
+                              int* err, cudaStream_t s);
 
 template <class T, class TG>
 cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& a, cudaStream_t s);
