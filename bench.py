@@ -405,31 +405,42 @@ def max_over_ranks(torch, value):
     return value
 
 
+def stage_flops(inf, wl):
+    """Algorithmic FP32 flops of each tabulation stage for one launch."""
+    m = wl.element.n_mbf
+    L = inf["sub_len"]
+    taps = inf["bp_taps"]
+    if inf.get("bp_form", 0) in (1, 2):
+        # interpolation-matrix products (complex MACs) + node stencils added into the matrices
+        bp = 8.0 * inf["work_bp_macs"] + (6.0 * taps + 16.0) * inf["work_bp_stencils"]
+    else:
+        bp = inf["work_bp_nodes"] * (4 * taps + 8)
+    return {
+        "contour": wl.contour.n * 200.0,
+        # complex GEMM of the MBF spectra (both sides) + kernel + harmonic DFT per point
+        "integrand": inf["work_points"] * (2 * 8.0 * inf["n_basis"] * m + m * m * (8.0 * inf["n_harm"] + 30.0)),
+        "fft": inf["work_subffts"] * 5.0 * L * math.log2(L),
+        "backproject": bp,
+    }
+
+
 def roofline(infos, wl, peaks, clk):
     """Dominant kernel of the tabulation step and its fraction of the bounding pipe."""
     inf = infos[-1]
     ms = {k: float(np.mean([i["ms_" + k] for i in infos])) for k in
           ("contour", "integrand", "fft", "backproject")}
     dominant = max(ms, key=ms.get)
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    m = wl.element.n_mbf
-    if dominant == "backproject":
-        flops = inf["work_bp_nodes"] * (4 * inf["bp_taps"] + 8)
-    elif dominant == "fft":
-        L = inf["sub_len"]
-        flops = inf["work_subffts"] * 5.0 * L * math.log2(L)
-    elif dominant == "integrand":
-        # complex GEMM of the MBF spectra (both sides) + kernel + harmonic DFT per point
-        flops = inf["work_points"] * (2 * 8.0 * inf["n_basis"] * m + m * m * (8.0 * inf["n_harm"] + 30.0))
-    else:
-        flops = wl.contour.n * 200.0
-    achieved = flops / (ms[dominant] / 1e3) / 1e12
+    fl = stage_flops(inf, wl)
+    stages = {k: {"ms": ms[k], "tflops": fl[k] / (ms[k] / 1e3) / 1e12,
+                  "frac": fl[k] / (ms[k] / 1e3) / 1e12 / peak_alu} for k in ms}
+    achieved = stages[dominant]["tflops"]
     return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_alu,
             "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)"
                          % peaks.get("sm_max_mhz", 2070.0),
-            "stage_ms": ms, "algorithmic_flops_per_launch": flops}
+            "stages": stages, "algorithmic_flops_per_launch": fl[dominant],
+            "spectra_on_tensor_cores": bool(inf.get("spectra_tc", 0)), "bp_form": inf.get("bp_form", 0)}
 
 
 def run_cfft(args):

@@ -86,7 +86,11 @@ typedef enum {
  *                1024); a value < 0 selects the per-row fill, which also
  *                serves the cases the bucketed fill does not cover (M other
  *                than 1, 2, 4; fill taps other than 8, 12, 16; an output
- *                precision different from the table's)                    */
+ *                precision different from the table's)
+ *   SPECTRA_SIMT a value > 0 evaluates the MBF spectra of the FP32-mixed
+ *                tabulation with SIMT FP32 arithmetic instead of the tensor
+ *                cores (which need a rooftop element, N_ALPHA = 128, M <= 4
+ *                and the GEMM width limit of cfft_mbf_spectra)            */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -96,7 +100,8 @@ typedef enum {
   CFFT_OPT_CHECK_FINITE = 5,
   CFFT_OPT_DERIVATIVES = 6,
   CFFT_OPT_BP_GATHER = 7,
-  CFFT_OPT_FILL_BLOCK = 8
+  CFFT_OPT_FILL_BLOCK = 8,
+  CFFT_OPT_SPECTRA_SIMT = 9
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -295,13 +300,21 @@ cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_
  * milliseconds (contour, integrand, fft, backproject; CUDA events on the
  * context stream), the number of kernels launched, and the work of each
  * stage: integrand points (nodes x angles), sub-FFTs run (each of length
- * sub_len), and back-projection node evaluations (series x rows x angles). */
+ * sub_len), and back-projection node evaluations (series x rows x angles).
+ * spectra_tc: 1 when the MBF spectra ran on the tensor cores; bp_form: 0 the
+ * gather form of the back-projection, 1 the matrix form, 2 the paired-
+ * harmonic matrix form; for the matrix forms work_bp_macs counts the complex
+ * multiply-adds of the interpolation-matrix products (rows x grid columns x
+ * series, every harmonic) and work_bp_stencils the node stencils added into
+ * the matrices (rows x angular nodes x matrices). */
 typedef struct {
   int taylor_order, n_alpha, sigma, fft_len, sub_len, grid_half, bp_taps, fill_taps;
   int series, classes, n_pairs, n_harm;
   double delta_s, ms_contour, ms_integrand, ms_fft, ms_backproject;
   int launches, n_basis;
   double work_points, work_subffts, work_bp_nodes;
+  int spectra_tc, bp_form;
+  double work_bp_macs, work_bp_stencils;
 } cfft_info;
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
 

@@ -78,7 +78,7 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic)
-  double opt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -126,6 +126,8 @@ cfft_status cuda_fail(cfft_ctx* c, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                                    \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);    \
   } while (0)
+
+cfft_status ensure_tc_element(cfft_ctx* ctx);
 
 struct DeviceGuard {
   int prev = -1;
@@ -239,6 +241,15 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
     CFFT_CUDA(ctx->dr_h.ensure(n * sizeof(double2)), "alloc contour");
   }
   CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");
+  CFFT_CUDA(cudaMemsetAsync(ctx->d_flag.as<int>() + 2, 0, sizeof(int), st), "flag");
+  // MBF spectra on the tensor cores (FP32-mixed rooftop elements), unless disabled
+  bool tc_spectra = false;
+  if (!fp64 && !(ctx->opt[CFFT_OPT_SPECTRA_SIMT] > 0) && n_alpha == 128) {
+    bool rooftop = true;
+    for (const ShapeClass& c : ctx->shapes) rooftop = rooftop && c.kind == 0;
+    if (rooftop && spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf) > 0 && ctx->n_mbf <= 4)
+      tc_spectra = ensure_tc_element(ctx) == CFFT_OK;
+  }
 
   // element data in T
   {
@@ -284,7 +295,9 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(cudaGetLastError(), "contour kernel");
   CFFT_CUDA(cudaEventRecord(ctx->ev[1], st), "event");
 
-  double bp_nodes = 0;
+  double bp_nodes = 0, bp_macs = 0, bp_stencils = 0;
+  int bp_form_used = 0;
+  bool in_tc = false;
   for (int ch = 0; ch < channels; ++ch) {
   // ---- a2/a3: spectra, kernel, harmonics
   IntegrandArgs<T> ia{};
@@ -306,7 +319,22 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ia.green_p = gp_ch[ch];
   ia.green_r = gr_ch[ch];
   ia.y = ctx->d_y.as<cpx<T>>();
-  CFFT_CUDA(launch_integrand<T>(ia, ctx->n_mbf_pad, st), "integrand kernel");
+  bool ran_tc = false;
+  if constexpr (sizeof(T) == 4) {
+    if (tc_spectra) {
+      ia.tc_bx = ctx->tc_bx.as<float>();
+      ia.tc_by = ctx->tc_by.as<float>();
+      ia.tc_bmat = ctx->tc_bmat.as<float>();
+      ia.tc_ncol = spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
+      ia.err = ctx->d_flag.as<int>() + 2;
+      if (integrand_tc_applies(ia)) {
+        CFFT_CUDA(launch_integrand_tc(ia, st), "integrand kernel (tensor cores)");
+        ran_tc = true;
+      }
+    }
+  }
+  if (!ran_tc) CFFT_CUDA(launch_integrand<T>(ia, ctx->n_mbf_pad, st), "integrand kernel");
+  in_tc = in_tc || ran_tc;
   ++launches;
   if (ch == 0) CFFT_CUDA(cudaEventRecord(ctx->ev[2], st), "event");
 
@@ -357,11 +385,22 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   int64_t tot = 0;
   int max_nodes = 0, max_seg = 0;
   bp_nodes = 0;
+  bp_macs = 0;
+  bp_stencils = 0;
+  const int ktile = pform ? 32 : 64;   // grid columns per matrix tile of the matrix forms
   for (int c = 0; c < n_chunks; ++c) {
     int r_top = std::min((c + 1) * rchunk, ctx->n_rho) - 1;
     double rho_top = r_top * d_rho;
     cn[c] = alpha_nodes(beta_abs_max, rho_top, ctx->q_max, margin);
-    bp_nodes += (double)cn[c] * (r_top + 1 - c * rchunk) * series;
+    const int rows_c = r_top + 1 - c * rchunk;
+    bp_nodes += (double)cn[c] * rows_c * series;
+    if (pform || wform) {
+      const int kmax_c = std::min(K - 1, (int)std::ceil(rho_top / ds) + bp_taps);
+      const int n_kt = (2 * kmax_c + ktile) / ktile;
+      bp_macs += (double)rows_c * n_kt * ktile * series;
+      const int n_mat = pform ? (ctx->q_max + 1) * ((series_per_q + 15) / 16) : nh;
+      bp_stencils += (double)rows_c * cn[c] * n_mat;
+    }
     coff[c] = tot;
     tot += cn[c];
     max_nodes = std::max(max_nodes, cn[c]);
@@ -411,6 +450,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ba.alpha_margin = margin;
   ba.grid = ctx->d_grid.as<cpx<T>>();
   ba.table = ctx->d_table.as<cpx<T>>() + ch * table_elems;
+  bp_form_used = pform ? 2 : (wform ? 1 : 0);
   if (pform || wform) {
     ba.chunk_nodes = ctx->d_cnodes.as<int>();
     ba.chunk_off = ctx->d_coff.as<int64_t>();
@@ -446,9 +486,11 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
     ++launches;
     CFFT_CUDA(cudaGetLastError(), "nonfinite kernel");
   }
-  int flag = 0;
+  int flag = 0, tc_flag = 0;
   if (check) CFFT_CUDA(cudaMemcpyAsync(&flag, ctx->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+  if (in_tc) CFFT_CUDA(cudaMemcpyAsync(&tc_flag, ctx->d_flag.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
   CFFT_CUDA(cudaStreamSynchronize(st), "tabulate");
+  if (tc_flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "integrand: a tensor-core wait ran past its bound");
 
   cfft_info& in = ctx->info;
   in.taylor_order = taylor;
@@ -478,6 +520,10 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   in.work_points = (double)n * n_alpha;
   in.work_subffts = (double)series * D * (taylor + 1);
   in.work_bp_nodes = bp_nodes;
+  in.spectra_tc = in_tc ? 1 : 0;
+  in.bp_form = bp_form_used;
+  in.work_bp_macs = bp_macs;
+  in.work_bp_stencils = bp_stencils;
   ctx->fill_taps = fill_taps;
   ctx->channels = channels;
   ctx->has_table = true;
@@ -1222,7 +1268,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 8) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 9) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   return CFFT_OK;
 }

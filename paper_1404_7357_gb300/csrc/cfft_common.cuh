@@ -88,14 +88,19 @@ __device__ __forceinline__ cpx<T> expipi(double x) {
   return mk(c, s);
 }
 
-// sin(z), cos(z) for complex z
+__device__ __forceinline__ float sinh_(float x) { return sinhf(x); }
+__device__ __forceinline__ double sinh_(double x) { return sinh(x); }
+__device__ __forceinline__ float cosh_(float x) { return coshf(x); }
+__device__ __forceinline__ double cosh_(double x) { return cosh(x); }
+
+// sin(z), cos(z) for complex z.  sinh of the imaginary part comes from the library
+// function, not from (e^y - e^-y)/2, whose cancellation for small y leaves an
+// absolute error of one ulp of 1 in Im sin z (amplified by 1/|z| in sin(z)/z).
 template <class T>
 __device__ __forceinline__ void csincos(cpx<T> z, cpx<T>* sz, cpx<T>* cz) {
   T s, c;
   sincos_(z.re, &s, &c);
-  T ep = exp_(z.im), em = exp_(-z.im);
-  T ch = (T)0.5 * (ep + em);
-  T sh = (T)0.5 * (ep - em);
+  const T ch = cosh_(z.im), sh = sinh_(z.im);
   *sz = mk(s * ch, c * sh);
   *cz = mk(c * ch, -s * sh);
 }
@@ -183,6 +188,12 @@ struct IntegrandArgs {
   const double2* green_p;
   const double2* green_r;
   cpx<T>* y;                      // out [cls][pair][qi][n]
+  // tensor-core spectra (FP32 rooftop elements): float centres, GEMM B operand, width
+  const float* tc_bx;
+  const float* tc_by;
+  const float* tc_bmat;
+  int tc_ncol;
+  int* err;                       // bit 4: a tensor-core wait ran past its bound
 };
 
 template <class T>
@@ -237,6 +248,10 @@ template <class T>
 cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s);
 template <class T>
 int integrand_tile_nodes(const IntegrandArgs<T>& a, int n_mbf_padded);
+// fused integrand with the MBF spectra on the tensor cores (FP32, N_alpha = 128,
+// a.tc_* set); false when the form does not apply
+bool integrand_tc_applies(const IntegrandArgs<float>& a);
+cudaError_t launch_integrand_tc(const IntegrandArgs<float>& a, cudaStream_t s);
 template <class T>
 cudaError_t launch_integrand_batch(const IntegrandArgs<T>& shape_args, const IntegrandArgs<T>* items,
                                    const int2* map, int n_blocks, int jt, int n_mbf_padded,

@@ -14,10 +14,14 @@
 //   M_a,d(k)    = sum_{s: dir(s) = d} S_s(k) T_{s,a}(k)
 //   Mbar_a,d(k) = sum_{s: dir(s) = d} S_s(k) B_{s,a}(k).
 //
-// Precision: each FP32 operand X is split X = X_hi + X_lo with X_hi its TF32
-// head (low 13 mantissa bits cleared, so X_lo is exact) and each product is
-// formed as A_hi B_hi + A_hi B_lo + A_lo B_hi with float32 accumulation in
-// tensor memory: the float32 accuracy of the SIMT form, on the tensor pipe.
+// Precision: each FP32 operand X is split X ~ X_hi + X_lo, both TF32 values
+// (X_hi the nearest TF32 to X, X_lo the nearest to X - X_hi; |X - X_hi - X_lo|
+// <= 2^-22 |X|), and each product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi
+// with float32 accumulation in tensor memory (per-term error about 3 x 2^-22).
+// The tensor core truncates when it adds into an accumulator, so the head x head
+// products and the two (small) correction products go to separate accumulators,
+// summed in float32 in the epilogue: measured against the oracle this keeps the
+// spectra near float32 accuracy instead of a few 1e-6 worse.
 //
 // Pipeline per 128-point tile: the K dimension runs in chunks of 8 basis
 // functions (K = 32).  All 256 threads generate the A chunk (one point and four
@@ -29,6 +33,7 @@
 #include <vector>
 
 #include "cfft_common.cuh"
+#include "spectra_tc.cuh"
 #include "tc_sm100.cuh"
 
 namespace cfft {
@@ -37,9 +42,6 @@ namespace {
 
 constexpr int kTcThreads = 256;
 constexpr int kTcRows = 128;               // points per tile = MMA M
-constexpr int kTcBasis = 8;                // basis functions per K chunk
-constexpr int kTcK = 4 * kTcBasis;         // K per chunk (floats)
-constexpr uint32_t kTcPolls = 1u << 26;    // bound of every mbarrier wait
 
 struct SpectraTcArgs {
   int n_points, n_basis, n_shape, n_mbf, ncol, ncol_alloc, n_chunks;
@@ -52,19 +54,6 @@ struct SpectraTcArgs {
   int* err;                  // device flag: bit 4 = a tensor-core wait timed out
 };
 
-__device__ __forceinline__ float tf32_head(float x) {
-  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ cpx<float> rooftop_factor(const ShapeClass& c, cpx<float> kx, cpx<float> ky) {
-  const float a = (float)c.p1, w = (float)c.p2;
-  const cpx<float> ku = c.dir == 0 ? kx : ky;
-  const cpx<float> kv = c.dir == 0 ? ky : kx;
-  const cpx<float> s1 = csinc(mk(ku.re * a * 0.5f, ku.im * a * 0.5f));
-  const cpx<float> s2 = csinc(mk(kv.re * w * 0.5f, kv.im * w * 0.5f));
-  return a * (s1 * s1 * s2);
-}
-
 size_t tc_smem_bytes(int ncol, int n_basis) {
   const size_t a = (size_t)2 * 2 * kTcRows * kTcK * sizeof(float);
   const size_t b = (size_t)2 * 2 * ncol * kTcK * sizeof(float);
@@ -72,10 +61,6 @@ size_t tc_smem_bytes(int ncol, int n_basis) {
   const size_t basis = (size_t)2 * ((n_basis + kTcBasis - 1) / kTcBasis * kTcBasis) * sizeof(float);
   return 1024 + a + b + kp + basis + 64;
 }
-
-// columns of one (side, class) group: 2 M reals (re, im per MBF), padded to 8 so that
-// every group starts on an 8-column boundary of the accumulator
-__host__ __device__ constexpr int tc_group_cols(int m) { return 2 * m > 8 ? 2 * m : 8; }
 
 template <int MB>
 __global__ void __launch_bounds__(kTcThreads, 1) spectra_tc_kernel(SpectraTcArgs a) {
@@ -150,10 +135,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) spectra_tc_kernel(SpectraTcArgs
         const bool live = i < a.n_basis;
         const float e = live ? expf(psi) : 0.f, ie = live ? expf(-psi) : 0.f;
         const float v0 = cs * e, v1 = -sn * e, v2 = cs * ie, v3 = sn * ie;   // E, E'
-        const float h0 = tf32_head(v0), h1 = tf32_head(v1), h2 = tf32_head(v2), h3 = tf32_head(v3);
+        float h0, h1, h2, h3, l0, l1, l2, l3;
+        tf32_split(v0, h0, l0);
+        tf32_split(v1, h1, l1);
+        tf32_split(v2, h2, l2);
+        tf32_split(v3, h3, l3);
         const uint32_t off = tc::kmajor_offset(p, 4 * iu, kTcK) / 4;
         *reinterpret_cast<float4*>(ahi + off) = make_float4(h0, h1, h2, h3);
-        *reinterpret_cast<float4*>(alo + off) = make_float4(v0 - h0, v1 - h1, v2 - h2, v3 - h3);
+        *reinterpret_cast<float4*>(alo + off) = make_float4(l0, l1, l2, l3);
       }
       // ---- B chunk (prepared on the host): hi and lo blocks, contiguous
       {
@@ -172,9 +161,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) spectra_tc_kernel(SpectraTcArgs
           const uint32_t ko = s * 256;   // two core matrices (8 tf32) along K per MMA
           const uint64_t dah = tc::sdesc(a_hi + ko, 128, sbo), dal = tc::sdesc(a_lo + ko, 128, sbo);
           const uint64_t dbh = tc::sdesc(b_hi + ko, 128, sbo), dbl = tc::sdesc(b_lo + ko, 128, sbo);
-          tc::mma_tf32(tmem, dah, dbh, idesc, (c > 0 || s > 0) ? 1u : 0u);
-          tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
-          tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+          // head x head products and the two corrections in separate accumulators
+          const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+          tc::mma_tf32(tmem + (uint32_t)a.ncol, dah, dbl, idesc, acc);
+          tc::mma_tf32(tmem + (uint32_t)a.ncol, dal, dbh, idesc, 1u);
+          tc::mma_tf32(tmem, dah, dbh, idesc, acc);
         }
         tc::mma_commit(&mbar[buf]);
       }
@@ -208,8 +199,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) spectra_tc_kernel(SpectraTcArgs
           const uint32_t col0 = (uint32_t)((sd * a.n_shape + sc) * GC);
 #pragma unroll
           for (int cb = 0; cb < GC; cb += 8) {
-            float v[8];
+            float v[8], w8[8];
             tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + col0 + cb, v);
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + col0 + (uint32_t)a.ncol + cb, w8);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) v[jj] += w8[jj];
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
               const int m = (cb + j) / 2;
@@ -251,9 +245,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) spectra_tc_kernel(SpectraTcArgs
 
 }  // namespace
 
-// MBF count as compiled (1, 2, 4, 8; padding columns of Q are zero)
-static int tc_mbf_pad(int n_mbf) { return n_mbf <= 1 ? 1 : n_mbf <= 2 ? 2 : n_mbf <= 4 ? 4 : 8; }
-
 // GEMM width of an element (0 when the tensor-core form does not apply)
 int spectra_tc_columns(int n_shape, int n_mbf) {
   if (n_mbf < 1 || n_mbf > 8) return 0;
@@ -267,18 +258,23 @@ void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_
   const int ncol = spectra_tc_columns(n_shape, n_mbf);
   const int n_chunks = (n_basis + kTcBasis - 1) / kTcBasis;
   out->assign((size_t)n_chunks * 2 * ncol * kTcK, 0.f);
+  // nearest TF32 value, ties away from zero (the rounding of cvt.rna.tf32.f32)
+  auto rna = [](float v) {
+    uint32_t bits;
+    std::memcpy(&bits, &v, 4);
+    bits = (bits + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &bits, 4);
+    return r;
+  };
   auto put = [&](int i, int col, int part, double val) {
     const int c = i / kTcBasis, u = i % kTcBasis;
     const float v = (float)val;
-    uint32_t bits;
-    std::memcpy(&bits, &v, 4);
-    bits &= 0xFFFFE000u;
-    float hi;
-    std::memcpy(&hi, &bits, 4);
+    const float hi = rna(v), lo = rna(v - hi);
     const size_t blk = (size_t)c * 2 * ncol * kTcK;
     const uint32_t off = tc::kmajor_offset(col, 4 * u + part, kTcK) / 4;
     (*out)[blk + off] = hi;
-    (*out)[blk + (size_t)ncol * kTcK + off] = v - hi;
+    (*out)[blk + (size_t)ncol * kTcK + off] = lo;
   };
   for (int i = 0; i < n_basis; ++i) {
     const int s = basis_class[i];
@@ -312,7 +308,7 @@ cudaError_t launch_spectra_tc(int n_points, int n_basis, int n_shape, int n_mbf,
   a.n_shape = n_shape;
   a.n_mbf = n_mbf;
   a.ncol = ncol;
-  a.ncol_alloc = ncol <= 32 ? 32 : 64;
+  a.ncol_alloc = 2 * ncol <= 64 ? 64 : 128;   // two accumulators (head x head, corrections)
   a.n_chunks = (n_basis + kTcBasis - 1) / kTcBasis;
   a.shapes = shapes;
   a.bx = bx;

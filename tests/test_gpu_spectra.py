@@ -92,3 +92,44 @@ def test_spectra_rejects_strip(torch_cuda):
     with pytest.raises(cfft.CfftError) as ei:
         ctx.mbf_spectra(k)
     assert ei.value.status == 1
+
+
+def test_integrand_tensor_cores_vs_simt_and_oracle(torch_cuda):
+    """The FP32-mixed tabulation with the spectra on the tensor cores (default) and with
+    SIMT spectra: contour harmonics Y = H_ab,q beta_c w against the oracle's, and tables."""
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp32", n=1024, n_rho=256, rho_max=4.0, q_max=4)
+    nodes, hq = cc.oracle_harmonics(wl)
+    ref_tab, _, _ = cc.oracle_table(wl)
+    out = {}
+    for name, opts in (("tensor", None), ("simt", {cfft.OPT_SPECTRA_SIMT: 1})):
+        ctx, tab = cc.gpu_table(wl, options=opts)
+        assert ctx.info()["spectra_tc"] == (1 if name == "tensor" else 0)
+        y = ctx.debug_buffer("harmonics").cpu().numpy()[0].astype(np.complex128)
+        yref = (hq[0] * (nodes["beta_c"] * nodes["weight"])).reshape(y.shape)
+        ey = np.abs(y - yref).max() / np.abs(yref).max()
+        et = cc.rel_err_per_pair(tab, ref_tab).max()
+        out[name] = (ey, et)
+        print(name, "harmonics rel err %.3g, table rel err %.3g" % (ey, et))
+        assert ey < 1e-5 and et < 1e-5
+
+
+def test_spectra_small_complex_wavevectors(torch_cuda):
+    """Small complex k (|k a / 2| ~ 0.01 with a small imaginary part): the rooftop factor
+    sinc(z) there is sensitive to how sinh(Im z) is formed."""
+    torch = torch_cuda
+    el = workloads.patch_rooftops()
+    ctx = _ctx(el)
+    rng = np.random.default_rng(5)
+    n = 2000
+    b = rng.uniform(0.2, 1.0, n) + 1j * rng.uniform(1e-4, 0.01, n)
+    al = rng.uniform(0, 2 * np.pi, n)
+    k = torch.tensor(np.stack([b * np.cos(al), b * np.sin(al)], 1).astype(np.complex64), device="cuda:0")
+    got = ctx.mbf_spectra(k).cpu().numpy().astype(np.complex128)
+    kk = k.cpu().numpy().astype(np.complex128)
+    bs = cc.oracle_basis(el)
+    mx, my = osp.mbf_spectra(bs, kk[:, 0], kk[:, 1])
+    ref = np.stack([mx.T, my.T], -1)
+    err = np.abs(got[:, 0] - ref).max() / np.abs(ref).max()
+    print("small complex k rel err %.3g" % err)
+    assert err < 3e-6
