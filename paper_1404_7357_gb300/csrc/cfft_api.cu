@@ -821,7 +821,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       while (l > 1024 && p.P / l < 4) l /= 2;
       auto smem_of = [&](int ll) {
         int d = (int)(p.P / ll);
-        return (size_t)ll * sizeof(cpx<T>) +
+        // the transform buffer is padded by one entry in 16 for lengths >= 1024
+        return (size_t)(ll >= 1024 ? ll + ll / 16 : ll) * sizeof(cpx<T>) +
                fft_task_extra<T>(0, (2 * p.K + 1) / d + 4, (p.n + 127) / 128);
       };
       while (l > 1024 && smem_of(l) > 220 * 1024) l /= 2;

@@ -109,17 +109,181 @@ __device__ __forceinline__ void fft_inplace(cpx<T>* buf, const cpx<T>* thi, cons
   }
 }
 
+// ---- large-radix Stockham passes (lengths 2^10 .. 2^14)
+//
+// One pass of radix R (R = 2, 4, 8, 16) at span p: for each butterfly i < L/R with
+// k = i mod p the inputs x[i + r L/R] (r < R) are multiplied by W_{R p}^{r k} and
+// transformed by an R-point DFT in registers; output s goes to
+// x'[(i - k) R + k + s p].  A radix-16 DFT is two radix-4 stages with the internal
+// twiddles W_16^{r0 s0}.  The shared buffer is padded by one entry every 16
+// (index e -> e + e/16), which makes the strided writes of the first passes
+// conflict-free.  The twiddles of a butterfly come from the two-level tables
+// (W^{k stride} and W^{4 k stride}) and at most two products.
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+
+template <class T>
+__device__ __forceinline__ void dft4(cpx<T>& x0, cpx<T>& x1, cpx<T>& x2, cpx<T>& x3) {
+  const cpx<T> s02 = x0 + x2, d02 = x0 - x2, s13 = x1 + x3, d13 = x1 - x3;
+  const cpx<T> mid = mk(d13.im, -d13.re);  // -i (x1 - x3)
+  x0 = s02 + s13;
+  x1 = d02 + mid;
+  x2 = s02 - s13;
+  x3 = d02 - mid;
+}
+
+template <class T, int R>
+__device__ __forceinline__ void dft_r(cpx<T>* v) {
+  if constexpr (R == 2) {
+    const cpx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  } else if constexpr (R == 4) {
+    dft4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    // r = 2 r1 + r0: radix-4 over r1 for each r0, twiddle W_8^{r0 s0}, radix-2 over r0
+    cpx<T> a[2][4];
+#pragma unroll
+    for (int r0 = 0; r0 < 2; ++r0) {
+#pragma unroll
+      for (int r1 = 0; r1 < 4; ++r1) a[r0][r1] = v[2 * r1 + r0];
+      dft4(a[r0][0], a[r0][1], a[r0][2], a[r0][3]);
+    }
+    const T h = (T)0.70710678118654752440;
+    a[1][1] = mk(h * (a[1][1].re + a[1][1].im), h * (a[1][1].im - a[1][1].re));     // * W_8
+    a[1][2] = mk(a[1][2].im, -a[1][2].re);                                            // * W_8^2
+    a[1][3] = mk(h * (a[1][3].im - a[1][3].re), -h * (a[1][3].re + a[1][3].im));    // * W_8^3
+#pragma unroll
+    for (int s0 = 0; s0 < 4; ++s0) {
+      v[s0] = a[0][s0] + a[1][s0];
+      v[s0 + 4] = a[0][s0] - a[1][s0];
+    }
+  } else {
+    static_assert(R == 16, "radix");
+    // r = 4 r1 + r0: radix-4 over r1, twiddle W_16^{r0 s0}, radix-4 over r0
+    cpx<T> a[4][4];
+#pragma unroll
+    for (int r0 = 0; r0 < 4; ++r0) {
+#pragma unroll
+      for (int r1 = 0; r1 < 4; ++r1) a[r0][r1] = v[4 * r1 + r0];
+      dft4(a[r0][0], a[r0][1], a[r0][2], a[r0][3]);
+    }
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+    const T h = (T)0.70710678118654752440;
+    const cpx<T> w1 = mk(c1, -s1), w2 = mk(h, -h), w3 = mk(s1, -c1);
+    const cpx<T> w6 = mk(-h, -h), w9 = mk(-c1, s1);
+    a[1][1] = a[1][1] * w1;
+    a[1][2] = a[1][2] * w2;
+    a[1][3] = a[1][3] * w3;
+    a[2][1] = a[2][1] * w2;
+    a[2][2] = mk(a[2][2].im, -a[2][2].re);   // * W_16^4 = -i
+    a[2][3] = a[2][3] * w6;
+    a[3][1] = a[3][1] * w3;
+    a[3][2] = a[3][2] * w6;
+    a[3][3] = a[3][3] * w9;
+#pragma unroll
+    for (int s0 = 0; s0 < 4; ++s0) {
+      dft4(a[0][s0], a[1][s0], a[2][s0], a[3][s0]);
+      v[s0] = a[0][s0];
+      v[s0 + 4] = a[1][s0];
+      v[s0 + 8] = a[2][s0];
+      v[s0 + 12] = a[3][s0];
+    }
+  }
+}
+
+template <class T, int R, int LOG2L, int NT>
+__device__ __forceinline__ void stockham_pass(cpx<T>* buf, int p, const cpx<T>* thi, const cpx<T>* tlo) {
+  constexpr int L = 1 << LOG2L;
+  constexpr int NB = L / R;
+  constexpr int BPT = NB / NT;
+  static_assert(BPT >= 1 && NB % NT == 0, "butterflies per thread");
+  const int tid = threadIdx.x;
+  const int stride = L / (R * p);
+  cpx<T> v[BPT][R];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int i = tid + NT * b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b][r] = buf[pidx(i + r * NB)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int i = tid + NT * b;
+    const int k = i & (p - 1);
+    if (k != 0) {
+      const int e = k * stride;
+      const cpx<T> t1 = tw2(thi, tlo, e);
+      if constexpr (R == 2) {
+        v[b][1] = v[b][1] * t1;
+      } else {
+        const cpx<T> t2 = t1 * t1, t3 = t2 * t1;
+        v[b][1] = v[b][1] * t1;
+        v[b][2] = v[b][2] * t2;
+        v[b][3] = v[b][3] * t3;
+        if constexpr (R >= 8) {
+          const cpx<T> t4 = tw2(thi, tlo, 4 * e);
+          cpx<T> q = t4;
+#pragma unroll
+          for (int g = 1; g < R / 4; ++g) {
+            v[b][4 * g] = v[b][4 * g] * q;
+            v[b][4 * g + 1] = v[b][4 * g + 1] * (q * t1);
+            v[b][4 * g + 2] = v[b][4 * g + 2] * (q * t2);
+            v[b][4 * g + 3] = v[b][4 * g + 3] * (q * t3);
+            if (g + 1 < R / 4) q = tw2(thi, tlo, 4 * (g + 1) * e);
+          }
+        }
+      }
+    }
+    dft_r<T, R>(v[b]);
+    const int j = (i - k) * R + k;
+#pragma unroll
+    for (int s = 0; s < R; ++s) buf[pidx(j + s * p)] = v[b][s];
+  }
+  __syncthreads();
+}
+
+// in-place (Stockham, autosorting) length-2^LOG2L FFT over the padded buffer:
+// one pass of radix 2^(LOG2L mod 4) when that is not 1, then radix-16 passes
+template <class T, int LOG2L, int NT>
+__device__ __forceinline__ void fft16_inplace(cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo) {
+  constexpr int REM = LOG2L & 3;
+  int p = 1;
+  if constexpr (REM == 1) { stockham_pass<T, 2, LOG2L, NT>(buf, p, thi, tlo); p = 2; }
+  if constexpr (REM == 2) { stockham_pass<T, 4, LOG2L, NT>(buf, p, thi, tlo); p = 4; }
+  if constexpr (REM == 3) { stockham_pass<T, 8, LOG2L, NT>(buf, p, thi, tlo); p = 8; }
+#pragma unroll 1
+  for (int q = 0; q < LOG2L / 4; ++q) {
+    stockham_pass<T, 16, LOG2L, NT>(buf, p, thi, tlo);
+    p *= 16;
+  }
+}
+
 __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   int q = a / b;
   return (a % b != 0 && a < 0) ? q - 1 : q;
 }
 
 
-// one (series, k2) task: all Taylor terms of one residue class of the outputs
+// threads of a transform task and shared-buffer padding, by length
+template <int LOG2L>
+struct FftShape {
+  static constexpr int L = 1 << LOG2L;
+  static constexpr bool R16 = LOG2L >= 10;                       // large-radix passes
+  static constexpr int NT = R16 ? (L / 16 < 512 ? L / 16 : 512) : (L / 4 < 512 ? L / 4 : 512);
+  static constexpr int BUF = R16 ? L + L / 16 : L;               // padded buffer entries
+};
+
+// one (series, k2) task: all Taylor terms of one residue class of the outputs.
+// use_zt: the pre-twiddled active inputs x_j (beta_I/H)^n are kept in shared memory
+// and advanced by one multiplication per Taylor term instead of being re-read
 template <class T, int LOG2L, int NT>
 __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series, int k2,
-                                                unsigned char* smem_raw) {
+                                                unsigned char* smem_raw, int use_zt) {
   constexpr int L = 1 << LOG2L;
+  constexpr bool R16 = FftShape<LOG2L>::R16;
+  constexpr int BUF = FftShape<LOG2L>::BUF;
+  auto bidx = [](int e) { return R16 ? pidx(e) : e; };
   const int D = a.n_sub;
   const int K = a.grid_half;
   const int t_lo = -floor_div(K + k2, D);     // ceil((-K - k2) / D)
@@ -131,13 +295,14 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   const int64_t P = a.fft_len;
   // shared layout: FFT buffer | pre-twiddle lo, hi | FFT twiddle hi, lo | acc | fac | sk
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* plo = buf + L;            // exp(-2 pi i r k2 / P), r < 128
+  cpx<T>* plo = buf + BUF;          // exp(-2 pi i r k2 / P), r < 128
   cpx<T>* phi = plo + 128;          // exp(-2 pi i 128 m k2 / P), m < n_hi
   cpx<T>* thi = phi + n_hi;         // exp(-2 pi i 128 m / L), m < L / 128
   cpx<T>* tlo = thi + 128;          // exp(-2 pi i r / L), r < 128
   cpx<T>* acc = tlo + 128;
   T* fac = reinterpret_cast<T*>(acc + n_out);
   T* skv = fac + n_out;
+  cpx<T>* zt = reinterpret_cast<cpx<T>*>((reinterpret_cast<uintptr_t>(skv + n_out) + 15) & ~(uintptr_t)15);
   const cpx<T>* y = a.y + (size_t)series * n;
 
   // ---- per-task tables (float64 argument reduction, once)
@@ -166,29 +331,47 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   for (int nt = 0; nt <= a.taylor; ++nt) {
     const int lim = nt == 0 ? n : a.n_active;
     // ---- fold + pre-twiddle W_P^{j k2} + Taylor weight (beta_I/H)^n
-    for (int jp = tid; jp < L; jp += NT) {
-      cpx<T> v = mk((T)0, (T)0);
-      for (int j = jp; j < lim; j += L) {
-        cpx<T> x = y[j];
-        if (nt > 0) {
+    if (use_zt && nt > 0) {
+      // the active inputs, already pre-twiddled and weighted by (beta_I/H)^nt
+      for (int jp = tid; jp < L; jp += NT) {
+        cpx<T> v = mk((T)0, (T)0);
+        for (int j = jp; j < lim; j += L) {
+          const cpx<T> x = zt[j];
+          v = v + x;
           T b;
           if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
           else b = a.bi_rel[j];
-          x = powi_scale<T>(b, nt).re * x;
+          zt[j] = b * x;   // next Taylor term
         }
-        if (k2 != 0) x = x * (phi[j >> 7] * plo[j & 127]);
-        v = v + x;
+        buf[bidx(jp)] = v;
       }
-      buf[jp] = v;
+    } else {
+      for (int jp = tid; jp < L; jp += NT) {
+        cpx<T> v = mk((T)0, (T)0);
+        for (int j = jp; j < lim; j += L) {
+          cpx<T> x = y[j];
+          if (k2 != 0) x = x * (phi[j >> 7] * plo[j & 127]);
+          T b = (T)1;
+          if (nt > 0 || use_zt) {
+            if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
+            else b = a.bi_rel[j];
+          }
+          if (nt > 0) x = powi_scale<T>(b, nt).re * x;
+          else if (use_zt && j < a.n_active) zt[j] = b * x;   // first Taylor term for nt = 1
+          v = v + x;
+        }
+        buf[bidx(jp)] = v;
+      }
     }
     __syncthreads();
-    fft_inplace<T, LOG2L, NT>(buf, thi, tlo);
+    if constexpr (R16) fft16_inplace<T, LOG2L, NT>(buf, thi, tlo);
+    else fft_inplace<T, LOG2L, NT>(buf, thi, tlo);
     // ---- accumulate the needed outputs: k = k2 + D t, |k| <= K
     const T inv = (T)1 / (T)(nt + 1);
     for (int o = tid; o < n_out; o += NT) {
       int t = t_lo + o;
       int idx = t & (L - 1);  // t mod L (two's complement)
-      cpx<T> v = buf[idx];
+      cpx<T> v = buf[bidx(idx)];
       T f = fac[o];
       acc[o] = acc[o] + f * v;
       fac[o] = f * skv[o] * inv;
@@ -209,16 +392,16 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
 }
 
 template <class T, int LOG2L, int NT>
-__global__ void __launch_bounds__(NT) fft_taylor_kernel(FftArgs<T> a) {
+__global__ void __launch_bounds__(NT) fft_taylor_kernel(FftArgs<T> a, int use_zt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fft_taylor_task<T, LOG2L, NT>(a, blockIdx.x, blockIdx.y, smem_raw);
+  fft_taylor_task<T, LOG2L, NT>(a, blockIdx.x, blockIdx.y, smem_raw, use_zt);
 }
 
 // persistent form: CTAs pull (item, series, k2) tasks from a counter until none is left
 template <class T, int LOG2L, int NT>
 __global__ void __launch_bounds__(NT) fft_taylor_batch_kernel(const FftArgs<T>* items,
                                                               const int4* tasks, int n_tasks,
-                                                              int* counter) {
+                                                              int* counter, int use_zt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
   for (;;) {
@@ -229,33 +412,42 @@ __global__ void __launch_bounds__(NT) fft_taylor_batch_kernel(const FftArgs<T>* 
     if (t >= n_tasks) break;
     const int4 tk = tasks[t];
     const FftArgs<T> a = items[tk.x];
-    fft_taylor_task<T, LOG2L, NT>(a, tk.y, tk.z, smem_raw);
+    fft_taylor_task<T, LOG2L, NT>(a, tk.y, tk.z, smem_raw, use_zt);
     __syncthreads();
   }
 }
 
+// shared bytes of a transform task, with or without the active-input store
+template <class T, int LOG2L>
+size_t fft_task_smem(int n_active, int n_out_max, int hi_max, bool zt) {
+  return (size_t)FftShape<LOG2L>::BUF * sizeof(cpx<T>) + fft_task_extra<T>(n_active, n_out_max, hi_max) +
+         (zt ? (size_t)n_active * sizeof(cpx<T>) + 16 : 0);
+}
+
+constexpr size_t kFftSmemCap = 220 * 1024;
+
 template <class T, int LOG2L>
 cudaError_t launch_l(const FftArgs<T>& a, cudaStream_t s) {
-  constexpr int L = 1 << LOG2L;
-  constexpr int NT = (L / 4 < 512) ? L / 4 : 512;
+  constexpr int NT = FftShape<LOG2L>::NT;
   const int D = a.n_sub;
   const int n_out_max = (2 * a.grid_half + 1) / D + 2;
-  size_t smem = (size_t)L * sizeof(cpx<T>) +
-                fft_task_extra<T>(a.n_active, n_out_max, (a.n + 127) / 128);
+  const int hi = (a.n + 127) / 128;
+  const bool zt = a.taylor > 0 && fft_task_smem<T, LOG2L>(a.n_active, n_out_max, hi, true) <= kFftSmemCap;
+  const size_t smem = fft_task_smem<T, LOG2L>(a.n_active, n_out_max, hi, zt);
   cudaError_t e = cudaFuncSetAttribute(fft_taylor_kernel<T, LOG2L, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.series, D);
-  fft_taylor_kernel<T, LOG2L, NT><<<grid, NT, smem, s>>>(a);
+  fft_taylor_kernel<T, LOG2L, NT><<<grid, NT, smem, s>>>(a, zt ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <class T, int LOG2L>
 cudaError_t launch_l_batch(const FftArgs<T>* items, const int4* tasks, int n_tasks, int* counter,
                            int max_n_out, int max_active, int max_hi, int n_ctas, cudaStream_t s) {
-  constexpr int L = 1 << LOG2L;
-  constexpr int NT = (L / 4 < 512) ? L / 4 : 512;
-  size_t smem = (size_t)L * sizeof(cpx<T>) + fft_task_extra<T>(max_active, max_n_out + 2, max_hi);
+  constexpr int NT = FftShape<LOG2L>::NT;
+  const bool zt = fft_task_smem<T, LOG2L>(max_active, max_n_out + 2, max_hi, true) <= kFftSmemCap;
+  const size_t smem = fft_task_smem<T, LOG2L>(max_active, max_n_out + 2, max_hi, zt);
   cudaError_t e = cudaFuncSetAttribute(fft_taylor_batch_kernel<T, LOG2L, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -264,7 +456,7 @@ cudaError_t launch_l_batch(const FftArgs<T>* items, const int4* tasks, int n_tas
                                                     NT, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   fft_taylor_batch_kernel<T, LOG2L, NT><<<n_ctas * per_sm, NT, smem, s>>>(items, tasks, n_tasks,
-                                                                        counter);
+                                                                        counter, zt ? 1 : 0);
   return cudaGetLastError();
 }
 
