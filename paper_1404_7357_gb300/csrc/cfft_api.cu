@@ -106,6 +106,7 @@ struct cfft_ctx {
   // tensor-core spectra: float copies of the element and its GEMM B operand
   DevBuf tc_bx, tc_by, tc_bmat, tc_shapes;
   bool tc_ready = false;
+  float tc_rmax = 0;
 };
 
 namespace {
@@ -244,7 +245,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(cudaMemsetAsync(ctx->d_flag.as<int>() + 2, 0, sizeof(int), st), "flag");
   // MBF spectra on the tensor cores (FP32-mixed rooftop elements), unless disabled
   bool tc_spectra = false;
-  if (!fp64 && !(ctx->opt[CFFT_OPT_SPECTRA_SIMT] > 0) && n_alpha == 128) {
+  if (!fp64 && !(ctx->opt[CFFT_OPT_SPECTRA_SIMT] > 0) && (n_alpha == 128 || n_alpha == 256)) {
     bool rooftop = true;
     for (const ShapeClass& c : ctx->shapes) rooftop = rooftop && c.kind == 0;
     if (rooftop && spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf) > 0 && ctx->n_mbf <= 4)
@@ -326,6 +327,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
       ia.tc_by = ctx->tc_by.as<float>();
       ia.tc_bmat = ctx->tc_bmat.as<float>();
       ia.tc_ncol = spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
+      ia.tc_rmax = ctx->tc_rmax;
       ia.err = ctx->d_flag.as<int>() + 2;
       if (integrand_tc_applies(ia)) {
         CFFT_CUDA(launch_integrand_tc(ia, st), "integrand kernel (tensor cores)");
@@ -758,8 +760,28 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   shape_args.n_alpha = n_alpha;
   shape_args.n_mbf = M;
   shape_args.n_basis = ctx->n_basis;
-  const int jt = integrand_tile_nodes<T>(shape_args, ctx->n_mbf_pad);
+  int jt = integrand_tile_nodes<T>(shape_args, ctx->n_mbf_pad);
   if (jt < 1) return fail(ctx, CFFT_ERR_ARG, "element too large for the integrand tile");
+  // MBF spectra on the tensor cores (FP32-mixed rooftop elements), unless disabled
+  bool tc_b = false;
+  if constexpr (sizeof(T) == 4) {
+    if (!(ctx->opt[CFFT_OPT_SPECTRA_SIMT] > 0) && (n_alpha == 128 || n_alpha == 256) && ctx->n_mbf <= 4) {
+      bool rooftop = true;
+      for (const ShapeClass& c : ctx->shapes) rooftop = rooftop && c.kind == 0;
+      if (rooftop && spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf) > 0 &&
+          ensure_tc_element(ctx) == CFFT_OK) {
+        shape_args.tc_bx = ctx->tc_bx.as<float>();
+        shape_args.tc_by = ctx->tc_by.as<float>();
+        shape_args.tc_bmat = ctx->tc_bmat.as<float>();
+        shape_args.tc_ncol = spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
+        shape_args.tc_rmax = ctx->tc_rmax;
+        tc_b = integrand_tc_applies(shape_args);
+        if (tc_b) jt = integrand_tc_nodes(n_alpha);
+      }
+    }
+  }
+  CFFT_CUDA(ctx->b_flag.ensure(2 * sizeof(int)), "alloc flag");
+  CFFT_CUDA(cudaMemsetAsync(ctx->b_flag.p, 0, 2 * sizeof(int), st), "flag");
 
   // back-projection chunk shapes depend on rchunk; FFT tasks on the sub-FFT length
   // mode 0: plan + plain launches; 1: plan + capture into a new graph; 2: plan only
@@ -860,6 +882,14 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         ia.green_p = c_gp + node_off;
         ia.green_r = c_gr + node_off;
         ia.y = ctx->b_y.as<cpx<T>>() + (size_t)series * node_off;
+        if (tc_b) {
+          ia.tc_bx = shape_args.tc_bx;
+          ia.tc_by = shape_args.tc_by;
+          ia.tc_bmat = shape_args.tc_bmat;
+          ia.tc_ncol = shape_args.tc_ncol;
+          ia.tc_rmax = shape_args.tc_rmax;
+          ia.err = ctx->b_flag.as<int>() + 1;
+        }
         const int Li = li[i];
         int log2Li = 0;
         while ((1 << log2Li) < Li) ++log2Li;
@@ -993,9 +1023,19 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         launch_contour_batch(ctx->b_cargs.as<ContourArgs>(), ctx->b_cdata.as<ContourData>(),
                              ctx->b_cmap.as<int2>() + r.c0, (int)(r.c1 - r.c0), st);
         ++launches;
-        e = launch_integrand_batch<T>(shape_args, ctx->b_iargs.as<IntegrandArgs<T>>(),
-                                      ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), jt,
-                                      ctx->n_mbf_pad, st);
+        if constexpr (sizeof(T) == 4) {
+          if (tc_b)
+            e = launch_integrand_tc_batch(shape_args, ctx->b_iargs.as<IntegrandArgs<float>>(),
+                                          ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), st);
+          else
+            e = launch_integrand_batch<T>(shape_args, ctx->b_iargs.as<IntegrandArgs<T>>(),
+                                          ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), jt,
+                                          ctx->n_mbf_pad, st);
+        } else {
+          e = launch_integrand_batch<T>(shape_args, ctx->b_iargs.as<IntegrandArgs<T>>(),
+                                        ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), jt,
+                                        ctx->n_mbf_pad, st);
+        }
         if (e != cudaSuccess) return e;
         ++launches;
         if (w == 0) rec(ctx->bev[1]);
@@ -1107,9 +1147,11 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   CFFT_CUDA(cudaMemsetAsync(ctx->b_flag.p, 0, sizeof(int), st), "flag");
   launch_nonfinite<T>(reinterpret_cast<const cpx<T>*>(tables), (int64_t)(n_items * table_elems),
                       ctx->b_flag.as<int>(), st);
-  int flag = 0;
+  int flag = 0, tc_flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, ctx->b_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+  CFFT_CUDA(cudaMemcpyAsync(&tc_flag, ctx->b_flag.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
   CFFT_CUDA(cudaStreamSynchronize(st), "batch");
+  if (tc_flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "batch integrand: a tensor-core wait ran past its bound");
   float ms = 0;
   if (cudaEventElapsedTime(&ms, ctx->bev[0], ctx->bev[1]) == cudaSuccess) ctx->b_ms[0] = ms;
   if (cudaEventElapsedTime(&ms, ctx->bev[1], ctx->bev[2]) == cudaSuccess) ctx->b_ms[1] = ms;
@@ -1504,6 +1546,9 @@ cfft_status ensure_tc_element(cfft_ctx* ctx) {
   spectra_tc_bmatrix(ctx->n_basis, n_shape, cls.data(), ctx->n_mbf,
                      reinterpret_cast<const double*>(ctx->q.data()), ctx->n_mbf_pad, &bm);
   std::vector<float> fx(ctx->bx.begin(), ctx->bx.end()), fy(ctx->by.begin(), ctx->by.end());
+  double rmax = 0;
+  for (size_t i = 0; i < fx.size(); ++i) rmax = std::max(rmax, std::hypot(ctx->bx[i], ctx->by[i]));
+  ctx->tc_rmax = (float)(rmax * (1.0 + 1e-6));
   CFFT_CUDA(ctx->tc_bmat.ensure(bm.size() * sizeof(float)), "alloc tensor-core operand");
   CFFT_CUDA(ctx->tc_bx.ensure(fx.size() * sizeof(float)), "alloc element");
   CFFT_CUDA(ctx->tc_by.ensure(fy.size() * sizeof(float)), "alloc element");

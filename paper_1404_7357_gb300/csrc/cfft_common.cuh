@@ -193,6 +193,7 @@ struct IntegrandArgs {
   const float* tc_by;
   const float* tc_bmat;
   int tc_ncol;
+  float tc_rmax;                  // max |r_i| of the basis centres
   int* err;                       // bit 4: a tensor-core wait ran past its bound
 };
 
@@ -248,10 +249,14 @@ template <class T>
 cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s);
 template <class T>
 int integrand_tile_nodes(const IntegrandArgs<T>& a, int n_mbf_padded);
-// fused integrand with the MBF spectra on the tensor cores (FP32, N_alpha = 128,
+// fused integrand with the MBF spectra on the tensor cores (FP32, N_alpha = 128 or 256,
 // a.tc_* set); false when the form does not apply
 bool integrand_tc_applies(const IntegrandArgs<float>& a);
 cudaError_t launch_integrand_tc(const IntegrandArgs<float>& a, cudaStream_t s);
+// contour nodes per CTA of the tensor-core integrand (n_alpha 128 or 256), and its batched launch
+int integrand_tc_nodes(int n_alpha);
+cudaError_t launch_integrand_tc_batch(const IntegrandArgs<float>& shape_args, const IntegrandArgs<float>* items,
+                                      const int2* map, int n_blocks, cudaStream_t s);
 template <class T>
 cudaError_t launch_integrand_batch(const IntegrandArgs<T>& shape_args, const IntegrandArgs<T>* items,
                                    const int2* map, int n_blocks, int jt, int n_mbf_padded,

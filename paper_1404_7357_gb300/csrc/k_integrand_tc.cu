@@ -1,11 +1,11 @@
 // Fused contour integrand with the MBF spectra on the tensor cores (FP32-mixed,
-// rooftop elements, N_alpha = 128): Eq. 11 as a GEMM (see k_spectra_tc.cu for
+// rooftop elements, N_alpha = 128 or 256): Eq. 11 as a GEMM (see k_spectra_tc.cu for
 // the operand layout and the TF32 head/tail products), then the kernel of
 // Eq. 10 and its azimuthal harmonics times the contour measure of Eq. 9,
 // exactly as the SIMT form in k_integrand.cu computes them.
 //
-// A CTA owns JT = 4 consecutive contour nodes x 128 angles (4 tiles of 128
-// points, one tensor-memory accumulator each).  The basis dimension is the
+// A CTA owns 512 points: JT = 512 / N_alpha consecutive contour nodes x N_alpha
+// angles, as 4 tiles of 128 points (one tensor-memory accumulator pair each).  The basis dimension is the
 // outer loop and the nodes the inner one, so a thread keeps, for each of its
 // four basis functions, exp(-i beta_R,j p_i) (p_i = x_i cos alpha + y_i sin
 // alpha, the projection of the centre on the wave direction) and advances it
@@ -15,11 +15,13 @@
 // stage is written while the tensor core consumes the previous stage.
 //
 // After the GEMM, each point's spectra (both sides, both directions, every
-// MBF) go to shared memory component-major; H_ab(j, l) for a chunk of 8 MBF
-// pairs follows, folded 4-fold in angle as it is formed, and the angular DFT
-// runs over the folded rows (32 terms per harmonic; rows padded to 129
-// entries, conflict-free, twiddles broadcast).
+// MBF) go to shared memory component-major; H_ab(j, l) for a chunk of 32 / JT
+// MBF pairs follows, folded F = N_alpha / 32 -fold in angle as it is formed
+// (an F-point DFT per angle), and the angular DFT runs over the folded rows
+// (32 terms per harmonic; rows padded by one entry, conflict-free, twiddles
+// broadcast).
 #include "cfft_common.cuh"
+#include "dft_small.cuh"
 #include "spectra_tc.cuh"
 #include "tc_sm100.cuh"
 
@@ -28,34 +30,42 @@ namespace cfft {
 namespace {
 
 constexpr int kIThreads = 256;
-constexpr int kJT = 4;          // contour nodes per CTA
-constexpr int kNA = 128;        // angles (= MMA M)
-constexpr int kPC = 8;          // MBF pairs per H chunk
-constexpr int kRow = kNA + 1;   // padded H row
+constexpr int kTiles = 4;       // 128-point tiles (tensor-core M = 128) per CTA
+
+template <int NA>
+struct ItcShape {
+  static constexpr int TPN = NA / 128;     // tiles per contour node
+  static constexpr int JT = kTiles / TPN;  // contour nodes per CTA
+  static constexpr int F = NA / 32;        // angular fold of the DFT
+  static constexpr int PC = 32 / JT;       // MBF pairs per H chunk (32 rows = pairs x nodes)
+  static constexpr int ROW = NA + 1;       // padded H row
+};
 
 struct ItcLayout {
   size_t a, b, spec, hbuf, tw, bx, node, mbar, total;
 };
 
+template <int NA>
 __host__ __device__ inline ItcLayout itc_layout(int ncol, int mb, int nb_pad) {
+  using S = ItcShape<NA>;
   ItcLayout L{};
   // phase 1 (A, B operand buffers) and phases 2-3 (spectra, H rows) share one region
-  const size_t p1 = (size_t)2 * 2 * kNA * kTcK * 4 + (size_t)2 * 2 * ncol * kTcK * 4;
-  const size_t spec = (size_t)kJT * 4 * mb * kNA * 8;
-  const size_t p23 = spec + (size_t)kPC * kJT * kRow * 8;
+  const size_t p1 = (size_t)2 * 2 * 128 * kTcK * 4 + (size_t)2 * 2 * ncol * kTcK * 4;
+  const size_t spec = (size_t)S::JT * 4 * mb * NA * 8;
+  const size_t p23 = spec + (size_t)S::PC * S::JT * S::ROW * 8;
   L.a = 0;
-  L.b = (size_t)2 * 2 * kNA * kTcK * 4;
+  L.b = (size_t)2 * 2 * 128 * kTcK * 4;
   L.spec = 0;
   L.hbuf = spec;
   size_t o = (p1 > p23 ? p1 : p23);
   o = (o + 15) & ~(size_t)15;
   L.tw = o;
-  o += (size_t)kNA * 8;
+  o += (size_t)NA * 8;
   L.bx = o;
   o += (size_t)2 * nb_pad * 4;
   o = (o + 15) & ~(size_t)15;
   L.node = o;                      // per node: beta_R, beta_I, bw (2), P (2), R beta^2 (2) as floats
-  o += (size_t)kJT * 8 * 4;
+  o += (size_t)S::JT * 8 * 4;
   o = (o + 7) & ~(size_t)7;
   L.mbar = o;
   o += 2 * 8 + 16;
@@ -63,20 +73,26 @@ __host__ __device__ inline ItcLayout itc_layout(int ncol, int mb, int nb_pad) {
   return L;
 }
 
-template <int MB>
-__global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArgs<float> a) {
-  extern __shared__ unsigned char smem_raw[];
+size_t itc_smem(int na, int ncol, int mb, int nb_pad) {
+  return na == 256 ? itc_layout<256>(ncol, mb, nb_pad).total : itc_layout<128>(ncol, mb, nb_pad).total;
+}
+
+template <int MB, int NA>
+__device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a, const int j0,
+                                                  unsigned char* smem_raw) {
+  using S = ItcShape<NA>;
+  constexpr int TPN = S::TPN, JT = S::JT, F = S::F, PC = S::PC, ROW = S::ROW;
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int ncol = a.tc_ncol;
   const int n_chunks = (a.n_basis + kTcBasis - 1) / kTcBasis;
   const int nb_pad = n_chunks * kTcBasis;
-  const ItcLayout L = itc_layout(ncol, MB, nb_pad);
+  const ItcLayout L = itc_layout<NA>(ncol, MB, nb_pad);
   float* A = reinterpret_cast<float*>(base + L.a);
   float* B = reinterpret_cast<float*>(base + L.b);
-  cpx<float>* spec = reinterpret_cast<cpx<float>*>(base + L.spec);   // [t][comp][l]
-  cpx<float>* hbuf = reinterpret_cast<cpx<float>*>(base + L.hbuf);   // [pl][t][kRow]
-  cpx<float>* tw = reinterpret_cast<cpx<float>*>(base + L.tw);       // exp(-2 pi i l / N)
+  cpx<float>* spec = reinterpret_cast<cpx<float>*>(base + L.spec);   // [t][comp][angle]
+  cpx<float>* hbuf = reinterpret_cast<cpx<float>*>(base + L.hbuf);   // [pl][t][ROW]
+  cpx<float>* tw = reinterpret_cast<cpx<float>*>(base + L.tw);       // exp(-2 pi i l / N_alpha)
   float* sbx = reinterpret_cast<float*>(base + L.bx);
   float* sby = sbx + nb_pad;
   float* nd = reinterpret_cast<float*>(base + L.node);
@@ -85,17 +101,16 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int j0 = blockIdx.x * kJT;
-  for (int t = tid; t < kNA; t += kIThreads) {
+  for (int t = tid; t < NA; t += kIThreads) {
     float s, c;
-    sincospif(-2.0f * (float)t / (float)kNA, &s, &c);
+    sincospif(-2.0f * (float)t / (float)NA, &s, &c);
     tw[t] = mk(c, s);
   }
   for (int i = tid; i < nb_pad; i += kIThreads) {
     sbx[i] = i < a.n_basis ? a.tc_bx[i] : 0.f;
     sby[i] = i < a.n_basis ? a.tc_by[i] : 0.f;
   }
-  if (tid < kJT) {
+  if (tid < JT) {
     const int j = j0 + tid;
     float* o = nd + 8 * tid;
     if (j < a.n) {
@@ -114,10 +129,10 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
     tc::mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // per node: head x head products in one accumulator, the two correction products in a
+  // per tile: head x head products in one accumulator, the two correction products in a
   // second one (the tensor core truncates on every accumulation; splitting the sums
   // keeps the large accumulator's step count and the small one's magnitude low)
-  const uint32_t ncol_alloc = 2 * kJT * ncol <= 256 ? 256u : 512u;
+  const uint32_t ncol_alloc = 2 * kTiles * ncol <= 256 ? 256u : 512u;
   if (warp == 0) {
     tc::tmem_alloc(taddr_s, ncol_alloc);
     tc::tmem_relinquish();
@@ -130,12 +145,11 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
   const float h = (float)(a.n > 1 ? a.beta_c[1].x - a.beta_c[0].x : 2.0 * a.beta_c[0].x);
   uint32_t stages_issued = 0;
 
-  // ---------------- phase 1: MBF spectra of the 4 x 128 points on the tensor cores
+  // ---------------- phase 1: MBF spectra of the 512 points on the tensor cores
   {
-    const int l = tid & (kNA - 1), half = tid >> 7;
-    const float ca = tw[l].re, sa = -tw[l].im;   // cos, sin alpha_l
-    const uint32_t idesc = tc::idesc_tf32(kNA, ncol);
-    const uint32_t a_bytes = kNA * kTcK * 4, b_bytes = (uint32_t)ncol * kTcK * 4;
+    const int l = tid & 127, half = tid >> 7;
+    const uint32_t idesc = tc::idesc_tf32(128, ncol);
+    const uint32_t a_bytes = 128 * kTcK * 4, b_bytes = (uint32_t)ncol * kTcK * 4;
     const uint32_t sbo = (kTcK / 4) * 128;
     const int b_vec = ncol * kTcK / 2;           // float4 of one chunk's B operand (hi + lo)
     const float br_pi = nd[0] * 0.31830988618379067f, h_pi = h * 0.31830988618379067f;
@@ -147,21 +161,32 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
     }
     uint32_t stage = 0;
     for (int c = 0; c < n_chunks; ++c) {
-      // exp(-i beta_R p) of this thread's four basis functions at node j0, and its step
-      float pc[4], cs[4], sn[4], cd[4], sd[4];
+      // exp(-i beta_R p) at node j0 for this thread's angle in each angle block and its
+      // four basis functions, and the step to the next node
+      float pc[TPN][4], cs[TPN][4], sn[TPN][4], cd[TPN][4], sd[TPN][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = c * kTcBasis + 4 * half + u;
-        pc[u] = sbx[i] * ca + sby[i] * sa;
-        sincospif(br_pi * pc[u], &sn[u], &cs[u]);
-        sincospif(h_pi * pc[u], &sd[u], &cd[u]);
+      for (int ab = 0; ab < TPN; ++ab) {
+        const float ca = tw[128 * ab + l].re, sa = -tw[128 * ab + l].im;   // cos, sin alpha
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = c * kTcBasis + 4 * half + u;
+          pc[ab][u] = sbx[i] * ca + sby[i] * sa;
+          sincospif(br_pi * pc[ab][u], &sn[ab][u], &cs[ab][u]);
+          sincospif(h_pi * pc[ab][u], &sd[ab][u], &cd[ab][u]);
+        }
       }
       bool fail = false;
-      for (int t = 0; t < kJT; ++t, ++stage) {
+#pragma unroll
+      for (int tile = 0; tile < kTiles; ++tile) {
+        const int t = tile / TPN, ab = tile % TPN;
         const int buf = stage & 1;
-        // the MMAs of stage - 2 have read A[buf] (and, at t = 1, the previous chunk's B)
-        if (stage >= 2 && !tc::mbar_wait(&mbar[buf], ((stage - 2) >> 1) & 1, kTcPolls)) atomicOr(&s_fail, 1);
-        if (t == 1 && c + 1 < n_chunks) {
+        // the MMAs of stage - 2 have read A[buf] (and, at tile 1, the previous chunk's B):
+        // one lane per warp polls the mbarrier, the others wait at the warp barrier
+        if (stage >= 2) {
+          if (lane == 0 && !tc::mbar_wait(&mbar[buf], ((stage - 2) >> 1) & 1, kTcPolls)) atomicOr(&s_fail, 1);
+          __syncwarp();
+        }
+        if (tile == 1 && c + 1 < n_chunks) {
           const char* src = reinterpret_cast<const char*>(a.tc_bmat + (size_t)(c + 1) * 2 * ncol * kTcK);
           char* dst = reinterpret_cast<char*>(B + (size_t)((c + 1) & 1) * 2 * ncol * kTcK);
           for (int q = tid; q < b_vec; q += kIThreads)
@@ -170,17 +195,19 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
                          : "memory");
           asm volatile("cp.async.commit_group;" ::: "memory");
         }
-        if (t == 0 && c > 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
-        float* ahi = A + (size_t)buf * 2 * kNA * kTcK;
-        float* alo = ahi + kNA * kTcK;
+        if (tile == 0 && c > 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+        float* ahi = A + (size_t)buf * 2 * 128 * kTcK;
+        float* alo = ahi + 128 * kTcK;
         const float bi = nd[8 * t + 1];
+        // |beta_I p| <= beta_I r_max: the short series when that bound is small (a uniform
+        // choice per node); basis functions past n_basis meet zero rows of B
+        const bool series = bi * a.tc_rmax < 0.125f;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int iu = 4 * half + u;
-          const bool live = c * kTcBasis + iu < a.n_basis;
-          const float psi = bi * pc[u];
+          const float psi = bi * pc[ab][u];
           float ep, em;
-          if (fabsf(psi) < 0.125f) {
+          if (series) {
             // exp(+-psi) from its even and odd series parts (error < psi^6 / 720)
             const float p2 = psi * psi;
             const float ev = 1.f + p2 * (0.5f + p2 * (1.f / 24.f));
@@ -191,8 +218,7 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
             ep = expf(psi);
             em = expf(-psi);
           }
-          if (!live) { ep = 0.f; em = 0.f; }
-          const float v0 = cs[u] * ep, v1 = -sn[u] * ep, v2 = cs[u] * em, v3 = sn[u] * em;
+          const float v0 = cs[ab][u] * ep, v1 = -sn[ab][u] * ep, v2 = cs[ab][u] * em, v3 = sn[ab][u] * em;
           float h0, h1, h2, h3, l0, l1, l2, l3;
           tf32_split(v0, h0, l0);
           tf32_split(v1, h1, l1);
@@ -201,11 +227,11 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
           const uint32_t off = tc::kmajor_offset(l, 4 * iu, kTcK) / 4;
           *reinterpret_cast<float4*>(ahi + off) = make_float4(h0, h1, h2, h3);
           *reinterpret_cast<float4*>(alo + off) = make_float4(l0, l1, l2, l3);
-          // advance exp(-i beta_R p) to the next node
-          const float c2 = cs[u] * cd[u] - sn[u] * sd[u];
-          const float s2 = sn[u] * cd[u] + cs[u] * sd[u];
-          cs[u] = c2;
-          sn[u] = s2;
+          // advance exp(-i beta_R p) of this angle block to the next node
+          const float c2 = cs[ab][u] * cd[ab][u] - sn[ab][u] * sd[ab][u];
+          const float s2 = sn[ab][u] * cd[ab][u] + cs[ab][u] * sd[ab][u];
+          cs[ab][u] = c2;
+          sn[ab][u] = s2;
         }
         tc::fence_proxy_async();
         __syncthreads();
@@ -214,7 +240,7 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
           tc::fence_after_sync();
           const uint32_t a_hi = tc::smem_u32(ahi), a_lo = a_hi + a_bytes;
           const uint32_t b_hi = tc::smem_u32(B + (size_t)(c & 1) * 2 * ncol * kTcK), b_lo = b_hi + b_bytes;
-          const uint32_t d_big = tmem + (uint32_t)(2 * t * ncol), d_small = d_big + (uint32_t)ncol;
+          const uint32_t d_big = tmem + (uint32_t)(2 * tile * ncol), d_small = d_big + (uint32_t)ncol;
 #pragma unroll
           for (int s = 0; s < kTcK / 8; ++s) {
             const uint32_t ko = s * 256;
@@ -227,6 +253,7 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
           }
           tc::mma_commit(&mbar[buf]);
         }
+        ++stage;
       }
       if (fail) break;
     }
@@ -244,9 +271,10 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
     if (!s_fail) {
       constexpr int GC = tc_group_cols(MB);
       const int lq = warp & 3;
-      const int lp = 32 * lq + lane;                 // angle of this thread's TMEM lane
-      const float cl = tw[lp].re, sl = -tw[lp].im;
-      for (int t = warp >> 2; t < kJT; t += 2) {
+      for (int tile = warp >> 2; tile < kTiles; tile += 2) {
+        const int t = tile / TPN, ab = tile % TPN;
+        const int al = 128 * ab + 32 * lq + lane;      // angle of this thread's TMEM lane
+        const float cl = tw[al].re, sl = -tw[al].im;
         const cpx<float> bc = mk(nd[8 * t], nd[8 * t + 1]);
         const cpx<float> kx = mk(bc.re * cl, bc.im * cl), ky = mk(bc.re * sl, bc.im * sl);
         cpx<float> mx[2][MB], my[2][MB];
@@ -262,7 +290,7 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
           const cpx<float> sf = rooftop_factor(shp, kx, ky);
 #pragma unroll
           for (int sd2 = 0; sd2 < 2; ++sd2) {
-            const uint32_t col0 = (uint32_t)(2 * t * ncol + (sd2 * a.n_shape + sc) * GC);
+            const uint32_t col0 = (uint32_t)(2 * tile * ncol + (sd2 * a.n_shape + sc) * GC);
 #pragma unroll
             for (int cb = 0; cb < GC; cb += 8) {
               float v[8], w8[8];
@@ -287,8 +315,8 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
         for (int sd2 = 0; sd2 < 2; ++sd2)
 #pragma unroll
           for (int m = 0; m < MB; ++m) {
-            spec[((size_t)t * 4 * MB + (sd2 * MB + m) * 2 + 0) * kNA + lp] = mx[sd2][m];
-            spec[((size_t)t * 4 * MB + (sd2 * MB + m) * 2 + 1) * kNA + lp] = my[sd2][m];
+            spec[((size_t)t * 4 * MB + (sd2 * MB + m) * 2 + 0) * NA + al] = mx[sd2][m];
+            spec[((size_t)t * 4 * MB + (sd2 * MB + m) * 2 + 1) * NA + al] = my[sd2][m];
           }
       }
     }
@@ -298,35 +326,35 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
 
   if (!s_fail) {
     // ---------------- phases 2-3: kernel of Eq. 10, harmonics, contour measure
-    // With w = exp(-2 pi i / 128), sum_l H(l) w^(q l) = sum_{l < 32} w^(q l) G_r(l) where
-    // r = q mod 4 and G_r(l) = sum_k H(l + 32 k) (-i)^(r k) (the angles folded 4-fold,
-    // a 4-point DFT per l): every harmonic then costs 32 terms instead of 128.
+    // With w = exp(-2 pi i / N_alpha), sum_l H(l) w^(q l) = sum_{l < 32} w^(q l) G_r(l) where
+    // r = q mod F and G_r(l) = sum_k H(l + 32 k) W_F^(r k) (the angles folded F-fold, an
+    // F-point DFT per l): every harmonic then costs 32 terms instead of N_alpha.
     const int mr = a.n_mbf;
     const int n_pairs = mr * mr;
     const int nh = 2 * a.q_max + 1;
-    const int quarter = kNA / 4;
-    const float inv_na = 1.0f / (float)kNA;
+    const int quarter = NA / 4;
+    const float inv_na = 1.0f / (float)NA;
     for (int cls = 0; cls < a.n_cls; ++cls)
-      for (int pair0 = 0; pair0 < n_pairs; pair0 += kPC) {
-        const int npc = min(kPC, n_pairs - pair0);
+      for (int pair0 = 0; pair0 < n_pairs; pair0 += PC) {
+        const int npc = min(PC, n_pairs - pair0);
         const bool rot_t = (cls == 2), rot_b = (cls == 1);
-        for (int idx = tid; idx < npc * kJT * 32; idx += kIThreads) {
+        for (int idx = tid; idx < npc * JT * 32; idx += kIThreads) {
           const int l0 = idx & 31;
           const int rest = idx >> 5;
-          const int t = rest % kJT, pl = rest / kJT;
+          const int t = rest % JT, pl = rest / JT;
           const int pair = pair0 + pl;
           const int ia = pair / mr, ib = pair - ia * mr;
-          const cpx<float>* st = spec + (size_t)t * 4 * MB * kNA;
+          const cpx<float>* st = spec + (size_t)t * 4 * MB * NA;
           const float* o = nd + 8 * t;
           const cpx<float> gp = mk(o[4], o[5]), gr = mk(o[6], o[7]);
-          cpx<float> hk[4];
+          cpx<float> hk[F];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < F; ++k) {
             const int l = l0 + 32 * k;
-            const int lt = rot_t ? (l - quarter + kNA) & (kNA - 1) : l;
-            const int lb = rot_b ? (l - quarter + kNA) & (kNA - 1) : l;
-            cpx<float> tx = st[((0 * MB + ia) * 2 + 0) * kNA + lt], ty = st[((0 * MB + ia) * 2 + 1) * kNA + lt];
-            cpx<float> bx = st[((1 * MB + ib) * 2 + 0) * kNA + lb], by = st[((1 * MB + ib) * 2 + 1) * kNA + lb];
+            const int lt = rot_t ? (l - quarter + NA) & (NA - 1) : l;
+            const int lb = rot_b ? (l - quarter + NA) & (NA - 1) : l;
+            cpx<float> tx = st[((0 * MB + ia) * 2 + 0) * NA + lt], ty = st[((0 * MB + ia) * 2 + 1) * NA + lt];
+            cpx<float> bx = st[((1 * MB + ib) * 2 + 0) * NA + lb], by = st[((1 * MB + ib) * 2 + 1) * NA + lb];
             if (rot_t) { const cpx<float> q = tx; tx = mk(-ty.re, -ty.im); ty = q; }   // R90 (x,y) = (-y, x)
             if (rot_b) { const cpx<float> q = bx; bx = mk(-by.re, -by.im); by = q; }
             const float ua = tw[l].re, ub = -tw[l].im;
@@ -335,29 +363,28 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
             const cpx<float> eb = ua * bx + ub * by;
             hk[k] = gp * dot - gr * (et * eb);
           }
-          // G_0..G_3 at l0: the 4-point DFT of (H(l0), H(l0+32), H(l0+64), H(l0+96))
-          const cpx<float> s02 = hk[0] + hk[2], d02 = hk[0] - hk[2];
-          const cpx<float> s13 = hk[1] + hk[3], d13 = hk[1] - hk[3];
-          const cpx<float> mid = mk(d13.im, -d13.re);        // -i (h1 - h3)
-          cpx<float>* row = hbuf + (size_t)(pl * kJT + t) * kRow;
-          row[0 * 32 + l0] = s02 + s13;
-          row[1 * 32 + l0] = d02 + mid;
-          row[2 * 32 + l0] = s02 - s13;
-          row[3 * 32 + l0] = d02 - mid;
+          // G_0..G_{F-1} at l0: the F-point DFT of (H(l0 + 32 k))_k
+          if constexpr (F == 4) dft4(hk[0], hk[1], hk[2], hk[3]);
+          else dft8(hk);
+          cpx<float>* row = hbuf + (size_t)(pl * JT + t) * ROW;
+#pragma unroll
+          for (int k = 0; k < F; ++k) row[k * 32 + l0] = hk[k];
         }
         __syncthreads();
-        // warp w: harmonics of class r = w mod 4 (every fourth q), half w / 4 of them;
+        // warp w: harmonics of class r = w mod F (every F-th q), share w / F of them;
         // lanes: the 32 (pair, node) rows
         const int rowi = lane;
-        const int pl = rowi / kJT, t = rowi - pl * kJT;
+        const int pl = rowi / JT, t = rowi - pl * JT;
         const bool row_ok = pl < npc && j0 + t < a.n;
-        const int r = warp & 3;
-        // harmonic indices qi = q + q_max with q = r (mod 4), split between the two warps of r
-        const int q_first = -a.q_max + ((r - (-a.q_max)) % 4 + 4) % 4;
-        const int n_r = q_first > a.q_max ? 0 : (a.q_max - q_first) / 4 + 1;
-        const int k_lo = (warp >> 2) ? (n_r + 1) / 2 : 0, k_hi = (warp >> 2) ? n_r : (n_r + 1) / 2;
+        const int r = warp % F;
+        constexpr int WPC = 8 / F;   // warps per class
+        const int share = warp / F;
+        // harmonic indices qi = q + q_max with q = r (mod F), split between the warps of r
+        const int q_first = -a.q_max + ((r + a.q_max) % F + F) % F;
+        const int n_r = q_first > a.q_max ? 0 : (a.q_max - q_first) / F + 1;
+        const int k_lo = (n_r * share) / WPC, k_hi = (n_r * (share + 1)) / WPC;
         if (row_ok) {
-          const cpx<float>* g = hbuf + (size_t)rowi * kRow + r * 32;
+          const cpx<float>* g = hbuf + (size_t)rowi * ROW + r * 32;
           const float* o = nd + 8 * t;
           const cpx<float> w = mk(o[2], o[3]);
           const int j = j0 + t;
@@ -368,8 +395,8 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
               const int kk = min(kq + u, k_hi - 1);
-              qv[u] = q_first + 4 * kk;
-              mq[u] = ((qv[u] % kNA) + kNA) % kNA;
+              qv[u] = q_first + F * kk;
+              mq[u] = ((qv[u] % NA) + NA) % NA;
               e[u] = 0;
               acc[u] = mk(0.f, 0.f);
             }
@@ -379,7 +406,7 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
 #pragma unroll
               for (int u = 0; u < 3; ++u) {
                 cmac(acc[u], gv, tw[e[u]]);
-                e[u] = (e[u] + mq[u]) & (kNA - 1);
+                e[u] = (e[u] + mq[u]) & (NA - 1);
               }
             }
 #pragma unroll
@@ -408,32 +435,87 @@ __global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArg
   if (warp == 0) tc::tmem_dealloc(tmem, ncol_alloc);
 }
 
+template <int MB, int NA>
+__global__ void __launch_bounds__(kIThreads, 2) integrand_tc_kernel(IntegrandArgs<float> a) {
+  extern __shared__ unsigned char smem_raw[];
+  integrand_tc_body<MB, NA>(a, blockIdx.x * ItcShape<NA>::JT, smem_raw);
+}
+
+// batched form: block b processes the nodes from map[b].y of item map[b].x
+template <int MB, int NA>
+__global__ void __launch_bounds__(kIThreads, 2)
+integrand_tc_batch_kernel(const IntegrandArgs<float>* items, const int2* map) {
+  extern __shared__ unsigned char smem_raw[];
+  const int2 bm = map[blockIdx.x];
+  const IntegrandArgs<float> a = items[bm.x];
+  integrand_tc_body<MB, NA>(a, bm.y, smem_raw);
+}
+
+template <template <int, int> class K, class Go>
+cudaError_t dispatch_tc(int mb, int na, Go go) {
+  if (na == 256) {
+    switch (mb) {
+      case 1: return go(K<1, 256>::fn());
+      case 2: return go(K<2, 256>::fn());
+      default: return go(K<4, 256>::fn());
+    }
+  }
+  switch (mb) {
+    case 1: return go(K<1, 128>::fn());
+    case 2: return go(K<2, 128>::fn());
+    default: return go(K<4, 128>::fn());
+  }
+}
+
+template <int MB, int NA>
+struct SingleK {
+  static auto fn() { return integrand_tc_kernel<MB, NA>; }
+};
+template <int MB, int NA>
+struct BatchK {
+  static auto fn() { return integrand_tc_batch_kernel<MB, NA>; }
+};
+
 }  // namespace
 
 bool integrand_tc_applies(const IntegrandArgs<float>& a) {
-  if (a.n_alpha != kNA || a.tc_bmat == nullptr || a.tc_ncol <= 0 || a.n_mbf > 4) return false;
-  if (2 * kJT * a.tc_ncol > 512) return false;
+  if ((a.n_alpha != 128 && a.n_alpha != 256) || a.tc_bmat == nullptr || a.tc_ncol <= 0 || a.n_mbf > 4)
+    return false;
+  if (2 * kTiles * a.tc_ncol > 512) return false;
   const int nb_pad = (a.n_basis + kTcBasis - 1) / kTcBasis * kTcBasis;
-  return itc_layout(a.tc_ncol, tc_mbf_pad(a.n_mbf), nb_pad).total <= 220 * 1024;
+  return itc_smem(a.n_alpha, a.tc_ncol, tc_mbf_pad(a.n_mbf), nb_pad) <= 220 * 1024;
 }
+
+// contour nodes per CTA of the tensor-core integrand for n_alpha angles
+int integrand_tc_nodes(int n_alpha) { return n_alpha == 256 ? ItcShape<256>::JT : ItcShape<128>::JT; }
 
 cudaError_t launch_integrand_tc(const IntegrandArgs<float>& a, cudaStream_t s) {
   if (!integrand_tc_applies(a)) return cudaErrorInvalidValue;
   const int mb = tc_mbf_pad(a.n_mbf);
   const int nb_pad = (a.n_basis + kTcBasis - 1) / kTcBasis * kTcBasis;
-  const size_t smem = itc_layout(a.tc_ncol, mb, nb_pad).total;
-  const int grid = (a.n + kJT - 1) / kJT;
-  auto go = [&](auto kern) -> cudaError_t {
+  const size_t smem = itc_smem(a.n_alpha, a.tc_ncol, mb, nb_pad);
+  const int jt = integrand_tc_nodes(a.n_alpha);
+  const int grid = (a.n + jt - 1) / jt;
+  return dispatch_tc<SingleK>(mb, a.n_alpha, [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kIThreads, smem, s>>>(a);
     return cudaGetLastError();
-  };
-  switch (mb) {
-    case 1: return go(integrand_tc_kernel<1>);
-    case 2: return go(integrand_tc_kernel<2>);
-    default: return go(integrand_tc_kernel<4>);
-  }
+  });
+}
+
+cudaError_t launch_integrand_tc_batch(const IntegrandArgs<float>& shape_args, const IntegrandArgs<float>* items,
+                                      const int2* map, int n_blocks, cudaStream_t s) {
+  if (!integrand_tc_applies(shape_args)) return cudaErrorInvalidValue;
+  const int mb = tc_mbf_pad(shape_args.n_mbf);
+  const int nb_pad = (shape_args.n_basis + kTcBasis - 1) / kTcBasis * kTcBasis;
+  const size_t smem = itc_smem(shape_args.n_alpha, shape_args.tc_ncol, mb, nb_pad);
+  return dispatch_tc<BatchK>(mb, shape_args.n_alpha, [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<n_blocks, kIThreads, smem, s>>>(items, map);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace cfft

@@ -14,10 +14,9 @@
 //   M_a,d(k)    = sum_{s: dir(s) = d} S_s(k) T_{s,a}(k)
 //   Mbar_a,d(k) = sum_{s: dir(s) = d} S_s(k) B_{s,a}(k).
 //
-// Precision: each FP32 operand X is split X ~ X_hi + X_lo, both TF32 values
-// (X_hi the nearest TF32 to X, X_lo the nearest to X - X_hi; |X - X_hi - X_lo|
-// <= 2^-22 |X|), and each product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi
-// with float32 accumulation in tensor memory (per-term error about 3 x 2^-22).
+// Precision: each FP32 operand X is split X ~ X_hi + X_lo, both used at TF32
+// precision (|X - X_hi - X_lo| <= 2^-22 |X|), and each product is formed as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi with float32 accumulation in tensor memory.
 // The tensor core truncates when it adds into an accumulator, so the head x head
 // products and the two (small) correction products go to separate accumulators,
 // summed in float32 in the epilogue: measured against the oracle this keeps the

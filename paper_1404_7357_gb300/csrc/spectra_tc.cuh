@@ -19,17 +19,15 @@ __host__ __device__ constexpr int tc_group_cols(int m) { return 2 * m > 8 ? 2 * 
 // MBF count as compiled (1, 2, 4, 8; padding columns of Q are zero)
 __host__ __device__ inline int tc_mbf_pad(int n_mbf) { return n_mbf <= 1 ? 1 : n_mbf <= 2 ? 2 : n_mbf <= 4 ? 4 : 8; }
 
-// nearest TF32 value (ties away from zero), as a float with the low 13 bits clear
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// x ~ hi + lo with both parts TF32 values: |x - hi - lo| <= 2^-22 |x|
+// x = hi + lo exactly, hi with 11 significant bits (a TF32 value, nearest to x) by
+// Veltkamp's splitting with the factor 2^13 + 1, lo = x - hi with at most 13 bits.
+// The tensor core reads lo to TF32 precision, so the product uses x to within
+// 2^-11 |lo| <= 2^-23 |x|.  Three rounded multiplies/subtractions on the FP32 pipe
+// (the intrinsics keep the compiler from contracting them into an FMA).
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - hi);
+  const float t = __fmul_rn(x, 8193.0f);
+  hi = __fsub_rn(t, __fsub_rn(t, x));
+  lo = __fsub_rn(x, hi);
 }
 
 // closed-form rooftop transform a sinc^2(k_u a/2) sinc(k_v w/2) at complex k

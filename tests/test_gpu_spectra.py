@@ -94,15 +94,18 @@ def test_spectra_rejects_strip(torch_cuda):
     assert ei.value.status == 1
 
 
-def test_integrand_tensor_cores_vs_simt_and_oracle(torch_cuda):
+@pytest.mark.parametrize("n_alpha", [128, 256])
+def test_integrand_tensor_cores_vs_simt_and_oracle(torch_cuda, n_alpha):
     """The FP32-mixed tabulation with the spectra on the tensor cores (default) and with
-    SIMT spectra: contour harmonics Y = H_ab,q beta_c w against the oracle's, and tables."""
+    SIMT spectra: contour harmonics Y = H_ab,q beta_c w against the oracle's, and tables,
+    for 128 and 256 angles (angular folds 4 and 8)."""
     from paper_1404_7357_gb300 import cfft
     wl = cc.small_patch("fp32", n=1024, n_rho=256, rho_max=4.0, q_max=4)
     nodes, hq = cc.oracle_harmonics(wl)
     ref_tab, _, _ = cc.oracle_table(wl)
     out = {}
-    for name, opts in (("tensor", None), ("simt", {cfft.OPT_SPECTRA_SIMT: 1})):
+    for name, opts in (("tensor", {cfft.OPT_N_ALPHA: n_alpha}),
+                       ("simt", {cfft.OPT_N_ALPHA: n_alpha, cfft.OPT_SPECTRA_SIMT: 1})):
         ctx, tab = cc.gpu_table(wl, options=opts)
         assert ctx.info()["spectra_tc"] == (1 if name == "tensor" else 0)
         y = ctx.debug_buffer("harmonics").cpu().numpy()[0].astype(np.complex128)
@@ -110,7 +113,7 @@ def test_integrand_tensor_cores_vs_simt_and_oracle(torch_cuda):
         ey = np.abs(y - yref).max() / np.abs(yref).max()
         et = cc.rel_err_per_pair(tab, ref_tab).max()
         out[name] = (ey, et)
-        print(name, "harmonics rel err %.3g, table rel err %.3g" % (ey, et))
+        print(name, n_alpha, "harmonics rel err %.3g, table rel err %.3g" % (ey, et))
         assert ey < 1e-5 and et < 1e-5
 
 
