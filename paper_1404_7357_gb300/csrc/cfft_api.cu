@@ -397,11 +397,13 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
     const int rows_c = r_top + 1 - c * rchunk;
     bp_nodes += (double)cn[c] * rows_c * series;
     if (pform || wform) {
+      // matrix columns: both signs of k (matrix form) or k >= -(taps/2) with the grid folded
+      // about k = 0 (paired-harmonic form, which also visits only the nodes alpha <= pi/2)
       const int kmax_c = std::min(K - 1, (int)std::ceil(rho_top / ds) + bp_taps);
-      const int n_kt = (2 * kmax_c + ktile) / ktile;
+      const int n_kt = pform ? (kmax_c + bp_taps / 2 + ktile) / ktile : (2 * kmax_c + ktile) / ktile;
       bp_macs += (double)rows_c * n_kt * ktile * series;
       const int n_mat = pform ? (ctx->q_max + 1) * ((series_per_q + 15) / 16) : nh;
-      bp_stencils += (double)rows_c * cn[c] * n_mat;
+      bp_stencils += (double)rows_c * (pform ? (cn[c] + 1) / 2 : cn[c]) * n_mat;
     }
     coff[c] = tot;
     tot += cn[c];

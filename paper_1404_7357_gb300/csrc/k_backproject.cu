@@ -456,25 +456,35 @@ __device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int
   }
 }
 
-// ---- paired-harmonic matrix form (FP32-mixed)
+// ---- paired-harmonic, mirror-folded matrix form (FP32-mixed)
 //
-// cos(q alpha) is even in q, so the interpolation matrix W_q of the matrix form
-// is the same for q and -q: one W per |q| serves the grids of both harmonics
-// (32 series: 16 of q = +|q| and 16 of q = -|q|), halving the scatter.  A CTA
-// owns 256 rows (one thread per row), so every thread adds the stencils of its
-// row's nodes into its own column of W with plain read-modify-write (no
-// atomics, no search for the row of a work item).  The product
-// W [256 rows x 32 grid points] x G [32 points x 32 series] is register-tiled
-// 4 rows x 8 series per thread; the lanes of a warp cover 8 row quads x 4
-// series octets, so each 16-byte shared-memory load is one wavefront.
+// Two symmetries of the alpha quadrature shrink the matrix form:
+//  * cos(q alpha) is even in q, so one interpolation matrix serves q and -q
+//    (32 series per task: 16 of q = +|q|, 16 of q = -|q|);
+//  * the midpoint nodes are symmetric about alpha = pi/2: the node at pi - alpha
+//    has u = rho cos / ds of the opposite sign, the weight (-1)^q cos(q alpha),
+//    the mirrored Lagrange stencil and the conjugate demodulation phase.  For a
+//    node with u >= 0 and its mirror the two contributions sum to
+//      c sum_k L_k(u) [ Re(ph) G+(k) + i Im(ph) G-(k) ],
+//      G+-(k) = G(k) +- (-1)^q G(-k),
+//    so only the nodes with alpha <= pi/2 are visited (the middle node, when the
+//    count is odd, with weight 1/2), the K range is k >= -(taps/2 - 1), and the
+//    two matrices A = sum c L Re(ph), B = sum c L Im(ph) are real:
+//      Z(r) = sum_k A(r, k) G+(k) + i B(r, k) G-(k).
+// A CTA owns 256 rows (one thread per row): every thread adds the stencils of
+// its row's nodes into its own column of (A, B) with plain read-modify-write.
+// The product is register-tiled 4 rows x 8 series per thread; the lanes of a
+// warp cover 8 row quads x 4 series octets, so each 16-byte shared-memory load
+// is one wavefront.
 constexpr int kPR = 256;           // rows per tile = threads
 constexpr int kPK = 32;            // grid points per K-tile
-constexpr int kPStride = kPR + 8;  // W row stride (complex entries)
+constexpr int kPStride = kPR + 8;  // W row stride (entries (A, B))
 constexpr int kPSeries = 16;       // series per sign per task
 
 size_t pm_smem_bytes(int n_nodes_max) {
-  return (size_t)kPK * kPStride * sizeof(cpx<float>) + (size_t)kPK * 2 * kPSeries * sizeof(cpx<float>) +
-         (size_t)n_nodes_max * (sizeof(NodeCos<float>) + sizeof(float)) + 64;
+  const int n_half = (n_nodes_max + 1) / 2;
+  return (size_t)kPK * kPStride * sizeof(cpx<float>) + (size_t)2 * kPK * 2 * kPSeries * sizeof(cpx<float>) +
+         (size_t)n_half * (sizeof(NodeCos<float>) + sizeof(float)) + 64;
 }
 
 template <int TAPS>
@@ -485,20 +495,24 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
   const int r0 = tile * kPR;
   const int r1 = min(r0 + kPR, a.n_rho);
   const int np = a.chunk_nodes[tile];
+  const int nhalf = (np + 1) / 2;            // nodes with alpha <= pi / 2
   const int tid = threadIdx.x;
-  cpx<float>* W = reinterpret_cast<cpx<float>*>(smem_raw);
-  cpx<float>* G = W + kPK * kPStride;
-  NodeCos<float>* scos = reinterpret_cast<NodeCos<float>*>(G + kPK * 2 * kPSeries);
-  float* scq = reinterpret_cast<float*>(scos + np);
+  cpx<float>* W = reinterpret_cast<cpx<float>*>(smem_raw);          // (A, B) [kk][row]
+  cpx<float>* Gp = W + kPK * kPStride;                               // G+ [kk][series]
+  cpx<float>* Gm = Gp + kPK * 2 * kPSeries;                          // G- [kk][series]
+  NodeCos<float>* scos = reinterpret_cast<NodeCos<float>*>(Gm + kPK * 2 * kPSeries);
+  float* scq = reinterpret_cast<float*>(scos + nhalf);
   const int four_np = 4 * np;
-  for (int t = tid; t < np; t += blockDim.x) {
+  for (int t = tid; t < nhalf; t += blockDim.x) {
     const double c = a.cosv[a.chunk_off[tile] + t];
     NodeCos<float> nc;
     nc.hi = (float)c;
     nc.lo = (float)(c - (double)nc.hi);
     scos[t] = nc;
     int e = (int)(((int64_t)p * (2 * t + 1)) % four_np);
-    scq[t] = cospif((float)e / (float)(2 * np));
+    float cq = cospif((float)e / (float)(2 * np));
+    if (2 * t + 1 == np) cq *= 0.5f;          // the middle node is its own mirror
+    scq[t] = cq;
   }
   float den[TAPS];
 #pragma unroll
@@ -522,31 +536,33 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
   const int r = r0 + tid;
   const bool row_ok = r < r1;
   const double arow = (double)r * a.d_rho / a.d_s;
-  const double inv_arow = arow > 0.0 ? 1.0 / arow : 0.0;
+  const float inv_arow = arow > 0.0 ? (float)(1.0 / arow) : 0.f;
   const float ahi = (float)arow, alo = (float)(arow - (double)ahi);
   const float inv_sigma = 1.0f / (float)a.sigma;
   const float scale = (float)np / 3.14159265f;
   const double rho_top = (r1 - 1) * a.d_rho;
   const int kmax = min(a.grid_half - 1, (int)ceil(rho_top / a.d_s) + TAPS);
-  const int k_first = -kmax, n_ktiles = (2 * kmax + kPK) / kPK;
+  const int k_first = -HALF - 1, n_ktiles = (kmax - k_first + kPK) / kPK;
   const int qi_pos = a.q_max + p, qi_neg = a.q_max - p;
+  const float par = (p & 1) ? -1.f : 1.f;   // (-1)^q, the same for q and -q
   __syncthreads();
   for (int kt = 0; kt < n_ktiles; ++kt) {
     const int k0 = k_first + kt * kPK;
-    // ---- own column of W to zero, then the row's node stencils that reach this tile
+    // ---- own column of (A, B) to zero, then the row's node stencils that reach this tile
 #pragma unroll
     for (int kk = 0; kk < kPK; ++kk) W[kk * kPStride + tid] = mk(0.f, 0.f);
     if (row_ok) {
       int lo = 0, hi = -1;
-      if (arow <= 0.0) {
-        if (k0 <= TAPS - 1 - HALF && k0 + kPK - 1 >= -HALF) { lo = 0; hi = np - 1; }
+      if (!(arow > 0.0)) {
+        if (k0 <= TAPS - 1 - HALF && k0 + kPK - 1 >= -HALF) { lo = 0; hi = nhalf - 1; }
       } else {
-        // stencil bases b with [b - HALF, b - HALF + TAPS - 1] meeting [k0, k0 + PK)
-        const double chi = fmin(1.0, (double)(k0 + kPK + HALF) * inv_arow);
-        const double clo = fmax(-1.0, (double)(k0 + HALF - TAPS + 1) * inv_arow);
+        // stencil bases b with [b - HALF, b - HALF + TAPS - 1] meeting [k0, k0 + PK),
+        // among the nodes with u >= 0
+        const float chi = fminf(1.0f, (float)(k0 + kPK + HALF) * inv_arow);
+        const float clo = fmaxf(0.0f, (float)(k0 + HALF - TAPS + 1) * inv_arow);
         if (chi >= clo) {
-          lo = max((int)floorf(acosf((float)chi) * scale - 0.5f) - 1, 0);
-          hi = min((int)ceilf(acosf((float)clo) * scale - 0.5f) + 1, np - 1);
+          lo = max((int)floorf(acosf(chi) * scale - 0.5f) - 1, 0);
+          hi = min((int)ceilf(acosf(clo) * scale - 0.5f) + 1, nhalf - 1);
         }
       }
       cpx<float>* wcol = W + tid;
@@ -582,7 +598,7 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
           }
         }
         const float cq = scq[l];
-        const float wr = cq * cv, wi = cq * sv;
+        const float wr = cq * cv, wi = cq * sv;   // A gets Re(ph), B gets Im(ph)
         if (kb >= 0 && kb + TAPS <= kPK) {
 #pragma unroll
           for (int m = 0; m < TAPS; ++m) {
@@ -605,32 +621,41 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
         }
       }
     }
-    // ---- grid tile: columns 0..15 the series of q = +p, 16..31 those of q = -p
+    // ---- folded grid tiles G+-(k) = G(k) +- (-1)^q G(-k): columns 0..15 the series of
+    // q = +p, 16..31 those of q = -p
     for (int t = tid; t < kPK * 2 * kPSeries; t += blockDim.x) {
       const int c = t / kPK, kk = t - c * kPK;
       const int k = k0 + kk;
       const int g = chunk * kPSeries + (c & (kPSeries - 1));
       const int qi = c < kPSeries ? qi_pos : qi_neg;
-      const bool ok = g < S && (c < kPSeries || p > 0) && k >= -a.grid_half && k <= a.grid_half;
-      G[kk * 2 * kPSeries + c] =
-          ok ? a.grid[((size_t)g * a.n_harm + qi) * (2 * a.grid_half + 1) + k + a.grid_half] : mk(0.f, 0.f);
+      cpx<float> gk = mk(0.f, 0.f), gn = mk(0.f, 0.f);
+      if (g < S && (c < kPSeries || p > 0)) {
+        const cpx<float>* src = a.grid + ((size_t)g * a.n_harm + qi) * (2 * a.grid_half + 1) + a.grid_half;
+        if (k >= -a.grid_half && k <= a.grid_half) gk = src[k];
+        if (-k >= -a.grid_half && -k <= a.grid_half) gn = src[-k];
+      }
+      Gp[kk * 2 * kPSeries + c] = mk(gk.re + par * gn.re, gk.im + par * gn.im);
+      Gm[kk * 2 * kPSeries + c] = mk(gk.re - par * gn.re, gk.im - par * gn.im);
     }
     __syncthreads();
-    // ---- acc[4 rows][8 series] += W[:, rows] x G[:, series]
-#pragma unroll 2
+    // ---- acc[4 rows][8 series] += A G+ + i B G-
+#pragma unroll 1
     for (int kk = 0; kk < kPK; ++kk) {
       const float4* wp = reinterpret_cast<const float4*>(W + kk * kPStride + 4 * rq);
       const float4 wa = wp[0], wb = wp[1];
-      const cpx<float> wv[4] = {mk(wa.x, wa.y), mk(wa.z, wa.w), mk(wb.x, wb.y), mk(wb.z, wb.w)};
-      const float4* gp = reinterpret_cast<const float4*>(G + kk * 2 * kPSeries + 8 * so);
+      const float av[4] = {wa.x, wa.z, wb.x, wb.z}, bv[4] = {wa.y, wa.w, wb.y, wb.w};
+      const float4* gpp = reinterpret_cast<const float4*>(Gp + kk * 2 * kPSeries + 8 * so);
+      const float4* gmp = reinterpret_cast<const float4*>(Gm + kk * 2 * kPSeries + 8 * so);
 #pragma unroll
       for (int j2 = 0; j2 < 4; ++j2) {
-        const float4 gv = gp[j2];
-        const cpx<float> g0 = mk(gv.x, gv.y), g1 = mk(gv.z, gv.w);
+        const float4 gpv = gpp[j2], gmv = gmp[j2];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          cmac(acc[i][2 * j2], wv[i], g0);
-          cmac(acc[i][2 * j2 + 1], wv[i], g1);
+          // (re, im) += A (Gp.re, Gp.im) + B (-Gm.im, Gm.re)
+          acc[i][2 * j2].re = fmaf(av[i], gpv.x, fmaf(-bv[i], gmv.y, acc[i][2 * j2].re));
+          acc[i][2 * j2].im = fmaf(av[i], gpv.y, fmaf(bv[i], gmv.x, acc[i][2 * j2].im));
+          acc[i][2 * j2 + 1].re = fmaf(av[i], gpv.z, fmaf(-bv[i], gmv.w, acc[i][2 * j2 + 1].re));
+          acc[i][2 * j2 + 1].im = fmaf(av[i], gpv.w, fmaf(bv[i], gmv.z, acc[i][2 * j2 + 1].im));
         }
       }
     }
