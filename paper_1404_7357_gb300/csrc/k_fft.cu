@@ -166,27 +166,32 @@ __device__ __forceinline__ void dft_r(cpx<T>* v) {
   }
 }
 
-template <class T, int R, int LOG2L, int NT>
-__device__ __forceinline__ void stockham_pass(cpx<T>* buf, int p, const cpx<T>* thi, const cpx<T>* tlo) {
+// the span P of a pass is a compile-time constant, so the padded indices of a
+// butterfly's inputs and outputs are one base plus constant offsets
+template <class T, int R, int LOG2L, int NT, int P>
+__device__ __forceinline__ void stockham_pass(cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo) {
   constexpr int L = 1 << LOG2L;
   constexpr int NB = L / R;
   constexpr int BPT = NB / NT;
   static_assert(BPT >= 1 && NB % NT == 0, "butterflies per thread");
+  static_assert(NB % 16 == 0, "input groups start on a padding boundary");
+  constexpr int p = P;
   const int tid = threadIdx.x;
-  const int stride = L / (R * p);
+  constexpr int stride = L / (R * P);
   cpx<T> v[BPT][R];
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     const int i = tid + NT * b;
+    const int pi = pidx(i);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b][r] = buf[pidx(i + r * NB)];
+    for (int r = 0; r < R; ++r) v[b][r] = buf[pi + r * (NB + NB / 16)];
   }
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     const int i = tid + NT * b;
     const int k = i & (p - 1);
-    if (k != 0) {
+    if (p > 1 && k != 0) {
       const int e = k * stride;
       const cpx<T> t1 = tw2(thi, tlo, e);
       if constexpr (R == 2) {
@@ -212,10 +217,26 @@ __device__ __forceinline__ void stockham_pass(cpx<T>* buf, int p, const cpx<T>* 
     }
     dft_r<T, R>(v[b]);
     const int j = (i - k) * R + k;
+    if constexpr (P == 1 || P % 16 == 0) {
+      // pidx(j + s P) = pidx(j) + s (P + P / 16) (P = 1: j = i R and s < R <= 16)
+      const int pj = pidx(j);
+      constexpr int step = P == 1 ? 1 : P + P / 16;
 #pragma unroll
-    for (int s = 0; s < R; ++s) buf[pidx(j + s * p)] = v[b][s];
+      for (int s = 0; s < R; ++s) buf[pj + s * step] = v[b][s];
+    } else {
+#pragma unroll
+      for (int s = 0; s < R; ++s) buf[pidx(j + s * p)] = v[b][s];
+    }
   }
   __syncthreads();
+}
+
+template <class T, int LOG2L, int NT, int P, int REMAIN>
+__device__ __forceinline__ void radix16_passes(cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo) {
+  if constexpr (REMAIN > 0) {
+    stockham_pass<T, 16, LOG2L, NT, P>(buf, thi, tlo);
+    radix16_passes<T, LOG2L, NT, P * 16, REMAIN - 1>(buf, thi, tlo);
+  }
 }
 
 // in-place (Stockham, autosorting) length-2^LOG2L FFT over the padded buffer:
@@ -223,15 +244,10 @@ __device__ __forceinline__ void stockham_pass(cpx<T>* buf, int p, const cpx<T>* 
 template <class T, int LOG2L, int NT>
 __device__ __forceinline__ void fft16_inplace(cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo) {
   constexpr int REM = LOG2L & 3;
-  int p = 1;
-  if constexpr (REM == 1) { stockham_pass<T, 2, LOG2L, NT>(buf, p, thi, tlo); p = 2; }
-  if constexpr (REM == 2) { stockham_pass<T, 4, LOG2L, NT>(buf, p, thi, tlo); p = 4; }
-  if constexpr (REM == 3) { stockham_pass<T, 8, LOG2L, NT>(buf, p, thi, tlo); p = 8; }
-#pragma unroll 1
-  for (int q = 0; q < LOG2L / 4; ++q) {
-    stockham_pass<T, 16, LOG2L, NT>(buf, p, thi, tlo);
-    p *= 16;
-  }
+  if constexpr (REM == 1) stockham_pass<T, 2, LOG2L, NT, 1>(buf, thi, tlo);
+  if constexpr (REM == 2) stockham_pass<T, 4, LOG2L, NT, 1>(buf, thi, tlo);
+  if constexpr (REM == 3) stockham_pass<T, 8, LOG2L, NT, 1>(buf, thi, tlo);
+  radix16_passes<T, LOG2L, NT, (1 << REM), LOG2L / 4>(buf, thi, tlo);
 }
 
 __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
@@ -280,22 +296,23 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   cpx<T>* zt = reinterpret_cast<cpx<T>*>((reinterpret_cast<uintptr_t>(skv + n_out) + 15) & ~(uintptr_t)15);
   const cpx<T>* y = a.y + (size_t)series * n;
 
-  // ---- per-task tables (float64 argument reduction, once)
+  // ---- per-task tables (exact integer argument reduction; the sine and cosine in the
+  // precision of T: the angles are (integer < P) / P)
   for (int r = tid; r < 128; r += NT) {
-    double sv, cv;
-    sincospi(-2.0 * (double)(((int64_t)r * k2) % P) / (double)P, &sv, &cv);
-    plo[r] = mk((T)cv, (T)sv);
-    sincospi(-2.0 * (double)r / (double)L, &sv, &cv);
-    tlo[r] = mk((T)cv, (T)sv);
+    T sv, cv;
+    sincospi_((T)(-2.0 * (double)(((int64_t)r * k2) % P) / (double)P), &sv, &cv);
+    plo[r] = mk(cv, sv);
+    sincospi_((T)(-2.0 * (double)r / (double)L), &sv, &cv);
+    tlo[r] = mk(cv, sv);
     if (r < ((L >> 7) > 0 ? (L >> 7) : 1)) {
-      sincospi(-2.0 * (double)(128 * r) / (double)L, &sv, &cv);
-      thi[r] = mk((T)cv, (T)sv);
+      sincospi_((T)(-2.0 * (double)(128 * r) / (double)L), &sv, &cv);
+      thi[r] = mk(cv, sv);
     }
   }
   for (int m = tid; m < n_hi; m += NT) {
-    double sv, cv;
-    sincospi(-2.0 * (double)(((int64_t)m * 128 * k2) % P) / (double)P, &sv, &cv);
-    phi[m] = mk((T)cv, (T)sv);
+    T sv, cv;
+    sincospi_((T)(-2.0 * (double)(((int64_t)m * 128 * k2) % P) / (double)P), &sv, &cv);
+    phi[m] = mk(cv, sv);
   }
   for (int o = tid; o < n_out; o += NT) {
     acc[o] = mk((T)0, (T)0);

@@ -15,8 +15,8 @@
 // stage is written while the tensor core consumes the previous stage.
 //
 // After the GEMM, each point's spectra (both sides, both directions, every
-// MBF) go to shared memory component-major; H_ab(j, l) for a chunk of 32 / JT
-// MBF pairs follows, folded F = N_alpha / 32 -fold in angle as it is formed
+// MBF) go to shared memory component-major; H_ab(j, l) for a chunk of MBF pairs
+// (32 or 16 (pair, node) rows) follows, folded F = N_alpha / 32 -fold in angle as it is formed
 // (an F-point DFT per angle), and the angular DFT runs over the folded rows
 // (32 terms per harmonic; rows padded by one entry, conflict-free, twiddles
 // broadcast).
@@ -37,7 +37,8 @@ struct ItcShape {
   static constexpr int TPN = NA / 128;     // tiles per contour node
   static constexpr int JT = kTiles / TPN;  // contour nodes per CTA
   static constexpr int F = NA / 32;        // angular fold of the DFT
-  static constexpr int PC = 32 / JT;       // MBF pairs per H chunk (32 rows = pairs x nodes)
+  static constexpr int ROWS = NA == 256 ? 16 : 32;   // H rows (pairs x nodes) per chunk
+  static constexpr int PC = ROWS / JT;     // MBF pairs per H chunk
   static constexpr int ROW = NA + 1;       // padded H row
 };
 
@@ -52,7 +53,7 @@ __host__ __device__ inline ItcLayout itc_layout(int ncol, int mb, int nb_pad) {
   // phase 1 (A, B operand buffers) and phases 2-3 (spectra, H rows) share one region
   const size_t p1 = (size_t)2 * 2 * 128 * kTcK * 4 + (size_t)2 * 2 * ncol * kTcK * 4;
   const size_t spec = (size_t)S::JT * 4 * mb * NA * 8;
-  const size_t p23 = spec + (size_t)S::PC * S::JT * S::ROW * 8;
+  const size_t p23 = spec + (size_t)S::ROWS * S::ROW * 8;
   L.a = 0;
   L.b = (size_t)2 * 2 * 128 * kTcK * 4;
   L.spec = 0;
@@ -153,6 +154,7 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
     const uint32_t sbo = (kTcK / 4) * 128;
     const int b_vec = ncol * kTcK / 2;           // float4 of one chunk's B operand (hi + lo)
     const float br_pi = nd[0] * 0.31830988618379067f, h_pi = h * 0.31830988618379067f;
+    const bool small_step = h * a.tc_rmax < 0.0625f;
     // B operand of chunk 0 (later chunks are prefetched one chunk ahead)
     {
       const float4* src = reinterpret_cast<const float4*>(a.tc_bmat);
@@ -172,7 +174,14 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
           const int i = c * kTcBasis + 4 * half + u;
           pc[ab][u] = sbx[i] * ca + sby[i] * sa;
           sincospif(br_pi * pc[ab][u], &sn[ab][u], &cs[ab][u]);
-          sincospif(h_pi * pc[ab][u], &sd[ab][u], &cd[ab][u]);
+          if (small_step) {
+            // |h p| <= h r_max < 1/16: short series (truncation below 1e-14)
+            const float x = h * pc[ab][u], x2 = x * x;
+            sd[ab][u] = x * (1.f - x2 * (1.f / 6.f) * (1.f - x2 * (1.f / 20.f)));
+            cd[ab][u] = 1.f - x2 * 0.5f * (1.f - x2 * (1.f / 12.f) * (1.f - x2 * (1.f / 30.f)));
+          } else {
+            sincospif(h_pi * pc[ab][u], &sd[ab][u], &cd[ab][u]);
+          }
         }
       }
       bool fail = false;
@@ -371,14 +380,15 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
           for (int k = 0; k < F; ++k) row[k * 32 + l0] = hk[k];
         }
         __syncthreads();
-        // warp w: harmonics of class r = w mod F (every F-th q), share w / F of them;
-        // lanes: the 32 (pair, node) rows
-        const int rowi = lane;
+        // warp w: harmonics of class r = w mod F (every F-th q); lanes: the ROWS (pair,
+        // node) rows, each row served by 32 / ROWS lanes that split the class's harmonics
+        constexpr int ROWS = S::ROWS;
+        const int rowi = lane % ROWS;
         const int pl = rowi / JT, t = rowi - pl * JT;
         const bool row_ok = pl < npc && j0 + t < a.n;
         const int r = warp % F;
-        constexpr int WPC = 8 / F;   // warps per class
-        const int share = warp / F;
+        constexpr int WPC = (8 / F) * (32 / ROWS);   // shares per class
+        const int share = (warp / F) * (32 / ROWS) + lane / ROWS;
         // harmonic indices qi = q + q_max with q = r (mod F), split between the warps of r
         const int q_first = -a.q_max + ((r + a.q_max) % F + F) % F;
         const int n_r = q_first > a.q_max ? 0 : (a.q_max - q_first) / F + 1;
