@@ -239,6 +239,90 @@ __device__ __forceinline__ void radix16_passes(cpx<T>* buf, const cpx<T>* thi, c
   }
 }
 
+// W_{R P}^{r k} twiddles of one butterfly (k = butterfly index mod P, stride = L / (R P))
+template <class T, int R>
+__device__ __forceinline__ void twiddle_inputs(cpx<T>* v, int e, const cpx<T>* thi, const cpx<T>* tlo) {
+  const cpx<T> t1 = tw2(thi, tlo, e);
+  if constexpr (R == 2) {
+    v[1] = v[1] * t1;
+  } else {
+    const cpx<T> t2 = t1 * t1, t3 = t2 * t1;
+    v[1] = v[1] * t1;
+    v[2] = v[2] * t2;
+    v[3] = v[3] * t3;
+    if constexpr (R >= 8) {
+      cpx<T> q = tw2(thi, tlo, 4 * e);
+#pragma unroll
+      for (int g = 1; g < R / 4; ++g) {
+        v[4 * g] = v[4 * g] * q;
+        v[4 * g + 1] = v[4 * g + 1] * (q * t1);
+        v[4 * g + 2] = v[4 * g + 2] * (q * t2);
+        v[4 * g + 3] = v[4 * g + 3] * (q * t3);
+        if (g + 1 < R / 4) q = tw2(thi, tlo, 4 * (g + 1) * e);
+      }
+    }
+  }
+}
+
+// first pass (span 1, radix R) with its inputs produced by `input(jp)` instead of
+// being read back from the buffer: the fold of the transform's input feeds the
+// butterflies directly
+template <class T, int R, int LOG2L, int NT, class In>
+__device__ __forceinline__ void first_pass_fused(cpx<T>* buf, In input) {
+  constexpr int L = 1 << LOG2L;
+  constexpr int NB = L / R;
+  constexpr int BPT = NB / NT;
+  static_assert(BPT >= 1 && NB % NT == 0, "butterflies per thread");
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int b = 0; b < BPT; ++b) {
+    const int i = tid + NT * b;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = input(i + r * NB);
+    dft_r<T, R>(v);
+    const int pj = pidx(i * R);   // span 1: outputs i R + s, one base plus s
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) buf[pj + s2] = v[s2];
+  }
+  __syncthreads();
+}
+
+// last pass (radix 16, span L/16): each butterfly's outputs t = i + s L/16 that the
+// task needs go straight into the Taylor accumulation `use(t, value)`
+template <class T, int LOG2L, int NT, class Use>
+__device__ __forceinline__ void last_pass_fused(const cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo,
+                                                Use use) {
+  constexpr int L = 1 << LOG2L;
+  constexpr int P = L / 16;
+  constexpr int NB = P;
+  constexpr int BPT = NB / NT;
+  static_assert(BPT >= 1 && NB % NT == 0 && NB % 16 == 0, "butterflies per thread");
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int b = 0; b < BPT; ++b) {
+    const int i = tid + NT * b;   // = k (i < P), stride 1
+    const int pi = pidx(i);
+    cpx<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[pi + r * (NB + NB / 16)];
+    if (i != 0) twiddle_inputs<T, 16>(v, i, thi, tlo);
+    dft_r<T, 16>(v);
+#pragma unroll
+    for (int s2 = 0; s2 < 16; ++s2) use(i + s2 * P, v[s2]);
+  }
+  __syncthreads();
+}
+
+// radix-16 passes with spans P, 16 P, ... leaving the last (span L/16) to the caller
+template <class T, int LOG2L, int NT, int P>
+__device__ __forceinline__ void middle_passes(cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo) {
+  if constexpr (P < (1 << LOG2L) / 16) {
+    stockham_pass<T, 16, LOG2L, NT, P>(buf, thi, tlo);
+    middle_passes<T, LOG2L, NT, P * 16>(buf, thi, tlo);
+  }
+}
+
 // in-place (Stockham, autosorting) length-2^LOG2L FFT over the padded buffer:
 // one pass of radix 2^(LOG2L mod 4) when that is not 1, then radix-16 passes
 template <class T, int LOG2L, int NT>
@@ -322,6 +406,52 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   __syncthreads();
   for (int nt = 0; nt <= a.taylor; ++nt) {
     const int lim = nt == 0 ? n : a.n_active;
+    const T inv = (T)1 / (T)(nt + 1);
+    if constexpr (R16) {
+      // fold + pre-twiddle W_P^{j k2} + Taylor weight (beta_I/H)^n, fed to the first pass
+      auto input = [&](int jp) -> cpx<T> {
+        cpx<T> v = mk((T)0, (T)0);
+        if (use_zt && nt > 0) {
+          for (int j = jp; j < lim; j += L) {
+            const cpx<T> x = zt[j];
+            v = v + x;
+            T b;
+            if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
+            else b = a.bi_rel[j];
+            zt[j] = b * x;   // next Taylor term
+          }
+        } else {
+          for (int j = jp; j < lim; j += L) {
+            cpx<T> x = y[j];
+            if (k2 != 0) x = x * (phi[j >> 7] * plo[j & 127]);
+            T b = (T)1;
+            if (nt > 0 || use_zt) {
+              if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
+              else b = a.bi_rel[j];
+            }
+            if (nt > 0) x = powi_scale<T>(b, nt).re * x;
+            else if (use_zt && j < a.n_active) zt[j] = b * x;   // first Taylor term for nt = 1
+            v = v + x;
+          }
+        }
+        return v;
+      };
+      constexpr int REM = LOG2L & 3;
+      constexpr int R0 = REM == 0 ? 16 : (1 << REM);
+      first_pass_fused<T, R0, LOG2L, NT>(buf, input);
+      middle_passes<T, LOG2L, NT, R0>(buf, thi, tlo);
+      // the needed outputs k = k2 + D t, |k| <= K, accumulate (H s_k)^n / n! times the term
+      last_pass_fused<T, LOG2L, NT>(buf, thi, tlo, [&](int t, cpx<T> v) {
+        const int tt = t <= t_hi ? t : t - L;
+        if (tt >= t_lo && tt <= t_hi) {
+          const int o = tt - t_lo;
+          const T f = fac[o];
+          acc[o] = acc[o] + f * v;
+          fac[o] = f * skv[o] * inv;
+        }
+      });
+      continue;
+    }
     // ---- fold + pre-twiddle W_P^{j k2} + Taylor weight (beta_I/H)^n
     if (use_zt && nt > 0) {
       // the active inputs, already pre-twiddled and weighted by (beta_I/H)^nt
@@ -356,10 +486,8 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
       }
     }
     __syncthreads();
-    if constexpr (R16) fft16_inplace<T, LOG2L, NT>(buf, thi, tlo);
-    else fft_inplace<T, LOG2L, NT>(buf, thi, tlo);
+    fft_inplace<T, LOG2L, NT>(buf, thi, tlo);
     // ---- accumulate the needed outputs: k = k2 + D t, |k| <= K
-    const T inv = (T)1 / (T)(nt + 1);
     for (int o = tid; o < n_out; o += NT) {
       int t = t_lo + o;
       int idx = t & (L - 1);  // t mod L (two's complement)
@@ -383,15 +511,19 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   }
 }
 
+// at most 128 registers per thread whatever the block size
+template <int NT>
+constexpr int fft_min_blocks() { return NT >= 512 ? 1 : 512 / NT; }
+
 template <class T, int LOG2L, int NT>
-__global__ void __launch_bounds__(NT) fft_taylor_kernel(FftArgs<T> a, int use_zt) {
+__global__ void __launch_bounds__(NT, fft_min_blocks<NT>()) fft_taylor_kernel(FftArgs<T> a, int use_zt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fft_taylor_task<T, LOG2L, NT>(a, blockIdx.x, blockIdx.y, smem_raw, use_zt);
 }
 
 // persistent form: CTAs pull (item, series, k2) tasks from a counter until none is left
 template <class T, int LOG2L, int NT>
-__global__ void __launch_bounds__(NT) fft_taylor_batch_kernel(const FftArgs<T>* items,
+__global__ void __launch_bounds__(NT, fft_min_blocks<NT>()) fft_taylor_batch_kernel(const FftArgs<T>* items,
                                                               const int4* tasks, int n_tasks,
                                                               int* counter, int use_zt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
