@@ -82,11 +82,12 @@ typedef enum {
  *                back-projection instead of its matrix form (both evaluate
  *                the same quadrature; the matrix form needs at most 64 series
  *                per harmonic and 8, 12 or 16 taps)
- *   FILL_BLOCK   test elements per row block of the bucketed fill (default
- *                1024); a value < 0 selects the per-row fill, which also
- *                serves the cases the bucketed fill does not cover (M other
- *                than 1, 2, 4; fill taps other than 8, 12, 16; an output
- *                precision different from the table's)
+ *   FILL_BLOCK   test elements per row block of the bucketed fill and of
+ *                its adjoint (default 1024); a value < 0 selects the per-row
+ *                kernels, which also serve the cases the bucketed forms do
+ *                not cover (M other than 1, 2, 4; fill taps other than 8, 12,
+ *                16; an output or gradient precision different from the
+ *                table's)
  *   SPECTRA_SIMT a value > 0 evaluates the MBF spectra of the FP32-mixed
  *                tabulation with SIMT FP32 arithmetic instead of the tensor
  *                cores (which need a rooftop element, N_ALPHA = 128, M <= 4
@@ -287,9 +288,10 @@ cfft_status cfft_get_derivative_table(const cfft_ctx* ctx, int which, const void
  * tables for the substrate (requires CFFT_OPT_DERIVATIVES at tabulation,
  * else CFFT_ERR_STATE when grad_eps_h is not NULL).  grad_z: device,
  * complex128 (grad_complex128 != 0) or complex64, rows of ld entries, layout
- * of Z_out.  Outputs are overwritten.  Pairs are sorted as in the fill;
- * accumulation uses float64 atomics (results can differ in the last bits
- * from run to run).  Synchronizes the stream. */
+ * of Z_out.  Outputs are overwritten.  Pairs are bucketed as in the fill
+ * (the fill's scratch is reused); a pair's contribution is formed in the
+ * table precision and accumulated with float64 atomics (results can differ in
+ * the last bits from run to run).  Synchronizes the stream. */
 cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_xy,
                                const int* rot, const void* grad_z, int64_t ld,
                                int grad_complex128, double* grad_pos, double* grad_eps_h);

@@ -604,11 +604,49 @@ cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
   if (grad_pos) CFFT_CUDA(cudaMemsetAsync(grad_pos, 0, (size_t)2 * n_el * sizeof(double), ctx->stream), "zero");
   if (grad_theta) CFFT_CUDA(cudaMemsetAsync(grad_theta, 0, 2 * sizeof(double), ctx->stream), "zero");
-  cudaError_t le = launch_fill_backward<T, TG>(b, ctx->stream);
+  cudaError_t le = cudaSuccess;
+  bool bucketed = false;
+  if constexpr (std::is_same<T, TG>::value) {
+    // the adjoint over the fill's buckets (same plan and scratch as the fill)
+    FillBucketPlan plan{};
+    if (ctx->opt[CFFT_OPT_FILL_BLOCK] >= 0)
+      plan = plan_fill_bucketed<T>(n_el, fa.n_mbf, fa.n_harm, fa.n_rho, fa.taps, fa.n_cls,
+                                   (int)ctx->opt[CFFT_OPT_FILL_BLOCK]);
+    if (plan.ok) {
+      CFFT_CUDA(ctx->d_fill.ensure(plan.scratch), "alloc fill scratch");
+      FillArgs<T, T> ft{};
+      ft.n_el = fa.n_el;
+      ft.n_mbf = fa.n_mbf;
+      ft.q_max = fa.q_max;
+      ft.n_harm = fa.n_harm;
+      ft.n_rho = fa.n_rho;
+      ft.taps = fa.taps;
+      ft.n_cls = fa.n_cls;
+      ft.inv_d_rho = fa.inv_d_rho;
+      ft.rho_max = fa.rho_max;
+      ft.ld = 0;
+      ft.table = fa.table;
+      ft.pos = fa.pos;
+      ft.rot = fa.rot;
+      ft.z = nullptr;
+      ft.err = fa.err;
+      FillAdjointArgs<T> ad{};
+      ad.grad = b.grad;
+      ad.ld_g = ld_g;
+      ad.dtab_eps = b.dtab_eps;
+      ad.dtab_h = b.dtab_h;
+      ad.grad_pos = grad_pos;
+      ad.grad_theta = grad_theta;
+      le = launch_fill_adjoint_bucketed<T>(ft, ad, plan, ctx->d_fill.p, ctx->stream);
+      bucketed = true;
+    }
+  }
+  if (!bucketed) le = launch_fill_backward<T, TG>(b, ctx->stream);
   if (le != cudaSuccess) return cuda_fail(ctx, le, "fill backward kernel");
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "fill backward");
+  if (flag & 2) return fail(ctx, CFFT_ERR_NUMERIC, "fill adjoint: a stencil left its bucket (internal error)");
   if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the table's rho_max");
   return CFFT_OK;
 }

@@ -334,6 +334,20 @@ FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, in
 template <class T>
 cudaError_t launch_fill_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& plan, void* scratch,
                                  cudaStream_t s);
+// adjoint of the bucketed fill: position gradient (grad_pos) and, with both
+// derivative tables, the (eps_r, h) gradient (grad_theta[0..1]); both accumulated
+template <class T>
+struct FillAdjointArgs {
+  const cpx<T>* grad;        // dL/dZ, same layout as the matrix, leading dimension ld_g
+  int64_t ld_g;
+  const cpx<T>* dtab_eps;    // d table / d eps_r, or null
+  const cpx<T>* dtab_h;      // d table / d h, or null
+  double* grad_pos;          // [2 * n_el] or null
+  double* grad_theta;        // [2] or null
+};
+template <class T>
+cudaError_t launch_fill_adjoint_bucketed(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad,
+                                         const FillBucketPlan& plan, void* scratch, cudaStream_t s);
 
 // MBF spectra on the tensor cores (FP32 with TF32 head/tail splitting)
 int spectra_tc_columns(int n_shape, int n_mbf);

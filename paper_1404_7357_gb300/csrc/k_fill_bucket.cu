@@ -45,6 +45,7 @@ struct BucketArgs {
   unsigned* cursor; // [n_keys] counts, then scatter cursors
   unsigned* off;    // [n_keys + 1] exclusive offsets
   unsigned* list;   // sorted pair codes
+  unsigned* seg;    // [<= 1024] segment sums / offsets of the key scan
 };
 
 // renormalised float-float difference (a_hi + a_lo) - (b_hi + b_lo)
@@ -62,6 +63,7 @@ struct BGeom {
   int i0;       // first stencil row (negative: parity rows)
   T x;          // stencil coordinate of rho, u - i0
   T ex, ey;     // exp(i phi)
+  T rho;        // the pair distance (for the adjoint's d phi / d Delta)
   bool bad;     // rho beyond the table
 };
 
@@ -101,6 +103,7 @@ bucket_geom(const FillArgs<T, T>& a, const BucketArgs& b, int m, int n) {
   if (i0 + TAPS > a.n_rho) i0 = a.n_rho - TAPS;
   g.i0 = i0;
   g.x = (float)(fi - i0) + f;
+  g.rho = __fadd_rn(r, rl);
   if (r > 0.f) {
     g.ex = __fdiv_rn(dxh, r);
     g.ey = __fdiv_rn(dyh, r);
@@ -128,6 +131,7 @@ bucket_geom(const FillArgs<T, T>& a, const BucketArgs&, int m, int n) {
   if (i0 + TAPS > a.n_rho) i0 = a.n_rho - TAPS;
   g.i0 = i0;
   g.x = __dsub_rn(u, (double)i0);
+  g.rho = rho;
   g.ex = rho > 0.0 ? dx / rho : 1.0;
   g.ey = rho > 0.0 ? dy / rho : 0.0;
   return g;
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(kBThreads) bucket_sort_kernel(FillArgs<T, T> a
     if (g.bad) {
       if (!SCATTER) {
         atomicOr(a.err, 1);
+        if (a.z == nullptr) continue;   // the adjoint: no matrix
         const int M = a.n_mbf;
         for (int ia = 0; ia < M; ++ia)
           for (int ib = 0; ib < M; ++ib)
@@ -176,31 +181,82 @@ __global__ void __launch_bounds__(kBThreads) bucket_sort_kernel(FillArgs<T, T> a
   }
 }
 
-// exclusive scan of the key counts: off[k] = sum_{j<k} count[j], off[n] = total,
-// and the counts are replaced by the scatter cursors (= off)
-__global__ void __launch_bounds__(1024) bucket_scan_kernel(unsigned* cursor, unsigned* off, size_t n_keys) {
-  __shared__ unsigned part[1024];
-  const int tid = threadIdx.x;
-  const size_t per = (n_keys + 1023) / 1024;
-  const size_t k0 = (size_t)tid * per, k1 = min(k0 + per, n_keys);
-  unsigned sum = 0;
-  for (size_t k = k0; k < k1; ++k) sum += cursor[k];
-  part[tid] = sum;
+// exclusive scan of the key counts, off[k] = sum_{j<k} count[j], off[n] = total, with the
+// counts replaced by the scatter cursors (= off): three passes over segments of
+// kScanSeg keys (segment sums; a scan of the sums; the segments rescanned in tiles of
+// 1024 with warp-shuffle scans), every load and store coalesced
+constexpr int kScanSeg = 16 * 1024;
+
+__device__ __forceinline__ unsigned block_incl_scan(unsigned v, unsigned* warp_tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_tot[w] = v;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const unsigned v = tid >= o ? part[tid - o] : 0u;
+  if (w == 0) {
+    unsigned t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    warp_tot[lane] = t;   // inclusive over warps
+  }
+  __syncthreads();
+  return v + (w > 0 ? warp_tot[w - 1] : 0u);
+}
+
+__global__ void __launch_bounds__(1024) scan_segment_sums(const unsigned* cnt, size_t n_keys, unsigned* seg_sum) {
+  __shared__ unsigned red[32];
+  const size_t base = (size_t)blockIdx.x * kScanSeg;
+  unsigned v = 0;
+  for (int i = threadIdx.x; i < kScanSeg; i += blockDim.x)
+    if (base + i < n_keys) v += cnt[base + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) seg_sum[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the segment sums (at most 1024 segments) and the grand total
+__global__ void __launch_bounds__(1024) scan_segment_offsets(unsigned* seg_sum, int n_seg, unsigned* off,
+                                                             size_t n_keys) {
+  __shared__ unsigned wt[32];
+  const unsigned v = threadIdx.x < n_seg ? seg_sum[threadIdx.x] : 0u;
+  const unsigned incl = block_incl_scan(v, wt);
+  if (threadIdx.x < n_seg) seg_sum[threadIdx.x] = incl - v;
+  if (threadIdx.x == blockDim.x - 1) off[n_keys] = incl;
+}
+
+__global__ void __launch_bounds__(1024) scan_apply(unsigned* cnt, unsigned* off, size_t n_keys,
+                                                   const unsigned* seg_off) {
+  __shared__ unsigned wt[32];
+  __shared__ unsigned s_run;
+  const size_t base = (size_t)blockIdx.x * kScanSeg;
+  if (threadIdx.x == 0) s_run = seg_off[blockIdx.x];
+  __syncthreads();
+  for (int t0 = 0; t0 < kScanSeg; t0 += blockDim.x) {
+    const size_t k = base + t0 + threadIdx.x;
+    const unsigned c = k < n_keys ? cnt[k] : 0u;
+    const unsigned incl = block_incl_scan(c, wt);
+    const unsigned run = s_run;
+    if (k < n_keys) {
+      off[k] = run + incl - c;
+      cnt[k] = run + incl - c;
+    }
     __syncthreads();
-    part[tid] += v;
+    if (threadIdx.x == blockDim.x - 1) s_run = run + incl;
     __syncthreads();
   }
-  unsigned run = part[tid] - sum;
-  for (size_t k = k0; k < k1; ++k) {
-    const unsigned c = cursor[k];
-    off[k] = run;
-    cursor[k] = run;
-    run += c;
-  }
-  if (tid == 1023) off[n_keys] = part[1023];
 }
 
 // M consecutive complex entries from shared memory, in 16-byte loads when they allow
@@ -228,6 +284,25 @@ __device__ __forceinline__ void load_row(const cpx<T>* p, cpx<T>* v) {
 }
 
 // M consecutive complex entries to global memory; vec: the destination is 16-byte aligned
+// M consecutive complex entries from global memory; vec: the source is 16-byte aligned
+template <class T, int M>
+__device__ __forceinline__ void load_grad_row(const cpx<T>* src, cpx<T>* v, bool vec) {
+  if constexpr (sizeof(T) == 4 && (M % 2) == 0) {
+    if (vec) {
+      const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+      for (int i = 0; i < M / 2; ++i) {
+        const float4 f = __ldg(q + i);
+        v[2 * i] = mk(f.x, f.y);
+        v[2 * i + 1] = mk(f.z, f.w);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) v[i] = src[i];
+}
+
 template <class T, int M>
 __device__ __forceinline__ void store_row(cpx<T>* dst, const cpx<T>* v, bool vec) {
   if constexpr (sizeof(T) == 4 && (M % 2) == 0) {
@@ -249,6 +324,66 @@ __device__ __forceinline__ void store_row(cpx<T>* dst, const cpx<T>* v, bool vec
   }
 }
 
+// The table rows of one window, [q][row][ab] with row = r_first .. r_first + R - 1,
+// into shared memory; rows below 0 by the parity Z_q(-rho) = (-1)^q Z_q(rho),
+// rows past the table as zeros (never inside a stencil).
+template <class T, int M>
+__device__ __forceinline__ void load_window(const FillArgs<T, T>& a, const cpx<T>* tab_cls, int r_first,
+                                            int R, cpx<T>* S) {
+  constexpr int P2 = M * M;
+  const int total = a.n_harm * R * P2;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int ab = e % P2;
+    const int rest = e / P2;
+    const int qi = rest / R;
+    const int lr = rest - qi * R;
+    int r = r_first + lr;
+    cpx<T> v = mk((T)0, (T)0);
+    if (r < a.n_rho) {
+      const bool neg = r < 0;
+      if (neg) r = -r;
+      v = tab_cls[((size_t)ab * a.n_harm + qi) * a.n_rho + r];
+      if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
+    }
+    S[e] = v;
+  }
+}
+
+// Lagrange weights at x on the nodes 0..TAPS-1 (Eq. 9's interpolation), and with
+// SLOPE their derivatives d/dx, from prefix and suffix products of (x - j)
+template <class T, int TAPS, bool SLOPE>
+__device__ __forceinline__ void stencil_weights(T x, T* wt, T* dwt) {
+  T den[TAPS];
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t) {
+    long long d = 1;
+#pragma unroll
+    for (int j = 0; j < TAPS; ++j)
+      if (j != t) d *= (long long)(t - j);
+    den[t] = (T)1 / (T)d;
+  }
+  T pre = (T)1, dpre = (T)0;
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t) {
+    wt[t] = pre;
+    if (SLOPE) {
+      dwt[t] = dpre;
+      dpre = dpre * (x - (T)t) + pre;
+    }
+    pre *= (x - (T)t);
+  }
+  T suf = (T)1, dsuf = (T)0;
+#pragma unroll
+  for (int t = TAPS - 1; t >= 0; --t) {
+    if (SLOPE) {
+      dwt[t] = (dwt[t] * suf + wt[t] * dsuf) * den[t];
+      dsuf = dsuf * (x - (T)t) + suf;
+    }
+    wt[t] *= suf * den[t];
+    suf *= (x - (T)t);
+  }
+}
+
 template <class T, int M, int TAPS>
 __global__ void __launch_bounds__(kBThreads, 2) bucket_fill_kernel(FillArgs<T, T> a, BucketArgs b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,36 +399,8 @@ __global__ void __launch_bounds__(kBThreads, 2) bucket_fill_kernel(FillArgs<T, T
   const int R = b.win + TAPS - 1;       // table rows of the window
   const int r_first = cell0 - HALF;     // table row of window row 0
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
-  {
-    const cpx<T>* tab = a.table + (size_t)cls * P2 * a.n_harm * a.n_rho;
-    const int total = a.n_harm * R * P2;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      const int ab = e % P2;
-      const int rest = e / P2;
-      const int qi = rest / R;
-      const int lr = rest - qi * R;
-      int r = r_first + lr;
-      cpx<T> v = mk((T)0, (T)0);
-      if (r < a.n_rho) {
-        const bool neg = r < 0;
-        if (neg) r = -r;
-        v = tab[((size_t)ab * a.n_harm + qi) * a.n_rho + r];
-        // Z_q(-rho) = (-1)^q Z_q(rho)
-        if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
-      }
-      S[e] = v;
-    }
-  }
+  load_window<T, M>(a, a.table + (size_t)cls * P2 * a.n_harm * a.n_rho, r_first, R, S);
   __syncthreads();
-  T den[TAPS];
-#pragma unroll
-  for (int t = 0; t < TAPS; ++t) {
-    long long d = 1;
-#pragma unroll
-    for (int j = 0; j < TAPS; ++j)
-      if (j != t) d *= (long long)(t - j);
-    den[t] = (T)1 / (T)d;
-  }
   const unsigned nmask = (1u << b.nb_bits) - 1u;
   for (unsigned p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const unsigned code = b.list[p];
@@ -305,22 +412,8 @@ __global__ void __launch_bounds__(kBThreads, 2) bucket_fill_kernel(FillArgs<T, T
       atomicOr(a.err, 2);
       continue;
     }
-    // Lagrange weights at x on the nodes 0..TAPS-1
     T wt[TAPS];
-    {
-      T pre = (T)1;
-#pragma unroll
-      for (int t = 0; t < TAPS; ++t) {
-        wt[t] = pre;
-        pre *= (g.x - (T)t);
-      }
-      T suf = (T)1;
-#pragma unroll
-      for (int t = TAPS - 1; t >= 0; --t) {
-        wt[t] *= suf * den[t];
-        suf *= (g.x - (T)t);
-      }
-    }
+    stencil_weights<T, TAPS, false>(g.x, wt, nullptr);
     const cpx<T> e1 = mk(g.ex, g.ey);
     cpx<T> zq = mk((T)1, (T)0);  // exp(-i q_max phi)
     for (int k = 0; k < a.q_max; ++k) zq = zq * conj(e1);
@@ -359,8 +452,144 @@ __global__ void __launch_bounds__(kBThreads, 2) bucket_fill_kernel(FillArgs<T, T
   }
 }
 
-template <class T, int M, int TAPS>
-cudaError_t run_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
+// Adjoint of the fill over the same buckets.  With dL = Re sum conj(G) dZ and
+//   Z_ab(m, n) = sum_q e^{i q phi} sum_t w_t(x) Z^{cls}_ab,q(i0 + t),
+// POS = true takes, per pair, D = dZ/dx (weights w') and Q = sum_q q e^{i q phi} (...)
+// (dZ/dphi = i Q), and from s_rho = Re sum conj(G) D / d_rho and
+// s_phi = -Im sum conj(G) Q the gradient with respect to Delta = r_m - r_n through
+// rho and phi; it is added to element m and subtracted from element n.  POS =
+// false contracts conj(G) with the fill of a derivative table (table = dZ/d theta,
+// contour held fixed) into one scalar, d L / d theta.
+template <class T>
+struct AdjArgs {
+  const cpx<T>* grad;    // dL/dZ, entry (m*M + a, n*M + b) at (m*M + a) * ld_g + n*M + b
+  int64_t ld_g;
+  int vec_g;             // grad rows 16-byte aligned: vector loads
+  double* grad_pos;      // [2 * n_el], accumulated (POS)
+  double* grad_theta;    // one scalar, accumulated (!POS)
+};
+
+template <class T, int M, int TAPS, bool POS>
+__global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bucket_adjoint_kernel(FillArgs<T, T> a, BucketArgs b,
+                                                                      AdjArgs<T> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int HALF = TAPS / 2 - 1;
+  constexpr int P2 = M * M;
+  const int w = blockIdx.x, cls = blockIdx.y, blk = blockIdx.z;
+  const int cell0 = w * b.win;
+  if (cell0 >= b.n_cells) return;
+  const int cell1 = min(cell0 + b.win, b.n_cells);
+  const size_t kbase = ((size_t)blk * b.n_ck + cls) * b.n_cells;
+  const unsigned p0 = b.off[kbase + cell0], p1 = b.off[kbase + cell1];
+  if (p0 == p1) return;
+  const int R = b.win + TAPS - 1;
+  const int r_first = cell0 - HALF;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
+  load_window<T, M>(a, a.table + (size_t)cls * P2 * a.n_harm * a.n_rho, r_first, R, S);
+  __syncthreads();
+  const unsigned nmask = (1u << b.nb_bits) - 1u;
+  double theta_sum = 0.0;
+  for (unsigned p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const unsigned code = b.list[p];
+    const int n = (int)(code & nmask);
+    const int m = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
+    if (POS && m == n) continue;   // Z(m, m) does not depend on the positions
+    const BGeom<T> geo = bucket_geom<T, TAPS>(a, b, m, n);
+    const int lr0 = geo.i0 - r_first;
+    if (lr0 < 0 || lr0 >= b.win) {
+      atomicOr(a.err, 2);
+      continue;
+    }
+    T wt[TAPS], dwt[TAPS];
+    stencil_weights<T, TAPS, POS>(geo.x, wt, dwt);
+    const cpx<T> e1 = mk(geo.ex, geo.ey);
+    cpx<T> zq = mk((T)1, (T)0);
+    for (int k = 0; k < a.q_max; ++k) zq = zq * conj(e1);
+    const cpx<T>* grow = g.grad + (size_t)m * M * g.ld_g + (size_t)n * M;
+    T s_a = (T)0, s_b = (T)0;
+#pragma unroll 1
+    for (int ia = 0; ia < M; ++ia) {
+      cpx<T> accA[M], accB[M];
+#pragma unroll
+      for (int ib = 0; ib < M; ++ib) accA[ib] = accB[ib] = mk((T)0, (T)0);
+      cpx<T> ph = zq;
+      T qf = (T)(-a.q_max);
+      const cpx<T>* sp = S + (size_t)lr0 * P2 + ia * M;
+#pragma unroll 1
+      for (int qi = 0; qi < a.n_harm; ++qi) {
+        cpx<T> v[M], dv[M];
+#pragma unroll
+        for (int ib = 0; ib < M; ++ib) v[ib] = dv[ib] = mk((T)0, (T)0);
+#pragma unroll
+        for (int t = 0; t < TAPS; ++t) {
+          cpx<T> row[M];
+          load_row<T, M>(sp + t * P2, row);
+#pragma unroll
+          for (int ib = 0; ib < M; ++ib) {
+            v[ib].re = fma(wt[t], row[ib].re, v[ib].re);
+            v[ib].im = fma(wt[t], row[ib].im, v[ib].im);
+            if (POS) {
+              dv[ib].re = fma(dwt[t], row[ib].re, dv[ib].re);
+              dv[ib].im = fma(dwt[t], row[ib].im, dv[ib].im);
+            }
+          }
+        }
+#pragma unroll
+        for (int ib = 0; ib < M; ++ib) {
+          if (POS) {
+            cmac(accA[ib], ph, dv[ib]);
+            const cpx<T> pv = ph * v[ib];
+            accB[ib].re = fma(qf, pv.re, accB[ib].re);
+            accB[ib].im = fma(qf, pv.im, accB[ib].im);
+          } else {
+            cmac(accA[ib], ph, v[ib]);
+          }
+        }
+        ph = ph * e1;
+        qf += (T)1;
+        sp += (size_t)R * P2;
+      }
+      cpx<T> gv[M];
+      load_grad_row<T, M>(grow + (size_t)ia * g.ld_g, gv, g.vec_g != 0);
+#pragma unroll
+      for (int ib = 0; ib < M; ++ib) {
+        // Re(conj(G) A) and Im(conj(G) B)
+        s_a += gv[ib].re * accA[ib].re + gv[ib].im * accA[ib].im;
+        if (POS) s_b += gv[ib].re * accB[ib].im - gv[ib].im * accB[ib].re;
+      }
+    }
+    if (POS) {
+      const double s_rho = (double)s_a * a.inv_d_rho;   // d/d rho = (1 / d_rho) d/dx
+      const double s_phi = -(double)s_b;
+      const double c = (double)geo.ex, sn = (double)geo.ey, rho = (double)geo.rho;
+      const double gx = s_rho * c - s_phi * sn / rho;
+      const double gy = s_rho * sn + s_phi * c / rho;
+      atomicAdd(&g.grad_pos[2 * m], gx);
+      atomicAdd(&g.grad_pos[2 * m + 1], gy);
+      atomicAdd(&g.grad_pos[2 * n], -gx);
+      atomicAdd(&g.grad_pos[2 * n + 1], -gy);
+    } else {
+      theta_sum += (double)s_a;
+    }
+  }
+  if (!POS) {
+    __shared__ double red[kBThreads / 32];
+    double v = theta_sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kBThreads / 32; ++i) t += red[i];
+      atomicAdd(g.grad_theta, t);
+    }
+  }
+}
+
+// The scratch layout of a plan and the sort state shared by the fill and its adjoint
+template <class T>
+BucketArgs bucket_args(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* scratch) {
   BucketArgs b{};
   unsigned char* sp = reinterpret_cast<unsigned char*>(scratch);
   b.ps = reinterpret_cast<const float4*>(sp);
@@ -369,6 +598,8 @@ cudaError_t run_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& pl, void
   sp += (pl.n_keys_max * sizeof(unsigned) + 255) / 256 * 256;
   b.off = reinterpret_cast<unsigned*>(sp);
   sp += ((pl.n_keys_max + 1) * sizeof(unsigned) + 255) / 256 * 256;
+  b.seg = reinterpret_cast<unsigned*>(sp);
+  sp += 1024 * sizeof(unsigned);
   b.list = reinterpret_cast<unsigned*>(sp);
   b.br = pl.block_rows;
   b.nb_bits = pl.nb_bits;
@@ -378,34 +609,89 @@ cudaError_t run_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& pl, void
   const double inv = a.inv_d_rho;
   b.ih = (float)inv;
   b.il = (float)(inv - (double)b.ih);
-  b.vec_out = ((reinterpret_cast<uintptr_t>(a.z) & 15) == 0 &&
+  b.vec_out = (a.z != nullptr && (reinterpret_cast<uintptr_t>(a.z) & 15) == 0 &&
                ((size_t)a.ld * sizeof(cpx<T>)) % 16 == 0) ? 1 : 0;
+  return b;
+}
+
+// Waves of whole row blocks: per wave the counting sort (count, scan, scatter) of its
+// pairs, then `consume(b, grid)` launches the kernels that walk the buckets.
+template <class T, int TAPS, class Consume>
+cudaError_t run_waves(const FillArgs<T, T>& a, const FillBucketPlan& pl, BucketArgs b, cudaStream_t s,
+                      Consume consume) {
   if (sizeof(T) == 4) {
     split_positions_kernel<<<(a.n_el + 255) / 256, 256, 0, s>>>(a.pos, a.n_el,
                                                               const_cast<float4*>(b.ps));
   }
-  const size_t smem = pl.smem;
-  cudaError_t e = cudaFuncSetAttribute(bucket_fill_kernel<T, M, TAPS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int n_windows = (pl.n_cells + pl.win - 1) / pl.win;
   for (int m0 = 0; m0 < a.n_el; m0 += pl.rows_per_wave) {
     b.m0 = m0;
     b.rows = min(pl.rows_per_wave, a.n_el - m0);
     const int n_blocks = (b.rows + b.br - 1) / b.br;
     const size_t n_keys = (size_t)n_blocks * b.n_ck * b.n_cells;
-    e = cudaMemsetAsync(b.cursor, 0, n_keys * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(b.cursor, 0, n_keys * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     dim3 sg((a.n_el + kBThreads - 1) / kBThreads, min(b.rows, 65535));
     bucket_sort_kernel<T, TAPS, false><<<sg, kBThreads, 0, s>>>(a, b);
-    bucket_scan_kernel<<<1, 1024, 0, s>>>(b.cursor, b.off, n_keys);
+    const int n_seg = (int)((n_keys + kScanSeg - 1) / kScanSeg);
+    if (n_seg > 1024) return cudaErrorInvalidValue;
+    scan_segment_sums<<<n_seg, 1024, 0, s>>>(b.cursor, n_keys, b.seg);
+    scan_segment_offsets<<<1, 1024, 0, s>>>(b.seg, n_seg, b.off, n_keys);
+    scan_apply<<<n_seg, 1024, 0, s>>>(b.cursor, b.off, n_keys, b.seg);
     bucket_sort_kernel<T, TAPS, true><<<sg, kBThreads, 0, s>>>(a, b);
-    dim3 fg(n_windows, b.n_ck, n_blocks);
-    bucket_fill_kernel<T, M, TAPS><<<fg, kBThreads, smem, s>>>(a, b);
+    e = consume(b, dim3(n_windows, b.n_ck, n_blocks));
+    if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+template <class T, int M, int TAPS>
+cudaError_t run_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
+  const size_t smem = pl.smem;
+  cudaError_t e = cudaFuncSetAttribute(bucket_fill_kernel<T, M, TAPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return run_waves<T, TAPS>(a, pl, bucket_args(a, pl, scratch), s, [&](const BucketArgs& b, dim3 fg) {
+    bucket_fill_kernel<T, M, TAPS><<<fg, kBThreads, smem, s>>>(a, b);
+    return cudaSuccess;
+  });
+}
+
+template <class T, int M, int TAPS>
+cudaError_t run_adjoint(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad, const FillBucketPlan& pl,
+                        void* scratch, cudaStream_t s) {
+  const size_t smem = pl.smem;
+  cudaError_t e = cudaFuncSetAttribute(bucket_adjoint_kernel<T, M, TAPS, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bucket_adjoint_kernel<T, M, TAPS, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  AdjArgs<T> g{};
+  g.grad = ad.grad;
+  g.ld_g = ad.ld_g;
+  g.vec_g = ((reinterpret_cast<uintptr_t>(ad.grad) & 15) == 0 &&
+             ((size_t)ad.ld_g * sizeof(cpx<T>)) % 16 == 0) ? 1 : 0;
+  return run_waves<T, TAPS>(a, pl, bucket_args(a, pl, scratch), s, [&](const BucketArgs& b, dim3 fg) {
+    if (ad.grad_pos) {
+      AdjArgs<T> gp = g;
+      gp.grad_pos = ad.grad_pos;
+      bucket_adjoint_kernel<T, M, TAPS, true><<<fg, kBThreads, smem, s>>>(a, b, gp);
+    }
+    if (ad.grad_theta && ad.dtab_eps && ad.dtab_h) {
+      const cpx<T>* dt[2] = {ad.dtab_eps, ad.dtab_h};
+      for (int c = 0; c < 2; ++c) {
+        FillArgs<T, T> ac = a;
+        ac.table = dt[c];
+        AdjArgs<T> gt = g;
+        gt.grad_theta = ad.grad_theta + c;
+        bucket_adjoint_kernel<T, M, TAPS, false><<<fg, kBThreads, smem, s>>>(ac, b, gt);
+      }
+    }
+    return cudaSuccess;
+  });
 }
 
 template <class T, int M>
@@ -414,6 +700,17 @@ cudaError_t run_taps(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* sc
     case 8: return run_bucketed<T, M, 8>(a, pl, scratch, s);
     case 12: return run_bucketed<T, M, 12>(a, pl, scratch, s);
     case 16: return run_bucketed<T, M, 16>(a, pl, scratch, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T, int M>
+cudaError_t adjoint_taps(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad, const FillBucketPlan& pl,
+                         void* scratch, cudaStream_t s) {
+  switch (a.taps) {
+    case 8: return run_adjoint<T, M, 8>(a, ad, pl, scratch, s);
+    case 12: return run_adjoint<T, M, 12>(a, ad, pl, scratch, s);
+    case 16: return run_adjoint<T, M, 16>(a, ad, pl, scratch, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -456,9 +753,10 @@ FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, in
   pl.rows_per_wave = rows;
   const int n_blocks = (rows + br - 1) / br;
   pl.n_keys_max = (size_t)n_blocks * n_cls * pl.n_cells;
+  if (pl.n_keys_max > (size_t)1024 * kScanSeg) return pl;   // the key scan handles 16.7 M keys
   pl.scratch = ((size_t)n_el * sizeof(float4) + 255) / 256 * 256 +
                (pl.n_keys_max * sizeof(unsigned) + 255) / 256 * 256 +
-               ((pl.n_keys_max + 1) * sizeof(unsigned) + 255) / 256 * 256 +
+               ((pl.n_keys_max + 1) * sizeof(unsigned) + 255) / 256 * 256 + 1024 * sizeof(unsigned) +
                (size_t)rows * n_el * sizeof(unsigned) + 256;
   pl.ok = true;
   return pl;
@@ -476,11 +774,30 @@ cudaError_t launch_fill_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& 
   }
 }
 
+template <class T>
+cudaError_t launch_fill_adjoint_bucketed(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad,
+                                         const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
+  if (!pl.ok) return cudaErrorInvalidValue;
+  switch (a.n_mbf) {
+    case 1: return adjoint_taps<T, 1>(a, ad, pl, scratch, s);
+    case 2: return adjoint_taps<T, 2>(a, ad, pl, scratch, s);
+    case 4: return adjoint_taps<T, 4>(a, ad, pl, scratch, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template FillBucketPlan plan_fill_bucketed<float>(int, int, int, int, int, int, int);
 template FillBucketPlan plan_fill_bucketed<double>(int, int, int, int, int, int, int);
 template cudaError_t launch_fill_bucketed<float>(const FillArgs<float, float>&, const FillBucketPlan&, void*,
                                                  cudaStream_t);
 template cudaError_t launch_fill_bucketed<double>(const FillArgs<double, double>&, const FillBucketPlan&,
                                                   void*, cudaStream_t);
+
+template cudaError_t launch_fill_adjoint_bucketed<float>(const FillArgs<float, float>&,
+                                                         const FillAdjointArgs<float>&, const FillBucketPlan&,
+                                                         void*, cudaStream_t);
+template cudaError_t launch_fill_adjoint_bucketed<double>(const FillArgs<double, double>&,
+                                                          const FillAdjointArgs<double>&,
+                                                          const FillBucketPlan&, void*, cudaStream_t);
 
 }  // namespace cfft
