@@ -478,12 +478,17 @@ __device__ __forceinline__ void backproject_w_task(const BackprojArgs<T>& a, int
 // is one wavefront.
 constexpr int kPR = 256;           // rows per tile = threads
 constexpr int kPK = 32;            // grid points per K-tile
-constexpr int kPStride = kPR + 8;  // W row stride (entries (A, B))
+constexpr int kPStride = kPR;      // W row stride (entries (A, B)): a row's column in one bank pair
 constexpr int kPSeries = 16;       // series per sign per task
+// G+- tiles as [series][kk] with a pitch of kPK + 2 entries: the fill writes
+// consecutive kk (no bank conflicts) and the GEMM's 16-byte reads of the 4 series
+// a warp needs at once (series so + 4 j, so = lane / 8) fall on distinct banks
+constexpr int kGPitch = kPK + 2;
 
 size_t pm_smem_bytes(int n_nodes_max) {
   const int n_half = (n_nodes_max + 1) / 2;
-  return (size_t)kPK * kPStride * sizeof(cpx<float>) + (size_t)2 * kPK * 2 * kPSeries * sizeof(cpx<float>) +
+  return (size_t)kPK * kPStride * sizeof(cpx<float>) +
+         (size_t)2 * 2 * kPSeries * kGPitch * sizeof(cpx<float>) +
          (size_t)n_half * (sizeof(NodeCos<float>) + sizeof(float)) + 64;
 }
 
@@ -498,9 +503,9 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
   const int nhalf = (np + 1) / 2;            // nodes with alpha <= pi / 2
   const int tid = threadIdx.x;
   cpx<float>* W = reinterpret_cast<cpx<float>*>(smem_raw);          // (A, B) [kk][row]
-  cpx<float>* Gp = W + kPK * kPStride;                               // G+ [kk][series]
-  cpx<float>* Gm = Gp + kPK * 2 * kPSeries;                          // G- [kk][series]
-  NodeCos<float>* scos = reinterpret_cast<NodeCos<float>*>(Gm + kPK * 2 * kPSeries);
+  cpx<float>* Gp = W + kPK * kPStride;                               // G+ [series][kk]
+  cpx<float>* Gm = Gp + 2 * kPSeries * kGPitch;                      // G- [series][kk]
+  NodeCos<float>* scos = reinterpret_cast<NodeCos<float>*>(Gm + 2 * kPSeries * kGPitch);
   float* scq = reinterpret_cast<float*>(scos + nhalf);
   const int four_np = 4 * np;
   for (int t = tid; t < nhalf; t += blockDim.x) {
@@ -526,7 +531,7 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
   // GEMM layout
   const int lane = tid & 31, warp = tid >> 5;
   const int rq = warp * 8 + (lane & 7);     // rows 4 rq .. 4 rq + 3
-  const int so = lane >> 3;                 // series 8 so .. 8 so + 7
+  const int so = lane >> 3;                 // series so + 4 j, j = 0 .. 7
   cpx<float> acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -634,28 +639,31 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
         if (k >= -a.grid_half && k <= a.grid_half) gk = src[k];
         if (-k >= -a.grid_half && -k <= a.grid_half) gn = src[-k];
       }
-      Gp[kk * 2 * kPSeries + c] = mk(gk.re + par * gn.re, gk.im + par * gn.im);
-      Gm[kk * 2 * kPSeries + c] = mk(gk.re - par * gn.re, gk.im - par * gn.im);
+      Gp[c * kGPitch + kk] = mk(gk.re + par * gn.re, gk.im + par * gn.im);
+      Gm[c * kGPitch + kk] = mk(gk.re - par * gn.re, gk.im - par * gn.im);
     }
     __syncthreads();
-    // ---- acc[4 rows][8 series] += A G+ + i B G-
+    // ---- acc[4 rows][8 series] += A G+ + i B G-, two grid points per step
 #pragma unroll 1
-    for (int kk = 0; kk < kPK; ++kk) {
-      const float4* wp = reinterpret_cast<const float4*>(W + kk * kPStride + 4 * rq);
-      const float4 wa = wp[0], wb = wp[1];
-      const float av[4] = {wa.x, wa.z, wb.x, wb.z}, bv[4] = {wa.y, wa.w, wb.y, wb.w};
-      const float4* gpp = reinterpret_cast<const float4*>(Gp + kk * 2 * kPSeries + 8 * so);
-      const float4* gmp = reinterpret_cast<const float4*>(Gm + kk * 2 * kPSeries + 8 * so);
+    for (int kk = 0; kk < kPK; kk += 2) {
+      const float4* wp0 = reinterpret_cast<const float4*>(W + kk * kPStride + 4 * rq);
+      const float4* wp1 = reinterpret_cast<const float4*>(W + (kk + 1) * kPStride + 4 * rq);
+      const float4 wa0 = wp0[0], wb0 = wp0[1], wa1 = wp1[0], wb1 = wp1[1];
+      const float a0[4] = {wa0.x, wa0.z, wb0.x, wb0.z}, b0[4] = {wa0.y, wa0.w, wb0.y, wb0.w};
+      const float a1[4] = {wa1.x, wa1.z, wb1.x, wb1.z}, b1[4] = {wa1.y, wa1.w, wb1.y, wb1.w};
 #pragma unroll
-      for (int j2 = 0; j2 < 4; ++j2) {
-        const float4 gpv = gpp[j2], gmv = gmp[j2];
+      for (int j = 0; j < 8; ++j) {
+        const int c = so + 4 * j;
+        // (G(kk), G(kk + 1)) of series c
+        const float4 gpv = *reinterpret_cast<const float4*>(Gp + c * kGPitch + kk);
+        const float4 gmv = *reinterpret_cast<const float4*>(Gm + c * kGPitch + kk);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          // (re, im) += A (Gp.re, Gp.im) + B (-Gm.im, Gm.re)
-          acc[i][2 * j2].re = fmaf(av[i], gpv.x, fmaf(-bv[i], gmv.y, acc[i][2 * j2].re));
-          acc[i][2 * j2].im = fmaf(av[i], gpv.y, fmaf(bv[i], gmv.x, acc[i][2 * j2].im));
-          acc[i][2 * j2 + 1].re = fmaf(av[i], gpv.z, fmaf(-bv[i], gmv.w, acc[i][2 * j2 + 1].re));
-          acc[i][2 * j2 + 1].im = fmaf(av[i], gpv.w, fmaf(bv[i], gmv.z, acc[i][2 * j2 + 1].im));
+          // (re, im) += A (Gp.re, Gp.im) + B (-Gm.im, Gm.re), at kk and kk + 1
+          float re = fmaf(a0[i], gpv.x, fmaf(-b0[i], gmv.y, acc[i][j].re));
+          float im = fmaf(a0[i], gpv.y, fmaf(b0[i], gmv.x, acc[i][j].im));
+          acc[i][j].re = fmaf(a1[i], gpv.z, fmaf(-b1[i], gmv.w, re));
+          acc[i][j].im = fmaf(a1[i], gpv.w, fmaf(b1[i], gmv.z, im));
         }
       }
     }
@@ -664,7 +672,7 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
   const float norm = (float)(1.0 / (2.0 * 3.14159265358979323846 * (double)np));
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int c = 8 * so + j;
+    const int c = so + 4 * j;
     const int g = chunk * kPSeries + (c & (kPSeries - 1));
     if (g >= S || (c >= kPSeries && p == 0)) continue;
     const int qi = c < kPSeries ? qi_pos : qi_neg;
