@@ -104,7 +104,7 @@ struct cfft_ctx {
   double b_work_bp = 0, b_work_fft = 0;
   int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0;
   // tensor-core spectra: float copies of the element and its GEMM B operand
-  DevBuf tc_bx, tc_by, tc_bmat, tc_shapes;
+  DevBuf tc_bx, tc_by, tc_bmat, tc_bmat_mirror, tc_shapes;
   bool tc_ready = false;
   float tc_rmax = 0;
 };
@@ -325,8 +325,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
     if (tc_spectra) {
       ia.tc_bx = ctx->tc_bx.as<float>();
       ia.tc_by = ctx->tc_by.as<float>();
-      ia.tc_bmat = ctx->tc_bmat.as<float>();
-      ia.tc_ncol = spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
+      ia.tc_bmat = ctx->tc_bmat_mirror.as<float>();
+      ia.tc_ncol = 2 * spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
       ia.tc_rmax = ctx->tc_rmax;
       ia.err = ctx->d_flag.as<int>() + 2;
       if (integrand_tc_applies(ia)) {
@@ -812,8 +812,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
           ensure_tc_element(ctx) == CFFT_OK) {
         shape_args.tc_bx = ctx->tc_bx.as<float>();
         shape_args.tc_by = ctx->tc_by.as<float>();
-        shape_args.tc_bmat = ctx->tc_bmat.as<float>();
-        shape_args.tc_ncol = spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
+        shape_args.tc_bmat = ctx->tc_bmat_mirror.as<float>();
+        shape_args.tc_ncol = 2 * spectra_tc_columns((int)ctx->shapes.size(), ctx->n_mbf);
         shape_args.tc_rmax = ctx->tc_rmax;
         tc_b = integrand_tc_applies(shape_args);
         if (tc_b) jt = integrand_tc_nodes(n_alpha);
@@ -1582,14 +1582,19 @@ cfft_status ensure_tc_element(cfft_ctx* ctx) {
   std::vector<int> cls(ctx->n_basis);
   for (int s = 0; s < n_shape; ++s)
     for (int i = ctx->shapes[s].begin; i < ctx->shapes[s].end; ++i) cls[i] = s;
-  std::vector<float> bm;
+  std::vector<float> bm, bmm;
   spectra_tc_bmatrix(ctx->n_basis, n_shape, cls.data(), ctx->n_mbf,
-                     reinterpret_cast<const double*>(ctx->q.data()), ctx->n_mbf_pad, &bm);
+                     reinterpret_cast<const double*>(ctx->q.data()), ctx->n_mbf_pad, false, &bm);
+  spectra_tc_bmatrix(ctx->n_basis, n_shape, cls.data(), ctx->n_mbf,
+                     reinterpret_cast<const double*>(ctx->q.data()), ctx->n_mbf_pad, true, &bmm);
   std::vector<float> fx(ctx->bx.begin(), ctx->bx.end()), fy(ctx->by.begin(), ctx->by.end());
   double rmax = 0;
   for (size_t i = 0; i < fx.size(); ++i) rmax = std::max(rmax, std::hypot(ctx->bx[i], ctx->by[i]));
   ctx->tc_rmax = (float)(rmax * (1.0 + 1e-6));
   CFFT_CUDA(ctx->tc_bmat.ensure(bm.size() * sizeof(float)), "alloc tensor-core operand");
+  CFFT_CUDA(ctx->tc_bmat_mirror.ensure(bmm.size() * sizeof(float)), "alloc tensor-core operand");
+  CFFT_CUDA(cudaMemcpy(ctx->tc_bmat_mirror.p, bmm.data(), bmm.size() * sizeof(float), cudaMemcpyHostToDevice),
+            "upload");
   CFFT_CUDA(ctx->tc_bx.ensure(fx.size() * sizeof(float)), "alloc element");
   CFFT_CUDA(ctx->tc_by.ensure(fy.size() * sizeof(float)), "alloc element");
   CFFT_CUDA(ctx->tc_shapes.ensure(ctx->shapes.size() * sizeof(ShapeClass)), "alloc element");

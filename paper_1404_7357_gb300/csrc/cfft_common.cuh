@@ -188,7 +188,8 @@ struct IntegrandArgs {
   const double2* green_p;
   const double2* green_r;
   cpx<T>* y;                      // out [cls][pair][qi][n]
-  // tensor-core spectra (FP32 rooftop elements): float centres, GEMM B operand, width
+  // tensor-core spectra (FP32 rooftop elements): float centres, GEMM B operand (with the
+  // mirrored columns of the opposite wave direction) and its width (both blocks)
   const float* tc_bx;
   const float* tc_by;
   const float* tc_bmat;
@@ -352,7 +353,7 @@ cudaError_t launch_fill_adjoint_bucketed(const FillArgs<T, T>& a, const FillAdjo
 // MBF spectra on the tensor cores (FP32 with TF32 head/tail splitting)
 int spectra_tc_columns(int n_shape, int n_mbf);
 void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_mbf,
-                        const double* q_re_im, int q_stride, std::vector<float>* out);
+                        const double* q_re_im, int q_stride, bool mirror, std::vector<float>* out);
 cudaError_t launch_spectra_tc(int n_points, int n_basis, int n_shape, int n_mbf, const ShapeClass* shapes,
                               const float* bx, const float* by, const float* bmat, const void* k, void* out,
                               int* err, cudaStream_t s);

@@ -5,14 +5,19 @@
 // exactly as the SIMT form in k_integrand.cu computes them.
 //
 // A CTA owns 512 points: JT = 512 / N_alpha consecutive contour nodes x N_alpha
-// angles, as 4 tiles of 128 points (one tensor-memory accumulator pair each).  The basis dimension is the
-// outer loop and the nodes the inner one, so a thread keeps, for each of its
-// four basis functions, exp(-i beta_R,j p_i) (p_i = x_i cos alpha + y_i sin
-// alpha, the projection of the centre on the wave direction) and advances it
-// from node j to j + 1 by one complex rotation exp(-i h p_i) (the nodes are
-// equally spaced in beta_R); exp(+-beta_I,j p_i) is a short series (|beta_I p|
-// is small on the contour) or expf otherwise.  The A chunk of a (chunk, node)
-// stage is written while the tensor core consumes the previous stage.
+// angles.  The wave directions alpha and alpha + pi have opposite projections
+// p_i = x_i cos alpha + y_i sin alpha of every basis centre, so one A row (the
+// exponentials exp(-+i beta_c,j p_i) of direction alpha) serves both: the B
+// operand carries a second block of columns with the two sides' coefficients
+// exchanged (k_spectra_tc.cu), and the rows are the JT x N_alpha / 2 (node,
+// alpha < pi) pairs, as 2 tiles of 128 (one tensor-memory accumulator pair
+// each).  The basis dimension is the outer loop and the tiles the inner one, so
+// a thread keeps, for each of its four basis functions, exp(-i beta_R,j p_i)
+// and advances it from its node in one tile to its node in the next by one
+// complex rotation (the nodes are equally spaced in beta_R); exp(+-beta_I,j p_i)
+// is a short series (|beta_I p| is small on the contour) or expf otherwise.
+// The A chunk of a (chunk, tile) stage is written while the tensor core
+// consumes the previous stage.
 //
 // After the GEMM, each point's spectra (both sides, both directions, every
 // MBF) go to shared memory component-major; H_ab(j, l) for a chunk of MBF pairs
@@ -30,12 +35,13 @@ namespace cfft {
 namespace {
 
 constexpr int kIThreads = 256;
-constexpr int kTiles = 4;       // 128-point tiles (tensor-core M = 128) per CTA
+constexpr int kTiles = 2;       // 128-row tiles (tensor-core M = 128) per CTA
 
 template <int NA>
 struct ItcShape {
-  static constexpr int TPN = NA / 128;     // tiles per contour node
-  static constexpr int JT = kTiles / TPN;  // contour nodes per CTA
+  static constexpr int HA = NA / 2;        // directions alpha < pi (A rows per node)
+  static constexpr int NPT = 128 / HA;     // contour nodes per tile
+  static constexpr int JT = kTiles * NPT;  // contour nodes per CTA
   static constexpr int F = NA / 32;        // angular fold of the DFT
   static constexpr int ROWS = NA == 256 ? 16 : 32;   // H rows (pairs x nodes) per chunk
   static constexpr int PC = ROWS / JT;     // MBF pairs per H chunk
@@ -82,7 +88,7 @@ template <int MB, int NA>
 __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a, const int j0,
                                                   unsigned char* smem_raw) {
   using S = ItcShape<NA>;
-  constexpr int TPN = S::TPN, JT = S::JT, F = S::F, PC = S::PC, ROW = S::ROW;
+  constexpr int HA = S::HA, NPT = S::NPT, JT = S::JT, F = S::F, PC = S::PC, ROW = S::ROW;
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int ncol = a.tc_ncol;
@@ -148,13 +154,17 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
 
   // ---------------- phase 1: MBF spectra of the 512 points on the tensor cores
   {
-    const int l = tid & 127, half = tid >> 7;
+    // A row r of tile T: node T NPT + r / HA, direction alpha_(r mod HA) (and its mirror)
+    const int r = tid & 127, half = tid >> 7;
+    const int tn = r / HA, ang = r - tn * HA;
     const uint32_t idesc = tc::idesc_tf32(128, ncol);
     const uint32_t a_bytes = 128 * kTcK * 4, b_bytes = (uint32_t)ncol * kTcK * 4;
     const uint32_t sbo = (kTcK / 4) * 128;
     const int b_vec = ncol * kTcK / 2;           // float4 of one chunk's B operand (hi + lo)
-    const float br_pi = nd[0] * 0.31830988618379067f, h_pi = h * 0.31830988618379067f;
-    const bool small_step = h * a.tc_rmax < 0.0625f;
+    const float br_pi = nd[8 * tn] * 0.31830988618379067f;
+    const float hs = (float)NPT * h, hs_pi = hs * 0.31830988618379067f;   // node step between tiles
+    const bool small_step = hs * a.tc_rmax < 0.0625f;
+    const float ca = tw[ang].re, sa = -tw[ang].im;   // cos, sin alpha
     // B operand of chunk 0 (later chunks are prefetched one chunk ahead)
     {
       const float4* src = reinterpret_cast<const float4*>(a.tc_bmat);
@@ -163,31 +173,27 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
     }
     uint32_t stage = 0;
     for (int c = 0; c < n_chunks; ++c) {
-      // exp(-i beta_R p) at node j0 for this thread's angle in each angle block and its
-      // four basis functions, and the step to the next node
-      float pc[TPN][4], cs[TPN][4], sn[TPN][4], cd[TPN][4], sd[TPN][4];
+      // exp(-i beta_R p) at this thread's node of tile 0 for its four basis functions,
+      // and the rotation to its node of the next tile
+      float pc[4], cs[4], sn[4], cd[4], sd[4];
 #pragma unroll
-      for (int ab = 0; ab < TPN; ++ab) {
-        const float ca = tw[128 * ab + l].re, sa = -tw[128 * ab + l].im;   // cos, sin alpha
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = c * kTcBasis + 4 * half + u;
-          pc[ab][u] = sbx[i] * ca + sby[i] * sa;
-          sincospif(br_pi * pc[ab][u], &sn[ab][u], &cs[ab][u]);
-          if (small_step) {
-            // |h p| <= h r_max < 1/16: short series (truncation below 1e-14)
-            const float x = h * pc[ab][u], x2 = x * x;
-            sd[ab][u] = x * (1.f - x2 * (1.f / 6.f) * (1.f - x2 * (1.f / 20.f)));
-            cd[ab][u] = 1.f - x2 * 0.5f * (1.f - x2 * (1.f / 12.f) * (1.f - x2 * (1.f / 30.f)));
-          } else {
-            sincospif(h_pi * pc[ab][u], &sd[ab][u], &cd[ab][u]);
-          }
+      for (int u = 0; u < 4; ++u) {
+        const int i = c * kTcBasis + 4 * half + u;
+        pc[u] = sbx[i] * ca + sby[i] * sa;
+        sincospif(br_pi * pc[u], &sn[u], &cs[u]);
+        if (small_step) {
+          // |hs p| <= hs r_max < 1/16: short series (truncation below 1e-14)
+          const float x = hs * pc[u], x2 = x * x;
+          sd[u] = x * (1.f - x2 * (1.f / 6.f) * (1.f - x2 * (1.f / 20.f)));
+          cd[u] = 1.f - x2 * 0.5f * (1.f - x2 * (1.f / 12.f) * (1.f - x2 * (1.f / 30.f)));
+        } else {
+          sincospif(hs_pi * pc[u], &sd[u], &cd[u]);
         }
       }
       bool fail = false;
 #pragma unroll
       for (int tile = 0; tile < kTiles; ++tile) {
-        const int t = tile / TPN, ab = tile % TPN;
+        const int t = tile * NPT + tn;
         const int buf = stage & 1;
         // the MMAs of stage - 2 have read A[buf] (and, at tile 1, the previous chunk's B):
         // one lane per warp polls the mbarrier, the others wait at the warp barrier
@@ -208,13 +214,14 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
         float* ahi = A + (size_t)buf * 2 * 128 * kTcK;
         float* alo = ahi + 128 * kTcK;
         const float bi = nd[8 * t + 1];
-        // |beta_I p| <= beta_I r_max: the short series when that bound is small (a uniform
-        // choice per node); basis functions past n_basis meet zero rows of B
+        // |beta_I p| <= beta_I r_max: the short series when that bound is small (uniform
+        // per warp: a warp's rows share one node); basis functions past n_basis meet
+        // zero rows of B
         const bool series = bi * a.tc_rmax < 0.125f;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int iu = 4 * half + u;
-          const float psi = bi * pc[ab][u];
+          const float psi = bi * pc[u];
           float ep, em;
           if (series) {
             // exp(+-psi) from its even and odd series parts (error < psi^6 / 720)
@@ -227,20 +234,22 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
             ep = expf(psi);
             em = expf(-psi);
           }
-          const float v0 = cs[ab][u] * ep, v1 = -sn[ab][u] * ep, v2 = cs[ab][u] * em, v3 = sn[ab][u] * em;
+          const float v0 = cs[u] * ep, v1 = -sn[u] * ep, v2 = cs[u] * em, v3 = sn[u] * em;
           float h0, h1, h2, h3, l0, l1, l2, l3;
           tf32_split(v0, h0, l0);
           tf32_split(v1, h1, l1);
           tf32_split(v2, h2, l2);
           tf32_split(v3, h3, l3);
-          const uint32_t off = tc::kmajor_offset(l, 4 * iu, kTcK) / 4;
+          const uint32_t off = tc::kmajor_offset(r, 4 * iu, kTcK) / 4;
           *reinterpret_cast<float4*>(ahi + off) = make_float4(h0, h1, h2, h3);
           *reinterpret_cast<float4*>(alo + off) = make_float4(l0, l1, l2, l3);
-          // advance exp(-i beta_R p) of this angle block to the next node
-          const float c2 = cs[ab][u] * cd[ab][u] - sn[ab][u] * sd[ab][u];
-          const float s2 = sn[ab][u] * cd[ab][u] + cs[ab][u] * sd[ab][u];
-          cs[ab][u] = c2;
-          sn[ab][u] = s2;
+          if (tile + 1 < kTiles) {
+            // advance exp(-i beta_R p) to this thread's node of the next tile
+            const float c2 = cs[u] * cd[u] - sn[u] * sd[u];
+            const float s2 = sn[u] * cd[u] + cs[u] * sd[u];
+            cs[u] = c2;
+            sn[u] = s2;
+          }
         }
         tc::fence_proxy_async();
         __syncthreads();
@@ -279,13 +288,17 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
     // The A/B region is free now and becomes the spectra buffer.
     if (!s_fail) {
       constexpr int GC = tc_group_cols(MB);
-      const int lq = warp & 3;
-      for (int tile = warp >> 2; tile < kTiles; tile += 2) {
-        const int t = tile / TPN, ab = tile % TPN;
-        const int al = 128 * ab + 32 * lq + lane;      // angle of this thread's TMEM lane
-        const float cl = tw[al].re, sl = -tw[al].im;
-        const cpx<float> bc = mk(nd[8 * t], nd[8 * t + 1]);
-        const cpx<float> kx = mk(bc.re * cl, bc.im * cl), ky = mk(bc.re * sl, bc.im * sl);
+      const int hcol = ncol / 2;                       // columns of one direction block
+      const int lq = warp & 3, tile = warp >> 2;       // kTiles = 2: one tile per warp
+      const int r = 32 * lq + lane;                    // this thread's TMEM lane = A row
+      const int tn = r / HA, ang = r - tn * HA;
+      const int t = tile * NPT + tn;
+      const float cl = tw[ang].re, sl = -tw[ang].im;
+      const cpx<float> bc = mk(nd[8 * t], nd[8 * t + 1]);
+      const cpx<float> kx = mk(bc.re * cl, bc.im * cl), ky = mk(bc.re * sl, bc.im * sl);
+      // mir = 0: direction alpha; 1: alpha + pi (k -> -k; the rooftop factor is even)
+#pragma unroll 1
+      for (int mir = 0; mir < 2; ++mir) {
         cpx<float> mx[2][MB], my[2][MB];
 #pragma unroll
         for (int sd2 = 0; sd2 < 2; ++sd2)
@@ -299,7 +312,7 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
           const cpx<float> sf = rooftop_factor(shp, kx, ky);
 #pragma unroll
           for (int sd2 = 0; sd2 < 2; ++sd2) {
-            const uint32_t col0 = (uint32_t)(2 * tile * ncol + (sd2 * a.n_shape + sc) * GC);
+            const uint32_t col0 = (uint32_t)(2 * tile * ncol + mir * hcol + (sd2 * a.n_shape + sc) * GC);
 #pragma unroll
             for (int cb = 0; cb < GC; cb += 8) {
               float v[8], w8[8];
@@ -320,6 +333,7 @@ __device__ __forceinline__ void integrand_tc_body(const IntegrandArgs<float>& a,
           }
         }
         // component-major: comp = (side * MB + m) * 2 + d
+        const int al = ang + mir * HA;
 #pragma unroll
         for (int sd2 = 0; sd2 < 2; ++sd2)
 #pragma unroll

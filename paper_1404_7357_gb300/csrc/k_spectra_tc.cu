@@ -251,10 +251,15 @@ int spectra_tc_columns(int n_shape, int n_mbf) {
   return ncol <= 64 ? ncol : 0;
 }
 
-// B operand of the element: [chunk][hi, lo][ncol x 32] in the no-swizzle K-major layout
+// B operand of the element: [chunk][hi, lo][ncol x 32] in the no-swizzle K-major layout.
+// mirror: a second block of ncol columns gives the spectra at the opposite wave
+// direction alpha + pi from the same A row, whose projections p_i change sign, so
+// that E(alpha + pi) = E'(alpha) and E'(alpha + pi) = E(alpha): the side-t
+// coefficients move to the E' rows and the side-b ones to the E rows.
 void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_mbf,
-                        const double* q_re_im, int q_stride, std::vector<float>* out) {
-  const int ncol = spectra_tc_columns(n_shape, n_mbf);
+                        const double* q_re_im, int q_stride, bool mirror, std::vector<float>* out) {
+  const int ncol = spectra_tc_columns(n_shape, n_mbf) * (mirror ? 2 : 1);
+  const int half = mirror ? ncol / 2 : 0;
   const int n_chunks = (n_basis + kTcBasis - 1) / kTcBasis;
   out->assign((size_t)n_chunks * 2 * ncol * kTcK, 0.f);
   // nearest TF32 value, ties away from zero (the rounding of cvt.rna.tf32.f32)
@@ -292,6 +297,17 @@ void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_
       put(i, cb, 3, -qi);
       put(i, cb + 1, 2, qi);
       put(i, cb + 1, 3, qr);
+      if (mirror) {
+        // conj(Q) E(alpha + pi) = conj(Q) E'(alpha), Q E'(alpha + pi) = Q E(alpha)
+        put(i, half + ct, 2, qr);
+        put(i, half + ct, 3, qi);
+        put(i, half + ct + 1, 2, -qi);
+        put(i, half + ct + 1, 3, qr);
+        put(i, half + cb, 0, qr);
+        put(i, half + cb, 1, -qi);
+        put(i, half + cb + 1, 0, qi);
+        put(i, half + cb + 1, 1, qr);
+      }
     }
   }
 }
