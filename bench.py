@@ -438,6 +438,13 @@ def stage_flops(inf, wl):
     }
 
 
+# DRAM bytes (read + write) per launch of each table kernel on the full patch-m4 workload,
+# from one ncu capture of the current kernels (profiles/table_kernels_patch-m4.md);
+# valid only for the default table sizes
+KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.279e6, "fft": 90.669e6 + 9.122e6,
+                     "backproject": 17.986e6 + 0.009e6}
+
+
 def roofline(infos, wl, peaks, clk):
     """Dominant kernel of the tabulation step and its fraction of the bounding pipe."""
     inf = infos[-1]
@@ -448,9 +455,13 @@ def roofline(infos, wl, peaks, clk):
     fl = stage_flops(inf, wl)
     stages = {k: {"ms": ms[k], "tflops": fl[k] / (ms[k] / 1e3) / 1e12,
                   "frac": fl[k] / (ms[k] / 1e3) / 1e12 / peak_alu} for k in ms}
+    traffic = KERNEL_DRAM_BYTES if not TABLE_SIZE else {}
+    for k in stages:
+        stages[k]["dram_bytes"] = traffic.get(k)
     achieved = stages[dominant]["tflops"]
     return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_alu,
-            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic.get(dominant),
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)"
                          % peaks.get("sm_max_mhz", 2070.0),
             "stages": stages, "algorithmic_flops_per_launch": fl[dominant],
