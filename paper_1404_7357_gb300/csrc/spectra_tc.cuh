@@ -19,14 +19,13 @@ __host__ __device__ constexpr int tc_group_cols(int m) { return 2 * m > 8 ? 2 * 
 // MBF count as compiled (1, 2, 4, 8; padding columns of Q are zero)
 __host__ __device__ inline int tc_mbf_pad(int n_mbf) { return n_mbf <= 1 ? 1 : n_mbf <= 2 ? 2 : n_mbf <= 4 ? 4 : 8; }
 
-// x = hi + lo exactly, hi with 11 significant bits (a TF32 value, nearest to x) by
-// Veltkamp's splitting with the factor 2^13 + 1, lo = x - hi with at most 13 bits.
-// The tensor core reads lo to TF32 precision, so the product uses x to within
-// 2^-11 |lo| <= 2^-23 |x|.  Three rounded multiplies/subtractions on the FP32 pipe
-// (the intrinsics keep the compiler from contracting them into an FMA).
+// x = hi + lo exactly, hi with 11 significant bits (a TF32 value, nearest to x, ties
+// away from zero: half a TF32 unit added to the magnitude bits, then the 13 low bits
+// cleared), lo = x - hi (exact, at most 12 significant bits).  The tensor core reads
+// lo to TF32 precision, so the product uses x to within 2^-11 |lo| <= 2^-22 |x|.
+// Two integer operations and one rounded subtraction.
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  const float t = __fmul_rn(x, 8193.0f);
-  hi = __fsub_rn(t, __fsub_rn(t, x));
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
   lo = __fsub_rn(x, hi);
 }
 
