@@ -91,7 +91,10 @@ typedef enum {
  *   SPECTRA_SIMT a value > 0 evaluates the MBF spectra of the FP32-mixed
  *                tabulation with SIMT FP32 arithmetic instead of the tensor
  *                cores (which need a rooftop element, N_ALPHA = 128, M <= 4
- *                and the GEMM width limit of cfft_mbf_spectra)            */
+ *                and the GEMM width limit of cfft_mbf_spectra)
+ *   BP_SIMT      a value > 0 runs the FP32-mixed back-projection's matrix
+ *                products on the FP32 pipe (paired-harmonic form) instead of
+ *                the tensor cores (same quadrature; three TF32 products)  */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -102,7 +105,8 @@ typedef enum {
   CFFT_OPT_DERIVATIVES = 6,
   CFFT_OPT_BP_GATHER = 7,
   CFFT_OPT_FILL_BLOCK = 8,
-  CFFT_OPT_SPECTRA_SIMT = 9
+  CFFT_OPT_SPECTRA_SIMT = 9,
+  CFFT_OPT_BP_SIMT = 10
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -248,8 +252,10 @@ typedef struct {
  *              refresh the per-item parameters.  The batch runs on a
  *              library-owned stream ordered after the context's stream, so
  *              any context stream (also the legacy default one) works.
- * flags bit 1: autotune the sub-FFT length and the back-projection row chunk
- *              by timing the candidates on this batch (cached per structure).
+ * flags bit 1: autotune the sub-FFT length, and in FP32-mixed whether the
+ *              back-projection's products run on the tensor cores or the
+ *              FP32 pipe, by timing the candidates on this batch (cached per
+ *              structure).
  * Each n must be a multiple of 256 (sigma * n divisible by 1024).  Requires
  * cfft_set_mbf_spectra* (CFFT_ERR_STATE).  Synchronizes. */
 cfft_status cfft_tabulate_batch(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
@@ -258,11 +264,12 @@ cfft_status cfft_tabulate_batch(cfft_ctx* ctx, int n_items, const cfft_batch_ite
 
 /* Diagnostics of the last batch: stage times of the first wave (contour +
  * integrand, FFT, back-projection), the whole graph replay, work counts,
- * chosen sub-FFT length and row chunk, waves and kernel launches. */
+ * chosen sub-FFT length and row chunk, waves, kernel launches, and bp_tc = 1
+ * when the back-projection's products ran on the tensor cores. */
 typedef struct {
   double ms_integrand, ms_fft, ms_backproject, ms_graph;
   double work_subffts, work_bp_nodes;
-  int sub_len, rchunk, waves, launches;
+  int sub_len, rchunk, waves, launches, bp_tc;
 } cfft_batch_info;
 cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info);
 
@@ -305,7 +312,8 @@ cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_
  * sub_len), and back-projection node evaluations (series x rows x angles).
  * spectra_tc: 1 when the MBF spectra ran on the tensor cores; bp_form: 0 the
  * gather form of the back-projection, 1 the matrix form, 2 the paired-
- * harmonic matrix form; for the matrix forms work_bp_macs counts the complex
+ * harmonic matrix form, 3 the paired-harmonic form with its products on the
+ * tensor cores; for the matrix forms work_bp_macs counts the complex
  * multiply-adds of the interpolation-matrix products (rows x grid columns x
  * series, every harmonic) and work_bp_stencils the node stencils added into
  * the matrices (rows x angular nodes x matrices). */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libcfft.so")
 CFFT_FP64 = 0
 CFFT_FP32_MIXED = 1
 (OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
- OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT) = range(10)
+ OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT) = range(11)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 
@@ -49,7 +49,7 @@ class BatchItem(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("ms_integrand", "ms_fft", "ms_backproject", "ms_graph",
                                                 "work_subffts", "work_bp_nodes")] + \
-               [(n, ctypes.c_int) for n in ("sub_len", "rchunk", "waves", "launches")]
+               [(n, ctypes.c_int) for n in ("sub_len", "rchunk", "waves", "launches", "bp_tc")]
 
 
 class Info(ctypes.Structure):

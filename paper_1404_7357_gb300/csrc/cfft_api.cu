@@ -78,7 +78,7 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic)
-  double opt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -99,10 +99,11 @@ struct cfft_ctx {
   cudaEvent_t bev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraphExec_t bgraph = nullptr;
   std::string bsig;           // signature of the captured graph
-  std::map<std::string, std::pair<int, int>> tuned;  // signature -> (sub_len, rchunk)
+  struct TunedPlan { int sub_len, rchunk, bp_tc; };
+  std::map<std::string, TunedPlan> tuned;  // signature -> tuned shape
   double b_ms[4] = {0, 0, 0, 0};
   double b_work_bp = 0, b_work_fft = 0;
-  int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0;
+  int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0, b_bp_tc = 0;
   // tensor-core spectra: float copies of the element and its GEMM B operand
   DevBuf tc_bx, tc_by, tc_bmat, tc_bmat_mirror, tc_shapes;
   bool tc_ready = false;
@@ -298,7 +299,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
 
   double bp_nodes = 0, bp_macs = 0, bp_stencils = 0;
   int bp_form_used = 0;
-  bool in_tc = false;
+  bool in_tc = false, bp_tc = false;
   for (int ch = 0; ch < channels; ++ch) {
   // ---- a2/a3: spectra, kernel, harmonics
   IntegrandArgs<T> ia{};
@@ -378,6 +379,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   const bool taps_ok = bp_taps == 8 || bp_taps == 12 || bp_taps == 16;
   const bool gather = ctx->opt[CFFT_OPT_BP_GATHER] > 0;
   const bool pform = !fp64 && taps_ok && !gather;
+  const bool tform = pform && !(ctx->opt[CFFT_OPT_BP_SIMT] > 0);   // its products on the tensor cores
   const bool wform = !pform && series_per_q <= 64 && taps_ok && !gather;
   const int rchunk = pform ? backproject_pm_rows() : (wform ? backproject_w_rows() : 32);
   const int n_chunks = (ctx->n_rho + rchunk - 1) / rchunk;
@@ -389,7 +391,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   bp_nodes = 0;
   bp_macs = 0;
   bp_stencils = 0;
-  const int ktile = pform ? 32 : 64;   // grid columns per matrix tile of the matrix forms
+  // grid columns per matrix tile of the matrix forms
+  const int ktile = tform ? backproject_tc_ktile() : (pform ? 32 : 64);
   for (int c = 0; c < n_chunks; ++c) {
     int r_top = std::min((c + 1) * rchunk, ctx->n_rho) - 1;
     double rho_top = r_top * d_rho;
@@ -435,7 +438,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
     return fail(ctx, CFFT_ERR_ARG, "rho_max too large for one shared-memory segment");
   if (wform && backproject_w_smem<T>(max_nodes, series_per_q) > smem_cap)
     return fail(ctx, CFFT_ERR_ARG, "rho_max too large for the angular node table");
-  if (pform && backproject_pm_smem(max_nodes) > smem_cap)
+  if (pform && (tform ? backproject_tc_smem(max_nodes) : backproject_pm_smem(max_nodes)) > smem_cap)
     return fail(ctx, CFFT_ERR_ARG, "rho_max too large for the angular node table");
   group = std::min(group, series_per_q);
   BackprojArgs<T> ba{};
@@ -454,13 +457,17 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ba.alpha_margin = margin;
   ba.grid = ctx->d_grid.as<cpx<T>>();
   ba.table = ctx->d_table.as<cpx<T>>() + ch * table_elems;
-  bp_form_used = pform ? 2 : (wform ? 1 : 0);
+  bp_form_used = tform ? 3 : (pform ? 2 : (wform ? 1 : 0));
   if (pform || wform) {
     ba.chunk_nodes = ctx->d_cnodes.as<int>();
     ba.chunk_off = ctx->d_coff.as<int64_t>();
     ba.cosv = ctx->d_cos.as<double>();
     if constexpr (sizeof(T) == 4) {
-      if (pform) {
+      if (tform) {
+        ba.err = ctx->d_flag.as<int>() + 2;
+        CFFT_CUDA(launch_backproject_tc(ba, n_chunks, max_nodes, st), "backprojection kernel (tensor cores)");
+        bp_tc = true;
+      } else if (pform) {
         CFFT_CUDA(launch_backproject_pm(ba, n_chunks, max_nodes, st), "backprojection kernel");
       } else {
         CFFT_CUDA(launch_backproject_w<T>(ba, n_chunks, max_nodes, st), "backprojection kernel");
@@ -492,9 +499,10 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   }
   int flag = 0, tc_flag = 0;
   if (check) CFFT_CUDA(cudaMemcpyAsync(&flag, ctx->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
-  if (in_tc) CFFT_CUDA(cudaMemcpyAsync(&tc_flag, ctx->d_flag.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+  if (in_tc || bp_tc) CFFT_CUDA(cudaMemcpyAsync(&tc_flag, ctx->d_flag.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
   CFFT_CUDA(cudaStreamSynchronize(st), "tabulate");
   if (tc_flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "integrand: a tensor-core wait ran past its bound");
+  if (tc_flag & 32) return fail(ctx, CFFT_ERR_TIMEOUT, "back-projection: a tensor-core wait ran past its bound");
 
   cfft_info& in = ctx->info;
   in.taylor_order = taylor;
@@ -697,6 +705,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   if (bp_taps != 8 && bp_taps != 12 && bp_taps != 16)
     return fail(ctx, CFFT_ERR_ARG, "batched back-projection taps must be 8, 12 or 16");
   const bool pform_b = !fp64;  // paired-harmonic matrix form in FP32-mixed
+  // its products on the tensor cores (unless disabled; the autotuner may choose the FP32 pipe)
+  bool tform_b = pform_b && !(ctx->opt[CFFT_OPT_BP_SIMT] > 0);
   const double margin = ctx->opt[CFFT_OPT_ALPHA_MARGIN] > 0 ? ctx->opt[CFFT_OPT_ALPHA_MARGIN] : 24.0;
   const double d_rho = rho_max / (n_rho - 1);
   const size_t table_elems = (size_t)pairs * nh * n_rho;
@@ -868,7 +878,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     CFFT_CUDA(ctx->b_coff.ensure(coff.size() * sizeof(int64_t)), "alloc plan");
     CFFT_CUDA(ctx->b_cos.ensure(cos_total * sizeof(double)), "alloc plan");
     CFFT_CUDA(ctx->d_tw.ensure((size_t)L * sizeof(cpx<T>)), "alloc twiddles");
-    if (pform_b ? backproject_pm_smem(max_nodes) > 225 * 1024
+    if (pform_b ? (tform_b ? backproject_tc_smem(max_nodes) : backproject_pm_smem(max_nodes)) > 225 * 1024
                 : (backproject_w_smem<T>(max_nodes, pairs) > 225 * 1024 || pairs > 64))
       return fail(ctx, CFFT_ERR_ARG, "batch: rho_max too large for the angular node table");
     const int group = std::min(8, pairs);
@@ -976,6 +986,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         ba.chunk_nodes = ctx->b_cnodes.as<int>() + (size_t)i * n_chunks;
         ba.chunk_off = ctx->b_coff.as<int64_t>() + (size_t)i * n_chunks;
         ba.cosv = ctx->b_cos.as<double>();
+        ba.err = tform_b ? ctx->b_flag.as<int>() + 1 : nullptr;
         for (int c = n_chunks - 1; c >= 0; --c) {  // larger rho (more nodes) first
           int rows = std::min((c + 1) * rchunk, n_rho) - c * rchunk;
           if (pform_b) {
@@ -1037,6 +1048,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     ctx->b_work_fft = work_fft;
     ctx->b_sub_len = L;
     ctx->b_rchunk = rchunk;
+    ctx->b_bp_tc = tform_b ? 1 : 0;
     ctx->b_waves = (int)waves.size();
 
     // the launch sequence (stream-ordered on the batch stream)
@@ -1089,7 +1101,11 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         }
         if (w == 0) rec(ctx->bev[2]);
         if constexpr (sizeof(T) == 4) {
-          if (pform_b)
+          if (tform_b)
+            e = launch_backproject_tc_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
+                                            ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
+                                            bp_taps, max_nodes, 152, st);
+          else if (pform_b)
             e = launch_backproject_pm_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
                                             ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
                                             bp_taps, max_nodes, 152, st);
@@ -1152,8 +1168,9 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   int rchunk = pform_b ? backproject_pm_rows() : backproject_w_rows();
   auto tc = ctx->tuned.find(sig);
   if (tc != ctx->tuned.end()) {
-    L = tc->second.first;
-    rchunk = tc->second.second;
+    L = tc->second.sub_len;
+    rchunk = tc->second.rchunk;
+    tform_b = tform_b && tc->second.bp_tc != 0;
   } else if (flags & 2) {
     float best = 1e30f;
     for (int cand = 2048; cand <= l_common; cand *= 2) {
@@ -1165,12 +1182,22 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         L = cand;
       }
     }
-    ctx->tuned[sig] = {L, rchunk};
+    if (tform_b) {
+      // back-projection products: tensor cores or the FP32 pipe, whichever is faster here
+      float ms_tc = 0, ms_simt = 0;
+      cfft_status s = build_and_run(L, rchunk, 3, 2, &ms_tc);
+      if (s != CFFT_OK) return s;
+      tform_b = false;
+      s = build_and_run(L, rchunk, 3, 2, &ms_simt);
+      if (s != CFFT_OK) return s;
+      tform_b = ms_tc <= ms_simt;
+    }
+    ctx->tuned[sig] = {L, rchunk, tform_b ? 1 : 0};
   }
 
   const bool use_graph = (flags & 1) != 0;
   const bool reuse = use_graph && ctx->bgraph && ctx->bsig == sig && ctx->b_sub_len == L &&
-                     ctx->b_rchunk == rchunk;
+                     ctx->b_rchunk == rchunk && ctx->b_bp_tc == (tform_b ? 1 : 0);
   {
     // same structure: refresh the per-item parameters (substrate, contour) that the
     // captured graph reads; otherwise plan again and launch or capture
@@ -1192,6 +1219,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   CFFT_CUDA(cudaMemcpyAsync(&tc_flag, ctx->b_flag.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
   CFFT_CUDA(cudaStreamSynchronize(st), "batch");
   if (tc_flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "batch integrand: a tensor-core wait ran past its bound");
+  if (tc_flag & 32)
+    return fail(ctx, CFFT_ERR_TIMEOUT, "batch back-projection: a tensor-core wait ran past its bound");
   float ms = 0;
   if (cudaEventElapsedTime(&ms, ctx->bev[0], ctx->bev[1]) == cudaSuccess) ctx->b_ms[0] = ms;
   if (cudaEventElapsedTime(&ms, ctx->bev[1], ctx->bev[2]) == cudaSuccess) ctx->b_ms[1] = ms;
@@ -1351,7 +1380,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 9) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 10) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   return CFFT_OK;
 }
@@ -1485,6 +1514,7 @@ cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info) {
   info->rchunk = ctx->b_rchunk;
   info->waves = ctx->b_waves;
   info->launches = ctx->b_launches;
+  info->bp_tc = ctx->b_bp_tc;
   return CFFT_OK;
 }
 

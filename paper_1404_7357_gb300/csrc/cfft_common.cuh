@@ -226,7 +226,15 @@ struct BackprojArgs {
   const int* chunk_nodes;  // [chunks] angular nodes of each chunk of rows
   const int64_t* chunk_off;// [chunks] offset of its cosines in cosv
   const double* cosv;      // node cosines
+  int* err;                // tensor-core form: bit 5 set when a wait ran past its bound
 };
+
+// back-projection with the W x G+- product on the tensor cores (FP32-mixed)
+size_t backproject_tc_smem(int max_nodes);
+int backproject_tc_ktile();
+cudaError_t launch_backproject_tc(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s);
+cudaError_t launch_backproject_tc_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
+                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s);
 
 template <class T, class TO>
 struct FillArgs {

@@ -113,3 +113,24 @@ def test_batch_item_against_oracle(torch_cuda):
     err = cc.rel_err_per_pair(got[None], ref).max()
     print("batch item vs oracle", err)
     assert err < TOL["fp64"]
+
+
+def test_batch_backprojection_forms(torch_cuda):
+    """FP32-mixed batch with the back-projection's products on the tensor cores and on
+    the FP32 pipe (CFFT_OPT_BP_SIMT): both against single tabulations, several row tiles."""
+    from paper_1404_7357_gb300 import cfft
+    el = workloads.patch_rooftops()
+    items = _items(3, seed=13)
+    q_max, rho_max, n_rho = 2, 4.0, 600
+    refs = [_single(cfft, el, it, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, 128) for it in items]
+    for simt in (0, 1):
+        ctx = cfft.Context(0)
+        ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+        ctx.set_option(cfft.OPT_N_ALPHA, 128)
+        ctx.set_option(cfft.OPT_BP_SIMT, simt)
+        got = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, graph=True).cpu().numpy()
+        assert ctx.batch_info()["bp_tc"] == 1 - simt
+        for i in range(len(items)):
+            err = np.abs(got[i].astype(np.complex128) - refs[i]).max() / np.abs(refs[i]).max()
+            print("bp simt", simt, "item", i, "rel err vs single", err)
+            assert err < 2e-6

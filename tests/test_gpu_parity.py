@@ -208,3 +208,24 @@ def test_fp32_single_harmonic_and_ragged_tiles(torch_cuda):
     err = cc.rel_err_per_pair(got, ref).max()
     print("fp32 q_max=0 rel err", err)
     assert err < TOL["fp32"]
+
+
+@pytest.mark.parametrize("taps", [8, 12, 16])
+def test_backprojection_tensor_cores_vs_fp32_pipe(torch_cuda, taps):
+    """The paired-harmonic back-projection with its products on the tensor cores (three
+    TF32 products per K-tile, drained into FP32 registers) against the same form on the
+    FP32 pipe and against the oracle: 3 computed rotation classes (48 series per q, three
+    series chunks), a ragged last row tile, many K-tiles, each stencil width."""
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp32", n=2048, n_rho=600, rho_max=9.0, q_max=3, rotation_classes=4)
+    ctx_t, t_form = cc.gpu_table(wl, options={cfft.OPT_BP_TAPS: taps})
+    ctx_s, s_form = cc.gpu_table(wl, options={cfft.OPT_BP_TAPS: taps, cfft.OPT_BP_SIMT: 1})
+    assert ctx_t.info()["bp_form"] == 3 and ctx_s.info()["bp_form"] == 2
+    ref, _, _ = cc.oracle_table(wl, classes=(0, 1, 2, 3))
+    et = cc.rel_err_per_pair(t_form, ref).max()
+    es = cc.rel_err_per_pair(s_form, ref).max()
+    ets = cc.rel_err_per_pair(t_form, s_form.astype(np.complex128)).max()
+    print("taps", taps, "tensor-core form", et, "FP32-pipe form", es, "between", ets)
+    assert ets < 2e-6
+    if taps >= 12:   # 8 taps are below the FP32 interpolation target on this grid
+        assert et < TOL["fp32"] and es < TOL["fp32"]
