@@ -439,10 +439,9 @@ def stage_flops(inf, wl):
 
 
 # DRAM bytes (read + write) per launch of each table kernel on the full patch-m4 workload,
-# from one ncu capture of the current kernels (profiles/table_kernels_patch-m4.md);
+# from one ncu capture of the current kernel (None: changed since its last capture);
 # valid only for the default table sizes
-KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.279e6, "fft": 90.669e6 + 9.122e6,
-                     "backproject": 17.986e6 + 0.009e6}
+KERNEL_DRAM_BYTES = {"integrand": None, "fft": None, "backproject": 17.984e6 + 0.102e6}
 
 
 def roofline(infos, wl, peaks, clk):

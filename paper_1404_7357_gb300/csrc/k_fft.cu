@@ -314,6 +314,52 @@ __device__ __forceinline__ void last_pass_fused(const cpx<T>* buf, const cpx<T>*
   __syncthreads();
 }
 
+// the last pass when only the outputs s = 0 and s = 15 of each butterfly are needed
+// (t_hi < L/16 and t_lo > -L/16: the needed t = i and t = i - L/16 (mod L)): with
+// v_r the twiddled inputs and r = 4 r1 + r0,
+//   X_0  = sum_r0 a_r0,                 a_r0 = sum_r1 v_(4 r1 + r0),
+//   X_15 = sum_r0 W16^(-r0) b_r0,       b_r0 = sum_r1 i^r1 v_(4 r1 + r0)
+// (W16^(15 r) = W16^(-r), W16^(-4 r1) = i^r1)
+template <class T, int LOG2L, int NT, class Use>
+__device__ __forceinline__ void last_pass_pruned(const cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo,
+                                                 int t_lo, int t_hi, Use use) {
+  constexpr int L = 1 << LOG2L;
+  constexpr int P = L / 16;
+  constexpr int NB = P;
+  constexpr int BPT = NB / NT;
+  static_assert(BPT >= 1 && NB % NT == 0 && NB % 16 == 0, "butterflies per thread");
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int b = 0; b < BPT; ++b) {
+    const int i = tid + NT * b;
+    const bool need0 = i <= t_hi, need15 = i >= P + t_lo;
+    if (need0 || need15) {
+      const int pi = pidx(i);
+      cpx<T> v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = buf[pi + r * (NB + NB / 16)];
+      if (i != 0) twiddle_inputs<T, 16>(v, i, thi, tlo);
+      cpx<T> x0 = mk((T)0, (T)0), x15;
+      cpx<T> bq[4];
+#pragma unroll
+      for (int r0 = 0; r0 < 4; ++r0) {
+        const cpx<T> p0 = v[r0], p1 = v[4 + r0], p2 = v[8 + r0], p3 = v[12 + r0];
+        x0 = x0 + ((p0 + p2) + (p1 + p3));
+        // p0 + i p1 - p2 - i p3
+        const cpx<T> d02 = p0 - p2, d13 = p1 - p3;
+        bq[r0] = mk(d02.re - d13.im, d02.im + d13.re);
+      }
+      const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+      const T h = (T)0.70710678118654752440;
+      // W16^(-1) = (c1, s1), W16^(-2) = (h, h), W16^(-3) = (s1, c1)
+      x15 = bq[0] + bq[1] * mk(c1, s1) + bq[2] * mk(h, h) + bq[3] * mk(s1, c1);
+      if (need0) use(i, x0);
+      if (need15) use(i + 15 * P, x15);
+    }
+  }
+  __syncthreads();
+}
+
 // radix-16 passes with spans P, 16 P, ... leaving the last (span L/16) to the caller
 template <class T, int LOG2L, int NT, int P>
 __device__ __forceinline__ void middle_passes(cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo) {
@@ -441,7 +487,7 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
       first_pass_fused<T, R0, LOG2L, NT>(buf, input);
       middle_passes<T, LOG2L, NT, R0>(buf, thi, tlo);
       // the needed outputs k = k2 + D t, |k| <= K, accumulate (H s_k)^n / n! times the term
-      last_pass_fused<T, LOG2L, NT>(buf, thi, tlo, [&](int t, cpx<T> v) {
+      auto use = [&](int t, cpx<T> v) {
         const int tt = t <= t_hi ? t : t - L;
         if (tt >= t_lo && tt <= t_hi) {
           const int o = tt - t_lo;
@@ -449,7 +495,9 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
           acc[o] = acc[o] + f * v;
           fac[o] = f * skv[o] * inv;
         }
-      });
+      };
+      if (t_hi < L / 16 && t_lo > -(L / 16)) last_pass_pruned<T, LOG2L, NT>(buf, thi, tlo, t_lo, t_hi, use);
+      else last_pass_fused<T, LOG2L, NT>(buf, thi, tlo, use);
       continue;
     }
     // ---- fold + pre-twiddle W_P^{j k2} + Taylor weight (beta_I/H)^n
