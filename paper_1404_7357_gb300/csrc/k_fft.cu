@@ -187,6 +187,53 @@ __device__ __forceinline__ void stockham_pass(cpx<T>* buf, const cpx<T>* thi, co
     for (int r = 0; r < R; ++r) v[b][r] = buf[pi + r * (NB + NB / 16)];
   }
   __syncthreads();
+  if constexpr (BPT > 1 && R >= 4 && P > 1 && NT % P == 0) {
+    // every butterfly of this thread has the same k = tid mod P: its twiddles are formed
+    // once and applied to all of them as they are formed
+    const int k = tid & (p - 1);
+    if (k != 0) {
+      const int e = k * stride;
+      const cpx<T> t1 = tw2(thi, tlo, e), t2 = t1 * t1, t3 = t2 * t1;
+#pragma unroll
+      for (int b = 0; b < BPT; ++b) {
+        v[b][1] = v[b][1] * t1;
+        v[b][2] = v[b][2] * t2;
+        v[b][3] = v[b][3] * t3;
+      }
+      if constexpr (R >= 8) {
+        cpx<T> q = tw2(thi, tlo, 4 * e);
+#pragma unroll
+        for (int g = 1; g < R / 4; ++g) {
+          const cpx<T> q1 = q * t1, q2 = q * t2, q3 = q * t3;
+#pragma unroll
+          for (int b = 0; b < BPT; ++b) {
+            v[b][4 * g] = v[b][4 * g] * q;
+            v[b][4 * g + 1] = v[b][4 * g + 1] * q1;
+            v[b][4 * g + 2] = v[b][4 * g + 2] * q2;
+            v[b][4 * g + 3] = v[b][4 * g + 3] * q3;
+          }
+          if (g + 1 < R / 4) q = tw2(thi, tlo, 4 * (g + 1) * e);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+      const int i = tid + NT * b;
+      dft_r<T, R>(v[b]);
+      const int j = (i - k) * R + k;
+      if constexpr (P % 16 == 0) {
+        const int pj = pidx(j);
+        constexpr int step = P + P / 16;
+#pragma unroll
+        for (int s = 0; s < R; ++s) buf[pj + s * step] = v[b][s];
+      } else {
+#pragma unroll
+        for (int s = 0; s < R; ++s) buf[pidx(j + s * p)] = v[b][s];
+      }
+    }
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     const int i = tid + NT * b;
