@@ -94,7 +94,10 @@ typedef enum {
  *                and the GEMM width limit of cfft_mbf_spectra)
  *   BP_SIMT      a value > 0 runs the FP32-mixed back-projection's matrix
  *                products on the FP32 pipe (paired-harmonic form) instead of
- *                the tensor cores (same quadrature; three TF32 products)  */
+ *                the tensor cores (same quadrature; three TF32 products)
+ *   FILL_SIMT    a value > 0 runs the FP32 fill of M = 4 with 8 taps on the
+ *                FP32 pipe (bucketed form) instead of the tensor cores (the
+ *                interpolation as one contraction per stencil cell)       */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -106,7 +109,8 @@ typedef enum {
   CFFT_OPT_BP_GATHER = 7,
   CFFT_OPT_FILL_BLOCK = 8,
   CFFT_OPT_SPECTRA_SIMT = 9,
-  CFFT_OPT_BP_SIMT = 10
+  CFFT_OPT_BP_SIMT = 10,
+  CFFT_OPT_FILL_SIMT = 11
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`

@@ -78,7 +78,7 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic)
-  double opt[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -566,7 +566,7 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
   plan.ok = false;
   if (std::is_same<T, TO>::value && ctx->opt[CFFT_OPT_FILL_BLOCK] >= 0)
     plan = plan_fill_bucketed<T>(n_el, fa.n_mbf, fa.n_harm, fa.n_rho, fa.taps, fa.n_cls,
-                                 (int)ctx->opt[CFFT_OPT_FILL_BLOCK]);
+                                 (int)ctx->opt[CFFT_OPT_FILL_BLOCK], !(ctx->opt[CFFT_OPT_FILL_SIMT] > 0));
   if (plan.ok) CFFT_CUDA(ctx->d_fill.ensure(plan.scratch), "alloc fill scratch");
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
   cudaError_t le = launch_fill<T, TO>(fa, plan, ctx->d_fill.p, ctx->stream);
@@ -574,6 +574,7 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "fill");
+  if (flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "fill: a tensor-core wait ran past its bound");
   if (flag & 2) return fail(ctx, CFFT_ERR_NUMERIC, "fill: a stencil left its bucket (internal error)");
   if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the table's rho_max");
   return CFFT_OK;
@@ -619,7 +620,7 @@ cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const
     FillBucketPlan plan{};
     if (ctx->opt[CFFT_OPT_FILL_BLOCK] >= 0)
       plan = plan_fill_bucketed<T>(n_el, fa.n_mbf, fa.n_harm, fa.n_rho, fa.taps, fa.n_cls,
-                                   (int)ctx->opt[CFFT_OPT_FILL_BLOCK]);
+                                   (int)ctx->opt[CFFT_OPT_FILL_BLOCK], false);
     if (plan.ok) {
       CFFT_CUDA(ctx->d_fill.ensure(plan.scratch), "alloc fill scratch");
       FillArgs<T, T> ft{};
@@ -1380,7 +1381,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 10) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 11) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   return CFFT_OK;
 }

@@ -334,12 +334,13 @@ struct FillBackArgs {
 // stencil row, table windows staged in shared memory); ok = false: per-row fill
 struct FillBucketPlan {
   bool ok;
+  bool tc;                 // the tensor-core form (FP32, M = 4, 8 taps)
   int win, n_cells, nb_bits, block_rows, rows_per_wave;
   size_t n_keys_max, smem, scratch;
 };
 template <class T>
 FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, int taps, int n_cls,
-                                  int block_rows);
+                                  int block_rows, bool tc);
 template <class T>
 cudaError_t launch_fill_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& plan, void* scratch,
                                  cudaStream_t s);

@@ -24,6 +24,8 @@
 #include <type_traits>
 
 #include "cfft_common.cuh"
+#include "spectra_tc.cuh"
+#include "tc_sm100.cuh"
 
 namespace cfft {
 
@@ -587,6 +589,202 @@ __global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bucket_adjo
   }
 }
 
+
+// ---- the fill of M = 4 on the tensor cores (FP32-mixed, 8 taps)
+//
+// For the pairs of one stencil cell (table rows i0 .. i0 + 7 of one class) the
+// harmonic sum is a product with the cell's table slice, and the tap sum follows:
+//   D_p[t][ab] = sum_q e^{iq phi_p} T[q][i0+t][ab],   Z_p[ab] = sum_t w_t(x_p) D_p[t][ab].
+// The first is a real GEMM D (pairs x 256) = A (pairs x K) B (K x 256), K = 2 per
+// harmonic (padded to a multiple of 8), n = 2 (16 t + ab) + re/im:
+//   A(p, 2 qi) = Re e^{iq phi},  A(p, 2 qi + 1) = Im e^{iq phi},
+//   B(2 qi, 2 j) = Re T,  B(2 qi + 1, 2 j) = -Im T,  B(2 qi, 2 j + 1) = Im T,  B(2 qi + 1, 2 j + 1) = Re T.
+// A CTA owns one (cell, class, row block): B (TF32 head and tail) stays in shared
+// memory; the pairs go through in M-tiles of 128: the A tile (both halves of the
+// CTA form one row's harmonics each), three TF32 products of width 256 into two
+// tensor-memory accumulators, then each thread reads one MBF-row pair (a = 2h, 2h+1)
+// of its pair's D and applies the Lagrange weights.
+constexpr int kFcTaps = 8;
+constexpr int kFcN = 256;            // 8 taps x 16 MBF pairs x (re, im)
+
+__host__ __device__ constexpr int fc_kpad(int n_harm) { return (2 * n_harm + 7) & ~7; }
+
+size_t fc_smem_bytes(int n_harm) {
+  return (size_t)2 * kFcN * fc_kpad(n_harm) * 4 +      // B head, tail
+         (size_t)2 * 128 * fc_kpad(n_harm) * 4 + 1024; // A head, tail + alignment
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, float> a, BucketArgs b) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int HALF = kFcTaps / 2 - 1;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_fail;
+  const int cell = blockIdx.x, cls = blockIdx.y, blk = blockIdx.z;
+  const size_t key = ((size_t)blk * b.n_ck + cls) * b.n_cells + cell;
+  const unsigned p0 = b.off[key], p1 = b.off[key + 1];
+  if (p0 == p1) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nh = a.n_harm;
+  const int kpad = fc_kpad(nh);
+  const uint32_t sbo = (uint32_t)(kpad / 4) * 128u;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  float* Bh = reinterpret_cast<float*>(base);
+  float* Bl = Bh + (size_t)kFcN * kpad;
+  float* Ah = Bl + (size_t)kFcN * kpad;
+  float* Al = Ah + (size_t)128 * kpad;
+  if (tid == 0) {
+    s_fail = 0;
+    tc::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&taddr_s, 512);
+    tc::tmem_relinquish();
+  }
+  // ---- B: the cell's table rows i0 .. i0 + 7 (parity below row 0, zero past the end;
+  // K rows past 2 n_harm are zero)
+  const int i0 = cell - HALF;
+  {
+    const cpx<float>* tab = a.table + (size_t)cls * 16 * nh * a.n_rho;
+    const int total = (kpad / 2) * kFcTaps * 16;
+    for (int e = tid; e < total; e += blockDim.x) {
+      const int ab = e & 15, t = (e >> 4) & 7, qi = e >> 7;
+      cpx<float> v = mk(0.f, 0.f);
+      int r = i0 + t;
+      if (qi < nh && r < a.n_rho) {
+        const bool neg = r < 0;
+        if (neg) r = -r;
+        v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
+        if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
+      }
+      const int j = 16 * t + ab;
+      const float bv[4] = {v.re, -v.im, v.im, v.re};   // (n = 2j: k even, odd), (n = 2j + 1: k even, odd)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = 2 * j + (u >> 1), k = 2 * qi + (u & 1);
+        float h, l;
+        tf32_split(bv[u], h, l);
+        const uint32_t off = tc::kmajor_offset(n, k, kpad) / 4;
+        Bh[off] = h;
+        Bl[off] = l;
+      }
+    }
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = taddr_s;
+  const uint32_t idesc = tc::idesc_tf32(128, kFcN);
+  const int r = tid & 127, half = tid >> 7;
+  const unsigned nmask = (1u << b.nb_bits) - 1u;
+  uint32_t n_commit = 0;
+  for (unsigned t0 = p0; t0 < p1; t0 += 128) {
+    // ---- A row r: e^{iq phi} of this thread's pair, harmonics of parity `half`
+    {
+      const unsigned pidx = t0 + (unsigned)r;
+      cpx<float> e1 = mk(1.f, 0.f);
+      bool valid = pidx < p1;
+      if (valid) {
+        const unsigned code = b.list[pidx];
+        const int n = (int)(code & nmask);
+        const int m = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
+        const BGeom<float> g = bucket_geom<float, kFcTaps>(a, b, m, n);
+        if (g.i0 != i0) {   // a pair outside its bucket's cell: never expected
+          atomicOr(a.err, 2);
+          valid = false;
+        }
+        e1 = mk(g.ex, g.ey);
+      }
+      const cpx<float> e2 = e1 * e1;
+      cpx<float> ph = mk(valid ? 1.f : 0.f, 0.f);
+      for (int k = 0; k < a.q_max; ++k) ph = ph * conj(e1);   // q = -q_max
+      if (half) ph = ph * e1;                                   // q = -q_max + 1
+      for (int qi = half; 2 * qi < kpad; qi += 2) {
+        const cpx<float> v = qi < nh ? ph : mk(0.f, 0.f);
+        float h0, l0, h1, l1;
+        tf32_split(v.re, h0, l0);
+        tf32_split(v.im, h1, l1);
+        const uint32_t off = tc::kmajor_offset(r, 2 * qi, kpad) / 4;
+        *reinterpret_cast<float2*>(Ah + off) = make_float2(h0, h1);
+        *reinterpret_cast<float2*>(Al + off) = make_float2(l0, l1);
+        ph = ph * e2;
+      }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a_hi = tc::smem_u32(Ah), a_lo = tc::smem_u32(Al);
+      const uint32_t b_hi = tc::smem_u32(Bh), b_lo = tc::smem_u32(Bl);
+      for (int ks = 0; ks < kpad / 8; ++ks) {
+        const uint32_t ko = ks * 256;
+        const uint64_t dah = tc::sdesc(a_hi + ko, 128, sbo), dal = tc::sdesc(a_lo + ko, 128, sbo);
+        const uint64_t dbh = tc::sdesc(b_hi + ko, 128, sbo), dbl = tc::sdesc(b_lo + ko, 128, sbo);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        tc::mma_tf32(tmem + kFcN, dah, dbl, idesc, acc);
+        tc::mma_tf32(tmem + kFcN, dal, dbh, idesc, 1u);
+        tc::mma_tf32(tmem, dah, dbh, idesc, acc);
+      }
+      tc::mma_commit(&mbar);
+    }
+    // ---- epilogue: Z_p[ab] = sum_t w_t D_p[t][ab] for ab of MBF rows a = 2 hq, 2 hq + 1
+    if (lane == 0 && !tc::mbar_wait(&mbar, n_commit & 1u, kTcPolls)) atomicOr(&s_fail, 1);
+    __syncwarp();
+    ++n_commit;
+    tc::fence_after_sync();
+    if (!__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&s_fail), 0)) {
+      const int hq = warp >> 2;
+      const int row = 32 * (warp & 3) + lane;
+      const unsigned pr = t0 + (unsigned)row;
+      float wt[kFcTaps];
+      int mm = 0, nn = 0;
+      const bool ok = pr < p1;
+      if (ok) {
+        const unsigned code = b.list[pr];
+        nn = (int)(code & nmask);
+        mm = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
+        const BGeom<float> g = bucket_geom<float, kFcTaps>(a, b, mm, nn);
+        stencil_weights<float, kFcTaps, false>(g.x, wt, nullptr);
+      } else {
+#pragma unroll
+        for (int t = 0; t < kFcTaps; ++t) wt[t] = 0.f;
+      }
+      float z[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) z[u] = 0.f;
+      const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * hq);
+#pragma unroll
+      for (int t = 0; t < kFcTaps; ++t) {
+        float v[16], w[16];
+        tc::tmem_ld16x2(tl + 32 * t, tl + 32 * t + kFcN, v, w);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) z[u] = fmaf(wt[t], v[u] + w[u], z[u]);
+      }
+      if (ok) {
+#pragma unroll
+        for (int u2 = 0; u2 < 2; ++u2) {
+          cpx<float> zz[4];
+#pragma unroll
+          for (int ib = 0; ib < 4; ++ib) zz[ib] = mk(z[8 * u2 + 2 * ib], z[8 * u2 + 2 * ib + 1]);
+          store_row<float, 4>(a.z + ((size_t)mm * 4 + 2 * hq + u2) * a.ld + (size_t)nn * 4, zz, b.vec_out != 0);
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (s_fail) break;
+  }
+  if (s_fail && tid == 0) atomicOr(a.err, 16);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 // The scratch layout of a plan and the sort state shared by the fill and its adjoint
 template <class T>
 BucketArgs bucket_args(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* scratch) {
@@ -694,6 +892,16 @@ cudaError_t run_adjoint(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad, c
   });
 }
 
+cudaError_t run_fill_tc(const FillArgs<float, float>& a, const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
+  const size_t smem = pl.smem;
+  cudaError_t e = cudaFuncSetAttribute(fill_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return run_waves<float, kFcTaps>(a, pl, bucket_args(a, pl, scratch), s, [&](const BucketArgs& b, dim3 fg) {
+    fill_tc_kernel<<<fg, kBThreads, smem, s>>>(a, b);
+    return cudaSuccess;
+  });
+}
+
 template <class T, int M>
 cudaError_t run_taps(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
   switch (a.taps) {
@@ -722,7 +930,7 @@ cudaError_t adjoint_taps(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad, 
 // window of at least 4 stencil starts fitting in shared memory.
 template <class T>
 FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, int taps, int n_cls,
-                                  int block_rows) {
+                                  int block_rows, bool tc) {
   FillBucketPlan pl{};
   pl.ok = false;
   if (!(n_mbf == 1 || n_mbf == 2 || n_mbf == 4)) return pl;
@@ -731,19 +939,27 @@ FillBucketPlan plan_fill_bucketed(int n_el, int n_mbf, int n_harm, int n_rho, in
   int nb = 1;
   while ((1 << nb) < n_el) ++nb;
   if (nb > 24) return pl;
-  const size_t row_bytes = (size_t)n_harm * n_mbf * n_mbf * sizeof(cpx<T>);
-  // two CTAs per SM when the window stays useful, else one
-  int win = (int)((110 * 1024) / row_bytes) - (taps - 1);
-  if (win < 8) win = (int)((220 * 1024) / row_bytes) - (taps - 1);
-  if (win < 4) return pl;
-  win = std::min(win, 64);
-  pl.win = win;
-  pl.smem = (size_t)(win + taps - 1) * row_bytes;
+  // the tensor-core form: FP32, M = 4, 8 taps, one stencil cell per CTA
+  pl.tc = tc && sizeof(T) == 4 && n_mbf == 4 && taps == 8 && fc_smem_bytes(n_harm) <= 227 * 1024;
+  if (pl.tc) {
+    pl.win = 1;
+    pl.smem = fc_smem_bytes(n_harm);
+  } else {
+    const size_t row_bytes = (size_t)n_harm * n_mbf * n_mbf * sizeof(cpx<T>);
+    // two CTAs per SM when the window stays useful, else one
+    int win = (int)((110 * 1024) / row_bytes) - (taps - 1);
+    if (win < 8) win = (int)((220 * 1024) / row_bytes) - (taps - 1);
+    if (win < 4) return pl;
+    win = std::min(win, 64);
+    pl.win = win;
+    pl.smem = (size_t)(win + taps - 1) * row_bytes;
+  }
   pl.n_cells = n_rho - taps + (taps / 2 - 1) + 1;
   pl.nb_bits = nb;
-  // waves of whole row blocks with at most 2^27 pairs (512 MB of codes)
+  // waves of whole row blocks with at most 2^27 pairs (512 MB of codes); the
+  // tensor-core form takes whole-wave blocks (more pairs per stencil cell)
   const size_t pair_cap = (size_t)1 << 27;
-  int br = block_rows > 0 ? block_rows : 1024;
+  int br = block_rows > 0 ? block_rows : (pl.tc ? n_el : 1024);
   br = std::min(br, n_el);
   br = std::min(br, 1 << std::min(30, 32 - nb));
   br = std::max(1, std::min<int>(br, (int)std::max<size_t>(1, pair_cap / (size_t)n_el)));
@@ -766,6 +982,9 @@ template <class T>
 cudaError_t launch_fill_bucketed(const FillArgs<T, T>& a, const FillBucketPlan& pl, void* scratch,
                                  cudaStream_t s) {
   if (!pl.ok) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (pl.tc) return run_fill_tc(a, pl, scratch, s);
+  }
   switch (a.n_mbf) {
     case 1: return run_taps<T, 1>(a, pl, scratch, s);
     case 2: return run_taps<T, 2>(a, pl, scratch, s);
@@ -786,8 +1005,8 @@ cudaError_t launch_fill_adjoint_bucketed(const FillArgs<T, T>& a, const FillAdjo
   }
 }
 
-template FillBucketPlan plan_fill_bucketed<float>(int, int, int, int, int, int, int);
-template FillBucketPlan plan_fill_bucketed<double>(int, int, int, int, int, int, int);
+template FillBucketPlan plan_fill_bucketed<float>(int, int, int, int, int, int, int, bool);
+template FillBucketPlan plan_fill_bucketed<double>(int, int, int, int, int, int, int, bool);
 template cudaError_t launch_fill_bucketed<float>(const FillArgs<float, float>&, const FillBucketPlan&, void*,
                                                  cudaStream_t);
 template cudaError_t launch_fill_bucketed<double>(const FillArgs<double, double>&, const FillBucketPlan&,

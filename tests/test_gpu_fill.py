@@ -100,3 +100,32 @@ def test_bucketed_strip_m1_against_oracle(torch_cuda):
     err = np.abs(got.reshape(-1) - ref).max() / np.abs(ref).max()
     print("strip M=1 bucketed vs oracle", err)
     assert err < 1e-10
+
+
+@pytest.mark.parametrize("block", [0, 37])
+def test_tensor_core_fill_vs_fp32_pipe(torch_cuda, block):
+    """The fill of M = 4 with 8 taps as one tensor-core contraction per stencil cell
+    (three TF32 products) against the bucketed fill on the FP32 pipe and the oracle's
+    exact entries: 4 rotation classes, pairs near rho = 0 (parity rows), one row block
+    (block 0) and ragged row blocks (37)."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp32", n=1024, n_rho=1024, rho_max=9.0, q_max=4, rotation_classes=4)
+    ctx, _ = cc.gpu_table(wl)
+    pos = np.concatenate([workloads.poisson_disc(300, 4.4, 0.3, seed=61), [[0.01, -0.02], [0.012, -0.019]]])
+    rot = workloads.rotations(len(pos), seed=61)
+    ref = _fill(torch, ctx, pos, rot, 4, torch.complex64, block=block)                 # default: tensor cores
+    ctx.set_option(cfft.OPT_FILL_SIMT, 1)
+    simt = _fill(torch, ctx, pos, rot, 4, torch.complex64, block=block)
+    ctx.set_option(cfft.OPT_FILL_SIMT, 0)
+    scale = np.abs(simt).max()
+    err = np.abs(ref - simt).max() / scale
+    print("block", block, "tensor-core fill vs FP32-pipe fill", err)
+    assert err < 5e-6
+    # a sample of entries against the oracle's exact fill
+    nodes, hq = cc.oracle_harmonics(wl, classes=(0, 1, 2, 3))
+    idx = [(0, 1), (5, 300), (300, 301), (17, 17), (120, 44)]
+    exact = cc.oracle_fill_entries(wl, hq, nodes, pos, rot, idx)
+    for (i, j), blk in zip(idx, exact):
+        got = ref[4 * i:4 * i + 4, 4 * j:4 * j + 4]
+        assert np.abs(got - blk).max() < 1e-5 * scale, (i, j)
