@@ -601,9 +601,11 @@ __global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bucket_adjo
 //   B(2 qi, 2 j) = Re T,  B(2 qi + 1, 2 j) = -Im T,  B(2 qi, 2 j + 1) = Im T,  B(2 qi + 1, 2 j + 1) = Re T.
 // A CTA owns one (cell, class, row block): B (TF32 head and tail) stays in shared
 // memory; the pairs go through in M-tiles of 128: the A tile (both halves of the
-// CTA form one row's harmonics each), three TF32 products of width 256 into two
-// tensor-memory accumulators, then each thread reads one MBF-row pair (a = 2h, 2h+1)
-// of its pair's D and applies the Lagrange weights.
+// CTA form one row's harmonics each), three TF32 products of width 256 into one of
+// two tensor-memory accumulators (27 accumulation steps per tile: the truncating
+// accumulation stays near 1e-7), and while the tensor core runs tile j each thread
+// reads one MBF-row pair (a = 2h, 2h+1) of its pair's D of tile j-1 and applies the
+// Lagrange weights.
 constexpr int kFcTaps = 8;
 constexpr int kFcN = 256;            // 8 taps x 16 MBF pairs x (re, im)
 
@@ -681,6 +683,47 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
   const int r = tid & 127, half = tid >> 7;
   const unsigned nmask = (1u << b.nb_bits) - 1u;
   uint32_t n_commit = 0;
+  // Z of the tile starting at pair t0 from accumulator set `set`
+  auto epilogue = [&](unsigned t0, uint32_t set) {
+    const int hq = warp >> 2;
+    const int row = 32 * (warp & 3) + lane;
+    const unsigned pr = t0 + (unsigned)row;
+    float wt[kFcTaps];
+    int mm = 0, nn = 0;
+    const bool ok = pr < p1;
+    if (ok) {
+      const unsigned code = b.list[pr];
+      nn = (int)(code & nmask);
+      mm = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
+      const BGeom<float> g = bucket_geom<float, kFcTaps>(a, b, mm, nn);
+      stencil_weights<float, kFcTaps, false>(g.x, wt, nullptr);
+    } else {
+#pragma unroll
+      for (int t = 0; t < kFcTaps; ++t) wt[t] = 0.f;
+    }
+    float z[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) z[u] = 0.f;
+    const uint32_t tl = tmem + set * kFcN + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * hq);
+#pragma unroll
+    for (int t = 0; t < kFcTaps; t += 2) {
+      float v[16], w[16];
+      tc::tmem_ld16x2(tl + 32 * t, tl + 32 * (t + 1), v, w);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) z[u] = fmaf(wt[t + 1], w[u], fmaf(wt[t], v[u], z[u]));
+    }
+    if (ok) {
+#pragma unroll
+      for (int u2 = 0; u2 < 2; ++u2) {
+        cpx<float> zz[4];
+#pragma unroll
+        for (int ib = 0; ib < 4; ++ib) zz[ib] = mk(z[8 * u2 + 2 * ib], z[8 * u2 + 2 * ib + 1]);
+        store_row<float, 4>(a.z + ((size_t)mm * 4 + 2 * hq + u2) * a.ld + (size_t)nn * 4, zz, b.vec_out != 0);
+      }
+    }
+  };
+  unsigned prev_t0 = 0;
+  bool have_prev = false;
   for (unsigned t0 = p0; t0 < p1; t0 += 128) {
     // ---- A row r: e^{iq phi} of this thread's pair, harmonics of parity `half`
     {
@@ -716,67 +759,38 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {
+    const uint32_t set = n_commit & 1u;
+    if (tid == 0 && !s_fail) {
       tc::fence_after_sync();
       const uint32_t a_hi = tc::smem_u32(Ah), a_lo = tc::smem_u32(Al);
       const uint32_t b_hi = tc::smem_u32(Bh), b_lo = tc::smem_u32(Bl);
+      const uint32_t d = tmem + set * kFcN;
       for (int ks = 0; ks < kpad / 8; ++ks) {
         const uint32_t ko = ks * 256;
         const uint64_t dah = tc::sdesc(a_hi + ko, 128, sbo), dal = tc::sdesc(a_lo + ko, 128, sbo);
         const uint64_t dbh = tc::sdesc(b_hi + ko, 128, sbo), dbl = tc::sdesc(b_lo + ko, 128, sbo);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
-        tc::mma_tf32(tmem + kFcN, dah, dbl, idesc, acc);
-        tc::mma_tf32(tmem + kFcN, dal, dbh, idesc, 1u);
-        tc::mma_tf32(tmem, dah, dbh, idesc, acc);
+        tc::mma_tf32(d, dah, dbl, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(d, dal, dbh, idesc, 1u);
+        tc::mma_tf32(d, dah, dbh, idesc, 1u);
       }
       tc::mma_commit(&mbar);
     }
-    // ---- epilogue: Z_p[ab] = sum_t w_t D_p[t][ab] for ab of MBF rows a = 2 hq, 2 hq + 1
-    if (lane == 0 && !tc::mbar_wait(&mbar, n_commit & 1u, kTcPolls)) atomicOr(&s_fail, 1);
+    // the previous tile's epilogue while the tensor core runs this one
+    if (have_prev && !__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&s_fail), 0))
+      epilogue(prev_t0, set ^ 1u);
+    // this tile's products done: the A buffer is free, its accumulator readable
+    if (lane == 0 && !s_fail && !tc::mbar_wait(&mbar, n_commit & 1u, kTcPolls)) atomicOr(&s_fail, 1);
     __syncwarp();
     ++n_commit;
     tc::fence_after_sync();
-    if (!__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&s_fail), 0)) {
-      const int hq = warp >> 2;
-      const int row = 32 * (warp & 3) + lane;
-      const unsigned pr = t0 + (unsigned)row;
-      float wt[kFcTaps];
-      int mm = 0, nn = 0;
-      const bool ok = pr < p1;
-      if (ok) {
-        const unsigned code = b.list[pr];
-        nn = (int)(code & nmask);
-        mm = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
-        const BGeom<float> g = bucket_geom<float, kFcTaps>(a, b, mm, nn);
-        stencil_weights<float, kFcTaps, false>(g.x, wt, nullptr);
-      } else {
-#pragma unroll
-        for (int t = 0; t < kFcTaps; ++t) wt[t] = 0.f;
-      }
-      float z[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) z[u] = 0.f;
-      const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * hq);
-#pragma unroll
-      for (int t = 0; t < kFcTaps; ++t) {
-        float v[16], w[16];
-        tc::tmem_ld16x2(tl + 32 * t, tl + 32 * t + kFcN, v, w);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) z[u] = fmaf(wt[t], v[u] + w[u], z[u]);
-      }
-      if (ok) {
-#pragma unroll
-        for (int u2 = 0; u2 < 2; ++u2) {
-          cpx<float> zz[4];
-#pragma unroll
-          for (int ib = 0; ib < 4; ++ib) zz[ib] = mk(z[8 * u2 + 2 * ib], z[8 * u2 + 2 * ib + 1]);
-          store_row<float, 4>(a.z + ((size_t)mm * 4 + 2 * hq + u2) * a.ld + (size_t)nn * 4, zz, b.vec_out != 0);
-        }
-      }
-    }
     tc::fence_before_sync();
     __syncthreads();
     if (s_fail) break;
+    prev_t0 = t0;
+    have_prev = true;
+  }
+  if (have_prev && !s_fail) {
+    epilogue(prev_t0, (n_commit - 1) & 1u);
   }
   if (s_fail && tid == 0) atomicOr(a.err, 16);
   tc::fence_before_sync();
