@@ -69,12 +69,11 @@ struct BGeom {
   bool bad;     // rho beyond the table
 };
 
-// stencil of pair (m, n), FP32-mixed: float-float geometry
-template <class T, int TAPS>
-__device__ __forceinline__ typename std::enable_if<sizeof(T) == 4, BGeom<T>>::type
-bucket_geom(const FillArgs<T, T>& a, const BucketArgs& b, int m, int n) {
+// stencil of pair (m, n), FP32-mixed: float-float geometry from the split positions
+template <int TAPS>
+__device__ __forceinline__ BGeom<float> bucket_geom_ps(const FillArgs<float, float>& a, const BucketArgs& b,
+                                                       float4 pm, float4 pn) {
   constexpr int HALF = TAPS / 2 - 1;
-  const float4 pm = b.ps[m], pn = b.ps[n];
   float dxh, dxl, dyh, dyl;
   df_sub(pm.x, pm.y, pn.x, pn.y, dxh, dxl);
   df_sub(pm.z, pm.w, pn.z, pn.w, dyh, dyl);
@@ -97,7 +96,7 @@ bucket_geom(const FillArgs<T, T>& a, const BucketArgs& b, int m, int n) {
   float f = __fadd_rn(__fsub_rn(p, fl), pe);
   if (f < 0.f) { f = __fadd_rn(f, 1.f); fl = __fsub_rn(fl, 1.f); }
   if (f >= 1.f) { f = __fsub_rn(f, 1.f); fl = __fadd_rn(fl, 1.f); }
-  BGeom<T> g;
+  BGeom<float> g;
   const float top = (float)(a.n_rho - 1);
   g.bad = fl > top || (fl == top && f > 1e-6f) || !(r == r);
   const int fi = (int)fl;
@@ -114,6 +113,12 @@ bucket_geom(const FillArgs<T, T>& a, const BucketArgs& b, int m, int n) {
     g.ey = 0.f;
   }
   return g;
+}
+
+template <class T, int TAPS>
+__device__ __forceinline__ typename std::enable_if<sizeof(T) == 4, BGeom<T>>::type
+bucket_geom(const FillArgs<T, T>& a, const BucketArgs& b, int m, int n) {
+  return bucket_geom_ps<TAPS>(a, b, b.ps[m], b.ps[n]);
 }
 
 // stencil of pair (m, n), FP64 mode: float64 geometry
@@ -649,29 +654,37 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
   // K rows past 2 n_harm are zero)
   const int i0 = cell - HALF;
   {
+    // one 16-byte group per (column n, harmonics qi, qi + 1): consecutive threads take
+    // consecutive n, so the eight rows of a core matrix are written in one wavefront
     const cpx<float>* tab = a.table + (size_t)cls * 16 * nh * a.n_rho;
-    const int total = (kpad / 2) * kFcTaps * 16;
+    const int total = kFcN * (kpad / 4);
     for (int e = tid; e < total; e += blockDim.x) {
-      const int ab = e & 15, t = (e >> 4) & 7, qi = e >> 7;
-      cpx<float> v = mk(0.f, 0.f);
+      const int n = e & (kFcN - 1), k4 = e / kFcN;
+      const int j = n >> 1, c = n & 1, t = j >> 4, ab = j & 15;
       int r = i0 + t;
-      if (qi < nh && r < a.n_rho) {
-        const bool neg = r < 0;
-        if (neg) r = -r;
-        v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
-        if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
-      }
-      const int j = 16 * t + ab;
-      const float bv[4] = {v.re, -v.im, v.im, v.re};   // (n = 2j: k even, odd), (n = 2j + 1: k even, odd)
+      const bool neg = r < 0;
+      if (neg) r = -r;
+      float f[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int n = 2 * j + (u >> 1), k = 2 * qi + (u & 1);
-        float h, l;
-        tf32_split(bv[u], h, l);
-        const uint32_t off = tc::kmajor_offset(n, k, kpad) / 4;
-        Bh[off] = h;
-        Bl[off] = l;
+      for (int u = 0; u < 2; ++u) {
+        const int qi = 2 * k4 + u;
+        cpx<float> v = mk(0.f, 0.f);
+        if (qi < nh && r < a.n_rho) {
+          v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
+          if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
+        }
+        // column 2j (real part of D): (Re T, -Im T); column 2j + 1: (Im T, Re T)
+        f[2 * u] = c ? v.im : v.re;
+        f[2 * u + 1] = c ? v.re : -v.im;
       }
+      float4 h, l;
+      tf32_split(f[0], h.x, l.x);
+      tf32_split(f[1], h.y, l.y);
+      tf32_split(f[2], h.z, l.z);
+      tf32_split(f[3], h.w, l.w);
+      const uint32_t off = tc::kmajor_offset(n, 4 * k4, kpad) / 4;
+      *reinterpret_cast<float4*>(Bh + off) = h;
+      *reinterpret_cast<float4*>(Bl + off) = l;
     }
   }
   tc::fence_proxy_async();
@@ -683,28 +696,15 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
   const int r = tid & 127, half = tid >> 7;
   const unsigned nmask = (1u << b.nb_bits) - 1u;
   uint32_t n_commit = 0;
-  // Z of the tile starting at pair t0 from accumulator set `set`
-  auto epilogue = [&](unsigned t0, uint32_t set) {
-    const int hq = warp >> 2;
-    const int row = 32 * (warp & 3) + lane;
-    const unsigned pr = t0 + (unsigned)row;
+  // Z of a tile from accumulator set `set`: this thread's pair (row r; MBF rows
+  // a = 2 half, 2 half + 1) with stencil coordinate x, if ok
+  auto epilogue = [&](uint32_t set, bool ok, int mm, int nn, float x) {
     float wt[kFcTaps];
-    int mm = 0, nn = 0;
-    const bool ok = pr < p1;
-    if (ok) {
-      const unsigned code = b.list[pr];
-      nn = (int)(code & nmask);
-      mm = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
-      const BGeom<float> g = bucket_geom<float, kFcTaps>(a, b, mm, nn);
-      stencil_weights<float, kFcTaps, false>(g.x, wt, nullptr);
-    } else {
-#pragma unroll
-      for (int t = 0; t < kFcTaps; ++t) wt[t] = 0.f;
-    }
+    stencil_weights<float, kFcTaps, false>(x, wt, nullptr);
     float z[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) z[u] = 0.f;
-    const uint32_t tl = tmem + set * kFcN + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * hq);
+    const uint32_t tl = tmem + set * kFcN + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * half);
 #pragma unroll
     for (int t = 0; t < kFcTaps; t += 2) {
       float v[16], w[16];
@@ -718,42 +718,65 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
         cpx<float> zz[4];
 #pragma unroll
         for (int ib = 0; ib < 4; ++ib) zz[ib] = mk(z[8 * u2 + 2 * ib], z[8 * u2 + 2 * ib + 1]);
-        store_row<float, 4>(a.z + ((size_t)mm * 4 + 2 * hq + u2) * a.ld + (size_t)nn * 4, zz, b.vec_out != 0);
+        store_row<float, 4>(a.z + ((size_t)mm * 4 + 2 * half + u2) * a.ld + (size_t)nn * 4, zz, b.vec_out != 0);
       }
     }
   };
-  unsigned prev_t0 = 0;
-  bool have_prev = false;
+  // this thread's pair of the next tile: code and split positions, loaded ahead
+  auto fetch = [&](unsigned t0, bool& ok, int& m, int& n, float4& pm, float4& pn) {
+    const unsigned pidx = t0 + (unsigned)r;
+    ok = pidx < p1;
+    m = n = 0;
+    if (ok) {
+      const unsigned code = b.list[pidx];
+      n = (int)(code & nmask);
+      m = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
+      pm = b.ps[m];
+      pn = b.ps[n];
+    }
+  };
+  bool nx_ok;
+  int nx_m, nx_n;
+  float4 nx_pm = make_float4(0.f, 0.f, 0.f, 0.f), nx_pn = nx_pm;
+  fetch(p0, nx_ok, nx_m, nx_n, nx_pm, nx_pn);
+  bool pv_ok = false, have_prev = false;
+  int pv_m = 0, pv_n = 0;
+  float pv_x = 0.f;
   for (unsigned t0 = p0; t0 < p1; t0 += 128) {
-    // ---- A row r: e^{iq phi} of this thread's pair, harmonics of parity `half`
+    const bool ok0 = nx_ok;
+    const int m0 = nx_m, n0 = nx_n;
+    float x0 = 0.f;
+    bool ok = ok0;
+    // ---- A row r: e^{iq phi} of this thread's pair; harmonic pairs (qi, qi + 1) with
+    // qi = 4 u + 2 half, one 16-byte group each
     {
-      const unsigned pidx = t0 + (unsigned)r;
       cpx<float> e1 = mk(1.f, 0.f);
-      bool valid = pidx < p1;
-      if (valid) {
-        const unsigned code = b.list[pidx];
-        const int n = (int)(code & nmask);
-        const int m = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
-        const BGeom<float> g = bucket_geom<float, kFcTaps>(a, b, m, n);
+      if (ok) {
+        const BGeom<float> g = bucket_geom_ps<kFcTaps>(a, b, nx_pm, nx_pn);
         if (g.i0 != i0) {   // a pair outside its bucket's cell: never expected
           atomicOr(a.err, 2);
-          valid = false;
+          ok = false;
         }
         e1 = mk(g.ex, g.ey);
+        x0 = g.x;
       }
-      const cpx<float> e2 = e1 * e1;
-      cpx<float> ph = mk(valid ? 1.f : 0.f, 0.f);
+      const cpx<float> e2 = e1 * e1, e4 = e2 * e2;
+      cpx<float> ph = mk(ok ? 1.f : 0.f, 0.f);
       for (int k = 0; k < a.q_max; ++k) ph = ph * conj(e1);   // q = -q_max
-      if (half) ph = ph * e1;                                   // q = -q_max + 1
-      for (int qi = half; 2 * qi < kpad; qi += 2) {
-        const cpx<float> v = qi < nh ? ph : mk(0.f, 0.f);
-        float h0, l0, h1, l1;
-        tf32_split(v.re, h0, l0);
-        tf32_split(v.im, h1, l1);
+      if (half) ph = ph * e2;                                   // q = -q_max + 2
+      for (int qi = 2 * half; 2 * qi < kpad; qi += 4) {
+        const cpx<float> v0 = qi < nh ? ph : mk(0.f, 0.f);
+        const cpx<float> p1v = ph * e1;
+        const cpx<float> v1 = qi + 1 < nh ? p1v : mk(0.f, 0.f);
+        float4 h, l;
+        tf32_split(v0.re, h.x, l.x);
+        tf32_split(v0.im, h.y, l.y);
+        tf32_split(v1.re, h.z, l.z);
+        tf32_split(v1.im, h.w, l.w);
         const uint32_t off = tc::kmajor_offset(r, 2 * qi, kpad) / 4;
-        *reinterpret_cast<float2*>(Ah + off) = make_float2(h0, h1);
-        *reinterpret_cast<float2*>(Al + off) = make_float2(l0, l1);
-        ph = ph * e2;
+        *reinterpret_cast<float4*>(Ah + off) = h;
+        *reinterpret_cast<float4*>(Al + off) = l;
+        ph = ph * e4;
       }
     }
     tc::fence_proxy_async();
@@ -775,9 +798,10 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
       }
       tc::mma_commit(&mbar);
     }
-    // the previous tile's epilogue while the tensor core runs this one
+    // while the tensor core runs this tile: the next tile's pairs, the previous tile's Z
+    if (t0 + 128 < p1) fetch(t0 + 128, nx_ok, nx_m, nx_n, nx_pm, nx_pn);
     if (have_prev && !__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&s_fail), 0))
-      epilogue(prev_t0, set ^ 1u);
+      epilogue(set ^ 1u, pv_ok, pv_m, pv_n, pv_x);
     // this tile's products done: the A buffer is free, its accumulator readable
     if (lane == 0 && !s_fail && !tc::mbar_wait(&mbar, n_commit & 1u, kTcPolls)) atomicOr(&s_fail, 1);
     __syncwarp();
@@ -786,12 +810,13 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
     tc::fence_before_sync();
     __syncthreads();
     if (s_fail) break;
-    prev_t0 = t0;
+    pv_ok = ok;
+    pv_m = m0;
+    pv_n = n0;
+    pv_x = x0;
     have_prev = true;
   }
-  if (have_prev && !s_fail) {
-    epilogue(prev_t0, (n_commit - 1) & 1u);
-  }
+  if (have_prev && !s_fail) epilogue((n_commit - 1) & 1u, pv_ok, pv_m, pv_n, pv_x);
   if (s_fail && tid == 0) atomicOr(a.err, 16);
   tc::fence_before_sync();
   __syncthreads();
