@@ -424,8 +424,9 @@ def stage_flops(inf, wl):
     m = wl.element.n_mbf
     L = inf["sub_len"]
     taps = inf["bp_taps"]
-    if inf.get("bp_form", 0) in (1, 2):
+    if inf.get("bp_form", 0) in (1, 2, 3):
         # interpolation-matrix products (complex MACs) + node stencils added into the matrices
+        # (form 3 runs the products on the tensor cores: the same work, counted once)
         bp = 8.0 * inf["work_bp_macs"] + (6.0 * taps + 16.0) * inf["work_bp_stencils"]
     else:
         bp = inf["work_bp_nodes"] * (4 * taps + 8)
@@ -465,7 +466,10 @@ def roofline(infos, wl, peaks, clk):
             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)"
                          % peaks.get("sm_max_mhz", 2070.0),
             "stages": stages, "algorithmic_flops_per_launch": fl[dominant],
-            "spectra_on_tensor_cores": bool(inf.get("spectra_tc", 0)), "bp_form": inf.get("bp_form", 0)}
+            "spectra_on_tensor_cores": bool(inf.get("spectra_tc", 0)), "bp_form": inf.get("bp_form", 0),
+            "note": "algorithmic FP32 flops per stage (GEMM parts run as three TF32 products on the "
+                    "tensor cores in the integrand and back-projection, counted once) over the FP32 "
+                    "FMA peak"}
 
 
 def run_cfft(args):
