@@ -654,25 +654,40 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
   // K rows past 2 n_harm are zero)
   const int i0 = cell - HALF;
   {
+    // the cell's table rows, staged as [ab][qi][t] in the (still unused) A buffer with
+    // coalesced loads (8 consecutive rows per (ab, qi)); parity below row 0, zero past the end
+    cpx<float>* stg = reinterpret_cast<cpx<float>*>(Ah);
+    const cpx<float>* tab = a.table + (size_t)cls * 16 * nh * a.n_rho;
+    const int n_st = 16 * nh * kFcTaps;
+    const bool inside = i0 >= 0 && i0 + kFcTaps <= a.n_rho;
+#pragma unroll 4
+    for (int e = tid; e < n_st; e += blockDim.x) {
+      const int t = e & 7, rest = e >> 3;
+      const int qi = rest % nh, ab = rest / nh;
+      int r = i0 + t;
+      cpx<float> v = mk(0.f, 0.f);
+      if (inside) {
+        v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
+      } else if (r < a.n_rho) {
+        const bool neg = r < 0;
+        if (neg) r = -r;
+        v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
+        if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
+      }
+      stg[e] = v;
+    }
+    __syncthreads();
     // one 16-byte group per (column n, harmonics qi, qi + 1): consecutive threads take
     // consecutive n, so the eight rows of a core matrix are written in one wavefront
-    const cpx<float>* tab = a.table + (size_t)cls * 16 * nh * a.n_rho;
     const int total = kFcN * (kpad / 4);
     for (int e = tid; e < total; e += blockDim.x) {
       const int n = e & (kFcN - 1), k4 = e / kFcN;
       const int j = n >> 1, c = n & 1, t = j >> 4, ab = j & 15;
-      int r = i0 + t;
-      const bool neg = r < 0;
-      if (neg) r = -r;
       float f[4];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int qi = 2 * k4 + u;
-        cpx<float> v = mk(0.f, 0.f);
-        if (qi < nh && r < a.n_rho) {
-          v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
-          if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
-        }
+        const cpx<float> v = qi < nh ? stg[((size_t)ab * nh + qi) * kFcTaps + t] : mk(0.f, 0.f);
         // column 2j (real part of D): (Re T, -Im T); column 2j + 1: (Im T, Re T)
         f[2 * u] = c ? v.im : v.re;
         f[2 * u + 1] = c ? v.re : -v.im;
