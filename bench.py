@@ -309,12 +309,19 @@ def bench_fill(torch, cfft, args, dev):
                                                                    a * m, wl.rho_max, wl.n_rho),
            "table_ms": 1e3 * tab_s, "table_info": {k: info[k] for k in
                                                    ("taylor_order", "grid_half", "sigma", "fill_taps")}}
-    # fill roofline: FP32 pipe (interpolation + harmonic sum) vs HBM write of the matrix
+    # fill roofline: algorithmic FP32 work (interpolation + harmonic sum) vs the FP32 pipe,
+    # and, in the tensor-core form, the TF32 products it executes (three per K step of the
+    # per-cell GEMM: K = 2 n_harm padded to 8, N = 256, 128-pair tiles) vs the TF32 peak
     taps = info["fill_taps"]
     nh = 2 * wl.q_max + 1
     flops_per_pair = m * m * nh * (4 * taps + 8)
     sec = sum(ms) / steps / 1e3
-    res["alu_tflops"] = flops_per_pair * float(a) ** 2 / sec / 1e12
+    form = ctx.info()["fill_form"]
+    res["form"] = {1: "per-row", 2: "bucketed, FP32 pipe", 3: "tensor cores"}.get(form, "none")
+    res["algorithmic_tflops"] = flops_per_pair * float(a) ** 2 / sec / 1e12
+    if form == 3:
+        kpad = (2 * nh + 7) // 8 * 8
+        res["tensor_tflops_executed"] = 3 * 2.0 * kpad * 256 * float(a) ** 2 / sec / 1e12
     res["hbm_gbs_write"] = entries * 8 / sec / 1e9
     del z
     torch.cuda.empty_cache()
@@ -505,7 +512,13 @@ def run_cfft(args):
             "roofline": roofline(infos, wl, peaks, clk), "clocks": clk,
             "gpu_launches": launches, "e2e": e2e, "info": infos[-1]}
     if fill is not None:
-        fill["alu_frac"] = fill["alu_tflops"] / fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        fill["algorithmic_frac_of_fp32_peak"] = (fill["algorithmic_tflops"] /
+                                                 fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0)))
+        if "tensor_tflops_executed" in fill:
+            # TF32 dense peak from the measured bf16 peak and the nominal TF32 / bf16 ratio (1.1 / 2.25)
+            tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+            fill["tensor_peak_tflops_tf32"] = tf32_peak
+            fill["tensor_frac"] = fill["tensor_tflops_executed"] / tf32_peak
         line["fill"] = fill
     if batch is not None:
         line["batch"] = batch

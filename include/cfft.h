@@ -320,7 +320,9 @@ cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_
  * tensor cores; for the matrix forms work_bp_macs counts the complex
  * multiply-adds of the interpolation-matrix products (rows x grid columns x
  * series, every harmonic) and work_bp_stencils the node stencils added into
- * the matrices (rows x angular nodes x matrices). */
+ * the matrices (rows x angular nodes x matrices).  fill_form: the form of the
+ * last cfft_fill_reduced_matrix: 1 per-row, 2 bucketed on the FP32 pipe, 3 on
+ * the tensor cores (0: no fill yet). */
 typedef struct {
   int taylor_order, n_alpha, sigma, fft_len, sub_len, grid_half, bp_taps, fill_taps;
   int series, classes, n_pairs, n_harm;
@@ -329,6 +331,7 @@ typedef struct {
   double work_points, work_subffts, work_bp_nodes;
   int spectra_tc, bp_form;
   double work_bp_macs, work_bp_stencils;
+  int fill_form;
 } cfft_info;
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
 

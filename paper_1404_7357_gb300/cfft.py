@@ -61,7 +61,8 @@ class Info(ctypes.Structure):
                [(n, ctypes.c_int) for n in ("launches", "n_basis")] + \
                [(n, ctypes.c_double) for n in ("work_points", "work_subffts", "work_bp_nodes")] + \
                [(n, ctypes.c_int) for n in ("spectra_tc", "bp_form")] + \
-               [(n, ctypes.c_double) for n in ("work_bp_macs", "work_bp_stencils")]
+               [(n, ctypes.c_double) for n in ("work_bp_macs", "work_bp_stencils")] + \
+               [("fill_form", ctypes.c_int)]
 
 
 def _load():

@@ -569,6 +569,7 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
                                  (int)ctx->opt[CFFT_OPT_FILL_BLOCK], !(ctx->opt[CFFT_OPT_FILL_SIMT] > 0));
   if (plan.ok) CFFT_CUDA(ctx->d_fill.ensure(plan.scratch), "alloc fill scratch");
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
+  ctx->info.fill_form = plan.ok ? (plan.tc ? 3 : 2) : 1;
   cudaError_t le = launch_fill<T, TO>(fa, plan, ctx->d_fill.p, ctx->stream);
   if (le != cudaSuccess) return cuda_fail(ctx, le, "fill kernel");
   int flag = 0;
