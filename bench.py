@@ -7,9 +7,10 @@ M = 4 MBFs, all 16 MBF pairs, eps_r 4.4, h 0.03 lambda0, contour N = 16384,
 cfft_tabulate_reactions call (contour + Green's function, MBF spectra and
 harmonics, Taylor x pruned FFTs, back-projection) on inputs resident in HBM;
 the L2 cache is flushed between timed steps.  Beside it, the same metric end
-to end through the host-buffer C-ABI path, the reduced-matrix fill of the
-10,000-element irregular array (entries/s), the roofline of the dominant
-kernel, and the FP64 oracle timed on the host cores.
+to end through the host-buffer C-ABI path, the plain FP64 GPU form of the same
+tabulation, the reduced-matrix fill of the 10,000-element irregular array
+(entries/s), the batched sweep, the differentiable fill, the roofline of the
+dominant kernel, and the FP64 oracle timed on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cfft|reference]
 Under torchrun every rank runs its own replica of the workload (the path
@@ -243,6 +244,34 @@ def bench_tabulation(torch, cfft, args, dev):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     return wl, ctx, step_ms, infos, clk
+
+
+def bench_fp64(torch, cfft, args, dev):
+    """The plain FP64 GPU form of the same tabulation (FP64 arithmetic throughout, zero
+    padding 8, 16-tap stencils, Taylor order for 1e-13), a few steps with the L2 flushed."""
+    wl = table_workload()
+    ctx = cfft.Context(dev)
+    set_problem(ctx, wl)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP64, 1)   # warm-up
+    stream = torch.cuda.current_stream(dev)
+    steps = 2
+    ms = []
+    for _ in range(steps):
+        flush_l2(torch, flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP64, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    inf = ctx.info()
+    return {"metric": "C-FFT table samples/s (plain FP64 GPU form)",
+            "value": table_samples(wl) * steps / (sum(ms) / 1e3), "unit": "samples/s",
+            "ms_per_step": sum(ms) / steps, "steps": steps,
+            "stages_ms": {k: inf["ms_" + k] for k in ("contour", "integrand", "fft", "backproject")},
+            "info": {k: inf[k] for k in ("taylor_order", "sigma", "fft_len", "sub_len", "bp_taps",
+                                         "bp_form", "spectra_tc")}}
 
 
 def bench_e2e(torch, cfft, args, dev, wl):
@@ -501,6 +530,7 @@ def run_cfft(args):
     samples = table_samples(wl)
     value = samples * args.steps * world / total_s
     e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
+    fp64 = None if args.skip_fp64 else bench_fp64(torch, cfft, args, dev)
     fill = None if args.skip_fill else bench_fill(torch, cfft, args, dev)
     batch = None if args.skip_batch else bench_batch(torch, cfft, args, dev)
     grad = None if args.skip_grad else bench_grad(torch, cfft, args, dev)
@@ -511,6 +541,8 @@ def run_cfft(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_desc(wl),
             "roofline": roofline(infos, wl, peaks, clk), "clocks": clk,
             "gpu_launches": launches, "e2e": e2e, "info": infos[-1]}
+    if fp64 is not None:
+        line["fp64_gpu"] = fp64
     if fill is not None:
         fill["algorithmic_frac_of_fp32_peak"] = (fill["algorithmic_tflops"] /
                                                  fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0)))
@@ -560,6 +592,7 @@ def main():
     ap.add_argument("--only-fill", action="store_true", help="time the fill alone")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 GPU form")
     ap.add_argument("--table-n", type=int, help="contour samples (small profiling case)")
     ap.add_argument("--table-nrho", type=int, help="rho points (small profiling case)")
     ap.add_argument("--table-rho", type=float, help="rho_max (small profiling case)")
