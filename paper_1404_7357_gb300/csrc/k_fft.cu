@@ -362,11 +362,11 @@ __device__ __forceinline__ void last_pass_fused(const cpx<T>* buf, const cpx<T>*
 }
 
 // the last pass when only the outputs s = 0 and s = 15 of each butterfly are needed
-// (t_hi < L/16 and t_lo > -L/16: the needed t = i and t = i - L/16 (mod L)): with
-// v_r the twiddled inputs and r = 4 r1 + r0,
-//   X_0  = sum_r0 a_r0,                 a_r0 = sum_r1 v_(4 r1 + r0),
-//   X_15 = sum_r0 W16^(-r0) b_r0,       b_r0 = sum_r1 i^r1 v_(4 r1 + r0)
-// (W16^(15 r) = W16^(-r), W16^(-4 r1) = i^r1)
+// (t_hi < L/16 and t_lo > -L/16: the needed t = i and t = i - L/16 (mod L)).  With the
+// butterfly's inputs v_r and twiddles W_L^(r i), both outputs are polynomials in one
+// root of unity, evaluated by Horner's rule:
+//   X_0  = sum_r v_r z^r,   X_15 = sum_r v_r (z W16^-1)^r,   z = W_L^i
+// (W16^(15 r) = W16^(-r)), so no per-input twiddle is formed
 template <class T, int LOG2L, int NT, class Use>
 __device__ __forceinline__ void last_pass_pruned(const cpx<T>* buf, const cpx<T>* thi, const cpx<T>* tlo,
                                                  int t_lo, int t_hi, Use use) {
@@ -376,6 +376,7 @@ __device__ __forceinline__ void last_pass_pruned(const cpx<T>* buf, const cpx<T>
   constexpr int BPT = NB / NT;
   static_assert(BPT >= 1 && NB % NT == 0 && NB % 16 == 0, "butterflies per thread");
   const int tid = threadIdx.x;
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
 #pragma unroll 1
   for (int b = 0; b < BPT; ++b) {
     const int i = tid + NT * b;
@@ -385,21 +386,14 @@ __device__ __forceinline__ void last_pass_pruned(const cpx<T>* buf, const cpx<T>
       cpx<T> v[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = buf[pi + r * (NB + NB / 16)];
-      if (i != 0) twiddle_inputs<T, 16>(v, i, thi, tlo);
-      cpx<T> x0 = mk((T)0, (T)0), x15;
-      cpx<T> bq[4];
+      const cpx<T> z = tw2(thi, tlo, i);
+      const cpx<T> w = z * mk(c1, s1);   // z W16^-1
+      cpx<T> x0 = v[15], x15 = v[15];
 #pragma unroll
-      for (int r0 = 0; r0 < 4; ++r0) {
-        const cpx<T> p0 = v[r0], p1 = v[4 + r0], p2 = v[8 + r0], p3 = v[12 + r0];
-        x0 = x0 + ((p0 + p2) + (p1 + p3));
-        // p0 + i p1 - p2 - i p3
-        const cpx<T> d02 = p0 - p2, d13 = p1 - p3;
-        bq[r0] = mk(d02.re - d13.im, d02.im + d13.re);
+      for (int r = 14; r >= 0; --r) {
+        x0 = x0 * z + v[r];
+        x15 = x15 * w + v[r];
       }
-      const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
-      const T h = (T)0.70710678118654752440;
-      // W16^(-1) = (c1, s1), W16^(-2) = (h, h), W16^(-3) = (s1, c1)
-      x15 = bq[0] + bq[1] * mk(c1, s1) + bq[2] * mk(h, h) + bq[3] * mk(s1, c1);
       if (need0) use(i, x0);
       if (need15) use(i + 15 * P, x15);
     }
