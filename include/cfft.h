@@ -95,9 +95,12 @@ typedef enum {
  *   BP_SIMT      a value > 0 runs the FP32-mixed back-projection's matrix
  *                products on the FP32 pipe (paired-harmonic form) instead of
  *                the tensor cores (same quadrature; three TF32 products)
- *   FILL_SIMT    a value > 0 runs the FP32 fill of M = 4 with 8 taps on the
- *                FP32 pipe (bucketed form) instead of the tensor cores (the
- *                interpolation as one contraction per stencil cell)       */
+ *   FILL_SIMT    a value > 0 runs the FP32 fill of M = 4 with 8 taps and its
+ *                adjoint on the FP32 pipe (bucketed form) instead of the
+ *                tensor cores (the interpolation as one contraction per
+ *                stencil cell); 0 (default): the fill on the tensor cores,
+ *                the adjoint there from 512 element pairs per stencil cell;
+ *                a value < 0: both on the tensor cores whenever they apply */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,

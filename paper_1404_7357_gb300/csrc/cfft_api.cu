@@ -620,8 +620,15 @@ cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const
     // the adjoint over the fill's buckets (same plan and scratch as the fill)
     FillBucketPlan plan{};
     if (ctx->opt[CFFT_OPT_FILL_BLOCK] >= 0)
+    {
+      // the tensor-core adjoint stages each stencil cell's table slice three times (position
+      // and two substrate passes): it pays from about 512 pairs per cell (class) upwards
+      const double per_cell = (double)n_el * n_el / ((double)fa.n_cls * fa.n_rho);
+      const double sel = ctx->opt[CFFT_OPT_FILL_SIMT];
+      const bool tc = sel < 0 || (sel == 0 && per_cell >= 512.0);
       plan = plan_fill_bucketed<T>(n_el, fa.n_mbf, fa.n_harm, fa.n_rho, fa.taps, fa.n_cls,
-                                   (int)ctx->opt[CFFT_OPT_FILL_BLOCK], false);
+                                   (int)ctx->opt[CFFT_OPT_FILL_BLOCK], tc);
+    }
     if (plan.ok) {
       CFFT_CUDA(ctx->d_fill.ensure(plan.scratch), "alloc fill scratch");
       FillArgs<T, T> ft{};
@@ -656,6 +663,7 @@ cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, fa.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "fill backward");
+  if (flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "fill adjoint: a tensor-core wait ran past its bound");
   if (flag & 2) return fail(ctx, CFFT_ERR_NUMERIC, "fill adjoint: a stencil left its bucket (internal error)");
   if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the table's rho_max");
   return CFFT_OK;

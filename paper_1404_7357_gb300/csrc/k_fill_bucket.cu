@@ -621,45 +621,19 @@ size_t fc_smem_bytes(int n_harm) {
          (size_t)2 * 128 * fc_kpad(n_harm) * 4 + 1024; // A head, tail + alignment
 }
 
-__global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, float> a, BucketArgs b) {
-  extern __shared__ unsigned char smem_raw[];
-  constexpr int HALF = kFcTaps / 2 - 1;
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t taddr_s;
-  __shared__ int s_fail;
-  const int cell = blockIdx.x, cls = blockIdx.y, blk = blockIdx.z;
-  const size_t key = ((size_t)blk * b.n_ck + cls) * b.n_cells + cell;
-  const unsigned p0 = b.off[key], p1 = b.off[key + 1];
-  if (p0 == p1) return;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nh = a.n_harm;
-  const int kpad = fc_kpad(nh);
-  const uint32_t sbo = (uint32_t)(kpad / 4) * 128u;
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                         ~static_cast<uintptr_t>(1023));
-  float* Bh = reinterpret_cast<float*>(base);
-  float* Bl = Bh + (size_t)kFcN * kpad;
-  float* Ah = Bl + (size_t)kFcN * kpad;
-  float* Al = Ah + (size_t)128 * kpad;
-  if (tid == 0) {
-    s_fail = 0;
-    tc::mbar_init(&mbar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(&taddr_s, 512);
-    tc::tmem_relinquish();
-  }
-  // ---- B: the cell's table rows i0 .. i0 + 7 (parity below row 0, zero past the end;
-  // K rows past 2 n_harm are zero)
-  const int i0 = cell - HALF;
+// The B operand of one stencil cell (table rows i0 .. i0 + 7 of one class table):
+// [ab][qi][t] staged in stg with coalesced loads (parity below row 0, zero past the
+// end), then written as TF32 head and tail in the K-major layout, column n = 2 (16 t +
+// ab) + re/im, K = 2 qi + re/im of the A operand.  Ends with a CTA barrier.
+__device__ __forceinline__ void fc_build_b(const cpx<float>* tab_cls, int n_rho, int q_max, int nh, int kpad,
+                                           int i0, float* Bh, float* Bl, cpx<float>* stg) {
+  const int tid = threadIdx.x;
   {
     // the cell's table rows, staged as [ab][qi][t] in the (still unused) A buffer with
     // coalesced loads (8 consecutive rows per (ab, qi)); parity below row 0, zero past the end
-    cpx<float>* stg = reinterpret_cast<cpx<float>*>(Ah);
-    const cpx<float>* tab = a.table + (size_t)cls * 16 * nh * a.n_rho;
+    const cpx<float>* tab = tab_cls;
     const int n_st = 16 * nh * kFcTaps;
-    const bool inside = i0 >= 0 && i0 + kFcTaps <= a.n_rho;
+    const bool inside = i0 >= 0 && i0 + kFcTaps <= n_rho;
 #pragma unroll 4
     for (int e = tid; e < n_st; e += blockDim.x) {
       const int t = e & 7, rest = e >> 3;
@@ -667,12 +641,12 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
       int r = i0 + t;
       cpx<float> v = mk(0.f, 0.f);
       if (inside) {
-        v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
-      } else if (r < a.n_rho) {
+        v = tab[((size_t)ab * nh + qi) * n_rho + r];
+      } else if (r < n_rho) {
         const bool neg = r < 0;
         if (neg) r = -r;
-        v = tab[((size_t)ab * nh + qi) * a.n_rho + r];
-        if (neg && ((qi - a.q_max) & 1)) v = mk(-v.re, -v.im);
+        v = tab[((size_t)ab * nh + qi) * n_rho + r];
+        if (neg && ((qi - q_max) & 1)) v = mk(-v.re, -v.im);
       }
       stg[e] = v;
     }
@@ -706,6 +680,86 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+}
+
+// Row r of an A tile: e^{iq phi} (qweight: q e^{iq phi}) for the harmonic pairs
+// (qi, qi + 1), qi = 4 u + 2 half, one 16-byte group each, TF32 head and tail; zero when !ok
+__device__ __forceinline__ void fc_write_a(int r, int half, bool ok, cpx<float> e1, int q_max, int nh, int kpad,
+                                           bool qweight, float* Ah, float* Al) {
+  const cpx<float> e2 = e1 * e1, e4 = e2 * e2;
+  cpx<float> ph = mk(ok ? 1.f : 0.f, 0.f);
+  for (int k = 0; k < q_max; ++k) ph = ph * conj(e1);   // q = -q_max
+  if (half) ph = ph * e2;                                 // q = -q_max + 2
+  for (int qi = 2 * half; 2 * qi < kpad; qi += 4) {
+    cpx<float> v0 = qi < nh ? ph : mk(0.f, 0.f);
+    const cpx<float> p1v = ph * e1;
+    cpx<float> v1 = qi + 1 < nh ? p1v : mk(0.f, 0.f);
+    if (qweight) {
+      const float q0 = (float)(qi - q_max), q1 = q0 + 1.f;
+      v0 = mk(q0 * v0.re, q0 * v0.im);
+      v1 = mk(q1 * v1.re, q1 * v1.im);
+    }
+    float4 h, l;
+    tf32_split(v0.re, h.x, l.x);
+    tf32_split(v0.im, h.y, l.y);
+    tf32_split(v1.re, h.z, l.z);
+    tf32_split(v1.im, h.w, l.w);
+    const uint32_t off = tc::kmajor_offset(r, 2 * qi, kpad) / 4;
+    *reinterpret_cast<float4*>(Ah + off) = h;
+    *reinterpret_cast<float4*>(Al + off) = l;
+    ph = ph * e4;
+  }
+}
+
+// D (128 x 256, fp32 in tensor memory at d) = A B as three TF32 products (one thread)
+__device__ __forceinline__ void fc_mma(uint32_t d, const float* Ah, const float* Al, const float* Bh,
+                                       const float* Bl, int kpad, uint32_t sbo, uint32_t idesc) {
+  const uint32_t a_hi = tc::smem_u32(Ah), a_lo = tc::smem_u32(Al);
+  const uint32_t b_hi = tc::smem_u32(Bh), b_lo = tc::smem_u32(Bl);
+  for (int ks = 0; ks < kpad / 8; ++ks) {
+    const uint32_t ko = ks * 256;
+    const uint64_t dah = tc::sdesc(a_hi + ko, 128, sbo), dal = tc::sdesc(a_lo + ko, 128, sbo);
+    const uint64_t dbh = tc::sdesc(b_hi + ko, 128, sbo), dbl = tc::sdesc(b_lo + ko, 128, sbo);
+    tc::mma_tf32(d, dah, dbl, idesc, ks > 0 ? 1u : 0u);
+    tc::mma_tf32(d, dal, dbh, idesc, 1u);
+    tc::mma_tf32(d, dah, dbh, idesc, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, float> a, BucketArgs b) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int HALF = kFcTaps / 2 - 1;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_fail;
+  const int cell = blockIdx.x, cls = blockIdx.y, blk = blockIdx.z;
+  const size_t key = ((size_t)blk * b.n_ck + cls) * b.n_cells + cell;
+  const unsigned p0 = b.off[key], p1 = b.off[key + 1];
+  if (p0 == p1) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nh = a.n_harm;
+  const int kpad = fc_kpad(nh);
+  const uint32_t sbo = (uint32_t)(kpad / 4) * 128u;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  float* Bh = reinterpret_cast<float*>(base);
+  float* Bl = Bh + (size_t)kFcN * kpad;
+  float* Ah = Bl + (size_t)kFcN * kpad;
+  float* Al = Ah + (size_t)128 * kpad;
+  if (tid == 0) {
+    s_fail = 0;
+    tc::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&taddr_s, 512);
+    tc::tmem_relinquish();
+  }
+  // ---- B: the cell's table rows i0 .. i0 + 7 (parity below row 0, zero past the end;
+  // K rows past 2 n_harm are zero)
+  const int i0 = cell - HALF;
+  const cpx<float>* tab_cls = a.table + (size_t)cls * 16 * nh * a.n_rho;
+  fc_build_b(tab_cls, a.n_rho, a.q_max, nh, kpad, i0, Bh, Bl, reinterpret_cast<cpx<float>*>(Ah));
   const uint32_t tmem = taddr_s;
   const uint32_t idesc = tc::idesc_tf32(128, kFcN);
   const int r = tid & 127, half = tid >> 7;
@@ -775,24 +829,7 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
         e1 = mk(g.ex, g.ey);
         x0 = g.x;
       }
-      const cpx<float> e2 = e1 * e1, e4 = e2 * e2;
-      cpx<float> ph = mk(ok ? 1.f : 0.f, 0.f);
-      for (int k = 0; k < a.q_max; ++k) ph = ph * conj(e1);   // q = -q_max
-      if (half) ph = ph * e2;                                   // q = -q_max + 2
-      for (int qi = 2 * half; 2 * qi < kpad; qi += 4) {
-        const cpx<float> v0 = qi < nh ? ph : mk(0.f, 0.f);
-        const cpx<float> p1v = ph * e1;
-        const cpx<float> v1 = qi + 1 < nh ? p1v : mk(0.f, 0.f);
-        float4 h, l;
-        tf32_split(v0.re, h.x, l.x);
-        tf32_split(v0.im, h.y, l.y);
-        tf32_split(v1.re, h.z, l.z);
-        tf32_split(v1.im, h.w, l.w);
-        const uint32_t off = tc::kmajor_offset(r, 2 * qi, kpad) / 4;
-        *reinterpret_cast<float4*>(Ah + off) = h;
-        *reinterpret_cast<float4*>(Al + off) = l;
-        ph = ph * e4;
-      }
+      fc_write_a(r, half, ok, e1, a.q_max, nh, kpad, false, Ah, Al);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -800,17 +837,7 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
     const uint32_t set = n_commit & 1u;
     if (tid == 0 && !s_fail) {
       tc::fence_after_sync();
-      const uint32_t a_hi = tc::smem_u32(Ah), a_lo = tc::smem_u32(Al);
-      const uint32_t b_hi = tc::smem_u32(Bh), b_lo = tc::smem_u32(Bl);
-      const uint32_t d = tmem + set * kFcN;
-      for (int ks = 0; ks < kpad / 8; ++ks) {
-        const uint32_t ko = ks * 256;
-        const uint64_t dah = tc::sdesc(a_hi + ko, 128, sbo), dal = tc::sdesc(a_lo + ko, 128, sbo);
-        const uint64_t dbh = tc::sdesc(b_hi + ko, 128, sbo), dbl = tc::sdesc(b_lo + ko, 128, sbo);
-        tc::mma_tf32(d, dah, dbl, idesc, ks > 0 ? 1u : 0u);
-        tc::mma_tf32(d, dal, dbh, idesc, 1u);
-        tc::mma_tf32(d, dah, dbh, idesc, 1u);
-      }
+      fc_mma(tmem + set * kFcN, Ah, Al, Bh, Bl, kpad, sbo, idesc);
       tc::mma_commit(&mbar);
     }
     // while the tensor core runs this tile: the next tile's pairs, the previous tile's Z
@@ -832,6 +859,182 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
     have_prev = true;
   }
   if (have_prev && !s_fail) epilogue((n_commit - 1) & 1u, pv_ok, pv_m, pv_n, pv_x);
+  if (s_fail && tid == 0) atomicOr(a.err, 16);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+
+// Adjoint of the fill on the tensor cores, over the same per-cell buckets
+// (dL = Re sum conj(G) dZ', G = dL/dZ').  POS: two products with the cell's table
+// slice, D (A = e^{iq phi}) and Dq (A = q e^{iq phi}), in the two accumulators; per pair
+//   s_rho = Re sum_ab conj(G_ab) sum_t w'_t D[t][ab] / d_rho   (d Z'/d rho, the slope weights)
+//   s_phi = -Im sum_ab conj(G_ab) sum_t w_t Dq[t][ab]          (d Z'/d phi = i sum_q q ...)
+// give dL/d(r_m - r_n) through rho and phi (added to m, subtracted from n).  !POS: the
+// table is a derivative table; sum_ab Re conj(G_ab) sum_t w_t D[t][ab] goes into one scalar.
+template <bool POS>
+__global__ void __launch_bounds__(kBThreads, 1) adjoint_tc_kernel(FillArgs<float, float> a, BucketArgs b,
+                                                                  AdjArgs<float> g) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int HALF = kFcTaps / 2 - 1;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_fail;
+  __shared__ float part[2][128];
+  __shared__ double red[kBThreads / 32];
+  const int cell = blockIdx.x, cls = blockIdx.y, blk = blockIdx.z;
+  const size_t key = ((size_t)blk * b.n_ck + cls) * b.n_cells + cell;
+  const unsigned p0 = b.off[key], p1 = b.off[key + 1];
+  if (p0 == p1) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nh = a.n_harm;
+  const int kpad = fc_kpad(nh);
+  const uint32_t sbo = (uint32_t)(kpad / 4) * 128u;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  float* Bh = reinterpret_cast<float*>(base);
+  float* Bl = Bh + (size_t)kFcN * kpad;
+  float* Ah = Bl + (size_t)kFcN * kpad;
+  float* Al = Ah + (size_t)128 * kpad;
+  if (tid == 0) {
+    s_fail = 0;
+    tc::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&taddr_s, 512);
+    tc::tmem_relinquish();
+  }
+  const int i0 = cell - HALF;
+  fc_build_b(a.table + (size_t)cls * 16 * nh * a.n_rho, a.n_rho, a.q_max, nh, kpad, i0, Bh, Bl,
+             reinterpret_cast<cpx<float>*>(Ah));
+  const uint32_t tmem = taddr_s;
+  const uint32_t idesc = tc::idesc_tf32(128, kFcN);
+  const int r = tid & 127, half = tid >> 7;
+  const unsigned nmask = (1u << b.nb_bits) - 1u;
+  uint32_t n_commit = 0;
+  double theta_sum = 0.0;
+  bool failed = false;
+  for (unsigned t0 = p0; t0 < p1 && !failed; t0 += 128) {
+    const unsigned pidx = t0 + (unsigned)r;
+    bool ok = pidx < p1;
+    int m = 0, n = 0;
+    BGeom<float> geo{};
+    if (ok) {
+      const unsigned code = b.list[pidx];
+      n = (int)(code & nmask);
+      m = b.m0 + blk * b.br + (int)(code >> b.nb_bits);
+      geo = bucket_geom<float, kFcTaps>(a, b, m, n);
+      if (geo.i0 != i0) {   // a pair outside its bucket's cell: never expected
+        atomicOr(a.err, 2);
+        ok = false;
+      }
+      if (POS && m == n) ok = false;   // Z'(m, m) does not depend on the positions
+    }
+    const cpx<float> e1 = ok ? mk(geo.ex, geo.ey) : mk(1.f, 0.f);
+#pragma unroll 1
+    for (int pass = 0; pass < (POS ? 2 : 1); ++pass) {
+      fc_write_a(r, half, ok, e1, a.q_max, nh, kpad, pass == 1, Ah, Al);
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0 && !s_fail) {
+        tc::fence_after_sync();
+        fc_mma(tmem + (uint32_t)pass * kFcN, Ah, Al, Bh, Bl, kpad, sbo, idesc);
+        tc::mma_commit(&mbar);
+      }
+      // the products are done before any warp rewrites the A tile or reads the result
+      if (lane == 0 && !s_fail && !tc::mbar_wait(&mbar, n_commit & 1u, kTcPolls)) atomicOr(&s_fail, 1);
+      __syncwarp();
+      ++n_commit;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    failed = s_fail != 0;          // uniform: every wait of this tile precedes the barrier
+    tc::fence_after_sync();
+    if (!failed) {
+      float wt[kFcTaps], dwt[kFcTaps];
+      stencil_weights<float, kFcTaps, POS>(ok ? geo.x : 0.f, wt, dwt);
+      cpx<float> gv[8];
+      if (ok) {
+#pragma unroll
+        for (int u2 = 0; u2 < 2; ++u2)
+          load_grad_row<float, 4>(g.grad + ((size_t)m * 4 + 2 * half + u2) * g.ld_g + (size_t)n * 4, gv + 4 * u2,
+                                  g.vec_g != 0);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gv[j] = mk(0.f, 0.f);
+      }
+      const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * half);
+      float sa = 0.f, sb = 0.f;
+      {
+        float d[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) d[u] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kFcTaps; t += 2) {
+          float v[16], w[16];
+          tc::tmem_ld16x2(tl + 32 * t, tl + 32 * (t + 1), v, w);
+          const float c0 = POS ? dwt[t] : wt[t], c1 = POS ? dwt[t + 1] : wt[t + 1];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) d[u] = fmaf(c1, w[u], fmaf(c0, v[u], d[u]));
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sa += gv[j].re * d[2 * j] + gv[j].im * d[2 * j + 1];   // Re conj(G) D
+      }
+      if (POS) {
+        float d[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) d[u] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kFcTaps; t += 2) {
+          float v[16], w[16];
+          tc::tmem_ld16x2(tl + kFcN + 32 * t, tl + kFcN + 32 * (t + 1), v, w);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) d[u] = fmaf(wt[t + 1], w[u], fmaf(wt[t], v[u], d[u]));
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sb += gv[j].re * d[2 * j + 1] - gv[j].im * d[2 * j];   // Im conj(G) Q
+        // the two halves of a pair's MBF rows meet in shared memory
+        if (half) {
+          part[0][r] = sa;
+          part[1][r] = sb;
+        }
+        __syncthreads();
+        if (!half && ok) {
+          sa += part[0][r];
+          sb += part[1][r];
+          const double s_rho = (double)sa * a.inv_d_rho;   // d/d rho = (1 / d_rho) d/dx
+          const double s_phi = -(double)sb;
+          const double c = (double)geo.ex, sn = (double)geo.ey, rho = (double)geo.rho;
+          const double gx = s_rho * c - s_phi * sn / rho;
+          const double gy = s_rho * sn + s_phi * c / rho;
+          atomicAdd(&g.grad_pos[2 * m], gx);
+          atomicAdd(&g.grad_pos[2 * m + 1], gy);
+          atomicAdd(&g.grad_pos[2 * n], -gx);
+          atomicAdd(&g.grad_pos[2 * n + 1], -gy);
+        }
+      } else if (ok) {
+        theta_sum += (double)sa;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (!POS) {
+    double v = theta_sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0 && !failed) {
+      double t = 0.0;
+      for (int i = 0; i < kBThreads / 32; ++i) t += red[i];
+      atomicAdd(g.grad_theta, t);
+    }
+  }
   if (s_fail && tid == 0) atomicOr(a.err, 16);
   tc::fence_before_sync();
   __syncthreads();
@@ -946,6 +1149,38 @@ cudaError_t run_adjoint(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad, c
   });
 }
 
+cudaError_t run_adjoint_tc(const FillArgs<float, float>& a, const FillAdjointArgs<float>& ad,
+                           const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
+  const size_t smem = pl.smem;
+  cudaError_t e = cudaFuncSetAttribute(adjoint_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(adjoint_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  AdjArgs<float> g{};
+  g.grad = ad.grad;
+  g.ld_g = ad.ld_g;
+  g.vec_g = ((reinterpret_cast<uintptr_t>(ad.grad) & 15) == 0 && ((size_t)ad.ld_g * sizeof(cpx<float>)) % 16 == 0)
+                ? 1 : 0;
+  return run_waves<float, kFcTaps>(a, pl, bucket_args(a, pl, scratch), s, [&](const BucketArgs& b, dim3 fg) {
+    if (ad.grad_pos) {
+      AdjArgs<float> gp = g;
+      gp.grad_pos = ad.grad_pos;
+      adjoint_tc_kernel<true><<<fg, kBThreads, smem, s>>>(a, b, gp);
+    }
+    if (ad.grad_theta && ad.dtab_eps && ad.dtab_h) {
+      const cpx<float>* dt[2] = {ad.dtab_eps, ad.dtab_h};
+      for (int c = 0; c < 2; ++c) {
+        FillArgs<float, float> ac = a;
+        ac.table = dt[c];
+        AdjArgs<float> gt = g;
+        gt.grad_theta = ad.grad_theta + c;
+        adjoint_tc_kernel<false><<<fg, kBThreads, smem, s>>>(ac, b, gt);
+      }
+    }
+    return cudaSuccess;
+  });
+}
+
 cudaError_t run_fill_tc(const FillArgs<float, float>& a, const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
   const size_t smem = pl.smem;
   cudaError_t e = cudaFuncSetAttribute(fill_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1051,6 +1286,9 @@ template <class T>
 cudaError_t launch_fill_adjoint_bucketed(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad,
                                          const FillBucketPlan& pl, void* scratch, cudaStream_t s) {
   if (!pl.ok) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (pl.tc) return run_adjoint_tc(a, ad, pl, scratch, s);
+  }
   switch (a.n_mbf) {
     case 1: return adjoint_taps<T, 1>(a, ad, pl, scratch, s);
     case 2: return adjoint_taps<T, 2>(a, ad, pl, scratch, s);

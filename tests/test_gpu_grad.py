@@ -193,3 +193,27 @@ def test_bucketed_adjoint_m_and_taps(torch_cuda, m, taps):
     gp, gt = _adjoint(torch, ctx, pos, rot, g, 0)
     assert np.abs(gp - ref_p).max() < 1e-11 * np.abs(ref_p).max()
     assert np.all(np.abs(gt - ref_t) < 1e-11 * np.abs(ref_t))
+
+
+def test_tensor_core_adjoint_vs_fp32_pipe(torch_cuda):
+    """The adjoint of the tensor-core fill (forced: few pairs per cell here) against the
+    bucketed adjoint on the FP32 pipe: position gradient (value and slope products, the
+    q-weighted harmonics) and the substrate channels, 4 rotation classes, FP32."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp32", n=1024, n_rho=1024, rho_max=9.0, q_max=4, rotation_classes=4)
+    ctx = cc.gpu_context(wl, options={cfft.OPT_DERIVATIVES: 1})
+    ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 4)
+    pos = workloads.poisson_disc(300, 4.4, 0.3, seed=71)
+    rot = workloads.rotations(len(pos), seed=71)
+    a, m = len(pos), 4
+    g = torch.tensor(workloads.complex_normal((a * m, a * m), 72), device="cuda:0").to(torch.complex64)
+    ctx.set_option(cfft.OPT_FILL_SIMT, 1)
+    ref_p, ref_t = _adjoint(torch, ctx, pos, rot, g, 0)
+    ctx.set_option(cfft.OPT_FILL_SIMT, -1)
+    gp, gt = _adjoint(torch, ctx, pos, rot, g, 0)
+    ctx.set_option(cfft.OPT_FILL_SIMT, 0)
+    ep = np.abs(gp - ref_p).max() / np.abs(ref_p).max()
+    et = np.abs(gt - ref_t) / np.abs(ref_t)
+    print("tensor-core adjoint vs FP32 pipe: pos", ep, "eps/h", et)
+    assert ep < 2e-5 and np.all(et < 5e-5)
