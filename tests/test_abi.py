@@ -48,3 +48,42 @@ def test_create_without_device_fails_cleanly(lib):
     out = ctypes.c_void_p()
     assert lib.lib().cfft_create(ctypes.byref(out), 0, None) == 4  # CFFT_ERR_CUDA
     assert out.value is None
+
+
+def _header_struct(name):
+    """Field (name, C type) list of `typedef struct { ... } name;` in include/cfft.h."""
+    text = open(os.path.join(ROOT, "include", "cfft.h")).read()
+    m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = re.sub(r"/\*.*?\*/", "", decl, flags=re.S).strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        fields += [(n.strip(), ctype) for n in names.split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("cfft_info", "Info"), ("cfft_batch_info", "BatchInfo"),
+                                          ("cfft_batch_item", "BatchItem")])
+def test_struct_layouts_match_header(lib, cname, pyname):
+    """The ctypes mirrors of the ABI structs list the header's fields in its order with the
+    same C types (a field added on one side only would shift every later one)."""
+    from paper_1404_7357_gb300 import cfft
+    ctypes_of = {"int": ctypes.c_int, "double": ctypes.c_double}
+    header = _header_struct(cname)
+    binding = getattr(cfft, pyname)._fields_
+    assert [n for n, _ in header] == [n for n, _ in binding]
+    for (n, ct), (_, pt) in zip(header, binding):
+        assert ctypes_of[ct] is pt, (cname, n)
+
+
+def test_option_ids_match_header(lib):
+    """Every option constant of the binding has the value of the header's enum."""
+    from paper_1404_7357_gb300 import cfft
+    text = open(os.path.join(ROOT, "include", "cfft.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"CFFT_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert enum
+    for name, value in enum.items():
+        assert getattr(cfft, "OPT_" + name) == value, name

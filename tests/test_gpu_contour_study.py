@@ -1,5 +1,5 @@
 """Error versus contour height and Taylor order: the study of the paper's Table I
-(Section IV, "On the Contour height and Taylor's series order") on this build.
+(Section IV, "On the Contour height and Taylor's series order") with this library.
 
 Two strip MBFs at the diagonal separation d = 21.2 lambda0 (Delta = (15, 15)
 lambda0).  For each contour height, given as the paper's ratio gamma = beta_I /
