@@ -447,12 +447,20 @@ def barrier():
 
 
 def max_over_ranks(torch, value):
+    """The slowest rank's value (the whole job ends with it); CPU tensors under gloo."""
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
-        t = torch.tensor([value], dtype=torch.float64, device="cuda")
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
     return value
+
+
+def whole_job_rate(units_per_rank_step, steps, world, max_seconds):
+    """Units all ranks processed per second of the slowest rank: every rank runs its own
+    replica of the workload (weak scaling), so the job does world x the units of one."""
+    return units_per_rank_step * steps * world / max_seconds
 
 
 def stage_flops(inf, wl):
@@ -528,7 +536,7 @@ def run_cfft(args):
     wl, ctx, step_ms, infos, clk = bench_tabulation(torch, cfft, args, dev)
     total_s = max_over_ranks(torch, sum(step_ms) / 1e3)
     samples = table_samples(wl)
-    value = samples * args.steps * world / total_s
+    value = whole_job_rate(samples, args.steps, world, total_s)
     e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
     fp64 = None if args.skip_fp64 else bench_fp64(torch, cfft, args, dev)
     fill = None if args.skip_fill else bench_fill(torch, cfft, args, dev)
