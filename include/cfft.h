@@ -411,6 +411,15 @@ cfft_status cfft_backproject_static(int device, void* cuda_stream, const void* g
  * context stream; synchronizes to read the error flag. */
 cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void* k, void* out);
 
+/* Failure-detection self-test (no counterpart in the paper).  One device
+ * thread waits, with at most `polls` tries (1 .. 2^20), on an mbarrier phase
+ * that nothing completes -- the bounded wait every tensor-core kernel uses
+ * for its asynchronous products -- and records that it gave up.  Returns
+ * CFFT_ERR_TIMEOUT (the designed outcome; the context stays usable),
+ * CFFT_ERR_ARG for a bad bound, CFFT_ERR_CUDA on a launch failure.  No
+ * trap, fault or unbounded wait is involved.  Synchronizes the stream. */
+cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls);
+
 #ifdef __cplusplus
 }
 #endif

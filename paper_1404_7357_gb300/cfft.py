@@ -27,7 +27,7 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
-           "cfft_get_batch_info", "cfft_mbf_spectra"]
+           "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait"]
 
 
 class CfftLibraryError(ImportError):
@@ -96,6 +96,7 @@ def _load():
         "cfft_tabulate_batch": ([P, I, ctypes.POINTER(BatchItem), I, D, I, I, P, I], I),
         "cfft_get_batch_info": ([P, ctypes.POINTER(BatchInfo)], I),
         "cfft_mbf_spectra": ([P, I, P, P], I),
+        "cfft_selftest_bounded_wait": ([P, ctypes.c_uint], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -275,6 +276,11 @@ class Context:
                                              precision, ctypes.c_void_p(out.data_ptr()),
                                              int(graph) | (2 if autotune else 0)))
         return out
+
+    def selftest_bounded_wait(self, polls=4096):
+        """cfft_selftest_bounded_wait: a device-side wait that nothing ends runs out after
+        `polls` tries; raises CfftError with status CFFT_ERR_TIMEOUT (the designed outcome)."""
+        self._check(_lib.cfft_selftest_bounded_wait(self._h, ctypes.c_uint(polls)))
 
     def mbf_spectra(self, k, out=None):
         """cfft_mbf_spectra: k cuda complex64 (n, 2) wavevectors -> (n, 2 sides, M, 2 comps)

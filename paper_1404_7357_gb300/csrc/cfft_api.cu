@@ -1649,6 +1649,22 @@ cfft_status ensure_tc_element(cfft_ctx* ctx) {
 
 }  // namespace
 
+extern "C" cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (polls < 1 || polls > (1u << 20)) return fail(ctx, CFFT_ERR_ARG, "polls must be in 1 .. 2^20");
+  DeviceGuard g(ctx->device);
+  CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");
+  int* flag = ctx->d_flag.as<int>() + 3;
+  CFFT_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream), "flag");
+  cudaError_t e = launch_wait_selftest(polls, flag, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bounded-wait self-test kernel");
+  int h = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "self-test");
+  if (h & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "self-test: the bounded wait ran out (as designed)");
+  return CFFT_OK;
+}
+
 extern "C" cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void* k, void* out) {
   if (!ctx) return CFFT_ERR_ARG;
   if (n_points < 0 || (n_points > 0 && (!k || !out))) return fail(ctx, CFFT_ERR_ARG, "bad spectra arguments");

@@ -359,6 +359,9 @@ template <class T>
 cudaError_t launch_fill_adjoint_bucketed(const FillArgs<T, T>& a, const FillAdjointArgs<T>& ad,
                                          const FillBucketPlan& plan, void* scratch, cudaStream_t s);
 
+// the bounded mbarrier wait, run out on purpose: flag = 16 after `polls` tries
+cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s);
+
 // MBF spectra on the tensor cores (FP32 with TF32 head/tail splitting)
 int spectra_tc_columns(int n_shape, int n_mbf);
 void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_mbf,

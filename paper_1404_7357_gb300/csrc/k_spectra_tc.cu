@@ -312,6 +312,25 @@ void spectra_tc_bmatrix(int n_basis, int n_shape, const int* basis_class, int n_
   }
 }
 
+namespace {
+
+// one thread waits, at most `polls` tries, on the phase of an mbarrier that nothing
+// completes: the bounded wait of every tensor-core kernel, run out on purpose
+__global__ void wait_selftest_kernel(unsigned polls, int* flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  *flag = tc::mbar_wait(&bar, 0, polls) ? 1 : 16;
+}
+
+}  // namespace
+
+cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(polls, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spectra_tc(int n_points, int n_basis, int n_shape, int n_mbf, const ShapeClass* shapes,
                               const float* bx, const float* by, const float* bmat, const void* k, void* out,
                               int* err, cudaStream_t s) {
