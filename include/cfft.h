@@ -420,6 +420,20 @@ cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void* k, void* o
  * trap, fault or unbounded wait is involved.  Synchronizes the stream. */
 cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls);
 
+/* Checkpoint / resume of a table (the paper's tables are reusable across array
+ * layouts for a fixed substrate and element, Section IV-F): installs a table
+ * saved from cfft_copy_table (layout [class][pair][q][r] of cfft_get_table,
+ * complex128 for CFFT_FP64, complex64 otherwise) with its description: MBF
+ * count, harmonics |q| <= q_max, n_rho points on [0, rho_max], rotation classes
+ * (1 or 4), fill taps (even, 2..16, n_rho >= 2 taps).  Afterwards the fill and
+ * its position adjoint run without a tabulation (the substrate adjoint needs
+ * the derivative tables of a tabulation).  table: host (src_is_host != 0) or
+ * device memory, copied; the context keeps no reference.  CFFT_ERR_ARG for a
+ * bad description or an MBF count that differs from the context's element. */
+cfft_status cfft_load_table(cfft_ctx* ctx, int n_mbf, int q_max, double rho_max, int n_rho,
+                            cfft_precision precision, int rotation_classes, int fill_taps,
+                            const void* table, int src_is_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
-           "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait"]
+           "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table"]
 
 
 class CfftLibraryError(ImportError):
@@ -97,6 +97,7 @@ def _load():
         "cfft_get_batch_info": ([P, ctypes.POINTER(BatchInfo)], I),
         "cfft_mbf_spectra": ([P, I, P, P], I),
         "cfft_selftest_bounded_wait": ([P, ctypes.c_uint], I),
+        "cfft_load_table": ([P, I, I, D, I, I, I, I, P, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -180,6 +181,8 @@ class Context:
         self._check(_lib.cfft_set_option(self._h, key, float(value)))
 
     def tabulate_reactions(self, q_max, rho_max, n_rho, precision, rotation_classes=1):
+        self._table_desc = {"q_max": int(q_max), "rho_max": float(rho_max), "n_rho": int(n_rho),
+                            "precision": int(precision), "rotation_classes": int(rotation_classes)}
         self._check(_lib.cfft_tabulate_reactions(self._h, q_max, rho_max, n_rho, precision,
                                                  rotation_classes))
 
@@ -276,6 +279,36 @@ class Context:
                                              precision, ctypes.c_void_p(out.data_ptr()),
                                              int(graph) | (2 if autotune else 0)))
         return out
+
+    def save_table(self, path):
+        """Checkpoint: the current table as `path`.npy and its description as `path`.json."""
+        import json
+        import numpy as np
+        desc = dict(self._table_desc)
+        desc["n_mbf"] = int(self.n_mbf)
+        desc["fill_taps"] = int(self.info()["fill_taps"])
+        np.save(path + ".npy", self.copy_table(host=True).numpy())
+        with open(path + ".json", "w") as f:
+            json.dump(desc, f, indent=1)
+        return desc
+
+    def load_table(self, path):
+        """Resume from save_table: the table is installed (cfft_load_table) and the fill
+        runs without a tabulation."""
+        import json
+        import numpy as np
+        with open(path + ".json") as f:
+            d = json.load(f)
+        t = np.ascontiguousarray(np.load(path + ".npy"))
+        want = np.complex128 if d["precision"] == CFFT_FP64 else np.complex64
+        assert t.dtype == want and t.shape == (d["rotation_classes"], d["n_mbf"] ** 2, 2 * d["q_max"] + 1,
+                                               d["n_rho"])
+        self._check(_lib.cfft_load_table(self._h, d["n_mbf"], d["q_max"], d["rho_max"], d["n_rho"],
+                                         d["precision"], d["rotation_classes"], d["fill_taps"],
+                                         ctypes.c_void_p(t.ctypes.data), 1))
+        self.n_mbf = d["n_mbf"]
+        self._table_desc = {k: d[k] for k in ("q_max", "rho_max", "n_rho", "precision", "rotation_classes")}
+        return d
 
     def selftest_bounded_wait(self, polls=4096):
         """cfft_selftest_bounded_wait: a device-side wait that nothing ends runs out after

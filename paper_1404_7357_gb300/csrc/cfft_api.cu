@@ -561,6 +561,7 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
   fa.pos = pos;
   fa.rot = rot;
   fa.z = reinterpret_cast<cpx<TO>*>(z);
+  CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");   // a loaded table skips tabulation
   fa.err = ctx->d_flag.as<int>() + 1;
   FillBucketPlan plan{};
   plan.ok = false;
@@ -600,6 +601,7 @@ cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const
   fa.pos = pos;
   fa.rot = rot;
   fa.z = nullptr;
+  CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");   // a loaded table skips tabulation
   fa.err = ctx->d_flag.as<int>() + 1;
   const size_t table_elems = (size_t)ctx->cls_stored * ctx->n_mbf * ctx->n_mbf * fa.n_harm * ctx->n_rho;
   if (ctx->channels == 3) {
@@ -1443,6 +1445,44 @@ cfft_status cfft_copy_table(const cfft_ctx* cctx, void* dst, int64_t bytes, int 
                             dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                             ctx->stream), "copy table");
   if (dst_is_host) CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "copy table");
+  return CFFT_OK;
+}
+
+cfft_status cfft_load_table(cfft_ctx* ctx, int n_mbf, int q_max, double rho_max, int n_rho,
+                            cfft_precision precision, int rotation_classes, int fill_taps, const void* table,
+                            int src_is_host) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (!table) return fail(ctx, CFFT_ERR_ARG, "null table");
+  if (n_mbf < 1 || n_mbf > 8 || q_max < 0 || q_max > 64 || !(rho_max > 0.0) ||
+      (precision != CFFT_FP64 && precision != CFFT_FP32_MIXED) ||
+      (rotation_classes != 1 && rotation_classes != 4) || fill_taps < 2 || fill_taps > 16 || (fill_taps & 1) ||
+      n_rho < 2 * fill_taps)
+    return fail(ctx, CFFT_ERR_ARG, "bad table description");
+  if (ctx->has_el && ctx->n_mbf != n_mbf)
+    return fail(ctx, CFFT_ERR_ARG, "the table's MBF count differs from the context's element");
+  DeviceGuard g(ctx->device);
+  const size_t es = precision == CFFT_FP64 ? 16 : 8;
+  const size_t need = (size_t)rotation_classes * n_mbf * n_mbf * (2 * q_max + 1) * n_rho * es;
+  ctx->has_table = false;
+  CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");
+  CFFT_CUDA(ctx->d_table.ensure(need), "alloc table");
+  CFFT_CUDA(cudaMemcpyAsync(ctx->d_table.p, table, need, src_is_host ? cudaMemcpyHostToDevice
+                                                                      : cudaMemcpyDeviceToDevice,
+                            ctx->stream), "load table");
+  if (src_is_host) CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "load table");
+  if (!ctx->has_el) {
+    ctx->n_mbf = n_mbf;
+    ctx->n_mbf_pad = n_mbf <= 1 ? 1 : n_mbf <= 2 ? 2 : n_mbf <= 4 ? 4 : 8;
+  }
+  ctx->q_max = q_max;
+  ctx->rho_max = rho_max;
+  ctx->n_rho = n_rho;
+  ctx->prec = precision;
+  ctx->cls_stored = rotation_classes;
+  ctx->cls_computed = rotation_classes == 4 ? 3 : 1;
+  ctx->fill_taps = fill_taps;
+  ctx->channels = 1;
+  ctx->has_table = true;
   return CFFT_OK;
 }
 

@@ -129,3 +129,26 @@ def test_tensor_core_fill_vs_fp32_pipe(torch_cuda, block):
     for (i, j), blk in zip(idx, exact):
         got = ref[4 * i:4 * i + 4, 4 * j:4 * j + 4]
         assert np.abs(got - blk).max() < 1e-5 * scale, (i, j)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_table_checkpoint_and_resume(torch_cuda, tmp_path, precision):
+    """save_table / load_table (cfft_load_table): a fresh context with no substrate,
+    element or contour fills from the saved table exactly as the tabulating one does."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch(precision, n=1024, n_rho=512, rho_max=5.0, q_max=3, rotation_classes=4)
+    ctx, _ = cc.gpu_table(wl)
+    pos = workloads.poisson_disc(40, 2.4, 0.5, seed=81)
+    rot = workloads.rotations(len(pos), seed=81)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    ref = _fill(torch, ctx, pos, rot, 4, dt)
+    desc = ctx.save_table(str(tmp_path / "table"))
+    fresh = cfft.Context(0)
+    got_desc = fresh.load_table(str(tmp_path / "table"))
+    assert got_desc == desc
+    got = _fill(torch, fresh, pos, rot, 4, dt)
+    assert np.array_equal(got, ref)
+    # a description that does not fit is refused
+    with pytest.raises(cfft.CfftError):
+        fresh._check(cfft._lib.cfft_load_table(fresh._h, 4, 3, 5.0, 10, 0, 4, 8, None, 1))
