@@ -14,6 +14,13 @@
 // wavefront per load) and each load brings the M consecutive b-entries of a
 // row: per (q, a) and tap one or two 16-byte loads feed 2M FMAs.
 //
+// For M = 4 with 8 taps in FP32 the same buckets feed the tensor cores instead
+// (fill_tc_kernel, adjoint_tc_kernel below): one CTA per stencil cell, whose
+// pairs all use the same 8 table rows, so the harmonic sum of all of them is
+// one product with that slice of the table; the adjoint of the fill (gradient
+// with respect to the positions and, through derivative tables, the substrate)
+// runs over the same buckets in either form.
+//
 // Geometry in the FP32-mixed mode runs in float-float arithmetic (positions
 // split into a float head and tail; rho from a corrected float square root)
 // instead of float64, whose throughput is a small fraction of float32 on this
