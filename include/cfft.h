@@ -65,8 +65,10 @@ typedef enum {
                            square roots; table complex64 */
 } cfft_precision;
 
-/* Tunables of the tabulation (cfft_set_option).  A value <= 0 restores the
- * automatic choice, which depends on precision and element size:
+/* Tunables of the tabulation and the fill (cfft_set_option).  A value <= 0
+ * restores the automatic choice, which depends on precision and element size,
+ * except where an option below gives negative values a meaning of their own
+ * (CHECK_FINITE, FILL_BLOCK, FILL_SIMT):
  *   N_ALPHA     angular samples for the azimuthal harmonics (multiple of 4)
  *   SIGMA       zero-padding factor of the beta FFT (power of two >= 2)
  *   BP_TAPS     Lagrange taps of the back-projection interpolation
@@ -166,7 +168,9 @@ cfft_status cfft_set_mbf_spectra(cfft_ctx* ctx, int n_basis, const double* cente
 cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double beta_p,
                                double height, int taylor_order);
 
-/* Override a tunable (see cfft_option); value <= 0 restores automatic. */
+/* Override a tunable (see cfft_option; values <= 0 restore the automatic
+ * choice unless the option says otherwise).  CFFT_ERR_ARG for an unknown key.
+ * Takes effect at the next tabulation or fill. */
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value);
 
 /* Tabulate Z_ab,q(rho_r) for all MBF pairs (a, b), harmonics q = -q_max..q_max
