@@ -152,3 +152,39 @@ def test_table_checkpoint_and_resume(torch_cuda, tmp_path, precision):
     # a description that does not fit is refused
     with pytest.raises(cfft.CfftError):
         fresh._check(cfft._lib.cfft_load_table(fresh._h, 4, 3, 5.0, 10, 0, 4, 8, None, 1))
+
+
+@pytest.mark.slow
+def test_full_size_fill_sampled_against_oracle(torch_cuda):
+    """The benchmark's fill at full size and in its launch configuration (10,000-element
+    irregular array, 40,000^2 complex64, table of patch-m4 with 4 rotation classes to
+    121 lambda0 on 16,384 points, FP32-mixed, tensor-core form): sampled element-pair
+    blocks (near, middle and far pairs, every rotation class, a diagonal block) against
+    the oracle's exact fill on the same contour."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = workloads.patch_m4(n=16384, n_rho=16384, rho_max=121.0, q_max=16, precision="fp32",
+                            rotation_classes=4)
+    pos, rot = workloads.irregular_array()
+    ctx, _ = cc.gpu_table(wl)
+    a, m = len(pos), 4
+    z = torch.empty((a * m, a * m), dtype=torch.complex64, device="cuda:0")
+    ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), torch.tensor(rot, device="cuda:0"), z)
+    assert ctx.info()["fill_form"] == 3
+    rng = np.random.default_rng(91)
+    d = np.hypot(*(pos[:, None, :] - pos[None, :10, :]).transpose(2, 0, 1))   # to 10 anchors
+    pairs = [(0, 0)]
+    for lo, hi in ((0.4, 2.0), (20.0, 40.0), (60.0, 80.0), (100.0, 121.0)):
+        cand = np.argwhere((d >= lo) & (d < hi))
+        for k in rng.choice(len(cand), size=min(4, len(cand)), replace=False):
+            pairs.append((int(cand[k][0]), int(cand[k][1])))
+    got = [z[4 * i:4 * i + 4, 4 * j:4 * j + 4].cpu().numpy().astype(np.complex128) for i, j in pairs]
+    del z
+    torch.cuda.empty_cache()
+    nodes, hq = cc.oracle_harmonics(wl, classes=(0, 1, 2, 3))
+    ref = cc.oracle_fill_entries(wl, hq, nodes, pos, rot, pairs)
+    scale = max(np.abs(r).max() for r in ref)
+    err = max(np.abs(g - r).max() for g, r in zip(got, ref)) / scale
+    classes = {2 * int(rot[i]) + int(rot[j]) for i, j in pairs}
+    print("full-size fill, %d sampled blocks (classes %s): rel err %.3g" % (len(pairs), sorted(classes), err))
+    assert err < 1e-5
