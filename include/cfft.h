@@ -290,8 +290,9 @@ cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info);
  * applied to dP/dtheta and dR/dtheta (analytic derivatives of the TE/TM
  * expressions, float64) with the contour, Taylor order and grids unchanged.
  * which = 0: the table itself; 1: d/d eps_r; 2: d/d h.  Same layout and
- * element type as cfft_get_table; borrowed.  CFFT_ERR_STATE unless the last
- * tabulation ran with CFFT_OPT_DERIVATIVES > 0 (which > 0). */
+ * element type as cfft_get_table; borrowed.  For which = 1 or 2 the call
+ * returns CFFT_ERR_STATE unless the last tabulation ran with
+ * CFFT_OPT_DERIVATIVES > 0. */
 cfft_status cfft_get_derivative_table(const cfft_ctx* ctx, int which, const void** dev_ptr,
                                       int64_t shape[4]);
 
@@ -428,8 +429,9 @@ cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls);
  * layouts for a fixed substrate and element, Section IV-F): installs a table
  * saved from cfft_copy_table (layout [class][pair][q][r] of cfft_get_table,
  * complex128 for CFFT_FP64, complex64 otherwise) with its description: MBF
- * count, harmonics |q| <= q_max, n_rho points on [0, rho_max], rotation classes
- * (1 or 4), fill taps (even, 2..16, n_rho >= 2 taps).  Afterwards the fill and
+ * count (1..8), harmonics |q| <= q_max (0..64), n_rho points (at most 2^20)
+ * on [0, rho_max] (rho_max finite, > 0), rotation classes (1 or 4), fill taps
+ * (even, 2..16, n_rho >= 2 taps).  Afterwards the fill and
  * its position adjoint run without a tabulation (the substrate adjoint needs
  * the derivative tables of a tabulation).  table: host (src_is_host != 0) or
  * device memory, copied; the context keeps no reference.  CFFT_ERR_ARG for a

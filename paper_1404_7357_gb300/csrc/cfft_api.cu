@@ -99,6 +99,7 @@ struct cfft_ctx {
   cudaEvent_t bev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraphExec_t bgraph = nullptr;
   std::string bsig;           // signature of the captured graph
+  std::string bshape;         // what the captured graph bakes in: addresses, launch shapes, task ranges
   struct TunedPlan { int sub_len, rchunk, bp_tc; };
   std::map<std::string, TunedPlan> tuned;  // signature -> tuned shape
   double b_ms[4] = {0, 0, 0, 0};
@@ -233,7 +234,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(ctx->d_y.ensure((size_t)series * n * sizeof(cpx<T>)), "alloc harmonics");
   CFFT_CUDA(ctx->d_grid.ensure((size_t)series * (2 * K + 1) * sizeof(cpx<T>)), "alloc grid");
   const int cls_s = ctx->cls_stored;
-  const int channels = ctx->opt[6] > 0 ? 3 : 1;
+  const int channels = ctx->opt[CFFT_OPT_DERIVATIVES] > 0 ? 3 : 1;
   const size_t table_elems = (size_t)cls_s * pairs * nh * ctx->n_rho;
   CFFT_CUDA(ctx->d_table.ensure(channels * table_elems * sizeof(cpx<T>)), "alloc table");
   if (channels == 3) {
@@ -490,7 +491,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(cudaEventRecord(ctx->ev[4], st), "event");
 
   // ---- NaN / Inf check (synchronizes)
-  bool check = !(ctx->opt[5] < 0);
+  bool check = !(ctx->opt[CFFT_OPT_CHECK_FINITE] < 0);
   if (check) {
     CFFT_CUDA(cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), st), "flag");
     launch_nonfinite<T>(ctx->d_table.as<cpx<T>>(), (int64_t)(channels * table_elems), ctx->d_flag.as<int>(), st);
@@ -1032,6 +1033,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         r.fb.push_back(FftBucket{ftask[t].w, t, u, mo});
         t = u;
       }
+      if (r.fb.size() > 7)  // one completion counter per sub-FFT length, seven per wave
+        return fail(ctx, CFFT_ERR_ARG, "batch: more than seven sub-FFT lengths in one wave");
       // within a wave, the costliest back-projection tasks (largest rho) first
       std::stable_sort(btask.begin() + r.b0, btask.end(),
                        [](const int4& a, const int4& b) { return a.z > b.z; });
@@ -1062,6 +1065,35 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     ctx->b_rchunk = rchunk;
     ctx->b_bp_tc = tform_b ? 1 : 0;
     ctx->b_waves = (int)waves.size();
+
+    // everything a captured graph holds by value: buffer addresses, launch shapes and
+    // task ranges.  A replay is valid only while all of them are unchanged; the per-item
+    // values (substrate, contour) live in the argument buffers refreshed above.
+    std::string shape;
+    auto add = [&](long long v) {
+      shape += std::to_string(v);
+      shape += ',';
+    };
+    for (long long v : {(long long)L, (long long)rchunk, (long long)tform_b, (long long)tc_b, (long long)jt,
+                        (long long)n_chunks, (long long)max_nodes, (long long)max_seg, (long long)max_nout,
+                        (long long)max_active, (long long)max_n_item, (long long)cos_total})
+      add(v);
+    for (const void* ptr : {ctx->d_tw.p, ctx->b_cnodes.p, ctx->b_coff.p, ctx->b_cos.p, ctx->b_count.p,
+                            ctx->b_cargs.p, ctx->b_cdata.p, ctx->b_iargs.p, ctx->b_fargs.p, ctx->b_bargs.p,
+                            ctx->b_cmap.p, ctx->b_imap.p, ctx->b_ftask.p, ctx->b_btask.p, ctx->b_flag.p,
+                            ctx->b_y.p, ctx->b_grid.p, ctx->b_contour.p, ctx->d_bx.p, ctx->d_by.p, ctx->d_q.p,
+                            ctx->d_shapes.p, ctx->tc_bx.p, ctx->tc_by.p, ctx->tc_bmat_mirror.p})
+      add((long long)(uintptr_t)ptr);
+    for (const WaveRanges& r : wr) {
+      for (size_t v : {r.c0, r.c1, r.i0, r.i1, r.f0, r.f1, r.b0, r.b1}) add((long long)v);
+      for (const FftBucket& fb : r.fb) {
+        add(fb.log2L);
+        add((long long)fb.f0);
+        add((long long)fb.f1);
+        add(fb.max_nout);
+      }
+    }
+    if (mode == 2 && shape != ctx->bshape) mode = 1;  // the plan moved: capture again
 
     // the launch sequence (stream-ordered on the batch stream)
     int launches = 0;
@@ -1164,6 +1196,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       cudaGraphDestroy(graph);
       CFFT_CUDA(e, "graph instantiate");
       ctx->bsig = sig;
+      ctx->bshape = shape;
     } else {
       CFFT_CUDA(issue(), "batch launch");
     }
@@ -1272,7 +1305,8 @@ void cfft_destroy(cfft_ctx* ctx) {
                       &ctx->green_r, &ctx->dp_eps, &ctx->dr_eps, &ctx->dp_h, &ctx->dr_h, &ctx->d_shapes, &ctx->d_bx, &ctx->d_by, &ctx->d_q,
                       &ctx->d_y, &ctx->d_grid, &ctx->d_table, &ctx->d_tw, &ctx->d_cnodes,
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
-                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill};
+                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
+                      &ctx->tc_bmat_mirror, &ctx->tc_shapes};
     for (DevBuf* b : bufs) b->release();
     for (auto& e : ctx->ev)
       if (e) cudaEventDestroy(e);
@@ -1453,10 +1487,10 @@ cfft_status cfft_load_table(cfft_ctx* ctx, int n_mbf, int q_max, double rho_max,
                             int src_is_host) {
   if (!ctx) return CFFT_ERR_ARG;
   if (!table) return fail(ctx, CFFT_ERR_ARG, "null table");
-  if (n_mbf < 1 || n_mbf > 8 || q_max < 0 || q_max > 64 || !(rho_max > 0.0) ||
+  if (n_mbf < 1 || n_mbf > 8 || q_max < 0 || q_max > 64 || !(rho_max > 0.0) || !std::isfinite(rho_max) ||
       (precision != CFFT_FP64 && precision != CFFT_FP32_MIXED) ||
       (rotation_classes != 1 && rotation_classes != 4) || fill_taps < 2 || fill_taps > 16 || (fill_taps & 1) ||
-      n_rho < 2 * fill_taps)
+      n_rho < 2 * fill_taps || n_rho > (1 << 20))
     return fail(ctx, CFFT_ERR_ARG, "bad table description");
   if (ctx->has_el && ctx->n_mbf != n_mbf)
     return fail(ctx, CFFT_ERR_ARG, "the table's MBF count differs from the context's element");

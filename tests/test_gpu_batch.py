@@ -43,7 +43,7 @@ def _single(cfft, el, it, q_max, rho_max, n_rho, prec, n_alpha):
     ctx = cfft.Context(0)
     ctx.set_substrate(it["eps_r"], it["h"], it["k0"])
     ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
-    ctx.build_contour(it["n"], it["beta_max"], it["beta_p"], it["height"], -1)
+    ctx.build_contour(it["n"], it["beta_max"], it["beta_p"], it["height"], int(it.get("taylor_order", -1)))
     ctx.set_option(cfft.OPT_N_ALPHA, n_alpha)
     ctx.tabulate_reactions(q_max, rho_max, n_rho, prec, 1)
     return ctx.copy_table(host=True).numpy()[0]
@@ -96,6 +96,36 @@ def test_batch_graph_replay_tracks_new_parameters(torch_cuda):
     print("autotuned", info)
     tuned = out2.cpu().numpy()
     assert np.abs(tuned - second).max() < TOL["fp32"] * np.abs(second).max()
+
+
+def test_batch_graph_recaptured_when_the_contours_change(torch_cuda):
+    """Same item count, node counts and Taylor orders, new contours: beta_max, the pole
+    bound and the height move, so the transform grids and the angular node counts change.
+    The captured graph holds those shapes and buffer addresses, so it must not be replayed
+    on the new plan: it is captured again, and the tables match single tabulations."""
+    from paper_1404_7357_gb300 import cfft
+    el = workloads.patch_rooftops()
+    items = _items(4, seed=11)
+    for it in items:
+        it["taylor_order"] = 26   # fixed, so only the contour geometry changes below
+    q_max, rho_max, n_rho = 2, 3.0, 128
+    ctx = cfft.Context(0)
+    ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+    ctx.set_option(cfft.OPT_N_ALPHA, 128)
+    out = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, graph=True)
+    for it in items:
+        kd = it["k0"] * np.sqrt(it["eps_r"])
+        it["beta_max"] = 5.25 * kd
+        step = it["beta_max"] / it["n"]
+        it["beta_p"] = round(1.3 * kd / step) * step
+        it["height"] = 6.0 * step
+    out = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True)
+    got = out.cpu().numpy()
+    for i, it in enumerate(items):
+        ref = _single(cfft, el, it, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, 128)
+        err = np.abs(got[i].astype(np.complex128) - ref).max() / np.abs(ref).max()
+        print("item", i, "n", it["n"], "rel err after the contour change", err)
+        assert err < TOL["fp32"]
 
 
 def test_batch_item_against_oracle(torch_cuda):
