@@ -211,30 +211,55 @@ class Context:
                                          out.numel() * out.element_size(), int(not out.is_cuda)))
         return out
 
-    def fill_reduced_matrix(self, pos, rot, out, out_complex128=None):
+    def _check_layout(self, pos, rot, z, device):
+        """The fill's buffers as the C entry points read them: pos (A, 2) float64,
+        rot (A,) int32 or None, z a complex64/complex128 matrix of at least A*M x A*M
+        with unit column stride (rows ld = z's row stride apart)."""
+        torch = self._torch
+
+        def bad(msg):
+            raise ValueError("fill arguments: " + msg)
+        if pos.dtype not in (torch.float64, np.float64) or tuple(pos.shape)[1:] != (2,):
+            bad("pos must be float64 of shape (A, 2)")
+        a = int(pos.shape[0])
+        n = a * int(self.n_mbf)
+        if rot is not None and (rot.dtype not in (torch.int32, np.int32) or tuple(rot.shape) != (a,)):
+            bad("rot must be int32 of shape (A,)")
+        if z.dtype not in (torch.complex64, torch.complex128, np.complex64, np.complex128):
+            bad("the matrix must be complex64 or complex128")
+        if len(z.shape) != 2 or z.shape[0] < n or z.shape[1] < n:
+            bad("the matrix must be at least (A*M, A*M) = (%d, %d), got %s" % (n, n, tuple(z.shape)))
+        for t in (pos, rot, z):
+            if t is None:
+                continue
+            on_dev = bool(getattr(t, "is_cuda", False))
+            if on_dev != device:
+                bad("expected %s buffers" % ("CUDA" if device else "host"))
+        if device:
+            if not pos.is_contiguous() or (rot is not None and not rot.is_contiguous()) or z.stride(-1) != 1:
+                bad("pos and rot must be contiguous and the matrix rows unit-stride")
+        return a
+
+    def fill_reduced_matrix(self, pos, rot, out):
         """pos: cuda float64 (A, 2); rot: cuda int32 (A,) or None; out: cuda complex (A*M, ld)."""
         torch = self._torch
-        assert pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()
-        if rot is not None:
-            assert rot.is_cuda and rot.dtype == torch.int32 and rot.is_contiguous()
-        assert out.is_cuda and out.stride(-1) == 1
-        is128 = out.dtype == torch.complex128 if out_complex128 is None else out_complex128
+        a = self._check_layout(pos, rot, out, device=True)
         self._check(_lib.cfft_fill_reduced_matrix(
-            self._h, pos.shape[0], ctypes.c_void_p(pos.data_ptr()),
+            self._h, a, ctypes.c_void_p(pos.data_ptr()),
             ctypes.c_void_p(rot.data_ptr() if rot is not None else 0),
-            ctypes.c_void_p(out.data_ptr()), out.stride(0), int(is128)))
+            ctypes.c_void_p(out.data_ptr()), out.stride(0), int(out.dtype == torch.complex128)))
         return out
 
     def fill_reduced_matrix_host(self, pos, rot, out):
-        """Host variant: numpy (or pinned torch CPU) arrays in and out."""
-        def addr(a):
-            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
-        is128 = str(out.dtype).endswith("complex128")
-        ld = out.stride(0) if hasattr(out, "data_ptr") else out.strides[0] // out.itemsize
+        """Host variant: C-contiguous numpy arrays in and out (out rows may be padded)."""
+        pos = np.ascontiguousarray(pos)
+        rot = None if rot is None else np.ascontiguousarray(rot)
+        a = self._check_layout(pos, rot, out, device=False)
+        if not isinstance(out, np.ndarray) or out.strides[1] != out.itemsize or not out.flags.writeable:
+            raise ValueError("fill arguments: out must be a writeable numpy matrix with unit-stride rows")
         self._check(_lib.cfft_fill_reduced_matrix_host(
-            self._h, len(pos), ctypes.c_void_p(addr(pos)),
-            ctypes.c_void_p(addr(rot) if rot is not None else 0), ctypes.c_void_p(addr(out)),
-            ld, int(is128)))
+            self._h, a, _ptr(pos), ctypes.c_void_p(rot.ctypes.data if rot is not None else 0),
+            _ptr(out), out.strides[0] // out.itemsize, int(out.dtype == np.complex128)))
         return out
 
     def derivative_table(self, which):
@@ -249,7 +274,7 @@ class Context:
     def fill_backward(self, pos, rot, grad_z, substrate=True):
         """Adjoint of the fill: (grad_pos (A, 2) float64, grad_eps_h (2,) float64 or None)."""
         torch = self._torch
-        assert grad_z.is_cuda and grad_z.stride(-1) == 1
+        self._check_layout(pos, rot, grad_z, device=True)
         grad_pos = torch.empty_like(pos)
         g_th = torch.empty(2, dtype=torch.float64, device=pos.device) if substrate else None
         self._check(_lib.cfft_fill_backward(

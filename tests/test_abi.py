@@ -87,3 +87,42 @@ def test_option_ids_match_header(lib):
     assert enum
     for name, value in enum.items():
         assert getattr(cfft, "OPT_" + name) == value, name
+
+
+def _unbound_context(cfft, n_mbf):
+    """A Context object with no C context behind it: enough to exercise the binding's
+    own argument checks, which run before any library call."""
+    import torch
+    c = object.__new__(cfft.Context)
+    c._torch = torch
+    c._h = ctypes.c_void_p()
+    c.device = 0
+    c.n_mbf = n_mbf
+    return c
+
+
+def test_fill_binding_rejects_bad_layouts(lib):
+    import numpy as np
+    import torch
+    c = _unbound_context(lib, 4)
+    pos = np.zeros((3, 2))
+    rot = np.zeros(3, dtype=np.int32)
+    z = np.zeros((12, 13), dtype=np.complex64)
+    assert c._check_layout(pos, rot, z, device=False) == 3
+    assert c._check_layout(pos, None, np.zeros((12, 12), dtype=np.complex128), device=False) == 3
+    bad = [
+        (pos.astype(np.float32), rot, z),                   # positions not float64
+        (np.zeros((3, 3)), rot, z),                          # not (A, 2)
+        (pos, rot.astype(np.int64), z),                      # rotations not int32
+        (pos, np.zeros(2, dtype=np.int32), z),               # one rotation per element
+        (pos, rot, np.zeros((11, 12), dtype=np.complex64)),  # fewer than A*M rows
+        (pos, rot, np.zeros((12, 11), dtype=np.complex64)),  # fewer than A*M columns
+        (pos, rot, np.zeros((12, 12), dtype=np.float64)),    # not complex
+    ]
+    for p, r, m in bad:
+        with pytest.raises(ValueError):
+            c._check_layout(p, r, m, device=False)
+    # the device entry points take CUDA tensors only
+    with pytest.raises(ValueError):
+        c._check_layout(torch.zeros((3, 2), dtype=torch.float64), None,
+                        torch.zeros((12, 12), dtype=torch.complex64), device=True)
