@@ -344,12 +344,16 @@ class Context:
         """cfft_mbf_spectra: k cuda complex64 (n, 2) wavevectors -> (n, 2 sides, M, 2 comps)
         complex64 MBF spectra (side 0: Eq. 11; side 1: the conjugated continuation)."""
         torch = self._torch
-        assert k.is_cuda and k.dtype == torch.complex64 and k.is_contiguous() and k.shape[-1] == 2
+        if not (k.is_cuda and k.dtype == torch.complex64 and k.is_contiguous() and k.dim() == 2 and
+                k.shape[1] == 2):
+            raise ValueError("k must be a contiguous CUDA complex64 tensor of shape (n, 2)")
         n = k.shape[0]
         shape = (n, 2, self.n_mbf, 2)
         if out is None:
             out = torch.empty(shape, dtype=torch.complex64, device=k.device)
-        assert tuple(out.shape) == shape and out.dtype == torch.complex64 and out.is_contiguous()
+        if not (out.is_cuda and tuple(out.shape) == shape and out.dtype == torch.complex64 and
+                out.is_contiguous()):
+            raise ValueError("out must be a contiguous CUDA complex64 tensor of shape %s" % (shape,))
         self._check(_lib.cfft_mbf_spectra(self._h, n, ctypes.c_void_p(k.data_ptr()),
                                           ctypes.c_void_p(out.data_ptr())))
         return out
@@ -389,9 +393,16 @@ def backproject_static(grid, table, series_per_q, q_max, rho_max, grid_half, del
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    assert grid.is_cuda and table.is_cuda and grid.dtype == table.dtype
-    assert grid.is_contiguous() and table.is_contiguous()
+    if not (grid.is_cuda and table.is_cuda and grid.dtype == table.dtype and
+            grid.dtype in (torch.complex64, torch.complex128)):
+        raise ValueError("grid and table: CUDA tensors of one complex dtype")
+    if not (grid.is_contiguous() and table.is_contiguous()):
+        raise ValueError("grid and table must be contiguous")
+    series = series_per_q * (2 * q_max + 1)
     n_rho = table.shape[-1]
+    if grid.numel() != series * (2 * grid_half + 1) or table.numel() != series * n_rho:
+        raise ValueError("grid must hold [series][2*grid_half+1] and table [series][n_rho], "
+                         "series = series_per_q * (2*q_max+1) = %d" % series)
     st = _lib.cfft_backproject_static(dev, ctypes.c_void_p(handle), ctypes.c_void_p(grid.data_ptr()),
                                       ctypes.c_void_p(table.data_ptr()), series_per_q, q_max, n_rho,
                                       float(rho_max), grid_half, float(delta_s), sigma, taps,

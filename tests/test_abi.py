@@ -126,3 +126,14 @@ def test_fill_binding_rejects_bad_layouts(lib):
     with pytest.raises(ValueError):
         c._check_layout(torch.zeros((3, 2), dtype=torch.float64), None,
                         torch.zeros((12, 12), dtype=torch.complex64), device=True)
+
+
+def test_static_backprojection_and_spectra_bindings_refuse_host_tensors(lib):
+    import torch
+    grid = torch.zeros((1, 1, 1, 101), dtype=torch.complex64)
+    table = torch.zeros((1, 1, 1, 64), dtype=torch.complex64)
+    with pytest.raises(ValueError):
+        lib.backproject_static(grid, table, 1, 0, 10.0, 50, 0.1, 4, 8, 10.0, stream=0)
+    c = _unbound_context(lib, 2)
+    with pytest.raises(ValueError):
+        c.mbf_spectra(torch.zeros((8, 2), dtype=torch.complex64))

@@ -58,9 +58,13 @@ def test_static_backprojection_rejects_oversized_requests(torch_cuda):
     grid = torch.zeros((1, 1, 1, 101), dtype=torch.complex64, device="cuda:0")
     table = torch.zeros((1, 1, 1, 64), dtype=torch.complex64, device="cuda:0")
     # far more angular nodes than the fixed scratch holds: rejected before any work is queued
+    wide = torch.zeros((1, 1, 1, 2 * 200000 + 1), dtype=torch.complex64, device="cuda:0")
     with pytest.raises(cfft.CfftError) as ei:
-        cfft.backproject_static(grid, table, 1, 0, 1.0e5, 200000, 1.0, 4, 8, 100.0)
+        cfft.backproject_static(wide, table, 1, 0, 1.0e5, 200000, 1.0, 4, 8, 100.0)
     assert ei.value.status == 1
+    # a grid that does not hold [series][2*grid_half+1]: refused by the binding
+    with pytest.raises(ValueError):
+        cfft.backproject_static(grid, table, 1, 0, 1.0e5, 200000, 1.0, 4, 8, 100.0)
     # rho_max beyond the grid half-width: rejected as well
     with pytest.raises(cfft.CfftError) as ei:
         cfft.backproject_static(grid, table, 1, 0, 10.0, 50, 0.1, 4, 8, 10.0)
