@@ -78,6 +78,9 @@ cfft_status run(cudaStream_t st, unsigned char* scratch, const void* grid, void*
                 double delta_s, int sigma, int taps, double beta_abs_max, double margin) {
   const int n_chunks = (n_rho + kRowChunk - 1) / kRowChunk;
   const double d_rho = rho_max / (n_rho - 1);
+  // the grid must reach rho_max plus half a stencil (compared in floating point, so that
+  // no huge ratio is converted to an integer)
+  if (std::ceil(rho_max / delta_s) + taps / 2 + 2 > (double)grid_half) return CFFT_ERR_ARG;
   // host-side bounds of the scratch and shared-memory use (the device recomputes the
   // same counts; +2 covers a last-bit difference of cbrt between host and device)
   int64_t total = 0;
@@ -92,7 +95,6 @@ cfft_status run(cudaStream_t st, unsigned char* scratch, const void* grid, void*
     max_seg = std::max(max_seg, 2 * kseg + 1);
   }
   if (n_chunks > kMaxChunks || (size_t)total > kMaxCosines) return CFFT_ERR_ARG;
-  if ((int64_t)std::ceil(rho_max / delta_s) + taps / 2 + 2 > grid_half) return CFFT_ERR_ARG;
   int group = 8;
   const size_t cap = 225 * 1024;
   while (group > 1 && backproject_smem<T>(group, max_seg, max_nodes) > cap) --group;
@@ -141,7 +143,9 @@ extern "C" cfft_status cfft_backproject_static(int device, void* cuda_stream, co
   if (!grid || !table || device < 0 || device >= kMaxDevices) return CFFT_ERR_ARG;
   if (series_per_q < 1 || q_max < 0 || q_max > 64 || n_rho < 2 || !(rho_max > 0) ||
       grid_half < 1 || !(delta_s > 0) || sigma < 2 || (sigma & (sigma - 1)) ||
-      !(beta_abs_max > 0) || !(alpha_margin > 0))
+      !(beta_abs_max > 0) || !(alpha_margin > 0) ||
+      !(taps == 4 || taps == 6 || taps == 8 || taps == 10 || taps == 12 || taps == 16 || taps == 20 ||
+        taps == 24))
     return CFFT_ERR_ARG;
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return CFFT_ERR_CUDA;

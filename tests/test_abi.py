@@ -137,3 +137,19 @@ def test_static_backprojection_and_spectra_bindings_refuse_host_tensors(lib):
     c = _unbound_context(lib, 2)
     with pytest.raises(ValueError):
         c.mbf_spectra(torch.zeros((8, 2), dtype=torch.complex64))
+
+
+def test_static_backprojection_argument_checks_need_no_device(lib):
+    h = lib.lib()
+    dummy = ctypes.c_void_p(16)   # never dereferenced: every case below is refused first
+
+    def call(**kw):
+        a = dict(device=0, grid=dummy, table=dummy, series_per_q=1, q_max=0, n_rho=64, rho_max=1.0,
+                 grid_half=64, delta_s=0.1, sigma=4, taps=8, beta=10.0, margin=24.0)
+        a.update(kw)
+        return h.cfft_backproject_static(a["device"], None, a["grid"], a["table"], a["series_per_q"],
+                                         a["q_max"], a["n_rho"], a["rho_max"], a["grid_half"],
+                                         a["delta_s"], a["sigma"], a["taps"], a["beta"], a["margin"], 0)
+    for kw in ({"taps": 5}, {"taps": 14}, {"sigma": 3}, {"grid": None}, {"n_rho": 1},
+               {"rho_max": float("nan")}, {"q_max": 65}, {"device": -1}, {"delta_s": 0.0}):
+        assert call(**kw) == 1, kw                              # CFFT_ERR_ARG
