@@ -1,0 +1,91 @@
+"""The arithmetic bench.py reports beside its timings, checked on CPU with made-up
+stage times: the FP32 peak from unit counts and clock, the samples of one
+tabulation, the algorithmic work of each stage, the roofline of the dominant
+kernel and the whole-job rate of replicas."""
+import math
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import workloads  # noqa: E402
+
+
+def _info(**kw):
+    inf = {"ms_contour": 0.03, "ms_integrand": 1.25, "ms_fft": 1.51, "ms_backproject": 1.66,
+           "sub_len": 16384, "bp_taps": 12, "bp_form": 3, "work_bp_macs": 4.8e9,
+           "work_bp_stencils": 6.2e7, "work_bp_nodes": 1.0e9, "work_points": 16384 * 128.0,
+           "n_basis": 200, "n_harm": 33, "work_subffts": 25344.0, "spectra_tc": 1}
+    inf.update(kw)
+    return inf
+
+
+def test_fp32_peak_from_unit_counts():
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
+    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(80.55, abs=0.01)
+
+
+def test_table_samples_of_the_headline_workload():
+    wl = workloads.patch_m4(precision="fp32")
+    # 1 class x 16 MBF pairs x 33 harmonics x 8192 rho points
+    assert bench.table_samples(wl) == 16 * 33 * 8192
+    wl4 = workloads.patch_m4(precision="fp32", rotation_classes=4)
+    assert bench.table_samples(wl4) == 3 * 16 * 33 * 8192    # (90, 90) is derived, not tabulated
+
+
+def test_stage_flops_per_form():
+    wl = workloads.patch_m4(precision="fp32")
+    m = wl.element.n_mbf
+    fl = bench.stage_flops(_info(), wl)
+    assert fl["fft"] == pytest.approx(25344 * 5 * 16384 * 14)
+    assert fl["integrand"] == pytest.approx(16384 * 128 * (2 * 8 * 200 * m + m * m * (8 * 33 + 30)))
+    # matrix forms: 8 flops per complex MAC plus the node stencils added into the matrices
+    assert fl["backproject"] == pytest.approx(8 * 4.8e9 + (6 * 12 + 16) * 6.2e7)
+    for form in (1, 2):
+        assert bench.stage_flops(_info(bp_form=form), wl)["backproject"] == fl["backproject"]
+    # gather form: one stencil per node and series
+    assert bench.stage_flops(_info(bp_form=0), wl)["backproject"] == pytest.approx(1.0e9 * (4 * 12 + 8))
+
+
+def test_roofline_of_the_dominant_kernel():
+    wl = workloads.patch_m4(precision="fp32")
+    infos = [_info(ms_backproject=1.60), _info(ms_backproject=1.72)]
+    r = bench.roofline(infos, wl, {"sm_max_mhz": 2070.0}, None)
+    assert r["kernel"] == "backproject"                      # 1.66 ms mean, the longest stage
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    fl = bench.stage_flops(infos[-1], wl)["backproject"]
+    assert r["achieved"] == pytest.approx(fl / 1.66e-3 / 1e12)
+    assert r["peak"] == pytest.approx(bench.fp32_peak_tflops(2070.0))
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["algorithmic_flops_per_launch"] == fl
+    # DRAM traffic of the default sizes from the committed capture; none for other sizes
+    assert r["traffic"] == bench.KERNEL_DRAM_BYTES["backproject"]
+    for k, st in r["stages"].items():
+        assert st["frac"] == pytest.approx(st["tflops"] / r["peak"])
+    bench.TABLE_SIZE["n"] = 2048
+    try:
+        assert bench.roofline(infos, wl, {"sm_max_mhz": 2070.0}, None)["traffic"] is None
+    finally:
+        bench.TABLE_SIZE.clear()
+
+
+def test_whole_job_rate_counts_every_replica():
+    # 2 ranks x 4 steps x 100 units, the slowest rank took 2 s
+    assert bench.whole_job_rate(100.0, 4, 2, 2.0) == pytest.approx(400.0)
+    assert bench.whole_job_rate(100.0, 4, 1, 2.0) == pytest.approx(200.0)
+
+
+def test_peaks_fallback_is_labelled(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    p = bench.load_peaks()
+    assert p["_source"] == "fallback" and p["hbm_gbs"] == 6800.0 and p["bf16_tflops"] == 1900.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6791.0, "bf16_tflops": 1908.7}')
+    p = bench.load_peaks()
+    assert p["_source"] == "measured" and p["hbm_gbs"] == 6791.0
+    assert math.isclose(p["bf16_tflops"], 1908.7)
