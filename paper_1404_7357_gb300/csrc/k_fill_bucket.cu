@@ -772,6 +772,7 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
   const int r = tid & 127, half = tid >> 7;
   const unsigned nmask = (1u << b.nb_bits) - 1u;
   uint32_t n_commit = 0;
+  uint32_t n_issued = 0;   // products committed (thread 0)
   // Z of a tile from accumulator set `set`: this thread's pair (row r; MBF rows
   // a = 2 half, 2 half + 1) with stencil coordinate x, if ok
   auto epilogue = [&](uint32_t set, bool ok, int mm, int nn, float x) {
@@ -846,6 +847,7 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
       tc::fence_after_sync();
       fc_mma(tmem + set * kFcN, Ah, Al, Bh, Bl, kpad, sbo, idesc);
       tc::mma_commit(&mbar);
+      ++n_issued;
     }
     // while the tensor core runs this tile: the next tile's pairs, the previous tile's Z
     if (t0 + 128 < p1) fetch(t0 + 128, nx_ok, nx_m, nx_n, nx_pm, nx_pn);
@@ -866,7 +868,12 @@ __global__ void __launch_bounds__(kBThreads, 1) fill_tc_kernel(FillArgs<float, f
     have_prev = true;
   }
   if (have_prev && !s_fail) epilogue((n_commit - 1) & 1u, pv_ok, pv_m, pv_n, pv_x);
-  if (s_fail && tid == 0) atomicOr(a.err, 16);
+  if (s_fail && tid == 0) {
+    atomicOr(a.err, 16);
+    // the products whose wait ran out may still be writing tensor memory: wait for them
+    // once more (bounded) before it is released
+    if (n_issued > 0) tc::mbar_wait(&mbar, (n_issued - 1) & 1u, kTcPolls);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -922,6 +929,7 @@ __global__ void __launch_bounds__(kBThreads, 1) adjoint_tc_kernel(FillArgs<float
   const int r = tid & 127, half = tid >> 7;
   const unsigned nmask = (1u << b.nb_bits) - 1u;
   uint32_t n_commit = 0;
+  uint32_t n_issued = 0;   // products committed (thread 0)
   double theta_sum = 0.0;
   bool failed = false;
   for (unsigned t0 = p0; t0 < p1 && !failed; t0 += 128) {
@@ -951,6 +959,7 @@ __global__ void __launch_bounds__(kBThreads, 1) adjoint_tc_kernel(FillArgs<float
         tc::fence_after_sync();
         fc_mma(tmem + (uint32_t)pass * kFcN, Ah, Al, Bh, Bl, kpad, sbo, idesc);
         tc::mma_commit(&mbar);
+        ++n_issued;
       }
       // the products are done before any warp rewrites the A tile or reads the result
       if (lane == 0 && !s_fail && !tc::mbar_wait(&mbar, n_commit & 1u, kTcPolls)) atomicOr(&s_fail, 1);
@@ -1042,7 +1051,12 @@ __global__ void __launch_bounds__(kBThreads, 1) adjoint_tc_kernel(FillArgs<float
       atomicAdd(g.grad_theta, t);
     }
   }
-  if (s_fail && tid == 0) atomicOr(a.err, 16);
+  if (s_fail && tid == 0) {
+    atomicOr(a.err, 16);
+    // the products whose wait ran out may still be writing tensor memory: wait for them
+    // once more (bounded) before it is released
+    if (n_issued > 0) tc::mbar_wait(&mbar, (n_issued - 1) & 1u, kTcPolls);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
