@@ -164,3 +164,44 @@ def test_batch_backprojection_forms(torch_cuda):
             err = np.abs(got[i].astype(np.complex128) - refs[i]).max() / np.abs(refs[i]).max()
             print("bp simt", simt, "item", i, "rel err vs single", err)
             assert err < 2e-6
+
+
+@pytest.mark.slow
+def test_full_size_sweep_sampled_against_oracle(torch_cuda):
+    """The benchmarked sweep at full size -- 512 items (64 frequencies x 8 substrates),
+    contours of 4k..64k nodes, M = 4, |q| <= 16, 2048 rho points to 50 lambda0, FP32-mixed,
+    autotuned and replayed from one CUDA graph -- checked against the oracle on sampled
+    rho rows (every pair and harmonic) of three items: the coarsest contour whose height
+    sits at the cap height * rho_max = 3 (the fewest node spacings high), the largest
+    beta_max, and a low contour."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    items = workloads.sweep_items()
+    q_max, rho_max, n_rho = 16, 50.0, 2048
+    el = workloads.patch_rooftops()
+    ctx = cfft.Context(0)
+    ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+    out = torch.empty((len(items), 16, 2 * q_max + 1, n_rho), dtype=torch.complex64, device="cuda:0")
+    ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True, autotune=True)
+    ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True)  # replay
+    print("sweep batch info", ctx.batch_info())
+    x = np.array([it["height"] * rho_max for it in items])
+    ns = np.array([it["n"] for it in items])
+    bmax = np.array([it["beta_max"] for it in items])
+    small = ns <= 16384                              # keeps the oracle's share to seconds
+    capped = np.flatnonzero(small & (x > 3.0 - 1e-9))
+    picks = [int(capped[np.argmax(bmax[capped] / ns[capped])]),     # fewest node spacings high
+             int(np.flatnonzero(small)[np.argmax(bmax[small])]),
+             int(np.flatnonzero(small)[np.argmin(x[small])])]
+    rows = np.array([0, 1, 511, 1024, 1800, 2047])
+    for i in picks:
+        it = items[i]
+        wl = workloads.TableWorkload("sweep-item", workloads.Substrate(it["eps_r"], it["h"], it["k0"]), el,
+                                     workloads.ContourSpec(it["n"], it["beta_max"], it["beta_p"], it["height"]),
+                                     q_max, rho_max, n_rho, "fp32")
+        got = out[i].cpu().numpy()[..., rows][None]
+        ref, _, _ = cc.oracle_table(wl, rho_index=rows)
+        err = cc.rel_err_per_pair(got, ref).max()
+        print("sweep item %d: n %d beta_max %.1f height*rho_max %.2f  rel err %.2e" % (
+            i, it["n"], it["beta_max"], x[i], err))
+        assert err < TOL["fp32"]

@@ -3,6 +3,7 @@ properties the benchmarks and tests rely on."""
 import math
 
 import numpy as np
+import pytest
 from scipy.spatial import cKDTree
 
 import workloads
@@ -39,6 +40,9 @@ def test_sweep_items_sampling_rule_and_contours():
         assert abs(it["beta_p"] / step - round(it["beta_p"] / step)) < 1e-9   # beta_p on a cell boundary
         assert abs(it["beta_p"] - 1.3 * kd) <= step                    # beyond every pole (< k_d)
         assert it["n"] % 256 == 0 and 2.0 <= it["eps_r"] <= 10.0 and 0.02 <= it["h"] <= 0.1
+        # six node spacings, capped at height * rho_max = 3 (float32 growth exp(height * rho))
+        assert it["height"] == pytest.approx(min(6.0 * step, 3.0 / 50.0), rel=1e-12)
+        assert it["height"] * 50.0 <= 3.0 + 1e-12 and it["height"] >= 2.5 * step
     ns = {it["n"] for it in items}
     assert min(ns) >= 4096 and max(ns) <= 65536 and len(ns) > 1        # uneven contour lengths
 

@@ -205,13 +205,17 @@ def irregular_array(n_elements=10000, radius=60.0, r_min=0.5, seed=3):
 
 
 def sweep_items(n_freq=64, n_sub=8, seed=4, rho_max=50.0, oversample=3.0, f_lo=0.8, f_hi=1.2,
-                n_base=4096, n_levels=5, height_in_steps=6.0):
+                n_base=4096, n_levels=5, height_in_steps=6.0, taylor_arg_max=3.0):
     """Batched sweep: n_freq frequencies (k0 = 2 pi f, lengths in wavelengths at the band
     centre) x n_sub substrates with eps_r ~ U[2, 10], h ~ U[0.02, 0.1] (seeded).  Each item
-    gets its own contour: beta_max = 5 k_d, beta_p ~ 1.3 k_d on a cell boundary, height a
-    few node spacings, and n = n_base * 2^u with u uniform in {0 .. n_levels-1}, raised
-    until the s-period 2 pi / step covers 2 rho_max `oversample` times (the 1-D form of
-    the paper's sampling rule, Eq. 26)."""
+    gets its own contour: beta_max = 5 k_d, beta_p ~ 1.3 k_d on a cell boundary, and
+    n = n_base * 2^u with u uniform in {0 .. n_levels-1}, raised until the s-period
+    2 pi / step covers 2 rho_max `oversample` times (the 1-D form of the paper's sampling
+    rule, Eq. 26).  The height is `height_in_steps` node spacings, capped so that
+    height * rho_max <= taylor_arg_max: the contour samples enter the transform weighted
+    by exp(beta_I s), up to exp(height * rho_max) at the largest distance, so their float32
+    rounding grows by that factor (the small-gamma condition of the Taylor expansion,
+    Section III-B-3).  On the coarsest contours the cap leaves about 2.9 spacings."""
     rng = np.random.default_rng(seed)
     eps = rng.uniform(2.0, 10.0, n_sub)
     hs = rng.uniform(0.02, 0.1, n_sub)
@@ -228,5 +232,6 @@ def sweep_items(n_freq=64, n_sub=8, seed=4, rho_max=50.0, oversample=3.0, f_lo=0
             step = beta_max / n
             items.append({"eps_r": float(eps[si]), "h": float(hs[si]), "k0": k0, "n": int(n),
                           "beta_max": beta_max, "beta_p": round(1.3 * kd / step) * step,
-                          "height": height_in_steps * step, "taylor_order": -1})
+                          "height": min(height_in_steps * step, taylor_arg_max / rho_max),
+                          "taylor_order": -1})
     return items
