@@ -357,9 +357,10 @@ def bench_fill(torch, cfft, args, dev):
     return res
 
 
-def bench_batch(torch, cfft, args, dev):
+def bench_batch(torch, cfft, args, dev, check=False):
     """Batched sweep: 64 frequencies x 8 substrates, contours of 4k..64k samples, patch
-    element (M = 4), |q| <= 16, 2048 rho points to 50 lambda0, FP32-mixed, one CUDA graph."""
+    element (M = 4), |q| <= 16, 2048 rho points to 50 lambda0, FP32-mixed, one CUDA graph.
+    check: afterwards, one benchmarked item against the oracle (sweep_parity)."""
     items = workloads.sweep_items()
     q_max, rho_max, n_rho = 16, 50.0, 2048
     el = table_workload().element
@@ -380,13 +381,45 @@ def bench_batch(torch, cfft, args, dev):
     info = ctx.batch_info()
     samples = len(items) * 16 * (2 * q_max + 1) * n_rho
     ns = [it["n"] for it in items]
-    return {"metric": "C-FFT table samples/s (batched sweep)", "value": samples * steps / sum(times),
-            "unit": "samples/s", "ms_per_sweep": 1e3 * sum(times) / steps,
-            "ms_graph_replay": info["ms_graph"], "first_call_s": first_s,
-            "workload": "64 frequencies (0.8..1.2) x 8 substrates (eps_r U[2,10], h U[0.02,0.1]); "
-                        "contours n in [%d, %d] (mean %.0f); M=4; |q|<=16; %d rho points to %g lambda0; "
-                        "FP32-mixed; one CUDA graph" % (min(ns), max(ns), np.mean(ns), n_rho, rho_max),
-            "info": info}
+    res = {"metric": "C-FFT table samples/s (batched sweep)", "value": samples * steps / sum(times),
+           "unit": "samples/s", "ms_per_sweep": 1e3 * sum(times) / steps,
+           "ms_graph_replay": info["ms_graph"], "first_call_s": first_s,
+           "workload": "64 frequencies (0.8..1.2) x 8 substrates (eps_r U[2,10], h U[0.02,0.1]); "
+                       "contours n in [%d, %d] (mean %.0f); heights min(6 spacings, 3/rho_max); M=4; "
+                       "|q|<=16; %d rho points to %g lambda0; FP32-mixed; one CUDA graph"
+                       % (min(ns), max(ns), np.mean(ns), n_rho, rho_max),
+           "info": info}
+    if check:
+        try:
+            res["parity"] = sweep_parity(out, items, q_max, rho_max, n_rho, el)
+        except Exception as e:   # the timing stands; say why the check did not run
+            res["parity"] = {"error": repr(e)[:300]}
+    return res
+
+
+def sweep_parity(out, items, q_max, rho_max, n_rho, el):
+    """The benchmarked sweep's item with the highest capped contour and the widest node
+    spacing (the largest float32 growth exp(H rho)) against the oracle on three rho rows,
+    every pair and harmonic: max over pairs of max |err| / max |oracle|."""
+    x = np.array([it["height"] * rho_max for it in items])
+    ns = np.array([it["n"] for it in items])
+    bmax = np.array([it["beta_max"] for it in items])
+    cand = np.flatnonzero(x >= x.max() - 1e-9)
+    i = int(cand[np.argmax(bmax[cand] / ns[cand])])
+    it = items[i]
+    wl = workloads.TableWorkload("sweep-item", workloads.Substrate(it["eps_r"], it["h"], it["k0"]), el,
+                                 workloads.ContourSpec(it["n"], it["beta_max"], it["beta_p"], it["height"]),
+                                 q_max, rho_max, n_rho, "fp32")
+    rows = np.array([0, n_rho // 2, n_rho - 1])
+    t0 = time.perf_counter()
+    ref = oracle_sample(wl, rows, max(1, min(32, os.cpu_count() or 1)))
+    dt = time.perf_counter() - t0
+    got = out[i].cpu().numpy()[..., rows].astype(np.complex128)
+    err = (np.abs(got - ref).reshape(ref.shape[0], -1).max(-1) /
+           np.abs(ref).reshape(ref.shape[0], -1).max(-1))
+    return {"max_rel_err_vs_oracle": float(err.max()), "tolerance": 1e-5, "item": i,
+            "n": int(it["n"]), "height_times_rho_max": float(x[i]), "rows": rows.tolist(),
+            "oracle_s": dt}
 
 
 def bench_grad(torch, cfft, args, dev):
@@ -540,7 +573,8 @@ def run_cfft(args):
     e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
     fp64 = None if args.skip_fp64 else bench_fp64(torch, cfft, args, dev)
     fill = None if args.skip_fill else bench_fill(torch, cfft, args, dev)
-    batch = None if args.skip_batch else bench_batch(torch, cfft, args, dev)
+    batch = None if args.skip_batch else bench_batch(
+        torch, cfft, args, dev, check=(rank == 0 and world == 1 and not args.skip_cpu))
     grad = None if args.skip_grad else bench_grad(torch, cfft, args, dev)
     launches = int(sum(i["launches"] for i in infos))
     line = {"metric": "C-FFT table samples/s", "value": value, "unit": "samples/s",

@@ -1,7 +1,8 @@
 """The arithmetic bench.py reports beside its timings, checked on CPU with made-up
 stage times: the FP32 peak from unit counts and clock, the samples of one
 tabulation, the algorithmic work of each stage, the roofline of the dominant
-kernel and the whole-job rate of replicas."""
+kernel, the whole-job rate of replicas and the indexing of the sweep's sampled
+parity check."""
 import math
 import os
 import sys
@@ -11,6 +12,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
 
 import bench  # noqa: E402
 import workloads  # noqa: E402
@@ -89,3 +92,32 @@ def test_peaks_fallback_is_labelled(tmp_path, monkeypatch):
     p = bench.load_peaks()
     assert p["_source"] == "measured" and p["hbm_gbs"] == 6791.0
     assert math.isclose(p["bf16_tflops"], 1908.7)
+
+
+def test_sweep_parity_compares_the_benchmarked_rows(monkeypatch):
+    """sweep_parity picks the capped item with the widest node spacing and compares the
+    tables it was given on the rows it asked the oracle for (the oracle is replaced by a
+    stand-in here; only the indexing and the error measure are checked)."""
+    import torch
+    items = workloads.sweep_items(n_freq=4, n_sub=2, seed=4)
+    q_max, rho_max, n_rho = 1, 50.0, 64
+    rng = np.random.default_rng(1)
+    table = rng.standard_normal((len(items), 16, 2 * q_max + 1, n_rho)) + 0j
+    seen = {}
+
+    def fake_oracle(wl, rows, workers):
+        seen["n"], seen["rows"] = wl.contour.n, list(rows)
+        i = [k for k, it in enumerate(items) if it["n"] == wl.contour.n and
+             it["beta_max"] == wl.contour.beta_max][0]
+        ref = table[i][..., rows].copy()
+        ref[3, 1, 2] += 1e-3 * np.abs(ref[3]).max()          # one planted difference
+        return ref
+    monkeypatch.setattr(bench, "oracle_sample", fake_oracle)
+    out = torch.tensor(table.astype(np.complex64))
+    r = bench.sweep_parity(out, items, q_max, rho_max, n_rho, workloads.patch_rooftops())
+    x = np.array([it["height"] * rho_max for it in items])
+    spacing = np.array([it["beta_max"] / it["n"] for it in items])
+    assert x[r["item"]] == pytest.approx(x.max())
+    assert spacing[r["item"]] == max(spacing[x >= x.max() - 1e-9])
+    assert seen["rows"] == [0, n_rho // 2, n_rho - 1] and seen["n"] == items[r["item"]]["n"]
+    assert r["max_rel_err_vs_oracle"] == pytest.approx(1e-3, rel=1e-3)
