@@ -163,6 +163,11 @@ cfft_status cfft_set_mbf_spectra(cfft_ctx* ctx, int n_basis, const double* cente
  * taylor_order is the highest power N_t kept in the Taylor expansion of the
  * contour factor (Eq. 22); -1 chooses it from the precision's tolerance and
  * the largest rho of the table at tabulation time.
+ * Accuracy: the samples enter the transform weighted by up to
+ * exp(height * rho_max), so their rounding grows by that factor; for the
+ * 1e-5 target of CFFT_FP32_MIXED keep height * rho_max <= 3 (and height a few
+ * node spacings beta_max / n, so that the rectangle rule stays accurate next
+ * to the poles).
  * Limits: 16 <= n <= 1048576; 0 < beta_p < beta_max; height >= 0;
  * -1 <= taylor_order <= 64.  Requires a substrate (else CFFT_ERR_STATE). */
 cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double beta_p,
