@@ -104,6 +104,36 @@ def test_fill_small_array(torch_cuda, precision):
     assert err < TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("case", ["one", "two", "three"])
+def test_fill_smallest_arrays(torch_cuda, precision, case):
+    """Degenerate arrays: one element (its self block only, rho = 0), two and three
+    elements with mixed rotations; every entry against the oracle's exact fill (FP32:
+    the tensor-core form, one stencil cell per CTA and a ragged tile of pairs)."""
+    torch = torch_cuda
+    pos, rot = {"one": ([[0.3, -0.2]], [1]),
+                "two": ([[0.0, 0.0], [1.7, 2.1]], [0, 1]),
+                "three": ([[0.0, 0.0], [0.6, 0.0], [-2.0, 3.5]], [1, 0, 1])}[case]
+    pos, rot = np.array(pos, dtype=np.float64), np.array(rot, dtype=np.int32)
+    wl = cc.small_patch(precision, n=1024, n_rho=512, rho_max=5.0, q_max=4, rotation_classes=4)
+    ctx, _ = cc.gpu_table(wl)
+    a, m = len(pos), wl.element.n_mbf
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    z = torch.full((a * m, a * m), complex(float("nan"), 0.0), dtype=dt, device="cuda:0")
+    ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), torch.tensor(rot, device="cuda:0"), z)
+    got = z.cpu().numpy()
+    assert np.isfinite(got).all()          # every entry written
+    nodes, hq = cc.oracle_harmonics(wl, classes=(0, 1, 2, 3))
+    pairs = [(i, j) for i in range(a) for j in range(a)]
+    ref = cc.oracle_fill_entries(wl, hq, nodes, pos, rot, pairs)
+    refm = np.zeros((a * m, a * m), dtype=np.complex128)
+    for (i, j), blk in zip(pairs, ref):
+        refm[i * m:(i + 1) * m, j * m:(j + 1) * m] = blk
+    err = np.abs(got - refm).max() / np.abs(refm).max()
+    print(precision, case, "fill form", ctx.info()["fill_form"], "rel err", err)
+    assert err < TOL[precision]
+
+
 def test_fill_host_variant_matches_device(torch_cuda):
     torch = torch_cuda
     wl = cc.small_patch("fp32", n=1024, n_rho=512, rho_max=5.0, q_max=2)
