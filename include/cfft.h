@@ -36,6 +36,11 @@
  *     non-zero cfft_status and cfft_last_error() describes it; the context
  *     stays usable unless the status is CFFT_ERR_CUDA from a sticky device
  *     error.
+ *   - Threads: a context is not safe for concurrent calls (its buffers,
+ *     scratch, error message and captured graph are shared); use one context
+ *     per host thread, or serialise the calls.  Distinct contexts are
+ *     independent, except that cfft_backproject_static shares one scratch
+ *     array per device (see there).
  */
 #ifndef CFFT_H
 #define CFFT_H
