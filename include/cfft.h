@@ -270,7 +270,11 @@ typedef struct {
  * flags bit 0: capture the launch sequence into a CUDA graph on the first
  *              call with a given structure (items' n and Taylor orders,
  *              sizes, output buffer) and replay it on later calls, which only
- *              refresh the per-item parameters.  The batch runs on a
+ *              refresh the per-item parameters.  A call whose plan moved
+ *              anything the graph holds by value (grid widths and angular
+ *              node counts that follow the contours, launch shapes, the
+ *              library's buffer addresses) captures again instead of
+ *              replaying.  The batch runs on a
  *              library-owned stream ordered after the context's stream, so
  *              any context stream (also the legacy default one) works.
  * flags bit 1: autotune the sub-FFT length, and in FP32-mixed whether the
@@ -285,12 +289,13 @@ cfft_status cfft_tabulate_batch(cfft_ctx* ctx, int n_items, const cfft_batch_ite
 
 /* Diagnostics of the last batch: stage times of the first wave (contour +
  * integrand, FFT, back-projection), the whole graph replay, work counts,
- * chosen sub-FFT length and row chunk, waves, kernel launches, and bp_tc = 1
- * when the back-projection's products ran on the tensor cores. */
+ * chosen sub-FFT length and row chunk, waves, kernel launches, bp_tc = 1
+ * when the back-projection's products ran on the tensor cores, and the number
+ * of graph captures the context has made (a replayed call leaves it unchanged). */
 typedef struct {
   double ms_integrand, ms_fft, ms_backproject, ms_graph;
   double work_subffts, work_bp_nodes;
-  int sub_len, rchunk, waves, launches, bp_tc;
+  int sub_len, rchunk, waves, launches, bp_tc, captures;
 } cfft_batch_info;
 cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info);
 

@@ -49,7 +49,7 @@ class BatchItem(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("ms_integrand", "ms_fft", "ms_backproject", "ms_graph",
                                                 "work_subffts", "work_bp_nodes")] + \
-               [(n, ctypes.c_int) for n in ("sub_len", "rchunk", "waves", "launches", "bp_tc")]
+               [(n, ctypes.c_int) for n in ("sub_len", "rchunk", "waves", "launches", "bp_tc", "captures")]
 
 
 class Info(ctypes.Structure):

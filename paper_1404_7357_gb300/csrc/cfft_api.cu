@@ -104,7 +104,7 @@ struct cfft_ctx {
   std::map<std::string, TunedPlan> tuned;  // signature -> tuned shape
   double b_ms[4] = {0, 0, 0, 0};
   double b_work_bp = 0, b_work_fft = 0;
-  int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0, b_bp_tc = 0;
+  int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0, b_bp_tc = 0, b_captures = 0;
   // tensor-core spectra: float copies of the element and its GEMM B operand
   DevBuf tc_bx, tc_by, tc_bmat, tc_bmat_mirror, tc_shapes;
   bool tc_ready = false;
@@ -1197,6 +1197,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       CFFT_CUDA(e, "graph instantiate");
       ctx->bsig = sig;
       ctx->bshape = shape;
+      ++ctx->b_captures;
     } else {
       CFFT_CUDA(issue(), "batch launch");
     }
@@ -1599,6 +1600,7 @@ cfft_status cfft_get_batch_info(const cfft_ctx* ctx, cfft_batch_info* info) {
   info->waves = ctx->b_waves;
   info->launches = ctx->b_launches;
   info->bp_tc = ctx->b_bp_tc;
+  info->captures = ctx->b_captures;
   return CFFT_OK;
 }
 

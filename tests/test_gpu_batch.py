@@ -79,11 +79,13 @@ def test_batch_graph_replay_tracks_new_parameters(torch_cuda):
     ctx.set_option(cfft.OPT_N_ALPHA, 128)
     out = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, graph=True)
     first = out.cpu().numpy().copy()
+    assert ctx.batch_info()["captures"] == 1
     # same structure, new substrates: the captured graph is replayed on refreshed parameters
     for it in items:
         it["h"] *= 1.1
     out = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True)
     second = out.cpu().numpy()
+    assert ctx.batch_info()["captures"] == 1      # replayed, not captured again
     assert np.abs(second - first).max() > 1e-3 * np.abs(first).max()
     for i, it in enumerate(items):
         ref = _single(cfft, el, it, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, 128)
@@ -113,6 +115,7 @@ def test_batch_graph_recaptured_when_the_contours_change(torch_cuda):
     ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
     ctx.set_option(cfft.OPT_N_ALPHA, 128)
     out = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, graph=True)
+    assert ctx.batch_info()["captures"] == 1
     for it in items:
         kd = it["k0"] * np.sqrt(it["eps_r"])
         it["beta_max"] = 5.25 * kd
@@ -120,6 +123,7 @@ def test_batch_graph_recaptured_when_the_contours_change(torch_cuda):
         it["beta_p"] = round(1.3 * kd / step) * step
         it["height"] = 6.0 * step
     out = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, out=out, graph=True)
+    assert ctx.batch_info()["captures"] == 2      # the plan moved: captured again
     got = out.cpu().numpy()
     for i, it in enumerate(items):
         ref = _single(cfft, el, it, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, 128)
