@@ -330,6 +330,16 @@ cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_
                                const int* rot, const void* grad_z, int64_t ld,
                                int grad_complex128, double* grad_pos, double* grad_eps_h);
 
+/* The same adjoint for the array objective L = sum_i |(Z' v - t)_i|^2 (no
+ * counterpart in the paper): given the excitation v and the residual
+ * r = Z' v - t (device, A*M entries each, complex128 when complex128 != 0,
+ * else complex64), dL/dZ' = 2 r v^H is formed in context-owned scratch
+ * ((A*M)^2 entries, kept for the next call) and cfft_fill_backward runs on it;
+ * outputs and errors as there (CFFT_ERR_OOM when the scratch does not fit). */
+cfft_status cfft_fill_backward_residual(cfft_ctx* ctx, int n_elements, const double* pos_xy,
+                                        const int* rot, const void* v, const void* resid,
+                                        int complex128, double* grad_pos, double* grad_eps_h);
+
 /* Diagnostics of the last tabulation (host values): taylor order used,
  * n_alpha, sigma, FFT length, sub-FFT length, grid half-width K, back-
  * projection taps, fill taps, series count, the device time of each stage in

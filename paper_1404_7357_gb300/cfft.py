@@ -27,7 +27,8 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
-           "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table"]
+           "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table",
+           "cfft_fill_backward_residual"]
 
 
 class CfftLibraryError(ImportError):
@@ -93,6 +94,7 @@ def _load():
         "cfft_backproject_static": ([I, P, P, P, I, I, I, D, I, D, I, I, D, D, I], I),
         "cfft_get_derivative_table": ([P, I, ctypes.POINTER(P), ctypes.POINTER(L)], I),
         "cfft_fill_backward": ([P, I, P, P, P, L, I, P, P], I),
+        "cfft_fill_backward_residual": ([P, I, P, P, P, P, I, P, P], I),
         "cfft_tabulate_batch": ([P, I, ctypes.POINTER(BatchItem), I, D, I, I, P, I], I),
         "cfft_get_batch_info": ([P, ctypes.POINTER(BatchInfo)], I),
         "cfft_mbf_spectra": ([P, I, P, P], I),
@@ -304,6 +306,32 @@ class Context:
                                              precision, ctypes.c_void_p(out.data_ptr()),
                                              int(graph) | (2 if autotune else 0)))
         return out
+
+    def fill_backward_residual(self, pos, rot, v, resid, substrate=True):
+        """Adjoint for L = sum |Z' v - t|^2 from v and r = Z' v - t (cuda complex vectors of
+        A*M entries): (grad_pos (A, 2) float64, grad_eps_h (2,) float64 or None)."""
+        torch = self._torch
+        n = pos.shape[0] * int(self.n_mbf)
+        for x in (v, resid):
+            if not (x.is_cuda and x.dtype == resid.dtype and x.dtype in (torch.complex64, torch.complex128)
+                    and x.is_contiguous() and x.numel() == n):
+                raise ValueError("v and resid: contiguous CUDA complex vectors of A*M = %d entries, "
+                                 "one dtype" % n)
+        if not (pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous() and
+                tuple(pos.shape[1:]) == (2,)):
+            raise ValueError("pos must be a contiguous CUDA float64 tensor of shape (A, 2)")
+        if rot is not None and not (rot.is_cuda and rot.dtype == torch.int32 and rot.is_contiguous() and
+                                    tuple(rot.shape) == (pos.shape[0],)):
+            raise ValueError("rot must be a contiguous CUDA int32 tensor of shape (A,)")
+        grad_pos = torch.empty_like(pos)
+        g_th = torch.empty(2, dtype=torch.float64, device=pos.device) if substrate else None
+        self._check(_lib.cfft_fill_backward_residual(
+            self._h, pos.shape[0], ctypes.c_void_p(pos.data_ptr()),
+            ctypes.c_void_p(rot.data_ptr() if rot is not None else 0),
+            ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(resid.data_ptr()),
+            int(resid.dtype == torch.complex128), ctypes.c_void_p(grad_pos.data_ptr()),
+            ctypes.c_void_p(g_th.data_ptr() if g_th is not None else 0)))
+        return grad_pos, g_th
 
     def save_table(self, path):
         """Checkpoint: the current table as `path`.npy and its description as `path`.json."""

@@ -89,7 +89,7 @@ struct cfft_ctx {
   DevBuf beta_c, weight, bw, bi_rel, green_p, green_r, dp_eps, dr_eps, dp_h, dr_h;
   int channels = 1;  // 1: table; 3: table, d/d eps_r, d/d h
   DevBuf d_shapes, d_bx, d_by, d_q, d_y, d_grid, d_table, d_tw, d_cnodes, d_coff, d_cos, d_lag,
-      d_flag, d_pos, d_rot, d_zbuf, d_fill;
+      d_flag, d_pos, d_rot, d_zbuf, d_fill, d_gres;
   int tw_len = 0, tw_prec = -1;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // batched sweep: plan arrays, scratch, stream, captured graph, tuned shape
@@ -1306,7 +1306,7 @@ void cfft_destroy(cfft_ctx* ctx) {
                       &ctx->green_r, &ctx->dp_eps, &ctx->dr_eps, &ctx->dp_h, &ctx->dr_h, &ctx->d_shapes, &ctx->d_bx, &ctx->d_by, &ctx->d_q,
                       &ctx->d_y, &ctx->d_grid, &ctx->d_table, &ctx->d_tw, &ctx->d_cnodes,
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
-                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
+                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
                       &ctx->tc_bmat_mirror, &ctx->tc_shapes};
     for (DevBuf* b : bufs) b->release();
     for (auto& e : ctx->ev)
@@ -1635,6 +1635,25 @@ cfft_status cfft_fill_backward(cfft_ctx* ctx, int n_elements, const double* pos_
   if (grad_complex128)
     return fill_backward_impl<float, double>(ctx, n_elements, pos_xy, r, grad_z, ld, grad_pos, grad_eps_h);
   return fill_backward_impl<float, float>(ctx, n_elements, pos_xy, r, grad_z, ld, grad_pos, grad_eps_h);
+}
+
+cfft_status cfft_fill_backward_residual(cfft_ctx* ctx, int n_elements, const double* pos_xy, const int* rot,
+                                        const void* v, const void* resid, int complex128, double* grad_pos,
+                                        double* grad_eps_h) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (!v || !resid) return fail(ctx, CFFT_ERR_ARG, "null v or residual");
+  const int64_t n = (int64_t)n_elements * ctx->n_mbf;
+  cfft_status s = check_fill_args(ctx, n_elements, pos_xy, rot, const_cast<void*>(resid), n);
+  if (s != CFFT_OK) return s;
+  if (!grad_pos && !grad_eps_h) return fail(ctx, CFFT_ERR_ARG, "nothing to compute");
+  DeviceGuard g(ctx->device);
+  // dL/dZ' = 2 r v^H, formed in the context's scratch, then the general adjoint
+  const size_t es = complex128 ? 16 : 8;
+  CFFT_CUDA(ctx->d_gres.ensure((size_t)n * (size_t)n * es), "alloc dL/dZ'");
+  cudaError_t e = complex128 ? launch_residual_outer<double>(resid, v, (int)n, ctx->d_gres.p, ctx->stream)
+                             : launch_residual_outer<float>(resid, v, (int)n, ctx->d_gres.p, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "residual outer-product kernel");
+  return cfft_fill_backward(ctx, n_elements, pos_xy, rot, ctx->d_gres.p, n, complex128, grad_pos, grad_eps_h);
 }
 
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info) {

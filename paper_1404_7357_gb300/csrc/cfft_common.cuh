@@ -372,6 +372,9 @@ cudaError_t launch_spectra_tc(int n_points, int n_basis, int n_shape, int n_mbf,
 
 template <class T, class TG>
 cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& a, cudaStream_t s);
+// g[i][j] = 2 r_i conj(v_j), n x n row-major (dL/dZ' of sum |Z' v - t|^2 with r = Z' v - t)
+template <class T>
+cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, cudaStream_t s);
 // plan.ok: bucketed fill with `scratch` of plan.scratch bytes; else the per-row fill
 template <class T, class TO>
 cudaError_t launch_fill(const FillArgs<T, TO>& a, const FillBucketPlan& plan, void* scratch, cudaStream_t s);

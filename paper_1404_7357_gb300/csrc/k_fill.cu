@@ -19,6 +19,7 @@
 // warp touches one or two cache lines instead of 32, while every store stays
 // inside the CTA's 4 rows of the matrix (one page range, not the whole
 // matrix).  Each thread writes its M x M block as M runs of M entries.
+#include <algorithm>
 #include <type_traits>
 
 #include "cfft_common.cuh"
@@ -378,6 +379,39 @@ cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& b, cudaStream_t s) {
   fill_backward_row_kernel<T, TG><<<a.n_el, kRowThreads, smem, s>>>(b, inv_bin, bpc);
   return cudaGetLastError();
 }
+
+namespace {
+
+// dL/dZ' of the array objective L = sum_i |r_i|^2, r = Z' v - t: with
+// dL = 2 Re sum_i conj(r_i) sum_j dZ'_ij v_j = Re sum_ij conj(G_ij) dZ'_ij,
+// G_ij = 2 r_i conj(v_j) (row-major n x n, one grid-stride pass, coalesced stores)
+template <class T>
+__global__ void residual_outer_kernel(const cpx<T>* r, const cpx<T>* v, int n, cpx<T>* g) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n);
+    const int j = (int)(e - (int64_t)i * n);
+    const cpx<T> ri = r[i], vj = v[j];
+    g[e] = mk((T)2 * (ri.re * vj.re + ri.im * vj.im), (T)2 * (ri.im * vj.re - ri.re * vj.im));
+  }
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, cudaStream_t s) {
+  if (n < 1 || !r || !v || !g) return cudaErrorInvalidValue;
+  const int64_t total = (int64_t)n * n;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)152 * 16);
+  residual_outer_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(
+      reinterpret_cast<const cpx<T>*>(r), reinterpret_cast<const cpx<T>*>(v), n, reinterpret_cast<cpx<T>*>(g));
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_residual_outer<float>(const void*, const void*, int, void*, cudaStream_t);
+template cudaError_t launch_residual_outer<double>(const void*, const void*, int, void*, cudaStream_t);
 
 template cudaError_t launch_fill<float, float>(const FillArgs<float, float>&, const FillBucketPlan&, void*, cudaStream_t);
 template cudaError_t launch_fill<float, double>(const FillArgs<float, double>&, const FillBucketPlan&, void*, cudaStream_t);
