@@ -121,3 +121,20 @@ def test_sweep_parity_compares_the_benchmarked_rows(monkeypatch):
     assert spacing[r["item"]] == max(spacing[x >= x.max() - 1e-9])
     assert seen["rows"] == [0, n_rho // 2, n_rho - 1] and seen["n"] == items[r["item"]]["n"]
     assert r["max_rel_err_vs_oracle"] == pytest.approx(1e-3, rel=1e-3)
+
+
+def test_table_rel_err_per_pair_normalisation():
+    """The bench's parity figure: per MBF pair, max |err| over harmonics and sampled rows
+    over that pair's max |oracle|, then the worst pair (a torch host table or an array)."""
+    import torch
+    rng = np.random.default_rng(3)
+    table = rng.standard_normal((1, 4, 3, 50)) + 1j * rng.standard_normal((1, 4, 3, 50))
+    rows = np.array([0, 7, 49])
+    ref = table[0][..., rows].copy()
+    ref[1] *= 1e3                          # a large pair: its error counts relative to itself
+    got = table.copy()
+    got[0, 1][..., rows] = ref[1] * (1 + 1e-6)
+    got[0, 2, 0, 7] += 1e-4 * np.abs(ref[2]).max()
+    err = bench.table_rel_err(torch.tensor(got), ref, rows)
+    assert err == pytest.approx(1e-4, rel=1e-6)
+    assert bench.table_rel_err(got, ref, rows) == err
