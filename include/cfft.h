@@ -195,7 +195,9 @@ cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value);
  * rotation_classes = 4: element rotations in {0, 90 deg}; the table holds the
  * classes (test, basis) = (0,0), (0,90), (90,0), (90,90) in that order.
  * Limits: 0 <= q_max <= 64; 2 <= n_rho <= 1048576; rho_max > 0.
- * Errors: CFFT_ERR_STATE (no substrate/element/contour), CFFT_ERR_ARG,
+ * Errors: CFFT_ERR_STATE (no substrate/element/contour), CFFT_ERR_ARG (also
+ * when taylor_order is -1 and no order up to 64 meets the precision's
+ * tolerance: height * rho_max beyond about 13 in FP64, 16 in FP32-mixed),
  * CFFT_ERR_OOM, CFFT_ERR_NUMERIC (NaN/Inf produced). */
 cfft_status cfft_tabulate_reactions(cfft_ctx* ctx, int q_max, double rho_max, int n_rho,
                                     cfft_precision precision, int rotation_classes);

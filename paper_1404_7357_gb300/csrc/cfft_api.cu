@@ -152,14 +152,15 @@ int next_pow2(int v) {
 
 double lgamma_fact(int n) { return std::lgamma((double)n + 1.0); }
 
-// smallest N_t with x^(N_t+1)/(N_t+1)! e^x <= tol (remainder bound of Eq. 22)
+// smallest N_t with x^(N_t+1)/(N_t+1)! e^x <= tol (remainder bound of Eq. 22), or -1
+// when no order up to 64 reaches tol (a contour too high for the table's rho_max)
 int auto_taylor(double x, double tol) {
   if (x <= 0) return 0;
   for (int nt = 0; nt <= 64; ++nt) {
     double lg = (nt + 1) * std::log(x) - lgamma_fact(nt + 1) + x;
     if (lg <= std::log(tol)) return nt;
   }
-  return 64;
+  return -1;
 }
 
 // angular nodes of the back-projection for the largest rho of a chunk
@@ -205,6 +206,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   double margin = ctx->opt[CFFT_OPT_ALPHA_MARGIN] > 0 ? ctx->opt[CFFT_OPT_ALPHA_MARGIN] : 24.0;
   int taylor = ctx->taylor_req;
   if (taylor < 0) taylor = auto_taylor(ctx->height * ctx->rho_max, fp64 ? 1e-13 : 1e-7);
+  if (taylor < 0)
+    return fail(ctx, CFFT_ERR_ARG, "height * rho_max too large: no Taylor order up to 64 converges");
   const int64_t P = (int64_t)sigma * n;
   const double ds = 2.0 * kPi / ((double)P * step);
   const int K = (int)std::ceil(ctx->rho_max / ds) + bp_taps / 2 + 2;
@@ -737,6 +740,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     p.beta_abs = std::hypot(it.beta_max, it.height);
     p.taylor = it.taylor_order >= 0 ? it.taylor_order
                                     : auto_taylor(it.height * rho_max, fp64 ? 1e-13 : 1e-7);
+    if (p.taylor < 0)
+      return fail(ctx, CFFT_ERR_ARG, "batch item: height * rho_max too large for the Taylor expansion");
     p.P = (int64_t)sigma * it.n;
     p.ds = 2.0 * kPi / ((double)p.P * p.step);
     p.K = (int)std::ceil(rho_max / p.ds) + bp_taps / 2 + 2;
