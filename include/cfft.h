@@ -452,6 +452,14 @@ cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void* k, void* o
  * trap, fault or unbounded wait is involved.  Synchronizes the stream. */
 cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls);
 
+/* Failure-injection hook for tests (host side only; no device fault): the next
+ * `after` device allocations the library makes succeed and the one after them
+ * fails as if the device were out of memory -- no allocation is attempted, the
+ * call in progress returns CFFT_ERR_OOM, and the hook disarms itself.
+ * after < 0 disarms it.  Process-wide, for single-threaded tests only.  The
+ * context stays usable: a later call allocates what it needs again. */
+void cfft_test_fail_allocation(int after);
+
 /* Checkpoint / resume of a table (the paper's tables are reusable across array
  * layouts for a fixed substrate and element, Section IV-F): installs a table
  * saved from cfft_copy_table (layout [class][pair][q][r] of cfft_get_table,

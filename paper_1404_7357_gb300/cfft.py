@@ -28,7 +28,7 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
            "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table",
-           "cfft_fill_backward_residual"]
+           "cfft_fill_backward_residual", "cfft_test_fail_allocation"]
 
 
 class CfftLibraryError(ImportError):
@@ -95,6 +95,7 @@ def _load():
         "cfft_get_derivative_table": ([P, I, ctypes.POINTER(P), ctypes.POINTER(L)], I),
         "cfft_fill_backward": ([P, I, P, P, P, L, I, P, P], I),
         "cfft_fill_backward_residual": ([P, I, P, P, P, P, I, P, P], I),
+        "cfft_test_fail_allocation": ([I], None),
         "cfft_tabulate_batch": ([P, I, ctypes.POINTER(BatchItem), I, D, I, I, P, I], I),
         "cfft_get_batch_info": ([P, ctypes.POINTER(BatchInfo)], I),
         "cfft_mbf_spectra": ([P, I, P, P], I),
@@ -409,6 +410,12 @@ class Context:
 
     def synchronize(self):
         self._check(_lib.cfft_synchronize(self._h))
+
+
+def test_fail_allocation(after):
+    """cfft_test_fail_allocation: after `after` successful device allocations the next one
+    fails as out of memory (host-side injection; after < 0 disarms)."""
+    _lib.cfft_test_fail_allocation(int(after))
 
 
 def backproject_static(grid, table, series_per_q, q_max, rho_max, grid_half, delta_s, sigma, taps,

@@ -33,6 +33,10 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// failure injection on the host (cfft_test_fail_allocation): the number of library
+// allocations still to succeed before one fails as out of memory; -1 = disarmed
+long g_alloc_countdown = -1;
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -42,6 +46,11 @@ struct DevBuf {
     p = nullptr;
     bytes = 0;
     if (need == 0) need = 16;
+    if (g_alloc_countdown == 0) {   // injected: no allocation is attempted
+      g_alloc_countdown = -1;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_alloc_countdown > 0) --g_alloc_countdown;
     cudaError_t e = cudaMalloc(&p, need);
     if (e == cudaSuccess) bytes = need;
     return e;
@@ -1748,6 +1757,8 @@ cfft_status ensure_tc_element(cfft_ctx* ctx) {
 }
 
 }  // namespace
+
+extern "C" void cfft_test_fail_allocation(int after) { g_alloc_countdown = after < 0 ? -1 : after; }
 
 extern "C" cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls) {
   if (!ctx) return CFFT_ERR_ARG;
