@@ -155,9 +155,10 @@ def table_samples(wl):
     return classes * m * m * (2 * wl.q_max + 1) * wl.n_rho
 
 
-def oracle_sample(wl, rows, workers):
+def oracle_sample(wl, rows, workers, keep=False):
     """FP64 oracle on a bounded sample: harmonics at every contour node (needed by any
-    rho), Bessel sums for the given rows, all pairs and harmonics."""
+    rho), Bessel sums for the given rows, all pairs and harmonics.  keep: also return the
+    contour nodes and the harmonics (for further exact evaluations on the same contour)."""
     from oracle import contour as oc, reaction as orx, spectra as osp
     el = wl.element
     bs = osp.BasisSet("rooftop", el.q, cx=el.cx, cy=el.cy, direction=el.direction,
@@ -168,7 +169,8 @@ def oracle_sample(wl, rows, workers):
     hq = orx.harmonics(bs, nodes["beta_c"], wl.qs, 128, s.eps_r, s.h, s.k0, workers=workers)
     z = orx.table_bessel(hq, wl.qs, nodes["beta_c"], nodes["weight"], wl.rho[rows])
     m = el.n_mbf
-    return z.reshape(m * m, len(wl.qs), len(rows))
+    z = z.reshape(m * m, len(wl.qs), len(rows))
+    return (z, nodes, hq) if keep else z
 
 
 def run_reference(args):
@@ -353,9 +355,46 @@ def bench_fill(torch, cfft, args, dev):
         kpad = (2 * nh + 7) // 8 * 8
         res["tensor_tflops_executed"] = 3 * 2.0 * kpad * 256 * float(a) ** 2 / sec / 1e12
     res["hbm_gbs_write"] = entries * 8 / sec / 1e9
+    # element-pair blocks of rotation class (0, 0) for the oracle comparison (after timing)
+    pairs = fill_sample_pairs(pos, rot)
+    blocks = [z[m * i:m * i + m, m * j:m * j + m].cpu().numpy().astype(np.complex128) for i, j in pairs]
     del z
     torch.cuda.empty_cache()
-    return res
+    return res, (wl, pos, rot, pairs, blocks)
+
+
+def fill_sample_pairs(pos, rot, seed=91):
+    """Element pairs (test m, basis n), both unrotated, spread over the distances the fill's
+    table covers: one diagonal block and up to four pairs in each of four distance bins,
+    measured from ten anchor elements."""
+    unrot = np.flatnonzero(np.asarray(rot) == 0)
+    anchors = unrot[:10]
+    d = np.hypot(*(pos[:, None, :] - pos[None, anchors, :]).transpose(2, 0, 1))    # (A, anchors)
+    ok = (np.asarray(rot) == 0)[:, None]
+    rng = np.random.default_rng(seed)
+    pairs = [(int(anchors[0]), int(anchors[0]))]
+    for lo, hi in ((0.4, 2.0), (20.0, 40.0), (60.0, 80.0), (100.0, 121.0)):
+        cand = np.argwhere((d >= lo) & (d < hi) & ok)
+        for k in rng.choice(len(cand), size=min(4, len(cand)), replace=False):
+            pairs.append((int(cand[k][0]), int(anchors[cand[k][1]])))
+    return pairs
+
+
+def fill_parity(sample, table_wl, nodes, hq):
+    """The sampled blocks of the benchmarked fill against the oracle's exact fill (Bessel
+    sums at each pair's exact rho) with the harmonics of the table workload's contour,
+    which is the fill's own contour; max |err| over the blocks / max |oracle|."""
+    from oracle import fill as ofill
+    wl, pos, rot, pairs, blocks = sample
+    same = (wl.contour == table_wl.contour and wl.q_max == table_wl.q_max and
+            wl.substrate == table_wl.substrate)
+    if not same:
+        return {"skipped": "the fill's contour differs from the table workload's"}
+    ref = ofill.entries({0: hq}, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, pairs)
+    scale = max(np.abs(r).max() for r in ref)
+    err = max(np.abs(g - r).max() for g, r in zip(blocks, ref)) / scale
+    return {"max_rel_err_vs_oracle": float(err), "tolerance": 1e-5, "blocks": len(pairs),
+            "rotation_class": "(0, 0)"}
 
 
 def bench_batch(torch, cfft, args, dev, check=False):
@@ -572,7 +611,7 @@ def run_cfft(args):
     peaks = load_peaks()
 
     if args.only_fill:
-        fill = bench_fill(torch, cfft, args, dev)
+        fill, _ = bench_fill(torch, cfft, args, dev)
         if rank == 0:
             print(json.dumps({"fill": fill}), flush=True)
         return
@@ -582,7 +621,7 @@ def run_cfft(args):
     value = whole_job_rate(samples, args.steps, world, total_s)
     e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
     fp64, fp64_table = (None, None) if args.skip_fp64 else bench_fp64(torch, cfft, args, dev)
-    fill = None if args.skip_fill else bench_fill(torch, cfft, args, dev)
+    fill, fill_sample = (None, None) if args.skip_fill else bench_fill(torch, cfft, args, dev)
     batch = None if args.skip_batch else bench_batch(
         torch, cfft, args, dev, check=(rank == 0 and world == 1 and not args.skip_cpu))
     grad = None if args.skip_grad else bench_grad(torch, cfft, args, dev)
@@ -613,7 +652,7 @@ def run_cfft(args):
         workers = max(1, min(32, os.cpu_count() or 1))
         rows = np.linspace(0, wl.n_rho - 1, 8).astype(int)
         t0 = time.perf_counter()
-        ref = oracle_sample(wl, rows, workers)
+        ref, nodes, hq = oracle_sample(wl, rows, workers, keep=True)
         dt = time.perf_counter() - t0
         ns = ref.size
         line["cpu_baseline"] = {"value": ns / dt, "unit": "samples/s", "cores": workers,
@@ -623,6 +662,11 @@ def run_cfft(args):
                                                                                wl.n_rho, dt)}
         line["parity"] = {"max_rel_err_vs_oracle": table_rel_err(host_table, ref, rows),
                           "rows": rows.tolist(), "tolerance": 1e-5}
+        if fill_sample is not None:
+            try:   # the fill's sampled blocks against the exact fill on the same harmonics
+                line["fill"]["parity"] = fill_parity(fill_sample, wl, nodes, hq)
+            except Exception as e:
+                line["fill"]["parity"] = {"error": repr(e)[:300]}
         if fp64_table is not None:
             # the plain FP64 GPU form against the same oracle sample
             line["fp64_gpu"]["parity"] = {"max_rel_err_vs_oracle": table_rel_err(fp64_table, ref, rows),

@@ -138,3 +138,37 @@ def test_table_rel_err_per_pair_normalisation():
     err = bench.table_rel_err(torch.tensor(got), ref, rows)
     assert err == pytest.approx(1e-4, rel=1e-6)
     assert bench.table_rel_err(got, ref, rows) == err
+
+
+def test_fill_sample_pairs_cover_the_distance_bins():
+    pos, rot = workloads.irregular_array()
+    pairs = bench.fill_sample_pairs(pos, rot)
+    assert len(pairs) == 17 and pairs[0][0] == pairs[0][1]
+    d = [float(np.hypot(*(pos[i] - pos[j]))) for i, j in pairs]
+    assert all(rot[i] == 0 and rot[j] == 0 for i, j in pairs)        # class (0, 0) only
+    for b, (lo, hi) in enumerate(((0.4, 2.0), (20.0, 40.0), (60.0, 80.0), (100.0, 121.0))):
+        assert all(lo <= x < hi for x in d[1 + 4 * b:5 + 4 * b])
+    assert bench.fill_sample_pairs(pos, rot) == pairs                 # seeded
+
+
+def test_fill_parity_measure():
+    """fill_parity compares the blocks it is given with the oracle's exact fill (tiny
+    synthetic harmonics here) and refuses a fill whose contour is not the table's."""
+    from oracle import contour as oc
+    from oracle import fill as ofill
+    wl = workloads.patch_m4(n=64, n_rho=32, rho_max=5.0, q_max=2)
+    nodes = oc.contour_nodes(wl.contour.n, wl.contour.beta_max, wl.contour.beta_p, wl.contour.height)
+    rng = np.random.default_rng(5)
+    hq = rng.standard_normal((4, 4, 5, 64)) * 1e-3 + 1j * rng.standard_normal((4, 4, 5, 64)) * 1e-3
+    pos = np.array([[0.0, 0.0], [1.0, 0.5], [-2.0, 1.0]])
+    rot = np.zeros(3, dtype=np.int32)
+    pairs = [(0, 0), (0, 1), (2, 1)]
+    blocks = list(ofill.entries({0: hq}, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, pairs))
+    assert bench.fill_parity((wl, pos, rot, pairs, blocks), wl, nodes, hq)["max_rel_err_vs_oracle"] == 0.0
+    scale = max(np.abs(b).max() for b in blocks)
+    blocks[2] = blocks[2].copy()
+    blocks[2][1, 3] += 1e-4 * scale
+    r = bench.fill_parity((wl, pos, rot, pairs, blocks), wl, nodes, hq)
+    assert r["max_rel_err_vs_oracle"] == pytest.approx(1e-4, rel=1e-9) and r["blocks"] == 3
+    other = workloads.patch_m4(n=128, n_rho=32, rho_max=5.0, q_max=2)
+    assert "skipped" in bench.fill_parity((other, pos, rot, pairs, blocks), wl, nodes, hq)
