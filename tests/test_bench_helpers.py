@@ -1,8 +1,8 @@
 """The arithmetic bench.py reports beside its timings, checked on CPU with made-up
 stage times: the FP32 peak from unit counts and clock, the samples of one
 tabulation, the algorithmic work of each stage, the roofline of the dominant
-kernel, the whole-job rate of replicas and the indexing of the sweep's sampled
-parity check."""
+kernel, the whole-job rate of replicas, the sampled parity checks, and the
+assembly of the JSON line around stand-ins for the GPU stages."""
 import math
 import os
 import sys
@@ -172,3 +172,52 @@ def test_fill_parity_measure():
     assert r["max_rel_err_vs_oracle"] == pytest.approx(1e-4, rel=1e-9) and r["blocks"] == 3
     other = workloads.patch_m4(n=128, n_rho=32, rho_max=5.0, q_max=2)
     assert "skipped" in bench.fill_parity((other, pos, rot, pairs, blocks), wl, nodes, hq)
+
+
+def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
+    """run_cfft's assembly of the JSON line, on CPU: the GPU stages are replaced by
+    stand-ins that return what the real ones return (a small table workload, tables equal
+    to the oracle's, fill blocks from the oracle's exact fill), while the oracle legs run
+    for real.  Checks the keys the line must carry and that each parity entry is computed
+    on the data it names."""
+    import json
+    import types
+    import torch
+    from oracle import fill as ofill
+    from tests import cfft_cases as cc
+
+    wl = workloads.patch_m4(n=64, n_rho=32, rho_max=2.0, q_max=2)
+    ref_full, nodes, hq = cc.oracle_table(wl)
+    table = ref_full.astype(np.complex64)                       # (1, 16, 5, 32)
+    pos = np.array([[0.0, 0.0], [0.9, 0.4], [-1.0, 0.5]])
+    rot = np.zeros(3, dtype=np.int32)
+    pairs = [(0, 0), (1, 0), (2, 1)]
+    blocks = list(ofill.entries({0: hq[0]}, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, pairs))
+    infos = [dict(_info(), launches=6, n_basis=200, n_harm=5, sub_len=256) for _ in range(2)]
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(bench, "bench_tabulation",
+                        lambda *a: (wl, None, [4.5, 4.4], infos, {"sm_mhz": 2070.0, "reasons": []}))
+    monkeypatch.setattr(bench, "bench_e2e", lambda *a: ({"value": 1.0, "unit": "samples/s",
+                                                         "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1},
+                                                        torch.tensor(table)))
+    monkeypatch.setattr(bench, "bench_fp64", lambda *a: ({"metric": "fp64"}, torch.tensor(ref_full)))
+    monkeypatch.setattr(bench, "bench_fill", lambda *a: ({"algorithmic_tflops": 1.0, "tensor_tflops_executed": 2.0},
+                                                        (wl, pos, rot, pairs, blocks)))
+    monkeypatch.setattr(bench, "bench_batch", lambda *a, **k: {"metric": "batch", "parity": {"error": "n/a"}})
+    monkeypatch.setattr(bench, "bench_grad", lambda *a: {"metric": "grad"})
+    args = types.SimpleNamespace(steps=2, warmup=3, only_fill=False, skip_fp64=False, skip_fill=False,
+                                 skip_batch=False, skip_grad=False, skip_cpu=False)
+    bench.run_cfft(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "clocks", "gpu_launches",
+                "e2e", "cpu_baseline", "parity", "fp64_gpu", "fill", "batch", "grad"):
+        assert key in line, key
+    assert line["gpu_launches"] == 12 and line["steps"] == 2
+    assert line["value"] == pytest.approx(bench.table_samples(wl) * 2 / 8.9e-3)
+    assert line["parity"]["max_rel_err_vs_oracle"] < 1e-6              # complex64 copy of the oracle
+    assert line["fp64_gpu"]["parity"]["max_rel_err_vs_oracle"] == 0.0   # the oracle itself
+    assert line["fill"]["parity"]["max_rel_err_vs_oracle"] == 0.0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["roofline"]["bound"] == "alu" and 0 < line["roofline"]["frac"]
