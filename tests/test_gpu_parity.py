@@ -134,6 +134,35 @@ def test_fill_smallest_arrays(torch_cuda, precision, case):
     assert err < TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_eight_mbfs_table_and_fill(torch_cuda, precision):
+    """The largest MBF count the ABI takes (M = 8: 64 pairs, four chunks of the
+    integrand's pair loop, four series chunks per harmonic in the back-projection, the
+    per-row fill): the whole table and a small array's fill against the oracle."""
+    import dataclasses
+    torch = torch_cuda
+    wl = cc.small_patch(precision, n=1024, n_rho=256, rho_max=3.0, q_max=2)
+    el = wl.element
+    wl = dataclasses.replace(wl, element=dataclasses.replace(el, q=workloads.complex_normal((el.q.shape[0], 8), 81)))
+    assert wl.element.n_mbf == 8
+    ctx, got = cc.gpu_table(wl)
+    ref, nodes, hq = cc.oracle_table(wl)
+    err = cc.rel_err_per_pair(got, ref).max()
+    pos = workloads.poisson_disc(5, 1.2, 0.5, seed=82)
+    a, m = len(pos), 8
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    z = torch.zeros((a * m, a * m), dtype=dt, device="cuda:0")
+    ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), None, z)
+    pairs = [(i, j) for i in range(a) for j in range(a)]
+    blocks = cc.oracle_fill_entries(wl, hq, nodes, pos, np.zeros(a, dtype=np.int32), pairs)
+    zref = np.zeros((a * m, a * m), dtype=np.complex128)
+    for (i, j), blk in zip(pairs, blocks):
+        zref[i * m:(i + 1) * m, j * m:(j + 1) * m] = blk
+    ferr = np.abs(z.cpu().numpy() - zref).max() / np.abs(zref).max()
+    print(precision, "M = 8: table rel err", err, "fill rel err", ferr, "fill form", ctx.info()["fill_form"])
+    assert err < TOL[precision] and ferr < TOL[precision]
+
+
 def test_fill_host_variant_matches_device(torch_cuda):
     torch = torch_cuda
     wl = cc.small_patch("fp32", n=1024, n_rho=512, rho_max=5.0, q_max=2)
