@@ -397,10 +397,10 @@ def fill_parity(sample, table_wl, nodes, hq):
             "rotation_class": "(0, 0)"}
 
 
-def bench_batch(torch, cfft, args, dev, check=False):
+def bench_batch(torch, cfft, args, dev):
     """Batched sweep: 64 frequencies x 8 substrates, contours of 4k..64k samples, patch
     element (M = 4), |q| <= 16, 2048 rho points to 50 lambda0, FP32-mixed, one CUDA graph.
-    check: afterwards, one benchmarked item against the oracle (sweep_parity)."""
+    Also returns the sampled rows of one item for the oracle comparison (sweep_sample)."""
     items = workloads.sweep_items()
     q_max, rho_max, n_rho = 16, 50.0, 2048
     el = table_workload().element
@@ -429,18 +429,13 @@ def bench_batch(torch, cfft, args, dev, check=False):
                        "|q|<=16; %d rho points to %g lambda0; FP32-mixed; one CUDA graph"
                        % (min(ns), max(ns), np.mean(ns), n_rho, rho_max),
            "info": info}
-    if check:
-        try:
-            res["parity"] = sweep_parity(out, items, q_max, rho_max, n_rho, el)
-        except Exception as e:   # the timing stands; say why the check did not run
-            res["parity"] = {"error": repr(e)[:300]}
-    return res
+    return res, sweep_sample(out, items, q_max, rho_max, n_rho, el)
 
 
-def sweep_parity(out, items, q_max, rho_max, n_rho, el):
+def sweep_sample(out, items, q_max, rho_max, n_rho, el):
     """The benchmarked sweep's item with the highest capped contour and the widest node
-    spacing (the largest float32 growth exp(H rho)) against the oracle on three rho rows,
-    every pair and harmonic: max over pairs of max |err| / max |oracle|."""
+    spacing (the largest float32 growth exp(H rho)): its workload and three of its table
+    rows (host copies, every pair and harmonic) for the comparison with the oracle."""
     x = np.array([it["height"] * rho_max for it in items])
     ns = np.array([it["n"] for it in items])
     bmax = np.array([it["beta_max"] for it in items])
@@ -451,15 +446,21 @@ def sweep_parity(out, items, q_max, rho_max, n_rho, el):
                                  workloads.ContourSpec(it["n"], it["beta_max"], it["beta_p"], it["height"]),
                                  q_max, rho_max, n_rho, "fp32")
     rows = np.array([0, n_rho // 2, n_rho - 1])
+    got = np.asarray(out[i].cpu())[..., rows].astype(np.complex128)
+    return {"item": i, "wl": wl, "rows": rows, "got": got, "height_times_rho_max": float(x[i])}
+
+
+def sweep_parity(sample, workers):
+    """The sampled sweep rows against the oracle: max over pairs of max |err| / max |oracle|."""
     t0 = time.perf_counter()
-    ref = oracle_sample(wl, rows, max(1, min(32, os.cpu_count() or 1)))
+    ref = oracle_sample(sample["wl"], sample["rows"], workers)
     dt = time.perf_counter() - t0
-    got = out[i].cpu().numpy()[..., rows].astype(np.complex128)
+    got = sample["got"]
     err = (np.abs(got - ref).reshape(ref.shape[0], -1).max(-1) /
            np.abs(ref).reshape(ref.shape[0], -1).max(-1))
-    return {"max_rel_err_vs_oracle": float(err.max()), "tolerance": 1e-5, "item": i,
-            "n": int(it["n"]), "height_times_rho_max": float(x[i]), "rows": rows.tolist(),
-            "oracle_s": dt}
+    return {"max_rel_err_vs_oracle": float(err.max()), "tolerance": 1e-5, "item": sample["item"],
+            "n": int(sample["wl"].contour.n), "height_times_rho_max": sample["height_times_rho_max"],
+            "rows": sample["rows"].tolist(), "oracle_s": dt}
 
 
 def bench_grad(torch, cfft, args, dev):
@@ -622,8 +623,7 @@ def run_cfft(args):
     e2e, host_table = bench_e2e(torch, cfft, args, dev, wl)
     fp64, fp64_table = (None, None) if args.skip_fp64 else bench_fp64(torch, cfft, args, dev)
     fill, fill_sample = (None, None) if args.skip_fill else bench_fill(torch, cfft, args, dev)
-    batch = None if args.skip_batch else bench_batch(
-        torch, cfft, args, dev, check=(rank == 0 and world == 1 and not args.skip_cpu))
+    batch, batch_sample = (None, None) if args.skip_batch else bench_batch(torch, cfft, args, dev)
     grad = None if args.skip_grad else bench_grad(torch, cfft, args, dev)
     launches = int(sum(i["launches"] for i in infos))
     line = {"metric": "C-FFT table samples/s", "value": value, "unit": "samples/s",
@@ -662,6 +662,11 @@ def run_cfft(args):
                                                                                wl.n_rho, dt)}
         line["parity"] = {"max_rel_err_vs_oracle": table_rel_err(host_table, ref, rows),
                           "rows": rows.tolist(), "tolerance": 1e-5}
+        if batch_sample is not None:
+            try:   # one benchmarked sweep item against the oracle on three rows
+                line["batch"]["parity"] = sweep_parity(batch_sample, workers)
+            except Exception as e:
+                line["batch"]["parity"] = {"error": repr(e)[:300]}
         if fill_sample is not None:
             try:   # the fill's sampled blocks against the exact fill on the same harmonics
                 line["fill"]["parity"] = fill_parity(fill_sample, wl, nodes, hq)

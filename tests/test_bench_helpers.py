@@ -114,7 +114,8 @@ def test_sweep_parity_compares_the_benchmarked_rows(monkeypatch):
         return ref
     monkeypatch.setattr(bench, "oracle_sample", fake_oracle)
     out = torch.tensor(table.astype(np.complex64))
-    r = bench.sweep_parity(out, items, q_max, rho_max, n_rho, workloads.patch_rooftops())
+    sample = bench.sweep_sample(out, items, q_max, rho_max, n_rho, workloads.patch_rooftops())
+    r = bench.sweep_parity(sample, 1)
     x = np.array([it["height"] * rho_max for it in items])
     spacing = np.array([it["beta_max"] / it["n"] for it in items])
     assert x[r["item"]] == pytest.approx(x.max())
@@ -204,7 +205,9 @@ def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
     monkeypatch.setattr(bench, "bench_fp64", lambda *a: ({"metric": "fp64"}, torch.tensor(ref_full)))
     monkeypatch.setattr(bench, "bench_fill", lambda *a: ({"algorithmic_tflops": 1.0, "tensor_tflops_executed": 2.0},
                                                         (wl, pos, rot, pairs, blocks)))
-    monkeypatch.setattr(bench, "bench_batch", lambda *a, **k: {"metric": "batch", "parity": {"error": "n/a"}})
+    monkeypatch.setattr(bench, "bench_batch", lambda *a: ({"metric": "batch"}, {
+        "item": 0, "wl": wl, "rows": np.array([0, 16, 31]), "got": ref_full[0][..., [0, 16, 31]],
+        "height_times_rho_max": 0.1}))
     monkeypatch.setattr(bench, "bench_grad", lambda *a: {"metric": "grad"})
     args = types.SimpleNamespace(steps=2, warmup=3, only_fill=False, skip_fp64=False, skip_fill=False,
                                  skip_batch=False, skip_grad=False, skip_cpu=False)
@@ -219,5 +222,6 @@ def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
     assert line["parity"]["max_rel_err_vs_oracle"] < 1e-6              # complex64 copy of the oracle
     assert line["fp64_gpu"]["parity"]["max_rel_err_vs_oracle"] == 0.0   # the oracle itself
     assert line["fill"]["parity"]["max_rel_err_vs_oracle"] == 0.0
+    assert line["batch"]["parity"]["max_rel_err_vs_oracle"] < 1e-10
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["roofline"]["bound"] == "alu" and 0 < line["roofline"]["frac"]
