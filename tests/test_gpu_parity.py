@@ -38,6 +38,23 @@ def test_strip_fp64_full_table(torch_cuda):
     assert err.max() < TOL["fp64"]
 
 
+@pytest.mark.parametrize("bp_simt", [0, 1])
+def test_strip_fp32_single_series(torch_cuda, bp_simt):
+    """The strip (M = 1) in FP32-mixed: one series per harmonic, so the back-projection's
+    16-series chunk is mostly empty (tensor-core products and FP32-pipe products), and
+    the SIMT spectra of a non-rooftop element; the whole table against the oracle."""
+    import dataclasses
+    from paper_1404_7357_gb300 import cfft
+    wl = dataclasses.replace(workloads.strip_fp64(n=1024, n_rho=512, rho_max=8.0), precision="fp32")
+    ctx, got = cc.gpu_table(wl, options={cfft.OPT_BP_SIMT: bp_simt})
+    ref, _, _ = cc.oracle_table(wl)
+    err = cc.rel_err_per_pair(got, ref).max()
+    info = ctx.info()
+    print("strip fp32 bp_simt", bp_simt, "bp form", info["bp_form"], "rel err", err)
+    assert info["bp_form"] == (2 if bp_simt else 3)
+    assert err < TOL["fp32"]
+
+
 def test_strip_fp64_stages(torch_cuda):
     wl = workloads.strip_fp64(n=1024, n_rho=256, rho_max=10.0)
     ctx, got = cc.gpu_table(wl)
