@@ -132,6 +132,32 @@ def test_batch_graph_recaptured_when_the_contours_change(torch_cuda):
         assert err < TOL["fp32"]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_strip_matches_single_tabulations(torch_cuda, precision):
+    """A batch of the strip element (M = 1: one series per harmonic, SIMT spectra) against
+    single tabulations of the same items."""
+    from paper_1404_7357_gb300 import cfft
+    prec = cfft.CFFT_FP64 if precision == "fp64" else cfft.CFFT_FP32_MIXED
+    el = workloads.strip_element()
+    items = _items(3, seed=17)
+    q_max, rho_max, n_rho = 3, 3.0, 200
+    ctx = cfft.Context(0)
+    ctx.set_mbf_spectra_strip(el.length, el.strip_width)
+    ctx.set_option(cfft.OPT_N_ALPHA, 128)
+    got = ctx.tabulate_batch(items, q_max, rho_max, n_rho, prec, graph=True).cpu().numpy()
+    for i, it in enumerate(items):
+        one = cfft.Context(0)
+        one.set_substrate(it["eps_r"], it["h"], it["k0"])
+        one.set_mbf_spectra_strip(el.length, el.strip_width)
+        one.build_contour(it["n"], it["beta_max"], it["beta_p"], it["height"], -1)
+        one.set_option(cfft.OPT_N_ALPHA, 128)
+        one.tabulate_reactions(q_max, rho_max, n_rho, prec, 1)
+        ref = one.copy_table(host=True).numpy()[0]
+        err = np.abs(got[i].astype(np.complex128) - ref).max() / np.abs(ref).max()
+        print(precision, "strip batch item", i, "rel err vs single", err)
+        assert err < TOL[precision]
+
+
 def test_batch_item_against_oracle(torch_cuda):
     from paper_1404_7357_gb300 import cfft
     el = workloads.patch_rooftops()
