@@ -3,7 +3,9 @@
 Each test plants one mistake in the oracle (on the CPU, through monkeypatch)
 -- a dropped contour Jacobian, a flipped off-diagonal Green's term, a
 conjugate on the wrong side, a (+i)^q instead of (-i)^q, a transposed
-rotation, a wrong free-space branch -- and checks that the quantity the
+rotation, a wrong free-space branch, a reversed separation vector, a diagonal
+Green's term copied from the other, a dropped radial measure, the opposite
+sign of the harmonic transform -- and checks that the quantity the
 corresponding pin asserts moves far outside that pin's tolerance.
 """
 import math
@@ -164,3 +166,33 @@ def test_wrong_free_space_branch_is_caught(monkeypatch):
     monkeypatch.setattr(green, "_branch_sqrt_free", lambda w: 1j * np.sqrt(np.asarray(w, dtype=np.complex128)))
     bc = np.array([0.5, 1.5]) * K0 + 0.05j
     assert np.any(green.kz_free(bc ** 2, K0).imag > 0)   # the radiation-condition pin fails
+
+
+def test_reversed_separation_is_caught(monkeypatch):
+    # Delta = r_basis - r_test instead of r_test - r_basis: phi -> phi + pi
+    orig = reaction.reaction_from_table
+    monkeypatch.setattr(reaction, "reaction_from_table", lambda zq, qs, phi: orig(zq, qs, phi + math.pi))
+    assert gaussian_2d_error() > 1e-2
+
+
+def test_copied_diagonal_green_term_is_caught(monkeypatch):
+    # Gyy written as a copy of Gxx (kx where ky belongs)
+    orig = green.dyadic_green
+    monkeypatch.setattr(green, "dyadic_green",
+                        lambda kx, ky, e, h, k0: (lambda g: (g[0], g[1], g[0]))(orig(kx, ky, e, h, k0)))
+    assert rotational_covariance_error() > 1e-3
+
+
+def test_dropped_radial_measure_is_caught(monkeypatch):
+    # the beta of beta d beta left out of the radial quadrature
+    orig = reaction.table_bessel
+    monkeypatch.setattr(reaction, "table_bessel",
+                        lambda hq, qs, beta_c, weight, rho: orig(np.asarray(hq) / beta_c, qs, beta_c, weight, rho))
+    assert gaussian_hankel_error() > 1e-3
+
+
+def test_harmonic_sign_convention_is_caught(monkeypatch):
+    # H_q taken with exp(+i q alpha) instead of exp(-i q alpha): q -> -q (the q list is symmetric)
+    orig = reaction.harmonics
+    monkeypatch.setattr(reaction, "harmonics", lambda *a, **k: orig(*a, **k)[..., ::-1, :])
+    assert gaussian_2d_error() > 1e-2
