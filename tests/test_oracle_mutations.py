@@ -196,3 +196,74 @@ def test_harmonic_sign_convention_is_caught(monkeypatch):
     orig = reaction.harmonics
     monkeypatch.setattr(reaction, "harmonics", lambda *a, **k: orig(*a, **k)[..., ::-1, :])
     assert gaussian_2d_error() > 1e-2
+
+
+def gaussian_array_error():
+    """Reduced matrix of a 3-element array of x- and y-directed Gaussian currents
+    (rotations 0/90) under a unit dyadic vs its closed form (the pin of
+    test_oracle_fill.py, one resolution)."""
+    from oracle import fill
+    s = 0.1
+    cs = np.array([[0.04, -0.02], [-0.03, 0.05]])
+    dirs = np.array([[1.0, 0.0], [0.0, 1.0]])
+    bs = spectra.BasisSet("gaussian", np.eye(2), cx=cs[:, 0], cy=cs[:, 1], direction=np.array([0, 1]), s=s)
+    pos = np.array([[0.0, 0.0], [0.25, 0.1], [-0.12, 0.3]])
+    rot = np.array([0, 1, 0])
+    qs = np.arange(-16, 17)
+    c = contour.contour_nodes(2000, 60.0, 12.0, 0.4)
+    hq = {cls: reaction.harmonics(bs, c["beta_c"], qs, 96, 0, 0, K0, *reaction.rotation_angles(cls),
+                                  green_fn=green.identity_green) for cls in range(4)}
+    z = fill.full_matrix(hq, qs, c["beta_c"], c["weight"], pos, rot)
+
+    def rmat(t):
+        return np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]])
+    exact = np.empty_like(z)
+    for m in range(3):
+        for n in range(3):
+            tm, tn = rot[m] * math.pi / 2, rot[n] * math.pi / 2
+            for a in range(2):
+                for b in range(2):
+                    d = pos[m] - pos[n] + rmat(tm) @ cs[a] - rmat(tn) @ cs[b]
+                    align = (rmat(tm) @ dirs[a]) @ (rmat(tn) @ dirs[b])
+                    exact[2 * m + a, 2 * n + b] = align * math.exp(-d @ d / (8 * s * s)) / (8 * math.pi * s * s)
+    return np.abs(z - exact).max() * 8 * math.pi * s * s
+
+
+def rooftop_error():
+    """Closed-form rooftop transform vs Gauss-Legendre quadrature of the current (pin: 1e-12)."""
+    from tests.test_oracle_spectra import brute_rooftop
+    worst = 0.0
+    for kx, ky in ((3.1, -2.2), (12.0, 7.5), (40.0 + 0.3j, -25.0 + 0.1j)):
+        got = spectra.rooftop_ft(kx, ky, 0.12, -0.07, 0, 0.05, 0.03)
+        ref = brute_rooftop(kx, ky, 0.12, -0.07, 0, 0.05, 0.03)
+        worst = max(worst, abs(got - ref) / abs(ref))
+    return worst
+
+
+def test_unmutated_fill_and_rooftop_meet_their_pins():
+    assert gaussian_array_error() < 1e-4      # one resolution: O(h^2) quadrature error
+    assert rooftop_error() < 1e-10
+
+
+def test_swapped_rotation_class_is_caught(monkeypatch):
+    from oracle import fill
+    monkeypatch.setattr(fill, "class_index", lambda rot, m, n: 2 * int(rot[n]) + int(rot[m]))
+    assert gaussian_array_error() > 1e-2
+
+
+def test_swapped_pair_geometry_is_caught(monkeypatch):
+    from oracle import fill
+    orig = fill.pair_geometry
+    monkeypatch.setattr(fill, "pair_geometry", lambda pos, m, n: orig(pos, n, m))
+    assert gaussian_array_error() > 1e-2
+
+
+def test_rooftop_with_a_single_sinc_is_caught(monkeypatch):
+    def one_sinc(kx, ky, cx, cy, direction, half_len, width):
+        kx = np.asarray(kx, dtype=np.complex128)
+        ky = np.asarray(ky, dtype=np.complex128)
+        ku, kv = (kx, ky) if direction == 0 else (ky, kx)
+        shape = half_len * spectra.sinc(ku * half_len / 2.0) * spectra.sinc(kv * width / 2.0)
+        return np.exp(-1j * (kx * cx + ky * cy)) * shape
+    monkeypatch.setattr(spectra, "rooftop_ft", one_sinc)
+    assert rooftop_error() > 1e-3
