@@ -133,3 +133,42 @@ def test_vanishing_slab_gives_zero():
     ky = np.array([0.1, 1.0]) * K0
     g = green.dyadic_green(kx, ky, 2.2, 0.0, K0)
     assert all(np.all(np.abs(c) == 0) for c in g)
+
+
+def tl_dyadic(kx, ky, eps_r, h, k0, z0):
+    """The same dyadic from the transverse-resonance (transmission-line) picture, derived
+    independently of the oracle's closed form: along k the current sees the TM line, across
+    k the TE line, each an air half-space (admittance k2/(w mu0) for TE, w eps0/k2 for TM)
+    in parallel with the slab line shorted by the ground plane at depth h
+    (-j cot(k1 h) times k1/(w mu0), resp. w eps0 eps_r/k1).  With E = -Z J along each
+    direction, G = -Z_TE I - (Z_TM - Z_TE) k k^T / beta^2."""
+    kx = np.asarray(kx, dtype=np.complex128)
+    ky = np.asarray(ky, dtype=np.complex128)
+    b2 = kx * kx + ky * ky
+    k2 = -1j * np.sqrt(b2 - k0 * k0 + 0j)            # Im k2 <= 0 (radiation condition)
+    k1 = np.sqrt(eps_r * k0 * k0 - b2 + 0j)
+    w_mu0, w_eps0 = k0 * z0, k0 / z0
+    cot = np.cos(k1 * h) / np.sin(k1 * h)
+    z_te = 1.0 / (k2 / w_mu0 - 1j * k1 * cot / w_mu0)
+    z_tm = 1.0 / (w_eps0 / k2 - 1j * w_eps0 * eps_r * cot / k1)
+    gxx = -z_te - (z_tm - z_te) * kx * kx / b2
+    gxy = -(z_tm - z_te) * kx * ky / b2
+    gyy = -z_te - (z_tm - z_te) * ky * ky / b2
+    return gxx, gxy, gyy
+
+
+@pytest.mark.parametrize("eps_r,h", [(2.2, 0.05), (4.4, 0.03), (10.0, 0.1)])
+def test_dyadic_matches_transmission_line_model(eps_r, h):
+    """Every order of the numerators (not only the leading thin-slab terms) against the
+    transmission-line derivation, on the real axis below and above k0 and on the contour
+    side of the plane (beta_I > 0), including points next to the surface-wave poles."""
+    kd = K0 * math.sqrt(eps_r)
+    betas = np.array([0.37 * K0, 0.99 * K0, 1.02 * K0, 0.5 * (K0 + kd), 0.98 * kd, 1.7 * kd, 4.6 * kd])
+    betas = np.concatenate([betas, betas + 0.03j, betas[2:] + 0.2j])
+    alphas = np.linspace(0.1, 2.9, betas.size)
+    kx, ky = betas * np.cos(alphas), betas * np.sin(alphas)
+    got = green.dyadic_green(kx, ky, eps_r, h, K0)
+    ref = tl_dyadic(kx, ky, eps_r, h, K0, green.Z0)
+    scale = np.maximum(np.abs(ref[0]), np.abs(ref[2]))
+    for g, r in zip(got, ref):
+        assert np.all(np.abs(g - r) <= 1e-11 * scale)

@@ -267,3 +267,38 @@ def test_rooftop_with_a_single_sinc_is_caught(monkeypatch):
         return np.exp(-1j * (kx * cx + ky * cy)) * shape
     monkeypatch.setattr(spectra, "rooftop_ft", one_sinc)
     assert rooftop_error() > 1e-3
+
+
+def tl_model_error():
+    """max |G - G_TL| / |G_TL| against the transmission-line derivation (pin: 1e-11)."""
+    from tests.test_oracle_green import tl_dyadic
+    eps_r, h = 4.4, 0.03
+    betas = np.array([0.5, 1.3, 2.4, 9.0]) * K0 + 0.02j
+    kx, ky = betas * math.cos(0.7), betas * math.sin(0.7)
+    got = green.dyadic_green(kx, ky, eps_r, h, K0)
+    ref = tl_dyadic(kx, ky, eps_r, h, K0, green.Z0)
+    scale = np.maximum(np.abs(ref[0]), np.abs(ref[2]))
+    return max(np.max(np.abs(g - r) / scale) for g, r in zip(got, ref))
+
+
+def test_consistent_numerator_sign_slip_is_caught(monkeypatch):
+    # the j k1 sin(k1 h) terms of every numerator with the opposite sign: the dyadic stays
+    # covariant, its leading thin-slab terms and its poles are unchanged -- only the
+    # transmission-line pin sees it
+    def slipped(kx, ky, eps_r, h, k0):
+        kx = np.asarray(kx, dtype=np.complex128)
+        ky = np.asarray(ky, dtype=np.complex128)
+        b2 = kx * kx + ky * ky
+        k1, k2 = green.kz_slab(b2, eps_r, k0), green.kz_free(b2, k0)
+        c, s = np.cos(k1 * h), np.sin(k1 * h)
+        te, tm = green.te_tm(b2, eps_r, h, k0)
+        common = s / (te * tm)
+        z = -1j * green.Z0 / k0
+        gxx = z * ((eps_r * k0 ** 2 - kx * kx) * k2 * c - 1j * (k0 ** 2 - kx * kx) * k1 * s) * common
+        gyy = z * ((eps_r * k0 ** 2 - ky * ky) * k2 * c - 1j * (k0 ** 2 - ky * ky) * k1 * s) * common
+        gxy = -z * kx * ky * (k2 * c - 1j * k1 * s) * common
+        return gxx, gxy, gyy
+    assert tl_model_error() < 1e-11
+    monkeypatch.setattr(green, "dyadic_green", slipped)
+    assert rotational_covariance_error() < 1e-12      # the covariance pin does not see it
+    assert tl_model_error() > 1e-3
