@@ -23,6 +23,9 @@ Everything here is written from the paper's definitions, in the paper's order:
                    quadrature along the contour ("O1", converged).
 * ``fill``      -- exact per-entry evaluation of the reduced matrix Z' (Eq. 3
                    restated per element pair through Eq. 9).
+* ``solve``     -- the reduced system of Section II: excitation V' = Q^H V
+                   (Eq. 4), a direct solution of Z' I' = V', the currents
+                   I = Q I' and the port currents of delta-gap excitations.
 
 All arithmetic is numpy/scipy float64 / complex128.  Nothing here is blocked,
 fused or reordered beyond the definitions; speed is not a goal.
