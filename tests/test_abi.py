@@ -153,3 +153,18 @@ def test_static_backprojection_argument_checks_need_no_device(lib):
     for kw in ({"taps": 5}, {"taps": 14}, {"sigma": 3}, {"grid": None}, {"n_rho": 1},
                {"rho_max": float("nan")}, {"q_max": 65}, {"device": -1}, {"delta_s": 0.0}):
         assert call(**kw) == 1, kw                              # CFFT_ERR_ARG
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/cfft.h is a C header (C99, pedantic): plain pointers and sizes, no C++ or
+    torch types, so that any C caller can use the library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "cfft.h"\nint main(void) { cfft_ctx* c = 0; (void)c; return (int)CFFT_OK; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
