@@ -168,3 +168,20 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_readme_c_example_compiles(tmp_path):
+    """The C example of README.md stays valid against include/cfft.h (syntax and types)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    text = open(os.path.join(ROOT, "README.md")).read()
+    m = re.search(r"```c\n(.*?)```", text, flags=re.S)
+    assert m, "README.md has no C example"
+    src = tmp_path / "readme_example.c"
+    src.write_text(m.group(1))
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
