@@ -121,9 +121,17 @@ def test_fill_small_array(torch_cuda, precision):
     assert err < TOL[precision]
 
 
+@pytest.fixture(scope="module")
+def small_array_oracle():
+    """Oracle harmonics of the small patch table used by the smallest-array fills (FP64
+    definitions, the same for both GPU precisions), computed once for the module."""
+    wl = cc.small_patch("fp64", n=1024, n_rho=512, rho_max=5.0, q_max=4, rotation_classes=4)
+    return cc.oracle_harmonics(wl, classes=(0, 1, 2, 3))
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("case", ["one", "two", "three"])
-def test_fill_smallest_arrays(torch_cuda, precision, case):
+def test_fill_smallest_arrays(torch_cuda, small_array_oracle, precision, case):
     """Degenerate arrays: one element (its self block only, rho = 0), two and three
     elements with mixed rotations; every entry against the oracle's exact fill (FP32:
     the tensor-core form, one stencil cell per CTA and a ragged tile of pairs)."""
@@ -140,7 +148,7 @@ def test_fill_smallest_arrays(torch_cuda, precision, case):
     ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), torch.tensor(rot, device="cuda:0"), z)
     got = z.cpu().numpy()
     assert np.isfinite(got).all()          # every entry written
-    nodes, hq = cc.oracle_harmonics(wl, classes=(0, 1, 2, 3))
+    nodes, hq = small_array_oracle
     pairs = [(i, j) for i in range(a) for j in range(a)]
     ref = cc.oracle_fill_entries(wl, hq, nodes, pos, rot, pairs)
     refm = np.zeros((a * m, a * m), dtype=np.complex128)
