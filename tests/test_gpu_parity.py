@@ -159,19 +159,30 @@ def test_fill_smallest_arrays(torch_cuda, small_array_oracle, precision, case):
     assert err < TOL[precision]
 
 
+def _eight_mbf_patch(precision):
+    import dataclasses
+    wl = cc.small_patch(precision, n=1024, n_rho=256, rho_max=3.0, q_max=2)
+    el = wl.element
+    return dataclasses.replace(wl, element=dataclasses.replace(el, q=workloads.complex_normal((el.q.shape[0], 8), 81)))
+
+
+@pytest.fixture(scope="module")
+def eight_mbf_oracle():
+    """The oracle table of the eight-MBF patch (FP64 definitions, the same for both GPU
+    precisions), computed once for the module."""
+    return cc.oracle_table(_eight_mbf_patch("fp64"))
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_eight_mbfs_table_and_fill(torch_cuda, precision):
+def test_eight_mbfs_table_and_fill(torch_cuda, eight_mbf_oracle, precision):
     """The largest MBF count the ABI takes (M = 8: 64 pairs, four chunks of the
     integrand's pair loop, four series chunks per harmonic in the back-projection, the
     per-row fill): the whole table and a small array's fill against the oracle."""
-    import dataclasses
     torch = torch_cuda
-    wl = cc.small_patch(precision, n=1024, n_rho=256, rho_max=3.0, q_max=2)
-    el = wl.element
-    wl = dataclasses.replace(wl, element=dataclasses.replace(el, q=workloads.complex_normal((el.q.shape[0], 8), 81)))
+    wl = _eight_mbf_patch(precision)
     assert wl.element.n_mbf == 8
     ctx, got = cc.gpu_table(wl)
-    ref, nodes, hq = cc.oracle_table(wl)
+    ref, nodes, hq = eight_mbf_oracle
     err = cc.rel_err_per_pair(got, ref).max()
     pos = workloads.poisson_disc(5, 1.2, 0.5, seed=82)
     a, m = len(pos), 8
