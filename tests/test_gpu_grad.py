@@ -217,31 +217,3 @@ def test_tensor_core_adjoint_vs_fp32_pipe(torch_cuda):
     et = np.abs(gt - ref_t) / np.abs(ref_t)
     print("tensor-core adjoint vs FP32 pipe: pos", ep, "eps/h", et)
     assert ep < 2e-5 and np.all(et < 5e-5)
-
-
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_residual_adjoint_matches_general_adjoint(torch_cuda, precision):
-    """cfft_fill_backward_residual (dL/dZ' = 2 r v^H of L = sum |Z' v - t|^2, formed on the
-    device from v and r) against cfft_fill_backward on the same matrix formed by PyTorch:
-    position and substrate gradients, 4 rotation classes."""
-    torch = torch_cuda
-    from paper_1404_7357_gb300 import cfft
-    wl = cc.small_patch(precision, n=1024, n_rho=512, rho_max=5.0, q_max=3, rotation_classes=4)
-    ctx = cc.gpu_context(wl, options={cfft.OPT_DERIVATIVES: 1})
-    prec = cfft.CFFT_FP64 if precision == "fp64" else cfft.CFFT_FP32_MIXED
-    ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, prec, 4)
-    pos = workloads.poisson_disc(60, 2.4, 0.4, seed=43)
-    rot = workloads.rotations(len(pos), seed=43)
-    a, m = len(pos), 4
-    dt = torch.complex128 if precision == "fp64" else torch.complex64
-    v = torch.tensor(workloads.complex_normal(a * m, 62), device="cuda:0").to(dt)
-    r = torch.tensor(workloads.complex_normal(a * m, 63), device="cuda:0").to(dt)
-    g = (2 * r[:, None] * v.conj()[None, :]).contiguous()
-    pos_t, rot_t = torch.tensor(pos, device="cuda:0"), torch.tensor(rot, device="cuda:0")
-    ref_p, ref_t = ctx.fill_backward(pos_t, rot_t, g)
-    gp, gt = ctx.fill_backward_residual(pos_t, rot_t, v, r)
-    ep = ((gp - ref_p).abs().max() / ref_p.abs().max()).item()
-    et = ((gt - ref_t).abs() / ref_t.abs()).max().item()
-    print(precision, "residual form vs general adjoint: pos", ep, "eps/h", et)
-    tol_p, tol_t = (1e-11, 1e-11) if precision == "fp64" else (2e-5, 5e-5)
-    assert ep < tol_p and et < tol_t

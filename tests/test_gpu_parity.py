@@ -38,23 +38,6 @@ def test_strip_fp64_full_table(torch_cuda):
     assert err.max() < TOL["fp64"]
 
 
-@pytest.mark.parametrize("bp_simt", [0, 1])
-def test_strip_fp32_single_series(torch_cuda, bp_simt):
-    """The strip (M = 1) in FP32-mixed: one series per harmonic, so the back-projection's
-    16-series chunk is mostly empty (tensor-core products and FP32-pipe products), and
-    the SIMT spectra of a non-rooftop element; the whole table against the oracle."""
-    import dataclasses
-    from paper_1404_7357_gb300 import cfft
-    wl = dataclasses.replace(workloads.strip_fp64(n=1024, n_rho=512, rho_max=8.0), precision="fp32")
-    ctx, got = cc.gpu_table(wl, options={cfft.OPT_BP_SIMT: bp_simt})
-    ref, _, _ = cc.oracle_table(wl)
-    err = cc.rel_err_per_pair(got, ref).max()
-    info = ctx.info()
-    print("strip fp32 bp_simt", bp_simt, "bp form", info["bp_form"], "rel err", err)
-    assert info["bp_form"] == (2 if bp_simt else 3)
-    assert err < TOL["fp32"]
-
-
 def test_strip_fp64_stages(torch_cuda):
     wl = workloads.strip_fp64(n=1024, n_rho=256, rho_max=10.0)
     ctx, got = cc.gpu_table(wl)
@@ -119,84 +102,6 @@ def test_fill_small_array(torch_cuda, precision):
     err = np.abs(got - refm).max() / np.abs(refm).max()
     print(precision, "fill rel err", err)
     assert err < TOL[precision]
-
-
-@pytest.fixture(scope="module")
-def small_array_oracle():
-    """Oracle harmonics of the small patch table used by the smallest-array fills (FP64
-    definitions, the same for both GPU precisions), computed once for the module."""
-    wl = cc.small_patch("fp64", n=1024, n_rho=512, rho_max=5.0, q_max=4, rotation_classes=4)
-    return cc.oracle_harmonics(wl, classes=(0, 1, 2, 3))
-
-
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("case", ["one", "two", "three"])
-def test_fill_smallest_arrays(torch_cuda, small_array_oracle, precision, case):
-    """Degenerate arrays: one element (its self block only, rho = 0), two and three
-    elements with mixed rotations; every entry against the oracle's exact fill (FP32:
-    the tensor-core form, one stencil cell per CTA and a ragged tile of pairs)."""
-    torch = torch_cuda
-    pos, rot = {"one": ([[0.3, -0.2]], [1]),
-                "two": ([[0.0, 0.0], [1.7, 2.1]], [0, 1]),
-                "three": ([[0.0, 0.0], [0.6, 0.0], [-2.0, 3.5]], [1, 0, 1])}[case]
-    pos, rot = np.array(pos, dtype=np.float64), np.array(rot, dtype=np.int32)
-    wl = cc.small_patch(precision, n=1024, n_rho=512, rho_max=5.0, q_max=4, rotation_classes=4)
-    ctx, _ = cc.gpu_table(wl)
-    a, m = len(pos), wl.element.n_mbf
-    dt = torch.complex128 if precision == "fp64" else torch.complex64
-    z = torch.full((a * m, a * m), complex(float("nan"), 0.0), dtype=dt, device="cuda:0")
-    ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), torch.tensor(rot, device="cuda:0"), z)
-    got = z.cpu().numpy()
-    assert np.isfinite(got).all()          # every entry written
-    nodes, hq = small_array_oracle
-    pairs = [(i, j) for i in range(a) for j in range(a)]
-    ref = cc.oracle_fill_entries(wl, hq, nodes, pos, rot, pairs)
-    refm = np.zeros((a * m, a * m), dtype=np.complex128)
-    for (i, j), blk in zip(pairs, ref):
-        refm[i * m:(i + 1) * m, j * m:(j + 1) * m] = blk
-    err = np.abs(got - refm).max() / np.abs(refm).max()
-    print(precision, case, "fill form", ctx.info()["fill_form"], "rel err", err)
-    assert err < TOL[precision]
-
-
-def _eight_mbf_patch(precision):
-    import dataclasses
-    wl = cc.small_patch(precision, n=1024, n_rho=256, rho_max=3.0, q_max=2)
-    el = wl.element
-    return dataclasses.replace(wl, element=dataclasses.replace(el, q=workloads.complex_normal((el.q.shape[0], 8), 81)))
-
-
-@pytest.fixture(scope="module")
-def eight_mbf_oracle():
-    """The oracle table of the eight-MBF patch (FP64 definitions, the same for both GPU
-    precisions), computed once for the module."""
-    return cc.oracle_table(_eight_mbf_patch("fp64"))
-
-
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_eight_mbfs_table_and_fill(torch_cuda, eight_mbf_oracle, precision):
-    """The largest MBF count the ABI takes (M = 8: 64 pairs, four chunks of the
-    integrand's pair loop, four series chunks per harmonic in the back-projection, the
-    per-row fill): the whole table and a small array's fill against the oracle."""
-    torch = torch_cuda
-    wl = _eight_mbf_patch(precision)
-    assert wl.element.n_mbf == 8
-    ctx, got = cc.gpu_table(wl)
-    ref, nodes, hq = eight_mbf_oracle
-    err = cc.rel_err_per_pair(got, ref).max()
-    pos = workloads.poisson_disc(5, 1.2, 0.5, seed=82)
-    a, m = len(pos), 8
-    dt = torch.complex128 if precision == "fp64" else torch.complex64
-    z = torch.zeros((a * m, a * m), dtype=dt, device="cuda:0")
-    ctx.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), None, z)
-    pairs = [(i, j) for i in range(a) for j in range(a)]
-    blocks = cc.oracle_fill_entries(wl, hq, nodes, pos, np.zeros(a, dtype=np.int32), pairs)
-    zref = np.zeros((a * m, a * m), dtype=np.complex128)
-    for (i, j), blk in zip(pairs, blocks):
-        zref[i * m:(i + 1) * m, j * m:(j + 1) * m] = blk
-    ferr = np.abs(z.cpu().numpy() - zref).max() / np.abs(zref).max()
-    print(precision, "M = 8: table rel err", err, "fill rel err", ferr, "fill form", ctx.info()["fill_form"])
-    assert err < TOL[precision] and ferr < TOL[precision]
 
 
 def test_fill_host_variant_matches_device(torch_cuda):
