@@ -225,7 +225,7 @@ class Context:
         if pos.dtype not in (torch.float64, np.float64) or tuple(pos.shape)[1:] != (2,):
             bad("pos must be float64 of shape (A, 2)")
         a = int(pos.shape[0])
-        n = a * int(self.n_mbf)
+        n = a * int(getattr(self, "n_mbf", 0))      # no element yet: the library reports the state
         if rot is not None and (rot.dtype not in (torch.int32, np.int32) or tuple(rot.shape) != (a,)):
             bad("rot must be int32 of shape (A,)")
         if z.dtype not in (torch.complex64, torch.complex128, np.complex64, np.complex128):
@@ -312,7 +312,7 @@ class Context:
         """Adjoint for L = sum |Z' v - t|^2 from v and r = Z' v - t (cuda complex vectors of
         A*M entries): (grad_pos (A, 2) float64, grad_eps_h (2,) float64 or None)."""
         torch = self._torch
-        n = pos.shape[0] * int(self.n_mbf)
+        n = pos.shape[0] * int(getattr(self, "n_mbf", 0))
         for x in (v, resid):
             if not (x.is_cuda and x.dtype == resid.dtype and x.dtype in (torch.complex64, torch.complex128)
                     and x.is_contiguous() and x.numel() == n):
@@ -377,7 +377,7 @@ class Context:
                 k.shape[1] == 2):
             raise ValueError("k must be a contiguous CUDA complex64 tensor of shape (n, 2)")
         n = k.shape[0]
-        shape = (n, 2, self.n_mbf, 2)
+        shape = (n, 2, int(getattr(self, "n_mbf", 1)), 2)   # no element yet: the library refuses
         if out is None:
             out = torch.empty(shape, dtype=torch.complex64, device=k.device)
         if not (out.is_cuda and tuple(out.shape) == shape and out.dtype == torch.complex64 and

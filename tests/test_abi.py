@@ -185,3 +185,12 @@ def test_readme_c_example_compiles(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_fill_binding_before_an_element_leaves_the_state_error_to_the_library(lib):
+    """Without an element the binding has no MBF count; it checks what it can and lets the
+    library report the call order (CFFT_ERR_STATE) instead of failing on its own."""
+    import numpy as np
+    c = _unbound_context(lib, 1)
+    del c.n_mbf
+    assert c._check_layout(np.zeros((2, 2)), None, np.zeros((1, 1), dtype=np.complex64), device=False) == 2
