@@ -10,7 +10,9 @@ the L2 cache is flushed between timed steps.  Beside it, the same metric end
 to end through the host-buffer C-ABI path, the plain FP64 GPU form of the same
 tabulation, the reduced-matrix fill of the 10,000-element irregular array
 (entries/s), the batched sweep, the differentiable fill, the roofline of the
-dominant kernel, and the FP64 oracle timed on the host cores.
+dominant kernel, and the FP64 oracle timed on the host cores.  On a one-GPU run the
+oracle leg also checks sampled outputs of each line against the FP64 oracle
+(the FP32 and FP64 tables, the fill's element-pair blocks, one sweep item).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cfft|reference]
 Under torchrun every rank runs its own replica of the workload (the path
