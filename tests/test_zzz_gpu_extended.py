@@ -300,3 +300,22 @@ def test_injected_allocation_failures_leave_contexts_usable(torch_cuda):
             print("allocation failure after", after, "allocations: OOM reported, context usable")
     finally:
         cfft.test_fail_allocation(-1)
+
+
+def test_empty_inputs(torch_cuda):
+    """Empty inputs: a fill of no elements and a batch of no items are refused as
+    arguments (CFFT_ERR_ARG); spectra at no points are an empty result."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp32", n=1024, n_rho=128, rho_max=3.0, q_max=1)
+    ctx, _ = cc.gpu_table(wl)
+    pos = torch.zeros((0, 2), dtype=torch.float64, device="cuda:0")
+    z = torch.zeros((0, 0), dtype=torch.complex64, device="cuda:0")
+    with pytest.raises(cfft.CfftError) as ei:
+        ctx.fill_reduced_matrix(pos, None, z)
+    assert ei.value.status == 1
+    with pytest.raises(cfft.CfftError) as ei:
+        ctx.tabulate_batch([], 1, 3.0, 128, cfft.CFFT_FP32_MIXED)
+    assert ei.value.status == 1
+    out = ctx.mbf_spectra(torch.zeros((0, 2), dtype=torch.complex64, device="cuda:0"))
+    assert tuple(out.shape) == (0, 2, 4, 2)
