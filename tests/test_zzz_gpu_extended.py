@@ -1,7 +1,7 @@
 """GPU cases for configurations and failure paths beyond the per-stage files: the batched
 sweep's graph capture and recapture, the strip element in batches and in FP32-mixed, the
 benchmarked sweep at full size, eight MBFs, the smallest arrays, the residual form of
-the fill adjoint, and out-of-memory injected on the host.  Every case runs through the
+the fill adjoint, out-of-memory injected on the host, and empty inputs.  Every case runs through the
 C ABI and is compared with the oracle or with a path checked against it.  Nothing here
 traps, faults or waits without a bound."""
 import numpy as np
