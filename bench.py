@@ -357,7 +357,10 @@ def bench_fill(torch, cfft, args, dev):
         kpad = (2 * nh + 7) // 8 * 8
         res["tensor_tflops_executed"] = 3 * 2.0 * kpad * 256 * float(a) ** 2 / sec / 1e12
     res["hbm_gbs_write"] = entries * 8 / sec / 1e9
-    # element-pair blocks of rotation class (0, 0) for the oracle comparison (after timing)
+    fi = ctx.info()
+    res["fill_table"] = {"err_est_on_tabulated_grid": fi["fill_err_est"], "refine": fi["fill_refine"],
+                         "n_rho": fi["fill_n_rho"]}
+    # element-pair blocks of every rotation class for the oracle comparison (after timing)
     pairs = fill_sample_pairs(pos, rot)
     blocks = [z[m * i:m * i + m, m * j:m * j + m].cpu().numpy().astype(np.complex128) for i, j in pairs]
     del z
@@ -365,38 +368,60 @@ def bench_fill(torch, cfft, args, dev):
     return res, (wl, pos, rot, pairs, blocks)
 
 
+FILL_BINS = ((0.4, 2.0), (20.0, 40.0), (60.0, 80.0), (100.0, 121.0))
+
+
 def fill_sample_pairs(pos, rot, seed=91):
-    """Element pairs (test m, basis n), both unrotated, spread over the distances the fill's
-    table covers: one diagonal block and up to four pairs in each of four distance bins,
-    measured from ten anchor elements."""
-    unrot = np.flatnonzero(np.asarray(rot) == 0)
-    anchors = unrot[:10]
-    d = np.hypot(*(pos[:, None, :] - pos[None, anchors, :]).transpose(2, 0, 1))    # (A, anchors)
-    ok = (np.asarray(rot) == 0)[:, None]
+    """Element pairs (test m, basis n) of every rotation class (rot[m], rot[n]) in
+    {0, 90 deg}^2, spread over the distances the fill's table covers: one diagonal block,
+    then for each distance bin one pair of each class, measured from ten anchor basis
+    elements of the class's basis rotation."""
+    rot = np.asarray(rot)
     rng = np.random.default_rng(seed)
-    pairs = [(int(anchors[0]), int(anchors[0]))]
-    for lo, hi in ((0.4, 2.0), (20.0, 40.0), (60.0, 80.0), (100.0, 121.0)):
-        cand = np.argwhere((d >= lo) & (d < hi) & ok)
-        for k in rng.choice(len(cand), size=min(4, len(cand)), replace=False):
+    pairs = [(int(np.flatnonzero(rot == 0)[0]),) * 2]
+    for lo, hi in FILL_BINS:
+        for cls in range(4):
+            r_m, r_n = cls >> 1, cls & 1
+            anchors = np.flatnonzero(rot == r_n)[:10]
+            d = np.hypot(*(pos[:, None, :] - pos[None, anchors, :]).transpose(2, 0, 1))  # (A, anchors)
+            cand = np.argwhere((d >= lo) & (d < hi) & (rot == r_m)[:, None])
+            k = rng.integers(len(cand))
             pairs.append((int(cand[k][0]), int(anchors[cand[k][1]])))
     return pairs
 
 
-def fill_parity(sample, table_wl, nodes, hq):
+def class_harmonics(wl, nodes, cls, workers):
+    """Oracle harmonics of rotation class cls on the table workload's contour nodes."""
+    from oracle import reaction as orx, spectra as osp
+    el = wl.element
+    bs = osp.BasisSet("rooftop", el.q, cx=el.cx, cy=el.cy, direction=el.direction,
+                      half_len=el.half_len, width=el.width)
+    s = wl.substrate
+    return orx.harmonics(bs, nodes["beta_c"], wl.qs, 128, s.eps_r, s.h, s.k0, *orx.rotation_angles(cls),
+                         workers=workers)
+
+
+def fill_parity(sample, table_wl, nodes, hq, workers=1):
     """The sampled blocks of the benchmarked fill against the oracle's exact fill (Bessel
     sums at each pair's exact rho) with the harmonics of the table workload's contour,
-    which is the fill's own contour; max |err| over the blocks / max |oracle|."""
+    which is the fill's own contour; max |err| over the blocks / max |oracle|.  hq holds
+    the unrotated class; the other classes the pairs need are computed here."""
     from oracle import fill as ofill
     wl, pos, rot, pairs, blocks = sample
     same = (wl.contour == table_wl.contour and wl.q_max == table_wl.q_max and
             wl.substrate == table_wl.substrate)
     if not same:
         return {"skipped": "the fill's contour differs from the table workload's"}
-    ref = ofill.entries({0: hq}, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, pairs)
+    classes = sorted({2 * int(rot[i]) + int(rot[j]) for i, j in pairs})
+    hq_by = {0: hq}
+    for cls in classes:
+        if cls not in hq_by:
+            hq_by[cls] = class_harmonics(wl, nodes, cls, workers)
+    ref = ofill.entries(hq_by, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, pairs)
     scale = max(np.abs(r).max() for r in ref)
     err = max(np.abs(g - r).max() for g, r in zip(blocks, ref)) / scale
     return {"max_rel_err_vs_oracle": float(err), "tolerance": 1e-5, "blocks": len(pairs),
-            "rotation_class": "(0, 0)"}
+            "rotation_classes": classes}
 
 
 def bench_batch(torch, cfft, args, dev):
@@ -671,7 +696,7 @@ def run_cfft(args):
                 line["batch"]["parity"] = {"error": repr(e)[:300]}
         if fill_sample is not None:
             try:   # the fill's sampled blocks against the exact fill on the same harmonics
-                line["fill"]["parity"] = fill_parity(fill_sample, wl, nodes, hq)
+                line["fill"]["parity"] = fill_parity(fill_sample, wl, nodes, hq, workers)
             except Exception as e:
                 line["fill"]["parity"] = {"error": repr(e)[:300]}
         if fp64_table is not None:

@@ -107,7 +107,11 @@ typedef enum {
  *                tensor cores (the interpolation as one contraction per
  *                stencil cell); 0 (default): the fill on the tensor cores,
  *                the adjoint there from 512 element pairs per stencil cell;
- *                a value < 0: both on the tensor cores whenever they apply */
+ *                a value < 0: both on the tensor cores whenever they apply
+ *   FILL_REFINE  grid of the table the fill interpolates.  Default (< 1):
+ *                automatic, see cfft_fill_reduced_matrix; a value k >= 1
+ *                fixes it at k times finer than the tabulated grid, without
+ *                the accuracy check (k = 1: the tabulated table as it is) */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -120,7 +124,8 @@ typedef enum {
   CFFT_OPT_FILL_BLOCK = 8,
   CFFT_OPT_SPECTRA_SIMT = 9,
   CFFT_OPT_BP_SIMT = 10,
-  CFFT_OPT_FILL_SIMT = 11
+  CFFT_OPT_FILL_SIMT = 11,
+  CFFT_OPT_FILL_REFINE = 12
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -190,7 +195,12 @@ cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value);
  * H = M_t . G . M_b^* (Eq. 10), azimuthal harmonics, the Taylor expansion of
  * the contour factor (Eq. 22), one zero-padded FFT per (pair, harmonic,
  * Taylor term) (Eq. 23-24) and a back-projection over the angle to the
- * uniform rho grid.
+ * uniform rho grid.  The back-projection's midpoint rule in the angle takes,
+ * for the rows of each chunk up to rho, ceil((z + q_max)/2 + c z^(1/3) +
+ * margin/2) + 1 nodes with z = |beta_c|max rho, margin = ALPHA_MARGIN (24)
+ * and c = 4 in FP64, 2 in FP32-mixed: the first aliased angular harmonic
+ * then lies far enough beyond z that its Bessel factor is below the
+ * precision's target at every rho.
  * rotation_classes = 1: elements unrotated (one class);
  * rotation_classes = 4: element rotations in {0, 90 deg}; the table holds the
  * classes (test, basis) = (0,0), (0,90), (90,0), (90,90) in that order.
@@ -234,7 +244,23 @@ cfft_status cfft_copy_table(const cfft_ctx* ctx, void* dst, int64_t bytes, int d
  * share table rows run together on one copy of those rows in shared memory;
  * the context owns that scratch (4 bytes per element pair of up to 2^27 pairs
  * at a time, 8 bytes per (row block, class, table row), 16 bytes per element)
- * and keeps it for the next fill. */
+ * and keeps it for the next fill.
+ * Accuracy: the fill's interpolation keeps within a quarter of the table
+ * precision's target (1e-10 of the table maximum per (class, pair) for FP64,
+ * 1e-5 for FP32-mixed) at every distance up to rho_max.  The first fill or
+ * adjoint after a tabulation estimates the interpolation error on the
+ * tabulated rho grid from the table's p-th differences (the Lagrange
+ * remainder; p = fill taps), for the interior stencils and for the stencil
+ * shifted inward at rho_max.  When the estimate misses that share, the
+ * context tabulates the same reactions once more, with the options in force
+ * at the tabulation, on a grid finer by an integer factor r >= 1 that
+ * reaches p/2 rows beyond rho_max (so that every stencil is centred), and
+ * the fill and its adjoint interpolate that table from then on;
+ * cfft_get_table keeps returning the tabulated grid.  cfft_get_info reports
+ * the estimate, r and the grid used (fill_err_est, fill_refine,
+ * fill_n_rho).  A loaded table (cfft_load_table) cannot be tabulated again:
+ * when its grid misses the share the fill returns CFFT_ERR_ARG
+ * (CFFT_OPT_FILL_REFINE set to 1 accepts the grid as it is). */
 cfft_status cfft_fill_reduced_matrix(cfft_ctx* ctx, int n_elements, const double* pos_xy,
                                      const int* rot, void* z_out, int64_t ld,
                                      int out_complex128);
@@ -357,7 +383,12 @@ cfft_status cfft_fill_backward_residual(cfft_ctx* ctx, int n_elements, const dou
  * series, every harmonic) and work_bp_stencils the node stencils added into
  * the matrices (rows x angular nodes x matrices).  fill_form: the form of the
  * last cfft_fill_reduced_matrix: 1 per-row, 2 bucketed on the FP32 pipe, 3 on
- * the tensor cores (0: no fill yet). */
+ * the tensor cores (0: no fill yet).  fill_err_est: the estimated
+ * interpolation error of the fill on the tabulated grid, relative to the
+ * table maximum (-1: not estimated); fill_refine: the factor r of the grid
+ * the fill interpolates (0: no fill since the last tabulation); fill_n_rho:
+ * that grid's points (n_rho when the fill uses the tabulated table, else
+ * (n_rho - 1) r + 1 + fill_taps / 2, reaching beyond rho_max). */
 typedef struct {
   int taylor_order, n_alpha, sigma, fft_len, sub_len, grid_half, bp_taps, fill_taps;
   int series, classes, n_pairs, n_harm;
@@ -367,6 +398,8 @@ typedef struct {
   int spectra_tc, bp_form;
   double work_bp_macs, work_bp_stencils;
   int fill_form;
+  double fill_err_est;
+  int fill_refine, fill_n_rho;
 } cfft_info;
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
 
@@ -388,10 +421,10 @@ cfft_status cfft_debug_buffer(const cfft_ctx* ctx, const char* name, const void*
 cfft_status cfft_synchronize(cfft_ctx* ctx);
 
 /* Allocation-free back-projection.  The paper has no counterpart: this entry
- * point exists for callers that cannot call cudaMalloc -- code that runs
- * while a CUDA graph is being captured, plug-ins whose host application owns
- * every device allocation, real-time loops that cannot afford an allocation
- * that may synchronize the device.  It runs the back-projection stage of
+ * point exists for callers that cannot call cudaMalloc -- plug-ins whose host
+ * application owns every device allocation, real-time loops that cannot
+ * afford an allocation that may synchronize the device.  It runs the
+ * back-projection stage of
  * cfft_tabulate_reactions on caller-owned buffers and allocates nothing:
  * its scratch (angular node counts, offsets and cosines for every chunk of
  * 32 rho rows) lives in one 8 MiB device array inside the library, present
@@ -407,7 +440,11 @@ cfft_status cfft_synchronize(cfft_ctx* ctx);
  *           Lagrange taps (4, 6, 8, 10, 12, 16, 20 or 24), step and half-width
  *           (cfft_get_info reports them for a tabulation); beta_abs_max is
  *           |beta_c| at the end of the contour, alpha_margin the angular node
- *           margin (24 reproduces the default of cfft_tabulate_reactions)
+ *           margin (24 is the default of cfft_tabulate_reactions; the node
+ *           rule's cube-root term follows the element type as there).  The
+ *           angular node counts are computed on the device here and on the
+ *           host in the tabulation, so the result matches the tabulation's
+ *           table within its precision's tolerance, not bit for bit
  * Limits: at most 65536 chunks (n_rho <= 2097152) and at most 950,272
  * angular nodes summed over the chunks (about n_rho * beta_abs_max * rho_max
  * / 128; 8192 rows to rho 50 at beta 66 use about 2.1e5); a request beyond

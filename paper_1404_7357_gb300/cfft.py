@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_PKG, "libcfft.so")
 CFFT_FP64 = 0
 CFFT_FP32_MIXED = 1
 (OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
- OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT, OPT_FILL_SIMT) = range(12)
+ OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT, OPT_FILL_SIMT,
+ OPT_FILL_REFINE) = range(13)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 
@@ -63,7 +64,8 @@ class Info(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("work_points", "work_subffts", "work_bp_nodes")] + \
                [(n, ctypes.c_int) for n in ("spectra_tc", "bp_form")] + \
                [(n, ctypes.c_double) for n in ("work_bp_macs", "work_bp_stencils")] + \
-               [("fill_form", ctypes.c_int)]
+               [("fill_form", ctypes.c_int), ("fill_err_est", ctypes.c_double)] + \
+               [(n, ctypes.c_int) for n in ("fill_refine", "fill_n_rho")]
 
 
 def _load():

@@ -86,14 +86,23 @@ struct cfft_ctx {
   bool has_contour = false;
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
-  // options (<= 0: automatic)
-  double opt[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // options (<= 0: automatic) and the options the last table was made with
+  double opt[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double tab_opt[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
   double rho_max = 0;
   cfft_precision prec = CFFT_FP64;
   cfft_info info{};
+  // the table the fill interpolates: the tabulated one, or (fill_own) d_ftable on n_frho
+  // points to frho_max, fill_r times finer than the tabulated grid and reaching beyond
+  // rho_max (fill_r = 0: not decided yet; decided at the first fill or adjoint after a
+  // tabulation or load)
+  int fill_r = 0, n_frho = 0;
+  double frho_max = 0;
+  bool fill_own = false, table_loaded = false;
+  DevBuf d_ftable, d_fest;
   // device buffers
   DevBuf beta_c, weight, bw, bi_rel, green_p, green_r, dp_eps, dr_eps, dp_h, dr_h;
   int channels = 1;  // 1: table; 3: table, d/d eps_r, d/d h
@@ -172,14 +181,26 @@ int auto_taylor(double x, double tol) {
   return -1;
 }
 
-// angular nodes of the back-projection for the largest rho of a chunk
-int alpha_nodes(double beta_abs_max, double rho, int q_max, double margin) {
+// angular nodes of the back-projection for the largest rho of a chunk.  With z = |beta| rho
+// the integrand g(rho cos alpha) holds angular harmonics up to about z, and the midpoint
+// rule's error is the first aliased one, J_n(z) with n ~ 2 N - |q|.  Above its order J_n
+// falls like Ai(x), x = (2/n)^(1/3) (n - z), so the excess n - z must grow like z^(1/3):
+// 2 N = z + |q| + 2 c z^(1/3) + margin keeps x >= 2^(4/3) c at every rho.  c = 2 (x >= 5)
+// holds the float32 target; the float64 target needs c = 4 (x >= 10): on the 200-rooftop
+// patch at rho = 50 wavelengths (z = 3300) c = 2 leaves 4.5e-10 of the table maximum,
+// c = 4 leaves 2e-15
+int alpha_nodes(double beta_abs_max, double rho, int q_max, double margin, double cbrt_coef) {
   double z = beta_abs_max * rho;
-  return (int)std::ceil(0.5 * (z + q_max) + 2.0 * std::cbrt(z) + 0.5 * margin) + 1;
+  return (int)std::ceil(0.5 * (z + q_max) + cbrt_coef * std::cbrt(z) + 0.5 * margin) + 1;
 }
 
+double alpha_cbrt_coef(bool fp64) { return fp64 ? 4.0 : 2.0; }
+
+// One tabulation into `dst` on n_rho points rho_r = r rho_max / (n_rho - 1).  primary: the
+// table of cfft_tabulate_reactions (its diagnostics go to ctx->info); otherwise the table
+// that the fill interpolates when the tabulated grid misses the fill's target.
 template <class T>
-cfft_status tabulate_impl(cfft_ctx* ctx) {
+cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst, bool primary) {
   cudaStream_t st = ctx->stream;
   const bool fp64 = sizeof(T) == 8;
   const int n = ctx->n;
@@ -211,15 +232,15 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
       fill_taps < 2 || fill_taps > 16 || (fill_taps & 1))
     return fail(ctx, CFFT_ERR_ARG,
                 "back-projection taps must be one of 4,6,8,10,12,16,20,24; fill taps even, 2..16");
-  if (ctx->n_rho < 2 * fill_taps) return fail(ctx, CFFT_ERR_ARG, "n_rho must be >= 2 * fill taps");
+  if (n_rho < 2 * fill_taps) return fail(ctx, CFFT_ERR_ARG, "n_rho must be >= 2 * fill taps");
   double margin = ctx->opt[CFFT_OPT_ALPHA_MARGIN] > 0 ? ctx->opt[CFFT_OPT_ALPHA_MARGIN] : 24.0;
   int taylor = ctx->taylor_req;
-  if (taylor < 0) taylor = auto_taylor(ctx->height * ctx->rho_max, fp64 ? 1e-13 : 1e-7);
+  if (taylor < 0) taylor = auto_taylor(ctx->height * rho_max, fp64 ? 1e-13 : 1e-7);
   if (taylor < 0)
     return fail(ctx, CFFT_ERR_ARG, "height * rho_max too large: no Taylor order up to 64 converges");
   const int64_t P = (int64_t)sigma * n;
   const double ds = 2.0 * kPi / ((double)P * step);
-  const int K = (int)std::ceil(ctx->rho_max / ds) + bp_taps / 2 + 2;
+  const int K = (int)std::ceil(rho_max / ds) + bp_taps / 2 + 2;
   if (2 * (int64_t)K + 1 > P)
     return fail(ctx, CFFT_ERR_ARG, "rho_max exceeds the unaliased range 2 pi / step of the contour");
   // sub-FFT length: power of two dividing P, within shared memory
@@ -247,8 +268,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   CFFT_CUDA(ctx->d_grid.ensure((size_t)series * (2 * K + 1) * sizeof(cpx<T>)), "alloc grid");
   const int cls_s = ctx->cls_stored;
   const int channels = ctx->opt[CFFT_OPT_DERIVATIVES] > 0 ? 3 : 1;
-  const size_t table_elems = (size_t)cls_s * pairs * nh * ctx->n_rho;
-  CFFT_CUDA(ctx->d_table.ensure(channels * table_elems * sizeof(cpx<T>)), "alloc table");
+  const size_t table_elems = (size_t)cls_s * pairs * nh * n_rho;
+  CFFT_CUDA(dst.ensure(channels * table_elems * sizeof(cpx<T>)), "alloc table");
   if (channels == 3) {
     CFFT_CUDA(ctx->dp_eps.ensure(n * sizeof(double2)), "alloc contour");
     CFFT_CUDA(ctx->dr_eps.ensure(n * sizeof(double2)), "alloc contour");
@@ -395,8 +416,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   const bool tform = pform && !(ctx->opt[CFFT_OPT_BP_SIMT] > 0);   // its products on the tensor cores
   const bool wform = !pform && series_per_q <= 64 && taps_ok && !gather;
   const int rchunk = pform ? backproject_pm_rows() : (wform ? backproject_w_rows() : 32);
-  const int n_chunks = (ctx->n_rho + rchunk - 1) / rchunk;
-  const double d_rho = ctx->rho_max / (ctx->n_rho - 1);
+  const int n_chunks = (n_rho + rchunk - 1) / rchunk;
+  const double d_rho = rho_max / (n_rho - 1);
   std::vector<int> cn(n_chunks);
   std::vector<int64_t> coff(n_chunks);
   int64_t tot = 0;
@@ -407,9 +428,9 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   // grid columns per matrix tile of the matrix forms
   const int ktile = tform ? backproject_tc_ktile() : (pform ? 32 : 64);
   for (int c = 0; c < n_chunks; ++c) {
-    int r_top = std::min((c + 1) * rchunk, ctx->n_rho) - 1;
+    int r_top = std::min((c + 1) * rchunk, n_rho) - 1;
     double rho_top = r_top * d_rho;
-    cn[c] = alpha_nodes(beta_abs_max, rho_top, ctx->q_max, margin);
+    cn[c] = alpha_nodes(beta_abs_max, rho_top, ctx->q_max, margin, alpha_cbrt_coef(fp64));
     const int rows_c = r_top + 1 - c * rchunk;
     bp_nodes += (double)cn[c] * rows_c * series;
     if (pform || wform) {
@@ -458,7 +479,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ba.series_per_q = series_per_q;
   ba.n_harm = nh;
   ba.q_max = ctx->q_max;
-  ba.n_rho = ctx->n_rho;
+  ba.n_rho = n_rho;
   ba.grid_half = K;
   ba.sigma = sigma;
   ba.taps = bp_taps;
@@ -469,7 +490,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   ba.beta_abs_max = beta_abs_max;
   ba.alpha_margin = margin;
   ba.grid = ctx->d_grid.as<cpx<T>>();
-  ba.table = ctx->d_table.as<cpx<T>>() + ch * table_elems;
+  ba.table = dst.as<cpx<T>>() + ch * table_elems;
   bp_form_used = tform ? 3 : (pform ? 2 : (wform ? 1 : 0));
   if (pform || wform) {
     ba.chunk_nodes = ctx->d_cnodes.as<int>();
@@ -495,7 +516,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   }
   ++launches;
   if (cls_s == 4) {
-    launch_class_phase<T>(ctx->d_table.as<cpx<T>>() + ch * table_elems, pairs, nh, ctx->q_max, ctx->n_rho, st);
+    launch_class_phase<T>(dst.as<cpx<T>>() + ch * table_elems, pairs, nh, ctx->q_max, n_rho, st);
     ++launches;
     CFFT_CUDA(cudaGetLastError(), "class phase kernel");
   }
@@ -506,7 +527,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   bool check = !(ctx->opt[CFFT_OPT_CHECK_FINITE] < 0);
   if (check) {
     CFFT_CUDA(cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), st), "flag");
-    launch_nonfinite<T>(ctx->d_table.as<cpx<T>>(), (int64_t)(channels * table_elems), ctx->d_flag.as<int>(), st);
+    launch_nonfinite<T>(dst.as<cpx<T>>(), (int64_t)(channels * table_elems), ctx->d_flag.as<int>(), st);
     ++launches;
     CFFT_CUDA(cudaGetLastError(), "nonfinite kernel");
   }
@@ -517,7 +538,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   if (tc_flag & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "integrand: a tensor-core wait ran past its bound");
   if (tc_flag & 32) return fail(ctx, CFFT_ERR_TIMEOUT, "back-projection: a tensor-core wait ran past its bound");
 
-  cfft_info& in = ctx->info;
+  cfft_info scratch_info{};
+  cfft_info& in = primary ? ctx->info : scratch_info;
   in.taylor_order = taylor;
   in.n_alpha = n_alpha;
   in.sigma = sigma;
@@ -549,28 +571,151 @@ cfft_status tabulate_impl(cfft_ctx* ctx) {
   in.bp_form = bp_form_used;
   in.work_bp_macs = bp_macs;
   in.work_bp_stencils = bp_stencils;
-  ctx->fill_taps = fill_taps;
-  ctx->channels = channels;
-  ctx->has_table = true;
+  in.fill_err_est = -1.0;
+  in.fill_refine = 0;
+  in.fill_n_rho = 0;
   if (flag) return fail(ctx, CFFT_ERR_NUMERIC, "non-finite value in the reaction table");
+  if (primary) {
+    ctx->fill_taps = fill_taps;
+    ctx->channels = channels;
+    ctx->has_table = true;
+  }
   return CFFT_OK;
+}
+
+// largest |prod_{t=0}^{p-1} (x - t)| / p! over x in [x0, x1] (the Lagrange remainder's
+// node polynomial of a p-tap stencil), by dense sampling of the interval
+double lagrange_node_factor(int p, double x0, double x1) {
+  double best = 0.0;
+  const int steps = 4096;
+  for (int k = 0; k <= steps; ++k) {
+    const double x = x0 + (x1 - x0) * k / steps;
+    double prod = 1.0;
+    for (int t = 0; t < p; ++t) prod *= (x - t);
+    best = std::max(best, std::fabs(prod));
+  }
+  return best / std::exp(lgamma_fact(p));
+}
+
+// Decide, once per table, which table the fill interpolates.  The fill targets the
+// precision's tolerance (1e-10 of the table maximum in FP64, 1e-5 in FP32-mixed, per
+// (class, pair)); the interpolation may use a quarter of it.  The a posteriori estimate
+// (the p-th differences of the table, launch_fill_estimate) bounds the interpolation
+// error on the tabulated grid, for the interior stencils and for the last one, which is
+// shifted inward at rho_max (its node polynomial is far larger).  When either misses that
+// share, the same tabulation runs again on a grid finer by the integer factor r (interior
+// error falling like r^-p) that reaches p/2 rows beyond rho_max, so that the stencil of
+// every pair up to rho_max is centred, and the fill uses that table.  A loaded table cannot
+// be tabulated again: it is refused instead.  CFFT_OPT_FILL_REFINE >= 1 fixes r (1: the
+// tabulated grid as it is, no estimate).
+template <class T>
+cfft_status ensure_fill_table_t(cfft_ctx* ctx) {
+  if (ctx->fill_r > 0) return CFFT_OK;
+  cudaStream_t st = ctx->stream;
+  const int p = ctx->fill_taps;
+  const int nh = 2 * ctx->q_max + 1;
+  const int forced = (int)std::lround(ctx->opt[CFFT_OPT_FILL_REFINE]);
+  double est_c = -1.0, est_e = -1.0;
+  int r = 1;
+  bool own = false;   // the fill gets a table of its own (finer and/or extended)
+  const double share = 0.25 * (ctx->prec == CFFT_FP64 ? 1e-10 : 1e-5);
+  if (forced >= 1) {
+    r = forced;
+    own = r > 1;
+  } else {
+    const int64_t groups = (int64_t)ctx->channels * ctx->cls_stored * ctx->n_mbf * ctx->n_mbf;
+    const int64_t n_series = groups * nh;
+    CFFT_CUDA(ctx->d_fest.ensure((size_t)n_series * sizeof(double4)), "alloc fill estimate");
+    const double fac_c = lagrange_node_factor(p, 0.5 * p - 1.0, 0.5 * p);
+    const double fac_e = lagrange_node_factor(p, 0.5 * p - 1.0, p - 1.0);
+    CFFT_CUDA(launch_fill_estimate<T>(ctx->d_table.p, n_series, ctx->n_rho, ctx->q_max, p, fac_c, fac_e,
+                                      ctx->d_fest.as<double4>(), st), "fill estimate kernel");
+    std::vector<double4> h((size_t)n_series);
+    CFFT_CUDA(cudaMemcpyAsync(h.data(), ctx->d_fest.p, h.size() * sizeof(double4), cudaMemcpyDeviceToHost, st),
+              "fill estimate");
+    CFFT_CUDA(cudaStreamSynchronize(st), "fill estimate");
+    est_c = 0.0;
+    est_e = 0.0;
+    for (int64_t g = 0; g < groups; ++g) {
+      double zmax = 0.0, ec = 0.0, ee = 0.0;
+      for (int q = 0; q < nh; ++q) {
+        const double4& v = h[(size_t)(g * nh + q)];
+        zmax = std::max(zmax, v.x);
+        ec = std::max(ec, v.y);
+        ee = std::max(ee, v.z);
+      }
+      if (zmax > 0.0) {
+        est_c = std::max(est_c, ec / zmax);
+        est_e = std::max(est_e, ee / zmax);
+      }
+    }
+    if (std::max(est_c, est_e) > share) {
+      own = true;
+      // aim the interior at a quarter of the share, so that the finer grid keeps a margin
+      if (est_c > 0.25 * share) r = (int)std::ceil(std::pow(4.0 * est_c / share, 1.0 / p) - 1e-9);
+      r = std::max(r, 1);
+    }
+  }
+  ctx->info.fill_err_est = std::max(est_c, est_e);
+  const int ext = own ? p / 2 : 0;   // rows beyond rho_max
+  const int64_t n_f = (int64_t)(ctx->n_rho - 1) * r + 1 + ext;
+  if (own && ctx->table_loaded)
+    return fail(ctx, CFFT_ERR_ARG,
+                "the loaded table's rho grid misses the fill's target (estimated interpolation error " +
+                std::to_string(est_c) + " inside, " + std::to_string(est_e) +
+                " at rho_max, of the table maximum): load a table on a finer grid that reaches " +
+                std::to_string(p / 2) + " rows beyond the largest element distance, or set "
+                "CFFT_OPT_FILL_REFINE = 1 to fill on this grid");
+  if (n_f > (1 << 20))
+    return fail(ctx, CFFT_ERR_ARG, "the fill needs a table of " + std::to_string(n_f) +
+                " rho points (more than 1048576): tabulate to a smaller rho_max or raise the fill taps");
+  const double d_f = ctx->rho_max / ((double)(ctx->n_rho - 1) * r);
+  const double rho_f = d_f * (double)(n_f - 1);
+  if (own) {
+    // the same tabulation on the fill's grid, with the options the table was made with
+    double saved[13];
+    std::memcpy(saved, ctx->opt, sizeof(saved));
+    std::memcpy(ctx->opt, ctx->tab_opt, sizeof(saved));
+    cfft_status stt = tabulate_impl<T>(ctx, (int)n_f, rho_f, ctx->d_ftable, false);
+    std::memcpy(ctx->opt, saved, sizeof(saved));
+    if (stt != CFFT_OK) return stt;
+  }
+  ctx->fill_r = r;
+  ctx->fill_own = own;
+  ctx->n_frho = own ? (int)n_f : ctx->n_rho;
+  ctx->frho_max = own ? rho_f : ctx->rho_max;
+  ctx->info.fill_refine = r;
+  ctx->info.fill_n_rho = ctx->n_frho;
+  return CFFT_OK;
+}
+
+cfft_status ensure_fill_table(cfft_ctx* ctx) {
+  return ctx->prec == CFFT_FP64 ? ensure_fill_table_t<double>(ctx) : ensure_fill_table_t<float>(ctx);
+}
+
+// the table the fill and its adjoint interpolate
+template <class T>
+const cpx<T>* fill_table(const cfft_ctx* ctx) {
+  return (ctx->fill_own ? ctx->d_ftable : ctx->d_table).template as<cpx<T>>();
 }
 
 template <class T, class TO>
 cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot, void* z,
                       int64_t ld) {
+  cfft_status fs = ensure_fill_table(ctx);
+  if (fs != CFFT_OK) return fs;
   FillArgs<T, TO> fa{};
   fa.n_el = n_el;
   fa.n_mbf = ctx->n_mbf;
   fa.q_max = ctx->q_max;
   fa.n_harm = 2 * ctx->q_max + 1;
-  fa.n_rho = ctx->n_rho;
+  fa.n_rho = ctx->n_frho;
   fa.taps = ctx->fill_taps;
   fa.n_cls = ctx->cls_stored;
-  fa.inv_d_rho = (ctx->n_rho - 1) / ctx->rho_max;
+  fa.inv_d_rho = (ctx->n_frho - 1) / ctx->frho_max;
   fa.rho_max = ctx->rho_max;
   fa.ld = ld;
-  fa.table = ctx->d_table.as<cpx<T>>();
+  fa.table = fill_table<T>(ctx);
   fa.pos = pos;
   fa.rot = rot;
   fa.z = reinterpret_cast<cpx<TO>*>(z);
@@ -598,32 +743,34 @@ cfft_status fill_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot
 template <class T, class TG>
 cfft_status fill_backward_impl(cfft_ctx* ctx, int n_el, const double* pos, const int* rot,
                                const void* grad, int64_t ld_g, double* grad_pos, double* grad_theta) {
+  cfft_status fs = ensure_fill_table(ctx);
+  if (fs != CFFT_OK) return fs;
   FillBackArgs<T, TG> b{};
   FillArgs<T, float>& fa = b.f;
   fa.n_el = n_el;
   fa.n_mbf = ctx->n_mbf;
   fa.q_max = ctx->q_max;
   fa.n_harm = 2 * ctx->q_max + 1;
-  fa.n_rho = ctx->n_rho;
+  fa.n_rho = ctx->n_frho;
   fa.taps = ctx->fill_taps;
   fa.n_cls = ctx->cls_stored;
-  fa.inv_d_rho = (ctx->n_rho - 1) / ctx->rho_max;
+  fa.inv_d_rho = (ctx->n_frho - 1) / ctx->frho_max;
   fa.rho_max = ctx->rho_max;
   fa.ld = 0;
-  fa.table = ctx->d_table.as<cpx<T>>();
+  fa.table = fill_table<T>(ctx);
   fa.pos = pos;
   fa.rot = rot;
   fa.z = nullptr;
   CFFT_CUDA(ctx->d_flag.ensure(sizeof(int) * 4), "alloc flag");   // a loaded table skips tabulation
   fa.err = ctx->d_flag.as<int>() + 1;
-  const size_t table_elems = (size_t)ctx->cls_stored * ctx->n_mbf * ctx->n_mbf * fa.n_harm * ctx->n_rho;
+  const size_t table_elems = (size_t)ctx->cls_stored * ctx->n_mbf * ctx->n_mbf * fa.n_harm * ctx->n_frho;
   if (ctx->channels == 3) {
     b.dtab_eps = fa.table + table_elems;
     b.dtab_h = fa.table + 2 * table_elems;
   }
   b.grad = reinterpret_cast<const cpx<TG>*>(grad);
   b.ld_g = ld_g;
-  b.d_rho = ctx->rho_max / (ctx->n_rho - 1);
+  b.d_rho = ctx->frho_max / (ctx->n_frho - 1);
   b.grad_pos = grad_pos;
   b.grad_theta = grad_theta;
   CFFT_CUDA(cudaMemsetAsync(fa.err, 0, sizeof(int), ctx->stream), "flag");
@@ -890,7 +1037,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       for (int c = 0; c < n_chunks; ++c) {
         int r_top = std::min((c + 1) * rchunk, n_rho) - 1;
         double rho_top = r_top * d_rho;
-        int np = alpha_nodes(ip[i].beta_abs, rho_top, q_max, margin);
+        int np = alpha_nodes(ip[i].beta_abs, rho_top, q_max, margin, alpha_cbrt_coef(fp64));
         cnodes[(size_t)i * n_chunks + c] = np;
         coff[(size_t)i * n_chunks + c] = cos_total;
         cos_total += np;
@@ -1320,7 +1467,7 @@ void cfft_destroy(cfft_ctx* ctx) {
                       &ctx->green_r, &ctx->dp_eps, &ctx->dr_eps, &ctx->dp_h, &ctx->dr_h, &ctx->d_shapes, &ctx->d_bx, &ctx->d_by, &ctx->d_q,
                       &ctx->d_y, &ctx->d_grid, &ctx->d_table, &ctx->d_tw, &ctx->d_cnodes,
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
-                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
+                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->d_ftable, &ctx->d_fest, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
                       &ctx->tc_bmat_mirror, &ctx->tc_shapes};
     for (DevBuf* b : bufs) b->release();
     for (auto& e : ctx->ev)
@@ -1441,8 +1588,9 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 11) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 12) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
+  if (key == CFFT_OPT_FILL_REFINE) ctx->fill_r = 0;   // decided again at the next fill
   return CFFT_OK;
 }
 
@@ -1465,8 +1613,11 @@ cfft_status cfft_tabulate_reactions(cfft_ctx* ctx, int q_max, double rho_max, in
   ctx->prec = precision;
   ctx->cls_stored = rotation_classes;
   ctx->cls_computed = rotation_classes == 4 ? 3 : 1;
-  if (precision == CFFT_FP64) return tabulate_impl<double>(ctx);
-  return tabulate_impl<float>(ctx);
+  ctx->fill_r = 0;
+  ctx->table_loaded = false;
+  std::memcpy(ctx->tab_opt, ctx->opt, sizeof(ctx->tab_opt));
+  if (precision == CFFT_FP64) return tabulate_impl<double>(ctx, n_rho, rho_max, ctx->d_table, true);
+  return tabulate_impl<float>(ctx, n_rho, rho_max, ctx->d_table, true);
 }
 
 cfft_status cfft_get_table(const cfft_ctx* ctx, const void** dev_ptr, int64_t shape[4],
@@ -1531,6 +1682,11 @@ cfft_status cfft_load_table(cfft_ctx* ctx, int n_mbf, int q_max, double rho_max,
   ctx->cls_computed = rotation_classes == 4 ? 3 : 1;
   ctx->fill_taps = fill_taps;
   ctx->channels = 1;
+  ctx->fill_r = 0;
+  ctx->table_loaded = true;
+  ctx->info.fill_err_est = -1.0;
+  ctx->info.fill_refine = 0;
+  ctx->info.fill_n_rho = 0;
   ctx->has_table = true;
   return CFFT_OK;
 }

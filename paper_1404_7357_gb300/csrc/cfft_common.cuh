@@ -375,6 +375,12 @@ cudaError_t launch_fill_backward(const FillBackArgs<T, TG>& a, cudaStream_t s);
 // g[i][j] = 2 r_i conj(v_j), n x n row-major (dL/dZ' of sum |Z' v - t|^2 with r = Z' v - t)
 template <class T>
 cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, cudaStream_t s);
+// a posteriori interpolation-error estimate of the fill on a table's rho grid: per series
+// (n_rho entries each) out = (max |Z|, max over interior windows of |p-th difference| *
+// fac_c, the last window's |p-th difference| * fac_e, 0)
+template <class T>
+cudaError_t launch_fill_estimate(const void* table, int64_t n_series, int n_rho, int q_max, int taps,
+                                 double fac_c, double fac_e, double4* out, cudaStream_t s);
 // plan.ok: bucketed fill with `scratch` of plan.scratch bytes; else the per-row fill
 template <class T, class TO>
 cudaError_t launch_fill(const FillArgs<T, TO>& a, const FillBucketPlan& plan, void* scratch, cudaStream_t s);

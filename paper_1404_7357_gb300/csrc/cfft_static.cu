@@ -1,10 +1,9 @@
 // Allocation-free back-projection entry point (cfft_backproject_static).
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured (an allocation there would break or be baked into the
-// capture), plug-ins hosted by an application that owns every device
-// allocation through its own pool, and real-time loops where a driver-level
-// allocation (which may synchronize the device) is not acceptable.  For them
+// Some callers cannot call cudaMalloc: plug-ins hosted by an application that
+// owns every device allocation through its own pool, and real-time loops
+// where a driver-level allocation (which may synchronize the device) is not
+// acceptable.  For them
 // this entry point runs the back-projection stage on caller-owned input and
 // output buffers and keeps its only scratch -- the angular node counts,
 // their offsets and the node cosines of every chunk of rows -- in the
@@ -49,13 +48,14 @@ void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
 // the angular node rule of the tabulation, per chunk, and the running offsets
+// (cbrt_coef: 2 for complex64 tables, 4 for complex128, as in the tabulation)
 __global__ void static_chunk_nodes_kernel(int n_chunks, int n_rho, double d_rho,
                                           double beta_abs_max, int q_max, double margin,
-                                          int* nodes, int64_t* offsets) {
+                                          double cbrt_coef, int* nodes, int64_t* offsets) {
   for (int c = threadIdx.x; c < n_chunks; c += blockDim.x) {
     int r_top = min((c + 1) * kRowChunk, n_rho) - 1;
     double z = beta_abs_max * (r_top * d_rho);
-    nodes[c] = (int)ceil(0.5 * (z + q_max) + 2.0 * cbrt(z) + 0.5 * margin) + 1;
+    nodes[c] = (int)ceil(0.5 * (z + q_max) + cbrt_coef * cbrt(z) + 0.5 * margin) + 1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -67,9 +67,9 @@ __global__ void static_chunk_nodes_kernel(int n_chunks, int n_rho, double d_rho,
   }
 }
 
-int host_nodes(double beta_abs_max, double rho, int q_max, double margin) {
+int host_nodes(double beta_abs_max, double rho, int q_max, double margin, double cbrt_coef) {
   double z = beta_abs_max * rho;
-  return (int)std::ceil(0.5 * (z + q_max) + 2.0 * std::cbrt(z) + 0.5 * margin) + 1;
+  return (int)std::ceil(0.5 * (z + q_max) + cbrt_coef * std::cbrt(z) + 0.5 * margin) + 1;
 }
 
 template <class T>
@@ -78,6 +78,7 @@ cfft_status run(cudaStream_t st, unsigned char* scratch, const void* grid, void*
                 double delta_s, int sigma, int taps, double beta_abs_max, double margin) {
   const int n_chunks = (n_rho + kRowChunk - 1) / kRowChunk;
   const double d_rho = rho_max / (n_rho - 1);
+  const double cbrt_coef = sizeof(T) == 8 ? 4.0 : 2.0;
   // the grid must reach rho_max plus half a stencil (compared in floating point, so that
   // no huge ratio is converted to an integer)
   if (std::ceil(rho_max / delta_s) + taps / 2 + 2 > (double)grid_half) return CFFT_ERR_ARG;
@@ -88,7 +89,7 @@ cfft_status run(cudaStream_t st, unsigned char* scratch, const void* grid, void*
   for (int c = 0; c < n_chunks; ++c) {
     int r_top = std::min((c + 1) * kRowChunk, n_rho) - 1;
     double rho_top = r_top * d_rho;
-    int np = host_nodes(beta_abs_max, rho_top, q_max, margin) + 2;
+    int np = host_nodes(beta_abs_max, rho_top, q_max, margin, cbrt_coef) + 2;
     total += np;
     max_nodes = std::max(max_nodes, np);
     int kseg = std::min(grid_half, (int)std::ceil(rho_top / delta_s) + taps / 2 + 2);
@@ -106,7 +107,7 @@ cfft_status run(cudaStream_t st, unsigned char* scratch, const void* grid, void*
   double* cosv = reinterpret_cast<double*>(scratch + kCountsBytes + kOffsetsBytes);
   // every scratch entry the back-projection reads is rewritten here first
   static_chunk_nodes_kernel<<<1, 1024, 0, st>>>(n_chunks, n_rho, d_rho, beta_abs_max, q_max,
-                                                margin, nodes, offsets);
+                                                margin, cbrt_coef, nodes, offsets);
   if (cudaGetLastError() != cudaSuccess) return CFFT_ERR_CUDA;
   if (launch_chunk_cosines(nodes, offsets, n_chunks, max_nodes, cosv, st) != cudaSuccess)
     return CFFT_ERR_CUDA;

@@ -410,6 +410,97 @@ cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, 
   return cudaGetLastError();
 }
 
+namespace {
+
+// A posteriori estimate of the fill's interpolation error on a table's rho grid.
+// The Lagrange stencil of p taps at step d leaves the remainder
+//   f(u) - L(u) = f^(p)(xi) / p! * prod_t (u - t) d^p,
+// and the p-th difference of p + 1 consecutive table rows is d^p f^(p) at a
+// point of their span, so for every window of p + 1 rows the error of the
+// stencils there is about |nabla^p Z| * pi_max / p!, with pi_max the largest
+// |prod_t (x - t)| over the stencil coordinates x that those stencils use
+// (fac_c: the central interval of an interior stencil; fac_e: the last stencil,
+// shifted inward at rho_max).  Rows below rho = 0 follow the parity
+// Z_q(-rho) = (-1)^q Z_q(rho), as in the fill.  One block per table series
+// (channel, class, pair, harmonic); out[series] = (max |Z|, max estimate of the
+// interior stencils, estimate of the last stencil, 0).
+template <class T>
+__global__ void fill_estimate_kernel(const cpx<T>* table, int n_rho, int q_max, int n_harm,
+                                     int taps, double fac_c, double fac_e, double4* out) {
+  const int64_t series = blockIdx.x;
+  const cpx<T>* z = table + series * (int64_t)n_rho;
+  const int q = (int)(series % n_harm) - q_max;
+  const double par = (q & 1) ? -1.0 : 1.0;
+  double coef[kMaxTaps + 1];
+  {
+    // (-1)^(p-k) C(p, k)
+    double c = 1.0;
+#pragma unroll
+    for (int k = 0; k <= kMaxTaps; ++k) {
+      if (k <= taps) coef[k] = ((taps - k) & 1) ? -c : c;
+      c = c * (double)(taps - k) / (double)(k + 1);
+    }
+  }
+  double zmax = 0.0, emax = 0.0, eedge = 0.0;
+  for (int r = threadIdx.x; r < n_rho; r += blockDim.x) {
+    const cpx<T> v = z[r];
+    zmax = fmax(zmax, hypot((double)v.re, (double)v.im));
+  }
+  const int j_lo = -(taps / 2 - 1), j_hi = n_rho - taps - 1;
+  for (int j = j_lo + (int)threadIdx.x; j <= j_hi; j += blockDim.x) {
+    double dr = 0.0, di = 0.0;
+#pragma unroll
+    for (int k = 0; k <= kMaxTaps; ++k) {
+      if (k <= taps) {
+        const int i = j + k;
+        const cpx<T> v = z[i < 0 ? -i : i];
+        const double s = (i < 0 ? par : 1.0) * coef[k];
+        dr = fma(s, (double)v.re, dr);
+        di = fma(s, (double)v.im, di);
+      }
+    }
+    if (j == j_hi)
+      eedge = hypot(dr, di) * fac_e;
+    else
+      emax = fmax(emax, hypot(dr, di) * fac_c);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, off));
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    eedge = fmax(eedge, __shfl_xor_sync(0xffffffffu, eedge, off));
+  }
+  __shared__ double4 red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double4(zmax, emax, eedge, 0.0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+      acc.x = fmax(acc.x, red[w].x);
+      acc.y = fmax(acc.y, red[w].y);
+      acc.z = fmax(acc.z, red[w].z);
+    }
+    out[series] = acc;
+  }
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_fill_estimate(const void* table, int64_t n_series, int n_rho, int q_max, int taps,
+                                 double fac_c, double fac_e, double4* out, cudaStream_t s) {
+  if (n_series < 1 || n_series > 0x7fffffff || taps < 2 || taps > kMaxTaps || n_rho < taps + 1)
+    return cudaErrorInvalidValue;
+  fill_estimate_kernel<T><<<(unsigned)n_series, 256, 0, s>>>(
+      reinterpret_cast<const cpx<T>*>(table), n_rho, q_max, 2 * q_max + 1, taps, fac_c, fac_e, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fill_estimate<float>(const void*, int64_t, int, int, int, double, double,
+                                                 double4*, cudaStream_t);
+template cudaError_t launch_fill_estimate<double>(const void*, int64_t, int, int, int, double, double,
+                                                  double4*, cudaStream_t);
+
 template cudaError_t launch_residual_outer<float>(const void*, const void*, int, void*, cudaStream_t);
 template cudaError_t launch_residual_outer<double>(const void*, const void*, int, void*, cudaStream_t);
 

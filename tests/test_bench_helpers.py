@@ -146,9 +146,10 @@ def test_fill_sample_pairs_cover_the_distance_bins():
     pairs = bench.fill_sample_pairs(pos, rot)
     assert len(pairs) == 17 and pairs[0][0] == pairs[0][1]
     d = [float(np.hypot(*(pos[i] - pos[j]))) for i, j in pairs]
-    assert all(rot[i] == 0 and rot[j] == 0 for i, j in pairs)        # class (0, 0) only
-    for b, (lo, hi) in enumerate(((0.4, 2.0), (20.0, 40.0), (60.0, 80.0), (100.0, 121.0))):
+    cls = [2 * int(rot[i]) + int(rot[j]) for i, j in pairs]
+    for b, (lo, hi) in enumerate(bench.FILL_BINS):
         assert all(lo <= x < hi for x in d[1 + 4 * b:5 + 4 * b])
+        assert cls[1 + 4 * b:5 + 4 * b] == [0, 1, 2, 3]               # every rotation class per bin
     assert bench.fill_sample_pairs(pos, rot) == pairs                 # seeded
 
 
@@ -173,6 +174,29 @@ def test_fill_parity_measure():
     assert r["max_rel_err_vs_oracle"] == pytest.approx(1e-4, rel=1e-9) and r["blocks"] == 3
     other = workloads.patch_m4(n=128, n_rho=32, rho_max=5.0, q_max=2)
     assert "skipped" in bench.fill_parity((other, pos, rot, pairs, blocks), wl, nodes, hq)
+
+
+def test_fill_parity_rotated_classes():
+    """With rotated elements fill_parity computes the harmonics of each class the pairs
+    need (only the unrotated class is handed in): exact blocks give zero error, a block
+    computed with the unrotated class in place of a mixed one does not."""
+    from oracle import contour as oc
+    from oracle import fill as ofill
+    wl = workloads.patch_m4(n=64, n_rho=32, rho_max=5.0, q_max=2)
+    c = wl.contour
+    nodes = oc.contour_nodes(c.n, c.beta_max, c.beta_p, c.height)
+    hq = {cls: bench.class_harmonics(wl, nodes, cls, 1) for cls in range(4)}
+    pos = np.array([[0.0, 0.0], [1.0, 0.5], [-2.0, 1.0]])
+    rot = np.array([0, 1, 1], dtype=np.int32)
+    pairs = [(0, 0), (0, 1), (1, 0), (2, 1)]            # classes 0, 1, 2, 3
+    blocks = list(ofill.entries(hq, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, pairs))
+    r = bench.fill_parity((wl, pos, rot, pairs, blocks), wl, nodes, hq[0])
+    assert r["max_rel_err_vs_oracle"] == 0.0 and r["rotation_classes"] == [0, 1, 2, 3]
+    wrong = ofill.entries({0: hq[0], 1: hq[0]}, wl.qs, nodes["beta_c"], nodes["weight"], pos, rot, [(0, 1)])
+    expect = np.abs(wrong[0] - blocks[1]).max() / max(np.abs(x).max() for x in blocks)
+    blocks[1] = wrong[0]
+    got = bench.fill_parity((wl, pos, rot, pairs, blocks), wl, nodes, hq[0])["max_rel_err_vs_oracle"]
+    assert expect > 1e-8 and got == pytest.approx(expect, rel=1e-12)
 
 
 def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):

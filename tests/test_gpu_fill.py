@@ -12,6 +12,8 @@ from tests import cfft_cases as cc
 
 pytestmark = pytest.mark.gpu
 
+TOL = {"fp32": 1e-5, "fp64": 1e-10}
+
 
 @pytest.fixture(scope="module")
 def torch_cuda():
@@ -137,12 +139,14 @@ def test_table_checkpoint_and_resume(torch_cuda, tmp_path, precision):
     element or contour fills from the saved table exactly as the tabulating one does."""
     torch = torch_cuda
     from paper_1404_7357_gb300 import cfft
-    wl = cc.small_patch(precision, n=1024, n_rho=512, rho_max=5.0, q_max=3, rotation_classes=4)
+    wl = cc.small_patch(precision, n=1024, n_rho=1024, rho_max=5.0, q_max=3, rotation_classes=4)
     ctx, _ = cc.gpu_table(wl)
     pos = workloads.poisson_disc(40, 2.4, 0.5, seed=81)
     rot = workloads.rotations(len(pos), seed=81)
     dt = torch.complex128 if precision == "fp64" else torch.complex64
     ref = _fill(torch, ctx, pos, rot, 4, dt)
+    # this grid meets the fill's target as tabulated: the fill used the saved table itself
+    assert ctx.info()["fill_refine"] == 1 and ctx.info()["fill_n_rho"] == wl.n_rho
     desc = ctx.save_table(str(tmp_path / "table"))
     fresh = cfft.Context(0)
     got_desc = fresh.load_table(str(tmp_path / "table"))
@@ -152,6 +156,75 @@ def test_table_checkpoint_and_resume(torch_cuda, tmp_path, precision):
     # a description that does not fit is refused
     with pytest.raises(cfft.CfftError):
         fresh._check(cfft._lib.cfft_load_table(fresh._h, 4, 3, 5.0, 10, 0, 4, 8, None, 1))
+
+
+def _line_array():
+    """Elements on a line whose pair distances run from 0.03 to 2.97 wavelengths: the short
+    ones where the table varies fastest, the long ones within half a stencil of rho_max."""
+    x = np.array([0.0, 0.031, 0.077, 0.52, 1.5, 2.97])
+    return np.stack([x, 0.37 * x], 1) / np.hypot(1.0, 0.37)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_fill_meets_target_at_every_distance(torch_cuda, precision):
+    """The table grid here (256 rho points to 3 wavelengths) is too coarse for the fill's
+    Lagrange stencil at short distances and next to rho_max.  The library estimates the
+    interpolation error from the table's p-th differences, finds it above the precision's
+    share, and tabulates the fill's own table on a finer grid reaching past rho_max: every
+    entry then meets the target against the oracle's exact fill.  Forcing the tabulated grid
+    (FILL_REFINE = 1) shows the error the refinement removes, and that the estimate is not
+    below it."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch(precision, n=1024, n_rho=256, rho_max=3.0, q_max=2)
+    ctx, _ = cc.gpu_table(wl)
+    pos = _line_array()
+    a, m = len(pos), 4
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    nodes, hq = cc.oracle_harmonics(wl)
+    pairs = [(i, j) for i in range(a) for j in range(a)]
+    blocks = cc.oracle_fill_entries(wl, hq, nodes, pos, np.zeros(a, dtype=np.int32), pairs)
+    zref = np.zeros((a * m, a * m), dtype=np.complex128)
+    for (i, j), blk in zip(pairs, blocks):
+        zref[i * m:(i + 1) * m, j * m:(j + 1) * m] = blk
+    scale = np.abs(zref).max()
+    got = _fill(torch, ctx, pos, None, m, dt)
+    info = ctx.info()
+    err = np.abs(got - zref).max() / scale
+    ctx.set_option(cfft.OPT_FILL_REFINE, 1)
+    coarse = _fill(torch, ctx, pos, None, m, dt)
+    err_coarse = np.abs(coarse - zref).max() / scale
+    print(precision, "estimate on the tabulated grid %.3g, refine %d, fill grid %d: error %.3g; on the "
+          "tabulated grid %.3g" % (info["fill_err_est"], info["fill_refine"], info["fill_n_rho"], err,
+                                    err_coarse))
+    share = 0.25 * TOL[precision]
+    assert info["fill_err_est"] > share and info["fill_n_rho"] > wl.n_rho
+    assert info["fill_n_rho"] == (wl.n_rho - 1) * info["fill_refine"] + 1 + info["fill_taps"] // 2
+    assert err < TOL[precision]
+    assert err_coarse > err and err_coarse < 2.0 * info["fill_err_est"]
+
+
+def test_loaded_coarse_table_is_refused(torch_cuda, tmp_path):
+    """A loaded table cannot be tabulated again: a fill on a grid that misses the target is
+    refused (CFFT_ERR_ARG) instead of returning a less accurate matrix; FILL_REFINE = 1 then
+    fills on that grid, exactly as the tabulating context does with the same setting."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    wl = cc.small_patch("fp64", n=1024, n_rho=256, rho_max=3.0, q_max=2)
+    ctx, _ = cc.gpu_table(wl)
+    ctx.set_option(cfft.OPT_FILL_REFINE, 1)
+    pos = _line_array()
+    ref = _fill(torch, ctx, pos, None, 4, torch.complex128)
+    ctx.save_table(str(tmp_path / "coarse"))
+    fresh = cfft.Context(0)
+    fresh.load_table(str(tmp_path / "coarse"))
+    z = torch.zeros((len(pos) * 4, len(pos) * 4), dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(cfft.CfftError) as ei:
+        fresh.fill_reduced_matrix(torch.tensor(pos, device="cuda:0"), None, z)
+    assert ei.value.status == 1
+    fresh.set_option(cfft.OPT_FILL_REFINE, 1)
+    got = _fill(torch, fresh, pos, None, 4, torch.complex128)
+    assert np.array_equal(got, ref)
 
 
 @pytest.mark.slow

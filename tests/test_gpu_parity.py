@@ -184,6 +184,24 @@ def test_patch_full_size_sampled(torch_cuda):
     assert err.max() < TOL["fp32"]
 
 
+@pytest.mark.slow
+def test_patch_full_size_fp64_sampled(torch_cuda):
+    """The same full-size patch table in the plain FP64 form (zero padding 8, 16-tap
+    stencils, Taylor order for 1e-13), against the oracle at the 1e-10 target on sampled
+    rho rows for every pair and harmonic -- up to rho = 50 wavelengths, where the angular
+    quadrature of the back-projection needs the most nodes."""
+    wl = workloads.patch_m4(precision="fp64")
+    ctx, got = cc.gpu_table(wl)
+    rows = np.array([0, 1, 7, 333, 2048, 4097, 6000, 7500, 8191])
+    ref, _, _ = cc.oracle_table(wl, rho_index=rows)
+    err = cc.rel_err_per_pair(got[..., rows], ref)
+    # per sampled row, so that a failure shows where in rho it lies
+    per_row = (np.abs(got[..., rows] - ref).max(axis=(0, 1, 2)) /
+               np.abs(ref).reshape(-1, len(rows)).max())
+    print("full-size FP64 sampled rel err", err.max(), "by row", dict(zip(rows.tolist(), per_row)))
+    assert err.max() < TOL["fp64"]
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_backprojection_forms_agree(torch_cuda, precision):
     """The matrix form and the direct gather form of the back-projection evaluate the
