@@ -53,9 +53,10 @@ def load_peaks():
     return d
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA pipe peak: 152 SMs x 128 lanes x 2 flops x clock."""
-    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, n_sm=N_SM):
+    """FP32 FMA pipe peak from unit counts: SMs x 128 lanes x 2 flops x clock (GB300: 152
+    SMs; the bench passes the device's own count)."""
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def dist_env():
@@ -276,7 +277,19 @@ def bench_fp64(torch, cfft, args, dev):
             "ms_per_step": sum(ms) / steps, "steps": steps,
             "stages_ms": {k: inf["ms_" + k] for k in ("contour", "integrand", "fft", "backproject")},
             "info": {k: inf[k] for k in ("taylor_order", "sigma", "fft_len", "sub_len", "bp_taps",
-                                         "bp_form", "spectra_tc")}}, table
+                                         "bp_form", "spectra_tc")}, "_info": inf}, table
+
+
+def fp64_roofline(inf, wl, fp64_peak):
+    """Stages of the plain FP64 tabulation against the measured FP64 FMA peak: every flop
+    of that form runs on the FP64 pipe (no tensor cores)."""
+    fl = stage_flops(inf, wl)
+    out = {}
+    for k in ("contour", "integrand", "fft", "backproject"):
+        t = inf["ms_" + k] / 1e3
+        tf = fl[k]["algorithmic"] / t / 1e12
+        out[k] = {"ms": inf["ms_" + k], "tflops": tf, "frac": tf / fp64_peak}
+    return {"bound": "fp64", "peak_tflops": fp64_peak, "stages": out}
 
 
 def bench_e2e(torch, cfft, args, dev, wl):
@@ -574,21 +587,35 @@ def table_rel_err(table, ref, rows):
 
 
 def stage_flops(inf, wl):
-    """Algorithmic FP32 flops of each tabulation stage for one launch."""
+    """Work of each tabulation stage for one launch, split by pipe: "fp32" = algorithmic
+    flops on the FP32 pipe, "tensor" = the tensor-core flops the stage executed (three TF32
+    products per term, as the library counts them), "algorithmic" = the stage's arithmetic
+    counted once whichever pipe ran it.  The back-projection's matrix forms evaluate the
+    quadrature as interpolation-matrix products (8 flops per complex MAC) plus the node
+    stencils added into the matrices ((6 taps + 16) flops each); "per_node_unit" is the
+    gather form's (8 taps + 8) flops per (rho, alpha') node and series, the scope table's
+    unit, which the matrix form beats by sharing each stencil across a chunk of series."""
     m = wl.element.n_mbf
     L = inf["sub_len"]
     taps = inf["bp_taps"]
-    if inf.get("bp_form", 0) in (1, 2, 3):
-        # interpolation-matrix products (complex MACs) + node stencils added into the matrices
-        # (form 3 runs the products on the tensor cores: the same work, counted once)
-        bp = 8.0 * inf["work_bp_macs"] + (6.0 * taps + 16.0) * inf["work_bp_stencils"]
+    form = inf.get("bp_form", 0)
+    per_node = inf["work_bp_nodes"] * (8.0 * taps + 8.0)
+    if form in (1, 2, 3):
+        prod = 8.0 * inf["work_bp_macs"]
+        sten = (6.0 * taps + 16.0) * inf["work_bp_stencils"]
+        bp = {"algorithmic": prod + sten, "fp32": sten if form == 3 else prod + sten,
+              "tensor": inf.get("tc_flops_backproject", 0.0) if form == 3 else 0.0}
     else:
-        bp = inf["work_bp_nodes"] * (4 * taps + 8)
+        bp = {"algorithmic": per_node, "fp32": per_node, "tensor": 0.0}
+    bp["per_node_unit"] = per_node
+    gemm = inf["work_points"] * 2 * 8.0 * inf["n_basis"] * m           # both MBF spectra (Eq. 11)
+    rest = inf["work_points"] * m * m * (8.0 * inf["n_harm"] + 30.0)    # kernel + harmonic DFT
+    tc_int = inf.get("tc_flops_integrand", 0.0) if inf.get("spectra_tc", 0) else 0.0
+    fft = inf["work_subffts"] * 5.0 * L * math.log2(L)
     return {
-        "contour": wl.contour.n * 200.0,
-        # complex GEMM of the MBF spectra (both sides) + kernel + harmonic DFT per point
-        "integrand": inf["work_points"] * (2 * 8.0 * inf["n_basis"] * m + m * m * (8.0 * inf["n_harm"] + 30.0)),
-        "fft": inf["work_subffts"] * 5.0 * L * math.log2(L),
+        "contour": {"algorithmic": wl.contour.n * 200.0, "fp32": wl.contour.n * 200.0, "tensor": 0.0},
+        "integrand": {"algorithmic": gemm + rest, "fp32": rest if tc_int else gemm + rest, "tensor": tc_int},
+        "fft": {"algorithmic": fft, "fp32": fft, "tensor": 0.0},
         "backproject": bp,
     }
 
@@ -600,30 +627,74 @@ KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.332e6, "fft": 84.809e6 + 8.149e6,
                      "backproject": 17.984e6 + 0.072e6}
 
 
+def pipe_peaks(peaks):
+    """TFLOP/s of the FP32 pipe and of the TF32 tensor cores the roofline divides by: the
+    library's microbenchmarks when the bench measured them ("micro"), else the FP32 unit
+    count x the maximum clock and the bf16 GEMM peak x the nominal TF32 / bf16 ratio."""
+    micro = peaks.get("micro")
+    if micro:
+        return micro["fp32"], micro["tf32"], "measured: cfft_measure_peak microbenchmarks on this GPU"
+    return (fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0), peaks.get("n_sm", N_SM)),
+            peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25,
+            "derived: FP32 unit count x max SM clock; bf16 GEMM peak x 1.1 / 2.25 for TF32")
+
+
 def roofline(infos, wl, peaks, clk):
-    """Dominant kernel of the tabulation step and its fraction of the bounding pipe."""
+    """Dominant kernel of the tabulation step and its fraction of the bounding pipe.  A
+    stage that runs on two pipes (FP32 and tensor cores) is bounded below by
+    max(FP32 flops / FP32 peak, tensor flops / TF32 peak); its bound is the pipe with the
+    larger share and "frac" is that pipe's achieved rate over its peak (= the two-pipe bound
+    over the measured time)."""
     inf = infos[-1]
     ms = {k: float(np.mean([i["ms_" + k] for i in infos])) for k in
           ("contour", "integrand", "fft", "backproject")}
     dominant = max(ms, key=ms.get)
-    peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    p32, ptc, source = pipe_peaks(peaks)
     fl = stage_flops(inf, wl)
-    stages = {k: {"ms": ms[k], "tflops": fl[k] / (ms[k] / 1e3) / 1e12,
-                  "frac": fl[k] / (ms[k] / 1e3) / 1e12 / peak_alu} for k in ms}
     traffic = KERNEL_DRAM_BYTES if not TABLE_SIZE else {}
-    for k in stages:
-        stages[k]["dram_bytes"] = traffic.get(k)
-    achieved = stages[dominant]["tflops"]
-    return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_alu,
-            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic.get(dominant),
+    stages = {}
+    for k in ms:
+        t = ms[k] / 1e3
+        f = fl[k]
+        t32, ttc = f["fp32"] / (p32 * 1e12), f["tensor"] / (ptc * 1e12)
+        bound = "tensor" if ttc > t32 else "alu"
+        st = {"ms": ms[k], "bound": bound,
+              "fp32_flops": f["fp32"], "fp32_tflops": f["fp32"] / t / 1e12, "fp32_frac": t32 / t,
+              "tensor_flops_executed": f["tensor"], "tensor_tflops": f["tensor"] / t / 1e12,
+              "tensor_frac": ttc / t, "frac": max(t32, ttc) / t,
+              "algorithmic_tflops": f["algorithmic"] / t / 1e12, "dram_bytes": traffic.get(k)}
+        if "per_node_unit" in f:
+            st["per_node_unit_tflops"] = f["per_node_unit"] / t / 1e12
+        stages[k] = st
+    d = stages[dominant]
+    if d["bound"] == "tensor":
+        achieved, peak, kind = d["tensor_tflops"], ptc, "TF32 tensor cores (kind::tf32)"
+    else:
+        achieved, peak, kind = d["fp32_tflops"], p32, "FP32 FMA pipe"
+    return {"kernel": dominant, "bound": "tensor" if d["bound"] == "tensor" else "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic.get(dominant),
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)"
-                         % peaks.get("sm_max_mhz", 2070.0),
-            "stages": stages, "algorithmic_flops_per_launch": fl[dominant],
+            "peak_note": "%s; peak source: %s" % (kind, source),
+            "peaks_tflops": {"fp32": p32, "tf32": ptc}, "stages": stages,
+            "algorithmic_flops_per_launch": fl[dominant]["algorithmic"],
             "spectra_on_tensor_cores": bool(inf.get("spectra_tc", 0)), "bp_form": inf.get("bp_form", 0),
-            "note": "algorithmic FP32 flops per stage (GEMM parts run as three TF32 products on the "
-                    "tensor cores in the integrand and back-projection, counted once) over the FP32 "
-                    "FMA peak"}
+            "note": "per stage: FP32-pipe flops and executed tensor-core flops (three TF32 products "
+                    "per term) against the measured peak of each pipe; frac = the two-pipe lower "
+                    "bound on the stage's time over its measured time"}
+
+
+def measure_peaks(cfft, dev, reps=5):
+    """The device's FP32, FP64, TF32-tensor and bf16-tensor peaks from the library's
+    microbenchmarks (TFLOP/s, best of reps launches each), with the SM clock sampled."""
+    clocks = ClockSampler(dev)
+    clocks.start()
+    out = {}
+    for name, which in (("fp32", cfft.PEAK_FP32), ("fp64", cfft.PEAK_FP64), ("tf32", cfft.PEAK_TF32),
+                        ("bf16", cfft.PEAK_BF16)):
+        out[name] = cfft.measure_peak(dev, which, reps)[0]
+    out["clocks"] = clocks.stop()
+    return out
 
 
 def run_cfft(args):
@@ -637,6 +708,8 @@ def run_cfft(args):
     torch.cuda.set_device(dev)
     from paper_1404_7357_gb300 import cfft
     peaks = load_peaks()
+    peaks["n_sm"] = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks["micro"] = measure_peaks(cfft, dev)
 
     if args.only_fill:
         fill, _ = bench_fill(torch, cfft, args, dev)
@@ -660,21 +733,30 @@ def run_cfft(args):
             "roofline": roofline(infos, wl, peaks, clk), "clocks": clk,
             "gpu_launches": launches, "e2e": e2e, "info": infos[-1]}
     if fp64 is not None:
+        inf64 = fp64.pop("_info")
+        if peaks.get("micro"):
+            fp64["roofline"] = fp64_roofline(inf64, wl, peaks["micro"]["fp64"])
         line["fp64_gpu"] = fp64
     if fill is not None:
-        fill["algorithmic_frac_of_fp32_peak"] = (fill["algorithmic_tflops"] /
-                                                 fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0)))
+        p32, ptc, _ = pipe_peaks(peaks)
+        fill["algorithmic_frac_of_fp32_peak"] = fill["algorithmic_tflops"] / p32
         if "tensor_tflops_executed" in fill:
-            # TF32 dense peak from the measured bf16 peak and the nominal TF32 / bf16 ratio (1.1 / 2.25)
-            tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
-            fill["tensor_peak_tflops_tf32"] = tf32_peak
-            fill["tensor_frac"] = fill["tensor_tflops_executed"] / tf32_peak
+            fill["tensor_peak_tflops_tf32"] = ptc
+            fill["tensor_frac"] = fill["tensor_tflops_executed"] / ptc
+        fill["hbm_frac_write"] = fill["hbm_gbs_write"] / peaks.get("hbm_gbs", 6800.0)
         line["fill"] = fill
     if batch is not None:
         line["batch"] = batch
     if grad is not None:
         line["grad"] = grad
     line["peaks_source"] = peaks["_source"]
+    if peaks.get("micro"):
+        line["peaks_measured"] = {"fp32_tflops": peaks["micro"]["fp32"], "fp64_tflops": peaks["micro"]["fp64"],
+                                  "tf32_tflops": peaks["micro"]["tf32"], "bf16_tflops": peaks["micro"]["bf16"],
+                                  "bf16_tflops_cublas": peaks.get("bf16_tflops"),
+                                  "clocks": peaks["micro"]["clocks"],
+                                  "how": "cfft_measure_peak: FMA chains (FP32, FP64) and tcgen05.mma "
+                                         "M128 N256 (kind::tf32, kind::f16 bf16), best of 5 launches"}
     if rank == 0 and world == 1 and not args.skip_cpu:
         workers = max(1, min(32, os.cpu_count() or 1))
         rows = np.linspace(0, wl.n_rho - 1, 8).astype(int)

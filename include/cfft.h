@@ -388,7 +388,11 @@ cfft_status cfft_fill_backward_residual(cfft_ctx* ctx, int n_elements, const dou
  * table maximum (-1: not estimated); fill_refine: the factor r of the grid
  * the fill interpolates (0: no fill since the last tabulation); fill_n_rho:
  * that grid's points (n_rho when the fill uses the tabulated table, else
- * (n_rho - 1) r + 1 + fill_taps / 2, reaching beyond rho_max). */
+ * (n_rho - 1) r + 1 + fill_taps / 2, reaching beyond rho_max).
+ * tc_flops_integrand, tc_flops_backproject: the tensor-core flops the
+ * integrand's spectra GEMM and the back-projection's products executed in the
+ * tabulation (three TF32 products per term, padding included; 0 when that
+ * stage ran on the FP32 pipe). */
 typedef struct {
   int taylor_order, n_alpha, sigma, fft_len, sub_len, grid_half, bp_taps, fill_taps;
   int series, classes, n_pairs, n_harm;
@@ -400,6 +404,7 @@ typedef struct {
   int fill_form;
   double fill_err_est;
   int fill_refine, fill_n_rho;
+  double tc_flops_integrand, tc_flops_backproject;
 } cfft_info;
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
 
@@ -496,6 +501,22 @@ cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls);
  * after < 0 disarms it.  Process-wide, for single-threaded tests only.  The
  * context stays usable: a later call allocates what it needs again. */
 void cfft_test_fail_allocation(int after);
+
+/* Arithmetic peak microbenchmark (no counterpart in the paper; the roofline
+ * fractions of the measurement divide by its results).  which:
+ *   0  FP32 FMA pipe: independent fused multiply-add chains on every SM
+ *      (2 flops per FMA)
+ *   1  FP64 FMA pipe: the same in float64
+ *   2  tensor cores, tcgen05.mma kind::tf32: M 128 x N 256 x K 8 products from
+ *      shared memory into fp32 accumulators in tensor memory, one CTA per SM
+ *   3  tensor cores, kind::f16 with bf16 operands (K 16), the same shape
+ * One untimed launch, then `reps` (1..100) launches timed with CUDA events on
+ * a stream of the call's own; *tflops = flops of a launch / the shortest
+ * launch time, *best_ms = that time (may be NULL).  Allocates and frees a
+ * small output buffer; synchronizes its stream.  Errors: CFFT_ERR_ARG (bad
+ * which, reps, device or pointer), CFFT_ERR_CUDA, CFFT_ERR_TIMEOUT (a bounded
+ * tensor-core wait gave up). */
+cfft_status cfft_measure_peak(int device, int which, int reps, double* tflops, double* best_ms);
 
 /* Checkpoint / resume of a table (the paper's tables are reusable across array
  * layouts for a fixed substrate and element, Section IV-F): installs a table

@@ -65,7 +65,8 @@ class Info(ctypes.Structure):
                [(n, ctypes.c_int) for n in ("spectra_tc", "bp_form")] + \
                [(n, ctypes.c_double) for n in ("work_bp_macs", "work_bp_stencils")] + \
                [("fill_form", ctypes.c_int), ("fill_err_est", ctypes.c_double)] + \
-               [(n, ctypes.c_int) for n in ("fill_refine", "fill_n_rho")]
+               [(n, ctypes.c_int) for n in ("fill_refine", "fill_n_rho")] + \
+               [(n, ctypes.c_double) for n in ("tc_flops_integrand", "tc_flops_backproject")]
 
 
 def _load():
@@ -103,6 +104,7 @@ def _load():
         "cfft_mbf_spectra": ([P, I, P, P], I),
         "cfft_selftest_bounded_wait": ([P, ctypes.c_uint], I),
         "cfft_load_table": ([P, I, I, D, I, I, I, I, P, I], I),
+        "cfft_measure_peak": ([I, I, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -418,6 +420,20 @@ def test_fail_allocation(after):
     """cfft_test_fail_allocation: after `after` successful device allocations the next one
     fails as out of memory (host-side injection; after < 0 disarms)."""
     _lib.cfft_test_fail_allocation(int(after))
+
+
+PEAK_FP32, PEAK_FP64, PEAK_TF32, PEAK_BF16 = range(4)
+
+
+def measure_peak(device, which, reps=5):
+    """cfft_measure_peak: (TFLOP/s, ms) of the best of ``reps`` timed launches of the
+    microbenchmark ``which`` (PEAK_FP32, PEAK_FP64 FMA pipes; PEAK_TF32, PEAK_BF16 tensor
+    cores) on CUDA device ``device``."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = _lib.cfft_measure_peak(int(device), int(which), int(reps), ctypes.byref(tf), ctypes.byref(ms))
+    if st != 0:
+        raise CfftError(st, "cfft_measure_peak failed")
+    return tf.value, ms.value
 
 
 def backproject_static(grid, table, series_per_q, q_max, rho_max, grid_half, delta_s, sigma, taps,

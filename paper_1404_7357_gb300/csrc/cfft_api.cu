@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "cfft_common.cuh"
+#include "spectra_tc.cuh"
 
 namespace cfft {
 template <class T>
@@ -70,6 +71,7 @@ struct DevBuf {
 
 struct cfft_ctx {
   int device = 0;
+  int sm_count = 1;   // of the device (persistent grids, FFT sub-length choice)
   cudaStream_t stream = nullptr;
   std::string err = "no error";
   // substrate
@@ -248,7 +250,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   int L = 1;
   while ((P % (2 * (int64_t)L)) == 0 && 2 * L <= l_max) L *= 2;
   if (L < 64) return fail(ctx, CFFT_ERR_ARG, "sigma * n must be divisible by 64");
-  while (L > 256 && (int64_t)series * (P / L) < 2 * 152) L /= 2;
+  while (L > 256 && (int64_t)series * (P / L) < 2 * ctx->sm_count) L /= 2;
   int log2L = 0;
   while ((1 << log2L) < L) ++log2L;
   const int D = (int)(P / L);
@@ -331,7 +333,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   CFFT_CUDA(cudaGetLastError(), "contour kernel");
   CFFT_CUDA(cudaEventRecord(ctx->ev[1], st), "event");
 
-  double bp_nodes = 0, bp_macs = 0, bp_stencils = 0;
+  double bp_nodes = 0, bp_macs = 0, bp_stencils = 0, tc_int_flops = 0, tc_bp_flops = 0;
   int bp_form_used = 0;
   bool in_tc = false, bp_tc = false;
   for (int ch = 0; ch < channels; ++ch) {
@@ -367,6 +369,11 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
       if (integrand_tc_applies(ia)) {
         CFFT_CUDA(launch_integrand_tc(ia, st), "integrand kernel (tensor cores)");
         ran_tc = true;
+        // executed: per CTA of integrand_tc_nodes contour nodes, 256 A rows x K = 4 per
+        // (padded) basis function x tc_ncol columns, three TF32 products
+        const int jt = integrand_tc_nodes(n_alpha);
+        const double nb_pad = (double)((ctx->n_basis + kTcBasis - 1) / kTcBasis * kTcBasis);
+        tc_int_flops += (double)((n + jt - 1) / jt) * 3.0 * 2.0 * 256.0 * 4.0 * nb_pad * ia.tc_ncol;
       }
     }
   }
@@ -439,6 +446,11 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
       const int kmax_c = std::min(K - 1, (int)std::ceil(rho_top / ds) + bp_taps);
       const int n_kt = pform ? (kmax_c + bp_taps / 2 + ktile) / ktile : (2 * kmax_c + ktile) / ktile;
       bp_macs += (double)rows_c * n_kt * ktile * series;
+      if (tform)
+        // executed: per row tile (rchunk rows), |q| and chunk of 16 series per sign, each
+        // K-tile is a (rchunk x 2 ktile) x (2 ktile x 64) product, three TF32 products
+        tc_bp_flops += 3.0 * 2.0 * rchunk * (2.0 * ktile) * 64.0 * n_kt * (ctx->q_max + 1) *
+                       ((series_per_q + 15) / 16);
       const int n_mat = pform ? (ctx->q_max + 1) * ((series_per_q + 15) / 16) : nh;
       bp_stencils += (double)rows_c * (pform ? (cn[c] + 1) / 2 : cn[c]) * n_mat;
     }
@@ -571,6 +583,8 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   in.bp_form = bp_form_used;
   in.work_bp_macs = bp_macs;
   in.work_bp_stencils = bp_stencils;
+  in.tc_flops_integrand = tc_int_flops;
+  in.tc_flops_backproject = tc_bp_flops;
   in.fill_err_est = -1.0;
   in.fill_refine = 0;
   in.fill_n_rho = 0;
@@ -623,7 +637,8 @@ cfft_status ensure_fill_table_t(cfft_ctx* ctx) {
     r = forced;
     own = r > 1;
   } else {
-    const int64_t groups = (int64_t)ctx->channels * ctx->cls_stored * ctx->n_mbf * ctx->n_mbf;
+    // the table itself (channel 0): the derivative tables share its grid and integrand
+    const int64_t groups = (int64_t)ctx->cls_stored * ctx->n_mbf * ctx->n_mbf;
     const int64_t n_series = groups * nh;
     CFFT_CUDA(ctx->d_fest.ensure((size_t)n_series * sizeof(double4)), "alloc fill estimate");
     const double fac_c = lagrange_node_factor(p, 0.5 * p - 1.0, 0.5 * p);
@@ -1300,7 +1315,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
           const FftBucket& fb = r.fb[bkt];
           e = launch_fft_batch<T>(ctx->b_fargs.as<FftArgs<T>>(), ctx->b_ftask.as<int4>() + fb.f0,
                                   (int)(fb.f1 - fb.f0), counters + 1 + bkt, fb.log2L, fb.max_nout,
-                                  max_active, (max_n_item + 127) / 128, 152, st);
+                                  max_active, (max_n_item + 127) / 128, ctx->sm_count, st);
           if (e != cudaSuccess) return e;
           ++launches;
         }
@@ -1309,19 +1324,19 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
           if (tform_b)
             e = launch_backproject_tc_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
                                             ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
-                                            bp_taps, max_nodes, 152, st);
+                                            bp_taps, max_nodes, ctx->sm_count, st);
           else if (pform_b)
             e = launch_backproject_pm_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
                                             ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
-                                            bp_taps, max_nodes, 152, st);
+                                            bp_taps, max_nodes, ctx->sm_count, st);
           else
             e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
                                               ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
-                                              counters, bp_taps, max_nodes, pairs, 152, st);
+                                              counters, bp_taps, max_nodes, pairs, ctx->sm_count, st);
         } else {
           e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
                                             ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
-                                            counters, bp_taps, max_nodes, pairs, 152, st);
+                                            counters, bp_taps, max_nodes, pairs, ctx->sm_count, st);
         }
         if (e != cudaSuccess) return e;
         ++launches;
@@ -1454,6 +1469,12 @@ cfft_status cfft_create(cfft_ctx** out, int device, void* cuda_stream) {
   if (!c) return CFFT_ERR_OOM;
   c->device = device;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      c->sm_count < 1) {
+    cudaGetLastError();
+    delete c;
+    return CFFT_ERR_CUDA;
+  }
   *out = c;
   return CFFT_OK;
 }

@@ -10,6 +10,18 @@
 
 namespace cfft {
 
+// streaming multiprocessors of the current device (persistent grids and grid-stride caps
+// are sized from it; the runtime caches the attribute)
+inline int current_sm_count() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 1;
+  }
+  return v;
+}
+
 template <class T>
 struct alignas(2 * sizeof(T)) cpx {
   T re, im;

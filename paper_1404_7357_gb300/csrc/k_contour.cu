@@ -169,7 +169,7 @@ void launch_class_phase(cpx<T>* table, int pairs, int n_harm, int q_max, int n_r
 template <class T>
 void launch_nonfinite(const cpx<T>* buf, int64_t count, int* flag, cudaStream_t s) {
   int blocks = (int)((count + 255) / 256);
-  if (blocks > 4 * 152) blocks = 4 * 152;
+  if (blocks > 4 * current_sm_count()) blocks = 4 * current_sm_count();
   if (blocks < 1) blocks = 1;
   nonfinite_kernel<T><<<blocks, 256, 0, s>>>(buf, count, flag);
 }

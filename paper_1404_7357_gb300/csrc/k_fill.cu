@@ -404,7 +404,7 @@ cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, 
   if (n < 1 || !r || !v || !g) return cudaErrorInvalidValue;
   const int64_t total = (int64_t)n * n;
   const int threads = 256;
-  const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)152 * 16);
+  const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)current_sm_count() * 16);
   residual_outer_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(
       reinterpret_cast<const cpx<T>*>(r), reinterpret_cast<const cpx<T>*>(v), n, reinterpret_cast<cpx<T>*>(g));
   return cudaGetLastError();
@@ -427,42 +427,44 @@ namespace {
 template <class T>
 __global__ void fill_estimate_kernel(const cpx<T>* table, int n_rho, int q_max, int n_harm,
                                      int taps, double fac_c, double fac_e, double4* out) {
+  // arithmetic in the table's precision; squared magnitudes until the end
   const int64_t series = blockIdx.x;
   const cpx<T>* z = table + series * (int64_t)n_rho;
   const int q = (int)(series % n_harm) - q_max;
-  const double par = (q & 1) ? -1.0 : 1.0;
-  double coef[kMaxTaps + 1];
+  const T par = (q & 1) ? (T)-1 : (T)1;
+  T coef[kMaxTaps + 1];
   {
     // (-1)^(p-k) C(p, k)
     double c = 1.0;
 #pragma unroll
     for (int k = 0; k <= kMaxTaps; ++k) {
-      if (k <= taps) coef[k] = ((taps - k) & 1) ? -c : c;
+      if (k <= taps) coef[k] = (T)(((taps - k) & 1) ? -c : c);
       c = c * (double)(taps - k) / (double)(k + 1);
     }
   }
-  double zmax = 0.0, emax = 0.0, eedge = 0.0;
+  T zmax = 0, emax = 0, eedge = 0;
   for (int r = threadIdx.x; r < n_rho; r += blockDim.x) {
     const cpx<T> v = z[r];
-    zmax = fmax(zmax, hypot((double)v.re, (double)v.im));
+    zmax = fmax(zmax, v.re * v.re + v.im * v.im);
   }
   const int j_lo = -(taps / 2 - 1), j_hi = n_rho - taps - 1;
   for (int j = j_lo + (int)threadIdx.x; j <= j_hi; j += blockDim.x) {
-    double dr = 0.0, di = 0.0;
+    T dr = 0, di = 0;
 #pragma unroll
     for (int k = 0; k <= kMaxTaps; ++k) {
       if (k <= taps) {
         const int i = j + k;
         const cpx<T> v = z[i < 0 ? -i : i];
-        const double s = (i < 0 ? par : 1.0) * coef[k];
-        dr = fma(s, (double)v.re, dr);
-        di = fma(s, (double)v.im, di);
+        const T s = (i < 0 ? par : (T)1) * coef[k];
+        dr = fma(s, v.re, dr);
+        di = fma(s, v.im, di);
       }
     }
+    const T d2 = dr * dr + di * di;
     if (j == j_hi)
-      eedge = hypot(dr, di) * fac_e;
+      eedge = d2;
     else
-      emax = fmax(emax, hypot(dr, di) * fac_c);
+      emax = fmax(emax, d2);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -480,7 +482,7 @@ __global__ void fill_estimate_kernel(const cpx<T>* table, int n_rho, int q_max, 
       acc.y = fmax(acc.y, red[w].y);
       acc.z = fmax(acc.z, red[w].z);
     }
-    out[series] = acc;
+    out[series] = make_double4(sqrt(acc.x), sqrt(acc.y) * fac_c, sqrt(acc.z) * fac_e, 0.0);
   }
 }
 

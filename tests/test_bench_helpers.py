@@ -45,37 +45,73 @@ def test_table_samples_of_the_headline_workload():
 def test_stage_flops_per_form():
     wl = workloads.patch_m4(precision="fp32")
     m = wl.element.n_mbf
-    fl = bench.stage_flops(_info(), wl)
-    assert fl["fft"] == pytest.approx(25344 * 5 * 16384 * 14)
-    assert fl["integrand"] == pytest.approx(16384 * 128 * (2 * 8 * 200 * m + m * m * (8 * 33 + 30)))
+    inf = _info(tc_flops_backproject=1.2e11, tc_flops_integrand=3.2e11)
+    fl = bench.stage_flops(inf, wl)
+    assert fl["fft"]["algorithmic"] == pytest.approx(25344 * 5 * 16384 * 14) == fl["fft"]["fp32"]
+    assert fl["fft"]["tensor"] == 0.0
+    gemm = 16384 * 128 * 2 * 8 * 200 * m
+    rest = 16384 * 128 * m * m * (8 * 33 + 30)
+    assert fl["integrand"]["algorithmic"] == pytest.approx(gemm + rest)
+    # spectra on the tensor cores: the GEMM leaves the FP32 pipe, the executed products count there
+    assert fl["integrand"]["fp32"] == pytest.approx(rest) and fl["integrand"]["tensor"] == 3.2e11
+    assert bench.stage_flops(_info(spectra_tc=0), wl)["integrand"]["fp32"] == pytest.approx(gemm + rest)
     # matrix forms: 8 flops per complex MAC plus the node stencils added into the matrices
-    assert fl["backproject"] == pytest.approx(8 * 4.8e9 + (6 * 12 + 16) * 6.2e7)
+    prod, sten = 8 * 4.8e9, (6 * 12 + 16) * 6.2e7
+    bp = fl["backproject"]
+    assert bp["algorithmic"] == pytest.approx(prod + sten)
+    assert bp["fp32"] == pytest.approx(sten) and bp["tensor"] == 1.2e11      # form 3: products on tensor cores
     for form in (1, 2):
-        assert bench.stage_flops(_info(bp_form=form), wl)["backproject"] == fl["backproject"]
-    # gather form: one stencil per node and series
-    assert bench.stage_flops(_info(bp_form=0), wl)["backproject"] == pytest.approx(1.0e9 * (4 * 12 + 8))
+        f = bench.stage_flops(_info(bp_form=form), wl)["backproject"]
+        assert f["algorithmic"] == bp["algorithmic"] and f["fp32"] == pytest.approx(prod + sten)
+        assert f["tensor"] == 0.0
+    # the scope table's per-node unit, and the gather form that does exactly that work
+    assert bp["per_node_unit"] == pytest.approx(1.0e9 * (8 * 12 + 8))
+    g = bench.stage_flops(_info(bp_form=0), wl)["backproject"]
+    assert g["algorithmic"] == g["fp32"] == g["per_node_unit"] == pytest.approx(1.0e9 * (8 * 12 + 8))
 
 
 def test_roofline_of_the_dominant_kernel():
     wl = workloads.patch_m4(precision="fp32")
-    infos = [_info(ms_backproject=1.60), _info(ms_backproject=1.72)]
-    r = bench.roofline(infos, wl, {"sm_max_mhz": 2070.0}, None)
+    infos = [_info(ms_backproject=1.60, tc_flops_backproject=1.2e11),
+             _info(ms_backproject=1.72, tc_flops_backproject=1.2e11)]
+    peaks = {"sm_max_mhz": 2070.0, "micro": {"fp32": 75.0, "tf32": 1000.0}}
+    r = bench.roofline(infos, wl, peaks, None)
     assert r["kernel"] == "backproject"                      # 1.66 ms mean, the longest stage
-    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     fl = bench.stage_flops(infos[-1], wl)["backproject"]
-    assert r["achieved"] == pytest.approx(fl / 1.66e-3 / 1e12)
-    assert r["peak"] == pytest.approx(bench.fp32_peak_tflops(2070.0))
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["algorithmic_flops_per_launch"] == fl
+    t32, ttc = fl["fp32"] / 75e12, fl["tensor"] / 1000e12
+    # products on the tensor cores take the larger share of the two-pipe bound
+    assert ttc > t32 and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(fl["tensor"] / 1.66e-3 / 1e12)
+    assert r["peak"] == 1000.0 and "measured" in r["peak_note"]
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"]) == pytest.approx(ttc / 1.66e-3)
+    assert r["algorithmic_flops_per_launch"] == fl["algorithmic"]
+    st = r["stages"]["backproject"]
+    assert st["fp32_frac"] == pytest.approx(t32 / 1.66e-3) and st["frac"] == pytest.approx(ttc / 1.66e-3)
+    # a stage on the FP32 pipe alone: bound "alu", frac = FP32 rate / FP32 peak
+    fft = r["stages"]["fft"]
+    assert fft["bound"] == "alu" and fft["frac"] == pytest.approx(fft["fp32_tflops"] / 75.0)
     # DRAM traffic of the default sizes from the committed capture; none for other sizes
     assert r["traffic"] == bench.KERNEL_DRAM_BYTES["backproject"]
-    for k, st in r["stages"].items():
-        assert st["frac"] == pytest.approx(st["tflops"] / r["peak"])
+    # without the microbenchmarks: the derived peaks, labelled as such
+    r2 = bench.roofline(infos, wl, {"sm_max_mhz": 2070.0, "bf16_tflops": 1900.0}, None)
+    assert r2["peaks_tflops"]["fp32"] == pytest.approx(bench.fp32_peak_tflops(2070.0))
+    assert r2["peaks_tflops"]["tf32"] == pytest.approx(1900.0 * 1.1 / 2.25) and "derived" in r2["peak_note"]
     bench.TABLE_SIZE["n"] = 2048
     try:
-        assert bench.roofline(infos, wl, {"sm_max_mhz": 2070.0}, None)["traffic"] is None
+        assert bench.roofline(infos, wl, peaks, None)["traffic"] is None
     finally:
         bench.TABLE_SIZE.clear()
+
+
+def test_fp64_roofline_counts_every_flop_on_the_fp64_pipe():
+    wl = workloads.patch_m4(precision="fp64")
+    inf = _info(bp_form=1, spectra_tc=0, ms_integrand=75.0, ms_fft=137.0, ms_backproject=245.0)
+    r = bench.fp64_roofline(inf, wl, 1.2)
+    fl = bench.stage_flops(inf, wl)
+    for k in ("integrand", "fft", "backproject"):
+        tf = fl[k]["algorithmic"] / (inf["ms_" + k] / 1e3) / 1e12
+        assert r["stages"][k]["tflops"] == pytest.approx(tf)
+        assert r["stages"][k]["frac"] == pytest.approx(tf / 1.2)
 
 
 def test_whole_job_rate_counts_every_replica():
@@ -221,13 +257,18 @@ def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
     infos = [dict(_info(), launches=6, n_basis=200, n_harm=5, sub_len=256) for _ in range(2)]
 
     monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: types.SimpleNamespace(multi_processor_count=152))
+    monkeypatch.setattr(bench, "measure_peaks", lambda *a: {"fp32": 75.0, "fp64": 1.2, "tf32": 1000.0,
+                                                             "bf16": 1950.0, "clocks": {"sm_mhz": 2070.0}})
     monkeypatch.setattr(bench, "bench_tabulation",
                         lambda *a: (wl, None, [4.5, 4.4], infos, {"sm_mhz": 2070.0, "reasons": []}))
     monkeypatch.setattr(bench, "bench_e2e", lambda *a: ({"value": 1.0, "unit": "samples/s",
                                                          "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1},
                                                         torch.tensor(table)))
-    monkeypatch.setattr(bench, "bench_fp64", lambda *a: ({"metric": "fp64"}, torch.tensor(ref_full)))
-    monkeypatch.setattr(bench, "bench_fill", lambda *a: ({"algorithmic_tflops": 1.0, "tensor_tflops_executed": 2.0},
+    monkeypatch.setattr(bench, "bench_fp64", lambda *a: ({"metric": "fp64", "_info": dict(infos[0], bp_form=1)},
+                                                        torch.tensor(ref_full)))
+    monkeypatch.setattr(bench, "bench_fill", lambda *a: ({"algorithmic_tflops": 1.0, "tensor_tflops_executed": 2.0,
+                                                         "hbm_gbs_write": 500.0},
                                                         (wl, pos, rot, pairs, blocks)))
     monkeypatch.setattr(bench, "bench_batch", lambda *a: ({"metric": "batch"}, {
         "item": 0, "wl": wl, "rows": np.array([0, 16, 31]), "got": ref_full[0][..., [0, 16, 31]],
@@ -248,4 +289,6 @@ def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
     assert line["fill"]["parity"]["max_rel_err_vs_oracle"] == 0.0
     assert line["batch"]["parity"]["max_rel_err_vs_oracle"] < 1e-10
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
-    assert line["roofline"]["bound"] == "alu" and 0 < line["roofline"]["frac"]
+    assert line["roofline"]["bound"] in ("alu", "tensor") and 0 < line["roofline"]["frac"]
+    assert line["peaks_measured"]["tf32_tflops"] == 1000.0 and "roofline" in line["fp64_gpu"]
+    assert "_info" not in line["fp64_gpu"]
