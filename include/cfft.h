@@ -502,6 +502,68 @@ cfft_status cfft_selftest_bounded_wait(cfft_ctx* ctx, unsigned polls);
  * context stays usable: a later call allocates what it needs again. */
 void cfft_test_fail_allocation(int after);
 
+/* Reduced excitation of an array of identical elements (Section II, Eq. 4):
+ *   v_red[m M + a] = sum_i conj(Q_ia) v[m][i]
+ * for every element m and MBF a, with Q the coefficient matrix given to
+ * cfft_set_mbf_spectra (basis functions in the caller's order; the strip
+ * element has Q = [1]).  The order m M + a is the row order of the reduced
+ * matrix Z' of cfft_fill_reduced_matrix.
+ *   v      device, [n_elements][n_basis] elementary excitation vectors
+ *   v_red  device, [n_elements * M]
+ * complex128 != 0: both complex128, else complex64 (accumulated in float64).
+ * CFFT_ERR_STATE without an element.  Synchronizes the context stream. */
+cfft_status cfft_reduced_excitation(cfft_ctx* ctx, int n_elements, const void* v, void* v_red,
+                                    int complex128);
+
+/* Delta-gap ports (Section IV: the arrays are excited at a port of each
+ * element): a voltage amplitudes[m] across basis function `port` of element m,
+ * V_m = amplitudes[m] e_port, so v_red[m M + a] = amplitudes[m] conj(Q_port,a).
+ *   amplitudes  device, [n_elements]; v_red device, [n_elements * M]
+ * CFFT_ERR_ARG for a port outside 0..n_basis-1.  Synchronizes. */
+cfft_status cfft_port_excitation(cfft_ctx* ctx, int n_elements, int port, const void* amplitudes,
+                                 void* v_red, int complex128);
+
+/* Port currents from the reduced solution: the current of element m on its port
+ * basis function, (Q I'_m)[port] = sum_a Q_port,a i_red[m M + a] (the elementary
+ * currents of Section II are I_m = Q I'_m).
+ *   i_red  device, [n_elements * M]; i_port device, [n_elements]
+ * Synchronizes. */
+cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const void* i_red,
+                               void* i_port, int complex128);
+
+/* Direct solution of the reduced system Z' I' = V' (Section II: the MBF
+ * reduction makes the system small enough to solve directly; Table II,
+ * "Solving time").  z: device, n rows of ld >= n entries, row-major as
+ * cfft_fill_reduced_matrix writes it; not modified (the context factors a copy
+ * of n x n entries, kept until the next solve or destroy).  v: device, [n]
+ * right-hand side; i_out: device, [n] solution.  Element types: complex128
+ * when complex128 != 0, else complex64.
+ * mode 0: LU with partial pivoting (|re| + |im| of the column, ties to the
+ *         lowest row) in the matrix's own precision.
+ * mode 1 (complex128 only): the LU of a complex64 copy, then iterative
+ *         refinement in float64 against z: x += LU^-1 (v - z x) until the
+ *         correction falls below float64 resolution or the residual stops
+ *         falling (at most 30 steps).
+ * The factorization runs in panels of 64 columns: one cooperative launch per
+ * panel (pivot search and elimination, one bounded grid barrier per column),
+ * the panel's row moves applied to the whole matrix, a triangular solve for
+ * the panel's rows and a complex matrix product for the trailing matrix.
+ * cfft_get_solve_info reports the times and the relative residual
+ * |v - z x| / |v| computed in float64 from z.  Errors: CFFT_ERR_ARG,
+ * CFFT_ERR_OOM, CFFT_ERR_NUMERIC (a zero pivot: z singular), CFFT_ERR_TIMEOUT
+ * (a grid-barrier wait gave up).  Synchronizes. */
+cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, int64_t ld, const void* v,
+                               void* i_out, int complex128, int mode);
+
+/* Diagnostics of the last cfft_solve_reduced: factorization and solve times
+ * (ms, CUDA events on the context stream; the solve includes refinement),
+ * relative residual, order n, mode, refinement steps (mode 1), panel width. */
+typedef struct {
+  double ms_factor, ms_solve, residual;
+  int n, mode, refinements, panel_width;
+} cfft_solve_info;
+cfft_status cfft_get_solve_info(const cfft_ctx* ctx, cfft_solve_info* info);
+
 /* Arithmetic peak microbenchmark (no counterpart in the paper; the roofline
  * fractions of the measurement divide by its results).  which:
  *   0  FP32 FMA pipe: independent fused multiply-add chains on every SM

@@ -29,7 +29,9 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
            "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table",
-           "cfft_fill_backward_residual", "cfft_test_fail_allocation"]
+           "cfft_fill_backward_residual", "cfft_test_fail_allocation", "cfft_measure_peak",
+           "cfft_reduced_excitation", "cfft_port_excitation", "cfft_port_currents", "cfft_solve_reduced",
+           "cfft_get_solve_info"]
 
 
 class CfftLibraryError(ImportError):
@@ -69,6 +71,11 @@ class Info(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("tc_flops_integrand", "tc_flops_backproject")]
 
 
+class SolveInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("ms_factor", "ms_solve", "residual")] + \
+               [(n, ctypes.c_int) for n in ("n", "mode", "refinements", "panel_width")]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise CfftLibraryError("libcfft.so not built (run __graft_entry__.build()): %s" % LIB_PATH)
@@ -105,6 +112,11 @@ def _load():
         "cfft_selftest_bounded_wait": ([P, ctypes.c_uint], I),
         "cfft_load_table": ([P, I, I, D, I, I, I, I, P, I], I),
         "cfft_measure_peak": ([I, I, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "cfft_reduced_excitation": ([P, I, P, P, I], I),
+        "cfft_port_excitation": ([P, I, I, P, P, I], I),
+        "cfft_port_currents": ([P, I, I, P, P, I], I),
+        "cfft_solve_reduced": ([P, I, P, L, P, P, I, I], I),
+        "cfft_get_solve_info": ([P, ctypes.POINTER(SolveInfo)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -414,6 +426,70 @@ class Context:
 
     def synchronize(self):
         self._check(_lib.cfft_synchronize(self._h))
+
+    # ---- reduced system (Section II): excitation, direct solution, port currents
+
+    def _vec(self, t, name, n=None):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype in (torch.complex64, torch.complex128)
+                and t.is_contiguous()):
+            raise ValueError("%s: a contiguous complex CUDA tensor" % name)
+        if n is not None and t.numel() != n:
+            raise ValueError("%s: %d entries expected, got %d" % (name, n, t.numel()))
+        return int(t.dtype == torch.complex128)
+
+    def reduced_excitation(self, v):
+        """V' = Q^H V_m per element (Eq. 4): v (A, n_basis) complex CUDA -> (A * M,)."""
+        if v.dim() != 2:
+            raise ValueError("v: (n_elements, n_basis)")
+        c128 = self._vec(v, "v")
+        out = self._torch.empty(v.shape[0] * self.n_mbf, dtype=v.dtype, device=v.device)
+        self._check(_lib.cfft_reduced_excitation(self._h, v.shape[0], ctypes.c_void_p(v.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr()), c128))
+        return out
+
+    def port_excitation(self, port, amplitudes):
+        """V' of delta-gap ports across basis function `port`: amplitudes (A,) -> (A * M,)."""
+        c128 = self._vec(amplitudes, "amplitudes")
+        a = amplitudes.numel()
+        out = self._torch.empty(a * self.n_mbf, dtype=amplitudes.dtype, device=amplitudes.device)
+        self._check(_lib.cfft_port_excitation(self._h, a, int(port), ctypes.c_void_p(amplitudes.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr()), c128))
+        return out
+
+    def port_currents(self, port, i_red):
+        """(Q I'_m)[port] for every element: i_red (A * M,) -> (A,)."""
+        c128 = self._vec(i_red, "i_red")
+        if i_red.numel() % self.n_mbf:
+            raise ValueError("i_red: a multiple of M entries")
+        a = i_red.numel() // self.n_mbf
+        out = self._torch.empty(a, dtype=i_red.dtype, device=i_red.device)
+        self._check(_lib.cfft_port_currents(self._h, a, int(port), ctypes.c_void_p(i_red.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()), c128))
+        return out
+
+    def solve_reduced(self, z, v, refine=False):
+        """I' with Z' I' = V' (dense LU with partial pivoting on the GPU): z (n, ld >= n) complex
+        CUDA with unit-stride rows (not modified), v (n,).  refine: complex128 z factored in
+        complex64 and refined in float64."""
+        torch = self._torch
+        if not (isinstance(z, torch.Tensor) and z.is_cuda and z.dim() == 2 and z.stride(1) == 1 and
+                z.shape[1] >= z.shape[0] and z.dtype in (torch.complex64, torch.complex128)):
+            raise ValueError("z: complex CUDA matrix (n, >= n) with unit-stride rows")
+        n = z.shape[0]
+        c128 = self._vec(v, "v", n)
+        if v.dtype != z.dtype:
+            raise ValueError("z and v: the same dtype")
+        out = torch.empty(n, dtype=z.dtype, device=z.device)
+        self._check(_lib.cfft_solve_reduced(self._h, n, ctypes.c_void_p(z.data_ptr()), z.stride(0),
+                                            ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            c128, 1 if refine else 0))
+        return out
+
+    def solve_info(self):
+        inf = SolveInfo()
+        self._check(_lib.cfft_get_solve_info(self._h, ctypes.byref(inf)))
+        return {n: getattr(inf, n) for n, _ in SolveInfo._fields_}
 
 
 def test_fail_allocation(after):

@@ -125,6 +125,14 @@ struct cfft_ctx {
   double b_ms[4] = {0, 0, 0, 0};
   double b_work_bp = 0, b_work_fft = 0;
   int b_launches = 0, b_sub_len = 0, b_rchunk = 0, b_waves = 0, b_bp_tc = 0, b_captures = 0;
+  // the element's coefficient matrix Q in the caller's basis order ([n_basis][n_mbf]), for
+  // the reduced excitation and port currents, and its device copy
+  std::vector<std::complex<double>> q_user;
+  DevBuf d_quser;
+  // dense LU of the reduced system: the factored copy, work arrays, vectors, timing
+  DevBuf lu_a, lu_moves, lu_nmoves, lu_cand_v, lu_cand_r, lu_bar, lu_err, lu_x, lu_y, lu_x64, lu_r, lu_sums;
+  cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};
+  cfft_solve_info solve_info{};
   // tensor-core spectra: float copies of the element and its GEMM B operand
   DevBuf tc_bx, tc_by, tc_bmat, tc_bmat_mirror, tc_shapes;
   bool tc_ready = false;
@@ -1488,10 +1496,14 @@ void cfft_destroy(cfft_ctx* ctx) {
                       &ctx->green_r, &ctx->dp_eps, &ctx->dr_eps, &ctx->dp_h, &ctx->dr_h, &ctx->d_shapes, &ctx->d_bx, &ctx->d_by, &ctx->d_q,
                       &ctx->d_y, &ctx->d_grid, &ctx->d_table, &ctx->d_tw, &ctx->d_cnodes,
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
-                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->d_ftable, &ctx->d_fest, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
+                      &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->d_ftable, &ctx->d_fest, &ctx->d_quser, &ctx->lu_a, &ctx->lu_moves,
+                      &ctx->lu_nmoves, &ctx->lu_cand_v, &ctx->lu_cand_r, &ctx->lu_bar, &ctx->lu_err, &ctx->lu_x,
+                      &ctx->lu_y, &ctx->lu_x64, &ctx->lu_r, &ctx->lu_sums, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
                       &ctx->tc_bmat_mirror, &ctx->tc_shapes};
     for (DevBuf* b : bufs) b->release();
     for (auto& e : ctx->ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : ctx->lu_ev)
       if (e) cudaEventDestroy(e);
     DevBuf* bb[] = {&ctx->b_cargs, &ctx->b_cdata, &ctx->b_iargs, &ctx->b_fargs, &ctx->b_bargs,
                     &ctx->b_cmap, &ctx->b_imap, &ctx->b_ftask, &ctx->b_btask, &ctx->b_count,
@@ -1534,6 +1546,7 @@ cfft_status cfft_set_mbf_spectra_strip(cfft_ctx* ctx, double length, double widt
   ctx->n_mbf = 1;
   ctx->n_mbf_pad = 1;
   ctx->q.assign(1, {1.0, 0.0});
+  ctx->q_user.assign(1, {1.0, 0.0});
   ctx->elem_radius = 0.5 * std::hypot(length, width);
   ctx->has_el = true;
   ctx->has_table = false;
@@ -1577,6 +1590,8 @@ cfft_status cfft_set_mbf_spectra(cfft_ctx* ctx, int n_basis, const double* cente
     }
     ctx->shapes.push_back(sc);
   }
+  ctx->q_user.resize((size_t)n_basis * n_mbf);
+  for (size_t e = 0; e < ctx->q_user.size(); ++e) ctx->q_user[e] = {q[2 * e], q[2 * e + 1]};
   ctx->n_basis = n_basis;
   ctx->n_mbf = n_mbf;
   ctx->n_mbf_pad = pad;
@@ -1972,5 +1987,181 @@ extern "C" cfft_status cfft_mbf_spectra(cfft_ctx* ctx, int n_points, const void*
   CFFT_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "spectra");
   if (h & 16) return fail(ctx, CFFT_ERR_TIMEOUT, "tensor-core spectra: an mbarrier wait ran past its bound");
+  return CFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reduced MBF system (Section II): excitation, direct solution, port currents.
+
+namespace {
+
+cfft_status upload_quser(cfft_ctx* ctx) {
+  const size_t bytes = ctx->q_user.size() * sizeof(std::complex<double>);
+  CFFT_CUDA(ctx->d_quser.ensure(bytes), "alloc Q");
+  CFFT_CUDA(cudaMemcpyAsync(ctx->d_quser.p, ctx->q_user.data(), bytes, cudaMemcpyHostToDevice, ctx->stream),
+            "upload Q");
+  return CFFT_OK;
+}
+
+cfft_status excitation_call(cfft_ctx* ctx, int kind, int n_el, int port, const void* in, void* out, int c128) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (!ctx->has_el) return fail(ctx, CFFT_ERR_STATE, "the excitation needs the element's MBFs (set_mbf_spectra)");
+  if (n_el < 1 || !in || !out) return fail(ctx, CFFT_ERR_ARG, "need n_elements >= 1 and device buffers");
+  if (kind != 0 && (port < 0 || port >= ctx->n_basis))
+    return fail(ctx, CFFT_ERR_ARG, "port must index a basis function of the element");
+  DeviceGuard g(ctx->device);
+  cfft_status st = upload_quser(ctx);
+  if (st != CFFT_OK) return st;
+  const double* q = ctx->d_quser.as<double>();
+  cudaError_t e = c128 ? launch_excitation<double>(kind, n_el, ctx->n_basis, ctx->n_mbf, port, in, q, out, ctx->stream)
+                       : launch_excitation<float>(kind, n_el, ctx->n_basis, ctx->n_mbf, port, in, q, out, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "excitation kernel");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "excitation");   // Q's staging copy is the context's
+  return CFFT_OK;
+}
+
+cfft_status lu_work(cfft_ctx* ctx, int n, LuWork* w) {
+  const int nb = lu_panel_width();
+  const int panels = (n + nb - 1) / nb;
+  CFFT_CUDA(ctx->lu_moves.ensure((size_t)panels * 2 * nb * sizeof(int2)), "alloc LU");
+  CFFT_CUDA(ctx->lu_nmoves.ensure((size_t)panels * sizeof(int)), "alloc LU");
+  CFFT_CUDA(ctx->lu_cand_v.ensure((size_t)ctx->sm_count * 8 * sizeof(double)), "alloc LU");
+  CFFT_CUDA(ctx->lu_cand_r.ensure((size_t)ctx->sm_count * 8 * sizeof(int)), "alloc LU");
+  CFFT_CUDA(ctx->lu_bar.ensure((size_t)panels * sizeof(unsigned)), "alloc LU");
+  CFFT_CUDA(ctx->lu_err.ensure(sizeof(int)), "alloc LU");
+  CFFT_CUDA(ctx->lu_sums.ensure(4 * sizeof(double)), "alloc LU");
+  w->moves = ctx->lu_moves.as<int2>();
+  w->n_moves = ctx->lu_nmoves.as<int>();
+  w->cand_val = ctx->lu_cand_v.as<double>();
+  w->cand_row = ctx->lu_cand_r.as<int>();
+  w->bar = ctx->lu_bar.as<unsigned>();
+  w->err = ctx->lu_err.as<int>();
+  return CFFT_OK;
+}
+
+// factor the context's copy of Z (element type T, dense n x n) and report the panel status
+template <class T>
+cfft_status lu_factor_checked(cfft_ctx* ctx, int n, const LuWork& w) {
+  cudaError_t e = lu_factor<T>(ctx->lu_a.as<cpx<T>>(), n, n, w, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "LU factorization");
+  int flag = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "LU flag");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "LU factorization");
+  if (flag & 2) return fail(ctx, CFFT_ERR_TIMEOUT, "LU panel: a grid-barrier wait ran past its bound");
+  if (flag & 4) return fail(ctx, CFFT_ERR_NUMERIC, "LU: the reduced matrix is singular (zero pivot)");
+  return CFFT_OK;
+}
+
+cfft_status read_sums(cfft_ctx* ctx, double* h, int count) {
+  CFFT_CUDA(cudaMemcpyAsync(h, ctx->lu_sums.p, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "sums");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "sums");
+  return CFFT_OK;
+}
+
+}  // namespace
+
+extern "C" cfft_status cfft_reduced_excitation(cfft_ctx* ctx, int n_elements, const void* v, void* v_red,
+                                               int complex128) {
+  return excitation_call(ctx, 0, n_elements, 0, v, v_red, complex128);
+}
+
+extern "C" cfft_status cfft_port_excitation(cfft_ctx* ctx, int n_elements, int port, const void* amplitudes,
+                                            void* v_red, int complex128) {
+  return excitation_call(ctx, 1, n_elements, port, amplitudes, v_red, complex128);
+}
+
+extern "C" cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const void* i_red,
+                                          void* i_port, int complex128) {
+  return excitation_call(ctx, 2, n_elements, port, i_red, i_port, complex128);
+}
+
+extern "C" cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, int64_t ld, const void* v,
+                                          void* i_out, int complex128, int mode) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (n < 1 || n > (1 << 18) || ld < n || !z || !v || !i_out)
+    return fail(ctx, CFFT_ERR_ARG, "solve: need 1 <= n <= 262144, ld >= n and device buffers");
+  if (mode != 0 && mode != 1) return fail(ctx, CFFT_ERR_ARG, "solve: mode must be 0 or 1");
+  if (mode == 1 && !complex128) return fail(ctx, CFFT_ERR_ARG, "solve: refinement needs a complex128 matrix");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = ctx->stream;
+  for (auto& e : ctx->lu_ev)
+    if (!e) CFFT_CUDA(cudaEventCreate(&e), "event");
+  LuWork w{};
+  cfft_status s = lu_work(ctx, n, &w);
+  if (s != CFFT_OK) return s;
+  const bool fp64_lu = complex128 && mode == 0;
+  const size_t es = fp64_lu ? 16 : 8;
+  CFFT_CUDA(ctx->lu_a.ensure((size_t)n * n * es), "alloc LU matrix");
+  CFFT_CUDA(ctx->lu_x.ensure((size_t)n * es), "alloc LU vectors");
+  CFFT_CUDA(ctx->lu_y.ensure((size_t)n * es), "alloc LU vectors");
+  double h[4] = {0, 0, 0, 0};
+  int steps = 0;
+  CFFT_CUDA(cudaEventRecord(ctx->lu_ev[0], st), "event");
+  if (!complex128) {
+    CFFT_CUDA((copy_matrix<float, float>(z, ld, n, ctx->lu_a.p, st)), "LU copy");
+    if ((s = lu_factor_checked<float>(ctx, n, w)) != CFFT_OK) return s;
+    CFFT_CUDA(cudaEventRecord(ctx->lu_ev[1], st), "event");
+    CFFT_CUDA((copy_vector<float, float>(v, n, ctx->lu_x.p, st)), "LU copy");
+    CFFT_CUDA(lu_solve<float>(ctx->lu_a.as<cpx<float>>(), n, n, w, ctx->lu_x.as<cpx<float>>(),
+                              ctx->lu_y.as<cpx<float>>(), st), "LU solve");
+    CFFT_CUDA((copy_vector<float, float>(ctx->lu_x.p, n, i_out, st)), "LU copy");
+    CFFT_CUDA(cudaEventRecord(ctx->lu_ev[2], st), "event");
+    CFFT_CUDA(residual_f32(z, ld, n, i_out, v, ctx->lu_sums.as<double>(), st), "residual");
+  } else if (fp64_lu) {
+    CFFT_CUDA((copy_matrix<double, double>(z, ld, n, ctx->lu_a.p, st)), "LU copy");
+    if ((s = lu_factor_checked<double>(ctx, n, w)) != CFFT_OK) return s;
+    CFFT_CUDA(cudaEventRecord(ctx->lu_ev[1], st), "event");
+    CFFT_CUDA((copy_vector<double, double>(v, n, ctx->lu_x.p, st)), "LU copy");
+    CFFT_CUDA(lu_solve<double>(ctx->lu_a.as<cpx<double>>(), n, n, w, ctx->lu_x.as<cpx<double>>(),
+                               ctx->lu_y.as<cpx<double>>(), st), "LU solve");
+    CFFT_CUDA((copy_vector<double, double>(ctx->lu_x.p, n, i_out, st)), "LU copy");
+    CFFT_CUDA(cudaEventRecord(ctx->lu_ev[2], st), "event");
+    CFFT_CUDA(residual_f64(z, ld, n, i_out, v, nullptr, ctx->lu_sums.as<double>(), st), "residual");
+  } else {
+    // float32 factorization, float64 iterative refinement against the float64 matrix:
+    // x_0 = 0, r_0 = v; d = LU^-1 r (float32), x += d, r = v - Z x (float64)
+    CFFT_CUDA(ctx->lu_x64.ensure((size_t)n * 16), "alloc LU vectors");
+    CFFT_CUDA(ctx->lu_r.ensure((size_t)n * 16), "alloc LU vectors");
+    CFFT_CUDA((copy_matrix<float, double>(z, ld, n, ctx->lu_a.p, st)), "LU copy");
+    if ((s = lu_factor_checked<float>(ctx, n, w)) != CFFT_OK) return s;
+    CFFT_CUDA(cudaEventRecord(ctx->lu_ev[1], st), "event");
+    CFFT_CUDA(cudaMemsetAsync(ctx->lu_x64.p, 0, (size_t)n * 16, st), "LU zero");
+    CFFT_CUDA((copy_vector<double, double>(v, n, ctx->lu_r.p, st)), "LU copy");
+    double rr_prev = -1.0;
+    for (steps = 1; steps <= 30; ++steps) {
+      CFFT_CUDA((copy_vector<float, double>(ctx->lu_r.p, n, ctx->lu_x.p, st)), "LU copy");
+      CFFT_CUDA(lu_solve<float>(ctx->lu_a.as<cpx<float>>(), n, n, w, ctx->lu_x.as<cpx<float>>(),
+                                ctx->lu_y.as<cpx<float>>(), st), "LU solve");
+      CFFT_CUDA(add_correction(ctx->lu_x64.p, ctx->lu_x.p, n, ctx->lu_sums.as<double>() + 2, st), "refinement");
+      CFFT_CUDA(residual_f64(z, ld, n, ctx->lu_x64.p, v, ctx->lu_r.p, ctx->lu_sums.as<double>(), st), "residual");
+      if ((s = read_sums(ctx, h, 4)) != CFFT_OK) return s;
+      const double rr = h[0], dd = h[2], xx = h[3];
+      // stop when the correction is below float64 resolution or the residual stops falling
+      if (!(dd > 1e-30 * xx) || (rr_prev >= 0.0 && rr > 0.25 * rr_prev)) break;
+      rr_prev = rr;
+    }
+    if (steps > 30) steps = 30;
+    CFFT_CUDA((copy_vector<double, double>(ctx->lu_x64.p, n, i_out, st)), "LU copy");
+    CFFT_CUDA(cudaEventRecord(ctx->lu_ev[2], st), "event");
+    CFFT_CUDA(residual_f64(z, ld, n, i_out, v, nullptr, ctx->lu_sums.as<double>(), st), "residual");
+  }
+  if ((s = read_sums(ctx, h, 2)) != CFFT_OK) return s;
+  float ms = 0.f;
+  cfft_solve_info& in = ctx->solve_info;
+  in = cfft_solve_info{};
+  if (cudaEventElapsedTime(&ms, ctx->lu_ev[0], ctx->lu_ev[1]) == cudaSuccess) in.ms_factor = ms;
+  if (cudaEventElapsedTime(&ms, ctx->lu_ev[1], ctx->lu_ev[2]) == cudaSuccess) in.ms_solve = ms;
+  in.residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  in.n = n;
+  in.mode = mode;
+  in.refinements = steps;
+  in.panel_width = lu_panel_width();
+  if (!std::isfinite(in.residual)) return fail(ctx, CFFT_ERR_NUMERIC, "solve: non-finite solution");
+  return CFFT_OK;
+}
+
+extern "C" cfft_status cfft_get_solve_info(const cfft_ctx* ctx, cfft_solve_info* info) {
+  if (!ctx || !info) return CFFT_ERR_ARG;
+  *info = ctx->solve_info;
   return CFFT_OK;
 }

@@ -393,6 +393,34 @@ cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, 
 template <class T>
 cudaError_t launch_fill_estimate(const void* table, int64_t n_series, int n_rho, int q_max, int taps,
                                  double fac_c, double fac_e, double4* out, cudaStream_t s);
+// dense LU of the reduced system (k_solve.cu): device work arrays of one factorization
+struct LuWork {
+  int2* moves;         // [panels][2 * panel width] row moves (source, destination)
+  int* n_moves;        // [panels]
+  double* cand_val;    // [SMs] pivot candidates of the panel CTAs
+  int* cand_row;
+  unsigned* bar;       // [panels] grid-barrier counters
+  int* err;            // bit 1: barrier wait ran out; bit 2: zero pivot
+};
+int lu_panel_width();
+template <class T>
+cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_t s);
+template <class T>
+cudaError_t lu_solve(const cpx<T>* a, int64_t ld, int n, const LuWork& w, cpx<T>* x, cpx<T>* y, cudaStream_t s);
+cudaError_t residual_f64(const void* z, int64_t ld, int n, const void* x, const void* b, void* r, double* sums,
+                         cudaStream_t s);
+cudaError_t residual_f32(const void* z, int64_t ld, int n, const void* x, const void* b, double* sums,
+                         cudaStream_t s);
+template <class TD, class TS>
+cudaError_t copy_matrix(const void* src, int64_t ld, int n, void* dst, cudaStream_t s);
+template <class TD, class TS>
+cudaError_t copy_vector(const void* src, int n, void* dst, cudaStream_t s);
+cudaError_t add_correction(void* x, const void* d, int n, double* sums, cudaStream_t s);
+// kind 0: V' = Q^H V; 1: delta-gap port excitation; 2: port currents (q: complex128 [B][M])
+template <class T>
+cudaError_t launch_excitation(int kind, int n_el, int n_basis, int m, int port, const void* in, const double* q,
+                              void* out, cudaStream_t s);
+
 // plan.ok: bucketed fill with `scratch` of plan.scratch bytes; else the per-row fill
 template <class T, class TO>
 cudaError_t launch_fill(const FillArgs<T, TO>& a, const FillBucketPlan& plan, void* scratch, cudaStream_t s);

@@ -1,0 +1,669 @@
+// Reduced MBF system on the GPU (Section II): the reduced excitation V' = Q^H V
+// (Eq. 4), the direct solution of Z' I' = V' by a blocked LU factorization with
+// partial pivoting, and the port currents (Q I'_m)[port].  The paper solves the
+// reduced system directly because the MBF reduction makes it small (Table II,
+// "Solving time"); this is that step, dense, on one GPU.
+//
+// LU (right-looking, row-major, panels of kNb columns):
+//   panel    one cooperative launch over the panel's rows: per column, every CTA
+//            proposes its largest |re| + |im| among the rows not yet chosen, a
+//            bounded grid barrier, every CTA takes the same pivot (ties: lowest
+//            row), reads the pivot row and eliminates the column from its own
+//            rows.  Pivoting is logical: rows stay where they are and the chosen
+//            rows are recorded; one barrier per column.
+//   moves    the panel's pivot rows go to rows k..k+kb-1 and the rows they
+//            displace to the vacated places, as a list of (source, destination)
+//            row moves applied to every column of the matrix.
+//   trsm     U12 = L11^-1 A12 (unit lower L11), one thread per column.
+//   gemm     A22 -= L21 U12, 64 x 64 tiles of complex entries, K = the panel.
+// The solve applies every panel's moves to the right-hand side, then blocked
+// forward (unit L) and backward (U) substitution: per panel one launch whose
+// CTAs each solve the small diagonal block (one warp) and update their rows.
+//
+// Every grid-barrier wait is bounded: a wait that runs out sets an error bit,
+// and every CTA leaves the panel (the host then returns CFFT_ERR_TIMEOUT).
+#include <algorithm>
+
+#include "cfft_common.cuh"
+
+namespace cfft {
+
+namespace {
+
+constexpr int kNb = 64;                 // panel width
+constexpr int kPanelThreads = 256;
+constexpr unsigned kBarrierPolls = 1u << 22;
+
+template <class T>
+__device__ __forceinline__ cpx<T> ldcg(const cpx<T>* p);
+template <>
+__device__ __forceinline__ cpx<float> ldcg(const cpx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cpx<double> ldcg(const cpx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk(v.x, v.y);
+}
+
+template <class T>
+__device__ __forceinline__ cpx<T> crecip(cpx<T> z) {
+  return cdiv(mk((T)1, (T)0), z);
+}
+
+// grid barrier of a cooperative launch (all CTAs resident): arrive, then poll with a bound
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* s_fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    unsigned polls = 0;
+    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+      if (++polls > kBarrierPolls) {
+        *s_fail = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *reinterpret_cast<volatile int*>(s_fail) == 0;
+}
+
+template <class T>
+struct PanelArgs {
+  cpx<T>* a;
+  int64_t ld;
+  int n, k, kb;
+  double* cand_val;   // [grid] per-CTA pivot candidates
+  int* cand_row;
+  unsigned* bar;      // barrier counter of this panel, zero at launch
+  int2* moves;        // (source row, destination row), at most 2 kb
+  int* n_moves;
+  int* err;           // bit 1: a barrier wait ran out; bit 2: zero pivot
+};
+
+__device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int oi) {
+  if (ov > v || (ov == v && oi < i)) {
+    v = ov;
+    i = oi;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p) {
+  constexpr int kWarps = kPanelThreads / 32;
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int R = p.n - p.k;
+  const int per = (R + G - 1) / G;
+  const int lo = p.k + min(g * per, R), hi = p.k + min((g + 1) * per, R);
+  extern __shared__ unsigned char chosen[];   // [per]: row already a pivot
+  __shared__ cpx<T> prow[kNb];
+  __shared__ double wv[kWarps];
+  __shared__ int wi[kWarps];
+  __shared__ int s_piv[kNb];
+  __shared__ int s_fail, s_p;
+  for (int i = tid; i < per; i += blockDim.x) chosen[i] = 0;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  unsigned target = 0;
+  bool ok = true;
+  for (int j = 0; j < p.kb; ++j) {
+    const int c = p.k + j;
+    // this CTA's candidate: largest |re| + |im| in column c among its rows not chosen yet
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = lo + tid; i < hi; i += blockDim.x) {
+      if (chosen[i - lo]) continue;
+      const cpx<T> v = ldcg(p.a + (int64_t)i * p.ld + c);
+      argmax_merge(best, bi, fabs((double)v.re) + fabs((double)v.im), i);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+      argmax_merge(best, bi, __shfl_xor_sync(0xffffffffu, best, off), __shfl_xor_sync(0xffffffffu, bi, off));
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double v = wv[0];
+      int r = wi[0];
+      for (int w = 1; w < kWarps; ++w) argmax_merge(v, r, wv[w], wi[w]);
+      p.cand_val[g] = v;
+      p.cand_row[g] = r;
+    }
+    target += (unsigned)G;
+    if (!grid_barrier(p.bar, target, &s_fail)) {
+      ok = false;
+      break;
+    }
+    // the pivot: best candidate over all CTAs (the same choice in every CTA)
+    if (warp == 0) {
+      double v = -1.0;
+      int r = 0x7fffffff;
+      for (int t = lane; t < G; t += 32) argmax_merge(v, r, __ldcg(p.cand_val + t), __ldcg(p.cand_row + t));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        argmax_merge(v, r, __shfl_xor_sync(0xffffffffu, v, off), __shfl_xor_sync(0xffffffffu, r, off));
+      if (lane == 0) {
+        if (!(v > 0.0) && g == 0) atomicOr(p.err, 4);
+        s_p = (r >= p.k && r < p.n) ? r : -1;
+      }
+    }
+    __syncthreads();
+    const int pr = s_p;
+    if (pr < 0) {   // no row left (cannot happen with n - k >= kb); leave the panel
+      if (tid == 0 && g == 0) atomicOr(p.err, 4);
+      ok = false;
+      break;
+    }
+    // the pivot row's entries c .. k+kb-1 (its owner finished them before the barrier)
+    for (int t = tid; t < p.kb - j; t += blockDim.x) prow[t] = ldcg(p.a + (int64_t)pr * p.ld + c + t);
+    if (tid == 0) {
+      if (pr >= lo && pr < hi) chosen[pr - lo] = 1;
+      s_piv[j] = pr;
+    }
+    __syncthreads();
+    const cpx<T> inv = crecip(prow[0]);
+    // eliminate column c from this CTA's other rows: one warp per row, lanes over columns
+    for (int i = lo + warp; i < hi; i += kWarps) {
+      if (chosen[i - lo]) continue;
+      cpx<T>* row = p.a + (int64_t)i * p.ld + c;
+      const cpx<T> l = ldcg(row) * inv;
+      for (int t = 1 + lane; t < p.kb - j; t += 32) {
+        cpx<T> v = ldcg(row + t);
+        cmac(v, mk(-l.re, -l.im), prow[t]);
+        row[t] = v;
+      }
+      __syncwarp();
+      if (lane == 0) row[0] = l;
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0 && s_fail) atomicOr(p.err, 2);
+    return;
+  }
+  if (g == 0 && tid == 0) {
+    // rows k+j <- pivot j; the rows of [k, k+kb) that were not chosen go to the places the
+    // chosen rows outside that range leave free, both in increasing order
+    int nm = 0, nd = 0, nv = 0;
+    int displaced[kNb], vacated[kNb];
+    for (int j = 0; j < p.kb; ++j) {
+      if (s_piv[j] != p.k + j) p.moves[nm++] = make_int2(s_piv[j], p.k + j);
+      if (s_piv[j] >= p.k + p.kb) vacated[nv++] = s_piv[j];
+    }
+    for (int r = p.k; r < p.k + p.kb; ++r) {
+      bool taken = false;
+      for (int j = 0; j < p.kb; ++j) taken = taken || s_piv[j] == r;
+      if (!taken) displaced[nd++] = r;
+    }
+    // nd == nv: both count the pivots from outside [k, k+kb)
+    for (int t = 0; t < nd && t < nv; ++t) {
+      // vacated rows in increasing order
+      int m = t;
+      for (int u = t + 1; u < nv; ++u)
+        if (vacated[u] < vacated[m]) m = u;
+      const int tmp = vacated[t];
+      vacated[t] = vacated[m];
+      vacated[m] = tmp;
+      p.moves[nm++] = make_int2(displaced[t], vacated[t]);
+    }
+    *p.n_moves = nm;
+  }
+}
+
+// the panel's row moves on columns [0, n_cols): all sources read before any destination
+// is written (16 columns per block, every move)
+template <class T>
+__global__ void __launch_bounds__(256) lu_moves_kernel(cpx<T>* a, int64_t ld, int n_cols, const int2* moves,
+                                                       const int* n_moves) {
+  __shared__ cpx<T> buf[2 * kNb][16];
+  __shared__ int2 mv[2 * kNb];
+  const int nm = min(*n_moves, 2 * kNb);
+  const int tid = threadIdx.x, cl = tid & 15, mr = tid >> 4;
+  const int col = blockIdx.x * 16 + cl;
+  for (int m = tid; m < nm; m += blockDim.x) mv[m] = moves[m];
+  __syncthreads();
+  for (int m = mr; m < nm; m += 16)
+    if (col < n_cols) buf[m][cl] = a[(int64_t)mv[m].x * ld + col];
+  __syncthreads();
+  for (int m = mr; m < nm; m += 16)
+    if (col < n_cols) a[(int64_t)mv[m].y * ld + col] = buf[m][cl];
+}
+
+// U12 = L11^-1 A12 on rows k..k+kb-1, columns c0.. (one thread per column; L11 and the
+// columns' partial results in shared memory)
+template <class T>
+__global__ void lu_trsm_kernel(cpx<T>* a, int64_t ld, int n, int k, int kb) {
+  extern __shared__ unsigned char sm[];
+  cpx<T>* L = reinterpret_cast<cpx<T>*>(sm);          // [kb][kb]
+  cpx<T>* X = L + kb * kb;                            // [kb][blockDim]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e / kb, j = e % kb;
+    L[e] = j < i ? a[(int64_t)(k + i) * ld + k + j] : mk((T)0, (T)0);
+  }
+  __syncthreads();
+  const int col = k + kb + blockIdx.x * nt + tid;
+  if (col >= n) return;
+  for (int i = 0; i < kb; ++i) {
+    cpx<T> x = a[(int64_t)(k + i) * ld + col];
+    for (int j = 0; j < i; ++j) cmac(x, mk(-L[i * kb + j].re, -L[i * kb + j].im), X[j * nt + tid]);
+    X[i * nt + tid] = x;
+    a[(int64_t)(k + i) * ld + col] = x;
+  }
+}
+
+// A22 -= L21 U12: a 64 x 64 tile of complex entries per block, 256 threads with 4 x 4 each,
+// the whole K (the panel width) staged in shared memory (A transposed, padded)
+template <class T>
+__global__ void __launch_bounds__(256) lu_gemm_kernel(cpx<T>* a, int64_t ld, int n, int k, int kb) {
+  constexpr int BM = 64, BN = 64, PA = BM + 1;
+  extern __shared__ unsigned char sm[];
+  cpx<T>* As = reinterpret_cast<cpx<T>*>(sm);   // [kb][PA]
+  cpx<T>* Bs = As + kb * PA;                    // [kb][BN]
+  const int tid = threadIdx.x;
+  const int r0 = k + kb + blockIdx.y * BM, c0 = k + kb + blockIdx.x * BN;
+  for (int e = tid; e < BM * kb; e += 256) {
+    const int row = e / kb, kk = e % kb;
+    As[kk * PA + row] = r0 + row < n ? a[(int64_t)(r0 + row) * ld + k + kk] : mk((T)0, (T)0);
+  }
+  for (int e = tid; e < kb * BN; e += 256) {
+    const int kk = e / BN, col = e % BN;
+    Bs[kk * BN + col] = c0 + col < n ? a[(int64_t)(k + kk) * ld + c0 + col] : mk((T)0, (T)0);
+  }
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
+  cpx<T> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk((T)0, (T)0);
+  for (int kk = 0; kk < kb; ++kk) {
+    cpx<T> av[4], bv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = As[kk * PA + ty * 4 + i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = Bs[kk * BN + tx * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cmac(acc[i][j], av[i], bv[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty * 4 + i;
+    if (r >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = c0 + tx * 4 + j;
+      if (cc < n) {
+        cpx<T>& z = a[(int64_t)r * ld + cc];
+        z = z - acc[i][j];
+      }
+    }
+  }
+}
+
+// every panel's row moves on the right-hand side, in panel order (one block)
+template <class T>
+__global__ void lu_vector_moves_kernel(cpx<T>* x, int n_panels, const int2* moves, const int* n_moves) {
+  __shared__ cpx<T> buf[2 * kNb];
+  for (int pnl = 0; pnl < n_panels; ++pnl) {
+    const int nm = min(n_moves[pnl], 2 * kNb);
+    const int2* mv = moves + (size_t)pnl * 2 * kNb;
+    for (int m = threadIdx.x; m < nm; m += blockDim.x) buf[m] = x[mv[m].x];
+    __syncthreads();
+    for (int m = threadIdx.x; m < nm; m += blockDim.x) x[mv[m].y] = buf[m];
+    __syncthreads();
+  }
+}
+
+// solve the diagonal block of rows k..k+kb-1 with one warp: unit lower (forward) or
+// upper (backward); rhs from `src`, result to shared `yb`
+template <class T, bool UPPER>
+__device__ void block_solve(const cpx<T>* a, int64_t ld, int k, int kb, const cpx<T>* src, cpx<T>* yb) {
+  const int lane = threadIdx.x & 31;
+  for (int s = 0; s < kb; ++s) {
+    const int i = UPPER ? kb - 1 - s : s;
+    cpx<T> acc = mk((T)0, (T)0);
+    if (UPPER) {
+      for (int j = i + 1 + lane; j < kb; j += 32) cmac(acc, a[(int64_t)(k + i) * ld + k + j], yb[j]);
+    } else {
+      for (int j = lane; j < i; j += 32) cmac(acc, a[(int64_t)(k + i) * ld + k + j], yb[j]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+    }
+    if (lane == 0) {
+      cpx<T> v = src[k + i] - acc;
+      if (UPPER) v = cdiv(v, a[(int64_t)(k + i) * ld + k + i]);
+      yb[i] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// forward step of panel k: y_b = L11^-1 x_b (written to y), x[r] -= L[r][k..] y_b for the
+// rows below (one warp per row)
+template <class T>
+__global__ void __launch_bounds__(256) lu_forward_kernel(const cpx<T>* a, int64_t ld, int n, int k, int kb,
+                                                         cpx<T>* x, cpx<T>* y) {
+  __shared__ cpx<T> yb[kNb];
+  if (threadIdx.x < 32) block_solve<T, false>(a, ld, k, kb, x, yb);
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) y[k + t] = yb[t];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = k + kb + blockIdx.x * nw + warp; r < n; r += gridDim.x * nw) {
+    cpx<T> acc = mk((T)0, (T)0);
+    for (int j = lane; j < kb; j += 32) cmac(acc, a[(int64_t)r * ld + k + j], yb[j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+    }
+    if (lane == 0) x[r] = x[r] - acc;
+  }
+}
+
+// backward step of panel k: x_b = U11^-1 y_b (written to x), y[r] -= U[r][k..] x_b for the
+// rows above
+template <class T>
+__global__ void __launch_bounds__(256) lu_backward_kernel(const cpx<T>* a, int64_t ld, int k, int kb,
+                                                          cpx<T>* y, cpx<T>* x) {
+  __shared__ cpx<T> xb[kNb];
+  if (threadIdx.x < 32) block_solve<T, true>(a, ld, k, kb, y, xb);
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) x[k + t] = xb[t];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = blockIdx.x * nw + warp; r < k; r += gridDim.x * nw) {
+    cpx<T> acc = mk((T)0, (T)0);
+    for (int j = lane; j < kb; j += 32) cmac(acc, a[(int64_t)r * ld + k + j], xb[j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+    }
+    if (lane == 0) y[r] = y[r] - acc;
+  }
+}
+
+// r = b - Z x in float64 from the float64 matrix (one warp per row), and |r|^2, |b|^2 sums
+__global__ void __launch_bounds__(256) residual_kernel(const cpx<double>* z, int64_t ld, int n, const cpx<double>* x,
+                                                       const cpx<double>* b, cpx<double>* r, double* sums) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double rr = 0.0, bb = 0.0;
+  for (int i = blockIdx.x * nw + warp; i < n; i += gridDim.x * nw) {
+    cpx<double> acc = mk(0.0, 0.0);
+    for (int j = lane; j < n; j += 32) cmac(acc, z[(int64_t)i * ld + j], x[j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+    }
+    if (lane == 0) {
+      const cpx<double> v = b[i] - acc;
+      if (r) r[i] = v;
+      rr += v.re * v.re + v.im * v.im;
+      bb += b[i].re * b[i].re + b[i].im * b[i].im;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(sums, rr);
+    atomicAdd(sums + 1, bb);
+  }
+}
+
+// the same residual from a complex64 matrix and vectors (accumulated in float64)
+__global__ void __launch_bounds__(256) residual32_kernel(const cpx<float>* z, int64_t ld, int n, const cpx<float>* x,
+                                                         const cpx<float>* b, double* sums) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double rr = 0.0, bb = 0.0;
+  for (int i = blockIdx.x * nw + warp; i < n; i += gridDim.x * nw) {
+    cpx<double> acc = mk(0.0, 0.0);
+    for (int j = lane; j < n; j += 32) cmac(acc, ccast<double>(z[(int64_t)i * ld + j]), ccast<double>(x[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+    }
+    if (lane == 0) {
+      const cpx<double> v = ccast<double>(b[i]) - acc;
+      rr += v.re * v.re + v.im * v.im;
+      bb += (double)b[i].re * b[i].re + (double)b[i].im * b[i].im;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(sums, rr);
+    atomicAdd(sums + 1, bb);
+  }
+}
+
+// copy an n x n block (row stride ld_src) into a dense n x n buffer, changing precision
+template <class TD, class TS>
+__global__ void copy_matrix_kernel(const cpx<TS>* src, int64_t ld, int n, cpx<TD>* dst) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    dst[e] = ccast<TD>(src[i * ld + j]);
+  }
+}
+
+template <class TD, class TS>
+__global__ void copy_vector_kernel(const cpx<TS>* src, int n, cpx<TD>* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = ccast<TD>(src[i]);
+}
+
+// x += d (float64 + float32 correction); sums[0] += |d|^2, sums[1] += |x|^2
+__global__ void add_correction_kernel(cpx<double>* x, const cpx<float>* d, int n, double* sums) {
+  double dd = 0.0, xx = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const cpx<double> di = ccast<double>(d[i]);
+    const cpx<double> v = x[i] + di;
+    x[i] = v;
+    dd += di.re * di.re + di.im * di.im;
+    xx += v.re * v.re + v.im * v.im;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    dd += __shfl_xor_sync(0xffffffffu, dd, off);
+    xx += __shfl_xor_sync(0xffffffffu, xx, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums, dd);
+    atomicAdd(sums + 1, xx);
+  }
+}
+
+// V'_{e,a} = sum_i conj(Q_ia) V_{e,i}  (Eq. 4), one thread per (element, MBF)
+template <class T>
+__global__ void reduced_excitation_kernel(int n_el, int n_basis, int m, const cpx<T>* v, const cpx<double>* q,
+                                          cpx<T>* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_el * m) return;
+  const int e = t / m, a = t % m;
+  cpx<double> acc = mk(0.0, 0.0);
+  for (int i = 0; i < n_basis; ++i) cmac_conj(acc, q[(size_t)i * m + a], ccast<double>(v[(size_t)e * n_basis + i]));
+  out[t] = ccast<T>(acc);
+}
+
+// delta-gap port across basis function `port`: V'_{e,a} = amp_e conj(Q_port,a)
+template <class T>
+__global__ void port_excitation_kernel(int n_el, int m, int port, const cpx<T>* amp, const cpx<double>* q,
+                                       cpx<T>* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_el * m) return;
+  const int e = t / m, a = t % m;
+  out[t] = ccast<T>(conj(q[(size_t)port * m + a]) * ccast<double>(amp[e]));
+}
+
+// port current of element e: (Q I'_e)[port] = sum_a Q_port,a I'_{e,a}
+template <class T>
+__global__ void port_currents_kernel(int n_el, int m, int port, const cpx<T>* ired, const cpx<double>* q,
+                                     cpx<T>* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_el) return;
+  cpx<double> acc = mk(0.0, 0.0);
+  for (int a = 0; a < m; ++a) cmac(acc, q[(size_t)port * m + a], ccast<double>(ired[(size_t)e * m + a]));
+  out[e] = ccast<T>(acc);
+}
+
+int grid_for(int64_t items, int per_block, int cap) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, cap));
+}
+
+}  // namespace
+
+int lu_panel_width() { return kNb; }
+
+template <class T>
+cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_t s) {
+  const int sms = current_sm_count();
+  const int n_panels = (n + kNb - 1) / kNb;
+  cudaError_t e = cudaMemsetAsync(w.bar, 0, (size_t)n_panels * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const size_t trsm_threads = sizeof(T) == 8 ? 64 : 128;
+  const size_t trsm_smem = (size_t)kNb * kNb * sizeof(cpx<T>) + (size_t)kNb * trsm_threads * sizeof(cpx<T>);
+  const size_t gemm_smem = (size_t)kNb * (65 + 64) * sizeof(cpx<T>);
+  if ((e = cudaFuncSetAttribute(lu_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(lu_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem)) !=
+      cudaSuccess)
+    return e;
+  int per_sm = 0;
+  for (int pnl = 0; pnl < n_panels; ++pnl) {
+    const int k = pnl * kNb, kb = std::min(kNb, n - k), R = n - k;
+    // cooperative grid: all CTAs resident (bounded by occupancy), at least 16 rows each
+    int G = std::min(sms, std::max(1, R / 16));
+    const int per = (R + G - 1) / G;
+    const size_t psmem = (size_t)per + 16;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<T>, kPanelThreads, psmem)) !=
+        cudaSuccess)
+      return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    G = std::min(G, per_sm * sms);
+    PanelArgs<T> pa{a, ld, n, k, kb, w.cand_val, w.cand_row, w.bar + pnl, w.moves + (size_t)pnl * 2 * kNb,
+                    w.n_moves + pnl, w.err};
+    void* args[] = {&pa};
+    const int per2 = (R + G - 1) / G;
+    if ((e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<T>, dim3(G), dim3(kPanelThreads), args,
+                                         (size_t)per2 + 16, s)) != cudaSuccess)
+      return e;
+    lu_moves_kernel<T><<<(n + 15) / 16, 256, 0, s>>>(a, ld, n, w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl);
+    const int rest = n - k - kb;
+    if (rest > 0) {
+      lu_trsm_kernel<T><<<(rest + (int)trsm_threads - 1) / (int)trsm_threads, (int)trsm_threads, trsm_smem, s>>>(
+          a, ld, n, k, kb);
+      lu_gemm_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, gemm_smem, s>>>(a, ld, n, k, kb);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t lu_solve(const cpx<T>* a, int64_t ld, int n, const LuWork& w, cpx<T>* x, cpx<T>* y, cudaStream_t s) {
+  const int sms = current_sm_count();
+  const int n_panels = (n + kNb - 1) / kNb;
+  lu_vector_moves_kernel<T><<<1, 128, 0, s>>>(x, n_panels, w.moves, w.n_moves);
+  for (int pnl = 0; pnl < n_panels; ++pnl) {
+    const int k = pnl * kNb, kb = std::min(kNb, n - k);
+    lu_forward_kernel<T><<<grid_for(n - k - kb, 8, 2 * sms), 256, 0, s>>>(a, ld, n, k, kb, x, y);
+  }
+  for (int pnl = n_panels - 1; pnl >= 0; --pnl) {
+    const int k = pnl * kNb, kb = std::min(kNb, n - k);
+    lu_backward_kernel<T><<<grid_for(k, 8, 2 * sms), 256, 0, s>>>(a, ld, k, kb, y, x);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t residual_f64(const void* z, int64_t ld, int n, const void* x, const void* b, void* r, double* sums,
+                         cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  residual_kernel<<<grid_for(n, 8, 8 * current_sm_count()), 256, 0, s>>>(
+      reinterpret_cast<const cpx<double>*>(z), ld, n, reinterpret_cast<const cpx<double>*>(x),
+      reinterpret_cast<const cpx<double>*>(b), reinterpret_cast<cpx<double>*>(r), sums);
+  return cudaGetLastError();
+}
+
+cudaError_t residual_f32(const void* z, int64_t ld, int n, const void* x, const void* b, double* sums,
+                         cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  residual32_kernel<<<grid_for(n, 8, 8 * current_sm_count()), 256, 0, s>>>(
+      reinterpret_cast<const cpx<float>*>(z), ld, n, reinterpret_cast<const cpx<float>*>(x),
+      reinterpret_cast<const cpx<float>*>(b), sums);
+  return cudaGetLastError();
+}
+
+template <class TD, class TS>
+cudaError_t copy_matrix(const void* src, int64_t ld, int n, void* dst, cudaStream_t s) {
+  copy_matrix_kernel<TD, TS><<<grid_for((int64_t)n * n, 256, 16 * current_sm_count()), 256, 0, s>>>(
+      reinterpret_cast<const cpx<TS>*>(src), ld, n, reinterpret_cast<cpx<TD>*>(dst));
+  return cudaGetLastError();
+}
+
+template <class TD, class TS>
+cudaError_t copy_vector(const void* src, int n, void* dst, cudaStream_t s) {
+  copy_vector_kernel<TD, TS><<<grid_for(n, 256, 4 * current_sm_count()), 256, 0, s>>>(
+      reinterpret_cast<const cpx<TS>*>(src), n, reinterpret_cast<cpx<TD>*>(dst));
+  return cudaGetLastError();
+}
+
+cudaError_t add_correction(void* x, const void* d, int n, double* sums, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  add_correction_kernel<<<grid_for(n, 256, 4 * current_sm_count()), 256, 0, s>>>(
+      reinterpret_cast<cpx<double>*>(x), reinterpret_cast<const cpx<float>*>(d), n, sums);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_excitation(int kind, int n_el, int n_basis, int m, int port, const void* in, const double* q,
+                              void* out, cudaStream_t s) {
+  const cpx<double>* qd = reinterpret_cast<const cpx<double>*>(q);
+  const int items = kind == 2 ? n_el : n_el * m;
+  const int blocks = (items + 255) / 256;
+  if (kind == 0)
+    reduced_excitation_kernel<T><<<blocks, 256, 0, s>>>(n_el, n_basis, m, reinterpret_cast<const cpx<T>*>(in), qd,
+                                                        reinterpret_cast<cpx<T>*>(out));
+  else if (kind == 1)
+    port_excitation_kernel<T><<<blocks, 256, 0, s>>>(n_el, m, port, reinterpret_cast<const cpx<T>*>(in), qd,
+                                                     reinterpret_cast<cpx<T>*>(out));
+  else
+    port_currents_kernel<T><<<blocks, 256, 0, s>>>(n_el, m, port, reinterpret_cast<const cpx<T>*>(in), qd,
+                                                   reinterpret_cast<cpx<T>*>(out));
+  return cudaGetLastError();
+}
+
+template cudaError_t lu_factor<float>(cpx<float>*, int64_t, int, const LuWork&, cudaStream_t);
+template cudaError_t lu_factor<double>(cpx<double>*, int64_t, int, const LuWork&, cudaStream_t);
+template cudaError_t lu_solve<float>(const cpx<float>*, int64_t, int, const LuWork&, cpx<float>*, cpx<float>*,
+                                     cudaStream_t);
+template cudaError_t lu_solve<double>(const cpx<double>*, int64_t, int, const LuWork&, cpx<double>*, cpx<double>*,
+                                      cudaStream_t);
+template cudaError_t copy_matrix<float, double>(const void*, int64_t, int, void*, cudaStream_t);
+template cudaError_t copy_matrix<float, float>(const void*, int64_t, int, void*, cudaStream_t);
+template cudaError_t copy_matrix<double, double>(const void*, int64_t, int, void*, cudaStream_t);
+template cudaError_t copy_vector<float, double>(const void*, int, void*, cudaStream_t);
+template cudaError_t copy_vector<double, float>(const void*, int, void*, cudaStream_t);
+template cudaError_t copy_vector<float, float>(const void*, int, void*, cudaStream_t);
+template cudaError_t copy_vector<double, double>(const void*, int, void*, cudaStream_t);
+template cudaError_t launch_excitation<float>(int, int, int, int, int, const void*, const double*, void*,
+                                              cudaStream_t);
+template cudaError_t launch_excitation<double>(int, int, int, int, int, const void*, const double*, void*,
+                                               cudaStream_t);
+
+}  // namespace cfft
