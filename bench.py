@@ -554,6 +554,50 @@ def bench_grad(torch, cfft, args, dev):
             "grad_norm_pos": float(pos_t.grad.norm()), "grad_eps_h": eh.grad.tolist()}
 
 
+def bench_solve(torch, cfft, args, dev):
+    """Reduced system of the 2,000-element array (M = 4: an 8,000 x 8,000 complex matrix, the
+    gradient workload's layout): FP32 fill, delta-gap port excitation, then the LU solve in
+    complex64, and FP32 factorization + FP64 refinement on a complex128 copy of the same
+    matrix; times from the library's CUDA events (factorization, solve)."""
+    wl = workloads.patch_m4(precision="fp32", rotation_classes=4)
+    pos, rot = workloads.poisson_disc(2000, 25.0, 0.5, seed=5), workloads.rotations(2000, seed=5)
+    ctx = cfft.Context(dev)
+    set_problem(ctx, wl)
+    ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, cfft.CFFT_FP32_MIXED, 4)
+    m = wl.element.n_mbf
+    n = 2000 * m
+    z = torch.empty((n, n), dtype=torch.complex64, device=dev)
+    ctx.fill_reduced_matrix(torch.tensor(pos, device=dev), torch.tensor(rot, dtype=torch.int32, device=dev), z)
+    port = 37
+    amps = torch.ones(2000, dtype=torch.complex64, device=dev)
+    v = ctx.port_excitation(port, amps)
+    res = {"workload": "A=2000 Poisson-disc elements in a disc of radius 25 lambda0, rotations {0,90}, M=4: "
+                       "dense %d x %d reduced matrix, delta-gap port on basis function %d" % (n, n, port),
+           "flops_per_factorization": 8.0 * n ** 3 / 3.0}
+    for name, mat, refine in (("complex64", z, False), ("complex128_refined", None, True)):
+        if mat is None:
+            mat = z.to(torch.complex128)
+            vv = v.to(torch.complex128)
+        else:
+            vv = v
+        runs = []
+        for _ in range(2):
+            i_red = ctx.solve_reduced(mat, vv, refine=refine)
+            runs.append(ctx.solve_info())
+        inf = runs[-1]
+        r = {"ms_factor": inf["ms_factor"], "ms_solve": inf["ms_solve"], "residual": inf["residual"],
+             "refinements": inf["refinements"],
+             "factor_tflops": res["flops_per_factorization"] / (inf["ms_factor"] / 1e3) / 1e12}
+        if name == "complex64":
+            ip = ctx.port_currents(port, i_red)
+            r["port_current_mean_abs"] = float(ip.abs().mean())
+        res[name] = r
+        del mat
+    del z
+    torch.cuda.empty_cache()
+    return res
+
+
 def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -725,6 +769,7 @@ def run_cfft(args):
     fill, fill_sample = (None, None) if args.skip_fill else bench_fill(torch, cfft, args, dev)
     batch, batch_sample = (None, None) if args.skip_batch else bench_batch(torch, cfft, args, dev)
     grad = None if args.skip_grad else bench_grad(torch, cfft, args, dev)
+    solve = None if args.skip_solve else bench_solve(torch, cfft, args, dev)
     launches = int(sum(i["launches"] for i in infos))
     line = {"metric": "C-FFT table samples/s", "value": value, "unit": "samples/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -749,6 +794,10 @@ def run_cfft(args):
         line["batch"] = batch
     if grad is not None:
         line["grad"] = grad
+    if solve is not None:
+        p32, _, _ = pipe_peaks(peaks)
+        solve["complex64"]["factor_frac_of_fp32_peak"] = solve["complex64"]["factor_tflops"] / p32
+        line["solve"] = solve
     line["peaks_source"] = peaks["_source"]
     if peaks.get("micro"):
         line["peaks_measured"] = {"fp32_tflops": peaks["micro"]["fp32"], "fp64_tflops": peaks["micro"]["fp64"],
@@ -803,6 +852,7 @@ def main():
     ap.add_argument("--only-fill", action="store_true", help="time the fill alone")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
+    ap.add_argument("--skip-solve", action="store_true", help="skip the reduced-system solve")
     ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 GPU form")
     ap.add_argument("--table-n", type=int, help="contour samples (small profiling case)")
     ap.add_argument("--table-nrho", type=int, help="rho points (small profiling case)")

@@ -130,8 +130,9 @@ struct cfft_ctx {
   std::vector<std::complex<double>> q_user;
   DevBuf d_quser;
   // dense LU of the reduced system: the factored copy, work arrays, vectors, timing
-  DevBuf lu_a, lu_moves, lu_nmoves, lu_cand_v, lu_cand_r, lu_bar, lu_err, lu_x, lu_y, lu_x64, lu_r, lu_sums;
+  DevBuf lu_a, lu_moves, lu_nmoves, lu_cand_v, lu_cand_r, lu_cand_d, lu_bar, lu_err, lu_x, lu_y, lu_x64, lu_r, lu_sums;
   cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};
+  int lu_diag[3] = {0, 0, 0};
   cfft_solve_info solve_info{};
   // tensor-core spectra: float copies of the element and its GEMM B operand
   DevBuf tc_bx, tc_by, tc_bmat, tc_bmat_mirror, tc_shapes;
@@ -1497,7 +1498,7 @@ void cfft_destroy(cfft_ctx* ctx) {
                       &ctx->d_y, &ctx->d_grid, &ctx->d_table, &ctx->d_tw, &ctx->d_cnodes,
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
                       &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->d_ftable, &ctx->d_fest, &ctx->d_quser, &ctx->lu_a, &ctx->lu_moves,
-                      &ctx->lu_nmoves, &ctx->lu_cand_v, &ctx->lu_cand_r, &ctx->lu_bar, &ctx->lu_err, &ctx->lu_x,
+                      &ctx->lu_nmoves, &ctx->lu_cand_v, &ctx->lu_cand_r, &ctx->lu_cand_d, &ctx->lu_bar, &ctx->lu_err, &ctx->lu_x,
                       &ctx->lu_y, &ctx->lu_x64, &ctx->lu_r, &ctx->lu_sums, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
                       &ctx->tc_bmat_mirror, &ctx->tc_shapes};
     for (DevBuf* b : bufs) b->release();
@@ -2025,8 +2026,9 @@ cfft_status lu_work(cfft_ctx* ctx, int n, LuWork* w) {
   const int panels = (n + nb - 1) / nb;
   CFFT_CUDA(ctx->lu_moves.ensure((size_t)panels * 2 * nb * sizeof(int2)), "alloc LU");
   CFFT_CUDA(ctx->lu_nmoves.ensure((size_t)panels * sizeof(int)), "alloc LU");
-  CFFT_CUDA(ctx->lu_cand_v.ensure((size_t)ctx->sm_count * 8 * sizeof(double)), "alloc LU");
-  CFFT_CUDA(ctx->lu_cand_r.ensure((size_t)ctx->sm_count * 8 * sizeof(int)), "alloc LU");
+  CFFT_CUDA(ctx->lu_cand_v.ensure((size_t)ctx->sm_count * 2 * sizeof(double)), "alloc LU");
+  CFFT_CUDA(ctx->lu_cand_r.ensure((size_t)ctx->sm_count * 2 * sizeof(int)), "alloc LU");
+  CFFT_CUDA(ctx->lu_cand_d.ensure((size_t)ctx->sm_count * 2 * nb * 16), "alloc LU");
   CFFT_CUDA(ctx->lu_bar.ensure((size_t)panels * sizeof(unsigned)), "alloc LU");
   CFFT_CUDA(ctx->lu_err.ensure(sizeof(int)), "alloc LU");
   CFFT_CUDA(ctx->lu_sums.ensure(4 * sizeof(double)), "alloc LU");
@@ -2034,6 +2036,8 @@ cfft_status lu_work(cfft_ctx* ctx, int n, LuWork* w) {
   w->n_moves = ctx->lu_nmoves.as<int>();
   w->cand_val = ctx->lu_cand_v.as<double>();
   w->cand_row = ctx->lu_cand_r.as<int>();
+  w->cand_data = ctx->lu_cand_d.p;
+  w->diag = ctx->lu_diag;
   w->bar = ctx->lu_bar.as<unsigned>();
   w->err = ctx->lu_err.as<int>();
   return CFFT_OK;
@@ -2043,7 +2047,12 @@ cfft_status lu_work(cfft_ctx* ctx, int n, LuWork* w) {
 template <class T>
 cfft_status lu_factor_checked(cfft_ctx* ctx, int n, const LuWork& w) {
   cudaError_t e = lu_factor<T>(ctx->lu_a.as<cpx<T>>(), n, n, w, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "LU factorization");
+  if (e != cudaSuccess) {
+    cfft_status st = cuda_fail(ctx, e, "LU factorization");
+    ctx->err += " (panel grid " + std::to_string(w.diag[0]) + ", resident per SM " + std::to_string(w.diag[1]) +
+                ", shared bytes " + std::to_string(w.diag[2]) + ")";
+    return st;
+  }
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "LU flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "LU factorization");
@@ -2090,6 +2099,10 @@ extern "C" cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, i
   cfft_status s = lu_work(ctx, n, &w);
   if (s != CFFT_OK) return s;
   const bool fp64_lu = complex128 && mode == 0;
+  const int n_lim = fp64_lu ? lu_max_order<double>(ctx->sm_count) : lu_max_order<float>(ctx->sm_count);
+  if (n > n_lim)
+    return fail(ctx, CFFT_ERR_ARG, "solve: order " + std::to_string(n) + " exceeds " + std::to_string(n_lim) +
+                " (the panel's rows must fit the shared memory of the panel CTAs)");
   const size_t es = fp64_lu ? 16 : 8;
   CFFT_CUDA(ctx->lu_a.ensure((size_t)n * n * es), "alloc LU matrix");
   CFFT_CUDA(ctx->lu_x.ensure((size_t)n * es), "alloc LU vectors");

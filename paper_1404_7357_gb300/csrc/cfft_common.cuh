@@ -397,12 +397,17 @@ cudaError_t launch_fill_estimate(const void* table, int64_t n_series, int n_rho,
 struct LuWork {
   int2* moves;         // [panels][2 * panel width] row moves (source, destination)
   int* n_moves;        // [panels]
-  double* cand_val;    // [SMs] pivot candidates of the panel CTAs
+  double* cand_val;    // [2][SMs] pivot candidates of the panel CTAs (value, row, entries)
   int* cand_row;
+  void* cand_data;     // [2][SMs][panel width] complex, the element type
   unsigned* bar;       // [panels] grid-barrier counters
   int* err;            // bit 1: barrier wait ran out; bit 2: zero pivot
+  int* diag;           // host: [3] panel grid, resident CTAs per SM, shared bytes of the last panel
 };
 int lu_panel_width();
+// the largest order whose panels fit the panel CTAs' shared memory on `sms` SMs
+template <class T>
+int lu_max_order(int sms);
 template <class T>
 cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_t s);
 template <class T>

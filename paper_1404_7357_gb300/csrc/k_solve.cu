@@ -64,7 +64,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* s_fail) {
         *s_fail = 1;
         break;
       }
-      __nanosleep(64);
+      if (polls > 256) __nanosleep(32);   // poll tightly first: the wait is usually short
     }
     __threadfence();
   }
@@ -77,8 +77,9 @@ struct PanelArgs {
   cpx<T>* a;
   int64_t ld;
   int n, k, kb;
-  double* cand_val;   // [grid] per-CTA pivot candidates
-  int* cand_row;
+  double* cand_val;   // [2][grid] per-CTA pivot candidates (value), double-buffered by column
+  int* cand_row;      // [2][grid] (row)
+  cpx<T>* cand_data;  // [2][grid][kNb] the candidate rows' remaining panel entries
   unsigned* bar;      // barrier counter of this panel, zero at launch
   int2* moves;        // (source row, destination row), at most 2 kb
   int* n_moves;
@@ -92,32 +93,41 @@ __device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int o
   }
 }
 
+// One panel of kb columns on rows k..n-1.  Each CTA holds its slice of rows in shared
+// memory for the whole panel; per column it stages its best candidate (value, row, the
+// row's remaining entries) in global memory, and after the barrier every CTA reads all
+// candidates and takes the same pivot row.  The staging is double-buffered by column, so
+// a CTA that is one column ahead never overwrites what a slower CTA still reads.
 template <class T>
 __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p) {
   constexpr int kWarps = kPanelThreads / 32;
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int R = p.n - p.k;
+  const int R = p.n - p.k, kb = p.kb;
   const int per = (R + G - 1) / G;
-  const int lo = p.k + min(g * per, R), hi = p.k + min((g + 1) * per, R);
-  extern __shared__ unsigned char chosen[];   // [per]: row already a pivot
+  const int lo = p.k + min(g * per, R), hi = p.k + min((g + 1) * per, R), nr = hi - lo;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* rows = reinterpret_cast<cpx<T>*>(smem_raw);                       // [per][kb]
+  unsigned char* chosen = smem_raw + (size_t)per * kb * sizeof(cpx<T>);     // [per]
   __shared__ cpx<T> prow[kNb];
   __shared__ double wv[kWarps];
   __shared__ int wi[kWarps];
   __shared__ int s_piv[kNb];
-  __shared__ int s_fail, s_p;
+  __shared__ int s_fail, s_p, s_w;
+  for (int e = tid; e < nr * kb; e += blockDim.x)
+    rows[e] = p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb];
   for (int i = tid; i < per; i += blockDim.x) chosen[i] = 0;
   if (tid == 0) s_fail = 0;
   __syncthreads();
   unsigned target = 0;
   bool ok = true;
-  for (int j = 0; j < p.kb; ++j) {
-    const int c = p.k + j;
-    // this CTA's candidate: largest |re| + |im| in column c among its rows not chosen yet
+  for (int j = 0; j < kb; ++j) {
+    const int buf = j & 1;
+    // this CTA's candidate: largest |re| + |im| in column j among its rows not chosen yet
     double best = -1.0;
     int bi = 0x7fffffff;
-    for (int i = lo + tid; i < hi; i += blockDim.x) {
-      if (chosen[i - lo]) continue;
-      const cpx<T> v = ldcg(p.a + (int64_t)i * p.ld + c);
+    for (int i = tid; i < nr; i += blockDim.x) {
+      if (chosen[i]) continue;
+      const cpx<T> v = rows[i * kb + j];
       argmax_merge(best, bi, fabs((double)v.re) + fabs((double)v.im), i);
     }
 #pragma unroll
@@ -132,9 +142,16 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
       double v = wv[0];
       int r = wi[0];
       for (int w = 1; w < kWarps; ++w) argmax_merge(v, r, wv[w], wi[w]);
-      p.cand_val[g] = v;
-      p.cand_row[g] = r;
+      wv[0] = v;
+      wi[0] = r;
+      p.cand_val[buf * G + g] = v;
+      p.cand_row[buf * G + g] = r < nr ? lo + r : 0x7fffffff;
     }
+    __syncthreads();
+    const int bl = wi[0];
+    if (bl < nr)
+      for (int t = tid; t < kb - j; t += blockDim.x)
+        p.cand_data[((size_t)buf * G + g) * kNb + t] = rows[bl * kb + j + t];
     target += (unsigned)G;
     if (!grid_barrier(p.bar, target, &s_fail)) {
       ok = false;
@@ -143,14 +160,31 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
     // the pivot: best candidate over all CTAs (the same choice in every CTA)
     if (warp == 0) {
       double v = -1.0;
-      int r = 0x7fffffff;
-      for (int t = lane; t < G; t += 32) argmax_merge(v, r, __ldcg(p.cand_val + t), __ldcg(p.cand_row + t));
+      int r = 0x7fffffff, w = -1;
+      for (int t = lane; t < G; t += 32) {
+        const double cv = __ldcg(p.cand_val + buf * G + t);
+        const int cr = __ldcg(p.cand_row + buf * G + t);
+        if (cv > v || (cv == v && cr < r)) {
+          v = cv;
+          r = cr;
+          w = t;
+        }
+      }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        argmax_merge(v, r, __shfl_xor_sync(0xffffffffu, v, off), __shfl_xor_sync(0xffffffffu, r, off));
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int orow = __shfl_xor_sync(0xffffffffu, r, off), ow = __shfl_xor_sync(0xffffffffu, w, off);
+        if (ov > v || (ov == v && orow < r)) {
+          v = ov;
+          r = orow;
+          w = ow;
+        }
+      }
       if (lane == 0) {
         if (!(v > 0.0) && g == 0) atomicOr(p.err, 4);
-        s_p = (r >= p.k && r < p.n) ? r : -1;
+        const bool valid = r >= p.k && r < p.n && w >= 0;
+        s_p = valid ? r : -1;
+        s_w = valid ? w : -1;
       }
     }
     __syncthreads();
@@ -160,26 +194,25 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
       ok = false;
       break;
     }
-    // the pivot row's entries c .. k+kb-1 (its owner finished them before the barrier)
-    for (int t = tid; t < p.kb - j; t += blockDim.x) prow[t] = ldcg(p.a + (int64_t)pr * p.ld + c + t);
+    for (int t = tid; t < kb - j; t += blockDim.x) prow[t] = ldcg(p.cand_data + ((size_t)buf * G + s_w) * kNb + t);
     if (tid == 0) {
       if (pr >= lo && pr < hi) chosen[pr - lo] = 1;
       s_piv[j] = pr;
     }
     __syncthreads();
     const cpx<T> inv = crecip(prow[0]);
-    // eliminate column c from this CTA's other rows: one warp per row, lanes over columns
-    for (int i = lo + warp; i < hi; i += kWarps) {
-      if (chosen[i - lo]) continue;
-      cpx<T>* row = p.a + (int64_t)i * p.ld + c;
-      const cpx<T> l = ldcg(row) * inv;
-      for (int t = 1 + lane; t < p.kb - j; t += 32) {
-        cpx<T> v = ldcg(row + t);
-        cmac(v, mk(-l.re, -l.im), prow[t]);
-        row[t] = v;
-      }
-      __syncwarp();
-      if (lane == 0) row[0] = l;
+    // eliminate column j from this CTA's other rows: the multipliers first (one thread per
+    // row), then the updates (one warp per row, lanes over columns; rows independent)
+    for (int i = tid; i < nr; i += blockDim.x)
+      if (!chosen[i]) rows[i * kb + j] = rows[i * kb + j] * inv;
+    __syncthreads();
+#pragma unroll 4
+    for (int i = warp; i < nr; i += kWarps) {
+      if (chosen[i]) continue;
+      cpx<T>* row = rows + i * kb + j;
+      const cpx<T> l = row[0];
+      const cpx<T> ml = mk(-l.re, -l.im);
+      for (int t = 1 + lane; t < kb - j; t += 32) cmac(row[t], ml, prow[t]);
     }
     __syncthreads();
   }
@@ -187,23 +220,24 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
     if (tid == 0 && s_fail) atomicOr(p.err, 2);
     return;
   }
+  for (int e = tid; e < nr * kb; e += blockDim.x)
+    p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb] = rows[e];
   if (g == 0 && tid == 0) {
     // rows k+j <- pivot j; the rows of [k, k+kb) that were not chosen go to the places the
     // chosen rows outside that range leave free, both in increasing order
     int nm = 0, nd = 0, nv = 0;
     int displaced[kNb], vacated[kNb];
-    for (int j = 0; j < p.kb; ++j) {
+    for (int j = 0; j < kb; ++j) {
       if (s_piv[j] != p.k + j) p.moves[nm++] = make_int2(s_piv[j], p.k + j);
-      if (s_piv[j] >= p.k + p.kb) vacated[nv++] = s_piv[j];
+      if (s_piv[j] >= p.k + kb) vacated[nv++] = s_piv[j];
     }
-    for (int r = p.k; r < p.k + p.kb; ++r) {
+    for (int r = p.k; r < p.k + kb; ++r) {
       bool taken = false;
-      for (int j = 0; j < p.kb; ++j) taken = taken || s_piv[j] == r;
+      for (int j = 0; j < kb; ++j) taken = taken || s_piv[j] == r;
       if (!taken) displaced[nd++] = r;
     }
     // nd == nv: both count the pivots from outside [k, k+kb)
     for (int t = 0; t < nd && t < nv; ++t) {
-      // vacated rows in increasing order
       int m = t;
       for (int u = t + 1; u < nv; ++u)
         if (vacated[u] < vacated[m]) m = u;
@@ -235,26 +269,56 @@ __global__ void __launch_bounds__(256) lu_moves_kernel(cpx<T>* a, int64_t ld, in
     if (col < n_cols) a[(int64_t)mv[m].y * ld + col] = buf[m][cl];
 }
 
-// U12 = L11^-1 A12 on rows k..k+kb-1, columns c0.. (one thread per column; L11 and the
-// columns' partial results in shared memory)
+// Column-oriented substitution with one warp: the right-hand side's entries of rows
+// lane and lane + 32 stay in the lane's registers; at step j the solved entry x_j is
+// shuffled to every lane, and the rows below (lower) or above (upper) subtract their
+// coefficient times x_j.  M: the kb x kb diagonal block in shared memory (row stride ms).
+template <class T, bool UPPER>
+__device__ __forceinline__ void warp_substitute(const cpx<T>* M, int ms, int kb, cpx<T>& x0, cpx<T>& x1) {
+  const int lane = threadIdx.x & 31;
+  for (int s = 0; s < kb; ++s) {
+    const int j = UPPER ? kb - 1 - s : s;
+    if (UPPER) {   // x_j /= U_jj by the lane that holds row j
+      if (j < 32 && lane == j) x0 = cdiv(x0, M[j * ms + j]);
+      if (j >= 32 && lane == j - 32) x1 = cdiv(x1, M[j * ms + j]);
+    }
+    const T r0 = __shfl_sync(0xffffffffu, j < 32 ? x0.re : x1.re, j & 31);
+    const T i0 = __shfl_sync(0xffffffffu, j < 32 ? x0.im : x1.im, j & 31);
+    const cpx<T> xj = mk(-r0, -i0);
+    const bool t0 = UPPER ? lane < j : (lane > j && lane < kb);
+    const bool t1 = UPPER ? lane + 32 < j : (lane + 32 > j && lane + 32 < kb);
+    if (t0) cmac(x0, M[lane * ms + j], xj);
+    if (t1) cmac(x1, M[(lane + 32) * ms + j], xj);
+  }
+}
+
+// U12 = L11^-1 A12 on rows k..k+kb-1: L11 and a tile of 32 columns in shared memory,
+// one warp per column (lanes over rows), the tile stored back coalesced
 template <class T>
-__global__ void lu_trsm_kernel(cpx<T>* a, int64_t ld, int n, int k, int kb) {
-  extern __shared__ unsigned char sm[];
-  cpx<T>* L = reinterpret_cast<cpx<T>*>(sm);          // [kb][kb]
-  cpx<T>* X = L + kb * kb;                            // [kb][blockDim]
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < kb * kb; e += nt) {
-    const int i = e / kb, j = e % kb;
-    L[e] = j < i ? a[(int64_t)(k + i) * ld + k + j] : mk((T)0, (T)0);
+__global__ void __launch_bounds__(256) lu_trsm_kernel(cpx<T>* a, int64_t ld, int n, int k, int kb) {
+  constexpr int TC = 32, LS = kNb + 1;
+  extern __shared__ __align__(16) unsigned char sm[];
+  cpx<T>* L = reinterpret_cast<cpx<T>*>(sm);          // [kb][LS]
+  cpx<T>* X = L + kNb * LS;                            // [kNb][TC]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = k + kb + blockIdx.x * TC;
+  for (int e = tid; e < kb * kb; e += blockDim.x) L[(e / kb) * LS + e % kb] = a[(int64_t)(k + e / kb) * ld + k + e % kb];
+  for (int e = tid; e < kb * TC; e += blockDim.x) {
+    const int r = e / TC, c = e % TC;
+    X[r * TC + c] = c0 + c < n ? a[(int64_t)(k + r) * ld + c0 + c] : mk((T)0, (T)0);
   }
   __syncthreads();
-  const int col = k + kb + blockIdx.x * nt + tid;
-  if (col >= n) return;
-  for (int i = 0; i < kb; ++i) {
-    cpx<T> x = a[(int64_t)(k + i) * ld + col];
-    for (int j = 0; j < i; ++j) cmac(x, mk(-L[i * kb + j].re, -L[i * kb + j].im), X[j * nt + tid]);
-    X[i * nt + tid] = x;
-    a[(int64_t)(k + i) * ld + col] = x;
+  for (int c = warp; c < TC; c += blockDim.x / 32) {
+    cpx<T> x0 = lane < kb ? X[lane * TC + c] : mk((T)0, (T)0);
+    cpx<T> x1 = lane + 32 < kb ? X[(lane + 32) * TC + c] : mk((T)0, (T)0);
+    warp_substitute<T, false>(L, LS, kb, x0, x1);
+    if (lane < kb) X[lane * TC + c] = x0;
+    if (lane + 32 < kb) X[(lane + 32) * TC + c] = x1;
+  }
+  __syncthreads();
+  for (int e = tid; e < kb * TC; e += blockDim.x) {
+    const int r = e / TC, c = e % TC;
+    if (c0 + c < n) a[(int64_t)(k + r) * ld + c0 + c] = X[r * TC + c];
   }
 }
 
@@ -323,31 +387,23 @@ __global__ void lu_vector_moves_kernel(cpx<T>* x, int n_panels, const int2* move
   }
 }
 
-// solve the diagonal block of rows k..k+kb-1 with one warp: unit lower (forward) or
-// upper (backward); rhs from `src`, result to shared `yb`
+// the diagonal block of rows k..k+kb-1 into shared memory (coalesced), then one warp
+// solves it against src[k..k+kb) (unit lower: forward; upper: backward) into xb
 template <class T, bool UPPER>
-__device__ void block_solve(const cpx<T>* a, int64_t ld, int k, int kb, const cpx<T>* src, cpx<T>* yb) {
-  const int lane = threadIdx.x & 31;
-  for (int s = 0; s < kb; ++s) {
-    const int i = UPPER ? kb - 1 - s : s;
-    cpx<T> acc = mk((T)0, (T)0);
-    if (UPPER) {
-      for (int j = i + 1 + lane; j < kb; j += 32) cmac(acc, a[(int64_t)(k + i) * ld + k + j], yb[j]);
-    } else {
-      for (int j = lane; j < i; j += 32) cmac(acc, a[(int64_t)(k + i) * ld + k + j], yb[j]);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
-      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
-    }
-    if (lane == 0) {
-      cpx<T> v = src[k + i] - acc;
-      if (UPPER) v = cdiv(v, a[(int64_t)(k + i) * ld + k + i]);
-      yb[i] = v;
-    }
-    __syncwarp();
+__device__ void block_solve(const cpx<T>* a, int64_t ld, int k, int kb, const cpx<T>* src, cpx<T>* D,
+                            cpx<T>* xb) {
+  constexpr int LS = kNb + 1;
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) D[(e / kb) * LS + e % kb] = a[(int64_t)(k + e / kb) * ld + k + e % kb];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    cpx<T> x0 = lane < kb ? src[k + lane] : mk((T)0, (T)0);
+    cpx<T> x1 = lane + 32 < kb ? src[k + lane + 32] : mk((T)0, (T)0);
+    warp_substitute<T, UPPER>(D, LS, kb, x0, x1);
+    if (lane < kb) xb[lane] = x0;
+    if (lane + 32 < kb) xb[lane + 32] = x1;
   }
+  __syncthreads();
 }
 
 // forward step of panel k: y_b = L11^-1 x_b (written to y), x[r] -= L[r][k..] y_b for the
@@ -356,8 +412,8 @@ template <class T>
 __global__ void __launch_bounds__(256) lu_forward_kernel(const cpx<T>* a, int64_t ld, int n, int k, int kb,
                                                          cpx<T>* x, cpx<T>* y) {
   __shared__ cpx<T> yb[kNb];
-  if (threadIdx.x < 32) block_solve<T, false>(a, ld, k, kb, x, yb);
-  __syncthreads();
+  extern __shared__ __align__(16) unsigned char sm[];
+  block_solve<T, false>(a, ld, k, kb, x, reinterpret_cast<cpx<T>*>(sm), yb);
   if (blockIdx.x == 0)
     for (int t = threadIdx.x; t < kb; t += blockDim.x) y[k + t] = yb[t];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -379,8 +435,8 @@ template <class T>
 __global__ void __launch_bounds__(256) lu_backward_kernel(const cpx<T>* a, int64_t ld, int k, int kb,
                                                           cpx<T>* y, cpx<T>* x) {
   __shared__ cpx<T> xb[kNb];
-  if (threadIdx.x < 32) block_solve<T, true>(a, ld, k, kb, y, xb);
-  __syncthreads();
+  extern __shared__ __align__(16) unsigned char sm[];
+  block_solve<T, true>(a, ld, k, kb, y, reinterpret_cast<cpx<T>*>(sm), xb);
   if (blockIdx.x == 0)
     for (int t = threadIdx.x; t < kb; t += blockDim.x) x[k + t] = xb[t];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -524,17 +580,48 @@ int grid_for(int64_t items, int per_block, int cap) {
 
 int lu_panel_width() { return kNb; }
 
+// panel CTAs: enough that each CTA's rows fit kPanelSmem bytes of shared memory, and about
+// kPanelRows rows each (the per-column elimination is short; the grid barrier's cost grows
+// slowly with the CTA count), at most one per SM
+constexpr size_t kPanelSmem = 160 * 1024;
+constexpr int kPanelRows = 64;
+
+template <class T>
+int lu_panel_grid(int rows, int sms) {
+  const int64_t row_bytes = (int64_t)kNb * sizeof(cpx<T>);
+  const int64_t need = (rows * row_bytes + (int64_t)kPanelSmem - 1) / (int64_t)kPanelSmem;
+  const int64_t g = std::max<int64_t>(need, std::min<int64_t>(sms, (rows + kPanelRows - 1) / kPanelRows));
+  return (int)std::max<int64_t>(1, g);
+}
+
+template <class T>
+int lu_max_order(int sms) {
+  return (int)((int64_t)sms * (int64_t)kPanelSmem / ((int64_t)kNb * sizeof(cpx<T>)));
+}
+
 template <class T>
 cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_t s) {
   const int sms = current_sm_count();
   const int n_panels = (n + kNb - 1) / kNb;
+  if (lu_panel_grid<T>(n, sms) > sms) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(w.bar, 0, (size_t)n_panels * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const size_t trsm_threads = sizeof(T) == 8 ? 64 : 128;
-  const size_t trsm_smem = (size_t)kNb * kNb * sizeof(cpx<T>) + (size_t)kNb * trsm_threads * sizeof(cpx<T>);
+  const size_t trsm_smem = (size_t)kNb * (kNb + 1 + 32) * sizeof(cpx<T>);
   const size_t gemm_smem = (size_t)kNb * (65 + 64) * sizeof(cpx<T>);
+  // the most shared memory any panel's CTAs take (the grid shrinks in steps as the rows do)
+  size_t panel_smem0 = 0;
+  for (int pnl = 0; pnl < n_panels; ++pnl) {
+    const int R = n - pnl * kNb, G = lu_panel_grid<T>(R, sms), per = (R + G - 1) / G;
+    panel_smem0 = std::max(panel_smem0, (size_t)per * kNb * sizeof(cpx<T>) + (size_t)per + 16);
+  }
+  if ((e = cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)panel_smem0)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(lu_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem)) !=
       cudaSuccess)
     return e;
@@ -542,29 +629,28 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
       cudaSuccess)
     return e;
   int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<T>, kPanelThreads,
+                                                         panel_smem0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   for (int pnl = 0; pnl < n_panels; ++pnl) {
     const int k = pnl * kNb, kb = std::min(kNb, n - k), R = n - k;
-    // cooperative grid: all CTAs resident (bounded by occupancy), at least 16 rows each
-    int G = std::min(sms, std::max(1, R / 16));
+    const int G = std::min(lu_panel_grid<T>(R, sms), per_sm * sms);   // all CTAs resident
     const int per = (R + G - 1) / G;
-    const size_t psmem = (size_t)per + 16;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<T>, kPanelThreads, psmem)) !=
-        cudaSuccess)
-      return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    G = std::min(G, per_sm * sms);
-    PanelArgs<T> pa{a, ld, n, k, kb, w.cand_val, w.cand_row, w.bar + pnl, w.moves + (size_t)pnl * 2 * kNb,
-                    w.n_moves + pnl, w.err};
+    const size_t psmem = (size_t)per * kb * sizeof(cpx<T>) + (size_t)per + 16;
+    PanelArgs<T> pa{a, ld, n, k, kb, w.cand_val, w.cand_row, reinterpret_cast<cpx<T>*>(w.cand_data),
+                    w.bar + pnl, w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl, w.err};
     void* args[] = {&pa};
-    const int per2 = (R + G - 1) / G;
-    if ((e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<T>, dim3(G), dim3(kPanelThreads), args,
-                                         (size_t)per2 + 16, s)) != cudaSuccess)
+    w.diag[0] = G;
+    w.diag[1] = per_sm;
+    w.diag[2] = (int)psmem;
+    if ((e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<T>, dim3(G), dim3(kPanelThreads), args, psmem,
+                                         s)) != cudaSuccess)
       return e;
     lu_moves_kernel<T><<<(n + 15) / 16, 256, 0, s>>>(a, ld, n, w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl);
     const int rest = n - k - kb;
     if (rest > 0) {
-      lu_trsm_kernel<T><<<(rest + (int)trsm_threads - 1) / (int)trsm_threads, (int)trsm_threads, trsm_smem, s>>>(
-          a, ld, n, k, kb);
+      lu_trsm_kernel<T><<<(rest + 31) / 32, 256, trsm_smem, s>>>(a, ld, n, k, kb);
       lu_gemm_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, gemm_smem, s>>>(a, ld, n, k, kb);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -576,14 +662,22 @@ template <class T>
 cudaError_t lu_solve(const cpx<T>* a, int64_t ld, int n, const LuWork& w, cpx<T>* x, cpx<T>* y, cudaStream_t s) {
   const int sms = current_sm_count();
   const int n_panels = (n + kNb - 1) / kNb;
+  const size_t dsm = (size_t)kNb * (kNb + 1) * sizeof(cpx<T>);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(lu_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(lu_backward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)) !=
+      cudaSuccess)
+    return e;
   lu_vector_moves_kernel<T><<<1, 128, 0, s>>>(x, n_panels, w.moves, w.n_moves);
   for (int pnl = 0; pnl < n_panels; ++pnl) {
     const int k = pnl * kNb, kb = std::min(kNb, n - k);
-    lu_forward_kernel<T><<<grid_for(n - k - kb, 8, 2 * sms), 256, 0, s>>>(a, ld, n, k, kb, x, y);
+    lu_forward_kernel<T><<<grid_for(n - k - kb, 8, 2 * sms), 256, dsm, s>>>(a, ld, n, k, kb, x, y);
   }
   for (int pnl = n_panels - 1; pnl >= 0; --pnl) {
     const int k = pnl * kNb, kb = std::min(kNb, n - k);
-    lu_backward_kernel<T><<<grid_for(k, 8, 2 * sms), 256, 0, s>>>(a, ld, k, kb, y, x);
+    lu_backward_kernel<T><<<grid_for(k, 8, 2 * sms), 256, dsm, s>>>(a, ld, k, kb, y, x);
   }
   return cudaGetLastError();
 }
@@ -648,6 +742,8 @@ cudaError_t launch_excitation(int kind, int n_el, int n_basis, int m, int port, 
   return cudaGetLastError();
 }
 
+template int lu_max_order<float>(int);
+template int lu_max_order<double>(int);
 template cudaError_t lu_factor<float>(cpx<float>*, int64_t, int, const LuWork&, cudaStream_t);
 template cudaError_t lu_factor<double>(cpx<double>*, int64_t, int, const LuWork&, cudaStream_t);
 template cudaError_t lu_solve<float>(const cpx<float>*, int64_t, int, const LuWork&, cpx<float>*, cpx<float>*,

@@ -274,8 +274,9 @@ def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
         "item": 0, "wl": wl, "rows": np.array([0, 16, 31]), "got": ref_full[0][..., [0, 16, 31]],
         "height_times_rho_max": 0.1}))
     monkeypatch.setattr(bench, "bench_grad", lambda *a: {"metric": "grad"})
+    monkeypatch.setattr(bench, "bench_solve", lambda *a: {"complex64": {"factor_tflops": 7.5}})
     args = types.SimpleNamespace(steps=2, warmup=3, only_fill=False, skip_fp64=False, skip_fill=False,
-                                 skip_batch=False, skip_grad=False, skip_cpu=False)
+                                 skip_batch=False, skip_grad=False, skip_cpu=False, skip_solve=False)
     bench.run_cfft(args)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -292,3 +293,4 @@ def test_bench_line_assembly_with_stand_in_stages(monkeypatch, capsys):
     assert line["roofline"]["bound"] in ("alu", "tensor") and 0 < line["roofline"]["frac"]
     assert line["peaks_measured"]["tf32_tflops"] == 1000.0 and "roofline" in line["fp64_gpu"]
     assert "_info" not in line["fp64_gpu"]
+    assert line["solve"]["complex64"]["factor_frac_of_fp32_peak"] == pytest.approx(7.5 / 75.0)
