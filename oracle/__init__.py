@@ -26,6 +26,11 @@ Everything here is written from the paper's definitions, in the paper's order:
 * ``solve``     -- the reduced system of Section II: excitation V' = Q^H V
                    (Eq. 4), a direct solution of Z' I' = V', the currents
                    I = Q I' and the port currents of delta-gap excitations.
+* ``cartesian`` -- the paper's own 2-D form (Section III-B-2/3, Eq. 21-24,
+                   Appendix I): the kernel at the complex extension
+                   k (1 + i gamma) on a real (kx, ky) grid, one FFT2 per Taylor
+                   monomial with Appendix I's signs, the zero-padded 2x
+                   refinement, second-order interpolation.
 
 All arithmetic is numpy/scipy float64 / complex128.  Nothing here is blocked,
 fused or reordered beyond the definitions; speed is not a goal.
@@ -34,5 +39,7 @@ Parity pins (what this oracle is checked against, in ``tests/test_oracle_*``):
 closed forms (Gaussian Hankel pair, 2-D Gaussian Fourier pair, rooftop/strip
 transforms by brute-force spatial quadrature), textbook surface-wave
 dispersion relations, contour independence by Cauchy, real-axis quadrature
-with surface-wave pole extraction, reciprocity and rotation symmetries.
+with surface-wave pole extraction, reciprocity and rotation symmetries; the
+Cartesian form against a closed form, the direct sum of its own definition
+and convergence to the polar integral.
 """
