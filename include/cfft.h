@@ -564,6 +564,55 @@ typedef struct {
 } cfft_solve_info;
 cfft_status cfft_get_solve_info(const cfft_ctx* ctx, cfft_solve_info* info);
 
+/* The paper's own 2-D Cartesian C-FFT (Section III-B-2 and III-B-3, Eq. 21-24,
+ * Appendix I), beside the harmonic tabulation.  On the real grid
+ * kx, ky = -beta_max + n dk (n < n_grid, dk = 2 beta_max / n_grid) the contour of
+ * cfft_build_contour enters through the extension k (1 + i gamma), gamma =
+ * beta_I(|k|) / |k| (Eq. 20), with the Jacobian (1 + i d beta_I/d beta_R)
+ * (1 + i gamma) (Eq. 21); samples outside |k| <= beta_max are zero (the polar
+ * integral's limit).  The contour factor exp(gamma k.Delta) is expanded in
+ * Taylor monomials (Eq. 22), each an FFT2 with the signs of Appendix I, the
+ * spectrum zero-padded to twice the size (the Whittaker-Shannon refinement at
+ * the end of Section III-B-3).  The table holds, for every MBF pair (a, b),
+ *   Z'_ab(x0 + i step, x0 + j step),  i, j < 2 n_grid,
+ *   x0 = -n_grid pi / (2 beta_max), step = pi / (2 beta_max)
+ * (row-major [pair a*M+b][i: dx][j: dy]; complex128 for CFFT_FP64, else
+ * complex64).  rho_max: the largest element distance the fill will ask for;
+ * it must lie inside the table by two steps (else CFFT_ERR_ARG: raise
+ * n_grid), and sets the automatic Taylor order (taylor_order = -1: from
+ * height * rho_max as for cfft_tabulate_reactions; a fixed order 0..40
+ * otherwise).  n_grid: a power of two in 16..2048.  The slope of the contour
+ * is discontinuous on the circle |k| = beta_p and the integrand is cut on
+ * |k| = beta_max; no Cartesian grid follows either, so the rectangle rule is
+ * first to second order in dk there (the harmonic tabulation integrates the
+ * same contour along beta to spectral accuracy).  One rotation class
+ * (unrotated elements).  Requires substrate, element and contour
+ * (CFFT_ERR_STATE).  Synchronizes. */
+cfft_status cfft_tabulate_cartesian(cfft_ctx* ctx, int n_grid, double rho_max, int taylor_order,
+                                    cfft_precision precision);
+
+/* Description of the Cartesian table: grid size, table size (2 n_grid), Taylor
+ * order, number of monomials (FFT2s per pair), element type, lattice origin
+ * and step, rho_max, and the device time of the tabulation in ms. */
+typedef struct {
+  int n_grid, n_table, taylor_order, monomials, complex128;
+  double x0, step, rho_max, ms;
+} cfft_cartesian_info;
+/* Borrow the Cartesian table (device, context-owned, valid until the next
+ * Cartesian tabulation or destroy) and its description.  CFFT_ERR_STATE if
+ * none. */
+cfft_status cfft_get_cartesian_table(const cfft_ctx* ctx, const void** dev_ptr, cfft_cartesian_info* info);
+
+/* Reduced matrix of unrotated elements from the Cartesian table by second-order
+ * (three-point) Lagrange interpolation in dx and dy around the nearest lattice
+ * node (the end of Section III-B-3):
+ *   Z_out[(m M + a) ld + n M + b] = Z'_ab(r_m - r_n)
+ * pos_xy, z_out, ld, out_complex128 as in cfft_fill_reduced_matrix.  A pair
+ * farther apart than the table's rho_max returns CFFT_ERR_ARG (its entries
+ * zero).  Synchronizes. */
+cfft_status cfft_fill_cartesian(cfft_ctx* ctx, int n_elements, const double* pos_xy, void* z_out,
+                                int64_t ld, int out_complex128);
+
 /* Arithmetic peak microbenchmark (no counterpart in the paper; the roofline
  * fractions of the measurement divide by its results).  which:
  *   0  FP32 FMA pipe: independent fused multiply-add chains on every SM

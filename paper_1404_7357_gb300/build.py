@@ -17,7 +17,7 @@ OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcfft.so")
 HEADERS = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")) + \
     [os.path.join(ROOT, "include", "cfft.h")]
-UNITS = ["k_contour", "k_integrand", "k_integrand_tc", "k_fft", "k_backproject", "k_backproject_tc", "k_fill", "k_fill_bucket", "k_spectra_tc", "k_peaks", "k_solve", "cfft_api", "cfft_static"]
+UNITS = ["k_contour", "k_integrand", "k_integrand_tc", "k_fft", "k_backproject", "k_backproject_tc", "k_fill", "k_fill_bucket", "k_spectra_tc", "k_peaks", "k_solve", "k_cartesian", "cfft_api", "cfft_static"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -31,7 +31,7 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table",
            "cfft_fill_backward_residual", "cfft_test_fail_allocation", "cfft_measure_peak",
            "cfft_reduced_excitation", "cfft_port_excitation", "cfft_port_currents", "cfft_solve_reduced",
-           "cfft_get_solve_info"]
+           "cfft_get_solve_info", "cfft_tabulate_cartesian", "cfft_get_cartesian_table", "cfft_fill_cartesian"]
 
 
 class CfftLibraryError(ImportError):
@@ -69,6 +69,11 @@ class Info(ctypes.Structure):
                [("fill_form", ctypes.c_int), ("fill_err_est", ctypes.c_double)] + \
                [(n, ctypes.c_int) for n in ("fill_refine", "fill_n_rho")] + \
                [(n, ctypes.c_double) for n in ("tc_flops_integrand", "tc_flops_backproject")]
+
+
+class CartesianInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("n_grid", "n_table", "taylor_order", "monomials", "complex128")] + \
+               [(n, ctypes.c_double) for n in ("x0", "step", "rho_max", "ms")]
 
 
 class SolveInfo(ctypes.Structure):
@@ -117,6 +122,9 @@ def _load():
         "cfft_port_currents": ([P, I, I, P, P, I], I),
         "cfft_solve_reduced": ([P, I, P, L, P, P, I, I], I),
         "cfft_get_solve_info": ([P, ctypes.POINTER(SolveInfo)], I),
+        "cfft_tabulate_cartesian": ([P, I, D, I, I], I),
+        "cfft_get_cartesian_table": ([P, ctypes.POINTER(P), ctypes.POINTER(CartesianInfo)], I),
+        "cfft_fill_cartesian": ([P, I, P, P, L, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -484,6 +492,38 @@ class Context:
         self._check(_lib.cfft_solve_reduced(self._h, n, ctypes.c_void_p(z.data_ptr()), z.stride(0),
                                             ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                             c128, 1 if refine else 0))
+        return out
+
+    # ---- the paper's 2-D Cartesian C-FFT (Eq. 21-24, Appendix I)
+
+    def tabulate_cartesian(self, n_grid, rho_max, precision, taylor_order=-1):
+        self._check(_lib.cfft_tabulate_cartesian(self._h, int(n_grid), float(rho_max), int(taylor_order),
+                                                 precision))
+        return self.cartesian_info()
+
+    def cartesian_info(self):
+        ptr = ctypes.c_void_p()
+        inf = CartesianInfo()
+        self._check(_lib.cfft_get_cartesian_table(self._h, ctypes.byref(ptr), ctypes.byref(inf)))
+        return {n: getattr(inf, n) for n, _ in CartesianInfo._fields_}
+
+    def cartesian_table(self):
+        """Copy of the Cartesian table: (M*M, 2 n_grid, 2 n_grid) complex CUDA tensor, axis 1 = dx."""
+        ptr = ctypes.c_void_p()
+        inf = CartesianInfo()
+        self._check(_lib.cfft_get_cartesian_table(self._h, ctypes.byref(ptr), ctypes.byref(inf)))
+        shape = (self.n_mbf * self.n_mbf, inf.n_table, inf.n_table)
+        view = _DeviceArray(ptr.value, shape, "<c16" if inf.complex128 else "<c8")
+        return self._torch.as_tensor(view, device="cuda:%d" % self.device).clone()
+
+    def fill_cartesian(self, pos, out):
+        """Reduced matrix of unrotated elements from the Cartesian table (second-order
+        interpolation): pos cuda float64 (A, 2), out cuda complex (A*M, ld)."""
+        torch = self._torch
+        a = self._check_layout(pos, None, out, device=True)
+        self._check(_lib.cfft_fill_cartesian(self._h, a, ctypes.c_void_p(pos.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                             int(out.dtype == torch.complex128)))
         return out
 
     def solve_info(self):

@@ -134,6 +134,10 @@ struct cfft_ctx {
   cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};
   int lu_diag[3] = {0, 0, 0};
   cfft_solve_info solve_info{};
+  // the 2-D Cartesian C-FFT table and its work buffers
+  DevBuf c_tab, c_work, c_work2, c_im, c_gx, c_gy, c_flag;
+  bool has_ctab = false;
+  cfft_cartesian_info c_info{};
   // tensor-core spectra: float copies of the element and its GEMM B operand
   DevBuf tc_bx, tc_by, tc_bmat, tc_bmat_mirror, tc_shapes;
   bool tc_ready = false;
@@ -1499,7 +1503,8 @@ void cfft_destroy(cfft_ctx* ctx) {
                       &ctx->d_coff, &ctx->d_cos, &ctx->d_lag, &ctx->d_flag, &ctx->d_pos,
                       &ctx->d_rot, &ctx->d_zbuf, &ctx->d_fill, &ctx->d_gres, &ctx->d_ftable, &ctx->d_fest, &ctx->d_quser, &ctx->lu_a, &ctx->lu_moves,
                       &ctx->lu_nmoves, &ctx->lu_cand_v, &ctx->lu_cand_r, &ctx->lu_cand_d, &ctx->lu_bar, &ctx->lu_err, &ctx->lu_x,
-                      &ctx->lu_y, &ctx->lu_x64, &ctx->lu_r, &ctx->lu_sums, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
+                      &ctx->lu_y, &ctx->lu_x64, &ctx->lu_r, &ctx->lu_sums, &ctx->c_tab, &ctx->c_work,
+                      &ctx->c_work2, &ctx->c_im, &ctx->c_gx, &ctx->c_gy, &ctx->c_flag, &ctx->tc_bx, &ctx->tc_by, &ctx->tc_bmat,
                       &ctx->tc_bmat_mirror, &ctx->tc_shapes};
     for (DevBuf* b : bufs) b->release();
     for (auto& e : ctx->ev)
@@ -2177,4 +2182,156 @@ extern "C" cfft_status cfft_get_solve_info(const cfft_ctx* ctx, cfft_solve_info*
   if (!ctx || !info) return CFFT_ERR_ARG;
   *info = ctx->solve_info;
   return CFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The paper's 2-D Cartesian C-FFT (Section III-B-2/3, Eq. 21-24, Appendix I).
+
+namespace {
+
+template <class T>
+cfft_status cartesian_impl(cfft_ctx* ctx, int n, double rho_max, int order) {
+  cudaStream_t st = ctx->stream;
+  const int m = ctx->n_mbf, pairs = m * m, p = 2 * n;
+  const size_t es = sizeof(cpx<T>);
+  // element data in T (bases sorted by shape class, Q padded)
+  std::vector<T> hx(ctx->n_basis), hy(ctx->n_basis);
+  std::vector<cpx<T>> hq((size_t)ctx->n_basis * ctx->n_mbf_pad);
+  for (int i = 0; i < ctx->n_basis; ++i) {
+    hx[i] = (T)ctx->bx[i];
+    hy[i] = (T)ctx->by[i];
+  }
+  for (size_t i = 0; i < hq.size(); ++i) hq[i] = mk((T)ctx->q[i].real(), (T)ctx->q[i].imag());
+  CFFT_CUDA(ctx->d_bx.ensure(hx.size() * sizeof(T)), "alloc element");
+  CFFT_CUDA(ctx->d_by.ensure(hy.size() * sizeof(T)), "alloc element");
+  CFFT_CUDA(ctx->d_q.ensure(hq.size() * sizeof(cpx<T>)), "alloc element");
+  CFFT_CUDA(ctx->d_shapes.ensure(ctx->shapes.size() * sizeof(ShapeClass)), "alloc element");
+  CFFT_CUDA(cudaMemcpyAsync(ctx->d_bx.p, hx.data(), hx.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload");
+  CFFT_CUDA(cudaMemcpyAsync(ctx->d_by.p, hy.data(), hy.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload");
+  CFFT_CUDA(cudaMemcpyAsync(ctx->d_q.p, hq.data(), hq.size() * sizeof(cpx<T>), cudaMemcpyHostToDevice, st), "upload");
+  CFFT_CUDA(cudaMemcpyAsync(ctx->d_shapes.p, ctx->shapes.data(), ctx->shapes.size() * sizeof(ShapeClass),
+                            cudaMemcpyHostToDevice, st), "upload");
+  CFFT_CUDA(cudaStreamSynchronize(st), "upload");   // the staging vectors die at scope end
+  const size_t big = (size_t)pairs * p * p * es;
+  CFFT_CUDA(ctx->c_tab.ensure(big), "alloc Cartesian table");
+  CFFT_CUDA(ctx->c_work.ensure(big), "alloc Cartesian work");
+  CFFT_CUDA(ctx->c_work2.ensure(big), "alloc Cartesian work");
+  CFFT_CUDA(ctx->c_im.ensure((size_t)pairs * n * n * es), "alloc Cartesian spectrum");
+  CFFT_CUDA(ctx->c_gx.ensure((size_t)n * n * sizeof(T)), "alloc Cartesian spectrum");
+  CFFT_CUDA(ctx->c_gy.ensure((size_t)n * n * sizeof(T)), "alloc Cartesian spectrum");
+  CFFT_CUDA(ctx->c_flag.ensure(sizeof(int)), "alloc flag");
+  CartArgs<T> a{};
+  a.n = n;
+  a.n_mbf = m;
+  a.n_shape = (int)ctx->shapes.size();
+  a.q_stride = ctx->n_mbf_pad;
+  a.k_max = ctx->beta_max;
+  a.dk = 2.0 * ctx->beta_max / n;
+  a.beta_p = ctx->beta_p;
+  a.height = ctx->height;
+  a.eps_r = ctx->eps_r;
+  a.hs = ctx->hs;
+  a.k0 = ctx->k0;
+  a.shapes = ctx->d_shapes.as<ShapeClass>();
+  a.bx = ctx->d_bx.as<T>();
+  a.by = ctx->d_by.as<T>();
+  a.q = ctx->d_q.as<cpx<T>>();
+  for (auto& e : ctx->ev)
+    if (!e) CFFT_CUDA(cudaEventCreate(&e), "event");
+  CFFT_CUDA(cudaEventRecord(ctx->ev[0], st), "event");
+  cudaError_t e = cartesian_tabulate<T>(a, order, ctx->c_tab.as<cpx<T>>(), ctx->c_work.as<cpx<T>>(),
+                                        ctx->c_work2.as<cpx<T>>(), ctx->c_im.as<cpx<T>>(), ctx->c_gx.as<T>(),
+                                        ctx->c_gy.as<T>(), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "Cartesian C-FFT");
+  CFFT_CUDA(cudaEventRecord(ctx->ev[1], st), "event");
+  CFFT_CUDA(cudaMemsetAsync(ctx->c_flag.p, 0, sizeof(int), st), "flag");
+  launch_nonfinite<T>(ctx->c_tab.as<cpx<T>>(), (int64_t)pairs * p * p, ctx->c_flag.as<int>(), st);
+  int flag = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&flag, ctx->c_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+  CFFT_CUDA(cudaStreamSynchronize(st), "Cartesian C-FFT");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+  cfft_cartesian_info& in = ctx->c_info;
+  in.n_grid = n;
+  in.n_table = p;
+  in.taylor_order = order;
+  in.monomials = (order + 1) * (order + 2) / 2;
+  in.complex128 = sizeof(T) == 8;
+  in.x0 = -(double)n * kPi / (2.0 * ctx->beta_max);
+  in.step = kPi / (2.0 * ctx->beta_max);
+  in.rho_max = 0.0;
+  in.ms = ms;
+  if (flag) return fail(ctx, CFFT_ERR_NUMERIC, "non-finite value in the Cartesian table");
+  return CFFT_OK;
+}
+
+template <class T, class TO>
+cfft_status cartesian_fill_impl(cfft_ctx* ctx, int n_el, const double* pos, void* z, int64_t ld) {
+  const cfft_cartesian_info& in = ctx->c_info;
+  CFFT_CUDA(ctx->c_flag.ensure(sizeof(int)), "alloc flag");
+  CFFT_CUDA(cudaMemsetAsync(ctx->c_flag.p, 0, sizeof(int), ctx->stream), "flag");
+  cudaError_t e = cartesian_fill<T, TO>(ctx->c_tab.as<cpx<T>>(), in.n_table, ctx->n_mbf, in.x0, in.step,
+                                        in.rho_max, n_el, pos, z, ld, ctx->c_flag.as<int>(), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "Cartesian fill");
+  int flag = 0;
+  CFFT_CUDA(cudaMemcpyAsync(&flag, ctx->c_flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag");
+  CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "Cartesian fill");
+  if (flag) return fail(ctx, CFFT_ERR_ARG, "an element pair lies beyond the Cartesian table's rho_max");
+  return CFFT_OK;
+}
+
+}  // namespace
+
+extern "C" cfft_status cfft_tabulate_cartesian(cfft_ctx* ctx, int n_grid, double rho_max, int taylor_order,
+                                               cfft_precision precision) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (!ctx->has_sub || !ctx->has_el || !ctx->has_contour)
+    return fail(ctx, CFFT_ERR_STATE, "the Cartesian tabulation needs substrate, element and contour");
+  if (n_grid < 16 || n_grid > 2048 || (n_grid & (n_grid - 1)))
+    return fail(ctx, CFFT_ERR_ARG, "n_grid must be a power of two in 16..2048");
+  if (precision != CFFT_FP64 && precision != CFFT_FP32_MIXED) return fail(ctx, CFFT_ERR_ARG, "bad precision");
+  if (taylor_order < -1 || taylor_order > 40) return fail(ctx, CFFT_ERR_ARG, "taylor_order must be in -1..40");
+  const double step = kPi / (2.0 * ctx->beta_max);
+  const double x_m = (double)n_grid * kPi / (2.0 * ctx->beta_max);
+  if (!(rho_max > 0.0) || !(rho_max <= x_m - 2.0 * step))
+    return fail(ctx, CFFT_ERR_ARG, "rho_max must be > 0 and inside the table (below n_grid pi / (2 beta_max) "
+                                   "less two steps): raise n_grid");
+  const bool fp64 = precision == CFFT_FP64;
+  int order = taylor_order;
+  if (order < 0) order = auto_taylor(ctx->height * rho_max, fp64 ? 1e-13 : 1e-7);
+  if (order < 0 || order > 40)
+    return fail(ctx, CFFT_ERR_ARG, "height * rho_max too large: no Taylor order up to 40 converges");
+  if (ctx->height == 0.0) order = 0;
+  DeviceGuard g(ctx->device);
+  ctx->has_ctab = false;
+  cfft_status s = fp64 ? cartesian_impl<double>(ctx, n_grid, rho_max, order)
+                       : cartesian_impl<float>(ctx, n_grid, rho_max, order);
+  if (s != CFFT_OK) return s;
+  ctx->c_info.rho_max = rho_max;
+  ctx->has_ctab = true;
+  return CFFT_OK;
+}
+
+extern "C" cfft_status cfft_get_cartesian_table(const cfft_ctx* ctx, const void** dev_ptr,
+                                                cfft_cartesian_info* info) {
+  if (!ctx || !dev_ptr || !info) return CFFT_ERR_ARG;
+  if (!ctx->has_ctab) return CFFT_ERR_STATE;
+  *dev_ptr = ctx->c_tab.p;
+  *info = ctx->c_info;
+  return CFFT_OK;
+}
+
+extern "C" cfft_status cfft_fill_cartesian(cfft_ctx* ctx, int n_elements, const double* pos_xy, void* z_out,
+                                           int64_t ld, int out_complex128) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (!ctx->has_ctab) return fail(ctx, CFFT_ERR_STATE, "fill before cfft_tabulate_cartesian");
+  if (n_elements < 1 || n_elements > 65535 || !pos_xy || !z_out)
+    return fail(ctx, CFFT_ERR_ARG, "need 1..65535 elements and device buffers");
+  if (ld < (int64_t)n_elements * ctx->n_mbf) return fail(ctx, CFFT_ERR_ARG, "ld < n_elements * M");
+  DeviceGuard g(ctx->device);
+  const bool t64 = ctx->c_info.complex128 != 0;
+  if (t64 && out_complex128) return cartesian_fill_impl<double, double>(ctx, n_elements, pos_xy, z_out, ld);
+  if (t64) return cartesian_fill_impl<double, float>(ctx, n_elements, pos_xy, z_out, ld);
+  if (out_complex128) return cartesian_fill_impl<float, double>(ctx, n_elements, pos_xy, z_out, ld);
+  return cartesian_fill_impl<float, float>(ctx, n_elements, pos_xy, z_out, ld);
 }

@@ -393,6 +393,26 @@ cudaError_t launch_residual_outer(const void* r, const void* v, int n, void* g, 
 template <class T>
 cudaError_t launch_fill_estimate(const void* table, int64_t n_series, int n_rho, int q_max, int taps,
                                  double fac_c, double fac_e, double4* out, cudaStream_t s);
+// the 2-D Cartesian C-FFT (k_cartesian.cu): N x N spectral samples on [-k_max, k_max)^2
+// (dk = 2 k_max / N), the contour (beta_p, height), the substrate and the element
+template <class T>
+struct CartArgs {
+  int n, n_mbf, n_shape, q_stride;
+  double k_max, dk, beta_p, height, eps_r, hs, k0;
+  const ShapeClass* shapes;
+  const T* bx;
+  const T* by;
+  const cpx<T>* q;   // [n_basis][q_stride], bases sorted by shape class
+};
+// the refined table [pairs][2N][2N] (dx-major) up to Taylor order `order`; work, work2:
+// [pairs][2N][2N]; im: [pairs][N][N]; gx, gy: [N][N]
+template <class T>
+cudaError_t cartesian_tabulate(const CartArgs<T>& a, int order, cpx<T>* table, cpx<T>* work, cpx<T>* work2,
+                               cpx<T>* im, T* gx, T* gy, cudaStream_t s);
+template <class T, class TO>
+cudaError_t cartesian_fill(const cpx<T>* table, int p, int m, double x0, double step, double rho_max, int n_el,
+                           const double* pos, void* z, int64_t ld, int* err, cudaStream_t s);
+
 // dense LU of the reduced system (k_solve.cu): device work arrays of one factorization
 struct LuWork {
   int2* moves;         // [panels][2 * panel width] row moves (source, destination)

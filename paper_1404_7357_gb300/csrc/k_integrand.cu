@@ -21,35 +21,13 @@
 //   Y[cls][pair][q][j] = H_ab,q(beta_j) beta_c,j w_j
 // which is the contour integrand of the one-dimensional transform in beta.
 #include "cfft_common.cuh"
+#include "shape_factor.cuh"
 
 namespace cfft {
 
 namespace {
 
 constexpr int kThreads = 256;
-
-template <class T>
-__device__ __forceinline__ cpx<T> shape_factor(const ShapeClass& c, cpx<T> kx, cpx<T> ky) {
-  if (c.kind == 0) {
-    const T a = (T)c.p1, w = (T)c.p2;
-    cpx<T> ku = c.dir == 0 ? kx : ky;
-    cpx<T> kv = c.dir == 0 ? ky : kx;
-    cpx<T> s1 = csinc(mk(ku.re * a * (T)0.5, ku.im * a * (T)0.5));
-    cpx<T> s2 = csinc(mk(kv.re * w * (T)0.5, kv.im * w * (T)0.5));
-    return a * (s1 * s1 * s2);
-  }
-  // cosine strip along x: cos(u) / (pi^2/4 - u^2) = sinc(pi/2 - u) / (pi/2 + u),
-  // with u = kx L/2 mirrored into Re u >= 0 (the factor is even in u)
-  const T len = (T)c.p1, wid = (T)c.p2;
-  cpx<T> u = mk(kx.re * len * (T)0.5, kx.im * len * (T)0.5);
-  if (u.re < (T)0) u = mk(-u.re, -u.im);
-  const T hp = (T)1.5707963267948966;
-  cpx<T> num = csinc(mk(hp - u.re, -u.im));
-  cpx<T> along = cdiv(num, mk(hp + u.re, u.im));
-  along = ((T)1.5707963267948966 * len) * along;  // (pi L / 2)
-  cpx<T> across = csinc(mk(ky.re * wid * (T)0.5, ky.im * wid * (T)0.5));
-  return along * across;
-}
 
 // M is the MBF count padded to a compiled size (padding columns of Q are zero);
 // a.n_mbf is the real count.  Pairs are processed pc at a time through hbuf.

@@ -66,7 +66,8 @@ def _header_struct(name):
 
 
 @pytest.mark.parametrize("cname,pyname", [("cfft_info", "Info"), ("cfft_batch_info", "BatchInfo"),
-                                          ("cfft_batch_item", "BatchItem"), ("cfft_solve_info", "SolveInfo")])
+                                          ("cfft_batch_item", "BatchItem"), ("cfft_solve_info", "SolveInfo"),
+                                          ("cfft_cartesian_info", "CartesianInfo")])
 def test_struct_layouts_match_header(lib, cname, pyname):
     """The ctypes mirrors of the ABI structs list the header's fields in its order with the
     same C types (a field added on one side only would shift every later one)."""
