@@ -144,6 +144,22 @@ const char* cfft_last_error(const cfft_ctx* ctx);
  * k0 > 0.  Invalidates any contour and table. */
 cfft_status cfft_set_substrate(cfft_ctx* ctx, double eps_r, double h, double k0);
 
+/* Green's function of the tabulation (Sections II and III-A: the paper tabulates Z^l,
+ * the layered-medium part from which an effective homogeneous medium and its image
+ * through the ground plane have been extracted, and treats that extracted part, Z^h, in
+ * the space domain).  extract = 0 (default): the full grounded-slab dyadic; extract = 1:
+ * the slab dyadic minus the dyadic of a current sheet in a homogeneous medium of
+ * permittivity eps_eff with the ground plane h below it (the matched line of the medium
+ * in parallel with its shorted line: Z_TE = k0 Z0 (1 - e^{-2j kz h}) / (2 kz),
+ * Z_TM = Z0 kz (1 - e^{-2j kz h}) / (2 k0 eps_eff), kz = -j sqrt(beta^2 - eps_eff k0^2)),
+ * so that the tables, fills and the Cartesian tabulation hold Z^l.  eps_eff <= 0 takes
+ * (eps_r + 1) / 2, which removes the slab's large-beta charge term; the substrate
+ * derivatives then include d eps_eff / d eps_r = 1/2.  For eps_r = 1 the extracted part
+ * is the whole slab (free space above a ground plane) and Z^l vanishes.  The space-domain
+ * evaluation of Z^h (multipoles in the paper) is not part of this library.  Invalidates
+ * the table.  CFFT_ERR_ARG for extract other than 0 or 1. */
+cfft_status cfft_set_green_extraction(cfft_ctx* ctx, int extract, double eps_eff);
+
 /* Element made of one x-directed cosine strip dipole of length `length` and
  * width `width` centred at the origin (one MBF, M = 1).  Its spectrum is
  * analytic (Section III-A).  Invalidates contour-independent caches. */

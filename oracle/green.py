@@ -18,12 +18,14 @@ with an exp(+j omega t) time convention (the paper's ``i`` is read as ``j``):
 with cos = cos(k1 h), sin = sin(k1 h), beta^2 = kx^2 + ky^2 (no conjugation,
 so the same expressions continue analytically to complex kx, ky as Eq. 18
 requires).  The surface-wave poles are the zeros of Te and Tm; the paper's
-contour (Eq. 8) passes above them.  No homogeneous-medium or image term is
-extracted (the paper's Section II split is not reproduced; see the design
-notes for this reading).
+contour (Eq. 8) passes above them.  ``dyadic_green`` extracts nothing;
+``layered_remainder`` subtracts an effective homogeneous medium and its image
+through the ground plane (``extracted_part``), the split of Section II.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 """
+import math
+
 import numpy as np
 
 # Free-space wave impedance (ohm), sqrt(mu0 / eps0).
@@ -84,3 +86,33 @@ def identity_green(kx, ky, *unused):
     """Unit dyadic (test mode: isolates the transform from the substrate)."""
     one = np.ones(np.broadcast(np.asarray(kx), np.asarray(ky)).shape, dtype=np.complex128)
     return one, 0.0 * one, one
+
+
+def extracted_part(kx, ky, eps_eff, h, k0):
+    """The effective homogeneous medium and its image through the ground plane (the part
+    of the slab Green's function that Sections II and III-A assign to Z^h).  Reading: a
+    current sheet in a homogeneous medium of permittivity eps_eff (mu_0), ground plane h
+    below: the medium's matched line in parallel with its line shorted at distance h,
+      Z = Z_c (1 - exp(-2 j kz h)) / 2,  Z_c^TE = k0 Z0 / kz,  Z_c^TM = Z0 kz / (k0 eps_eff),
+    kz = -j sqrt(beta^2 - eps_eff k0^2), in the dyadic -Z_TE I - (Z_TM - Z_TE) k k^T / beta^2.
+    Returns (Gxx, Gxy, Gyy)."""
+    kx = np.asarray(kx, dtype=np.complex128)
+    ky = np.asarray(ky, dtype=np.complex128)
+    beta_sq = kx * kx + ky * ky
+    kz = kz_free(beta_sq, math.sqrt(eps_eff) * k0)
+    f = 1.0 - np.exp(-2j * kz * h)
+    z_te = k0 * Z0 * f / (2.0 * kz)
+    # (Z_TM - Z_TE) / beta^2 with kz^2 - eps_eff k0^2 = -beta^2: finite at beta = 0
+    d = -Z0 * f / (2.0 * k0 * eps_eff * kz)
+    return -z_te - d * kx * kx, -d * kx * ky, -z_te - d * ky * ky
+
+
+def layered_remainder(eps_eff=None):
+    """Green's function of Z^l (Section II): the slab's dyadic minus ``extracted_part``,
+    with eps_eff = (eps_r + 1) / 2 unless given.  Same call signature as dyadic_green."""
+    def green(kx, ky, eps_r, h, k0):
+        e = 0.5 * (eps_r + 1.0) if eps_eff is None else eps_eff
+        gxx, gxy, gyy = dyadic_green(kx, ky, eps_r, h, k0)
+        exx, exy, eyy = extracted_part(kx, ky, e, h, k0)
+        return gxx - exx, gxy - exy, gyy - eyy
+    return green

@@ -31,7 +31,8 @@ EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate
            "cfft_get_batch_info", "cfft_mbf_spectra", "cfft_selftest_bounded_wait", "cfft_load_table",
            "cfft_fill_backward_residual", "cfft_test_fail_allocation", "cfft_measure_peak",
            "cfft_reduced_excitation", "cfft_port_excitation", "cfft_port_currents", "cfft_solve_reduced",
-           "cfft_get_solve_info", "cfft_tabulate_cartesian", "cfft_get_cartesian_table", "cfft_fill_cartesian"]
+           "cfft_get_solve_info", "cfft_tabulate_cartesian", "cfft_get_cartesian_table", "cfft_fill_cartesian",
+           "cfft_set_green_extraction"]
 
 
 class CfftLibraryError(ImportError):
@@ -125,6 +126,7 @@ def _load():
         "cfft_tabulate_cartesian": ([P, I, D, I, I], I),
         "cfft_get_cartesian_table": ([P, ctypes.POINTER(P), ctypes.POINTER(CartesianInfo)], I),
         "cfft_fill_cartesian": ([P, I, P, P, L, I], I),
+        "cfft_set_green_extraction": ([P, I, D], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +187,11 @@ class Context:
     # ---- problem description
     def set_substrate(self, eps_r, h, k0):
         self._check(_lib.cfft_set_substrate(self._h, eps_r, h, k0))
+
+    def set_green_extraction(self, extract=True, eps_eff=0.0):
+        """Tabulate Z^l: the slab's Green's function minus an effective homogeneous medium
+        (eps_eff, default (eps_r + 1) / 2) and its image through the ground plane."""
+        self._check(_lib.cfft_set_green_extraction(self._h, int(bool(extract)), float(eps_eff)))
 
     def set_mbf_spectra_strip(self, length, width):
         self._check(_lib.cfft_set_mbf_spectra_strip(self._h, length, width))

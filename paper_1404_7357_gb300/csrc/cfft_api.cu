@@ -77,6 +77,10 @@ struct cfft_ctx {
   // substrate
   bool has_sub = false;
   double eps_r = 1, hs = 0, k0 = 1;
+  // Green's function: 1 = the effective homogeneous medium and its image subtracted
+  // (eps_eff <= 0: (eps_r + 1) / 2)
+  int extract = 0;
+  double eps_eff_set = 0.0;
   // element (bases sorted by shape class; Q padded to n_mbf_pad columns)
   bool has_el = false;
   int n_basis = 0, n_mbf = 0, n_mbf_pad = 0;
@@ -211,6 +215,14 @@ int alpha_nodes(double beta_abs_max, double rho, int q_max, double margin, doubl
 
 double alpha_cbrt_coef(bool fp64) { return fp64 ? 4.0 : 2.0; }
 
+// the extraction fields of a contour for substrate permittivity eps_r
+void set_extraction(const cfft_ctx* ctx, double eps_r, int* extract, double* eps_eff, double* deps_eff) {
+  *extract = ctx->extract;
+  const bool automatic = !(ctx->eps_eff_set > 0.0);
+  *eps_eff = automatic ? 0.5 * (eps_r + 1.0) : ctx->eps_eff_set;
+  *deps_eff = automatic ? 0.5 : 0.0;
+}
+
 // One tabulation into `dst` on n_rho points rho_r = r rho_max / (n_rho - 1).  primary: the
 // table of cfft_tabulate_reactions (its diagnostics go to ctx->info); otherwise the table
 // that the fill interpolates when the tabulated grid misses the fill's target.
@@ -330,6 +342,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
 
   // ---- a1: contour + Green's function (float64)
   ContourArgs ca{n, ctx->beta_max, ctx->beta_p, ctx->height, step, ctx->eps_r, ctx->hs, ctx->k0};
+  set_extraction(ctx, ctx->eps_r, &ca.extract, &ca.eps_eff, &ca.deps_eff);
   ContourData cd{ctx->beta_c.as<double2>(), ctx->weight.as<double2>(), ctx->bw.as<double2>(),
                  ctx->bi_rel.as<double>(), reinterpret_cast<float*>(ctx->bi_rel.as<double>() + n),
                  ctx->green_p.as<double2>(), ctx->green_r.as<double2>(),
@@ -1111,6 +1124,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         const cfft_batch_item& it = items[i];
         const BatchItemPlan& p = ip[i];
         hca[i] = ContourArgs{it.n, it.beta_max, it.beta_p, it.height, p.step, it.eps_r, it.h, it.k0};
+        set_extraction(ctx, it.eps_r, &hca[i].extract, &hca[i].eps_eff, &hca[i].deps_eff);
         hcd[i] = ContourData{c_beta + node_off, c_w + node_off, c_bw + node_off, c_bi + node_off,
                              c_bif + node_off, c_gp + node_off, c_gr + node_off,
                              nullptr, nullptr, nullptr, nullptr};
@@ -1538,6 +1552,16 @@ cfft_status cfft_set_substrate(cfft_ctx* ctx, double eps_r, double h, double k0)
   ctx->k0 = k0;
   ctx->has_sub = true;
   ctx->has_contour = false;
+  ctx->has_table = false;
+  return CFFT_OK;
+}
+
+cfft_status cfft_set_green_extraction(cfft_ctx* ctx, int extract, double eps_eff) {
+  if (!ctx) return CFFT_ERR_ARG;
+  if (extract != 0 && extract != 1) return fail(ctx, CFFT_ERR_ARG, "extract must be 0 or 1");
+  if (!std::isfinite(eps_eff)) return fail(ctx, CFFT_ERR_ARG, "eps_eff must be finite");
+  ctx->extract = extract;
+  ctx->eps_eff_set = eps_eff;
   ctx->has_table = false;
   return CFFT_OK;
 }
@@ -2232,6 +2256,10 @@ cfft_status cartesian_impl(cfft_ctx* ctx, int n, double rho_max, int order) {
   a.eps_r = ctx->eps_r;
   a.hs = ctx->hs;
   a.k0 = ctx->k0;
+  {
+    double deps = 0.0;
+    set_extraction(ctx, ctx->eps_r, &a.extract, &a.eps_eff, &deps);
+  }
   a.shapes = ctx->d_shapes.as<ShapeClass>();
   a.bx = ctx->d_bx.as<T>();
   a.by = ctx->d_by.as<T>();

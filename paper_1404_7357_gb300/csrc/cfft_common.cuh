@@ -156,6 +156,8 @@ struct ContourArgs {
   int n;
   double beta_max, beta_p, height, step;  // step = beta_max / n
   double eps_r, hs, k0;
+  int extract;                            // 1: subtract the homogeneous medium and its image
+  double eps_eff, deps_eff;               // its permittivity and d eps_eff / d eps_r
 };
 
 // per-node contour data written by the contour kernel (float64 throughout)
@@ -399,6 +401,8 @@ template <class T>
 struct CartArgs {
   int n, n_mbf, n_shape, q_stride;
   double k_max, dk, beta_p, height, eps_r, hs, k0;
+  int extract;
+  double eps_eff;
   const ShapeClass* shapes;
   const T* bx;
   const T* by;

@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "cfft_common.cuh"
+#include "green_ext.cuh"
 #include "shape_factor.cuh"
 
 namespace cfft {
@@ -83,6 +84,11 @@ __global__ void cart_spectrum_kernel(CartArgs<T> a, cpx<T>* im, T* gx, T* gy) {
   gy[e] = (T)(gamma * ky * ih);
   cpx<double> p, rb2;
   slab_green(mk(br, bi), a.eps_r, a.hs, a.k0, &p, &rb2);
+  if (a.extract) {
+    const GreenExt ge = ext_green(mk(br, bi), a.eps_eff, 0.0, a.hs, a.k0, false);
+    p = p - ge.p;
+    rb2 = rb2 - ge.rb2;
+  }
   const double ux = br > 0.0 ? kx / br : 1.0, uy = br > 0.0 ? ky / br : 0.0;
   // MBF spectra at k_c = k (1 + i gamma): both sides, x and y components
   const cpx<T> kcx = mk((T)kx, (T)(gamma * kx)), kcy = mk((T)ky, (T)(gamma * ky));

@@ -14,6 +14,7 @@
 // Everything here is float64: the denominators near the surface-wave poles and
 // the branch-point square roots are where float32 loses the most digits.
 #include "cfft_common.cuh"
+#include "green_ext.cuh"
 
 namespace cfft {
 
@@ -47,6 +48,11 @@ __device__ __forceinline__ void contour_node(const ContourArgs& a, const Contour
   cpx<double> cfac = cdiv(mk(0.0, -kEta0 / a.k0) * sn, te * tm);
   cpx<double> p = cfac * ((a.eps_r * k02) * (k2 * cs) + j1 * (k02 * (k1 * sn)));
   cpx<double> r = cfac * (k2 * cs + j1 * (k1 * sn));
+  GreenExt ge{};
+  if (a.extract) {
+    ge = ext_green(bc, a.eps_eff, a.deps_eff, a.hs, a.k0, d.dp_eps != nullptr);
+    p = p - ge.p;
+  }
   d.beta_c[j] = make_double2(bc.re, bc.im);
   d.weight[j] = make_double2(w.re, w.im);
   cpx<double> bw = bc * w;
@@ -55,6 +61,7 @@ __device__ __forceinline__ void contour_node(const ContourArgs& a, const Contour
   if (d.bi_rel_f) d.bi_rel_f[j] = (float)d.bi_rel[j];
   d.green_p[j] = make_double2(p.re, p.im);
   cpx<double> rb2 = r * b2;  // R beta_c^2: the k k^T term is R beta_c^2 u u^T
+  if (a.extract) rb2 = rb2 - ge.rb2;
   d.green_r[j] = make_double2(rb2.re, rb2.im);
   if (d.dp_eps) {
     // derivatives with respect to eps_r (dk1 = k0^2 / (2 k1)) and h (k2 does not
@@ -80,6 +87,10 @@ __device__ __forceinline__ void contour_node(const ContourArgs& a, const Contour
       cpx<double> dnr = k2 * dc + j1 * (dk1 * sn + k1 * ds);
       cpx<double> dp = dcf * np + cfac * dnp;
       cpx<double> dr = (dcf * nr + cfac * dnr) * b2;
+      if (a.extract) {
+        dp = dp - ge.dp[which];
+        dr = dr - ge.drb2[which];
+      }
       (eps ? d.dp_eps : d.dp_h)[j] = make_double2(dp.re, dp.im);
       (eps ? d.dr_eps : d.dr_h)[j] = make_double2(dr.re, dr.im);
     }

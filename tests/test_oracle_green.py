@@ -172,3 +172,57 @@ def test_dyadic_matches_transmission_line_model(eps_r, h):
     scale = np.maximum(np.abs(ref[0]), np.abs(ref[2]))
     for g, r in zip(got, ref):
         assert np.all(np.abs(g - r) <= 1e-11 * scale)
+
+
+def test_remainder_vanishes_for_an_air_slab():
+    """With eps_r = 1 the grounded slab is free space above a ground plane, which is exactly
+    the extracted homogeneous medium (eps_eff = 1) and its image: Z^l's Green's function is
+    zero at real and complex beta, in every component."""
+    from oracle import green as og
+    k0 = 2 * np.pi
+    rem = og.layered_remainder()
+    for b in (0.3, 1.5, 3.0, 6.5, 10.0, 40.0):
+        for bi in (0.0, 0.2):
+            kx, ky = (b + 1j * bi) * 0.6, (b + 1j * bi) * 0.8
+            full = og.dyadic_green(kx, ky, 1.0, 0.05, k0)
+            part = rem(kx, ky, 1.0, 0.05, k0)
+            scale = max(abs(full[0]), abs(full[1]), abs(full[2]))
+            assert max(abs(part[0]), abs(part[1]), abs(part[2])) < 1e-13 * scale
+
+
+def test_remainder_loses_the_growing_charge_term():
+    """On a dielectric slab the full dyadic grows like beta at large beta (the charge term),
+    the remainder after extracting the eps_eff = (eps_r + 1)/2 medium and its image falls
+    off; a flipped image sign breaks the air-slab identity."""
+    from oracle import green as og
+    k0 = 2 * np.pi
+    rem = og.layered_remainder()
+    g100 = og.dyadic_green(60.0, 80.0, 4.4, 0.03, k0)
+    g400 = og.dyadic_green(240.0, 320.0, 4.4, 0.03, k0)
+    r100 = rem(60.0, 80.0, 4.4, 0.03, k0)
+    r400 = rem(240.0, 320.0, 4.4, 0.03, k0)
+    for c in range(3):
+        assert abs(g400[c]) / abs(g100[c]) > 3.0
+        assert abs(r400[c]) / abs(r100[c]) < 0.3
+        assert abs(r400[c]) < 1e-3 * abs(g400[c])
+    # planted mistake: the image added instead of subtracted
+    real = og.extracted_part
+
+    def wrong_image(kx, ky, eps_eff, h, k0_):
+        kx = np.asarray(kx, dtype=np.complex128)
+        ky = np.asarray(ky, dtype=np.complex128)
+        beta_sq = kx * kx + ky * ky
+        kz = og.kz_free(beta_sq, np.sqrt(eps_eff) * k0_)
+        f = 1.0 + np.exp(-2j * kz * h)
+        z_te = k0_ * og.Z0 * f / (2.0 * kz)
+        z_tm = og.Z0 * kz * f / (2.0 * k0_ * eps_eff)
+        d = (z_tm - z_te) / beta_sq
+        return -z_te - d * kx * kx, -d * kx * ky, -z_te - d * ky * ky
+
+    og.extracted_part = wrong_image
+    try:
+        part = og.layered_remainder()(1.8, 2.4, 1.0, 0.05, k0)
+        full = og.dyadic_green(1.8, 2.4, 1.0, 0.05, k0)
+        assert abs(part[0]) > 0.1 * abs(full[0])
+    finally:
+        og.extracted_part = real
