@@ -468,7 +468,10 @@ def bench_batch(torch, cfft, args, dev):
                        "contours n in [%d, %d] (mean %.0f); heights min(6 spacings, 3/rho_max); M=4; "
                        "|q|<=16; %d rho points to %g lambda0; FP32-mixed; one CUDA graph"
                        % (min(ns), max(ns), np.mean(ns), n_rho, rho_max),
-           "info": info}
+           "first_wave_stage_ms": {k: info["ms_" + k] for k in ("integrand", "fft", "backproject")},
+           "first_wave_note": "stage times of the first wave (of %d) from the tuning launches; the whole "
+                              "sweep is ms_graph_replay" % info["waves"],
+           "info": {k: v for k, v in info.items() if not k.startswith("ms_")}}
     return res, sweep_sample(out, items, q_max, rho_max, n_rho, el)
 
 

@@ -217,7 +217,9 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
     __syncthreads();
   }
   if (!ok) {
+    // the panel stopped (a zero pivot or a wait that ran out): no row moves for it
     if (tid == 0 && s_fail) atomicOr(p.err, 2);
+    if (tid == 0 && g == 0) *p.n_moves = 0;
     return;
   }
   for (int e = tid; e < nr * kb; e += blockDim.x)
@@ -257,16 +259,20 @@ __global__ void __launch_bounds__(256) lu_moves_kernel(cpx<T>* a, int64_t ld, in
                                                        const int* n_moves) {
   __shared__ cpx<T> buf[2 * kNb][16];
   __shared__ int2 mv[2 * kNb];
-  const int nm = min(*n_moves, 2 * kNb);
+  const int nm = max(0, min(*n_moves, 2 * kNb));
   const int tid = threadIdx.x, cl = tid & 15, mr = tid >> 4;
   const int col = blockIdx.x * 16 + cl;
-  for (int m = tid; m < nm; m += blockDim.x) mv[m] = moves[m];
+  // a move outside the matrix (none is written; checked all the same) is dropped
+  for (int m = tid; m < nm; m += blockDim.x) {
+    const int2 v = moves[m];
+    mv[m] = (v.x >= 0 && v.x < n_cols && v.y >= 0 && v.y < n_cols) ? v : make_int2(-1, -1);
+  }
   __syncthreads();
   for (int m = mr; m < nm; m += 16)
-    if (col < n_cols) buf[m][cl] = a[(int64_t)mv[m].x * ld + col];
+    if (col < n_cols && mv[m].x >= 0) buf[m][cl] = a[(int64_t)mv[m].x * ld + col];
   __syncthreads();
   for (int m = mr; m < nm; m += 16)
-    if (col < n_cols) a[(int64_t)mv[m].y * ld + col] = buf[m][cl];
+    if (col < n_cols && mv[m].x >= 0) a[(int64_t)mv[m].y * ld + col] = buf[m][cl];
 }
 
 // Column-oriented substitution with one warp: the right-hand side's entries of rows
@@ -375,14 +381,17 @@ __global__ void __launch_bounds__(256) lu_gemm_kernel(cpx<T>* a, int64_t ld, int
 
 // every panel's row moves on the right-hand side, in panel order (one block)
 template <class T>
-__global__ void lu_vector_moves_kernel(cpx<T>* x, int n_panels, const int2* moves, const int* n_moves) {
+__global__ void lu_vector_moves_kernel(cpx<T>* x, int n, int n_panels, const int2* moves, const int* n_moves) {
   __shared__ cpx<T> buf[2 * kNb];
   for (int pnl = 0; pnl < n_panels; ++pnl) {
-    const int nm = min(n_moves[pnl], 2 * kNb);
+    const int nm = max(0, min(n_moves[pnl], 2 * kNb));
     const int2* mv = moves + (size_t)pnl * 2 * kNb;
-    for (int m = threadIdx.x; m < nm; m += blockDim.x) buf[m] = x[mv[m].x];
+    auto valid = [&](int2 v) { return v.x >= 0 && v.x < n && v.y >= 0 && v.y < n; };
+    for (int m = threadIdx.x; m < nm; m += blockDim.x)
+      if (valid(mv[m])) buf[m] = x[mv[m].x];
     __syncthreads();
-    for (int m = threadIdx.x; m < nm; m += blockDim.x) x[mv[m].y] = buf[m];
+    for (int m = threadIdx.x; m < nm; m += blockDim.x)
+      if (valid(mv[m])) x[mv[m].y] = buf[m];
     __syncthreads();
   }
 }
@@ -608,6 +617,9 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
+  // no row moves until a panel records its own (a panel that stops early records none)
+  e = cudaMemsetAsync(w.n_moves, 0, (size_t)n_panels * sizeof(int), s);
+  if (e != cudaSuccess) return e;
   const size_t trsm_smem = (size_t)kNb * (kNb + 1 + 32) * sizeof(cpx<T>);
   const size_t gemm_smem = (size_t)kNb * (65 + 64) * sizeof(cpx<T>);
   // the most shared memory any panel's CTAs take (the grid shrinks in steps as the rows do)
@@ -670,7 +682,7 @@ cudaError_t lu_solve(const cpx<T>* a, int64_t ld, int n, const LuWork& w, cpx<T>
   if ((e = cudaFuncSetAttribute(lu_backward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)) !=
       cudaSuccess)
     return e;
-  lu_vector_moves_kernel<T><<<1, 128, 0, s>>>(x, n_panels, w.moves, w.n_moves);
+  lu_vector_moves_kernel<T><<<1, 128, 0, s>>>(x, n, n_panels, w.moves, w.n_moves);
   for (int pnl = 0; pnl < n_panels; ++pnl) {
     const int k = pnl * kNb, kb = std::min(kNb, n - k);
     lu_forward_kernel<T><<<grid_for(n - k - kb, 8, 2 * sms), 256, dsm, s>>>(a, ld, n, k, kb, x, y);
