@@ -111,7 +111,18 @@ typedef enum {
  *   FILL_REFINE  grid of the table the fill interpolates.  Default (< 1):
  *                automatic, see cfft_fill_reduced_matrix; a value k >= 1
  *                fixes it at k times finer than the tabulated grid, without
- *                the accuracy check (k = 1: the tabulated table as it is) */
+ *                the accuracy check (k = 1: the tabulated table as it is)
+ *   CONTOUR_SERIES  the series of the contour factor exp(beta_I s) that
+ *                separates the transform into FFTs.  1: the Taylor series of
+ *                Eq. 22 (term n: weight (beta_I/H)^n, coefficient
+ *                (H s)^n / n!).  2: its Chebyshev series about the middle
+ *                of the range of beta_I / H: exp(H s b) = exp(a) exp(a z),
+ *                a = H s / 2, z = 2 b - 1, exp(a z) = I_0(a) + 2 sum_m
+ *                I_m(a) T_m(z); the nodes beyond beta_p (b = 0) form one
+ *                extra FFT with weight 1.  Default (<= 0): an explicit
+ *                taylor_order keeps the Taylor series; the automatic order
+ *                takes the series with fewer FFTs for the precision's
+ *                remainder bound (Taylor on a tie) */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -125,7 +136,8 @@ typedef enum {
   CFFT_OPT_SPECTRA_SIMT = 9,
   CFFT_OPT_BP_SIMT = 10,
   CFFT_OPT_FILL_SIMT = 11,
-  CFFT_OPT_FILL_REFINE = 12
+  CFFT_OPT_FILL_REFINE = 12,
+  CFFT_OPT_CONTOUR_SERIES = 13
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -187,8 +199,9 @@ cfft_status cfft_set_mbf_spectra(cfft_ctx* ctx, int n_basis, const double* cente
  * beta_max bounds the spectral integration (5 k_d in Section III-A);
  * beta_p must exceed every surface-wave pole (> k0 sqrt(eps_r)).
  * taylor_order is the highest power N_t kept in the Taylor expansion of the
- * contour factor (Eq. 22); -1 chooses it from the precision's tolerance and
- * the largest rho of the table at tabulation time.
+ * contour factor (Eq. 22); -1 chooses the series (see CONTOUR_SERIES) and its
+ * order from the precision's tolerance and the largest rho of the table at
+ * tabulation time.
  * Accuracy: the samples enter the transform weighted by up to
  * exp(height * rho_max), so their rounding grows by that factor; for the
  * 1e-5 target of CFFT_FP32_MIXED keep height * rho_max <= 3 (and height a few
@@ -384,7 +397,10 @@ cfft_status cfft_fill_backward_residual(cfft_ctx* ctx, int n_elements, const dou
                                         const int* rot, const void* v, const void* resid,
                                         int complex128, double* grad_pos, double* grad_eps_h);
 
-/* Diagnostics of the last tabulation (host values): taylor order used,
+/* Diagnostics of the last tabulation (host values): highest term index of
+ * the contour-factor series used (taylor_order; contour_series 0: Taylor,
+ * 1: Chebyshev; the FFTs per (pair, harmonic) are taylor_order + 1, or + 2
+ * for Chebyshev),
  * n_alpha, sigma, FFT length, sub-FFT length, grid half-width K, back-
  * projection taps, fill taps, series count, the device time of each stage in
  * milliseconds (contour, integrand, fft, backproject; CUDA events on the
@@ -421,6 +437,7 @@ typedef struct {
   double fill_err_est;
   int fill_refine, fill_n_rho;
   double tc_flops_integrand, tc_flops_backproject;
+  int contour_series;
 } cfft_info;
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
 

@@ -93,8 +93,8 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic) and the options the last table was made with
-  double opt[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double tab_opt[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double tab_opt[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -200,6 +200,58 @@ int auto_taylor(double x, double tol) {
   return -1;
 }
 
+// modified Bessel function I_m(a), a >= 0, by its power series
+double bessel_i_host(int m, double a) {
+  const double half = 0.5 * a;
+  double t = 1.0;
+  for (int i = 1; i <= m; ++i) t *= half / i;
+  double sum = t;
+  for (int i = 1; i < 200; ++i) {
+    t *= half * half / ((double)i * (i + m));
+    sum += t;
+    if (t <= 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+// smallest degree N of the Chebyshev series of the contour factor (exp(H s b) =
+// exp(a) exp(a z), a = H s / 2, z = 2 b - 1) whose remainder bound
+// exp(a) * 2 sum_{m > N} I_m(a) at a = x / 2 is <= tol, or -1 beyond degree 64
+int auto_chebyshev(double x, double tol) {
+  if (x <= 0) return 0;
+  const double a = 0.5 * x;
+  for (int nc = 0; nc <= 64; ++nc) {
+    double tail = 0.0;
+    for (int m = nc + 1; m <= nc + 60; ++m) {
+      const double im = bessel_i_host(m, a);
+      tail += im;
+      if (im <= 1e-3 * tail) break;
+    }
+    if (std::exp(a) * 2.0 * tail <= tol) return nc;
+  }
+  return -1;
+}
+
+// the contour-factor series of a tabulation: {series, highest term index}.  An explicit
+// order keeps the paper's Taylor series (Eq. 22) unless the option asks for Chebyshev;
+// the automatic choice takes the series with fewer transforms (Taylor: N + 1; Chebyshev:
+// N + 2, one of them the nodes beyond the active prefix), Taylor on a tie
+struct SeriesChoice {
+  int series, order;
+};
+
+SeriesChoice choose_series(double x, bool fp64, int order_req, double opt) {
+  const double tol = fp64 ? 1e-13 : 1e-7;
+  const int mode = opt > 0 ? (int)opt : 0;   // 0 automatic, 1 Taylor, 2 Chebyshev
+  if (order_req >= 0) return {mode == 2 ? 1 : 0, order_req};
+  const int nt = auto_taylor(x, tol);
+  if (mode == 1) return {0, nt};
+  const int nc = auto_chebyshev(x, tol);
+  if (mode == 2) return {1, nc};
+  if (nc >= 0 && (nt < 0 || nc + 2 < nt + 1)) return {1, nc};
+  return {0, nt};
+}
+
 // angular nodes of the back-projection for the largest rho of a chunk.  With z = |beta| rho
 // the integrand g(rho cos alpha) holds angular harmonics up to about z, and the midpoint
 // rule's error is the first aliased one, J_n(z) with n ~ 2 N - |q|.  Above its order J_n
@@ -261,10 +313,12 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
                 "back-projection taps must be one of 4,6,8,10,12,16,20,24; fill taps even, 2..16");
   if (n_rho < 2 * fill_taps) return fail(ctx, CFFT_ERR_ARG, "n_rho must be >= 2 * fill taps");
   double margin = ctx->opt[CFFT_OPT_ALPHA_MARGIN] > 0 ? ctx->opt[CFFT_OPT_ALPHA_MARGIN] : 24.0;
-  int taylor = ctx->taylor_req;
-  if (taylor < 0) taylor = auto_taylor(ctx->height * rho_max, fp64 ? 1e-13 : 1e-7);
+  const SeriesChoice sc = choose_series(ctx->height * rho_max, fp64, ctx->taylor_req,
+                                        ctx->opt[CFFT_OPT_CONTOUR_SERIES]);
+  const int taylor = sc.order;
   if (taylor < 0)
-    return fail(ctx, CFFT_ERR_ARG, "height * rho_max too large: no Taylor order up to 64 converges");
+    return fail(ctx, CFFT_ERR_ARG, "height * rho_max too large: no series order up to 64 converges");
+  const int n_terms = taylor + (sc.series == 1 ? 2 : 1);
   const int64_t P = (int64_t)sigma * n;
   const double ds = 2.0 * kPi / ((double)P * step);
   const int K = (int)std::ceil(rho_max / ds) + bp_taps / 2 + 2;
@@ -427,6 +481,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   fa.fft_len = P;
   fa.grid_half = K;
   fa.taylor = taylor;
+  fa.expansion = sc.series;
   fa.n_active = n_active;
   fa.sigma = sigma;
   fa.ds_height = ds * ctx->height;
@@ -579,6 +634,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   cfft_info scratch_info{};
   cfft_info& in = primary ? ctx->info : scratch_info;
   in.taylor_order = taylor;
+  in.contour_series = sc.series;
   in.n_alpha = n_alpha;
   in.sigma = sigma;
   in.fft_len = (int)P;
@@ -603,7 +659,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   in.launches = launches;
   in.n_basis = ctx->n_basis;
   in.work_points = (double)n * n_alpha;
-  in.work_subffts = (double)series * D * (taylor + 1);
+  in.work_subffts = (double)series * D * n_terms;
   in.work_bp_nodes = bp_nodes;
   in.spectra_tc = in_tc ? 1 : 0;
   in.bp_form = bp_form_used;
@@ -714,7 +770,7 @@ cfft_status ensure_fill_table_t(cfft_ctx* ctx) {
   const double rho_f = d_f * (double)(n_f - 1);
   if (own) {
     // the same tabulation on the fill's grid, with the options the table was made with
-    double saved[13];
+    double saved[15];
     std::memcpy(saved, ctx->opt, sizeof(saved));
     std::memcpy(ctx->opt, ctx->tab_opt, sizeof(saved));
     cfft_status stt = tabulate_impl<T>(ctx, (int)n_f, rho_f, ctx->d_ftable, false);
@@ -898,7 +954,7 @@ cfft_status check_fill_args(cfft_ctx* ctx, int n_el, const double* pos, const in
 // sequence captured once into a CUDA graph and replayed.
 
 struct BatchItemPlan {
-  int n, taylor, n_active, K, D;
+  int n, taylor, series, n_active, K, D;
   int64_t P;
   double step, ds, beta_abs;
 };
@@ -935,10 +991,12 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     p.n = it.n;
     p.step = it.beta_max / it.n;
     p.beta_abs = std::hypot(it.beta_max, it.height);
-    p.taylor = it.taylor_order >= 0 ? it.taylor_order
-                                    : auto_taylor(it.height * rho_max, fp64 ? 1e-13 : 1e-7);
+    const SeriesChoice sc = choose_series(it.height * rho_max, fp64, it.taylor_order,
+                                          ctx->opt[CFFT_OPT_CONTOUR_SERIES]);
+    p.taylor = sc.order;
+    p.series = sc.series;
     if (p.taylor < 0)
-      return fail(ctx, CFFT_ERR_ARG, "batch item: height * rho_max too large for the Taylor expansion");
+      return fail(ctx, CFFT_ERR_ARG, "batch item: height * rho_max too large for the contour-factor series");
     p.P = (int64_t)sigma * it.n;
     p.ds = 2.0 * kPi / ((double)p.P * p.step);
     p.K = (int)std::ceil(rho_max / p.ds) + bp_taps / 2 + 2;
@@ -961,7 +1019,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
                     ":" + std::to_string(rho_max) + ":" + std::to_string(sizeof(T)) + ":" +
                     std::to_string(n_alpha) + ":" + std::to_string((size_t)tables) + ":" +
                     std::to_string(ctx->n_basis) + ":" + std::to_string(M);
-  for (int i = 0; i < n_items; ++i) sig += ":" + std::to_string(ip[i].n) + "/" + std::to_string(ip[i].taylor);
+  for (int i = 0; i < n_items; ++i) sig += ":" + std::to_string(ip[i].n) + "/" + std::to_string(ip[i].taylor) + "/" + std::to_string(ip[i].series);
 
   // ---- element data in T (shared by all items)
   {
@@ -1069,10 +1127,11 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     struct WaveRanges { size_t c0, c1, i0, i1, f0, f1, b0, b1; std::vector<FftBucket> fb; };
     std::vector<WaveRanges> wr;
     int64_t cos_total = 0;
-    int max_nodes = 0, max_seg = 0, max_nout = 0, max_active = 0, max_n_item = 0;
+    int max_nodes = 0, max_seg = 0, max_nout = 0, max_active = 0, max_n_item = 0, zt_arrays = 1;
     for (int i = 0; i < n_items; ++i) {
       max_active = std::max(max_active, ip[i].n_active);
       max_n_item = std::max(max_n_item, ip[i].n);
+      if (ip[i].series == 1) zt_arrays = 2;   // the Chebyshev recurrence keeps two terms
     }
     for (int i = 0; i < n_items; ++i) {
       for (int c = 0; c < n_chunks; ++c) {
@@ -1170,6 +1229,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         fa.fft_len = p.P;
         fa.grid_half = p.K;
         fa.taylor = p.taylor;
+        fa.expansion = p.series;
         fa.n_active = p.n_active;
         fa.sigma = sigma;
         fa.ds_height = p.ds * it.height;
@@ -1181,7 +1241,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         max_nout = std::max(max_nout, (2 * p.K + 1) / D + 2);
         for (int sr = 0; sr < series; ++sr)
           for (int k2 = 0; k2 < D; ++k2) ftask.push_back(make_int4(i, sr, k2, log2Li));
-        work_fft += (double)series * D * (p.taylor + 1);
+        work_fft += (double)series * D * (p.taylor + (p.series == 1 ? 2 : 1));
         BackprojArgs<T>& ba = hba[i];
         ba = BackprojArgs<T>{};
         ba.series_per_q = pairs;
@@ -1279,7 +1339,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     };
     for (long long v : {(long long)L, (long long)rchunk, (long long)tform_b, (long long)tc_b, (long long)jt,
                         (long long)n_chunks, (long long)max_nodes, (long long)max_seg, (long long)max_nout,
-                        (long long)max_active, (long long)max_n_item, (long long)cos_total})
+                        (long long)max_active, (long long)max_n_item, (long long)cos_total,
+                        (long long)zt_arrays})
       add(v);
     for (const void* ptr : {ctx->d_tw.p, ctx->b_cnodes.p, ctx->b_coff.p, ctx->b_cos.p, ctx->b_count.p,
                             ctx->b_cargs.p, ctx->b_cdata.p, ctx->b_iargs.p, ctx->b_fargs.p, ctx->b_bargs.p,
@@ -1342,7 +1403,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
           const FftBucket& fb = r.fb[bkt];
           e = launch_fft_batch<T>(ctx->b_fargs.as<FftArgs<T>>(), ctx->b_ftask.as<int4>() + fb.f0,
                                   (int)(fb.f1 - fb.f0), counters + 1 + bkt, fb.log2L, fb.max_nout,
-                                  max_active, (max_n_item + 127) / 128, ctx->sm_count, st);
+                                  max_active, (max_n_item + 127) / 128, zt_arrays, ctx->sm_count, st);
           if (e != cudaSuccess) return e;
           ++launches;
         }
@@ -1654,7 +1715,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 12) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 13) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   if (key == CFFT_OPT_FILL_REFINE) ctx->fill_r = 0;   // decided again at the next fill
   return CFFT_OK;

@@ -217,14 +217,16 @@ struct FftArgs {
   int series, n, sub_len, log2_sub, n_sub;   // n_sub = D = P / sub_len
   int64_t fft_len;                            // P = sigma * n
   int grid_half;                              // K
-  int taylor;                                 // N_t
+  int taylor;                                 // highest term index N of the series
+  int expansion;                              // contour-factor series: 0 Taylor (Eq. 22), 1 Chebyshev
   int n_active;                               // nodes with beta_I > 0 (prefix)
   int sigma;
-  double ds_height;                           // delta_s * height  (Taylor variable scale)
+  double ds_height;                           // delta_s * height  (series variable scale)
   const cpx<T>* y;                            // [series][n]
   const double* bi_rel;                       // [n]
   const float* bi_rel_f;                      // [n] float32 copy
   const cpx<T>* twiddle;                      // [sub_len] e^{-2 pi i t / sub_len}
+  const cpx<T>* prec;                         // [n] input precorrection (null: none)
   cpx<T>* grid;                               // [series][2K+1]
 };
 
@@ -289,14 +291,14 @@ void launch_contour_batch(const ContourArgs* items, const ContourData* data, con
 // shared-memory bytes of one transform task beyond its FFT buffer
 template <class T>
 __host__ __device__ constexpr size_t fft_task_extra(int /*n_active_max*/, int n_out_max, int hi_max) {
-  return (size_t)(256 + hi_max + 128 + 128) * sizeof(cpx<T>) +
-         (size_t)n_out_max * (sizeof(cpx<T>) + 2 * sizeof(T)) + 64;
+  return (size_t)(128 + hi_max + 128 + 128) * sizeof(cpx<T>) +
+         (size_t)n_out_max * (sizeof(cpx<T>) + sizeof(T)) + 64;
 }
 
 template <class T>
 cudaError_t launch_fft_batch(const FftArgs<T>* items, const int4* tasks, int n_tasks, int* counter,
-                             int log2_sub, int max_n_out, int max_active, int max_hi, int n_ctas,
-                             cudaStream_t s);
+                             int log2_sub, int max_n_out, int max_active, int max_hi, int zt_arrays,
+                             int n_ctas, cudaStream_t s);
 template <class T>
 size_t backproject_smem(int group, int max_seg, int max_nodes);
 template <class T>

@@ -436,9 +436,55 @@ struct FftShape {
   static constexpr int BUF = R16 ? L + L / 16 : L;               // padded buffer entries
 };
 
-// one (series, k2) task: all Taylor terms of one residue class of the outputs.
-// use_zt: the pre-twiddled active inputs x_j (beta_I/H)^n are kept in shared memory
-// and advanced by one multiplication per Taylor term instead of being re-read
+// Chebyshev polynomial T_m(z) by its three-term recurrence (|z| <= 1: stable)
+template <class T>
+__device__ __forceinline__ T cheb_t(int m, T z) {
+  if (m == 0) return (T)1;
+  T t0 = (T)1, t1 = z;
+  for (int i = 1; i < m; ++i) {
+    const T t2 = (T)2 * z * t1 - t0;
+    t0 = t1;
+    t1 = t2;
+  }
+  return t1;
+}
+
+// a / b for a small positive integer b: in float32 by the reciprocal-based quotient
+// (two units in the last place), in float64 exactly
+template <class T>
+__device__ __forceinline__ T div_int(T a, int b) {
+  if constexpr (sizeof(T) == 4) return __fdividef(a, (float)b);
+  else return a / (double)b;
+}
+
+// I_m(a) / ((a/2)^m / m!) = sum_i q^i m! / (i! (i+m)!), q = (a/2)^2: the power series of
+// the modified Bessel function I_m without its leading factor
+template <class T>
+__device__ __forceinline__ T bessel_i_tail(int m, T q) {
+  T t = (T)1, sum = (T)1;
+  const T eps = sizeof(T) == 4 ? (T)1e-8 : (T)1e-17;
+  for (int i = 1; i < 48; ++i) {
+    t = div_int<T>(t * q, i * (i + m));
+    sum += t;
+    if (t <= eps * sum) break;
+  }
+  return sum;
+}
+
+// one (series, k2) task: all terms of the contour-factor expansion of one residue class of
+// the outputs.  The real exponential exp(beta_I s) = exp(H s b), b = beta_I / H in [0, 1]
+// on the active prefix of the contour (0 beyond it), is expanded in one of two series:
+//  * series 0, the Taylor series of Eq. 22: term 0 = all nodes with weight 1, term n >= 1
+//    = the active nodes with weight b^n, output coefficient (H s)^n / n!;
+//  * series 1, the Chebyshev series of the same factor about the middle of b's range:
+//    exp(H s b) = exp(a) exp(a z), a = H s / 2, z = 2 b - 1 in [-1, 1], and
+//    exp(a z) = I_0(a) + 2 sum_m I_m(a) T_m(z); term 0 = the nodes beyond the active
+//    prefix (b = 0: weight 1, exactly), term m + 1 = the active nodes with weight T_m(z),
+//    output coefficient exp(a) (2 - [m = 0]) I_m(a).  Its coefficients fall like
+//    (a / 2)^m / m! instead of (2 a)^n / n!, so fewer transforms reach a tolerance.
+// use_zt: the pre-twiddled active inputs times the current weight are kept in shared
+// memory (two arrays for the Chebyshev recurrence) and advanced by the weight recurrence
+// instead of being re-read
 template <class T, int LOG2L, int NT>
 __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series, int k2,
                                                 unsigned char* smem_raw, int use_zt) {
@@ -452,10 +498,14 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   const int t_hi = floor_div(K - k2, D);
   const int n_out = t_hi - t_lo + 1;
   const int n = a.n;
+  const int na = a.n_active;
+  const bool cheb = a.expansion == 1;
+  const int n_terms = a.taylor + (cheb ? 2 : 1);
   const int n_hi = (n + 127) >> 7;
   const int tid = threadIdx.x;
   const int64_t P = a.fft_len;
-  // shared layout: FFT buffer | pre-twiddle lo, hi | FFT twiddle hi, lo | acc | fac | sk
+  // shared layout: FFT buffer | pre-twiddle lo, hi | FFT twiddle hi, lo | acc | coefficient |
+  // stored active inputs (one array, two for the Chebyshev recurrence)
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* plo = buf + BUF;          // exp(-2 pi i r k2 / P), r < 128
   cpx<T>* phi = plo + 128;          // exp(-2 pi i 128 m k2 / P), m < n_hi
@@ -463,9 +513,13 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   cpx<T>* tlo = thi + 128;          // exp(-2 pi i r / L), r < 128
   cpx<T>* acc = tlo + 128;
   T* fac = reinterpret_cast<T*>(acc + n_out);
-  T* skv = fac + n_out;
-  cpx<T>* zt = reinterpret_cast<cpx<T>*>((reinterpret_cast<uintptr_t>(skv + n_out) + 15) & ~(uintptr_t)15);
+  cpx<T>* zt = reinterpret_cast<cpx<T>*>((reinterpret_cast<uintptr_t>(fac + n_out) + 15) & ~(uintptr_t)15);
+  cpx<T>* zt2 = zt + na;
   const cpx<T>* y = a.y + (size_t)series * n;
+  auto brel = [&](int j) -> T {
+    if constexpr (sizeof(T) == 4) return a.bi_rel_f[j];
+    else return a.bi_rel[j];
+  };
 
   // ---- per-task tables (exact integer argument reduction; the sine and cosine in the
   // precision of T: the angles are (integer < P) / P)
@@ -485,105 +539,104 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
     sincospi_((T)(-2.0 * (double)(((int64_t)m * 128 * k2) % P) / (double)P), &sv, &cv);
     phi[m] = mk(cv, sv);
   }
+  // fac[o]: the running factor of output o's coefficient, (H s)^n / n! for the Taylor
+  // series, exp(a) (a/2)^m / m! for the Chebyshev series (a = H s / 2)
+  const T dsh = (T)a.ds_height;
   for (int o = tid; o < n_out; o += NT) {
     acc[o] = mk((T)0, (T)0);
-    fac[o] = (T)1;
-    skv[o] = (T)(a.ds_height * (double)(k2 + D * (t_lo + o)));
+    fac[o] = cheb ? exp((T)0.5 * dsh * (T)(k2 + D * (t_lo + o))) : (T)1;
   }
   __syncthreads();
-  for (int nt = 0; nt <= a.taylor; ++nt) {
-    const int lim = nt == 0 ? n : a.n_active;
-    const T inv = (T)1 / (T)(nt + 1);
-    if constexpr (R16) {
-      // fold + pre-twiddle W_P^{j k2} + Taylor weight (beta_I/H)^n, fed to the first pass
-      auto input = [&](int jp) -> cpx<T> {
-        cpx<T> v = mk((T)0, (T)0);
-        if (use_zt && nt > 0) {
-          for (int j = jp; j < lim; j += L) {
-            const cpx<T> x = zt[j];
-            v = v + x;
-            T b;
-            if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
-            else b = a.bi_rel[j];
-            zt[j] = b * x;   // next Taylor term
-          }
-        } else {
-          for (int j = jp; j < lim; j += L) {
-            cpx<T> x = y[j];
-            if (k2 != 0) x = x * (phi[j >> 7] * plo[j & 127]);
-            T b = (T)1;
-            if (nt > 0 || use_zt) {
-              if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
-              else b = a.bi_rel[j];
-            }
-            if (nt > 0) x = powi_scale<T>(b, nt).re * x;
-            else if (use_zt && j < a.n_active) zt[j] = b * x;   // first Taylor term for nt = 1
-            v = v + x;
+  for (int nt = 0; nt < n_terms; ++nt) {
+    // input nodes [j_lo, lim) of this term
+    const int j_lo = (cheb && nt == 0) ? na : 0;
+    const int lim = nt == 0 ? n : na;
+    // coefficient of output o in this term; advances its running factor to the next term
+    // (each needed output is used once per term, by one thread)
+    const T inv_next = (T)1 / (T)(cheb ? (nt > 0 ? nt : 1) : nt + 1);
+    auto coef = [&](int o) -> T {
+      const T x = dsh * (T)(k2 + D * (t_lo + o));   // H s_k
+      const T f = fac[o];
+      if (!cheb) {
+        fac[o] = f * x * inv_next;
+        return f;
+      }
+      if (nt == 0) return (T)1;
+      const int m = nt - 1;
+      const T h = (T)0.25 * x;   // a / 2
+      fac[o] = f * h * inv_next;
+      return (m == 0 ? (T)1 : (T)2) * f * bessel_i_tail<T>(m, h * h);
+    };
+    const bool stored = use_zt && (cheb ? nt > 1 : nt > 0);
+    // fold + pre-twiddle W_P^{j k2} + the term's weight, for the residue jp of the nodes
+    auto fold = [&](int jp) -> cpx<T> {
+      cpx<T> v = mk((T)0, (T)0);
+      if (stored) {
+        for (int j = jp; j < lim; j += L) {
+          const cpx<T> c = zt[j];
+          v = v + c;
+          if (!cheb) {
+            zt[j] = brel(j) * c;   // next Taylor term
+          } else {
+            const T z2 = (T)4 * brel(j) - (T)2;   // 2 z
+            const cpx<T> pv = zt2[j];
+            zt[j] = z2 * c - pv;   // next Chebyshev term
+            zt2[j] = c;
           }
         }
         return v;
-      };
+      }
+      int j = jp;
+      if (j < j_lo) j += ((j_lo - j + L - 1) / L) * L;   // first node of the class in range
+      for (; j < lim; j += L) {
+        cpx<T> x = y[j];
+        if (a.prec) x = x * a.prec[j];
+        if (k2 != 0) x = x * (phi[j >> 7] * plo[j & 127]);
+        if (!cheb) {
+          T b = (T)1;
+          if (nt > 0 || use_zt) b = brel(j);
+          if (nt > 0) x = powi_scale<T>(b, nt).re * x;
+          else if (use_zt && j < na) zt[j] = b * x;   // first Taylor term for nt = 1
+        } else if (nt >= 1) {
+          const T z = (T)2 * brel(j) - (T)1;
+          if (nt == 1) {
+            if (use_zt) {
+              zt[j] = z * x;   // T_1 x, the next term's input
+              zt2[j] = x;      // T_0 x
+            }
+          } else {
+            x = cheb_t<T>(nt - 1, z) * x;
+          }
+        }
+        v = v + x;
+      }
+      return v;
+    };
+    if constexpr (R16) {
       constexpr int REM = LOG2L & 3;
       constexpr int R0 = REM == 0 ? 16 : (1 << REM);
-      first_pass_fused<T, R0, LOG2L, NT>(buf, input);
+      first_pass_fused<T, R0, LOG2L, NT>(buf, fold);
       middle_passes<T, LOG2L, NT, R0>(buf, thi, tlo);
-      // the needed outputs k = k2 + D t, |k| <= K, accumulate (H s_k)^n / n! times the term
+      // the needed outputs k = k2 + D t, |k| <= K, accumulate the term's coefficient times it
       auto use = [&](int t, cpx<T> v) {
         const int tt = t <= t_hi ? t : t - L;
         if (tt >= t_lo && tt <= t_hi) {
           const int o = tt - t_lo;
-          const T f = fac[o];
-          acc[o] = acc[o] + f * v;
-          fac[o] = f * skv[o] * inv;
+          acc[o] = acc[o] + coef(o) * v;
         }
       };
       if (t_hi < L / 16 && t_lo > -(L / 16)) last_pass_pruned<T, LOG2L, NT>(buf, thi, tlo, t_lo, t_hi, use);
       else last_pass_fused<T, LOG2L, NT>(buf, thi, tlo, use);
       continue;
     }
-    // ---- fold + pre-twiddle W_P^{j k2} + Taylor weight (beta_I/H)^n
-    if (use_zt && nt > 0) {
-      // the active inputs, already pre-twiddled and weighted by (beta_I/H)^nt
-      for (int jp = tid; jp < L; jp += NT) {
-        cpx<T> v = mk((T)0, (T)0);
-        for (int j = jp; j < lim; j += L) {
-          const cpx<T> x = zt[j];
-          v = v + x;
-          T b;
-          if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
-          else b = a.bi_rel[j];
-          zt[j] = b * x;   // next Taylor term
-        }
-        buf[bidx(jp)] = v;
-      }
-    } else {
-      for (int jp = tid; jp < L; jp += NT) {
-        cpx<T> v = mk((T)0, (T)0);
-        for (int j = jp; j < lim; j += L) {
-          cpx<T> x = y[j];
-          if (k2 != 0) x = x * (phi[j >> 7] * plo[j & 127]);
-          T b = (T)1;
-          if (nt > 0 || use_zt) {
-            if constexpr (sizeof(T) == 4) b = a.bi_rel_f[j];
-            else b = a.bi_rel[j];
-          }
-          if (nt > 0) x = powi_scale<T>(b, nt).re * x;
-          else if (use_zt && j < a.n_active) zt[j] = b * x;   // first Taylor term for nt = 1
-          v = v + x;
-        }
-        buf[bidx(jp)] = v;
-      }
-    }
+    for (int jp = tid; jp < L; jp += NT) buf[bidx(jp)] = fold(jp);
     __syncthreads();
     fft_inplace<T, LOG2L, NT>(buf, thi, tlo);
     // ---- accumulate the needed outputs: k = k2 + D t, |k| <= K
     for (int o = tid; o < n_out; o += NT) {
       int t = t_lo + o;
       int idx = t & (L - 1);  // t mod L (two's complement)
-      cpx<T> v = buf[bidx(idx)];
-      T f = fac[o];
-      acc[o] = acc[o] + f * v;
-      fac[o] = f * skv[o] * inv;
+      acc[o] = acc[o] + coef(o) * buf[bidx(idx)];
     }
     __syncthreads();
   }
@@ -630,14 +683,15 @@ __global__ void __launch_bounds__(NT, fft_min_blocks<NT>()) fft_taylor_batch_ker
   }
 }
 
-// shared bytes of a transform task, with or without the active-input store
+// shared bytes of a transform task with zt_arrays stores of the active inputs (0: none)
 template <class T, int LOG2L>
-size_t fft_task_smem(int n_active, int n_out_max, int hi_max, bool zt) {
+size_t fft_task_smem(int n_active, int n_out_max, int hi_max, int zt_arrays) {
   return (size_t)FftShape<LOG2L>::BUF * sizeof(cpx<T>) + fft_task_extra<T>(n_active, n_out_max, hi_max) +
-         (zt ? (size_t)n_active * sizeof(cpx<T>) + 16 : 0);
+         (zt_arrays > 0 ? (size_t)zt_arrays * n_active * sizeof(cpx<T>) + 16 : 0);
 }
 
-constexpr size_t kFftSmemCap = 220 * 1024;
+// the opt-in maximum of dynamic shared memory per block (227 KB) less the static words
+constexpr size_t kFftSmemCap = 227 * 1024 - 64;
 
 template <class T, int LOG2L>
 cudaError_t launch_l(const FftArgs<T>& a, cudaStream_t s) {
@@ -645,8 +699,10 @@ cudaError_t launch_l(const FftArgs<T>& a, cudaStream_t s) {
   const int D = a.n_sub;
   const int n_out_max = (2 * a.grid_half + 1) / D + 2;
   const int hi = (a.n + 127) / 128;
-  const bool zt = a.taylor > 0 && fft_task_smem<T, LOG2L>(a.n_active, n_out_max, hi, true) <= kFftSmemCap;
-  const size_t smem = fft_task_smem<T, LOG2L>(a.n_active, n_out_max, hi, zt);
+  // the stored active inputs pay when at least two terms after the first read them
+  const int arrays = a.expansion == 1 ? 2 : 1;
+  const bool zt = a.taylor > 0 && fft_task_smem<T, LOG2L>(a.n_active, n_out_max, hi, arrays) <= kFftSmemCap;
+  const size_t smem = fft_task_smem<T, LOG2L>(a.n_active, n_out_max, hi, zt ? arrays : 0);
   cudaError_t e = cudaFuncSetAttribute(fft_taylor_kernel<T, LOG2L, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -657,10 +713,11 @@ cudaError_t launch_l(const FftArgs<T>& a, cudaStream_t s) {
 
 template <class T, int LOG2L>
 cudaError_t launch_l_batch(const FftArgs<T>* items, const int4* tasks, int n_tasks, int* counter,
-                           int max_n_out, int max_active, int max_hi, int n_ctas, cudaStream_t s) {
+                           int max_n_out, int max_active, int max_hi, int zt_arrays, int n_ctas,
+                           cudaStream_t s) {
   constexpr int NT = FftShape<LOG2L>::NT;
-  const bool zt = fft_task_smem<T, LOG2L>(max_active, max_n_out + 2, max_hi, true) <= kFftSmemCap;
-  const size_t smem = fft_task_smem<T, LOG2L>(max_active, max_n_out + 2, max_hi, zt);
+  const bool zt = fft_task_smem<T, LOG2L>(max_active, max_n_out + 2, max_hi, zt_arrays) <= kFftSmemCap;
+  const size_t smem = fft_task_smem<T, LOG2L>(max_active, max_n_out + 2, max_hi, zt ? zt_arrays : 0);
   cudaError_t e = cudaFuncSetAttribute(fft_taylor_batch_kernel<T, LOG2L, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -677,25 +734,25 @@ cudaError_t launch_l_batch(const FftArgs<T>* items, const int4* tasks, int n_tas
 
 template <class T>
 cudaError_t launch_fft_batch(const FftArgs<T>* items, const int4* tasks, int n_tasks, int* counter,
-                             int log2_sub, int max_n_out, int max_active, int max_hi, int n_ctas,
-                             cudaStream_t s) {
+                             int log2_sub, int max_n_out, int max_active, int max_hi, int zt_arrays,
+                             int n_ctas, cudaStream_t s) {
   switch (log2_sub) {
-    case 10: return launch_l_batch<T, 10>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, n_ctas, s);
-    case 11: return launch_l_batch<T, 11>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, n_ctas, s);
-    case 12: return launch_l_batch<T, 12>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, n_ctas, s);
-    case 13: return launch_l_batch<T, 13>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, n_ctas, s);
+    case 10: return launch_l_batch<T, 10>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, zt_arrays, n_ctas, s);
+    case 11: return launch_l_batch<T, 11>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, zt_arrays, n_ctas, s);
+    case 12: return launch_l_batch<T, 12>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, zt_arrays, n_ctas, s);
+    case 13: return launch_l_batch<T, 13>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, zt_arrays, n_ctas, s);
     case 14:
       if constexpr (sizeof(T) == 4)
-        return launch_l_batch<T, 14>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, n_ctas, s);
+        return launch_l_batch<T, 14>(items, tasks, n_tasks, counter, max_n_out, max_active, max_hi, zt_arrays, n_ctas, s);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_fft_batch<float>(const FftArgs<float>*, const int4*, int, int*, int, int,
-                                             int, int, int, cudaStream_t);
+                                             int, int, int, int, cudaStream_t);
 template cudaError_t launch_fft_batch<double>(const FftArgs<double>*, const int4*, int, int*, int,
-                                              int, int, int, int, cudaStream_t);
+                                              int, int, int, int, int, cudaStream_t);
 
 template <class T>
 cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s) {
