@@ -639,7 +639,7 @@ def stage_flops(inf, wl):
     products per term, as the library counts them), "algorithmic" = the stage's arithmetic
     counted once whichever pipe ran it.  The back-projection's matrix forms evaluate the
     quadrature as interpolation-matrix products (8 flops per complex MAC) plus the node
-    stencils added into the matrices ((6 taps + 16) flops each); "per_node_unit" is the
+    stencils added into the matrices (weights + 2 taps + 16 flops each); "per_node_unit" is the
     gather form's (8 taps + 8) flops per (rho, alpha') node and series, the scope table's
     unit, which the matrix form beats by sharing each stencil across a chunk of series."""
     m = wl.element.n_mbf
@@ -649,7 +649,11 @@ def stage_flops(inf, wl):
     per_node = inf["work_bp_nodes"] * (8.0 * taps + 8.0)
     if form in (1, 2, 3):
         prod = 8.0 * inf["work_bp_macs"]
-        sten = (6.0 * taps + 16.0) * inf["work_bp_stencils"]
+        # a stencil: its weights (Lagrange: prefix and suffix products, 4 flops a tap; ES:
+        # one Horner polynomial of degree taps + 1 per tap) plus 2 taps fused multiply-adds
+        # into the A and B rows and 16 for its position and phase
+        weights = 2.0 * taps * (taps + 1) if inf.get("bp_kernel", 0) == 1 else 4.0 * taps
+        sten = (weights + 2.0 * taps + 16.0) * inf["work_bp_stencils"]
         bp = {"algorithmic": prod + sten, "fp32": sten if form == 3 else prod + sten,
               "tensor": inf.get("tc_flops_backproject", 0.0) if form == 3 else 0.0}
     else:

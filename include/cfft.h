@@ -76,8 +76,9 @@ typedef enum {
  * (CHECK_FINITE, FILL_BLOCK, FILL_SIMT):
  *   N_ALPHA     angular samples for the azimuthal harmonics (multiple of 4)
  *   SIGMA       zero-padding factor of the beta FFT (power of two >= 2)
- *   BP_TAPS     Lagrange taps of the back-projection interpolation
- *               (one of 4, 6, 8, 10, 12, 16, 20, 24)
+ *   BP_TAPS     taps of the back-projection interpolation: Lagrange one
+ *               of 4, 6, 8, 10, 12, 16, 20, 24 (default 16 in FP64, 12 in
+ *               FP32-mixed), ES 6 or 8 (default 6)
  *   FILL_TAPS   Lagrange taps of the fill interpolation in rho (even)
  *   ALPHA_MARGIN extra angular nodes of the back-projection quadrature
  *   CHECK_FINITE a value < 0 skips the NaN/Inf scan (and its stream sync)
@@ -122,7 +123,18 @@ typedef enum {
  *                extra FFT with weight 1.  Default (<= 0): an explicit
  *                taylor_order keeps the Taylor series; the automatic order
  *                takes the series with fewer FFTs for the precision's
- *                remainder bound (Taylor on a tie) */
+ *                remainder bound (Taylor on a tie)
+ *   BP_KERNEL    interpolation kernel of the back-projection.  1: Lagrange
+ *                polynomials on the transform grid g(s_k).  2: the ES
+ *                kernel exp(beta (sqrt(1 - (2x/w)^2) - 1)) of width w = taps
+ *                on the grid precorrected in the spectral domain (every
+ *                contour sample divided by the kernel's Fourier transform at
+ *                its frequency, so the "grid" debug buffer then holds the
+ *                precorrected grid); FP32-mixed, matrix forms, 6 or 8 taps:
+ *                6 ES taps reach the accuracy of 12 Lagrange taps at sigma 4
+ *                (aliasing below 2e-6; 8 taps: 1e-8).  Default (<= 0): ES
+ *                in FP32-mixed when the taps allow it, Lagrange otherwise;
+ *                2 where ES cannot run is CFFT_ERR_ARG */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -137,7 +149,8 @@ typedef enum {
   CFFT_OPT_BP_SIMT = 10,
   CFFT_OPT_FILL_SIMT = 11,
   CFFT_OPT_FILL_REFINE = 12,
-  CFFT_OPT_CONTOUR_SERIES = 13
+  CFFT_OPT_CONTOUR_SERIES = 13,
+  CFFT_OPT_BP_KERNEL = 14
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -421,6 +434,7 @@ cfft_status cfft_fill_backward_residual(cfft_ctx* ctx, int n_elements, const dou
  * the fill interpolates (0: no fill since the last tabulation); fill_n_rho:
  * that grid's points (n_rho when the fill uses the tabulated table, else
  * (n_rho - 1) r + 1 + fill_taps / 2, reaching beyond rho_max).
+ * bp_kernel: the back-projection's interpolation kernel (0 Lagrange, 1 ES).
  * tc_flops_integrand, tc_flops_backproject: the tensor-core flops the
  * integrand's spectra GEMM and the back-projection's products executed in the
  * tabulation (three TF32 products per term, padding included; 0 when that
@@ -437,7 +451,7 @@ typedef struct {
   double fill_err_est;
   int fill_refine, fill_n_rho;
   double tc_flops_integrand, tc_flops_backproject;
-  int contour_series;
+  int contour_series, bp_kernel;
 } cfft_info;
 cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
 
@@ -445,8 +459,9 @@ cfft_status cfft_get_info(const cfft_ctx* ctx, cfft_info* info);
  * stage-by-stage verification:
  *   "harmonics": the contour integrand H_ab,q(beta_j) beta_c,j w_j,
  *                shape {computed classes, M*M, 2*q_max+1, n}
- *   "grid":      the Taylor-summed transform on s_k = k delta_s, k = -K..K,
- *                demodulated: g_ab,q(s_k) exp(i beta_max s_k / 2),
+ *   "grid":      the series-summed transform on s_k = k delta_s, k = -K..K,
+ *                demodulated: g_ab,q(s_k) exp(i beta_max s_k / 2) (with the
+ *                ES kernel: of the precorrected samples, see BP_KERNEL),
  *                shape {computed classes, M*M, 2*q_max+1, 2K+1}
  *   "contour":   the nodes beta_c,j (complex128), shape {1, n, 1, 1}
  * "computed classes" is 1, or 3 with four rotation classes (the (90, 90)

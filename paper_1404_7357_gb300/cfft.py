@@ -17,7 +17,7 @@ CFFT_FP64 = 0
 CFFT_FP32_MIXED = 1
 (OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
  OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT, OPT_FILL_SIMT,
- OPT_FILL_REFINE, OPT_CONTOUR_SERIES) = range(14)
+ OPT_FILL_REFINE, OPT_CONTOUR_SERIES, OPT_BP_KERNEL) = range(15)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 
@@ -70,7 +70,7 @@ class Info(ctypes.Structure):
                [("fill_form", ctypes.c_int), ("fill_err_est", ctypes.c_double)] + \
                [(n, ctypes.c_int) for n in ("fill_refine", "fill_n_rho")] + \
                [(n, ctypes.c_double) for n in ("tc_flops_integrand", "tc_flops_backproject")] + \
-               [("contour_series", ctypes.c_int)]
+               [("contour_series", ctypes.c_int), ("bp_kernel", ctypes.c_int)]
 
 
 class CartesianInfo(ctypes.Structure):

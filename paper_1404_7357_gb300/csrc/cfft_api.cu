@@ -112,7 +112,7 @@ struct cfft_ctx {
   // device buffers
   DevBuf beta_c, weight, bw, bi_rel, green_p, green_r, dp_eps, dr_eps, dp_h, dr_h;
   int channels = 1;  // 1: table; 3: table, d/d eps_r, d/d h
-  DevBuf d_shapes, d_bx, d_by, d_q, d_y, d_grid, d_table, d_tw, d_cnodes, d_coff, d_cos, d_lag,
+  DevBuf d_shapes, d_bx, d_by, d_q, d_y, d_grid, d_table, d_tw, d_cnodes, d_coff, d_cos, d_lag, d_prec,
       d_flag, d_pos, d_rot, d_zbuf, d_fill, d_gres;
   int tw_len = 0, tw_prec = -1;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -252,6 +252,17 @@ SeriesChoice choose_series(double x, bool fp64, int order_req, double opt) {
   return {0, nt};
 }
 
+// interpolation kernel of the back-projection: ES (spectrally precorrected grid) in
+// FP32-mixed for the paired matrix forms with 6 or 8 taps, Lagrange otherwise.  Option
+// BP_KERNEL: <= 0 automatic, 1 Lagrange, 2 ES.  Returns -1 for an ES request it cannot take.
+int choose_bp_kernel(bool fp64, bool gather, int taps_opt, double kern_opt) {
+  const int mode = kern_opt > 0 ? (int)kern_opt : 0;
+  const bool es_ok = !fp64 && !gather && (taps_opt <= 0 || taps_opt == 6 || taps_opt == 8);
+  if (mode == 1) return 0;
+  if (mode == 2) return es_ok ? 1 : -1;
+  return es_ok ? 1 : 0;
+}
+
 // angular nodes of the back-projection for the largest rho of a chunk.  With z = |beta| rho
 // the integrand g(rho cos alpha) holds angular harmonics up to about z, and the midpoint
 // rule's error is the first aliased one, J_n(z) with n ~ 2 N - |q|.  Above its order J_n
@@ -302,8 +313,14 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   int sigma = (int)ctx->opt[CFFT_OPT_SIGMA];
   if (sigma <= 0) sigma = fp64 ? 8 : 4;
   if (sigma < 2 || (sigma & (sigma - 1))) return fail(ctx, CFFT_ERR_ARG, "sigma must be a power of two >= 2");
+  const int bp_kern = choose_bp_kernel(fp64, ctx->opt[CFFT_OPT_BP_GATHER] > 0, (int)ctx->opt[CFFT_OPT_BP_TAPS],
+                                       ctx->opt[CFFT_OPT_BP_KERNEL]);
+  if (bp_kern < 0)
+    return fail(ctx, CFFT_ERR_ARG,
+                "the ES back-projection kernel needs FP32-mixed, the matrix form and 6 or 8 taps");
+  const bool bp_es = bp_kern == 1;
   int bp_taps = (int)ctx->opt[CFFT_OPT_BP_TAPS];
-  if (bp_taps <= 0) bp_taps = fp64 ? 16 : 12;
+  if (bp_taps <= 0) bp_taps = fp64 ? 16 : (bp_es ? 6 : 12);
   int fill_taps = (int)ctx->opt[CFFT_OPT_FILL_TAPS];
   if (fill_taps <= 0) fill_taps = fp64 ? 16 : 8;
   if (!(bp_taps == 4 || bp_taps == 6 || bp_taps == 8 || bp_taps == 10 || bp_taps == 12 ||
@@ -346,6 +363,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   CFFT_CUDA(ctx->green_p.ensure(n * sizeof(double2)), "alloc contour");
   CFFT_CUDA(ctx->green_r.ensure(n * sizeof(double2)), "alloc contour");
   CFFT_CUDA(ctx->d_y.ensure((size_t)series * n * sizeof(cpx<T>)), "alloc harmonics");
+  if (bp_es) CFFT_CUDA(ctx->d_prec.ensure((size_t)n * sizeof(float2)), "alloc precorrection");
   CFFT_CUDA(ctx->d_grid.ensure((size_t)series * (2 * K + 1) * sizeof(cpx<T>)), "alloc grid");
   const int cls_s = ctx->cls_stored;
   const int channels = ctx->opt[CFFT_OPT_DERIVATIVES] > 0 ? 3 : 1;
@@ -400,7 +418,12 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   ContourData cd{ctx->beta_c.as<double2>(), ctx->weight.as<double2>(), ctx->bw.as<double2>(),
                  ctx->bi_rel.as<double>(), reinterpret_cast<float*>(ctx->bi_rel.as<double>() + n),
                  ctx->green_p.as<double2>(), ctx->green_r.as<double2>(),
-                 nullptr, nullptr, nullptr, nullptr};
+                 nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (bp_es) {
+    ca.es_width = bp_taps;
+    ca.ds = ds;
+    cd.prec = ctx->d_prec.as<float2>();
+  }
   if (channels == 3) {
     cd.dp_eps = ctx->dp_eps.as<double2>();
     cd.dr_eps = ctx->dr_eps.as<double2>();
@@ -489,6 +512,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   fa.bi_rel = ctx->bi_rel.as<double>();
   fa.bi_rel_f = reinterpret_cast<const float*>(ctx->bi_rel.as<double>() + n);
   fa.twiddle = ctx->d_tw.as<cpx<T>>();
+  if constexpr (sizeof(T) == 4) fa.prec = bp_es ? ctx->d_prec.as<cpx<float>>() : nullptr;
   fa.grid = ctx->d_grid.as<cpx<T>>();
   CFFT_CUDA(launch_fft<T>(fa, st), "fft kernel");
   ++launches;
@@ -498,7 +522,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   // the matrix-form back-projection handles up to 64 series per harmonic with 8/12/16 taps;
   // otherwise the direct gather form runs
   // FP32-mixed: the paired-harmonic matrix form (one interpolation matrix per |q|)
-  const bool taps_ok = bp_taps == 8 || bp_taps == 12 || bp_taps == 16;
+  const bool taps_ok = bp_es ? (bp_taps == 6 || bp_taps == 8) : (bp_taps == 8 || bp_taps == 12 || bp_taps == 16);
   const bool gather = ctx->opt[CFFT_OPT_BP_GATHER] > 0;
   const bool pform = !fp64 && taps_ok && !gather;
   const bool tform = pform && !(ctx->opt[CFFT_OPT_BP_SIMT] > 0);   // its products on the tensor cores
@@ -584,6 +608,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   ba.alpha_margin = margin;
   ba.grid = ctx->d_grid.as<cpx<T>>();
   ba.table = dst.as<cpx<T>>() + ch * table_elems;
+  ba.kern = bp_es ? 1 : 0;
   bp_form_used = tform ? 3 : (pform ? 2 : (wform ? 1 : 0));
   if (pform || wform) {
     ba.chunk_nodes = ctx->d_cnodes.as<int>();
@@ -641,6 +666,7 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   in.sub_len = L;
   in.grid_half = K;
   in.bp_taps = bp_taps;
+  in.bp_kernel = bp_es ? 1 : 0;
   in.fill_taps = fill_taps;
   in.series = series;
   in.classes = cls_s;
@@ -970,9 +996,13 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   const int nh = 2 * q_max + 1;
   const int series = pairs * nh;
   const int sigma = ctx->opt[CFFT_OPT_SIGMA] > 0 ? (int)ctx->opt[CFFT_OPT_SIGMA] : (fp64 ? 8 : 4);
-  const int bp_taps = ctx->opt[CFFT_OPT_BP_TAPS] > 0 ? (int)ctx->opt[CFFT_OPT_BP_TAPS] : (fp64 ? 16 : 12);
-  if (bp_taps != 8 && bp_taps != 12 && bp_taps != 16)
-    return fail(ctx, CFFT_ERR_ARG, "batched back-projection taps must be 8, 12 or 16");
+  const int bp_kern = choose_bp_kernel(fp64, false, (int)ctx->opt[CFFT_OPT_BP_TAPS], ctx->opt[CFFT_OPT_BP_KERNEL]);
+  if (bp_kern < 0)
+    return fail(ctx, CFFT_ERR_ARG, "batch: the ES back-projection kernel needs FP32-mixed and 6 or 8 taps");
+  const bool bp_es = bp_kern == 1;
+  const int bp_taps = ctx->opt[CFFT_OPT_BP_TAPS] > 0 ? (int)ctx->opt[CFFT_OPT_BP_TAPS] : (fp64 ? 16 : (bp_es ? 6 : 12));
+  if (bp_es ? (bp_taps != 6 && bp_taps != 8) : (bp_taps != 8 && bp_taps != 12 && bp_taps != 16))
+    return fail(ctx, CFFT_ERR_ARG, "batched back-projection taps must be 8, 12 or 16 (6 or 8 with the ES kernel)");
   const bool pform_b = !fp64;  // paired-harmonic matrix form in FP32-mixed
   // its products on the tensor cores (unless disabled; the autotuner may choose the FP32 pipe)
   bool tform_b = pform_b && !(ctx->opt[CFFT_OPT_BP_SIMT] > 0);
@@ -1018,7 +1048,8 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   std::string sig = std::to_string(n_items) + ":" + std::to_string(q_max) + ":" + std::to_string(n_rho) +
                     ":" + std::to_string(rho_max) + ":" + std::to_string(sizeof(T)) + ":" +
                     std::to_string(n_alpha) + ":" + std::to_string((size_t)tables) + ":" +
-                    std::to_string(ctx->n_basis) + ":" + std::to_string(M);
+                    std::to_string(ctx->n_basis) + ":" + std::to_string(M) + ":" + std::to_string(bp_taps) + ":" +
+                    std::to_string(bp_kern);
   for (int i = 0; i < n_items; ++i) sig += ":" + std::to_string(ip[i].n) + "/" + std::to_string(ip[i].taylor) + "/" + std::to_string(ip[i].series);
 
   // ---- element data in T (shared by all items)
@@ -1077,6 +1108,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   double2* c_gr = c_gp + max_nodes_wave;
   double* c_bi = reinterpret_cast<double*>(c_gr + max_nodes_wave);
   float* c_bif = reinterpret_cast<float*>(c_bi + max_nodes_wave);
+  float2* c_prec = reinterpret_cast<float2*>(c_bif + max_nodes_wave + (max_nodes_wave & 1));
 
   // integrand tile height (the same element and n_alpha for every item)
   IntegrandArgs<T> shape_args{};
@@ -1183,10 +1215,14 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         const cfft_batch_item& it = items[i];
         const BatchItemPlan& p = ip[i];
         hca[i] = ContourArgs{it.n, it.beta_max, it.beta_p, it.height, p.step, it.eps_r, it.h, it.k0};
+        if (bp_es) {
+          hca[i].es_width = bp_taps;
+          hca[i].ds = p.ds;
+        }
         set_extraction(ctx, it.eps_r, &hca[i].extract, &hca[i].eps_eff, &hca[i].deps_eff);
         hcd[i] = ContourData{c_beta + node_off, c_w + node_off, c_bw + node_off, c_bi + node_off,
                              c_bif + node_off, c_gp + node_off, c_gr + node_off,
-                             nullptr, nullptr, nullptr, nullptr};
+                             nullptr, nullptr, nullptr, nullptr, bp_es ? c_prec + node_off : nullptr};
         for (int j0 = 0; j0 < it.n; j0 += 256) cmap.push_back(make_int2(i, j0));
         for (int j0 = 0; j0 < it.n; j0 += jt) imap.push_back(make_int2(i, j0));
         IntegrandArgs<T>& ia = hia[i];
@@ -1237,6 +1273,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         fa.bi_rel = c_bi + node_off;
         fa.bi_rel_f = c_bif + node_off;
         fa.twiddle = ctx->d_tw.as<cpx<T>>();
+        if constexpr (sizeof(T) == 4) fa.prec = bp_es ? reinterpret_cast<const cpx<float>*>(c_prec + node_off) : nullptr;
         fa.grid = ctx->b_grid.as<cpx<T>>() + grid_off;
         max_nout = std::max(max_nout, (2 * p.K + 1) / D + 2);
         for (int sr = 0; sr < series; ++sr)
@@ -1263,6 +1300,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
         ba.chunk_off = ctx->b_coff.as<int64_t>() + (size_t)i * n_chunks;
         ba.cosv = ctx->b_cos.as<double>();
         ba.err = tform_b ? ctx->b_flag.as<int>() + 1 : nullptr;
+        ba.kern = bp_es ? 1 : 0;
         for (int c = n_chunks - 1; c >= 0; --c) {  // larger rho (more nodes) first
           int rows = std::min((c + 1) * rchunk, n_rho) - c * rchunk;
           if (pform_b) {
@@ -1412,11 +1450,11 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
           if (tform_b)
             e = launch_backproject_tc_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
                                             ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
-                                            bp_taps, max_nodes, ctx->sm_count, st);
+                                            bp_taps, bp_kern, max_nodes, ctx->sm_count, st);
           else if (pform_b)
             e = launch_backproject_pm_batch(ctx->b_bargs.as<BackprojArgs<float>>(),
                                             ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0), counters,
-                                            bp_taps, max_nodes, ctx->sm_count, st);
+                                            bp_taps, bp_kern, max_nodes, ctx->sm_count, st);
           else
             e = launch_backproject_w_batch<T>(ctx->b_bargs.as<BackprojArgs<T>>(),
                                               ctx->b_btask.as<int4>() + r.b0, (int)(r.b1 - r.b0),
@@ -1715,7 +1753,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 13) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 14) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   if (key == CFFT_OPT_FILL_REFINE) ctx->fill_r = 0;   // decided again at the next fill
   return CFFT_OK;

@@ -158,6 +158,8 @@ struct ContourArgs {
   double eps_r, hs, k0;
   int extract;                            // 1: subtract the homogeneous medium and its image
   double eps_eff, deps_eff;               // its permittivity and d eps_eff / d eps_r
+  int es_width;                           // > 0: ES precorrection of that kernel width
+  double ds;                              // transform grid step (for the precorrection)
 };
 
 // per-node contour data written by the contour kernel (float64 throughout)
@@ -175,6 +177,9 @@ struct ContourData {
   double2* dr_eps;
   double2* dp_h;
   double2* dr_h;
+  // optional: 1 / phi_hat(omega_j) of the ES interpolation kernel, omega_j = (beta_c,j -
+  // beta_max / 2) ds, the precorrection of the FP32-mixed transform input
+  float2* prec;
 };
 
 struct ShapeClass {
@@ -243,6 +248,7 @@ struct BackprojArgs {
   const int64_t* chunk_off;// [chunks] offset of its cosines in cosv
   const double* cosv;      // node cosines
   int* err;                // tensor-core form: bit 5 set when a wait ran past its bound
+  int kern;                // interpolation kernel: 0 Lagrange, 1 ES (precorrected grid)
 };
 
 // back-projection with the W x G+- product on the tensor cores (FP32-mixed)
@@ -250,7 +256,8 @@ size_t backproject_tc_smem(int max_nodes);
 int backproject_tc_ktile();
 cudaError_t launch_backproject_tc(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s);
 cudaError_t launch_backproject_tc_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
-                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s);
+                                        int* counter, int taps, int kern, int max_nodes, int n_ctas,
+                                        cudaStream_t s);
 
 template <class T, class TO>
 struct FillArgs {
@@ -321,7 +328,8 @@ int backproject_pm_rows();
 int backproject_pm_series_chunk();
 cudaError_t launch_backproject_pm(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s);
 cudaError_t launch_backproject_pm_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
-                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s);
+                                        int* counter, int taps, int kern, int max_nodes, int n_ctas,
+                                        cudaStream_t s);
 int backproject_w_rows();
 template <class T>
 cudaError_t launch_backproject_w(const BackprojArgs<T>& a, int n_tiles, int max_nodes, cudaStream_t s);

@@ -27,6 +27,7 @@
 // every warp owns rows; lanes split the node pairs; the node weights are
 // computed once per node pair and applied to every series of the group.
 #include "cfft_common.cuh"
+#include "es_weights.cuh"
 
 namespace cfft {
 
@@ -492,7 +493,8 @@ size_t pm_smem_bytes(int n_nodes_max) {
          (size_t)n_half * (sizeof(NodeCos<float>) + sizeof(float)) + 64;
 }
 
-template <int TAPS>
+// KERN: the stencil weights, 0 Lagrange (grid of g itself), 1 ES (precorrected grid)
+template <int TAPS, int KERN>
 __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a, int tile, int p, int chunk,
                                                     unsigned char* smem_raw) {
   constexpr int HALF = TAPS / 2 - 1;
@@ -588,7 +590,9 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
         float sv, cv;
         sincospif(-(red + e * inv_sigma), &sv, &cv);
         float w[TAPS];
-        {
+        if constexpr (KERN == 1) {
+          es_weights<TAPS>(f, w);
+        } else {
           float pre = 1.f;
 #pragma unroll
           for (int m = 0; m < TAPS; ++m) {
@@ -686,7 +690,7 @@ __device__ __forceinline__ void backproject_pm_task(const BackprojArgs<float>& a
 }
 
 // tasks in a 1-D grid, larger rho tiles (more work) first
-template <int TAPS>
+template <int TAPS, int KERN>
 __global__ void __launch_bounds__(kPR, 2) backproject_pm_kernel(BackprojArgs<float> a, int n_tiles, int n_p,
                                                                 int n_chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -694,11 +698,11 @@ __global__ void __launch_bounds__(kPR, 2) backproject_pm_kernel(BackprojArgs<flo
   const int t = blockIdx.x;
   const int tile = n_tiles - 1 - t / per_tile;
   const int rem = t - (t / per_tile) * per_tile;
-  backproject_pm_task<TAPS>(a, tile, rem / n_chunk, rem - (rem / n_chunk) * n_chunk, smem_raw);
+  backproject_pm_task<TAPS, KERN>(a, tile, rem / n_chunk, rem - (rem / n_chunk) * n_chunk, smem_raw);
 }
 
 // persistent form over (item, |q|, tile, series chunk) tasks
-template <int TAPS>
+template <int TAPS, int KERN>
 __global__ void __launch_bounds__(kPR, 2)
 backproject_pm_batch_kernel(const BackprojArgs<float>* items, const int4* tasks, int n_tasks, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -711,7 +715,7 @@ backproject_pm_batch_kernel(const BackprojArgs<float>* items, const int4* tasks,
     if (t >= n_tasks) break;
     const int4 tk = tasks[t];
     const BackprojArgs<float> a = items[tk.x];
-    backproject_pm_task<TAPS>(a, tk.z, tk.y, tk.w, smem_raw);
+    backproject_pm_task<TAPS, KERN>(a, tk.z, tk.y, tk.w, smem_raw);
     __syncthreads();
   }
 }
@@ -912,49 +916,64 @@ size_t backproject_pm_smem(int max_nodes) { return pm_smem_bytes(max_nodes); }
 int backproject_pm_rows() { return kPR; }
 int backproject_pm_series_chunk() { return kPSeries; }
 
-template <int TAPS>
+template <int TAPS, int KERN>
 cudaError_t launch_pm_taps(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s) {
   const size_t smem = pm_smem_bytes(max_nodes);
-  cudaError_t e = cudaFuncSetAttribute(backproject_pm_kernel<TAPS>,
+  cudaError_t e = cudaFuncSetAttribute(backproject_pm_kernel<TAPS, KERN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int n_p = a.q_max + 1;
   const int n_chunk = (a.series_per_q + kPSeries - 1) / kPSeries;
-  backproject_pm_kernel<TAPS><<<n_tiles * n_p * n_chunk, kPR, smem, s>>>(a, n_tiles, n_p, n_chunk);
+  backproject_pm_kernel<TAPS, KERN><<<n_tiles * n_p * n_chunk, kPR, smem, s>>>(a, n_tiles, n_p, n_chunk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backproject_pm(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s) {
   if (a.rchunk != kPR) return cudaErrorInvalidValue;
+  if (a.kern == 1) {
+    switch (a.taps) {
+      case 6: return launch_pm_taps<6, 1>(a, n_tiles, max_nodes, s);
+      case 8: return launch_pm_taps<8, 1>(a, n_tiles, max_nodes, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.taps) {
-    case 8: return launch_pm_taps<8>(a, n_tiles, max_nodes, s);
-    case 12: return launch_pm_taps<12>(a, n_tiles, max_nodes, s);
-    case 16: return launch_pm_taps<16>(a, n_tiles, max_nodes, s);
+    case 8: return launch_pm_taps<8, 0>(a, n_tiles, max_nodes, s);
+    case 12: return launch_pm_taps<12, 0>(a, n_tiles, max_nodes, s);
+    case 16: return launch_pm_taps<16, 0>(a, n_tiles, max_nodes, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int TAPS>
+template <int TAPS, int KERN>
 cudaError_t launch_pm_batch_taps(const BackprojArgs<float>* items, const int4* tasks, int n_tasks, int* counter,
                                  int max_nodes, int n_ctas, cudaStream_t s) {
   const size_t smem = pm_smem_bytes(max_nodes);
-  cudaError_t e = cudaFuncSetAttribute(backproject_pm_batch_kernel<TAPS>,
+  cudaError_t e = cudaFuncSetAttribute(backproject_pm_batch_kernel<TAPS, KERN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_pm_batch_kernel<TAPS>, kPR, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_pm_batch_kernel<TAPS, KERN>, kPR, smem) !=
           cudaSuccess || per_sm < 1)
     per_sm = 1;
-  backproject_pm_batch_kernel<TAPS><<<n_ctas * per_sm, kPR, smem, s>>>(items, tasks, n_tasks, counter);
+  backproject_pm_batch_kernel<TAPS, KERN><<<n_ctas * per_sm, kPR, smem, s>>>(items, tasks, n_tasks, counter);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backproject_pm_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
-                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s) {
+                                        int* counter, int taps, int kern, int max_nodes, int n_ctas,
+                                        cudaStream_t s) {
+  if (kern == 1) {
+    switch (taps) {
+      case 6: return launch_pm_batch_taps<6, 1>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+      case 8: return launch_pm_batch_taps<8, 1>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (taps) {
-    case 8: return launch_pm_batch_taps<8>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
-    case 12: return launch_pm_batch_taps<12>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
-    case 16: return launch_pm_batch_taps<16>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 8: return launch_pm_batch_taps<8, 0>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 12: return launch_pm_batch_taps<12, 0>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 16: return launch_pm_batch_taps<16, 0>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -23,6 +23,7 @@
 // row into TF32 head (in place) and tail.  The G+- tiles are staged in shared
 // memory from coalesced global reads and rearranged into Bop.
 #include "cfft_common.cuh"
+#include "es_weights.cuh"
 #include "spectra_tc.cuh"
 #include "tc_sm100.cuh"
 
@@ -71,7 +72,8 @@ __device__ __forceinline__ uint32_t op_off(int row, int k4) {
 // one (tile, |q| = p, series chunk) task.  n_commit counts the completions of mbar this
 // CTA has waited for (the parity of the next one), n_issued (thread 0) the commits it
 // made; fail is the CTA's timeout flag: once set, no MMA is issued and no wait is made.
-template <int TAPS>
+// KERN: the stencil weights, 0 Lagrange (grid of g itself), 1 ES (precorrected grid)
+template <int TAPS, int KERN>
 __device__ __forceinline__ void bp_tc_task(const BackprojArgs<float>& a, int tile, int p, int chunk,
                                            unsigned char* base, uint64_t* mbar, uint32_t tmem,
                                            uint32_t& n_commit, uint32_t& n_issued, int* fail) {
@@ -216,7 +218,9 @@ __device__ __forceinline__ void bp_tc_task(const BackprojArgs<float>& a, int til
         float sv, cv;
         sincospif(-(red + e * inv_sigma), &sv, &cv);
         float w[TAPS];
-        {
+        if constexpr (KERN == 1) {
+          es_weights<TAPS>(f, w);
+        } else {
           float pre = 1.f;
 #pragma unroll
           for (int m = 0; m < TAPS; ++m) {
@@ -372,7 +376,7 @@ __device__ __forceinline__ void tc_cta_teardown(const TcCta& c, int fail, uint32
   if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(c.tmem, 256);
 }
 
-template <int TAPS>
+template <int TAPS, int KERN>
 __global__ void __launch_bounds__(kTR, 2) backproject_tc_kernel(BackprojArgs<float> a, int n_tiles, int n_p,
                                                                 int n_chunk) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -386,13 +390,13 @@ __global__ void __launch_bounds__(kTR, 2) backproject_tc_kernel(BackprojArgs<flo
   const int tile = n_tiles - 1 - t / per_tile;   // larger rho tiles (more work) first
   const int rem = t - (t / per_tile) * per_tile;
   uint32_t n_commit = 0, n_issued = 0;
-  bp_tc_task<TAPS>(a, tile, rem / n_chunk, rem - (rem / n_chunk) * n_chunk, cta.base, cta.mbar, cta.tmem,
-                   n_commit, n_issued, &s_fail);
+  bp_tc_task<TAPS, KERN>(a, tile, rem / n_chunk, rem - (rem / n_chunk) * n_chunk, cta.base, cta.mbar,
+                         cta.tmem, n_commit, n_issued, &s_fail);
   tc_cta_teardown(cta, s_fail, n_issued, a.err);
 }
 
 // persistent form over (item, |q|, tile, series chunk) tasks
-template <int TAPS>
+template <int TAPS, int KERN>
 __global__ void __launch_bounds__(kTR, 2)
 backproject_tc_batch_kernel(const BackprojArgs<float>* items, const int4* tasks, int n_tasks, int* counter) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -413,32 +417,32 @@ backproject_tc_batch_kernel(const BackprojArgs<float>* items, const int4* tasks,
     const int4 tk = tasks[t];
     const BackprojArgs<float> a = items[tk.x];
     err = a.err;
-    bp_tc_task<TAPS>(a, tk.z, tk.y, tk.w, cta.base, cta.mbar, cta.tmem, n_commit, n_issued, &s_fail);
+    bp_tc_task<TAPS, KERN>(a, tk.z, tk.y, tk.w, cta.base, cta.mbar, cta.tmem, n_commit, n_issued, &s_fail);
   }
   tc_cta_teardown(cta, s_fail, n_issued, err);
 }
 
-template <int TAPS>
+template <int TAPS, int KERN>
 cudaError_t launch_tc_taps(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s) {
   const size_t smem = tc_bp_smem_bytes(max_nodes);
-  cudaError_t e = cudaFuncSetAttribute(backproject_tc_kernel<TAPS>,
+  cudaError_t e = cudaFuncSetAttribute(backproject_tc_kernel<TAPS, KERN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int n_p = a.q_max + 1;
   const int n_chunk = (a.series_per_q + kTS - 1) / kTS;
-  backproject_tc_kernel<TAPS><<<n_tiles * n_p * n_chunk, kTR, smem, s>>>(a, n_tiles, n_p, n_chunk);
+  backproject_tc_kernel<TAPS, KERN><<<n_tiles * n_p * n_chunk, kTR, smem, s>>>(a, n_tiles, n_p, n_chunk);
   return cudaGetLastError();
 }
 
-template <int TAPS>
+template <int TAPS, int KERN>
 cudaError_t launch_tc_batch_taps(const BackprojArgs<float>* items, const int4* tasks, int n_tasks, int* counter,
                                  int max_nodes, int n_ctas, cudaStream_t s) {
   const size_t smem = tc_bp_smem_bytes(max_nodes);
-  cudaError_t e = cudaFuncSetAttribute(backproject_tc_batch_kernel<TAPS>,
+  cudaError_t e = cudaFuncSetAttribute(backproject_tc_batch_kernel<TAPS, KERN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // at most two CTAs per SM: their tensor memory (2 x 256 columns) then always fits
-  backproject_tc_batch_kernel<TAPS><<<2 * n_ctas, kTR, smem, s>>>(items, tasks, n_tasks, counter);
+  backproject_tc_batch_kernel<TAPS, KERN><<<2 * n_ctas, kTR, smem, s>>>(items, tasks, n_tasks, counter);
   return cudaGetLastError();
 }
 
@@ -449,20 +453,35 @@ int backproject_tc_ktile() { return kTK; }
 
 cudaError_t launch_backproject_tc(const BackprojArgs<float>& a, int n_tiles, int max_nodes, cudaStream_t s) {
   if (a.rchunk != kTR) return cudaErrorInvalidValue;
+  if (a.kern == 1) {
+    switch (a.taps) {
+      case 6: return launch_tc_taps<6, 1>(a, n_tiles, max_nodes, s);
+      case 8: return launch_tc_taps<8, 1>(a, n_tiles, max_nodes, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.taps) {
-    case 8: return launch_tc_taps<8>(a, n_tiles, max_nodes, s);
-    case 12: return launch_tc_taps<12>(a, n_tiles, max_nodes, s);
-    case 16: return launch_tc_taps<16>(a, n_tiles, max_nodes, s);
+    case 8: return launch_tc_taps<8, 0>(a, n_tiles, max_nodes, s);
+    case 12: return launch_tc_taps<12, 0>(a, n_tiles, max_nodes, s);
+    case 16: return launch_tc_taps<16, 0>(a, n_tiles, max_nodes, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_backproject_tc_batch(const BackprojArgs<float>* items, const int4* tasks, int n_tasks,
-                                        int* counter, int taps, int max_nodes, int n_ctas, cudaStream_t s) {
+                                        int* counter, int taps, int kern, int max_nodes, int n_ctas,
+                                        cudaStream_t s) {
+  if (kern == 1) {
+    switch (taps) {
+      case 6: return launch_tc_batch_taps<6, 1>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+      case 8: return launch_tc_batch_taps<8, 1>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (taps) {
-    case 8: return launch_tc_batch_taps<8>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
-    case 12: return launch_tc_batch_taps<12>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
-    case 16: return launch_tc_batch_taps<16>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 8: return launch_tc_batch_taps<8, 0>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 12: return launch_tc_batch_taps<12, 0>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
+    case 16: return launch_tc_batch_taps<16, 0>(items, tasks, n_tasks, counter, max_nodes, n_ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }

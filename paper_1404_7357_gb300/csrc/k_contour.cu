@@ -14,6 +14,7 @@
 // Everything here is float64: the denominators near the surface-wave poles and
 // the branch-point square roots are where float32 loses the most digits.
 #include "cfft_common.cuh"
+#include "es_weights.cuh"
 #include "green_ext.cuh"
 
 namespace cfft {
@@ -94,6 +95,11 @@ __device__ __forceinline__ void contour_node(const ContourArgs& a, const Contour
       (eps ? d.dp_eps : d.dp_h)[j] = make_double2(dp.re, dp.im);
       (eps ? d.dr_eps : d.dr_h)[j] = make_double2(dr.re, dr.im);
     }
+  }
+  if (d.prec) {
+    // precorrection of the transform input for the ES back-projection: the node's
+    // demodulated frequency in grid units, omega = (beta_c - beta_max / 2) ds
+    d.prec[j] = es_precorrection((float)((br - 0.5 * a.beta_max) * a.ds), (float)(bi * a.ds), a.es_width);
   }
 }
 

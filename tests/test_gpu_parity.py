@@ -228,22 +228,25 @@ def test_fp32_single_harmonic_and_ragged_tiles(torch_cuda):
     assert err < TOL["fp32"]
 
 
-@pytest.mark.parametrize("taps", [8, 12, 16])
-def test_backprojection_tensor_cores_vs_fp32_pipe(torch_cuda, taps):
+@pytest.mark.parametrize("taps,kern", [(8, 1), (12, 1), (16, 1), (6, 2), (8, 2)])
+def test_backprojection_tensor_cores_vs_fp32_pipe(torch_cuda, taps, kern):
     """The paired-harmonic back-projection with its products on the tensor cores (three
     TF32 products per K-tile, drained into FP32 registers) against the same form on the
     FP32 pipe and against the oracle: 3 computed rotation classes (48 series per q, three
-    series chunks), a ragged last row tile, many K-tiles, each stencil width."""
+    series chunks), a ragged last row tile, many K-tiles, each stencil width, Lagrange
+    (kern 1) and ES (kern 2) stencils."""
     from paper_1404_7357_gb300 import cfft
     wl = cc.small_patch("fp32", n=2048, n_rho=600, rho_max=9.0, q_max=3, rotation_classes=4)
-    ctx_t, t_form = cc.gpu_table(wl, options={cfft.OPT_BP_TAPS: taps})
-    ctx_s, s_form = cc.gpu_table(wl, options={cfft.OPT_BP_TAPS: taps, cfft.OPT_BP_SIMT: 1})
+    opts = {cfft.OPT_BP_TAPS: taps, cfft.OPT_BP_KERNEL: kern}
+    ctx_t, t_form = cc.gpu_table(wl, options=opts)
+    ctx_s, s_form = cc.gpu_table(wl, options={**opts, cfft.OPT_BP_SIMT: 1})
     assert ctx_t.info()["bp_form"] == 3 and ctx_s.info()["bp_form"] == 2
+    assert ctx_t.info()["bp_kernel"] == kern - 1 and ctx_s.info()["bp_kernel"] == kern - 1
     ref, _, _ = cc.oracle_table(wl, classes=(0, 1, 2, 3))
     et = cc.rel_err_per_pair(t_form, ref).max()
     es = cc.rel_err_per_pair(s_form, ref).max()
     ets = cc.rel_err_per_pair(t_form, s_form.astype(np.complex128)).max()
-    print("taps", taps, "tensor-core form", et, "FP32-pipe form", es, "between", ets)
+    print("taps", taps, "kernel", kern, "tensor-core form", et, "FP32-pipe form", es, "between", ets)
     assert ets < 2e-6
-    if taps >= 12:   # 8 taps are below the FP32 interpolation target on this grid
+    if taps >= 12 or kern == 2:   # 8 Lagrange taps are below the FP32 target on this grid
         assert et < TOL["fp32"] and es < TOL["fp32"]

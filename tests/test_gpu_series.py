@@ -51,7 +51,8 @@ def test_series_against_exact_sum_and_oracle(torch_cuda, precision):
     ref, _, _ = cc.oracle_table(wl)
     res = {}
     for mode in (1, 2):
-        ctx, got = cc.gpu_table(wl, options={cfft.OPT_CONTOUR_SERIES: mode})
+        # Lagrange back-projection: the grid then holds g(s_k) itself (no precorrection)
+        ctx, got = cc.gpu_table(wl, options={cfft.OPT_CONTOUR_SERIES: mode, cfft.OPT_BP_KERNEL: 1})
         info = ctx.info()
         assert info["contour_series"] == mode - 1
         ffts = info["taylor_order"] + (2 if mode == 2 else 1)

@@ -33,7 +33,9 @@ def test_static_backprojection_matches_tabulation(torch_cuda, precision):
     torch = torch_cuda
     from paper_1404_7357_gb300 import cfft
     wl = cc.small_patch(precision, n=1024, n_rho=256, rho_max=4.0, q_max=3)
-    ctx, ref = cc.gpu_table(wl)                 # the existing entry point's table
+    # the static entry interpolates with Lagrange stencils: the tabulation it is compared
+    # with uses them too (its grid then holds g(s_k) itself)
+    ctx, ref = cc.gpu_table(wl, options={cfft.OPT_BP_KERNEL: 1})   # the existing entry point's table
     info = ctx.info()
     grid = ctx.debug_buffer("grid").contiguous()  # (classes, pairs, harmonics, 2K+1), device
     c = wl.contour
