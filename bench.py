@@ -674,8 +674,8 @@ def stage_flops(inf, wl):
 # DRAM bytes (read + write) per launch of each table kernel on the full patch-m4 workload,
 # from one ncu capture of the current kernel (None: changed since its last capture);
 # valid only for the default table sizes
-KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.332e6, "fft": 84.809e6 + 8.149e6,
-                     "backproject": 17.984e6 + 0.072e6}
+KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.332e6, "fft": 92.082e6 + 9.485e6,
+                     "backproject": 17.955e6 + 0.097e6}
 
 
 def pipe_peaks(peaks):
