@@ -996,6 +996,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
   const int nh = 2 * q_max + 1;
   const int series = pairs * nh;
   const int sigma = ctx->opt[CFFT_OPT_SIGMA] > 0 ? (int)ctx->opt[CFFT_OPT_SIGMA] : (fp64 ? 8 : 4);
+  if (sigma < 2 || (sigma & (sigma - 1))) return fail(ctx, CFFT_ERR_ARG, "sigma must be a power of two >= 2");
   const int bp_kern = choose_bp_kernel(fp64, false, (int)ctx->opt[CFFT_OPT_BP_TAPS], ctx->opt[CFFT_OPT_BP_KERNEL]);
   if (bp_kern < 0)
     return fail(ctx, CFFT_ERR_ARG, "batch: the ES back-projection kernel needs FP32-mixed and 6 or 8 taps");

@@ -522,21 +522,28 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   };
 
   // ---- per-task tables (exact integer argument reduction; the sine and cosine in the
-  // precision of T: the angles are (integer < P) / P)
+  // precision of T: the angles are (integer < P) / P).  In float32 the quotient is formed
+  // in float32 too (P < 2^24 is exact there): float64 arithmetic runs at 1/64 rate
+  auto angle = [&](int64_t num) -> T {   // -2 num / P, num in [0, P)
+    if constexpr (sizeof(T) == 4) return -2.0f * (float)num / (float)P;
+    else return -2.0 * (double)num / (double)P;
+  };
   for (int r = tid; r < 128; r += NT) {
     T sv, cv;
-    sincospi_((T)(-2.0 * (double)(((int64_t)r * k2) % P) / (double)P), &sv, &cv);
+    int64_t rk = (int64_t)r * k2;     // < 128 D <= 2 P
+    if (rk >= P) rk %= P;
+    sincospi_(angle(rk), &sv, &cv);
     plo[r] = mk(cv, sv);
-    sincospi_((T)(-2.0 * (double)r / (double)L), &sv, &cv);
+    sincospi_((T)-2 * (T)r / (T)L, &sv, &cv);
     tlo[r] = mk(cv, sv);
     if (r < ((L >> 7) > 0 ? (L >> 7) : 1)) {
-      sincospi_((T)(-2.0 * (double)(128 * r) / (double)L), &sv, &cv);
+      sincospi_((T)-2 * (T)(128 * r) / (T)L, &sv, &cv);
       thi[r] = mk(cv, sv);
     }
   }
   for (int m = tid; m < n_hi; m += NT) {
     T sv, cv;
-    sincospi_((T)(-2.0 * (double)(((int64_t)m * 128 * k2) % P) / (double)P), &sv, &cv);
+    sincospi_(angle(((int64_t)m * 128 * k2) % P), &sv, &cv);
     phi[m] = mk(cv, sv);
   }
   // fac[o]: the running factor of output o's coefficient, (H s)^n / n! for the Taylor
@@ -645,10 +652,20 @@ __device__ __forceinline__ void fft_taylor_task(const FftArgs<T>& a, int series,
   const int64_t two_p = 2 * P;
   for (int o = tid; o < n_out; o += NT) {
     int k = k2 + D * (t_lo + o);
-    // pi k (1/sigma - 1/P) = pi k (n - 1) / P, reduced exactly modulo 2 pi
-    int64_t e = ((int64_t)k * (int64_t)(n - 1)) % two_p;
-    if (e < 0) e += two_p;
-    cpx<T> ph = expipi<T>((double)e / (double)P);
+    cpx<T> ph;
+    if constexpr (sizeof(T) == 4) {
+      // exp(i pi k / sigma) exp(-i pi k / P): sigma is a power of two, so k mod 2 sigma is
+      // exact in integers, and |k| <= K < P / 2 keeps the second angle below pi / 2
+      float s1, c1, s2, c2;
+      sincospif((float)(k & (2 * a.sigma - 1)) / (float)a.sigma, &s1, &c1);
+      sincospif(-(float)k / (float)P, &s2, &c2);
+      ph = mk(c1 * c2 - s1 * s2, s1 * c2 + c1 * s2);
+    } else {
+      // pi k (1/sigma - 1/P) = pi k (n - 1) / P, reduced exactly modulo 2 pi
+      int64_t e = ((int64_t)k * (int64_t)(n - 1)) % two_p;
+      if (e < 0) e += two_p;
+      ph = expipi<T>((double)e / (double)P);
+    }
     out[k + K] = acc[o] * ph;
   }
 }
