@@ -134,7 +134,10 @@ typedef enum {
  *                6 ES taps reach the accuracy of 12 Lagrange taps at sigma 4
  *                (aliasing below 2e-6; 8 taps: 1e-8).  Default (<= 0): ES
  *                in FP32-mixed when the taps allow it, Lagrange otherwise;
- *                2 where ES cannot run is CFFT_ERR_ARG */
+ *                2 where ES cannot run is CFFT_ERR_ARG
+ *   SOLVE_SIMT   a value > 0 runs the complex64 LU's trailing matrix
+ *                products (cfft_solve_reduced) on the FP32 pipe instead of
+ *                the tensor cores */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -150,7 +153,8 @@ typedef enum {
   CFFT_OPT_FILL_SIMT = 11,
   CFFT_OPT_FILL_REFINE = 12,
   CFFT_OPT_CONTOUR_SERIES = 13,
-  CFFT_OPT_BP_KERNEL = 14
+  CFFT_OPT_BP_KERNEL = 14,
+  CFFT_OPT_SOLVE_SIMT = 15
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -595,20 +599,24 @@ cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const vo
  * The factorization runs in panels of 64 columns: one cooperative launch per
  * panel (pivot search and elimination, one bounded grid barrier per column),
  * the panel's row moves applied to the whole matrix, a triangular solve for
- * the panel's rows and a complex matrix product for the trailing matrix.
+ * the panel's rows and a complex matrix product for the trailing matrix.  In
+ * complex64 that product runs on the tensor cores (three TF32 products, FP32
+ * accumulation) unless the option SOLVE_SIMT is > 0, which keeps it on the
+ * FP32 pipe.
  * cfft_get_solve_info reports the times and the relative residual
  * |v - z x| / |v| computed in float64 from z.  Errors: CFFT_ERR_ARG,
  * CFFT_ERR_OOM, CFFT_ERR_NUMERIC (a zero pivot: z singular), CFFT_ERR_TIMEOUT
- * (a grid-barrier wait gave up).  Synchronizes. */
+ * (a grid-barrier or tensor-core wait gave up).  Synchronizes. */
 cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, int64_t ld, const void* v,
                                void* i_out, int complex128, int mode);
 
 /* Diagnostics of the last cfft_solve_reduced: factorization and solve times
  * (ms, CUDA events on the context stream; the solve includes refinement),
- * relative residual, order n, mode, refinement steps (mode 1), panel width. */
+ * relative residual, order n, mode, refinement steps (mode 1), panel width,
+ * and update_tc = 1 when the trailing updates ran on the tensor cores. */
 typedef struct {
   double ms_factor, ms_solve, residual;
-  int n, mode, refinements, panel_width;
+  int n, mode, refinements, panel_width, update_tc;
 } cfft_solve_info;
 cfft_status cfft_get_solve_info(const cfft_ctx* ctx, cfft_solve_info* info);
 

@@ -17,7 +17,7 @@ CFFT_FP64 = 0
 CFFT_FP32_MIXED = 1
 (OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
  OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT, OPT_FILL_SIMT,
- OPT_FILL_REFINE, OPT_CONTOUR_SERIES, OPT_BP_KERNEL) = range(15)
+ OPT_FILL_REFINE, OPT_CONTOUR_SERIES, OPT_BP_KERNEL, OPT_SOLVE_SIMT) = range(16)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 
@@ -80,7 +80,7 @@ class CartesianInfo(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("ms_factor", "ms_solve", "residual")] + \
-               [(n, ctypes.c_int) for n in ("n", "mode", "refinements", "panel_width")]
+               [(n, ctypes.c_int) for n in ("n", "mode", "refinements", "panel_width", "update_tc")]
 
 
 def _load():

@@ -93,8 +93,8 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic) and the options the last table was made with
-  double opt[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double tab_opt[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double tab_opt[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -796,7 +796,7 @@ cfft_status ensure_fill_table_t(cfft_ctx* ctx) {
   const double rho_f = d_f * (double)(n_f - 1);
   if (own) {
     // the same tabulation on the fill's grid, with the options the table was made with
-    double saved[15];
+    double saved[16];
     std::memcpy(saved, ctx->opt, sizeof(saved));
     std::memcpy(ctx->opt, ctx->tab_opt, sizeof(saved));
     cfft_status stt = tabulate_impl<T>(ctx, (int)n_f, rho_f, ctx->d_ftable, false);
@@ -1754,7 +1754,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 14) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key > 15) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   if (key == CFFT_OPT_FILL_REFINE) ctx->fill_r = 0;   // decided again at the next fill
   return CFFT_OK;
@@ -2169,6 +2169,7 @@ cfft_status lu_work(cfft_ctx* ctx, int n, LuWork* w) {
   w->diag = ctx->lu_diag;
   w->bar = ctx->lu_bar.as<unsigned>();
   w->err = ctx->lu_err.as<int>();
+  w->tc_update = ctx->opt[CFFT_OPT_SOLVE_SIMT] > 0 ? 0 : 1;
   return CFFT_OK;
 }
 
@@ -2187,6 +2188,7 @@ cfft_status lu_factor_checked(cfft_ctx* ctx, int n, const LuWork& w) {
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "LU factorization");
   if (flag & 2) return fail(ctx, CFFT_ERR_TIMEOUT, "LU panel: a grid-barrier wait ran past its bound");
   if (flag & 4) return fail(ctx, CFFT_ERR_NUMERIC, "LU: the reduced matrix is singular (zero pivot)");
+  if (flag & 8) return fail(ctx, CFFT_ERR_TIMEOUT, "LU update: a tensor-core wait ran past its bound");
   return CFFT_OK;
 }
 
@@ -2298,6 +2300,7 @@ extern "C" cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, i
   in.mode = mode;
   in.refinements = steps;
   in.panel_width = lu_panel_width();
+  in.update_tc = (w.tc_update && (!complex128 || mode == 1)) ? 1 : 0;   // complex64 factorization
   if (!std::isfinite(in.residual)) return fail(ctx, CFFT_ERR_NUMERIC, "solve: non-finite solution");
   return CFFT_OK;
 }

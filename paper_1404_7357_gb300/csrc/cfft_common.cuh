@@ -435,8 +435,10 @@ struct LuWork {
   int* cand_row;
   void* cand_data;     // [2][SMs][panel width] complex, the element type
   unsigned* bar;       // [panels] grid-barrier counters
-  int* err;            // bit 1: barrier wait ran out; bit 2: zero pivot
+  int* err;            // bit 1: barrier wait ran out; bit 2: zero pivot; bit 3: a tensor-core
+                       // wait of the trailing update ran out
   int* diag;           // host: [3] panel grid, resident CTAs per SM, shared bytes of the last panel
+  int tc_update;       // complex64: the trailing update on the tensor cores
 };
 int lu_panel_width();
 // the largest order whose panels fit the panel CTAs' shared memory on `sms` SMs

@@ -15,7 +15,9 @@
 //            displace to the vacated places, as a list of (source, destination)
 //            row moves applied to every column of the matrix.
 //   trsm     U12 = L11^-1 A12 (unit lower L11), one thread per column.
-//   gemm     A22 -= L21 U12, 64 x 64 tiles of complex entries, K = the panel.
+//   gemm     A22 -= L21 U12, K = the panel: in complex64 on the tensor cores (the
+//            complex product as a real GEMM, three TF32 products), otherwise
+//            64 x 64 tiles of complex entries on the FP32 / FP64 pipe.
 // The solve applies every panel's moves to the right-hand side, then blocked
 // forward (unit L) and backward (U) substitution: per panel one launch whose
 // CTAs each solve the small diagonal block (one warp) and update their rows.
@@ -25,6 +27,8 @@
 #include <algorithm>
 
 #include "cfft_common.cuh"
+#include "spectra_tc.cuh"
+#include "tc_sm100.cuh"
 
 namespace cfft {
 
@@ -379,6 +383,185 @@ __global__ void __launch_bounds__(256) lu_gemm_kernel(cpx<T>* a, int64_t ld, int
   }
 }
 
+// ---- A22 -= L21 U12 on the tensor cores (complex64).  With the rows of L21 and of A22
+// stored interleaved (re, im), one tile
+//   D (128 rows x 128 reals = 64 complex columns) = A' (128 x 2 kb) B' (2 kb x 128)
+// with A' the rows of L21 as stored (k' = 2 c + part) and
+//   B'^T[2j][2c] = Re U_cj, B'^T[2j][2c+1] = -Im U_cj,
+//   B'^T[2j+1][2c] = Im U_cj, B'^T[2j+1][2c+1] = Re U_cj
+// holds (Re, Im) of (L21 U12)_ij in columns 2j, 2j+1: the layout of A22 itself.  Three
+// TF32 products (head x head into one tensor-memory accumulator, the two corrections
+// into a second, added in FP32 registers), K staged 16 reals (8 panel columns) at a time
+// in two buffers, so the threads build one stage while the tensor core consumes the
+// other.  Every mbarrier wait is bounded; a wait that runs out sets bit 3 of err and the
+// CTA issues nothing more.
+constexpr int kUM = 128, kUN = 128, kUK = 16;   // tile rows, tile real columns, reals per stage
+constexpr uint32_t kUSbo = (kUK / 4) * 128;      // 8-row group stride of the K-major operands
+constexpr size_t kUStage = (size_t)2 * kUM * kUK * 4 + (size_t)2 * kUN * kUK * 4;
+// shared bytes per CTA: two stages, padded so that at most two CTAs share an SM (their
+// 2 x 256 tensor-memory columns then always fit)
+constexpr size_t kUSmem = 96 * 1024;
+static_assert(2 * kUStage + 128 <= kUSmem, "update stages");
+
+__global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64_t ld, int n, int k, int kb, int* err) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_fail;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = k + kb + blockIdx.y * kUM;          // first row of the tile
+  const int c0 = k + kb + blockIdx.x * (kUN / 2);    // first complex column of the tile
+  float* af = reinterpret_cast<float*>(a);
+  const int64_t ldf = 2 * ld;
+  if (tid == 0) {
+    s_fail = 0;
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&taddr_s, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = taddr_s;
+  const uint32_t idesc = tc::idesc_tf32(kUM, kUN);
+  const int n_stages = (2 * kb + kUK - 1) / kUK;
+  const int arow = tid >> 1, ahalf = tid & 1;   // A: row, 8 of the stage's 16 reals
+  const int brow = tid >> 5, bcol = tid & 31;   // B: panel row of the stage, columns bcol, bcol + 32
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&s_fail) != 0; };
+  // a stage's global values, loaded one stage ahead (in flight across the barrier and the
+  // MMA issue of the stage before)
+  float av[8];
+  cpx<float> bv[2];
+  auto load_stage = [&](int st) {
+    const int R = r0 + arow;
+    const int f0 = kUK * st + 8 * ahalf;
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      float2 x = make_float2(0.f, 0.f);
+      if (R < n && f0 + i < 2 * kb) x = __ldcg(reinterpret_cast<const float2*>(af + (int64_t)R * ldf + 2 * (int64_t)k + f0 + i));
+      av[i] = x.x;
+      av[i + 1] = x.y;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = bcol + 32 * u, c = (kUK / 2) * st + brow;
+      float2 x = make_float2(0.f, 0.f);
+      if (c < kb && c0 + j < n) x = __ldcg(reinterpret_cast<const float2*>(a + (int64_t)(k + c) * ld + c0 + j));
+      bv[u] = mk(x.x, x.y);
+    }
+  };
+  load_stage(0);
+  uint32_t n_issued = 0;
+  for (int st = 0; st < n_stages; ++st) {
+    const int buf = st & 1;
+    float* Ahi = reinterpret_cast<float*>(base + buf * kUStage);
+    float* Alo = Ahi + kUM * kUK;
+    float* Bhi = Alo + kUM * kUK;
+    float* Blo = Bhi + kUN * kUK;
+    if (st >= 2) {
+      // the MMAs of stage st - 2 read this buffer: one lane per warp polls, the others wait
+      if (lane == 0 && !failed() && !tc::mbar_wait(&mbar[buf], ((st - 2) >> 1) & 1, kTcPolls)) atomicOr(&s_fail, 1);
+      __syncwarp();
+    }
+    {
+      // A: reals [16 st + 8 ahalf, + 8) of row r0 + arow of L21 (zero outside)
+      float h[8], l[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) tf32_split(av[i], h[i], l[i]);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint32_t off = tc::kmajor_offset(arow, 8 * ahalf + 4 * q, kUK) / 4;
+        *reinterpret_cast<float4*>(Ahi + off) = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        *reinterpret_cast<float4*>(Alo + off) = make_float4(l[4 * q], l[4 * q + 1], l[4 * q + 2], l[4 * q + 3]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      // B: U12 entry (panel column 8 st + brow, tile column bcol + 32 u), four reals of B'^T
+      const int j = bcol + 32 * u;
+      float h0, l0, h1, l1;
+      tf32_split(bv[u].re, h0, l0);
+      tf32_split(bv[u].im, h1, l1);
+      const uint32_t o0 = tc::kmajor_offset(2 * j, 2 * brow, kUK) / 4;
+      const uint32_t o1 = tc::kmajor_offset(2 * j + 1, 2 * brow, kUK) / 4;
+      *reinterpret_cast<float2*>(Bhi + o0) = make_float2(h0, -h1);
+      *reinterpret_cast<float2*>(Blo + o0) = make_float2(l0, -l1);
+      *reinterpret_cast<float2*>(Bhi + o1) = make_float2(h1, h0);
+      *reinterpret_cast<float2*>(Blo + o1) = make_float2(l1, l0);
+    }
+    if (st + 1 < n_stages) load_stage(st + 1);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && !failed()) {
+      tc::fence_after_sync();
+      const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll
+      for (int s2 = 0; s2 < kUK / 8; ++s2) {
+        const uint32_t ko = s2 * 256;
+        const uint64_t dah = tc::sdesc(ah + ko, 128, kUSbo), dal = tc::sdesc(al + ko, 128, kUSbo);
+        const uint64_t dbh = tc::sdesc(bh + ko, 128, kUSbo), dbl = tc::sdesc(bl + ko, 128, kUSbo);
+        const uint32_t accf = (st > 0 || s2 > 0) ? 1u : 0u;
+        tc::mma_tf32(tmem + kUN, dah, dbl, idesc, accf);
+        tc::mma_tf32(tmem + kUN, dal, dbh, idesc, 1u);
+        tc::mma_tf32(tmem, dah, dbh, idesc, accf);
+      }
+      tc::mma_commit(&mbar[buf]);
+      ++n_issued;
+    }
+  }
+  // this thread's row segment of A22 (warp w: tensor-memory lanes 32 (w mod 4).., real
+  // columns 64 (w / 4)..), read while the last products run; the tile is this CTA's alone
+  const int lq = warp & 3, ch = warp >> 2;
+  const int R = r0 + 32 * lq + lane;
+  const int jc0 = c0 + 32 * ch;                 // first complex column of the segment
+  float2 cz[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    cz[i] = (R < n && jc0 + i < n) ? __ldcg(reinterpret_cast<const float2*>(af + (int64_t)R * ldf + 2 * (int64_t)(jc0 + i)))
+                                   : make_float2(0.f, 0.f);
+  // the last commit covers every MMA of the CTA
+  if (tid == 0 && !failed() && n_stages > 0) {
+    const int last = n_stages - 1;
+    if (!tc::mbar_wait(&mbar[last & 1], (last >> 1) & 1, kTcPolls)) atomicOr(&s_fail, 1);
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  if (!failed()) {
+    const uint32_t tl = (uint32_t)(32 * lq) << 16;
+#pragma unroll
+    for (int cb = 0; cb < 64; cb += 16) {
+      const int col = 64 * ch + cb;
+      float v[16], w[16];
+      tc::tmem_ld16x2(tmem + tl + (uint32_t)col, tmem + tl + (uint32_t)(kUN + col), v, w);
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const int e = (cb + i) / 2;              // complex column within the segment
+        cz[e].x -= v[i] + w[i];
+        cz[e].y -= v[i + 1] + w[i + 1];
+      }
+    }
+    if (R < n) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (jc0 + i < n) *reinterpret_cast<float2*>(af + (int64_t)R * ldf + 2 * (int64_t)(jc0 + i)) = cz[i];
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 8);
+    // a bounded wait for the MMAs in flight before their tensor memory is freed
+    if (n_issued > 0) tc::mbar_wait(&mbar[(n_issued - 1) & 1], ((n_issued - 1) >> 1) & 1, kTcPolls);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
 // every panel's row moves on the right-hand side, in panel order (one block)
 template <class T>
 __global__ void lu_vector_moves_kernel(cpx<T>* x, int n, int n_panels, const int2* moves, const int* n_moves) {
@@ -640,6 +823,10 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
   if ((e = cudaFuncSetAttribute(lu_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem)) !=
       cudaSuccess)
     return e;
+  const bool tc_update = sizeof(T) == 4 && w.tc_update;
+  if (tc_update && (e = cudaFuncSetAttribute(lu_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kUSmem)) != cudaSuccess)
+    return e;
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<T>, kPanelThreads,
                                                          panel_smem0)) != cudaSuccess)
@@ -663,7 +850,15 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
     const int rest = n - k - kb;
     if (rest > 0) {
       lu_trsm_kernel<T><<<(rest + 31) / 32, 256, trsm_smem, s>>>(a, ld, n, k, kb);
-      lu_gemm_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, gemm_smem, s>>>(a, ld, n, k, kb);
+      if constexpr (sizeof(T) == 4) {
+        if (tc_update)
+          lu_gemm_tc_kernel<<<dim3((rest + kUN / 2 - 1) / (kUN / 2), (rest + kUM - 1) / kUM), 256, kUSmem, s>>>(
+              a, ld, n, k, kb, w.err);
+        else
+          lu_gemm_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, gemm_smem, s>>>(a, ld, n, k, kb);
+      } else {
+        lu_gemm_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, gemm_smem, s>>>(a, ld, n, k, kb);
+      }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -78,6 +78,36 @@ def test_lu_solve_against_numpy(torch_cuda, n, kind, mode):
     assert info["n"] == n and info["panel_width"] == 64
 
 
+@pytest.mark.parametrize("n", [200, 1030])
+def test_tensor_core_update_against_fp32_pipe(torch_cuda, n):
+    """The complex64 trailing updates on the tensor cores (the complex product as a real
+    GEMM, three TF32 products) against the same factorization with the updates on the FP32
+    pipe and against numpy: several 128-row by 64-column tiles, a ragged last panel and
+    ragged tiles (1030 = 16 x 64 + 6)."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    a = _matrix(n, 11 + n, "zero_diagonal")
+    b = np.random.default_rng(5 + n).standard_normal(n) + 1j * np.random.default_rng(6 + n).standard_normal(n)
+    ref = np.linalg.solve(a, b)
+    cond = np.linalg.cond(a)
+    xs, infos = {}, {}
+    for simt in (0, 1):
+        ctx = cfft.Context(0)
+        ctx.set_option(cfft.OPT_SOLVE_SIMT, simt)
+        z = torch.tensor(a, dtype=torch.complex64, device="cuda:0")
+        v = torch.tensor(b, dtype=torch.complex64, device="cuda:0")
+        xs[simt] = ctx.solve_reduced(z, v).cpu().numpy().astype(np.complex128)
+        infos[simt] = ctx.solve_info()
+    assert infos[0]["update_tc"] == 1 and infos[1]["update_tc"] == 0
+    eps = 6e-8
+    for simt in (0, 1):
+        err = np.abs(xs[simt] - ref).max() / np.abs(ref).max()
+        print("n", n, "simt", simt, "cond %.3g" % cond, "rel err %.3g" % err, "residual %.3g" % infos[simt]["residual"])
+        assert err < 50.0 * eps * cond * np.sqrt(n)
+    growth = 1.0 + np.linalg.norm(a, 2) * np.linalg.norm(ref) / np.linalg.norm(b)
+    assert infos[0]["residual"] < 50.0 * eps * np.sqrt(n) * growth
+
+
 def test_singular_matrix_is_reported(torch_cuda):
     torch = torch_cuda
     from paper_1404_7357_gb300 import cfft
