@@ -388,7 +388,7 @@ def fill_sample_pairs(pos, rot, seed=91):
     """Element pairs (test m, basis n) of every rotation class (rot[m], rot[n]) in
     {0, 90 deg}^2, spread over the distances the fill's table covers: one diagonal block,
     then for each distance bin one pair of each class, measured from ten anchor basis
-    elements of the class's basis rotation."""
+    elements of the class's basis rotation (bins the array does not reach are skipped)."""
     rot = np.asarray(rot)
     rng = np.random.default_rng(seed)
     pairs = [(int(np.flatnonzero(rot == 0)[0]),) * 2]
@@ -398,6 +398,8 @@ def fill_sample_pairs(pos, rot, seed=91):
             anchors = np.flatnonzero(rot == r_n)[:10]
             d = np.hypot(*(pos[:, None, :] - pos[None, anchors, :]).transpose(2, 0, 1))  # (A, anchors)
             cand = np.argwhere((d >= lo) & (d < hi) & (rot == r_m)[:, None])
+            if len(cand) == 0:   # a smaller array (profiling runs) may not reach the bin
+                continue
             k = rng.integers(len(cand))
             pairs.append((int(cand[k][0]), int(anchors[cand[k][1]])))
     return pairs

@@ -628,6 +628,10 @@ size_t fc_smem_bytes(int n_harm) {
          (size_t)2 * 128 * fc_kpad(n_harm) * 4 + 1024; // A head, tail + alignment
 }
 
+// staged table slice: [ab][qi][t] with 9 entries per (ab, qi), so that the reads of
+// consecutive ab (as consecutive threads make them) fall on distinct banks
+constexpr int kStgPitch = kFcTaps + 1;
+
 // The B operand of one stencil cell (table rows i0 .. i0 + 7 of one class table):
 // [ab][qi][t] staged in stg with coalesced loads (parity below row 0, zero past the
 // end), then written as TF32 head and tail in the K-major layout, column n = 2 (16 t +
@@ -655,7 +659,7 @@ __device__ __forceinline__ void fc_build_b(const cpx<float>* tab_cls, int n_rho,
         v = tab[((size_t)ab * nh + qi) * n_rho + r];
         if (neg && ((qi - q_max) & 1)) v = mk(-v.re, -v.im);
       }
-      stg[e] = v;
+      stg[(size_t)rest * kStgPitch + t] = v;
     }
     __syncthreads();
     // one 16-byte group per (column n, harmonics qi, qi + 1): consecutive threads take
@@ -668,7 +672,7 @@ __device__ __forceinline__ void fc_build_b(const cpx<float>* tab_cls, int n_rho,
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int qi = 2 * k4 + u;
-        const cpx<float> v = qi < nh ? stg[((size_t)ab * nh + qi) * kFcTaps + t] : mk(0.f, 0.f);
+        const cpx<float> v = qi < nh ? stg[((size_t)ab * nh + qi) * kStgPitch + t] : mk(0.f, 0.f);
         // column 2j (real part of D): (Re T, -Im T); column 2j + 1: (Im T, Re T)
         f[2 * u] = c ? v.im : v.re;
         f[2 * u + 1] = c ? v.re : -v.im;
