@@ -981,6 +981,7 @@ cfft_status check_fill_args(cfft_ctx* ctx, int n_el, const double* pos, const in
 
 struct BatchItemPlan {
   int n, taylor, series, n_active, K, D;
+  int na_need;   // angular samples the item's own spectra need (a power of two)
   int64_t P;
   double step, ds, beta_abs;
 };
@@ -1037,9 +1038,11 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     int lp = 1;
     while ((p.P % (2 * (int64_t)lp)) == 0 && 2 * lp <= l_common) lp *= 2;
     l_common = std::min(l_common, lp);
+    p.na_need = 0;
     if (ctx->opt[CFFT_OPT_N_ALPHA] <= 0) {
       double need = 2.0 * p.beta_abs * ctx->elem_radius + 2.0 * q_max + 32.0;
-      n_alpha = std::max(n_alpha, std::max(8, next_pow2((int)std::ceil(need))));
+      p.na_need = std::max(8, next_pow2((int)std::ceil(need)));
+      n_alpha = std::max(n_alpha, p.na_need);
     }
   }
   if (l_common < 1024) return fail(ctx, CFFT_ERR_ARG, "batch: sigma * n must be divisible by 1024");
@@ -1051,7 +1054,9 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
                     std::to_string(n_alpha) + ":" + std::to_string((size_t)tables) + ":" +
                     std::to_string(ctx->n_basis) + ":" + std::to_string(M) + ":" + std::to_string(bp_taps) + ":" +
                     std::to_string(bp_kern);
-  for (int i = 0; i < n_items; ++i) sig += ":" + std::to_string(ip[i].n) + "/" + std::to_string(ip[i].taylor) + "/" + std::to_string(ip[i].series);
+  for (int i = 0; i < n_items; ++i)
+    sig += ":" + std::to_string(ip[i].n) + "/" + std::to_string(ip[i].taylor) + "/" + std::to_string(ip[i].series) +
+           "/" + std::to_string(ip[i].na_need);
 
   // ---- element data in T (shared by all items)
   {
@@ -1136,6 +1141,17 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       }
     }
   }
+  // the tensor-core integrand at 256 angles for the items that need them and at 128 for
+  // the others (automatic angle count only): one launch per angle count and wave
+  std::vector<int> item_na(n_items, n_alpha);
+  IntegrandArgs<T> shape128 = shape_args;
+  shape128.n_alpha = 128;
+  bool split_na = false;
+  if constexpr (sizeof(T) == 4)
+    split_na = tc_b && n_alpha == 256 && ctx->opt[CFFT_OPT_N_ALPHA] <= 0 && integrand_tc_applies(shape128);
+  if (split_na)
+    for (int i = 0; i < n_items; ++i) item_na[i] = ip[i].na_need <= 128 ? 128 : 256;
+  const int jt128 = split_na ? integrand_tc_nodes(128) : jt;
   CFFT_CUDA(ctx->b_flag.ensure(2 * sizeof(int)), "alloc flag");
   CFFT_CUDA(cudaMemsetAsync(ctx->b_flag.p, 0, 2 * sizeof(int), st), "flag");
 
@@ -1157,7 +1173,9 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
     std::vector<int> cnodes((size_t)n_items * n_chunks);
     std::vector<int64_t> coff((size_t)n_items * n_chunks);
     struct FftBucket { int log2L; size_t f0, f1; int max_nout; };
-    struct WaveRanges { size_t c0, c1, i0, i1, f0, f1, b0, b1; std::vector<FftBucket> fb; };
+    // integrand blocks of a wave: [i0, im) at 128 angles when the counts are split, [im, i1)
+    // at n_alpha
+    struct WaveRanges { size_t c0, c1, i0, im, i1, f0, f1, b0, b1; std::vector<FftBucket> fb; };
     std::vector<WaveRanges> wr;
     int64_t cos_total = 0;
     int max_nodes = 0, max_seg = 0, max_nout = 0, max_active = 0, max_n_item = 0, zt_arrays = 1;
@@ -1210,7 +1228,15 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       li[i] = l;
     }
     for (const Wave& w : waves) {
-      WaveRanges r{cmap.size(), 0, imap.size(), 0, ftask.size(), 0, btask.size(), 0, {}};
+      WaveRanges r{cmap.size(), 0, imap.size(), 0, 0, ftask.size(), 0, btask.size(), 0, {}};
+      // the 128-angle items' integrand blocks first
+      for (int i = w.i0; i < w.i1; ++i)
+        if (item_na[i] != n_alpha)
+          for (int j0 = 0; j0 < items[i].n; j0 += jt128) imap.push_back(make_int2(i, j0));
+      r.im = imap.size();
+      for (int i = w.i0; i < w.i1; ++i)
+        if (item_na[i] == n_alpha)
+          for (int j0 = 0; j0 < items[i].n; j0 += jt) imap.push_back(make_int2(i, j0));
       int64_t node_off = 0, grid_off = 0;
       for (int i = w.i0; i < w.i1; ++i) {
         const cfft_batch_item& it = items[i];
@@ -1225,11 +1251,10 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
                              c_bif + node_off, c_gp + node_off, c_gr + node_off,
                              nullptr, nullptr, nullptr, nullptr, bp_es ? c_prec + node_off : nullptr};
         for (int j0 = 0; j0 < it.n; j0 += 256) cmap.push_back(make_int2(i, j0));
-        for (int j0 = 0; j0 < it.n; j0 += jt) imap.push_back(make_int2(i, j0));
         IntegrandArgs<T>& ia = hia[i];
         ia = IntegrandArgs<T>{};
         ia.n = it.n;
-        ia.n_alpha = n_alpha;
+        ia.n_alpha = item_na[i];
         ia.q_max = q_max;
         ia.n_cls = 1;
         ia.n_mbf = M;
@@ -1377,6 +1402,7 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
       shape += ',';
     };
     for (long long v : {(long long)L, (long long)rchunk, (long long)tform_b, (long long)tc_b, (long long)jt,
+                        (long long)split_na,
                         (long long)n_chunks, (long long)max_nodes, (long long)max_seg, (long long)max_nout,
                         (long long)max_active, (long long)max_n_item, (long long)cos_total,
                         (long long)zt_arrays})
@@ -1423,10 +1449,19 @@ cfft_status batch_impl(cfft_ctx* ctx, int n_items, const cfft_batch_item* items,
                              ctx->b_cmap.as<int2>() + r.c0, (int)(r.c1 - r.c0), st);
         ++launches;
         if constexpr (sizeof(T) == 4) {
-          if (tc_b)
-            e = launch_integrand_tc_batch(shape_args, ctx->b_iargs.as<IntegrandArgs<float>>(),
-                                          ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), st);
-          else
+          if (tc_b) {
+            e = cudaSuccess;
+            if (r.im > r.i0) {
+              e = launch_integrand_tc_batch(shape128, ctx->b_iargs.as<IntegrandArgs<float>>(),
+                                            ctx->b_imap.as<int2>() + r.i0, (int)(r.im - r.i0), st);
+              ++launches;
+            }
+            if (e == cudaSuccess && r.i1 > r.im)
+              e = launch_integrand_tc_batch(shape_args, ctx->b_iargs.as<IntegrandArgs<float>>(),
+                                            ctx->b_imap.as<int2>() + r.im, (int)(r.i1 - r.im), st);
+            else if (e == cudaSuccess)
+              --launches;   // no block at n_alpha in this wave
+          } else
             e = launch_integrand_batch<T>(shape_args, ctx->b_iargs.as<IntegrandArgs<T>>(),
                                           ctx->b_imap.as<int2>() + r.i0, (int)(r.i1 - r.i0), jt,
                                           ctx->n_mbf_pad, st);

@@ -98,6 +98,39 @@ def test_batch_graph_replay_tracks_new_parameters(torch_cuda):
     assert np.abs(tuned - second).max() < TOL["fp32"] * np.abs(second).max()
 
 
+def test_batch_per_item_angle_counts(torch_cuda):
+    """Automatic angle counts: the sweep runs the tensor-core integrand at 128 angles for
+    the items whose spectra need no more and at 256 for the others (one launch each); every
+    item against the single tabulation of that item, which chooses its own count."""
+    from paper_1404_7357_gb300 import cfft
+    el = workloads.patch_rooftops()
+    items = _items(6, seed=21)
+    items[0]["eps_r"], items[-1]["eps_r"] = 2.0, 10.0       # both ends of the substrate range
+    for it in (items[0], items[-1]):
+        kd = it["k0"] * np.sqrt(it["eps_r"])
+        it["beta_max"] = 5.0 * kd
+        step = it["beta_max"] / it["n"]
+        it["beta_p"] = round(1.3 * kd / step) * step
+        it["height"] = 6.0 * step
+    q_max, rho_max, n_rho = 16, 3.0, 256
+    ctx = cfft.Context(0)
+    ctx.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+    got = ctx.tabulate_batch(items, q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, graph=True).cpu().numpy()
+    counts = []
+    for i, it in enumerate(items):
+        c1 = cfft.Context(0)
+        c1.set_substrate(it["eps_r"], it["h"], it["k0"])
+        c1.set_mbf_spectra(np.stack([el.cx, el.cy], 1), el.direction, el.half_len, el.width, el.q)
+        c1.build_contour(it["n"], it["beta_max"], it["beta_p"], it["height"], -1)
+        c1.tabulate_reactions(q_max, rho_max, n_rho, cfft.CFFT_FP32_MIXED, 1)
+        ref = c1.copy_table(host=True).numpy()[0].astype(np.complex128)
+        counts.append(c1.info()["n_alpha"])
+        err = np.abs(got[i].astype(np.complex128) - ref).max() / np.abs(ref).max()
+        print("item", i, "eps", round(it["eps_r"], 2), "n_alpha", counts[-1], "rel err %.3g" % err)
+        assert err < 2e-6
+    assert 128 in counts and 256 in counts
+
+
 def test_batch_item_against_oracle(torch_cuda):
     from paper_1404_7357_gb300 import cfft
     el = workloads.patch_rooftops()
