@@ -676,8 +676,8 @@ def stage_flops(inf, wl):
 # DRAM bytes (read + write) per launch of each table kernel on the full patch-m4 workload,
 # from one ncu capture of the current kernel (None: changed since its last capture);
 # valid only for the default table sizes
-KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.332e6, "fft": 92.082e6 + 9.485e6,
-                     "backproject": 17.955e6 + 0.097e6}
+KERNEL_DRAM_BYTES = {"integrand": 1.528e6 + 14.413e6, "fft": 88.564e6 + 8.654e6,
+                     "backproject": 17.955e6 + 0.047e6}
 
 
 def pipe_peaks(peaks):
