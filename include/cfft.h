@@ -508,8 +508,7 @@ cfft_status cfft_synchronize(cfft_ctx* ctx);
  * them, or whose rho_max needs more grid than grid_half, returns
  * CFFT_ERR_ARG before any work is queued.
  * The first call on a device looks the scratch array's device address up
- * (with `device` made current for the call); make that first call before
- * any stream capture.  Every call reuses the same array and rewrites the
+ * (with `device` made current for the call).  Every call reuses the same array and rewrites the
  * entries it reads before reading them, so no call depends on what an
  * earlier one left there -- but two calls whose work overlaps on the GPU
  * (different streams, no ordering between them) race on the array.

@@ -1,8 +1,7 @@
 """cfft_backproject_static: the back-projection for callers that cannot allocate.
 
-A caller that captures work into a CUDA graph, lives inside an application
-that owns every device allocation, or runs a real-time loop cannot let the
-library call cudaMalloc.  This entry point keeps its scratch in a fixed
+A caller that lives inside an application that owns every device allocation,
+or runs a real-time loop, cannot let the library call cudaMalloc.  This entry point keeps its scratch in a fixed
 device array inside the library; the caller brings the transform grid and
 the output table.  Its result must match the table that cfft_tabulate_reactions
 produced from the same grid, on two calls in a row (the second call reuses
