@@ -137,7 +137,12 @@ typedef enum {
  *                2 where ES cannot run is CFFT_ERR_ARG
  *   SOLVE_SIMT   a value > 0 runs the complex64 LU's trailing matrix
  *                products (cfft_solve_reduced) on the FP32 pipe instead of
- *                the tensor cores */
+ *                the tensor cores
+ *   FFT_SUB_LEN  length L of the sub-FFTs of cfft_tabulate_reactions (the
+ *                transform of length P = sigma n is split into P / L
+ *                residue classes of its outputs, Eq. 23): a power of two in
+ *                64..16384 (64..8192 in FP64) dividing P, else CFFT_ERR_ARG
+ *                at the tabulation.  Default (<= 0): automatic */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -154,7 +159,8 @@ typedef enum {
   CFFT_OPT_FILL_REFINE = 12,
   CFFT_OPT_CONTOUR_SERIES = 13,
   CFFT_OPT_BP_KERNEL = 14,
-  CFFT_OPT_SOLVE_SIMT = 15
+  CFFT_OPT_SOLVE_SIMT = 15,
+  CFFT_OPT_FFT_SUB_LEN = 16
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`

@@ -17,7 +17,8 @@ CFFT_FP64 = 0
 CFFT_FP32_MIXED = 1
 (OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
  OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT, OPT_FILL_SIMT,
- OPT_FILL_REFINE, OPT_CONTOUR_SERIES, OPT_BP_KERNEL, OPT_SOLVE_SIMT) = range(16)
+ OPT_FILL_REFINE, OPT_CONTOUR_SERIES, OPT_BP_KERNEL, OPT_SOLVE_SIMT,
+ OPT_FFT_SUB_LEN) = range(17)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 

@@ -67,6 +67,8 @@ struct DevBuf {
   }
 };
 
+constexpr int kNumOptions = CFFT_OPT_FFT_SUB_LEN + 1;
+
 }  // namespace
 
 struct cfft_ctx {
@@ -93,8 +95,8 @@ struct cfft_ctx {
   int n = 0, taylor_req = -1;
   double beta_max = 0, beta_p = 0, height = 0;
   // options (<= 0: automatic) and the options the last table was made with
-  double opt[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double tab_opt[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double opt[kNumOptions] = {};
+  double tab_opt[kNumOptions] = {};
   // table
   bool has_table = false;
   int q_max = 0, n_rho = 0, cls_stored = 1, cls_computed = 1, fill_taps = 8;
@@ -347,6 +349,14 @@ cfft_status tabulate_impl(cfft_ctx* ctx, int n_rho, double rho_max, DevBuf& dst,
   while ((P % (2 * (int64_t)L)) == 0 && 2 * L <= l_max) L *= 2;
   if (L < 64) return fail(ctx, CFFT_ERR_ARG, "sigma * n must be divisible by 64");
   while (L > 256 && (int64_t)series * (P / L) < 2 * ctx->sm_count) L /= 2;
+  const double l_req = ctx->opt[CFFT_OPT_FFT_SUB_LEN];
+  if (l_req > 0) {
+    const int lr = (int)l_req;
+    if ((double)lr != l_req || lr < 64 || lr > l_max || (lr & (lr - 1)) || P % lr != 0)
+      return fail(ctx, CFFT_ERR_ARG, "FFT_SUB_LEN must be a power of two in 64.." + std::to_string(l_max) +
+                                         " dividing sigma * n");
+    L = lr;
+  }
   int log2L = 0;
   while ((1 << log2L) < L) ++log2L;
   const int D = (int)(P / L);
@@ -796,7 +806,7 @@ cfft_status ensure_fill_table_t(cfft_ctx* ctx) {
   const double rho_f = d_f * (double)(n_f - 1);
   if (own) {
     // the same tabulation on the fill's grid, with the options the table was made with
-    double saved[16];
+    double saved[kNumOptions];
     std::memcpy(saved, ctx->opt, sizeof(saved));
     std::memcpy(ctx->opt, ctx->tab_opt, sizeof(saved));
     cfft_status stt = tabulate_impl<T>(ctx, (int)n_f, rho_f, ctx->d_ftable, false);
@@ -1789,7 +1799,7 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
 
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
-  if ((int)key < 0 || (int)key > 15) return fail(ctx, CFFT_ERR_ARG, "unknown option");
+  if ((int)key < 0 || (int)key >= kNumOptions) return fail(ctx, CFFT_ERR_ARG, "unknown option");
   ctx->opt[(int)key] = value;
   if (key == CFFT_OPT_FILL_REFINE) ctx->fill_r = 0;   // decided again at the next fill
   return CFFT_OK;

@@ -88,3 +88,29 @@ def test_chebyshev_error_falls_with_degree(torch_cuda):
     assert all(b < a for a, b in zip(errs, errs[1:]))
     # remainder bound at degree 12, a = height rho_max / 2 = 1.37: 2 e^a I_13(a) = 8e-12
     assert errs[-1] < 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sub_fft_length_option(torch_cuda, precision):
+    """Eq. 23's split of the length-P transform into P / L residue classes of its outputs
+    gives the same grid for every sub-FFT length L (cfft_set_option FFT_SUB_LEN); lengths
+    that are not powers of two, too short or too long, or not dividing P are refused."""
+    from paper_1404_7357_gb300 import cfft
+    if precision == "fp64":
+        wl = workloads.strip_fp64(n=1024, n_rho=256, rho_max=10.0)
+    else:
+        wl = cc.small_patch("fp32", n=1024, n_rho=256, rho_max=4.0, q_max=3)
+    ref, _, _ = cc.oracle_table(wl)
+    grid_tol = 1e-11 if precision == "fp64" else 2e-5
+    for sub_len in (64, 512, 4096):
+        ctx, got = cc.gpu_table(wl, options={cfft.OPT_FFT_SUB_LEN: sub_len, cfft.OPT_BP_KERNEL: 1})
+        assert ctx.info()["sub_len"] == sub_len
+        ge, te = _grid_error(ctx, wl), cc.rel_err_per_pair(got, ref).max()
+        print(precision, "L =", sub_len, "grid", ge, "table", te)
+        assert ge < grid_tol and te < TOL[precision]
+    prec = cfft.CFFT_FP64 if precision == "fp64" else cfft.CFFT_FP32_MIXED
+    for bad in (96, 32, 32768, 65536):
+        ctx = cc.gpu_context(wl, options={cfft.OPT_FFT_SUB_LEN: bad})
+        with pytest.raises(cfft.CfftError) as ei:
+            ctx.tabulate_reactions(wl.q_max, wl.rho_max, wl.n_rho, prec, 1)
+        assert ei.value.status == 1
