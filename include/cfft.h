@@ -142,7 +142,11 @@ typedef enum {
  *                transform of length P = sigma n is split into P / L
  *                residue classes of its outputs, Eq. 23): a power of two in
  *                64..16384 (64..8192 in FP64) dividing P, else CFFT_ERR_ARG
- *                at the tabulation.  Default (<= 0): automatic */
+ *                at the tabulation.  Default (<= 0): automatic
+ *   SOLVE_GRID_PANEL  a value > 0 runs every LU panel of cfft_solve_reduced
+ *                as a cooperative launch over the grid (a bounded barrier
+ *                in global memory per column) instead of on one
+ *                thread-block cluster for panels of at most 2048 rows */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
   CFFT_OPT_SIGMA = 1,
@@ -160,7 +164,8 @@ typedef enum {
   CFFT_OPT_CONTOUR_SERIES = 13,
   CFFT_OPT_BP_KERNEL = 14,
   CFFT_OPT_SOLVE_SIMT = 15,
-  CFFT_OPT_FFT_SUB_LEN = 16
+  CFFT_OPT_FFT_SUB_LEN = 16,
+  CFFT_OPT_SOLVE_GRID_PANEL = 17
 } cfft_option;
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -601,9 +606,14 @@ cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const vo
  *         refinement in float64 against z: x += LU^-1 (v - z x) until the
  *         correction falls below float64 resolution or the residual stops
  *         falling (at most 30 steps).
- * The factorization runs in panels of 64 columns: one cooperative launch per
- * panel (pivot search and elimination, one bounded grid barrier per column),
- * the panel's row moves applied to the whole matrix, a triangular solve for
+ * The factorization runs in panels of 64 columns: one launch per panel (pivot
+ * search and elimination, one barrier per column: the hardware barrier of one
+ * thread-block cluster of 16 or 8 CTAs, candidates and pivot rows read from
+ * the peers' shared memory, for panels of at most 2048 rows that fit that
+ * cluster's shared memory; otherwise a cooperative launch over the grid with
+ * a bounded barrier in global memory), the panel's row moves applied to the
+ * whole matrix, a
+ * triangular solve for
  * the panel's rows and a complex matrix product for the trailing matrix.  In
  * complex64 that product runs on the tensor cores (three TF32 products, FP32
  * accumulation) unless the option SOLVE_SIMT is > 0, which keeps it on the
@@ -618,10 +628,11 @@ cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, int64_t ld, 
 /* Diagnostics of the last cfft_solve_reduced: factorization and solve times
  * (ms, CUDA events on the context stream; the solve includes refinement),
  * relative residual, order n, mode, refinement steps (mode 1), panel width,
- * and update_tc = 1 when the trailing updates ran on the tensor cores. */
+ * update_tc = 1 when the trailing updates ran on the tensor cores, the number
+ * of panels that ran on one thread-block cluster and its CTA count (0: none). */
 typedef struct {
   double ms_factor, ms_solve, residual;
-  int n, mode, refinements, panel_width, update_tc;
+  int n, mode, refinements, panel_width, update_tc, cluster_panels, panel_cluster;
 } cfft_solve_info;
 cfft_status cfft_get_solve_info(const cfft_ctx* ctx, cfft_solve_info* info);
 

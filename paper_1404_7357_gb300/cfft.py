@@ -18,7 +18,7 @@ CFFT_FP32_MIXED = 1
 (OPT_N_ALPHA, OPT_SIGMA, OPT_BP_TAPS, OPT_FILL_TAPS, OPT_ALPHA_MARGIN, OPT_CHECK_FINITE,
  OPT_DERIVATIVES, OPT_BP_GATHER, OPT_FILL_BLOCK, OPT_SPECTRA_SIMT, OPT_BP_SIMT, OPT_FILL_SIMT,
  OPT_FILL_REFINE, OPT_CONTOUR_SERIES, OPT_BP_KERNEL, OPT_SOLVE_SIMT,
- OPT_FFT_SUB_LEN) = range(17)
+ OPT_FFT_SUB_LEN, OPT_SOLVE_GRID_PANEL) = range(18)
 STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM",
           4: "CFFT_ERR_CUDA", 5: "CFFT_ERR_NUMERIC", 6: "CFFT_ERR_TIMEOUT"}
 
@@ -81,7 +81,8 @@ class CartesianInfo(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("ms_factor", "ms_solve", "residual")] + \
-               [(n, ctypes.c_int) for n in ("n", "mode", "refinements", "panel_width", "update_tc")]
+               [(n, ctypes.c_int) for n in ("n", "mode", "refinements", "panel_width", "update_tc",
+                                          "cluster_panels", "panel_cluster")]
 
 
 def _load():

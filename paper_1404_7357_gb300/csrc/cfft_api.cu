@@ -67,7 +67,7 @@ struct DevBuf {
   }
 };
 
-constexpr int kNumOptions = CFFT_OPT_FFT_SUB_LEN + 1;
+constexpr int kNumOptions = CFFT_OPT_SOLVE_GRID_PANEL + 1;
 
 }  // namespace
 
@@ -138,7 +138,7 @@ struct cfft_ctx {
   // dense LU of the reduced system: the factored copy, work arrays, vectors, timing
   DevBuf lu_a, lu_moves, lu_nmoves, lu_cand_v, lu_cand_r, lu_cand_d, lu_bar, lu_err, lu_x, lu_y, lu_x64, lu_r, lu_sums;
   cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};
-  int lu_diag[3] = {0, 0, 0};
+  int lu_diag[5] = {0, 0, 0, 0, 0};
   cfft_solve_info solve_info{};
   // the 2-D Cartesian C-FFT table and its work buffers
   DevBuf c_tab, c_work, c_work2, c_im, c_gx, c_gy, c_flag;
@@ -2215,6 +2215,7 @@ cfft_status lu_work(cfft_ctx* ctx, int n, LuWork* w) {
   w->bar = ctx->lu_bar.as<unsigned>();
   w->err = ctx->lu_err.as<int>();
   w->tc_update = ctx->opt[CFFT_OPT_SOLVE_SIMT] > 0 ? 0 : 1;
+  w->panel_cluster = ctx->opt[CFFT_OPT_SOLVE_GRID_PANEL] > 0 ? 0 : 1;
   return CFFT_OK;
 }
 
@@ -2346,6 +2347,8 @@ extern "C" cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, i
   in.refinements = steps;
   in.panel_width = lu_panel_width();
   in.update_tc = (w.tc_update && (!complex128 || mode == 1)) ? 1 : 0;   // complex64 factorization
+  in.cluster_panels = w.diag[3];
+  in.panel_cluster = w.diag[3] > 0 ? w.diag[4] : 0;
   if (!std::isfinite(in.residual)) return fail(ctx, CFFT_ERR_NUMERIC, "solve: non-finite solution");
   return CFFT_OK;
 }

@@ -437,8 +437,10 @@ struct LuWork {
   unsigned* bar;       // [panels] grid-barrier counters
   int* err;            // bit 1: barrier wait ran out; bit 2: zero pivot; bit 3: a tensor-core
                        // wait of the trailing update ran out
-  int* diag;           // host: [3] panel grid, resident CTAs per SM, shared bytes of the last panel
+  int* diag;           // host: [5] panel grid, resident CTAs per SM, shared bytes of the last grid
+                       // panel; panels run on one cluster, CTAs per cluster (0: none)
   int tc_update;       // complex64: the trailing update on the tensor cores
+  int panel_cluster;   // 1: panels whose rows fit one cluster's shared memory run there
 };
 int lu_panel_width();
 // the largest order whose panels fit the panel CTAs' shared memory on `sms` SMs

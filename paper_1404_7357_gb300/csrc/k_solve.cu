@@ -5,12 +5,17 @@
 // "Solving time"); this is that step, dense, on one GPU.
 //
 // LU (right-looking, row-major, panels of kNb columns):
-//   panel    one cooperative launch over the panel's rows: per column, every CTA
-//            proposes its largest |re| + |im| among the rows not yet chosen, a
-//            bounded grid barrier, every CTA takes the same pivot (ties: lowest
-//            row), reads the pivot row and eliminates the column from its own
-//            rows.  Pivoting is logical: rows stay where they are and the chosen
-//            rows are recorded; one barrier per column.
+//   panel    one launch over the panel's rows: per column, every CTA proposes its
+//            largest |re| + |im| among the rows not yet chosen, a barrier, every
+//            CTA takes the same pivot (ties: lowest row), reads the pivot row and
+//            eliminates the column from its own rows.  Pivoting is logical: rows
+//            stay where they are and the chosen rows are recorded; one barrier per
+//            column.  A panel of at most 2048 rows (that fits the shared memory
+//            of one thread-block cluster, 16 CTAs, else 8) runs on the cluster:
+//            the CTAs exchange candidates and the pivot row through distributed
+//            shared memory with the cluster's hardware barrier.  Longer panels
+//            run cooperatively over the grid, with a bounded grid barrier in
+//            global memory.
 //   moves    the panel's pivot rows go to rows k..k+kb-1 and the rows they
 //            displace to the vacated places, as a list of (source, destination)
 //            row moves applied to every column of the matrix.
@@ -23,7 +28,10 @@
 // CTAs each solve the small diagonal block (one warp) and update their rows.
 //
 // Every grid-barrier wait is bounded: a wait that runs out sets an error bit,
-// and every CTA leaves the panel (the host then returns CFFT_ERR_TIMEOUT).
+// and every CTA leaves the panel (the host then returns CFFT_ERR_TIMEOUT).  The
+// cluster barrier is the hardware's own: every CTA of the cluster is resident by
+// construction, and every CTA takes every barrier (the pivot, and so any early
+// stop, is the same decision in all of them).
 #include <algorithm>
 
 #include "cfft_common.cuh"
@@ -95,6 +103,36 @@ __device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int o
     v = ov;
     i = oi;
   }
+}
+
+// the panel's row moves from its pivots (one thread): rows k+j <- pivot j; the rows of
+// [k, k+kb) that were not chosen go to the places the chosen rows outside that range
+// leave free, both in increasing order
+template <class T>
+__device__ void panel_record_moves(const PanelArgs<T>& p, const int* s_piv) {
+  const int kb = p.kb;
+  int nm = 0, nd = 0, nv = 0;
+  int displaced[kNb], vacated[kNb];
+  for (int j = 0; j < kb; ++j) {
+    if (s_piv[j] != p.k + j) p.moves[nm++] = make_int2(s_piv[j], p.k + j);
+    if (s_piv[j] >= p.k + kb) vacated[nv++] = s_piv[j];
+  }
+  for (int r = p.k; r < p.k + kb; ++r) {
+    bool taken = false;
+    for (int j = 0; j < kb; ++j) taken = taken || s_piv[j] == r;
+    if (!taken) displaced[nd++] = r;
+  }
+  // nd == nv: both count the pivots from outside [k, k+kb)
+  for (int t = 0; t < nd && t < nv; ++t) {
+    int m = t;
+    for (int u = t + 1; u < nv; ++u)
+      if (vacated[u] < vacated[m]) m = u;
+    const int tmp = vacated[t];
+    vacated[t] = vacated[m];
+    vacated[m] = tmp;
+    p.moves[nm++] = make_int2(displaced[t], vacated[t]);
+  }
+  *p.n_moves = nm;
 }
 
 // One panel of kb columns on rows k..n-1.  Each CTA holds its slice of rows in shared
@@ -228,32 +266,170 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
   }
   for (int e = tid; e < nr * kb; e += blockDim.x)
     p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb] = rows[e];
-  if (g == 0 && tid == 0) {
-    // rows k+j <- pivot j; the rows of [k, k+kb) that were not chosen go to the places the
-    // chosen rows outside that range leave free, both in increasing order
-    int nm = 0, nd = 0, nv = 0;
-    int displaced[kNb], vacated[kNb];
-    for (int j = 0; j < kb; ++j) {
-      if (s_piv[j] != p.k + j) p.moves[nm++] = make_int2(s_piv[j], p.k + j);
-      if (s_piv[j] >= p.k + kb) vacated[nv++] = s_piv[j];
+  if (g == 0 && tid == 0) panel_record_moves(p, s_piv);
+}
+
+// ---- the panel inside one thread-block cluster (distributed shared memory)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of all CTAs of the cluster; orders this CTA's shared-memory writes before
+// the peers' reads after the barrier
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the address of `p` (this CTA's shared memory) in the shared memory of cluster CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_cluster_s32(uint32_t a) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ cpx<float> ld_cluster_cpx(const cpx<float>*, uint32_t a) {
+  float x, y;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a) : "memory");
+  return mk(x, y);
+}
+__device__ __forceinline__ cpx<double> ld_cluster_cpx(const cpx<double>*, uint32_t a) {
+  double x, y;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a) : "memory");
+  return mk(x, y);
+}
+
+// One panel of kb columns on rows k..n-1, the grid being one cluster of G CTAs.  Each CTA
+// holds its slice of rows in shared memory for the whole panel.  Per column it posts its
+// best candidate (value, row) in its own shared memory, the cluster barrier, then every
+// CTA reads the G candidates and takes the same pivot, and reads the pivot row from the
+// owner's shared memory.  The candidate slots are double-buffered by column: a CTA writes
+// the slot of column j + 2 only after the barrier of column j + 1, which every CTA passes
+// after its reads of column j.  A chosen row is never written again in the panel, so the
+// pivot row is read while its owner eliminates its other rows.  A last cluster barrier
+// keeps every CTA's shared memory in place until no peer reads it.
+template <class T>
+__global__ void __launch_bounds__(kPanelThreads) lu_panel_cluster_kernel(PanelArgs<T> p) {
+  constexpr int kWarps = kPanelThreads / 32;
+  const int G = gridDim.x, g = (int)cluster_rank(), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int R = p.n - p.k, kb = p.kb;
+  const int per = (R + G - 1) / G;
+  const int lo = p.k + min(g * per, R), hi = p.k + min((g + 1) * per, R), nr = hi - lo;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* rows = reinterpret_cast<cpx<T>*>(smem_raw);                       // [per][kb]
+  unsigned char* chosen = smem_raw + (size_t)per * kb * sizeof(cpx<T>);     // [per]
+  __shared__ cpx<T> prow[kNb];
+  __shared__ double wv[kWarps];
+  __shared__ int wi[kWarps];
+  __shared__ int s_piv[kNb];
+  __shared__ double s_cv[2];   // this CTA's candidate of the column (value), by column parity
+  __shared__ int s_cr[2];      // (row; INT_MAX: none)
+  __shared__ int s_p, s_w;
+  for (int e = tid; e < nr * kb; e += blockDim.x)
+    rows[e] = p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb];
+  for (int i = tid; i < per; i += blockDim.x) chosen[i] = 0;
+  __syncthreads();
+  bool ok = true;
+  for (int j = 0; j < kb; ++j) {
+    const int buf = j & 1;
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < nr; i += blockDim.x) {
+      if (chosen[i]) continue;
+      const cpx<T> v = rows[i * kb + j];
+      argmax_merge(best, bi, fabs((double)v.re) + fabs((double)v.im), i);
     }
-    for (int r = p.k; r < p.k + kb; ++r) {
-      bool taken = false;
-      for (int j = 0; j < kb; ++j) taken = taken || s_piv[j] == r;
-      if (!taken) displaced[nd++] = r;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+      argmax_merge(best, bi, __shfl_xor_sync(0xffffffffu, best, off), __shfl_xor_sync(0xffffffffu, bi, off));
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bi;
     }
-    // nd == nv: both count the pivots from outside [k, k+kb)
-    for (int t = 0; t < nd && t < nv; ++t) {
-      int m = t;
-      for (int u = t + 1; u < nv; ++u)
-        if (vacated[u] < vacated[m]) m = u;
-      const int tmp = vacated[t];
-      vacated[t] = vacated[m];
-      vacated[m] = tmp;
-      p.moves[nm++] = make_int2(displaced[t], vacated[t]);
+    __syncthreads();
+    if (tid == 0) {
+      double v = wv[0];
+      int r = wi[0];
+      for (int w = 1; w < kWarps; ++w) argmax_merge(v, r, wv[w], wi[w]);
+      s_cv[buf] = v;
+      s_cr[buf] = r < nr ? lo + r : 0x7fffffff;
     }
-    *p.n_moves = nm;
+    cluster_sync_all();
+    // the pivot: best candidate over the cluster (the same choice in every CTA)
+    if (warp == 0) {
+      double v = -1.0;
+      int r = 0x7fffffff, w = -1;
+      if (lane < G) {
+        v = ld_cluster_f64(cluster_addr(&s_cv[buf], lane));
+        r = ld_cluster_s32(cluster_addr(&s_cr[buf], lane));
+        w = lane;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int orow = __shfl_xor_sync(0xffffffffu, r, off), ow = __shfl_xor_sync(0xffffffffu, w, off);
+        if (ov > v || (ov == v && orow < r)) {
+          v = ov;
+          r = orow;
+          w = ow;
+        }
+      }
+      if (lane == 0) {
+        if (!(v > 0.0) && g == 0) atomicOr(p.err, 4);
+        const bool valid = r >= p.k && r < p.n && w >= 0;
+        s_p = valid ? r : -1;
+        s_w = valid ? w : -1;
+      }
+    }
+    __syncthreads();
+    const int pr = s_p;
+    if (pr < 0) {   // no row left (cannot happen with n - k >= kb): every CTA stops here
+      if (tid == 0 && g == 0) atomicOr(p.err, 4);
+      ok = false;
+      break;
+    }
+    {
+      // the pivot row's entries j.. from its owner (its local row pr - lo_w, lo_w >= k)
+      const int w = s_w;
+      const int lrow = pr - (p.k + min(w * per, R));
+      const cpx<T>* src = rows + (size_t)lrow * kb + j;
+      for (int t = tid; t < kb - j; t += blockDim.x) prow[t] = ld_cluster_cpx(src, cluster_addr(src + t, w));
+    }
+    if (tid == 0) {
+      if (pr >= lo && pr < hi) chosen[pr - lo] = 1;
+      s_piv[j] = pr;
+    }
+    __syncthreads();
+    const cpx<T> inv = crecip(prow[0]);
+    for (int i = tid; i < nr; i += blockDim.x)
+      if (!chosen[i]) rows[i * kb + j] = rows[i * kb + j] * inv;
+    __syncthreads();
+#pragma unroll 4
+    for (int i = warp; i < nr; i += kWarps) {
+      if (chosen[i]) continue;
+      cpx<T>* row = rows + i * kb + j;
+      const cpx<T> l = row[0];
+      const cpx<T> ml = mk(-l.re, -l.im);
+      for (int t = 1 + lane; t < kb - j; t += 32) cmac(row[t], ml, prow[t]);
+    }
+    __syncthreads();
   }
+  if (ok) {
+    for (int e = tid; e < nr * kb; e += blockDim.x)
+      p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb] = rows[e];
+    if (g == 0 && tid == 0) panel_record_moves(p, s_piv);
+  } else if (tid == 0 && g == 0) {
+    *p.n_moves = 0;   // the panel stopped: no row moves for it
+  }
+  cluster_sync_all();
 }
 
 // the panel's row moves on columns [0, n_cols): all sources read before any destination
@@ -402,6 +578,8 @@ constexpr size_t kUStage = (size_t)2 * kUM * kUK * 4 + (size_t)2 * kUN * kUK * 4
 // 2 x 256 tensor-memory columns then always fit)
 constexpr size_t kUSmem = 96 * 1024;
 static_assert(2 * kUStage + 128 <= kUSmem, "update stages");
+constexpr int kUPitch = kUN + 4;                 // row pitch (floats) of the staged product tile
+static_assert((size_t)kUM * kUPitch * 4 + 128 <= kUSmem, "staged product tile");
 
 __global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64_t ld, int n, int k, int kb, int* err) {
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -430,22 +608,22 @@ __global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64
   const uint32_t tmem = taddr_s;
   const uint32_t idesc = tc::idesc_tf32(kUM, kUN);
   const int n_stages = (2 * kb + kUK - 1) / kUK;
-  const int arow = tid >> 1, ahalf = tid & 1;   // A: row, 8 of the stage's 16 reals
+  // A: rows (tid >> 3) + 32 q, q < 4, reals 2 p, 2 p + 1 of the stage's 16 (p = tid & 7): the
+  // eight lanes of a row read its 64 bytes of the stage together
+  const int arow = tid >> 3, apiece = tid & 7;
   const int brow = tid >> 5, bcol = tid & 31;   // B: panel row of the stage, columns bcol, bcol + 32
   auto failed = [&]() { return *reinterpret_cast<volatile int*>(&s_fail) != 0; };
   // a stage's global values, loaded one stage ahead (in flight across the barrier and the
   // MMA issue of the stage before)
-  float av[8];
+  float2 av[4];
   cpx<float> bv[2];
   auto load_stage = [&](int st) {
-    const int R = r0 + arow;
-    const int f0 = kUK * st + 8 * ahalf;
+    const int f = kUK * st + 2 * apiece;   // even, as is 2 kb: both reals are in range or neither
 #pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-      float2 x = make_float2(0.f, 0.f);
-      if (R < n && f0 + i < 2 * kb) x = __ldcg(reinterpret_cast<const float2*>(af + (int64_t)R * ldf + 2 * (int64_t)k + f0 + i));
-      av[i] = x.x;
-      av[i + 1] = x.y;
+    for (int q = 0; q < 4; ++q) {
+      const int R = r0 + arow + 32 * q;
+      av[q] = (R < n && f < 2 * kb) ? __ldcg(reinterpret_cast<const float2*>(af + (int64_t)R * ldf + 2 * (int64_t)k + f))
+                                    : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -468,17 +646,15 @@ __global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64
       if (lane == 0 && !failed() && !tc::mbar_wait(&mbar[buf], ((st - 2) >> 1) & 1, kTcPolls)) atomicOr(&s_fail, 1);
       __syncwarp();
     }
-    {
-      // A: reals [16 st + 8 ahalf, + 8) of row r0 + arow of L21 (zero outside)
-      float h[8], l[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tf32_split(av[i], h[i], l[i]);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const uint32_t off = tc::kmajor_offset(arow, 8 * ahalf + 4 * q, kUK) / 4;
-        *reinterpret_cast<float4*>(Ahi + off) = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-        *reinterpret_cast<float4*>(Alo + off) = make_float4(l[4 * q], l[4 * q + 1], l[4 * q + 2], l[4 * q + 3]);
-      }
+    for (int q = 0; q < 4; ++q) {
+      // A: reals 16 st + 2 apiece, + 1 of row r0 + arow + 32 q of L21 (zero outside)
+      float h0, l0, h1, l1;
+      tf32_split(av[q].x, h0, l0);
+      tf32_split(av[q].y, h1, l1);
+      const uint32_t off = tc::kmajor_offset(arow + 32 * q, 2 * apiece, kUK) / 4;
+      *reinterpret_cast<float2*>(Ahi + off) = make_float2(h0, h1);
+      *reinterpret_cast<float2*>(Alo + off) = make_float2(l0, l1);
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -515,16 +691,16 @@ __global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64
       ++n_issued;
     }
   }
-  // this thread's row segment of A22 (warp w: tensor-memory lanes 32 (w mod 4).., real
-  // columns 64 (w / 4)..), read while the last products run; the tile is this CTA's alone
-  const int lq = warp & 3, ch = warp >> 2;
-  const int R = r0 + 32 * lq + lane;
-  const int jc0 = c0 + 32 * ch;                 // first complex column of the segment
+  // A22's tile, read while the last products run (the tile is this CTA's alone): warp w
+  // takes tile rows 16 w .. 16 w + 15, its lanes consecutive complex columns (two
+  // 256-byte halves of each row)
   float2 cz[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i)
-    cz[i] = (R < n && jc0 + i < n) ? __ldcg(reinterpret_cast<const float2*>(af + (int64_t)R * ldf + 2 * (int64_t)(jc0 + i)))
-                                   : make_float2(0.f, 0.f);
+  for (int i = 0; i < 32; ++i) {
+    const int R = r0 + 16 * warp + (i >> 1), jc = c0 + 32 * (i & 1) + lane;
+    cz[i] = (R < n && jc < n) ? __ldcg(reinterpret_cast<const float2*>(af + (int64_t)R * ldf + 2 * (int64_t)jc))
+                              : make_float2(0.f, 0.f);
+  }
   // the last commit covers every MMA of the CTA
   if (tid == 0 && !failed() && n_stages > 0) {
     const int last = n_stages - 1;
@@ -532,7 +708,14 @@ __global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64
   }
   __syncthreads();
   tc::fence_after_sync();
-  if (!failed()) {
+  const bool ok = !failed();   // no writer is left: the same value in every thread
+  if (ok) {
+    // the products (tensor-memory lane = tile row; warp w: lanes 32 (w mod 4).., real columns
+    // 64 (w / 4)..) into a shared tile over the stage buffers, which the finished MMAs no
+    // longer read
+    float* T = reinterpret_cast<float*>(base);
+    const int lq = warp & 3, ch = warp >> 2;
+    const int r = 32 * lq + lane;
     const uint32_t tl = (uint32_t)(32 * lq) << 16;
 #pragma unroll
     for (int cb = 0; cb < 64; cb += 16) {
@@ -540,16 +723,18 @@ __global__ void __launch_bounds__(256, 2) lu_gemm_tc_kernel(cpx<float>* a, int64
       float v[16], w[16];
       tc::tmem_ld16x2(tmem + tl + (uint32_t)col, tmem + tl + (uint32_t)(kUN + col), v, w);
 #pragma unroll
-      for (int i = 0; i < 16; i += 2) {
-        const int e = (cb + i) / 2;              // complex column within the segment
-        cz[e].x -= v[i] + w[i];
-        cz[e].y -= v[i + 1] + w[i + 1];
-      }
+      for (int i = 0; i < 16; i += 4)
+        *reinterpret_cast<float4*>(T + r * kUPitch + col + i) =
+            make_float4(v[i] + w[i], v[i + 1] + w[i + 1], v[i + 2] + w[i + 2], v[i + 3] + w[i + 3]);
     }
-    if (R < n) {
+    __syncthreads();
 #pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (jc0 + i < n) *reinterpret_cast<float2*>(af + (int64_t)R * ldf + 2 * (int64_t)(jc0 + i)) = cz[i];
+    for (int i = 0; i < 32; ++i) {
+      const int rr = 16 * warp + (i >> 1), h = i & 1;
+      const int R = r0 + rr, jc = c0 + 32 * h + lane;
+      const float2 d = *reinterpret_cast<const float2*>(T + rr * kUPitch + 64 * h + 2 * lane);
+      if (R < n && jc < n)
+        *reinterpret_cast<float2*>(af + (int64_t)R * ldf + 2 * (int64_t)jc) = make_float2(cz[i].x - d.x, cz[i].y - d.y);
     }
   } else if (tid == 0) {
     atomicOr(err, 8);
@@ -786,6 +971,52 @@ int lu_panel_grid(int rows, int sms) {
   return (int)std::max<int64_t>(1, g);
 }
 
+// the most rows of a panel of kb columns that one cluster of cs CTAs holds in shared
+// memory (the opt-in limit per CTA less room for the kernel's static words)
+template <class T>
+int cluster_panel_rows(int cs, int kb, int smem_optin) {
+  const int64_t avail = std::max<int64_t>(0, (int64_t)smem_optin - 4096);
+  return (int)std::min<int64_t>((int64_t)cs * (avail / ((int64_t)kb * (int64_t)sizeof(cpx<T>) + 1)), 1 << 30);
+}
+
+// panels of at most this many rows run on the cluster: there its cheaper barrier wins
+// (GB300, 16 CTAs: 12.2 ms against 15.0 for the whole 2,000^2 complex64 factorization);
+// on longer panels the elimination work of its 16 CTAs outweighs it (8,000^2 with every
+// panel that fits on the cluster: 90.3 ms against 83.6 on the grid)
+constexpr int kClusterPanelRows = 2048;
+
+// cluster size of the cluster panels on this device: 16 CTAs where the device schedules
+// such a cluster with the shared memory it needs, else 8, else 0 (grid panels only)
+template <class T>
+int choose_panel_cluster(int smem_optin, cudaStream_t s) {
+  const int dyn = std::max(0, smem_optin - 4096);
+  if (cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kPanelThreads);
+    cfg.dynamicSmemBytes = (size_t)dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, lu_panel_cluster_kernel<T>, &cfg) == cudaSuccess && nc >= 1) return c;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
 template <class T>
 int lu_max_order(int sms) {
   return (int)((int64_t)sms * (int64_t)kPanelSmem / ((int64_t)kNb * sizeof(cpx<T>)));
@@ -832,20 +1063,45 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
                                                          panel_smem0)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int smem_optin = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  const int cs = w.panel_cluster ? choose_panel_cluster<T>(smem_optin, s) : 0;
+  w.diag[3] = 0;
+  w.diag[4] = cs;
   for (int pnl = 0; pnl < n_panels; ++pnl) {
     const int k = pnl * kNb, kb = std::min(kNb, n - k), R = n - k;
-    const int G = std::min(lu_panel_grid<T>(R, sms), per_sm * sms);   // all CTAs resident
-    const int per = (R + G - 1) / G;
-    const size_t psmem = (size_t)per * kb * sizeof(cpx<T>) + (size_t)per + 16;
     PanelArgs<T> pa{a, ld, n, k, kb, w.cand_val, w.cand_row, reinterpret_cast<cpx<T>*>(w.cand_data),
                     w.bar + pnl, w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl, w.err};
-    void* args[] = {&pa};
-    w.diag[0] = G;
-    w.diag[1] = per_sm;
-    w.diag[2] = (int)psmem;
-    if ((e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<T>, dim3(G), dim3(kPanelThreads), args, psmem,
-                                         s)) != cudaSuccess)
-      return e;
+    if (cs > 0 && R <= std::min(kClusterPanelRows, cluster_panel_rows<T>(cs, kb, smem_optin))) {
+      const int per = (R + cs - 1) / cs;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(kPanelThreads);
+      cfg.dynamicSmemBytes = (size_t)per * kb * sizeof(cpx<T>) + (size_t)per + 16;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if ((e = cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T>, pa)) != cudaSuccess) return e;
+      ++w.diag[3];
+    } else {
+      const int G = std::min(lu_panel_grid<T>(R, sms), per_sm * sms);   // all CTAs resident
+      const int per = (R + G - 1) / G;
+      const size_t psmem = (size_t)per * kb * sizeof(cpx<T>) + (size_t)per + 16;
+      void* args[] = {&pa};
+      w.diag[0] = G;
+      w.diag[1] = per_sm;
+      w.diag[2] = (int)psmem;
+      if ((e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<T>, dim3(G), dim3(kPanelThreads), args,
+                                           psmem, s)) != cudaSuccess)
+        return e;
+    }
     lu_moves_kernel<T><<<(n + 15) / 16, 256, 0, s>>>(a, ld, n, w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl);
     const int rest = n - k - kb;
     if (rest > 0) {

@@ -108,6 +108,40 @@ def test_tensor_core_update_against_fp32_pipe(torch_cuda, n):
     assert infos[0]["residual"] < 50.0 * eps * np.sqrt(n) * growth
 
 
+@pytest.mark.parametrize("n,dtype", [(300, "complex64"), (1030, "complex128"), (2500, "complex128"),
+                                     (4000, "complex64")])
+def test_cluster_panel_against_grid_panel(torch_cuda, n, dtype):
+    """The LU panel on one thread-block cluster (candidates and pivot rows read from the
+    peers' shared memory, the cluster's hardware barrier) against the cooperative grid
+    form (option SOLVE_GRID_PANEL): every row sees the same operations in the same order
+    and every pivot is the same decision, so the two solutions are equal to the bit.  At
+    2500 and 4000 the first panels are longer than the cluster form takes (2048 rows)
+    and run on the grid, the others on the cluster."""
+    torch = torch_cuda
+    from paper_1404_7357_gb300 import cfft
+    tdt = getattr(torch, dtype)
+    a = _matrix(n, 31 + n, "zero_diagonal")
+    b = np.random.default_rng(7 + n).standard_normal(n) + 1j * np.random.default_rng(8 + n).standard_normal(n)
+    xs, infos = {}, {}
+    for grid in (0, 1):
+        ctx = cfft.Context(0)
+        ctx.set_option(cfft.OPT_SOLVE_GRID_PANEL, grid)
+        z = torch.tensor(a, dtype=tdt, device="cuda:0")
+        v = torch.tensor(b, dtype=tdt, device="cuda:0")
+        xs[grid] = ctx.solve_reduced(z, v).cpu().numpy()
+        infos[grid] = ctx.solve_info()
+        del z, v, ctx
+    n_panels = (n + 63) // 64
+    print("n", n, dtype, "cluster panels", infos[0]["cluster_panels"], "of", n_panels, "cluster",
+          infos[0]["panel_cluster"], "ms factor cluster %.2f grid %.2f" % (infos[0]["ms_factor"],
+                                                                          infos[1]["ms_factor"]))
+    assert infos[1]["cluster_panels"] == 0 and infos[1]["panel_cluster"] == 0
+    assert infos[0]["panel_cluster"] in (8, 16) and 0 < infos[0]["cluster_panels"] <= n_panels
+    if n > 2048:
+        assert infos[0]["cluster_panels"] < n_panels        # mixed: the first panels on the grid
+    assert np.array_equal(xs[0], xs[1])
+
+
 def test_singular_matrix_is_reported(torch_cuda):
     torch = torch_cuda
     from paper_1404_7357_gb300 import cfft
