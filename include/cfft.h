@@ -144,8 +144,9 @@ typedef enum {
  *                64..16384 (64..8192 in FP64) dividing P, else CFFT_ERR_ARG
  *                at the tabulation.  Default (<= 0): automatic
  *   SOLVE_GRID_PANEL  a value > 0 runs every LU panel of cfft_solve_reduced
- *                as a cooperative launch over the grid (a bounded barrier
- *                in global memory per column) instead of on one
+ *                as a cooperative launch over the grid (pivot keys
+ *                published and polled in global memory per column) instead
+ *                of on one
  *                thread-block cluster for panels of at most 2048 rows */
 typedef enum {
   CFFT_OPT_N_ALPHA = 0,
@@ -600,8 +601,9 @@ cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const vo
  * of n x n entries, kept until the next solve or destroy).  v: device, [n]
  * right-hand side; i_out: device, [n] solution.  Element types: complex128
  * when complex128 != 0, else complex64.
- * mode 0: LU with partial pivoting (|re| + |im| of the column, ties to the
- *         lowest row) in the matrix's own precision.
+ * mode 0: LU with partial pivoting (|re| + |im| of the column, compared on
+ *         the leading 32 bits of its double, ties to the lowest row) in the
+ *         matrix's own precision.
  * mode 1 (complex128 only): the LU of a complex64 copy, then iterative
  *         refinement in float64 against z: x += LU^-1 (v - z x) until the
  *         correction falls below float64 resolution or the residual stops
@@ -610,9 +612,10 @@ cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const vo
  * search and elimination, one barrier per column: the hardware barrier of one
  * thread-block cluster of 16 or 8 CTAs, candidates and pivot rows read from
  * the peers' shared memory, for panels of at most 2048 rows that fit that
- * cluster's shared memory; otherwise a cooperative launch over the grid with
- * a bounded barrier in global memory), the panel's row moves applied to the
- * whole matrix, a
+ * cluster's shared memory; otherwise a cooperative launch over the grid whose
+ * CTAs publish their candidates' pivot keys, tagged with the column, in
+ * global memory and poll them with a bound), the panel's row moves applied to
+ * the whole matrix, a
  * triangular solve for
  * the panel's rows and a complex matrix product for the trailing matrix.  In
  * complex64 that product runs on the tensor cores (three TF32 products, FP32

@@ -2232,7 +2232,7 @@ cfft_status lu_factor_checked(cfft_ctx* ctx, int n, const LuWork& w) {
   int flag = 0;
   CFFT_CUDA(cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "LU flag");
   CFFT_CUDA(cudaStreamSynchronize(ctx->stream), "LU factorization");
-  if (flag & 2) return fail(ctx, CFFT_ERR_TIMEOUT, "LU panel: a grid-barrier wait ran past its bound");
+  if (flag & 2) return fail(ctx, CFFT_ERR_TIMEOUT, "LU panel: a poll of the pivot keys ran past its bound");
   if (flag & 4) return fail(ctx, CFFT_ERR_NUMERIC, "LU: the reduced matrix is singular (zero pivot)");
   if (flag & 8) return fail(ctx, CFFT_ERR_TIMEOUT, "LU update: a tensor-core wait ran past its bound");
   return CFFT_OK;

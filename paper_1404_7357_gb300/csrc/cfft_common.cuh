@@ -431,11 +431,11 @@ cudaError_t cartesian_fill(const cpx<T>* table, int p, int m, double x0, double 
 struct LuWork {
   int2* moves;         // [panels][2 * panel width] row moves (source, destination)
   int* n_moves;        // [panels]
-  double* cand_val;    // [2][SMs] pivot candidates of the panel CTAs (value, row, entries)
-  int* cand_row;
-  void* cand_data;     // [2][SMs][panel width] complex, the element type
-  unsigned* bar;       // [panels] grid-barrier counters
-  int* err;            // bit 1: barrier wait ran out; bit 2: zero pivot; bit 3: a tensor-core
+  double* cand_val;    // [2][SMs] 64-bit words: the panel CTAs' pivot keys with column tags
+  int* cand_row;       // (unused)
+  void* cand_data;     // [2][SMs][panel width] complex, the element type: the candidates' entries
+  unsigned* bar;       // (unused)
+  int* err;            // bit 1: a key poll ran out; bit 2: zero pivot; bit 3: a tensor-core
                        // wait of the trailing update ran out
   int* diag;           // host: [5] panel grid, resident CTAs per SM, shared bytes of the last grid
                        // panel; panels run on one cluster, CTAs per cluster (0: none)

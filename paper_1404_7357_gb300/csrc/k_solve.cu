@@ -6,16 +6,18 @@
 //
 // LU (right-looking, row-major, panels of kNb columns):
 //   panel    one launch over the panel's rows: per column, every CTA proposes its
-//            largest |re| + |im| among the rows not yet chosen, a barrier, every
-//            CTA takes the same pivot (ties: lowest row), reads the pivot row and
+//            largest |re| + |im| among the rows not yet chosen (compared on the
+//            leading 32 bits of the double, ties: lowest row), a barrier, every
+//            CTA takes the same pivot, reads the pivot row and
 //            eliminates the column from its own rows.  Pivoting is logical: rows
 //            stay where they are and the chosen rows are recorded; one barrier per
 //            column.  A panel of at most 2048 rows (that fits the shared memory
 //            of one thread-block cluster, 16 CTAs, else 8) runs on the cluster:
 //            the CTAs exchange candidates and the pivot row through distributed
 //            shared memory with the cluster's hardware barrier.  Longer panels
-//            run cooperatively over the grid, with a bounded grid barrier in
-//            global memory.
+//            run cooperatively over the grid: each CTA publishes its candidate's
+//            key with a column tag in global memory, and polling the keys (with
+//            a bound) is the grid barrier.
 //   moves    the panel's pivot rows go to rows k..k+kb-1 and the rows they
 //            displace to the vacated places, as a list of (source, destination)
 //            row moves applied to every column of the matrix.
@@ -27,7 +29,7 @@
 // forward (unit L) and backward (U) substitution: per panel one launch whose
 // CTAs each solve the small diagonal block (one warp) and update their rows.
 //
-// Every grid-barrier wait is bounded: a wait that runs out sets an error bit,
+// Every poll of the grid panel is bounded: a poll that runs out sets an error bit,
 // and every CTA leaves the panel (the host then returns CFFT_ERR_TIMEOUT).  The
 // cluster barrier is the hardware's own: every CTA of the cluster is resident by
 // construction, and every CTA takes every barrier (the pivot, and so any early
@@ -64,45 +66,53 @@ __device__ __forceinline__ cpx<T> crecip(cpx<T> z) {
   return cdiv(mk((T)1, (T)0), z);
 }
 
-// grid barrier of a cooperative launch (all CTAs resident): arrive, then poll with a bound
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* s_fail) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    unsigned polls = 0;
-    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
-      if (++polls > kBarrierPolls) {
-        *s_fail = 1;
-        break;
-      }
-      if (polls > 256) __nanosleep(32);   // poll tightly first: the wait is usually short
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *reinterpret_cast<volatile int*>(s_fail) == 0;
-}
-
 template <class T>
 struct PanelArgs {
   cpx<T>* a;
   int64_t ld;
   int n, k, kb;
-  double* cand_val;   // [2][grid] per-CTA pivot candidates (value), double-buffered by column
-  int* cand_row;      // [2][grid] (row)
+  unsigned long long* slot;  // [2][grid] per-CTA pivot key | column tag, by column parity
   cpx<T>* cand_data;  // [2][grid][kNb] the candidate rows' remaining panel entries
-  unsigned* bar;      // barrier counter of this panel, zero at launch
   int2* moves;        // (source row, destination row), at most 2 kb
   int* n_moves;
   int* err;           // bit 1: a barrier wait ran out; bit 2: zero pivot
 };
 
-__device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int oi) {
-  if (ov > v || (ov == v && oi < i)) {
-    v = ov;
-    i = oi;
+// pivot key of row `row` with |re| + |im| = metric: the leading 32 bits of the metric (a
+// non-negative double, so its bits order like its value: exponent and 20 mantissa bits),
+// then the lower row (rows below 65535); the low 16 bits stay free for a column tag.  The
+// largest key is the pivot, so the choice does not depend on how the rows are split
+// between CTAs; 0 stands for no candidate.
+__device__ __forceinline__ unsigned long long pivot_key(double metric, int row) {
+  return (((unsigned long long)__double_as_longlong(metric) >> 32) << 32) |
+         ((unsigned long long)(0xFFFFu - (unsigned)row) << 16);
+}
+__device__ __forceinline__ int key_row(unsigned long long key) { return 0xFFFF - (int)((key >> 16) & 0xFFFFu); }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// the largest key of this CTA's rows not chosen yet in column j (every thread gets it)
+template <class T, int kWarps>
+__device__ __forceinline__ unsigned long long cta_best_key(const cpx<T>* rows, const unsigned char* chosen,
+                                                           int nr, int kb, int j, int lo,
+                                                           unsigned long long* wk) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long best = 0;
+  for (int i = tid; i < nr; i += blockDim.x) {
+    if (chosen[i]) continue;
+    const cpx<T> v = rows[i * kb + j];
+    best = umax64(best, pivot_key(fabs((double)v.re) + fabs((double)v.im), lo + i));
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
+  if (lane == 0) wk[warp] = best;
+  __syncthreads();
+  unsigned long long b = wk[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) b = umax64(b, wk[w]);
+  __syncthreads();   // wk is rewritten at the next column
+  return b;
 }
 
 // the panel's row moves from its pivots (one thread): rows k+j <- pivot j; the rows of
@@ -135,11 +145,16 @@ __device__ void panel_record_moves(const PanelArgs<T>& p, const int* s_piv) {
   *p.n_moves = nm;
 }
 
-// One panel of kb columns on rows k..n-1.  Each CTA holds its slice of rows in shared
-// memory for the whole panel; per column it stages its best candidate (value, row, the
-// row's remaining entries) in global memory, and after the barrier every CTA reads all
-// candidates and takes the same pivot row.  The staging is double-buffered by column, so
-// a CTA that is one column ahead never overwrites what a slower CTA still reads.
+// One panel of kb columns on rows k..n-1, cooperative over the grid.  Each CTA holds its
+// slice of rows in shared memory for the whole panel.  Per column it stages its best
+// candidate's remaining entries in global memory, then publishes its pivot key tagged with
+// the column (one 64-bit store after a fence); warp 0 of every CTA polls the G keys of the
+// column until all carry the tag (the poll is the grid barrier, and it delivers the
+// candidates), every CTA takes the largest key as the pivot and reads that row's entries.
+// Keys and entries are double-buffered by column parity: a CTA publishes column j + 2 only
+// after it has seen every key of column j + 1, which each CTA publishes after its reads of
+// column j.  Every poll is bounded; a CTA whose poll runs out leaves the panel, and the
+// others then run out on its missing keys.
 template <class T>
 __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p) {
   constexpr int kWarps = kPanelThreads / 32;
@@ -151,92 +166,71 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(PanelArgs<T> p)
   cpx<T>* rows = reinterpret_cast<cpx<T>*>(smem_raw);                       // [per][kb]
   unsigned char* chosen = smem_raw + (size_t)per * kb * sizeof(cpx<T>);     // [per]
   __shared__ cpx<T> prow[kNb];
-  __shared__ double wv[kWarps];
-  __shared__ int wi[kWarps];
+  __shared__ unsigned long long wk[kWarps];
+  __shared__ unsigned long long s_win;
   __shared__ int s_piv[kNb];
-  __shared__ int s_fail, s_p, s_w;
+  __shared__ int s_fail;
   for (int e = tid; e < nr * kb; e += blockDim.x)
     rows[e] = p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb];
   for (int i = tid; i < per; i += blockDim.x) chosen[i] = 0;
   if (tid == 0) s_fail = 0;
   __syncthreads();
-  unsigned target = 0;
   bool ok = true;
   for (int j = 0; j < kb; ++j) {
-    const int buf = j & 1;
-    // this CTA's candidate: largest |re| + |im| in column j among its rows not chosen yet
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = tid; i < nr; i += blockDim.x) {
-      if (chosen[i]) continue;
-      const cpx<T> v = rows[i * kb + j];
-      argmax_merge(best, bi, fabs((double)v.re) + fabs((double)v.im), i);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-      argmax_merge(best, bi, __shfl_xor_sync(0xffffffffu, best, off), __shfl_xor_sync(0xffffffffu, bi, off));
-    if (lane == 0) {
-      wv[warp] = best;
-      wi[warp] = bi;
+    const int buf = (p.k + j) & 1;
+    const unsigned long long tag = (unsigned long long)((p.k + j) & 0xFFFF);
+    const unsigned long long mine = cta_best_key<T, kWarps>(rows, chosen, nr, kb, j, lo, wk);
+    if (mine != 0) {
+      const int bl = key_row(mine) - lo;
+      for (int t = tid; t < kb - j; t += blockDim.x)
+        p.cand_data[((size_t)buf * G + g) * kNb + t] = rows[bl * kb + j + t];
     }
     __syncthreads();
     if (tid == 0) {
-      double v = wv[0];
-      int r = wi[0];
-      for (int w = 1; w < kWarps; ++w) argmax_merge(v, r, wv[w], wi[w]);
-      wv[0] = v;
-      wi[0] = r;
-      p.cand_val[buf * G + g] = v;
-      p.cand_row[buf * G + g] = r < nr ? lo + r : 0x7fffffff;
+      __threadfence();   // the entries before the key
+      *reinterpret_cast<volatile unsigned long long*>(p.slot + buf * G + g) = mine | tag;
+    }
+    if (warp == 0) {
+      unsigned long long kmax = 0;
+      bool fine = true;
+      for (int t = lane; t < G && fine; t += 32) {
+        const volatile unsigned long long* sp = reinterpret_cast<const volatile unsigned long long*>(p.slot + buf * G + t);
+        unsigned polls = 0;
+        unsigned long long x = *sp;
+        while ((x & 0xFFFFull) != tag) {
+          if (++polls > kBarrierPolls) {
+            fine = false;
+            break;
+          }
+          if (polls > 256) __nanosleep(32);
+          x = *sp;
+        }
+        kmax = umax64(kmax, x & ~0xFFFFull);
+      }
+      const bool all_fine = __all_sync(0xffffffffu, fine);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) kmax = umax64(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+      __threadfence();   // the winner's entries after its key
+      if (lane == 0) {
+        s_win = kmax;
+        if (!all_fine) s_fail = 1;
+      }
     }
     __syncthreads();
-    const int bl = wi[0];
-    if (bl < nr)
-      for (int t = tid; t < kb - j; t += blockDim.x)
-        p.cand_data[((size_t)buf * G + g) * kNb + t] = rows[bl * kb + j + t];
-    target += (unsigned)G;
-    if (!grid_barrier(p.bar, target, &s_fail)) {
+    if (s_fail) {
       ok = false;
       break;
     }
-    // the pivot: best candidate over all CTAs (the same choice in every CTA)
-    if (warp == 0) {
-      double v = -1.0;
-      int r = 0x7fffffff, w = -1;
-      for (int t = lane; t < G; t += 32) {
-        const double cv = __ldcg(p.cand_val + buf * G + t);
-        const int cr = __ldcg(p.cand_row + buf * G + t);
-        if (cv > v || (cv == v && cr < r)) {
-          v = cv;
-          r = cr;
-          w = t;
-        }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-        const int orow = __shfl_xor_sync(0xffffffffu, r, off), ow = __shfl_xor_sync(0xffffffffu, w, off);
-        if (ov > v || (ov == v && orow < r)) {
-          v = ov;
-          r = orow;
-          w = ow;
-        }
-      }
-      if (lane == 0) {
-        if (!(v > 0.0) && g == 0) atomicOr(p.err, 4);
-        const bool valid = r >= p.k && r < p.n && w >= 0;
-        s_p = valid ? r : -1;
-        s_w = valid ? w : -1;
-      }
-    }
-    __syncthreads();
-    const int pr = s_p;
-    if (pr < 0) {   // no row left (cannot happen with n - k >= kb); leave the panel
+    const unsigned long long win = s_win;
+    const int pr = win != 0 ? key_row(win) : -1;
+    if (!(pr >= p.k && pr < p.n)) {   // no row left (cannot happen with n - k >= kb)
       if (tid == 0 && g == 0) atomicOr(p.err, 4);
       ok = false;
       break;
     }
-    for (int t = tid; t < kb - j; t += blockDim.x) prow[t] = ldcg(p.cand_data + ((size_t)buf * G + s_w) * kNb + t);
+    if ((win >> 32) == 0 && tid == 0 && g == 0) atomicOr(p.err, 4);   // a zero pivot
+    const int w = (pr - p.k) / per;   // the CTA whose candidate it is
+    for (int t = tid; t < kb - j; t += blockDim.x) prow[t] = ldcg(p.cand_data + ((size_t)buf * G + w) * kNb + t);
     if (tid == 0) {
       if (pr >= lo && pr < hi) chosen[pr - lo] = 1;
       s_piv[j] = pr;
@@ -286,14 +280,9 @@ __device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(p)), "r"(rank));
   return r;
 }
-__device__ __forceinline__ double ld_cluster_f64(uint32_t a) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_cluster_s32(uint32_t a) {
-  int v;
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+__device__ __forceinline__ unsigned long long ld_cluster_u64(uint32_t a) {
+  unsigned long long v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
   return v;
 }
 __device__ __forceinline__ cpx<float> ld_cluster_cpx(const cpx<float>*, uint32_t a) {
@@ -309,9 +298,9 @@ __device__ __forceinline__ cpx<double> ld_cluster_cpx(const cpx<double>*, uint32
 
 // One panel of kb columns on rows k..n-1, the grid being one cluster of G CTAs.  Each CTA
 // holds its slice of rows in shared memory for the whole panel.  Per column it posts its
-// best candidate (value, row) in its own shared memory, the cluster barrier, then every
-// CTA reads the G candidates and takes the same pivot, and reads the pivot row from the
-// owner's shared memory.  The candidate slots are double-buffered by column: a CTA writes
+// best pivot key in its own shared memory, the cluster barrier, then every CTA reads the
+// G keys and takes the largest (the same pivot as the grid form), and reads the pivot row
+// from the owner's shared memory.  The candidate slots are double-buffered by column: a CTA writes
 // the slot of column j + 2 only after the barrier of column j + 1, which every CTA passes
 // after its reads of column j.  A chosen row is never written again in the panel, so the
 // pivot row is read while its owner eliminates its other rows.  A last cluster barrier
@@ -327,12 +316,10 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_cluster_kernel(PanelAr
   cpx<T>* rows = reinterpret_cast<cpx<T>*>(smem_raw);                       // [per][kb]
   unsigned char* chosen = smem_raw + (size_t)per * kb * sizeof(cpx<T>);     // [per]
   __shared__ cpx<T> prow[kNb];
-  __shared__ double wv[kWarps];
-  __shared__ int wi[kWarps];
+  __shared__ unsigned long long wk[kWarps];
   __shared__ int s_piv[kNb];
-  __shared__ double s_cv[2];   // this CTA's candidate of the column (value), by column parity
-  __shared__ int s_cr[2];      // (row; INT_MAX: none)
-  __shared__ int s_p, s_w;
+  __shared__ unsigned long long s_ck[2];   // this CTA's key of the column, by column parity
+  __shared__ unsigned long long s_win;
   for (int e = tid; e < nr * kb; e += blockDim.x)
     rows[e] = p.a[(int64_t)(lo + e / kb) * p.ld + p.k + e % kb];
   for (int i = tid; i < per; i += blockDim.x) chosen[i] = 0;
@@ -340,66 +327,29 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_cluster_kernel(PanelAr
   bool ok = true;
   for (int j = 0; j < kb; ++j) {
     const int buf = j & 1;
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = tid; i < nr; i += blockDim.x) {
-      if (chosen[i]) continue;
-      const cpx<T> v = rows[i * kb + j];
-      argmax_merge(best, bi, fabs((double)v.re) + fabs((double)v.im), i);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-      argmax_merge(best, bi, __shfl_xor_sync(0xffffffffu, best, off), __shfl_xor_sync(0xffffffffu, bi, off));
-    if (lane == 0) {
-      wv[warp] = best;
-      wi[warp] = bi;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double v = wv[0];
-      int r = wi[0];
-      for (int w = 1; w < kWarps; ++w) argmax_merge(v, r, wv[w], wi[w]);
-      s_cv[buf] = v;
-      s_cr[buf] = r < nr ? lo + r : 0x7fffffff;
-    }
+    const unsigned long long mine = cta_best_key<T, kWarps>(rows, chosen, nr, kb, j, lo, wk);
+    if (tid == 0) s_ck[buf] = mine;
     cluster_sync_all();
-    // the pivot: best candidate over the cluster (the same choice in every CTA)
+    // the pivot: the largest key over the cluster (the same choice in every CTA)
     if (warp == 0) {
-      double v = -1.0;
-      int r = 0x7fffffff, w = -1;
-      if (lane < G) {
-        v = ld_cluster_f64(cluster_addr(&s_cv[buf], lane));
-        r = ld_cluster_s32(cluster_addr(&s_cr[buf], lane));
-        w = lane;
-      }
+      unsigned long long kmax = lane < G ? ld_cluster_u64(cluster_addr(&s_ck[buf], lane)) : 0ull;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-        const int orow = __shfl_xor_sync(0xffffffffu, r, off), ow = __shfl_xor_sync(0xffffffffu, w, off);
-        if (ov > v || (ov == v && orow < r)) {
-          v = ov;
-          r = orow;
-          w = ow;
-        }
-      }
-      if (lane == 0) {
-        if (!(v > 0.0) && g == 0) atomicOr(p.err, 4);
-        const bool valid = r >= p.k && r < p.n && w >= 0;
-        s_p = valid ? r : -1;
-        s_w = valid ? w : -1;
-      }
+      for (int off = 16; off > 0; off >>= 1) kmax = umax64(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+      if (lane == 0) s_win = kmax;
     }
     __syncthreads();
-    const int pr = s_p;
-    if (pr < 0) {   // no row left (cannot happen with n - k >= kb): every CTA stops here
+    const unsigned long long win = s_win;
+    const int pr = win != 0 ? key_row(win) : -1;
+    if (!(pr >= p.k && pr < p.n)) {   // no row left (cannot happen with n - k >= kb): every CTA stops here
       if (tid == 0 && g == 0) atomicOr(p.err, 4);
       ok = false;
       break;
     }
+    if ((win >> 32) == 0 && tid == 0 && g == 0) atomicOr(p.err, 4);   // a zero pivot
     {
-      // the pivot row's entries j.. from its owner (its local row pr - lo_w, lo_w >= k)
-      const int w = s_w;
-      const int lrow = pr - (p.k + min(w * per, R));
+      // the pivot row's entries j.. from its owner (its local row pr - lo_w, lo_w = k + w per)
+      const int w = (pr - p.k) / per;
+      const int lrow = pr - (p.k + w * per);
       const cpx<T>* src = rows + (size_t)lrow * kb + j;
       for (int t = tid; t < kb - j; t += blockDim.x) prow[t] = ld_cluster_cpx(src, cluster_addr(src + t, w));
     }
@@ -1027,7 +977,9 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
   const int sms = current_sm_count();
   const int n_panels = (n + kNb - 1) / kNb;
   if (lu_panel_grid<T>(n, sms) > sms) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(w.bar, 0, (size_t)n_panels * sizeof(unsigned), s);
+  if (n > 65535) return cudaErrorInvalidValue;   // rows and column tags are 16-bit fields of the pivot keys
+  // every panel CTA's key slots start with a tag no column has (0xFFFF)
+  cudaError_t e = cudaMemsetAsync(w.cand_val, 0xFF, (size_t)2 * sms * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -1072,8 +1024,9 @@ cudaError_t lu_factor(cpx<T>* a, int64_t ld, int n, const LuWork& w, cudaStream_
   w.diag[4] = cs;
   for (int pnl = 0; pnl < n_panels; ++pnl) {
     const int k = pnl * kNb, kb = std::min(kNb, n - k), R = n - k;
-    PanelArgs<T> pa{a, ld, n, k, kb, w.cand_val, w.cand_row, reinterpret_cast<cpx<T>*>(w.cand_data),
-                    w.bar + pnl, w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl, w.err};
+    PanelArgs<T> pa{a, ld, n, k, kb, reinterpret_cast<unsigned long long*>(w.cand_val),
+                    reinterpret_cast<cpx<T>*>(w.cand_data), w.moves + (size_t)pnl * 2 * kNb, w.n_moves + pnl,
+                    w.err};
     if (cs > 0 && R <= std::min(kClusterPanelRows, cluster_panel_rows<T>(cs, kb, smem_optin))) {
       const int per = (R + cs - 1) / cs;
       cudaLaunchConfig_t cfg = {};
