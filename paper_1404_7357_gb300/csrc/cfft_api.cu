@@ -242,8 +242,14 @@ struct SeriesChoice {
   int series, order;
 };
 
+// remainder bound the automatic order holds the contour-factor series to, relative to the
+// summed magnitudes of the transform's inputs: 1e-13 in FP64; 2^-22 in FP32-mixed, below the
+// rounding of the float32 transform that follows (about log2(L) 2^-24 of the same sum, 8e-7
+// at L = 16384)
+constexpr double kSeriesTolFp64 = 1e-13, kSeriesTolFp32 = 0x1p-22;
+
 SeriesChoice choose_series(double x, bool fp64, int order_req, double opt) {
-  const double tol = fp64 ? 1e-13 : 1e-7;
+  const double tol = fp64 ? kSeriesTolFp64 : kSeriesTolFp32;
   const int mode = opt > 0 ? (int)opt : 0;   // 0 automatic, 1 Taylor, 2 Chebyshev
   if (order_req >= 0) return {mode == 2 ? 1 : 0, order_req};
   const int nt = auto_taylor(x, tol);
