@@ -600,7 +600,9 @@ cfft_status cfft_port_currents(cfft_ctx* ctx, int n_elements, int port, const vo
  * cfft_fill_reduced_matrix writes it; not modified (the context factors a copy
  * of n x n entries, kept until the next solve or destroy).  v: device, [n]
  * right-hand side; i_out: device, [n] solution.  Element types: complex128
- * when complex128 != 0, else complex64.
+ * when complex128 != 0, else complex64.  n is at most the order whose panel
+ * rows fit the panel CTAs' shared memory (48,640 in complex64 and 24,320 in
+ * complex128 on 152 SMs) and at most 65535; beyond, CFFT_ERR_ARG.
  * mode 0: LU with partial pivoting (|re| + |im| of the column, compared on
  *         the leading 32 bits of its double, ties to the lowest row) in the
  *         matrix's own precision.

@@ -2282,10 +2282,12 @@ extern "C" cfft_status cfft_solve_reduced(cfft_ctx* ctx, int n, const void* z, i
   cfft_status s = lu_work(ctx, n, &w);
   if (s != CFFT_OK) return s;
   const bool fp64_lu = complex128 && mode == 0;
-  const int n_lim = fp64_lu ? lu_max_order<double>(ctx->sm_count) : lu_max_order<float>(ctx->sm_count);
+  // the panel's rows must fit the shared memory of the panel CTAs, and rows and columns are
+  // 16-bit fields of the pivot keys
+  const int n_lim = std::min(65535, fp64_lu ? lu_max_order<double>(ctx->sm_count) : lu_max_order<float>(ctx->sm_count));
   if (n > n_lim)
     return fail(ctx, CFFT_ERR_ARG, "solve: order " + std::to_string(n) + " exceeds " + std::to_string(n_lim) +
-                " (the panel's rows must fit the shared memory of the panel CTAs)");
+                " (the panel's rows must fit the shared memory of the panel CTAs; pivot keys hold 16-bit rows)");
   const size_t es = fp64_lu ? 16 : 8;
   CFFT_CUDA(ctx->lu_a.ensure((size_t)n * n * es), "alloc LU matrix");
   CFFT_CUDA(ctx->lu_x.ensure((size_t)n * es), "alloc LU vectors");
