@@ -246,6 +246,22 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
  * Takes effect at the next tabulation or fill. */
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value);
 
+/* The series and order of the contour factor exp(beta_I s) that the automatic
+ * choice of cfft_tabulate_reactions takes for x = height * rho_max (Eq. 22 and
+ * its Chebyshev form, option CONTOUR_SERIES): the smallest order N whose
+ * remainder bound, relative to the summed magnitudes of the transform's
+ * inputs, is at most 1e-13 (CFFT_FP64) or 2^-22 (CFFT_FP32_MIXED); Taylor:
+ * x^(N+1) / (N+1)! e^x, Chebyshev: e^a 2 sum_{m>N} I_m(a) with a = x / 2.
+ * series_opt as the option CONTOUR_SERIES (<= 0: the series with fewer
+ * transforms, Taylor on a tie; 1 Taylor; 2 Chebyshev).  Out: *series 0
+ * Taylor, 1 Chebyshev; *order N; *n_ffts the transforms per (pair, harmonic,
+ * residue class of the outputs): N + 1 for Taylor, N + 2 for Chebyshev (the
+ * nodes beyond beta_p form one of them).  Host only: needs no context and no
+ * device.  CFFT_ERR_ARG for x < 0 or not finite, a bad precision, a NULL
+ * output, or no order up to 64 that reaches the bound. */
+cfft_status cfft_contour_series_order(double x, cfft_precision precision, int series_opt, int* series,
+                                      int* order, int* n_ffts);
+
 /* Tabulate Z_ab,q(rho_r) for all MBF pairs (a, b), harmonics q = -q_max..q_max
  * and rho_r = r * rho_max / (n_rho - 1), r = 0..n_rho-1:
  *   Z'_ab(rho, phi) = sum_q Z_ab,q(rho) exp(i q phi)               (Eq. 9)

@@ -25,7 +25,8 @@ STATUS = {0: "CFFT_OK", 1: "CFFT_ERR_ARG", 2: "CFFT_ERR_STATE", 3: "CFFT_ERR_OOM
 # every symbol include/cfft.h declares
 EXPORTS = ["cfft_create", "cfft_destroy", "cfft_last_error", "cfft_set_substrate",
            "cfft_set_mbf_spectra_strip", "cfft_set_mbf_spectra", "cfft_build_contour",
-           "cfft_set_option", "cfft_tabulate_reactions", "cfft_get_table", "cfft_copy_table",
+           "cfft_set_option", "cfft_contour_series_order", "cfft_tabulate_reactions", "cfft_get_table",
+           "cfft_copy_table",
            "cfft_fill_reduced_matrix", "cfft_fill_reduced_matrix_host", "cfft_get_info",
            "cfft_debug_buffer", "cfft_synchronize", "cfft_backproject_static",
            "cfft_get_derivative_table", "cfft_fill_backward", "cfft_tabulate_batch",
@@ -102,6 +103,7 @@ def _load():
         "cfft_set_mbf_spectra": ([P, I, P, P, P, P, I, P], I),
         "cfft_build_contour": ([P, I, D, D, D, I], I),
         "cfft_set_option": ([P, I, D], I),
+        "cfft_contour_series_order": ([D, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "cfft_tabulate_reactions": ([P, I, D, I, I, I], I),
         "cfft_get_table": ([P, ctypes.POINTER(P), ctypes.POINTER(L), ctypes.POINTER(I)], I),
         "cfft_copy_table": ([P, P, L, I], I),
@@ -143,6 +145,19 @@ _lib = _load()
 
 def lib():
     return _lib
+
+
+def contour_series_order(x, precision, series_opt=0):
+    """(series, order, transforms) of the contour factor that the automatic choice of
+    cfft_tabulate_reactions takes for x = height * rho_max: series 0 Taylor, 1 Chebyshev
+    (cfft_contour_series_order; host only, no device needed)."""
+    s, o, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = _lib.cfft_contour_series_order(float(x), int(precision), int(series_opt), ctypes.byref(s),
+                                        ctypes.byref(o), ctypes.byref(f))
+    if st != 0:
+        raise CfftError(st, "contour_series_order: x must be finite and >= 0, the precision valid, "
+                            "and some order up to 64 must reach the bound")
+    return s.value, o.value, f.value
 
 
 def _ptr(a):

@@ -1803,6 +1803,18 @@ cfft_status cfft_build_contour(cfft_ctx* ctx, int n, double beta_max, double bet
   return CFFT_OK;
 }
 
+cfft_status cfft_contour_series_order(double x, cfft_precision precision, int series_opt, int* series,
+                                      int* order, int* n_ffts) {
+  if (!series || !order || !n_ffts || !std::isfinite(x) || !(x >= 0.0)) return CFFT_ERR_ARG;
+  if (precision != CFFT_FP64 && precision != CFFT_FP32_MIXED) return CFFT_ERR_ARG;
+  const SeriesChoice sc = choose_series(x, precision == CFFT_FP64, -1, (double)series_opt);
+  if (sc.order < 0) return CFFT_ERR_ARG;
+  *series = sc.series;
+  *order = sc.order;
+  *n_ffts = sc.order + (sc.series == 1 ? 2 : 1);
+  return CFFT_OK;
+}
+
 cfft_status cfft_set_option(cfft_ctx* ctx, cfft_option key, double value) {
   if (!ctx) return CFFT_ERR_ARG;
   if ((int)key < 0 || (int)key >= kNumOptions) return fail(ctx, CFFT_ERR_ARG, "unknown option");
